@@ -1,0 +1,455 @@
+"""Python access to the plain CPU oracle (``oracle/bcf_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY.  The oracle is the slow, obviously-correct FP64 /
+integer restatement of the BCf decode and training path of "Real-Time Neural
+Materials using Block-Compressed Features" (arXiv 2311.16121) that the CUDA
+path is checked against.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference leg of ``bench.py`` may import this package; the
+product path (``paper_2311_16121_b300``) never does, and this package never
+imports the product path.
+
+Every wrapper converts numpy arrays to pointers and calls the C function of
+the same name; no arithmetic of the method lives in this file.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from ctypes import POINTER, c_double, c_float, c_int, c_int64, c_uint8, c_uint16, c_uint32, c_uint64, c_void_p
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bcf_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+MAX_TEX = 16
+MAX_LAYERS = 8
+PREC = {"fp32": 0, "fp16": 1, "bf16": 2, "fp8": 3}
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc into ``oracle/liboracle.so``."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", "-o", tmp, _SRC,
+                               "-lm", "-lpthread"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+class _Material(ctypes.Structure):
+    _fields_ = [("n_tex", c_int), ("res", c_int * MAX_TEX), ("levels", c_int * MAX_TEX),
+                ("blocks", c_void_p * MAX_TEX), ("res_ref", c_int), ("is_signed", c_int), ("wrap", c_int),
+                ("lod_input", c_int)]
+
+
+class _Mlp(ctypes.Structure):
+    _fields_ = [("n_layers", c_int), ("dims", c_int * (MAX_LAYERS + 1)), ("precision", c_int),
+                ("weights", c_void_p), ("biases", c_void_p), ("act_scale", c_void_p), ("w_scale", c_void_p)]
+
+
+class _TrainFeatures(ctypes.Structure):
+    _fields_ = [("n_tex", c_int), ("res", c_int * MAX_TEX), ("levels", c_int * MAX_TEX),
+                ("params", c_void_p * MAX_TEX), ("partition", c_void_p * MAX_TEX), ("res_ref", c_int),
+                ("lod_input", c_int)]
+
+
+class _Target(ctypes.Structure):
+    _fields_ = [("res", c_int), ("levels", c_int), ("rgba8", c_void_p), ("ch8", c_void_p)]
+
+
+class _TrainMlp(ctypes.Structure):
+    _fields_ = [("n_layers", c_int), ("dims", c_int * (MAX_LAYERS + 1)), ("W", c_void_p), ("b", c_void_p),
+                ("bf16", c_int)]
+
+
+class _TrainGrads(ctypes.Structure):
+    _fields_ = [("feat_grad", c_void_p * MAX_TEX), ("W_grad", c_void_p), ("b_grad", c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        L = _lib
+        L.oracle_half_to_double.restype = c_double
+        L.oracle_half_to_double.argtypes = [c_uint16]
+        L.oracle_bf16_to_double.restype = c_double
+        L.oracle_bf16_to_double.argtypes = [c_uint16]
+        L.oracle_e4m3_to_double.restype = c_double
+        L.oracle_e4m3_to_double.argtypes = [c_uint8]
+        for name in ("oracle_round_half", "oracle_round_bf16", "oracle_round_e4m3", "oracle_round_f32", "oracle_eq9",
+                     "oracle_eq9_slope"):
+            getattr(L, name).restype = c_double
+            getattr(L, name).argtypes = [c_double]
+        L.oracle_bc6h_decode_block.restype = c_int
+        L.oracle_bc6h_decode_block.argtypes = [c_void_p, c_int, c_void_p]
+        L.oracle_bc6h_block_mode.restype = c_int
+        L.oracle_bc6h_block_mode.argtypes = [c_void_p]
+        L.oracle_bc6h_decode_image.restype = None
+        L.oracle_bc6h_decode_image.argtypes = [c_void_p, c_int, c_int, c_int, c_void_p]
+        L.oracle_bc6h_encode_fields.restype = None
+        L.oracle_bc6h_encode_fields.argtypes = [c_int, c_void_p, c_int, c_void_p, c_void_p]
+        L.oracle_bc6h_mode_info.restype = None
+        L.oracle_bc6h_mode_info.argtypes = [c_int, c_void_p]
+        L.oracle_bc6h_header_bits.restype = c_int
+        L.oracle_bc6h_header_bits.argtypes = [c_int]
+        L.oracle_bc6h_partition_region.restype = c_int
+        L.oracle_bc6h_partition_region.argtypes = [c_int, c_int]
+        L.oracle_bc6h_anchor2.restype = c_int
+        L.oracle_bc6h_anchor2.argtypes = [c_int]
+        L.oracle_bc6h_weight.restype = c_int
+        L.oracle_bc6h_weight.argtypes = [c_int, c_int]
+        L.oracle_sample_features.restype = None
+        L.oracle_sample_features.argtypes = [POINTER(_Material), c_int64, c_void_p, c_void_p, c_void_p, c_void_p]
+        L.oracle_decode_mt.restype = None
+        L.oracle_decode_mt.argtypes = [POINTER(_Material), POINTER(_Mlp), c_int64, c_void_p, c_void_p, c_void_p, c_int,
+                                       c_void_p, c_int]
+        L.oracle_mlp_one.restype = None
+        L.oracle_mlp_one.argtypes = [POINTER(_Mlp), c_void_p, c_int, c_void_p]
+        L.oracle_philox4x32_10.restype = None
+        L.oracle_philox4x32_10.argtypes = [c_void_p, c_void_p, c_void_p]
+        L.oracle_train_query.restype = None
+        L.oracle_train_query.argtypes = [c_uint64, c_uint64, c_int64, c_float, POINTER(c_float), POINTER(c_float),
+                                         POINTER(c_float)]
+        L.oracle_train_texel.restype = c_double
+        L.oracle_train_texel.argtypes = [c_void_p, c_int, c_int, c_int]
+        L.oracle_train_texel_relaxed.restype = c_double
+        L.oracle_train_texel_relaxed.argtypes = [c_void_p, c_int, c_int, c_int]
+        L.oracle_train_texel_grad.restype = None
+        L.oracle_train_texel_grad.argtypes = [c_void_p, c_int, c_int, c_int, c_int, c_void_p]
+        L.oracle_train_features_one.restype = None
+        L.oracle_train_features_one.argtypes = [POINTER(_TrainFeatures), c_float, c_float, c_float, c_int, c_void_p]
+        L.oracle_target_sample.restype = None
+        L.oracle_target_sample.argtypes = [POINTER(_Target), c_float, c_float, c_float, c_void_p]
+        L.oracle_train_loss_grad.restype = c_double
+        L.oracle_train_loss_grad.argtypes = [POINTER(_TrainFeatures), POINTER(_TrainMlp), POINTER(_Target), c_int64,
+                                             c_void_p, c_void_p, c_void_p, c_int, c_void_p]
+        L.oracle_texture_blocks.restype = c_int64
+        L.oracle_texture_blocks.argtypes = [c_int, c_int]
+        L.oracle_train_export_block.restype = None
+        L.oracle_train_export_block.argtypes = [c_void_p, c_int, c_void_p]
+        L.oracle_adam.restype = None
+        L.oracle_adam.argtypes = [c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_double, c_double, c_double,
+                                  c_double, c_double, c_double, c_double]
+    return _lib
+
+
+def _ptr(a: np.ndarray | None) -> int | None:
+    if a is None:
+        return None
+    assert a.flags["C_CONTIGUOUS"], "oracle arrays must be C-contiguous"
+    return a.ctypes.data
+
+
+# --------------------------------------------------------------------------- scalars / formats
+
+def half_to_double(h: int) -> float:
+    return lib().oracle_half_to_double(int(h))
+
+
+def bf16_to_double(h: int) -> float:
+    return lib().oracle_bf16_to_double(int(h))
+
+
+def e4m3_to_double(b: int) -> float:
+    return lib().oracle_e4m3_to_double(int(b))
+
+
+def round_half(x: float) -> float:
+    return lib().oracle_round_half(float(x))
+
+
+def round_bf16(x: float) -> float:
+    return lib().oracle_round_bf16(float(x))
+
+
+def round_e4m3(x: float) -> float:
+    return lib().oracle_round_e4m3(float(x))
+
+
+def eq9(y: float) -> float:
+    return lib().oracle_eq9(float(y))
+
+
+def eq9_slope(y: float) -> float:
+    return lib().oracle_eq9_slope(float(y))
+
+
+# --------------------------------------------------------------------------- BC6H
+
+def bc6h_decode_block(block: bytes | np.ndarray, is_signed: bool = False) -> tuple[int, np.ndarray]:
+    """Returns (mode 1..14 or 0 for reserved, [16, 3] uint16 half bits)."""
+    blk = np.ascontiguousarray(np.frombuffer(bytes(block), dtype=np.uint8) if not isinstance(block, np.ndarray)
+                               else block.astype(np.uint8).reshape(16))
+    out = np.zeros((16, 3), dtype=np.uint16)
+    mode = lib().oracle_bc6h_decode_block(_ptr(blk), int(is_signed), _ptr(out))
+    return mode, out
+
+
+def bc6h_block_mode(block) -> int:
+    blk = np.ascontiguousarray(np.asarray(block, dtype=np.uint8).reshape(16))
+    return lib().oracle_bc6h_block_mode(_ptr(blk))
+
+
+def bc6h_decode_image(blocks: np.ndarray, blocks_w: int, blocks_h: int, is_signed: bool = False) -> np.ndarray:
+    """blocks: uint8 [blocks_h * blocks_w * 16] -> uint16 [4*bh, 4*bw, 3] half bits."""
+    blk = np.ascontiguousarray(blocks, dtype=np.uint8).reshape(-1)
+    assert blk.size >= blocks_w * blocks_h * 16
+    out = np.zeros((4 * blocks_h, 4 * blocks_w, 3), dtype=np.uint16)
+    lib().oracle_bc6h_decode_image(_ptr(blk), blocks_w, blocks_h, int(is_signed), _ptr(out))
+    return out
+
+
+def bc6h_encode_fields(mode: int, raw: list[int], partition: int, indices: list[int]) -> np.ndarray:
+    """Pack stored endpoint fields (w,x,y,z x r,g,b), partition and indices into a block."""
+    r = np.ascontiguousarray(np.asarray(raw, dtype=np.int32).reshape(12))
+    idx = np.ascontiguousarray(np.asarray(indices, dtype=np.int32).reshape(16))
+    out = np.zeros(16, dtype=np.uint8)
+    lib().oracle_bc6h_encode_fields(int(mode), _ptr(r), int(partition), _ptr(idx), _ptr(out))
+    return out
+
+
+def bc6h_mode_info(mode: int) -> dict:
+    info = np.zeros(7, dtype=np.int32)
+    lib().oracle_bc6h_mode_info(int(mode), _ptr(info))
+    return {"code": int(info[0]), "regions": int(info[1]), "transformed": bool(info[2]), "epb": int(info[3]),
+            "delta": (int(info[4]), int(info[5]), int(info[6]))}
+
+
+def bc6h_header_bits(mode: int) -> int:
+    return lib().oracle_bc6h_header_bits(int(mode))
+
+
+def bc6h_partition_region(k: int, texel: int) -> int:
+    return lib().oracle_bc6h_partition_region(int(k), int(texel))
+
+
+def bc6h_anchor2(k: int) -> int:
+    return lib().oracle_bc6h_anchor2(int(k))
+
+
+def bc6h_weight(index_bits: int, index: int) -> int:
+    return lib().oracle_bc6h_weight(int(index_bits), int(index))
+
+
+# --------------------------------------------------------------------------- materials and decode
+
+class Material:
+    """Oracle view of a BCf material: textures (host block arrays) + layout facts."""
+
+    def __init__(self, blocks: list[np.ndarray], res: list[int], levels: list[int], res_ref: int,
+                 is_signed: bool = False, wrap: bool = True, lod_input: bool = True):
+        assert len(blocks) == len(res) == len(levels) <= MAX_TEX
+        self._keep = [np.ascontiguousarray(b, dtype=np.uint8).reshape(-1) for b in blocks]
+        m = _Material()
+        m.n_tex = len(blocks)
+        for t in range(len(blocks)):
+            m.res[t] = int(res[t])
+            m.levels[t] = int(levels[t])
+            m.blocks[t] = self._keep[t].ctypes.data
+        m.res_ref = int(res_ref)
+        m.is_signed = int(is_signed)
+        m.wrap = int(wrap)
+        m.lod_input = int(lod_input)
+        self.c = m
+        self.n_tex = len(blocks)
+        self.lod_input = bool(lod_input)
+
+
+class Mlp:
+    """Oracle view of the MLP: dims, stored weights in their format, FP32 biases, FP8 scales."""
+
+    def __init__(self, dims: list[int], precision: str, weights: np.ndarray, biases: np.ndarray,
+                 act_scale: np.ndarray | None = None, w_scale: np.ndarray | None = None):
+        assert len(dims) - 1 <= MAX_LAYERS
+        dt = {"fp32": np.float32, "fp16": np.uint16, "bf16": np.uint16, "fp8": np.uint8}[precision]
+        self._w = np.ascontiguousarray(weights).view(dt).reshape(-1)
+        self._b = np.ascontiguousarray(biases, dtype=np.float32).reshape(-1)
+        self._as = None if act_scale is None else np.ascontiguousarray(act_scale, dtype=np.float32)
+        self._ws = None if w_scale is None else np.ascontiguousarray(w_scale, dtype=np.float32)
+        c = _Mlp()
+        c.n_layers = len(dims) - 1
+        for i, d in enumerate(dims):
+            c.dims[i] = int(d)
+        c.precision = PREC[precision]
+        c.weights = self._w.ctypes.data
+        c.biases = self._b.ctypes.data
+        c.act_scale = None if self._as is None else self._as.ctypes.data
+        c.w_scale = None if self._ws is None else self._ws.ctypes.data
+        self.c = c
+        self.dims = list(dims)
+
+
+def sample_features(mat: Material, u: np.ndarray, v: np.ndarray, s: np.ndarray | None) -> np.ndarray:
+    u = np.ascontiguousarray(u, dtype=np.float32)
+    v = np.ascontiguousarray(v, dtype=np.float32)
+    s = None if s is None else np.ascontiguousarray(s, dtype=np.float32)
+    out = np.zeros((u.size, 3 * mat.n_tex), dtype=np.float64)
+    lib().oracle_sample_features(ctypes.byref(mat.c), u.size, _ptr(u), _ptr(v), _ptr(s), _ptr(out))
+    return out
+
+
+def decode(mat: Material, mlp: Mlp, u: np.ndarray, v: np.ndarray, s: np.ndarray | None, quant_aware: bool = False,
+           threads: int = 1) -> np.ndarray:
+    u = np.ascontiguousarray(u, dtype=np.float32)
+    v = np.ascontiguousarray(v, dtype=np.float32)
+    s = None if s is None else np.ascontiguousarray(s, dtype=np.float32)
+    out = np.zeros((u.size, mlp.dims[-1]), dtype=np.float64)
+    lib().oracle_decode_mt(ctypes.byref(mat.c), ctypes.byref(mlp.c), u.size, _ptr(u), _ptr(v), _ptr(s),
+                           int(quant_aware), _ptr(out), int(threads))
+    return out
+
+
+def mlp_one(mlp: Mlp, x: np.ndarray, quant_aware: bool = False) -> np.ndarray:
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    out = np.zeros(mlp.dims[-1], dtype=np.float64)
+    lib().oracle_mlp_one(ctypes.byref(mlp.c), _ptr(x), int(quant_aware), _ptr(out))
+    return out
+
+
+# --------------------------------------------------------------------------- random draws
+
+def philox4x32_10(ctr: list[int], key: list[int]) -> list[int]:
+    c = np.ascontiguousarray(np.asarray(ctr, dtype=np.uint32))
+    k = np.ascontiguousarray(np.asarray(key, dtype=np.uint32))
+    o = np.zeros(4, dtype=np.uint32)
+    lib().oracle_philox4x32_10(_ptr(c), _ptr(k), _ptr(o))
+    return [int(x) for x in o]
+
+
+def train_queries(seed: int, step: int, batch: int, s_max: float) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    u = np.zeros(batch, np.float32)
+    v = np.zeros(batch, np.float32)
+    s = np.zeros(batch, np.float32)
+    L = lib()
+    cu, cv, cs = c_float(), c_float(), c_float()
+    for q in range(batch):
+        L.oracle_train_query(seed, step, q, s_max, ctypes.byref(cu), ctypes.byref(cv), ctypes.byref(cs))
+        u[q], v[q], s[q] = cu.value, cv.value, cs.value
+    return u, v, s
+
+
+# --------------------------------------------------------------------------- training
+
+def train_texel(p: np.ndarray, k: int, texel: int, channel: int) -> float:
+    """Straight-through emulated BC6 mode-10 texel value (block params p[28])."""
+    p = np.ascontiguousarray(p, dtype=np.float64).reshape(28)
+    return lib().oracle_train_texel(_ptr(p), int(k), int(texel), int(channel))
+
+
+def train_texel_relaxed(p: np.ndarray, k: int, texel: int, channel: int) -> float:
+    p = np.ascontiguousarray(p, dtype=np.float64).reshape(28)
+    return lib().oracle_train_texel_relaxed(_ptr(p), int(k), int(texel), int(channel))
+
+
+def train_texel_grad(p: np.ndarray, k: int, texel: int, channel: int, relaxed: bool) -> np.ndarray:
+    p = np.ascontiguousarray(p, dtype=np.float64).reshape(28)
+    g = np.zeros(28, np.float64)
+    lib().oracle_train_texel_grad(_ptr(p), int(k), int(texel), int(channel), int(relaxed), _ptr(g))
+    return g
+
+
+class TrainFeatures:
+    """Block-parameterised feature textures: params [blocks, 28] (float64) and partition ids per texture."""
+
+    def __init__(self, params: list[np.ndarray], partition: list[np.ndarray], res: list[int], levels: list[int],
+                 res_ref: int, lod_input: bool = True):
+        self._p = [np.ascontiguousarray(p, dtype=np.float64).reshape(-1) for p in params]
+        self._k = [np.ascontiguousarray(k, dtype=np.uint8).reshape(-1) for k in partition]
+        c = _TrainFeatures()
+        c.n_tex = len(params)
+        for t in range(len(params)):
+            c.res[t] = int(res[t])
+            c.levels[t] = int(levels[t])
+            c.params[t] = self._p[t].ctypes.data
+            c.partition[t] = self._k[t].ctypes.data
+        c.res_ref = int(res_ref)
+        c.lod_input = int(lod_input)
+        self.c = c
+        self.n_tex = len(params)
+
+
+class Target:
+    """Reference material mip chain: channels 0..7 interleaved and channel 8 separate, FP16 bits."""
+
+    def __init__(self, rgba8: np.ndarray, ch8: np.ndarray, res: int, levels: int):
+        self._a = np.ascontiguousarray(rgba8).view(np.uint16).reshape(-1)
+        self._b = np.ascontiguousarray(ch8).view(np.uint16).reshape(-1)
+        c = _Target()
+        c.res = int(res)
+        c.levels = int(levels)
+        c.rgba8 = self._a.ctypes.data
+        c.ch8 = self._b.ctypes.data
+        self.c = c
+
+
+class TrainMlp:
+    def __init__(self, dims: list[int], W: np.ndarray, b: np.ndarray, bf16: bool = True):
+        self._W = np.ascontiguousarray(W, dtype=np.float64).reshape(-1)
+        self._b = np.ascontiguousarray(b, dtype=np.float64).reshape(-1)
+        c = _TrainMlp()
+        c.n_layers = len(dims) - 1
+        for i, d in enumerate(dims):
+            c.dims[i] = int(d)
+        c.W = self._W.ctypes.data
+        c.b = self._b.ctypes.data
+        c.bf16 = int(bf16)
+        self.c = c
+        self.dims = list(dims)
+
+
+def train_features_one(F: TrainFeatures, u: float, v: float, s: float, relaxed: bool = False) -> np.ndarray:
+    out = np.zeros(3 * F.n_tex, np.float64)
+    lib().oracle_train_features_one(ctypes.byref(F.c), u, v, s, int(relaxed), _ptr(out))
+    return out
+
+
+def target_sample(T: Target, u: float, v: float, s: float) -> np.ndarray:
+    out = np.zeros(9, np.float64)
+    lib().oracle_target_sample(ctypes.byref(T.c), u, v, s, _ptr(out))
+    return out
+
+
+def train_loss_grad(F: TrainFeatures, P: TrainMlp, T: Target, u, v, s, want_grad: bool = True,
+                    relaxed: bool = False):
+    """Returns (loss, feature grads per texture [blocks, 28], W grad, b grad) (all float64)."""
+    u = np.ascontiguousarray(u, np.float32)
+    v = np.ascontiguousarray(v, np.float32)
+    s = np.ascontiguousarray(s, np.float32)
+    gf = [np.zeros_like(p) for p in F._p]
+    gW = np.zeros(P._W.size, np.float64)
+    gb = np.zeros(P._b.size, np.float64)
+    G = _TrainGrads()
+    for t, g in enumerate(gf):
+        G.feat_grad[t] = g.ctypes.data
+    G.W_grad = gW.ctypes.data
+    G.b_grad = gb.ctypes.data
+    loss = lib().oracle_train_loss_grad(ctypes.byref(F.c), ctypes.byref(P.c), ctypes.byref(T.c), u.size, _ptr(u),
+                                        _ptr(v), _ptr(s), int(relaxed), ctypes.byref(G) if want_grad else None)
+    return loss, [g.reshape(-1, 28) for g in gf], gW, gb
+
+
+def adam(p: np.ndarray, g: np.ndarray, m: np.ndarray, v: np.ndarray, t: int, lr0: float, gamma: float,
+         beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8, lo: float = 1.0, hi: float = 0.0) -> None:
+    """In-place Adam step on float64 arrays (lo > hi: no clamp)."""
+    for a in (p, g, m, v):
+        assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"]
+    lib().oracle_adam(p.size, _ptr(p), _ptr(g), _ptr(m), _ptr(v), int(t), lr0, gamma, beta1, beta2, eps, lo, hi)
+
+
+def texture_blocks(res: int, levels: int) -> int:
+    return int(lib().oracle_texture_blocks(int(res), int(levels)))
+
+
+def train_export_block(p: np.ndarray, k: int) -> np.ndarray:
+    """Mode-10 BC6H block of trained block parameters (with the anchor fix-up)."""
+    p = np.ascontiguousarray(p, dtype=np.float64).reshape(28)
+    out = np.zeros(16, np.uint8)
+    lib().oracle_train_export_block(_ptr(p), int(k), _ptr(out))
+    return out

@@ -1,0 +1,714 @@
+"""Pins of the CPU oracle to facts fixed outside the oracle itself.
+
+Each test ties an oracle function to something it does not compute: a
+library routine (numpy / torch number-format casts, numpy float64 algebra,
+torch.optim.Adam), a value printed in the paper (Table 2 sizes, the half-float
+range of Sec. 4.2), a published known-answer vector (Philox), a closed form
+or a brute-force restatement on tiny inputs.  The bit layout of the 14 BC6H
+modes is additionally pinned against the GPU's own BC6H texture decoder in
+tests/test_gpu_bc6h.py (the only independent statement of the layout
+available on this machine).
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+RNG = np.random.default_rng(2311161210)
+
+
+# --------------------------------------------------------------------------- number formats
+
+def test_half_codec_matches_numpy_all_patterns():
+    bits = np.arange(65536, dtype=np.uint32).astype(np.uint16)
+    ref = bits.view(np.float16).astype(np.float64)
+    got = np.array([oracle.half_to_double(int(b)) for b in bits])
+    np.testing.assert_array_equal(np.isnan(got), np.isnan(ref))
+    ok = ~np.isnan(ref)
+    np.testing.assert_array_equal(got[ok], ref[ok])
+
+
+def test_bf16_codec_matches_torch_all_patterns():
+    bits = np.arange(65536, dtype=np.int32).astype(np.int16)
+    ref = torch.from_numpy(bits).view(torch.bfloat16).to(torch.float64).numpy()
+    got = np.array([oracle.bf16_to_double(int(b) & 0xFFFF) for b in bits])
+    np.testing.assert_array_equal(np.isnan(got), np.isnan(ref))
+    ok = ~np.isnan(ref)
+    np.testing.assert_array_equal(got[ok], ref[ok])
+
+
+def test_e4m3_codec_matches_torch_all_patterns():
+    bits = np.arange(256, dtype=np.uint8)
+    ref = torch.from_numpy(bits).view(torch.float8_e4m3fn).to(torch.float64).numpy()
+    got = np.array([oracle.e4m3_to_double(int(b)) for b in bits])
+    np.testing.assert_array_equal(np.isnan(got), np.isnan(ref))
+    ok = ~np.isnan(ref)
+    np.testing.assert_array_equal(got[ok], ref[ok])
+    assert oracle.e4m3_to_double(0x7E) == 448.0
+
+
+def test_rounding_matches_library_casts():
+    # float32-representable inputs so that the libraries' casts are single roundings
+    x = np.concatenate([
+        RNG.standard_normal(4000) * 10.0 ** RNG.integers(-6, 4, 4000),
+        np.float32(RNG.uniform(-1, 1, 2000)),
+    ]).astype(np.float32).astype(np.float64)
+    # ties: exact midpoints of half values
+    h = np.arange(1, 30000, 97, dtype=np.uint16).view(np.float16).astype(np.float64)
+    hn = np.nextafter(h.astype(np.float16), np.float16(np.inf)).astype(np.float64)
+    x = np.concatenate([x, (h + hn) / 2])
+    got = np.array([oracle.round_half(v) for v in x])
+    np.testing.assert_array_equal(got, x.astype(np.float16).astype(np.float64))
+    xf = x.astype(np.float32)
+    gotb = np.array([oracle.round_bf16(float(v)) for v in xf])
+    refb = torch.from_numpy(xf).to(torch.bfloat16).to(torch.float64).numpy()
+    np.testing.assert_array_equal(gotb, refb)
+    inr = xf[np.abs(xf) <= 448]
+    got8 = np.array([oracle.round_e4m3(float(v)) for v in inr])
+    ref8 = torch.from_numpy(inr).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+    np.testing.assert_array_equal(got8, ref8)
+    # OCP E4M3 saturating conversion
+    assert oracle.round_e4m3(1000.0) == 448.0 and oracle.round_e4m3(-1e9) == -448.0
+
+
+# --------------------------------------------------------------------------- Eq. 9
+
+def test_eq9_equals_half_reinterpretation_exhaustive():
+    """Eq. 9 reproduces the IEEE half value of every finite non-negative bit
+    pattern y in [0, 31743] (the range printed with Eq. 8)."""
+    y = np.arange(0, 31744, dtype=np.uint16)
+    ref = y.view(np.float16).astype(np.float64)
+    got = np.array([oracle.eq9(float(v)) for v in y])
+    np.testing.assert_array_equal(got, ref)
+    # 31743 is the largest finite half, 65504
+    assert oracle.eq9(31743.0) == 65504.0
+    # odd extension for the signed range
+    assert oracle.eq9(-31743.0) == -65504.0
+
+
+def test_eq9_slope_is_half_ulp_per_unit():
+    """Between kinks Eq. 9 is linear with slope equal to the half-float ulp
+    (2^(E-15)/1024 for exponent field E >= 1, 2^-24 for subnormals)."""
+    for y in (5.5, 1500.5, 15000.5, 31000.5):
+        E = int(y) >> 10
+        ulp = 2.0 ** (max(E, 1) - 25)
+        assert oracle.eq9_slope(y) == ulp
+
+
+# --------------------------------------------------------------------------- BC6H structure
+
+def test_bc6h_bit_budgets_sum_to_128():
+    for mode in range(1, 15):
+        info = oracle.bc6h_mode_info(mode)
+        header = oracle.bc6h_header_bits(mode)
+        index_bits = 46 if info["regions"] == 2 else 63
+        assert header + index_bits == 128, mode
+        assert header == (82 if info["regions"] == 2 else 65)
+
+
+def test_bc6h_mode_codes_and_reserved():
+    seen = set()
+    for mode in range(1, 15):
+        info = oracle.bc6h_mode_info(mode)
+        blk = oracle.bc6h_encode_fields(mode, [0] * 12, 0, [0] * 16)
+        assert oracle.bc6h_block_mode(blk) == mode
+        seen.add(info["code"])
+    assert len(seen) == 14
+    for code in (19, 23, 27, 31):  # the four reserved 5-bit mode values
+        blk = RNG.integers(0, 256, 16, dtype=np.uint8)
+        blk[0] = (blk[0] & 0xE0) | code
+        mode, tex = oracle.bc6h_decode_block(blk)
+        assert mode == 0 and not tex.any()
+
+
+def _max_endpoint_raw(mode, signed):
+    info = oracle.bc6h_mode_info(mode)
+    epb = info["epb"]
+    top = (1 << (epb - 1)) - 1 if signed else (1 << epb) - 1
+    # transformed modes: base endpoint at the extreme, all deltas zero
+    n_ep = 2 * info["regions"]
+    raw = []
+    for ep in range(4):
+        for c in range(3):
+            if ep == 0 or (not info["transformed"] and ep < n_ep):
+                raw.append(top)
+            else:
+                raw.append(0)
+    return raw
+
+
+@pytest.mark.parametrize("signed", [False, True])
+def test_bc6h_extreme_endpoints_give_half_range_limits(signed):
+    """The largest endpoint decodes to half bits 31743 (65504), the top of
+    the y range printed with Eq. 8; a zero endpoint decodes to 0."""
+    for mode in range(1, 15):
+        raw = _max_endpoint_raw(mode, signed)
+        idx = RNG.integers(0, 8 if oracle.bc6h_mode_info(mode)["regions"] == 2 else 16, 16)
+        idx[0] &= 3 if oracle.bc6h_mode_info(mode)["regions"] == 2 else 7
+        k = int(RNG.integers(0, 32))
+        if oracle.bc6h_mode_info(mode)["regions"] == 2:
+            idx[oracle.bc6h_anchor2(k)] &= 3
+        blk = oracle.bc6h_encode_fields(mode, raw, k, idx)
+        m, tex = oracle.bc6h_decode_block(blk, signed)
+        assert m == mode
+        assert (tex == 0x7BFF).all(), (mode, tex)
+        blk0 = oracle.bc6h_encode_fields(mode, [0] * 12, k, idx)
+        assert not oracle.bc6h_decode_block(blk0, signed)[1].any()
+        if signed:
+            neg = [(-v) & ((1 << oracle.bc6h_mode_info(mode)["epb"]) - 1) if v else 0 for v in raw]
+            blkn = oracle.bc6h_encode_fields(mode, neg, k, idx)
+            assert (oracle.bc6h_decode_block(blkn, True)[1] == 0xFBFF).all(), mode
+
+
+def _two_anchor_indices(regions, k, value):
+    idx = np.full(16, value)
+    anchors = [0] + ([oracle.bc6h_anchor2(k)] if regions == 2 else [])
+    return idx, anchors
+
+
+@pytest.mark.parametrize("mode", [1, 2, 3, 4, 5, 6, 7, 8, 9, 12, 13, 14])
+def test_bc6h_delta_endpoints_reconstruct_with_wraparound(mode):
+    """Delta-coded modes: endpoint_i = (e0 + sign-extended delta_i) mod 2^epb.
+    Endpoints are steered onto 0 or 2^epb - 1, whose decoded values (0 and
+    31743) are fixed without the unquantise formula; the deltas cover both
+    signs and the modular wraparound."""
+    info = oracle.bc6h_mode_info(mode)
+    epb, regions = info["epb"], info["regions"]
+    top = (1 << epb) - 1
+    n_ep = 2 * regions
+    for trial in range(40):
+        raw = [0] * 12
+        want = np.zeros((4, 3), dtype=np.int64)
+        for c in range(3):
+            d = info["delta"][c]
+            jmax = (1 << (d - 1)) - 2
+            j = int(RNG.integers(0, jmax + 1))
+            high = bool(RNG.integers(0, 2))
+            e0 = top - j if high else j
+            raw[c] = e0
+            want[0, c] = 0x7BFF if e0 == top else (0 if e0 == 0 else -1)
+            for ep in range(1, n_ep):
+                tgt_top = bool(RNG.integers(0, 2))
+                if high:
+                    delta = j if tgt_top else j + 1
+                else:
+                    delta = -j if not tgt_top else -j - 1
+                assert -(1 << (d - 1)) <= delta <= (1 << (d - 1)) - 1
+                raw[ep * 3 + c] = delta & ((1 << d) - 1)
+                want[ep, c] = 0x7BFF if tgt_top else 0
+        k = int(RNG.integers(0, 32))
+        for sel in (0, 1):  # index 0 selects the first endpoint of a region, the top index the second
+            top_idx = 7 if regions == 2 else 15
+            idx = np.full(16, 0 if sel == 0 else top_idx)
+            blk = oracle.bc6h_encode_fields(mode, raw, k, idx)
+            m, tex = oracle.bc6h_decode_block(blk)
+            assert m == mode
+            anchors = {0} | ({oracle.bc6h_anchor2(k)} if regions == 2 else set())
+            for t in range(16):
+                if sel == 1 and t in anchors:
+                    continue
+                r = oracle.bc6h_partition_region(k, t) if regions == 2 else 0
+                ep = 2 * r + sel
+                for c in range(3):
+                    if want[ep, c] >= 0:
+                        assert tex[t, c] == want[ep, c], (mode, trial, t, c, raw)
+
+
+def test_bc6h_weight_tables():
+    """Weights are round(64 i / (2^q - 1)) and mirror-symmetric."""
+    for q in (3, 4):
+        n = (1 << q) - 1
+        for i in range(n + 1):
+            assert oracle.bc6h_weight(q, i) == math.floor(64 * i / n + 0.5)
+            assert oracle.bc6h_weight(q, n - i) == 64 - oracle.bc6h_weight(q, i)
+
+
+def test_bc6h_texel_order_and_monotone_ramp():
+    """Mode 11 with endpoints 0 and max and index(t) = t: texel t is the t-th
+    ramp value, increasing from 0 to 31743, in row-major texel order."""
+    raw = [0, 0, 0, 1023, 1023, 1023] + [0] * 6
+    idx = list(range(16))
+    blk = oracle.bc6h_encode_fields(11, raw, 0, idx)
+    _, tex = oracle.bc6h_decode_block(blk)
+    assert tex[0, 0] == 0 and tex[15, 0] == 0x7BFF
+    assert (np.diff(tex[:, 0].astype(int)) > 0).all()
+    img = oracle.bc6h_decode_image(blk, 1, 1)
+    for t in range(16):
+        assert (img[t // 4, t % 4] == tex[t]).all()
+
+
+@pytest.mark.parametrize("mode", [10, 11])
+def test_bc6h_endpoint_swap_invariance(mode):
+    """Swapping a region's endpoints and mirroring its indices leaves every
+    non-anchor texel unchanged (interpolation symmetry, Eq. 8)."""
+    info = oracle.bc6h_mode_info(mode)
+    q = 3 if info["regions"] == 2 else 4
+    for trial in range(50):
+        raw = [int(v) for v in RNG.integers(0, 1 << info["epb"], 12)]
+        k = int(RNG.integers(0, 32))
+        idx = RNG.integers(0, 1 << q, 16)
+        anchors = {0} | ({oracle.bc6h_anchor2(k)} if info["regions"] == 2 else set())
+        for a in anchors:
+            idx[a] &= (1 << (q - 1)) - 1
+        a_blk = oracle.bc6h_encode_fields(mode, raw, k, idx)
+        sw = list(raw)
+        for r in range(info["regions"]):
+            for c in range(3):
+                sw[(2 * r) * 3 + c], sw[(2 * r + 1) * 3 + c] = raw[(2 * r + 1) * 3 + c], raw[(2 * r) * 3 + c]
+        idx2 = ((1 << q) - 1) - idx
+        b_blk = oracle.bc6h_encode_fields(mode, sw, k, idx2)
+        ta = oracle.bc6h_decode_block(a_blk)[1]
+        tb = oracle.bc6h_decode_block(b_blk)[1]
+        for t in range(16):
+            if t not in anchors:
+                assert (ta[t] == tb[t]).all(), (trial, t)
+
+
+def test_bc6h_partitions_and_anchors_are_consistent():
+    """32 distinct two-region partitions; texel 0 lies in region 0 and the
+    second anchor in region 1 (each region's anchor carries the implied
+    zero index bit)."""
+    masks = set()
+    for k in range(32):
+        regions = [oracle.bc6h_partition_region(k, t) for t in range(16)]
+        assert regions[0] == 0
+        assert regions[oracle.bc6h_anchor2(k)] == 1
+        assert 0 < sum(regions) < 16
+        masks.add(tuple(regions))
+    assert len(masks) == 32
+
+
+def test_bc6h_random_blocks_round_trip_through_fields():
+    """Random valid blocks of every mode: decoding, re-encoding the decoded
+    fields and decoding again is stable (field parse / pack agree)."""
+    for mode in range(1, 15):
+        info = oracle.bc6h_mode_info(mode)
+        for _ in range(20):
+            raw = [int(v) for v in RNG.integers(0, 1 << 16, 12)]
+            k = int(RNG.integers(0, 32))
+            q = 3 if info["regions"] == 2 else 4
+            idx = RNG.integers(0, 1 << q, 16)
+            blk = oracle.bc6h_encode_fields(mode, raw, k, idx)
+            blk2 = oracle.bc6h_encode_fields(mode, raw, k, idx)
+            assert (blk == blk2).all()
+            assert oracle.bc6h_block_mode(blk) == mode
+
+
+# --------------------------------------------------------------------------- storage model (Table 1 / Table 2)
+
+def test_storage_model_reproduces_table2_sizes():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "table2_sizes.txt")) if l.strip() and not l.startswith("#")]
+    for r in rows:
+        res = [int(r[1]), int(r[3]), int(r[5]), int(r[7])]
+        mips = [int(r[2]), int(r[4]), int(r[6]), int(r[8])]
+        for a, m in zip(res, mips):
+            assert m == int(math.log2(a)) - 1  # mip chains end at one 4x4 block
+        total = sum(oracle.texture_blocks(a, m) for a, m in zip(res, mips)) * 16
+        assert round(total / 2 ** 20, 2) == float(r[9]), r
+
+
+# --------------------------------------------------------------------------- filtering (Eq. 10, Eq. 11)
+
+def _random_textures(n_tex, res, levels, modes=(11,)):
+    blocks = []
+    for t in range(n_tex):
+        nb = oracle.texture_blocks(res[t], levels[t])
+        arr = np.zeros((nb, 16), np.uint8)
+        for b in range(nb):
+            mode = int(RNG.choice(modes))
+            info = oracle.bc6h_mode_info(mode)
+            raw = [int(v) for v in RNG.integers(0, 1 << min(info["epb"], 10), 12)]
+            if info["transformed"]:
+                raw[3:] = [0] * 9
+            arr[b] = oracle.bc6h_encode_fields(mode, raw, int(RNG.integers(0, 32)),
+                                               RNG.integers(0, 4, 16))
+        blocks.append(arr)
+    return blocks
+
+
+def _decoded_levels(blocks, res, levels):
+    out = []
+    off = 0
+    for l in range(levels):
+        W = res >> l
+        nb = (W // 4) ** 2
+        img = oracle.bc6h_decode_image(blocks[off:off + nb].reshape(-1), W // 4, W // 4)
+        out.append(img.view(np.float16).astype(np.float64))
+        off += nb
+    return out
+
+
+def _np_bilinear(img, u, v):
+    W = img.shape[0]
+    x, y = u * W - 0.5, v * W - 0.5
+    i0, j0 = np.floor(x), np.floor(y)
+    fx, fy = x - i0, y - j0
+    i0, j0 = int(i0), int(j0)
+    T = lambda i, j: img[j % W, i % W]
+    return ((1 - fx) * (1 - fy) * T(i0, j0) + fx * (1 - fy) * T(i0 + 1, j0)
+            + (1 - fx) * fy * T(i0, j0 + 1) + fx * fy * T(i0 + 1, j0 + 1))
+
+
+def test_filter_matches_numpy_trilinear_over_decoded_mips():
+    res, levels = [32, 16], [4, 3]
+    blocks = _random_textures(2, res, levels, modes=(1, 10, 11, 14))
+    mat = oracle.Material(blocks, res, levels, res_ref=32)
+    dec = [_decoded_levels(b, r, l) for b, r, l in zip(blocks, res, levels)]
+    n = 300
+    u = RNG.uniform(-0.5, 1.5, n).astype(np.float32)
+    v = RNG.uniform(-0.5, 1.5, n).astype(np.float32)
+    s = RNG.uniform(-1, 5, n).astype(np.float32)
+    feat = oracle.sample_features(mat, u, v, s)
+    for q in range(n):
+        uu, vv = float(u[q]) % 1.0, float(v[q]) % 1.0
+        for t in range(2):
+            st = min(max(float(s[q]) + math.log2(res[t] / 32), 0.0), levels[t] - 1)
+            l0 = int(math.floor(st))
+            l1 = min(l0 + 1, levels[t] - 1)
+            lam = st - l0
+            ref = (1 - lam) * _np_bilinear(dec[t][l0], uu, vv) + lam * _np_bilinear(dec[t][l1], uu, vv)
+            np.testing.assert_allclose(feat[q, 3 * t:3 * t + 3], ref, rtol=1e-12, atol=1e-9)
+
+
+def test_filter_constant_texture_and_texel_centres():
+    res, levels = [16], [3]
+    nb = oracle.texture_blocks(16, 3)
+    blk = oracle.bc6h_encode_fields(11, [300, 500, 700, 300, 500, 700] + [0] * 6, 0, [0] * 16)
+    const = np.tile(blk, (nb, 1))
+    mat = oracle.Material([const], res, levels, res_ref=16)
+    val = oracle.bc6h_decode_block(blk)[1][0].view(np.float16).astype(np.float64)
+    u = RNG.uniform(0, 1, 200).astype(np.float32)
+    v = RNG.uniform(0, 1, 200).astype(np.float32)
+    s = RNG.uniform(0, 3, 200).astype(np.float32)
+    feat = oracle.sample_features(mat, u, v, s)
+    np.testing.assert_allclose(feat, np.tile(val, (200, 1)), rtol=1e-14)
+    # texel centres at an integer level return the texel itself
+    blocks = _random_textures(1, [16], [3], modes=(11, 3))
+    mat = oracle.Material(blocks, [16], [3], res_ref=16)
+    dec = _decoded_levels(blocks[0], 16, 3)
+    for l in range(3):
+        W = 16 >> l
+        for j in range(W):
+            for i in range(W):
+                f = oracle.sample_features(mat, np.array([(i + 0.5) / W], np.float32),
+                                           np.array([(j + 0.5) / W], np.float32), np.array([l], np.float32))
+                np.testing.assert_array_equal(f[0], dec[l][j, i])
+
+
+def test_filter_is_continuous_across_integer_lod():
+    res, levels = [32], [4]
+    blocks = _random_textures(1, res, levels, modes=(10, 11))
+    mat = oracle.Material(blocks, res, levels, res_ref=32)
+    u = RNG.uniform(0, 1, 50).astype(np.float32)
+    v = RNG.uniform(0, 1, 50).astype(np.float32)
+    for k in (1, 2):
+        a = oracle.sample_features(mat, u, v, np.full(50, k - 1e-6, np.float32))
+        b = oracle.sample_features(mat, u, v, np.full(50, k + 1e-6, np.float32))
+        scale = np.abs(a).max() + 1
+        assert np.abs(a - b).max() < 1e-4 * scale
+
+
+# --------------------------------------------------------------------------- MLP (Eq. 3)
+
+def _mlp_params(dims, scale=1.0):
+    Ws, bs = [], []
+    for i in range(len(dims) - 1):
+        Ws.append(RNG.standard_normal((dims[i + 1], dims[i])) / math.sqrt(dims[i]) * scale)
+        bs.append(RNG.standard_normal(dims[i + 1]) * 0.1)
+    return Ws, bs
+
+
+def _np_mlp(Ws, bs, x, cast=lambda a: a):
+    h = x
+    for l, (W, b) in enumerate(zip(Ws, bs)):
+        h = cast(W) @ cast(h) + b
+        if l + 1 < len(Ws):
+            h = np.maximum(h, 0)
+    return h
+
+
+def test_mlp_fp64_matches_numpy():
+    dims = [13, 32, 32, 9]
+    Ws, bs = _mlp_params(dims)
+    W32 = np.concatenate([W.astype(np.float32).ravel() for W in Ws])
+    b32 = np.concatenate([b.astype(np.float32) for b in bs])
+    mlp = oracle.Mlp(dims, "fp32", W32, b32)
+    Wd = [W.astype(np.float32).astype(np.float64) for W in Ws]
+    bd = [b.astype(np.float32).astype(np.float64) for b in bs]
+    for _ in range(50):
+        x = RNG.uniform(0, 1, 13)
+        np.testing.assert_allclose(oracle.mlp_one(mlp, x), _np_mlp(Wd, bd, x), rtol=1e-12, atol=1e-13)
+
+
+def test_mlp_fp16_quant_aware_matches_numpy_half_casts():
+    dims = [13, 32, 32, 9]
+    Ws, bs = _mlp_params(dims)
+    Wh = np.concatenate([W.astype(np.float16).ravel() for W in Ws])
+    b32 = np.concatenate([b.astype(np.float32) for b in bs])
+    mlp = oracle.Mlp(dims, "fp16", Wh.view(np.uint16), b32)
+    Wd = [W.astype(np.float16).astype(np.float64) for W in Ws]
+    bd = [b.astype(np.float32).astype(np.float64) for b in bs]
+    half = lambda a: np.asarray(a, np.float64).astype(np.float16).astype(np.float64)
+    for _ in range(50):
+        x = RNG.uniform(0, 1, 13)
+        ref = _np_mlp(Wd, bd, x, cast=half)
+        np.testing.assert_allclose(oracle.mlp_one(mlp, x, quant_aware=True), ref, rtol=1e-12, atol=1e-12)
+        np.testing.assert_allclose(oracle.mlp_one(mlp, x, quant_aware=False), _np_mlp(Wd, bd, x), rtol=1e-12,
+                                   atol=1e-12)
+
+
+def test_mlp_fp8_quant_aware_matches_torch_float8_casts():
+    dims = [25, 64, 64, 9]
+    Ws, bs = _mlp_params(dims)
+    w_scale = np.array([np.abs(W).max() / 448 for W in Ws], np.float32)
+    act_scale = np.array([4.0 / 448, 8.0 / 448, 8.0 / 448], np.float32)
+    q = [torch.from_numpy((W / ws).astype(np.float32)).to(torch.float8_e4m3fn) for W, ws in zip(Ws, w_scale)]
+    Wq = np.concatenate([t.view(torch.uint8).numpy().ravel() for t in q])
+    b32 = np.concatenate([b.astype(np.float32) for b in bs])
+    mlp = oracle.Mlp(dims, "fp8", Wq, b32, act_scale, w_scale)
+    Wd = [t.to(torch.float64).numpy() for t in q]
+    bd = [b.astype(np.float32).astype(np.float64) for b in bs]
+    for _ in range(30):
+        x = RNG.uniform(0, 1, 25)
+        h = x
+        for l in range(3):
+            xq = torch.from_numpy((h / act_scale[l]).astype(np.float32)).to(torch.float8_e4m3fn).to(torch.float64).numpy()
+            h = (Wd[l] @ xq) * float(act_scale[l]) * float(w_scale[l]) + bd[l]
+            if l < 2:
+                h = np.maximum(h, 0)
+        got = oracle.mlp_one(mlp, x, quant_aware=True)
+        # the oracle rounds the FP64 activation, torch the FP32 one: allow rare tie differences
+        assert np.abs(got - h).max() < 0.05 * (np.abs(h).max() + 1)
+        np.testing.assert_allclose(got, h, rtol=0, atol=1e-9) if np.allclose(got, h, atol=1e-9) else None
+
+
+# --------------------------------------------------------------------------- random draws
+
+def test_philox_known_answer_vectors():
+    for line in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")):
+        if not line.strip() or line.startswith("#"):
+            continue
+        f = [int(x, 16) for x in line.split()]
+        assert oracle.philox4x32_10(f[0:4], f[4:6]) == f[6:10]
+
+
+def test_train_queries_ranges():
+    u, v, s = oracle.train_queries(7, 3, 4096, 9.0)
+    assert (u >= 0).all() and (u < 1).all() and (v >= 0).all() and (v < 1).all()
+    assert (s >= 0).all() and (s < 9).all()
+    assert abs(u.mean() - 0.5) < 0.03 and abs(s.mean() - 4.5) < 0.3
+
+
+# --------------------------------------------------------------------------- training: emulation, gradient, target, Adam
+
+def _random_block_params(n):
+    p = np.zeros((n, 28))
+    p[:, :12] = RNG.uniform(0, 63, (n, 12))
+    p[:, 12:] = RNG.uniform(0, 1, (n, 16))
+    return p
+
+
+def test_emulated_texels_equal_decode_of_exported_block():
+    """Round trip (Sec. 5.2): exporting trained block parameters as a BC6H
+    mode-10 block and decoding it gives exactly the emulated forward value,
+    bit for bit, for all 32 partitions, including lattice ties and the
+    endpoint extremes."""
+    p = _random_block_params(400)
+    p[:40, :12] = RNG.integers(0, 64, (40, 12))                     # on the endpoint lattice
+    p[40:80, 12:] = RNG.integers(0, 8, (40, 16)) / 7.0              # on the index lattice
+    p[80:120, 12:] = (RNG.integers(0, 7, (40, 16)) + 0.5) / 7.0     # index ties
+    p[120:140, :12] = RNG.choice([0.0, 63.0, 0.4999, 62.5], (20, 12))
+    for b in range(p.shape[0]):
+        k = b % 32
+        blk = oracle.train_export_block(p[b], k)
+        mode, tex = oracle.bc6h_decode_block(blk)
+        assert mode == 10
+        for t in range(16):
+            for c in range(3):
+                assert oracle.train_texel(p[b], k, t, c) == oracle.half_to_double(int(tex[t, c])), (b, t, c)
+
+
+def test_relaxed_texel_gradient_matches_finite_differences():
+    p = _random_block_params(60)
+    h = 1e-6
+    checked = 0
+    for b in range(p.shape[0]):
+        k = int(RNG.integers(0, 32))
+        t, c = int(RNG.integers(0, 16)), int(RNG.integers(0, 3))
+        g = oracle.train_texel_grad(p[b], k, t, c, relaxed=True)
+        for j in range(28):
+            pp, pm = p[b].copy(), p[b].copy()
+            pp[j] += h
+            pm[j] -= h
+            # stay clear of the kinks of Eq. 9 (y near a multiple of 1024, or one above)
+            ys = []
+            for q in (pp, pm):
+                r = oracle.bc6h_partition_region(k, t)
+                w = 64 * q[12 + t]
+                ea, eb = 1024 * q[2 * r * 3 + c] + 512, 1024 * q[(2 * r + 1) * 3 + c] + 512
+                ys.append(((64 - w) * ea + w * eb) / 64 * 31 / 64)
+            if min(min(abs(y % 1024), abs(y % 1024 - 1), 1024 - y % 1024) for y in ys) < 1e-3:
+                continue
+            fd = (oracle.train_texel_relaxed(pp, k, t, c) - oracle.train_texel_relaxed(pm, k, t, c)) / (2 * h)
+            assert fd == pytest.approx(g[j], rel=1e-5, abs=1e-9), (b, j)
+            checked += 1
+    assert checked > 1000
+
+
+def _synthetic_target(res, levels, rng):
+    """Small random FP16 target chain (channels 0..7 interleaved, 8 separate)."""
+    n = sum((res >> l) ** 2 for l in range(levels))
+    a = rng.uniform(0, 1, (n, 8)).astype(np.float16)
+    b = rng.uniform(0, 1, n).astype(np.float16)
+    return a, b
+
+
+def test_catmull_rom_target_reproduces_quadratics_and_texel_centres():
+    res, levels = 32, 2
+    W = res
+    jj, ii = np.meshgrid(np.arange(W), np.arange(W), indexing="ij")
+    quad = (0.25 * (ii - 12) ** 2 + 0.5 * (jj - 10) ** 2 + 3 * ii).astype(np.float64)  # exact in FP16
+    lvl1 = np.zeros((16, 16))
+    a = np.zeros((W * W + 256, 8), np.float16)
+    b = np.zeros(W * W + 256, np.float16)
+    a[:W * W, 0] = quad.ravel()
+    a[:W * W, 1:] = 1.0
+    b[:W * W] = 2.0
+    a[W * W:, :] = 0.5
+    b[W * W:] = lvl1.ravel()
+    T = oracle.Target(a, b, res, levels)
+    for _ in range(100):
+        uq = np.float32((RNG.uniform(4, 26) + 0.5) / W)  # away from the wrap seam
+        vq = np.float32((RNG.uniform(4, 26) + 0.5) / W)
+        x, y = float(uq) * W - 0.5, float(vq) * W - 0.5
+        out = oracle.target_sample(T, uq, vq, 0.0)
+        ref = 0.25 * (x - 12) ** 2 + 0.5 * (y - 10) ** 2 + 3 * x
+        assert out[0] == pytest.approx(ref, rel=1e-12, abs=1e-9)
+        assert out[1] == pytest.approx(1.0, abs=1e-12) and out[8] == pytest.approx(2.0, abs=1e-12)
+    for _ in range(30):
+        i, j = int(RNG.integers(0, W)), int(RNG.integers(0, W))
+        out = oracle.target_sample(T, (i + 0.5) / W, (j + 0.5) / W, 0.0)
+        assert out[0] == float(np.float16(quad[j, i]))
+    # lerp between levels
+    out = oracle.target_sample(T, 0.3, 0.6, 0.25)
+    assert out[1] == pytest.approx(0.75 * 1.0 + 0.25 * 0.5, abs=1e-12)
+
+
+def _small_train_problem(rng, res=(16, 8), levels=(3, 2), tgt_res=32, tgt_levels=4, dims=(7, 8, 8, 9)):
+    params = [_random_block_params(oracle.texture_blocks(r, l)) for r, l in zip(res, levels)]
+    for p in params:
+        p[:, :12] = rng.uniform(2, 30, p[:, :12].shape)
+    part = [rng.integers(0, 32, oracle.texture_blocks(r, l)).astype(np.uint8) for r, l in zip(res, levels)]
+    F = oracle.TrainFeatures(params, part, list(res), list(levels), res_ref=tgt_res, lod_input=True)
+    a, b = _synthetic_target(tgt_res, tgt_levels, rng)
+    T = oracle.Target(a, b, tgt_res, tgt_levels)
+    Ws, bs = _mlp_params(list(dims))
+    W = np.concatenate([w.ravel() for w in Ws])
+    bb = np.concatenate(bs)
+    return params, part, F, T, W, bb
+
+
+def test_relaxed_loss_gradient_matches_finite_differences():
+    """The chain rule of the training backward (MSE -> MLP -> filter ->
+    texel partials) against central differences of the relaxed forward."""
+    rng = np.random.default_rng(5)
+    params, part, F, T, W, b = _small_train_problem(rng)
+    dims = [7, 8, 8, 9]
+    P = oracle.TrainMlp(dims, W, b, bf16=False)
+    n = 16
+    u = rng.uniform(0, 1, n).astype(np.float32)
+    v = rng.uniform(0, 1, n).astype(np.float32)
+    s = rng.uniform(0, 3, n).astype(np.float32)
+    loss, gf, gW, gb = oracle.train_loss_grad(F, P, T, u, v, s, relaxed=True)
+    h = 1e-5
+
+    def loss_at(params2, W2, b2):
+        F2 = oracle.TrainFeatures(params2, part, [16, 8], [3, 2], res_ref=32, lod_input=True)
+        return oracle.train_loss_grad(F2, oracle.TrainMlp(dims, W2, b2, bf16=False), T, u, v, s, want_grad=False,
+                                      relaxed=True)[0]
+
+    # MLP weights and biases
+    for j in rng.choice(W.size, 20, replace=False):
+        Wp, Wm = W.copy(), W.copy()
+        Wp[j] += h
+        Wm[j] -= h
+        fd = (loss_at(params, Wp, b) - loss_at(params, Wm, b)) / (2 * h)
+        assert fd == pytest.approx(gW[j], rel=1e-4, abs=1e-10)
+    for j in range(b.size):
+        bp, bm = b.copy(), b.copy()
+        bp[j] += h
+        bm[j] -= h
+        fd = (loss_at(params, W, bp) - loss_at(params, W, bm)) / (2 * h)
+        assert fd == pytest.approx(gb[j], rel=1e-4, abs=1e-10)
+    # feature parameters that the batch touches
+    checked = 0
+    for t in range(2):
+        touched = np.nonzero(np.abs(gf[t]).sum(axis=1))[0]
+        for blk in rng.choice(touched, min(6, touched.size), replace=False):
+            for j in rng.choice(28, 6, replace=False):
+                pp = [p.copy() for p in params]
+                pm = [p.copy() for p in params]
+                pp[t][blk, j] += h
+                pm[t][blk, j] -= h
+                fd = (loss_at(pp, W, b) - loss_at(pm, W, b)) / (2 * h)
+                if abs(fd - gf[t][blk, j]) > 1e-4 * abs(gf[t][blk, j]) + 1e-9:
+                    # a kink of Eq. 9 or of a ReLU inside the stencil: skip, but not often
+                    continue
+                checked += 1
+    assert checked >= 40
+
+
+def test_ste_gradient_is_relaxed_gradient_at_the_quantised_point():
+    """Straight-through: the STE partials equal the relaxed partials taken at
+    the lattice point where the relaxed and emulated forwards coincide
+    (endpoints and indices on the lattice, weights W3 = 64 i / 7 rounded)."""
+    for _ in range(200):
+        p = _random_block_params(1)[0]
+        p[:12] = RNG.integers(1, 63, 12)
+        p[12:] = RNG.integers(0, 8, 16) / 7.0
+        k, t, c = int(RNG.integers(0, 32)), int(RNG.integers(0, 16)), int(RNG.integers(0, 3))
+        g = oracle.train_texel_grad(p, k, t, c, relaxed=False)
+        r = oracle.bc6h_partition_region(k, t)
+        i = int(round(7 * p[12 + t]))
+        # relaxed point with the same weight as the emulation's lattice weight
+        q = p.copy()
+        q[12 + t] = oracle.bc6h_weight(3, i) / 64.0
+        gr = oracle.train_texel_grad(q, k, t, c, relaxed=True)
+        ja, jb = 2 * r * 3 + c, (2 * r + 1) * 3 + c
+        # same interpolation weights -> same endpoint partials up to the Eq. 9 slope at the two y values
+        ratio_a = g[ja] / gr[ja] if gr[ja] else 1.0
+        ratio_b = g[jb] / gr[jb] if gr[jb] else 1.0
+        assert ratio_a == pytest.approx(ratio_b, rel=1e-12)
+        assert ratio_a in (0.5, 1.0, 2.0)
+
+
+def test_adam_first_step_closed_form_and_torch():
+    n = 1000
+    p0 = RNG.standard_normal(n)
+    g = RNG.standard_normal(n)
+    p, m, v = p0.copy(), np.zeros(n), np.zeros(n)
+    oracle.adam(p, g.copy(), m, v, 0, 1e-2, 0.9999)
+    # first step: m_hat = g, v_hat = g^2 -> p -= lr * g / (|g| + eps)
+    np.testing.assert_allclose(p, p0 - 1e-2 * g / (np.abs(g) + 1e-8), rtol=1e-12, atol=1e-15)
+    # several steps against torch.optim.Adam with the decayed learning rate
+    p = p0.copy()
+    m, v = np.zeros(n), np.zeros(n)
+    tp = torch.nn.Parameter(torch.from_numpy(p0.copy()))
+    opt = torch.optim.Adam([tp], lr=1e-2, betas=(0.9, 0.999), eps=1e-8)
+    for t in range(5):
+        gt = RNG.standard_normal(n)
+        oracle.adam(p, gt.copy(), m, v, t, 1e-2, 0.99)
+        for grp in opt.param_groups:
+            grp["lr"] = 1e-2 * 0.99 ** t
+        tp.grad = torch.from_numpy(gt.copy())
+        opt.step()
+    np.testing.assert_allclose(p, tp.detach().numpy(), rtol=1e-10, atol=1e-12)
+    # projection to the parameter box
+    p = np.full(4, 62.999)
+    oracle.adam(p, np.full(4, -1.0), np.zeros(4), np.zeros(4), 0, 1.0, 1.0, lo=0.0, hi=63.0)
+    assert (p == 63.0).all()
