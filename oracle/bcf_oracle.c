@@ -329,15 +329,17 @@ static int bc6h_unquantize(int comp, int bits, int is_signed)
 static int floor_div64(int v) { return v >= 0 ? v / 64 : -((-v + 63) / 64); }
 
 /* Final scaling to half bits: 31/64 (unsigned) or 31/32 of the magnitude
- * with the sign moved to bit 15 (signed). */
+ * (signed).  For signed values the magnitude is scaled first and the sign
+ * bit is taken from the scaled integer, so a value that scales to 0 gives
+ * +0, never -0. */
 static uint16_t bc6h_finish(int comp, int is_signed)
 {
     if (!is_signed)
         return (uint16_t)((comp * 31) >> 6);
-    int neg = comp < 0;
-    int mag = neg ? -comp : comp;
-    mag = (mag * 31) >> 5;
-    return (uint16_t)((neg ? 0x8000 : 0) | mag);
+    int scaled = comp < 0 ? -(((-comp) * 31) >> 5) : (comp * 31) >> 5;
+    if (scaled < 0)
+        return (uint16_t)(0x8000 | -scaled);
+    return (uint16_t)scaled;
 }
 
 /* Identify the mode (1..14) of a block, or 0 for the four reserved codes. */

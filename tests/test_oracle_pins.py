@@ -165,6 +165,22 @@ def test_bc6h_extreme_endpoints_give_half_range_limits(signed):
             assert (oracle.bc6h_decode_block(blkn, True)[1] == 0xFBFF).all(), mode
 
 
+def test_bc6h_signed_finish_gives_positive_zero():
+    """Signed blocks: the 31/32 scaling is applied to the magnitude before the
+    sign is read back, so a small negative value that scales to 0 decodes to
+    +0 (0x0000), not -0 -- the order of the format definition's finish step,
+    which the GPU texture unit also follows (tests/test_gpu_decode.py)."""
+    # mode 14 (16-bit endpoints, unquantise is the identity): endpoint -1, zero deltas
+    raw = [0xFFFF, 0xFFFF, 0xFFFF] + [0] * 9
+    blk = oracle.bc6h_encode_fields(14, raw, 0, [0] * 16)
+    mode, tex = oracle.bc6h_decode_block(blk, True)
+    assert mode == 14 and not tex.any()
+    # endpoint -2: interpolates to -2 -> magnitude (2 * 31) >> 5 = 1 -> half bits 0x8001
+    raw = [0xFFFE, 0xFFFE, 0xFFFE] + [0] * 9
+    _, tex = oracle.bc6h_decode_block(oracle.bc6h_encode_fields(14, raw, 0, [0] * 16), True)
+    assert (tex == 0x8001).all()
+
+
 def _two_anchor_indices(regions, k, value):
     idx = np.full(16, value)
     anchors = [0] + ([oracle.bc6h_anchor2(k)] if regions == 2 else [])
