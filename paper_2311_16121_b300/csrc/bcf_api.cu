@@ -1,0 +1,255 @@
+// bcf_api.cu -- the libbcf C ABI (include/bcf.h): argument validation, the
+// material metadata and the kernel launches.  No entry point allocates on
+// the decode path; bcf_create_material allocates the small device metadata.
+#include <math.h>
+#include <new>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include "bcf_kernels.h"
+
+namespace bcf {
+
+static thread_local char g_err[512];
+
+void set_error(const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+}
+
+static bcf_status fail(bcf_status st, const char *fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof g_err, fmt, ap);
+    va_end(ap);
+    return st;
+}
+
+static bcf_status cuda_status(cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess)
+        return BCF_OK;
+    return fail(BCF_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+static bool is_pow2(int64_t v) { return v > 0 && (v & (v - 1)) == 0; }
+static int ilog2(int64_t v)
+{
+    int r = 0;
+    while ((1ll << r) < v)
+        ++r;
+    return r;
+}
+static bool aligned(const void *p, int a) { return ((uintptr_t)p % (uintptr_t)a) == 0; }
+static int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+} // namespace bcf
+
+using namespace bcf;
+
+extern "C" {
+
+const char *bcf_status_string(bcf_status s)
+{
+    switch (s) {
+    case BCF_OK: return "ok";
+    case BCF_ERR_INVALID_ARG: return "invalid argument";
+    case BCF_ERR_UNSUPPORTED: return "unsupported";
+    case BCF_ERR_CUDA: return "CUDA error";
+    case BCF_ERR_OOM: return "out of memory";
+    case BCF_ERR_TIMEOUT: return "device wait timed out";
+    case BCF_ERR_DEVICE_CHECK: return "device-side check failed";
+    }
+    return "unknown status";
+}
+
+const char *bcf_last_error(void) { return g_err; }
+
+int bcf_version(void) { return 100; }
+
+bcf_status bcf_decode_bc6h(const void *d_blocks, int32_t blocks_w, int32_t blocks_h, int32_t is_signed, uint16_t *d_out,
+                           bcf_stream stream)
+{
+    if (blocks_w < 0 || blocks_h < 0)
+        return fail(BCF_ERR_INVALID_ARG, "bcf_decode_bc6h: negative size %d x %d", blocks_w, blocks_h);
+    if ((int64_t)blocks_w * blocks_h == 0)
+        return BCF_OK;
+    if ((int64_t)blocks_w * blocks_h > (1ll << 31))
+        return fail(BCF_ERR_INVALID_ARG, "bcf_decode_bc6h: more than 2^31 blocks");
+    if (!d_blocks || !d_out || !aligned(d_blocks, 16) || !aligned(d_out, 8))
+        return fail(BCF_ERR_INVALID_ARG, "bcf_decode_bc6h: null or misaligned pointer");
+    return cuda_status(launch_unpack_image(d_blocks, blocks_w, blocks_h, is_signed != 0, d_out, (cudaStream_t)stream),
+                       "bcf_decode_bc6h launch");
+}
+
+bcf_status bcf_texunit_decode_bc6h(const void *d_blocks, int32_t blocks_w, int32_t blocks_h, int32_t is_signed,
+                                   uint16_t *d_out, bcf_stream stream)
+{
+    if (blocks_w <= 0 || blocks_h <= 0 || blocks_w > 16384 || blocks_h > 16384)
+        return fail(BCF_ERR_INVALID_ARG, "bcf_texunit_decode_bc6h: size %d x %d out of range", blocks_w, blocks_h);
+    if (!d_blocks || !d_out || !aligned(d_blocks, 16) || !aligned(d_out, 8))
+        return fail(BCF_ERR_INVALID_ARG, "bcf_texunit_decode_bc6h: null or misaligned pointer");
+    cudaError_t e = texunit_decode(d_blocks, blocks_w, blocks_h, is_signed != 0, d_out, (cudaStream_t)stream);
+    return e == cudaSuccess ? BCF_OK : BCF_ERR_CUDA;
+}
+
+bcf_status bcf_create_material(const bcf_material_desc *d, bcf_material *out)
+{
+    if (!d || !out)
+        return fail(BCF_ERR_INVALID_ARG, "bcf_create_material: null argument");
+    *out = nullptr;
+    if (d->num_textures < 1 || d->num_textures > BCF_MAX_TEX)
+        return fail(BCF_ERR_INVALID_ARG, "num_textures %d not in [1, %d]", d->num_textures, BCF_MAX_TEX);
+    if (!is_pow2(d->res_ref))
+        return fail(BCF_ERR_INVALID_ARG, "res_ref %d is not a power of two", d->res_ref);
+    MaterialDev M;
+    memset(&M, 0, sizeof M);
+    M.n_tex = d->num_textures;
+    M.is_signed = d->is_signed != 0;
+    M.wrap = d->wrap != 0;
+    M.lod_input = d->lod_input != 0;
+    for (int t = 0; t < M.n_tex; ++t) {
+        const int res = d->res[t];
+        if (!is_pow2(res) || res < 4 || res > 32768)
+            return fail(BCF_ERR_INVALID_ARG, "texture %d: res %d is not a power of two in [4, 32768]", t, res);
+        const int maxl = ilog2(res) - 1;
+        if (d->levels[t] < 1 || d->levels[t] > maxl || d->levels[t] > BCF_MAX_LEVELS)
+            return fail(BCF_ERR_INVALID_ARG, "texture %d: levels %d not in [1, %d]", t, d->levels[t], maxl);
+        if (!d->d_blocks[t] || !aligned(d->d_blocks[t], 16))
+            return fail(BCF_ERR_INVALID_ARG, "texture %d: null or non-16-byte-aligned block pointer", t);
+        TexDev &T = M.tex[t];
+        T.blocks = (const uint4 *)d->d_blocks[t];
+        T.res = res;
+        T.log2res = ilog2(res);
+        T.levels = d->levels[t];
+        T.lod_bias = ilog2(res) - ilog2(d->res_ref);
+        uint32_t off = 0;
+        for (int l = 0; l < BCF_MAX_LEVELS; ++l) {
+            T.level_off[l] = off;
+            if (l < T.levels) {
+                const uint32_t wb = (uint32_t)(res >> l) / 4;
+                off += wb * wb;
+            }
+        }
+    }
+    M.n_in = 3 * M.n_tex + M.lod_input;
+    MlpDev &P = M.mlp;
+    if (d->n_layers < 1 || d->n_layers > BCF_MAX_LAYERS)
+        return fail(BCF_ERR_INVALID_ARG, "n_layers %d not in [1, %d]", d->n_layers, BCF_MAX_LAYERS);
+    if (d->dims[0] != M.n_in)
+        return fail(BCF_ERR_INVALID_ARG, "dims[0] = %d but 3 * textures + lod_input = %d", d->dims[0], M.n_in);
+    if (d->precision < BCF_FP32 || d->precision > BCF_FP8_E4M3)
+        return fail(BCF_ERR_INVALID_ARG, "unknown precision %d", (int)d->precision);
+    if (!d->d_weights || !d->d_biases || !aligned(d->d_weights, 4) || !aligned(d->d_biases, 4))
+        return fail(BCF_ERR_INVALID_ARG, "null or misaligned weights / biases");
+    P.n_layers = d->n_layers;
+    P.precision = d->precision;
+    P.weights = d->d_weights;
+    P.biases = d->d_biases;
+    int woff = 0, boff = 0;
+    const int kq = d->precision == BCF_FP8_E4M3 ? 32 : 16;
+    for (int l = 0; l <= P.n_layers; ++l) {
+        if (d->dims[l] < 1 || d->dims[l] > BCF_MAX_WIDTH)
+            return fail(d->dims[l] < 1 ? BCF_ERR_INVALID_ARG : BCF_ERR_UNSUPPORTED, "dims[%d] = %d not in [1, %d]", l,
+                        d->dims[l], BCF_MAX_WIDTH);
+        P.dims[l] = d->dims[l];
+    }
+    for (int l = 0; l < P.n_layers; ++l) {
+        P.w_off[l] = woff;
+        P.b_off[l] = boff;
+        woff += P.dims[l] * P.dims[l + 1];
+        boff += P.dims[l + 1];
+        P.kpad[l] = round_up(P.dims[l], kq);
+    }
+    for (int l = 0; l < P.n_layers; ++l)
+        P.npad[l] = l + 1 < P.n_layers ? P.kpad[l + 1] : round_up(P.dims[l + 1], 8);
+    for (int l = 0; l < P.n_layers; ++l) {
+        P.act_scale[l] = 1.0f;
+        P.w_scale[l] = 1.0f;
+        P.inv_act_scale[l] = 1.0f;
+        if (d->precision == BCF_FP8_E4M3) {
+            const float a = d->act_scale[l], w = d->w_scale[l];
+            int ea, ew;
+            if (!(a > 0.0f) || !(w > 0.0f) || frexpf(a, &ea) != 0.5f || frexpf(w, &ew) != 0.5f)
+                return fail(BCF_ERR_UNSUPPORTED, "layer %d: FP8 scales must be positive powers of two (got %g, %g)", l,
+                            (double)a, (double)w);
+            P.act_scale[l] = a;
+            P.w_scale[l] = w;
+            P.inv_act_scale[l] = 1.0f / a;
+        }
+    }
+    M.n_out = P.dims[P.n_layers];
+    if (d->precision != BCF_FP32) {
+        P.smem_w_bytes = 0;
+        if (decode_mma_smem_bytes(P) > 200 * 1024)
+            return fail(BCF_ERR_UNSUPPORTED, "MLP too large for the shared-memory tensor-core path");
+    }
+    bcf_material m = new (std::nothrow) bcf_material_s;
+    if (!m)
+        return fail(BCF_ERR_OOM, "host allocation failed");
+    m->host = M;
+    m->dev = nullptr;
+    cudaGetDevice(&m->device);
+    cudaError_t e = cudaMalloc(&m->dev, sizeof(MaterialDev));
+    if (e != cudaSuccess) {
+        delete m;
+        return fail(BCF_ERR_OOM, "cudaMalloc(material metadata): %s", cudaGetErrorString(e));
+    }
+    e = cudaMemcpy(m->dev, &m->host, sizeof(MaterialDev), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(m->dev);
+        delete m;
+        return cuda_status(e, "cudaMemcpy(material metadata)");
+    }
+    *out = m;
+    return BCF_OK;
+}
+
+bcf_status bcf_destroy_material(bcf_material m)
+{
+    if (!m)
+        return BCF_OK;
+    cudaError_t e = cudaFree(m->dev);
+    delete m;
+    return cuda_status(e, "cudaFree(material metadata)");
+}
+
+bcf_status bcf_sample_features(bcf_material m, const float *d_u, const float *d_v, const float *d_s, int64_t n,
+                               float *d_feat, bcf_stream stream)
+{
+    if (!m || n < 0)
+        return fail(BCF_ERR_INVALID_ARG, "bcf_sample_features: null material or n < 0");
+    if (n == 0)
+        return BCF_OK;
+    if (!d_u || !d_v || !d_feat || !aligned(d_u, 4) || !aligned(d_v, 4) || !aligned(d_feat, 4) ||
+        (d_s && !aligned(d_s, 4)))
+        return fail(BCF_ERR_INVALID_ARG, "bcf_sample_features: null or misaligned pointer");
+    return cuda_status(launch_sample_features(m->host, d_u, d_v, d_s, n, d_feat, (cudaStream_t)stream),
+                       "bcf_sample_features launch");
+}
+
+bcf_status bcf_decode_material(bcf_material m, const float *d_u, const float *d_v, const float *d_s, int64_t n,
+                               void *d_out, bcf_precision out_precision, bcf_stream stream)
+{
+    if (!m || n < 0)
+        return fail(BCF_ERR_INVALID_ARG, "bcf_decode_material: null material or n < 0");
+    if (out_precision != BCF_FP32 && out_precision != BCF_FP16)
+        return fail(BCF_ERR_INVALID_ARG, "bcf_decode_material: out_precision must be FP32 or FP16");
+    if (n == 0)
+        return BCF_OK;
+    if (!d_u || !d_v || !d_out || !aligned(d_u, 4) || !aligned(d_v, 4) || !aligned(d_out, 16) ||
+        (d_s && !aligned(d_s, 4)))
+        return fail(BCF_ERR_INVALID_ARG, "bcf_decode_material: null or misaligned pointer");
+    const int fp16 = out_precision == BCF_FP16;
+    cudaError_t e = m->host.mlp.precision == BCF_FP32
+                        ? launch_decode_fp32(m->host, d_u, d_v, d_s, n, d_out, fp16, (cudaStream_t)stream)
+                        : launch_decode_mma(m->host, d_u, d_v, d_s, n, d_out, fp16, (cudaStream_t)stream);
+    return cuda_status(e, "bcf_decode_material launch");
+}
+
+} // extern "C"

@@ -1,0 +1,340 @@
+// bcf_decode.cu -- decode kernels: whole-image BC6H unpack, feature sampling,
+// and the fused query decode (unpack + trilinear filter + MLP, Eq. 3).
+#include <cuda_fp16.h>
+
+#include "bc6h_unpack.cuh"
+#include "bcf_kernels.h"
+#include "bcf_mlp.cuh"
+#include "bcf_sample.cuh"
+
+namespace bcf {
+
+// ------------------------------------------------------------ image unpack
+
+// One thread per block; the CTA decodes up to 64 consecutive blocks of one
+// block row into shared memory, then the four texel rows of that run are
+// written out with coalesced 8-byte stores.
+constexpr int kUnpackRun = 64;
+
+template <bool SGN>
+__global__ void __launch_bounds__(kUnpackRun) k_unpack_image(const uint4 *__restrict__ blocks, int bw, int bh,
+                                                             uint16_t *__restrict__ out)
+{
+    __shared__ __align__(16) uint16_t tile[4][kUnpackRun * 4 * 3];
+    const int runs_per_row = (bw + kUnpackRun - 1) / kUnpackRun;
+    const int by = blockIdx.x / runs_per_row;
+    const int bx0 = (blockIdx.x % runs_per_row) * kUnpackRun;
+    const int nb = min(kUnpackRun, bw - bx0);
+    const int tx = threadIdx.x;
+    if (tx < nb) {
+        const Bc6hBlock blk = load_block(blocks + (size_t)by * bw + bx0 + tx);
+        Bc6hHeader H;
+        bc6h_header(blk, SGN, H);
+#pragma unroll
+        for (int t = 0; t < 16; ++t) {
+            uint32_t r, g, b;
+            bc6h_texel(blk, H, t, SGN, r, g, b);
+            uint16_t *d = &tile[t >> 2][(tx * 4 + (t & 3)) * 3];
+            d[0] = (uint16_t)r;
+            d[1] = (uint16_t)g;
+            d[2] = (uint16_t)b;
+        }
+    }
+    __syncthreads();
+    // each texel row of the run is 24 * nb bytes = 3 * nb 8-byte words, 8-byte aligned in `out`
+    const size_t W = (size_t)bw * 4;
+    const int words = 3 * nb;
+    for (int rr = 0; rr < 4; ++rr) {
+        uint64_t *dst = reinterpret_cast<uint64_t *>(out + ((size_t)(by * 4 + rr) * W + (size_t)bx0 * 4) * 3);
+        const uint64_t *src = reinterpret_cast<const uint64_t *>(&tile[rr][0]);
+        for (int w = tx; w < words; w += blockDim.x)
+            dst[w] = src[w];
+    }
+}
+
+// ---------------------------------------------------------- feature sample
+
+__global__ void __launch_bounds__(128) k_sample_features(MaterialDev M, const float *__restrict__ u,
+                                                         const float *__restrict__ v, const float *__restrict__ s,
+                                                         int64_t n, float *__restrict__ feat)
+{
+    const int nf = 3 * M.n_tex;
+    __shared__ float srow[128 * (3 * BCF_MAX_TEX + 1)];
+    float *row = srow + threadIdx.x * (nf + 1);
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        query_features(M, u[q], v[q], s ? s[q] : 0.0f, row);
+        float *o = feat + q * nf;
+        for (int i = 0; i < nf; ++i)
+            o[i] = row[i];
+    }
+}
+
+// --------------------------------------------------- fused decode, FP32 SIMT
+
+// The plain evaluation: one thread per query, per-query BC6H unpack of the
+// texels it filters, FP32 SIMT MLP with weights broadcast from shared memory.
+template <int D0, int D1, int D2, int D3>
+__global__ void __launch_bounds__(128) k_decode_fp32(MaterialDev M, const float *__restrict__ u,
+                                                     const float *__restrict__ v, const float *__restrict__ s,
+                                                     int64_t n, void *__restrict__ out, int out_fp16)
+{
+    __shared__ float sW[D1 * D0 + D2 * D1 + D3 * D2];
+    __shared__ float sB[D1 + D2 + D3];
+    __shared__ float sX[128 * D0];
+    const float *Wg = (const float *)M.mlp.weights;
+    for (int i = threadIdx.x; i < D1 * D0 + D2 * D1 + D3 * D2; i += blockDim.x)
+        sW[i] = Wg[i];
+    for (int i = threadIdx.x; i < D1 + D2 + D3; i += blockDim.x)
+        sB[i] = M.mlp.biases[i];
+    __syncthreads();
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        float x[D0];
+        float *row = sX + threadIdx.x * D0;
+        query_features(M, u[q], v[q], s ? s[q] : 0.0f, row);
+#pragma unroll
+        for (int i = 0; i < D0; ++i)
+            x[i] = row[i];
+        float h1[D1], h2[D2], y[D3];
+        dense_fp32<D0, D1, true>(sW, sB, x, h1);
+        dense_fp32<D1, D2, true>(sW + D1 * D0, sB + D1, h1, h2);
+        dense_fp32<D2, D3, false>(sW + D1 * D0 + D2 * D1, sB + D1 + D2, h2, y);
+        if (out_fp16) {
+            __half *o = (__half *)out + q * D3;
+#pragma unroll
+            for (int c = 0; c < D3; ++c)
+                o[c] = __float2half_rn(y[c]);
+        } else {
+            float *o = (float *)out + q * D3;
+#pragma unroll
+            for (int c = 0; c < D3; ++c)
+                o[c] = y[c];
+        }
+    }
+}
+
+// Generic FP32 path for any layer count / width: activations in local memory.
+__global__ void __launch_bounds__(128) k_decode_fp32_generic(MaterialDev M, const float *__restrict__ u,
+                                                             const float *__restrict__ v,
+                                                             const float *__restrict__ s, int64_t n,
+                                                             void *__restrict__ out, int out_fp16)
+{
+    const MlpDev &P = M.mlp;
+    const float *Wg = (const float *)P.weights;
+    const int C = P.dims[P.n_layers];
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
+        float a[BCF_MAX_WIDTH], b[BCF_MAX_WIDTH];
+        query_features(M, u[q], v[q], s ? s[q] : 0.0f, a);
+        for (int l = 0; l < P.n_layers; ++l) {
+            const int ni = P.dims[l], no = P.dims[l + 1];
+            for (int o = 0; o < no; ++o) {
+                float acc = P.biases[P.b_off[l] + o];
+                for (int i = 0; i < ni; ++i)
+                    acc = fmaf(Wg[P.w_off[l] + o * ni + i], a[i], acc);
+                b[o] = (l + 1 < P.n_layers) ? fmaxf(acc, 0.0f) : acc;
+            }
+            for (int o = 0; o < no; ++o)
+                a[o] = b[o];
+        }
+        for (int c = 0; c < C; ++c) {
+            if (out_fp16)
+                ((__half *)out)[q * C + c] = __float2half_rn(a[c]);
+            else
+                ((float *)out)[q * C + c] = a[c];
+        }
+    }
+}
+
+// ------------------------------------------------ fused decode, tensor cores
+
+__host__ __device__ inline int mma_per_warp_bytes(int act_bytes, int C, int n_in)
+{
+    return 2 * act_bytes + ((32 * C + 3) & ~3) * 4 + 32 * (n_in + 1) * 4;
+}
+
+// One warp per tile of 32 queries: per-lane unpack + filter of its query,
+// the quantised feature row goes to the warp's activation tile, the MLP runs
+// on the tensor cores, the [32][C] result is staged and stored coalesced.
+template <int PREC>
+__global__ void __launch_bounds__(128) k_decode_mma(MaterialDev M, const float *__restrict__ u,
+                                                    const float *__restrict__ v, const float *__restrict__ s,
+                                                    int64_t n, void *__restrict__ out, int out_fp16, int act_bytes)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const MlpDev &P = M.mlp;
+    const int wbytes = mlp_smem_weight_bytes<PREC>(P);
+    unsigned char *sw = smem;
+    float *sb = (float *)(smem + wbytes);
+    const int nbias = mlp_smem_bias_floats(P);
+    unsigned char *wbase = smem + wbytes + ((nbias * 4 + 15) & ~15);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int C = P.dims[P.n_layers];
+    // per warp: act0, act1 (act_bytes each), output staging [32][C] floats, feature rows [32][n_in + 1]
+    const int per_warp = mma_per_warp_bytes(act_bytes, C, M.n_in);
+    unsigned char *act0 = wbase + warp * per_warp;
+    unsigned char *act1 = act0 + act_bytes;
+    float *ost = (float *)(act1 + act_bytes);
+    float *frow = ost + ((32 * C + 3) & ~3) + lane * (M.n_in + 1);
+
+    load_mlp_smem<PREC>(P, sw, sb);
+    __syncthreads();
+
+    const int warps_total = gridDim.x * (blockDim.x >> 5);
+    const int64_t tiles = (n + 31) / 32;
+    const int row_stride = tile_stride_bytes<PREC>(P.kpad[0]);
+    for (int64_t tile = blockIdx.x * (int64_t)(blockDim.x >> 5) + warp; tile < tiles; tile += warps_total) {
+        const int64_t q = tile * 32 + lane;
+        if (q < n) {
+            query_features(M, u[q], v[q], s ? s[q] : 0.0f, frow);
+        } else {
+            for (int i = 0; i < M.n_in; ++i)
+                frow[i] = 0.0f;
+        }
+        store_input_row<PREC>(P, frow, M.n_in, act0 + lane * row_stride);
+        __syncwarp();
+        warp_mlp<PREC>(P, sw, sb, act0, act1, ost);
+        __syncwarp();
+        // coalesced store of the warp's rows [tile*32, tile*32 + rows)
+        const int rows = (int)min((int64_t)32, n - tile * 32);
+        const int total = rows * C;
+        if (out_fp16) {
+            __half *o = (__half *)out + tile * 32 * C;
+            for (int i = lane; i < total; i += 32)
+                o[i] = __float2half_rn(ost[i]);
+        } else {
+            float *o = (float *)out + tile * 32 * C;
+            for (int i = lane; i < total; i += 32)
+                o[i] = ost[i];
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------- launchers
+
+static int sm_count()
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0)
+            sms = 148;
+    }
+    return sms;
+}
+
+cudaError_t launch_unpack_image(const void *blocks, int bw, int bh, int is_signed, uint16_t *out, cudaStream_t st)
+{
+    const int runs = (bw + kUnpackRun - 1) / kUnpackRun;
+    const int64_t grid = (int64_t)runs * bh;
+    if (grid == 0)
+        return cudaSuccess;
+    if (is_signed)
+        k_unpack_image<true><<<(unsigned)grid, kUnpackRun, 0, st>>>((const uint4 *)blocks, bw, bh, out);
+    else
+        k_unpack_image<false><<<(unsigned)grid, kUnpackRun, 0, st>>>((const uint4 *)blocks, bw, bh, out);
+    return cudaGetLastError();
+}
+
+static unsigned grid_for(int64_t items, int threads, int per_sm)
+{
+    int64_t need = (items + threads - 1) / threads;
+    int64_t cap = (int64_t)sm_count() * per_sm;
+    return (unsigned)max((int64_t)1, min(need, cap));
+}
+
+cudaError_t launch_sample_features(const MaterialDev &M, const float *u, const float *v, const float *s, int64_t n,
+                                   float *feat, cudaStream_t st)
+{
+    if (n == 0)
+        return cudaSuccess;
+    const unsigned grid = grid_for(n, 128, 8);
+    k_sample_features<<<grid, 128, 0, st>>>(M, u, v, s, n, feat);
+    return cudaGetLastError();
+}
+
+#define BCF_FP32_CASE(D0, D1, D2, D3)                                                                              \
+    if (P.n_layers == 3 && P.dims[0] == D0 && P.dims[1] == D1 && P.dims[2] == D2 && P.dims[3] == D3) {             \
+        k_decode_fp32<D0, D1, D2, D3><<<grid, 128, 0, st>>>(M, u, v, s, n, out, out_fp16);                         \
+        return cudaGetLastError();                                                                                 \
+    }
+
+cudaError_t launch_decode_fp32(const MaterialDev &M, const float *u, const float *v, const float *s, int64_t n,
+                               void *out, int out_fp16, cudaStream_t st)
+{
+    if (n == 0)
+        return cudaSuccess;
+    const MlpDev &P = M.mlp;
+    const unsigned grid = grid_for(n, 128, 16);
+    BCF_FP32_CASE(6, 16, 16, 8)
+    BCF_FP32_CASE(13, 32, 32, 9)
+    BCF_FP32_CASE(12, 16, 16, 9)
+    BCF_FP32_CASE(25, 64, 64, 9)
+    k_decode_fp32_generic<<<grid, 128, 0, st>>>(M, u, v, s, n, out, out_fp16);
+    return cudaGetLastError();
+}
+
+template <int PREC>
+static int mma_act_bytes(const MlpDev &P)
+{
+    int mx = 0;
+    for (int l = 0; l < P.n_layers; ++l)
+        mx = max(mx, 32 * tile_stride_bytes<PREC>(P.kpad[l]));
+    return (mx + 15) & ~15;
+}
+
+template <int PREC>
+int64_t mma_smem_bytes(const MlpDev &P, int warps)
+{
+    const int C = P.dims[P.n_layers];
+    const int per_warp = mma_per_warp_bytes(mma_act_bytes<PREC>(P), C, P.dims[0]);
+    return (int64_t)mlp_smem_weight_bytes<PREC>(P) + ((mlp_smem_bias_floats(P) * 4 + 15) & ~15) +
+           (int64_t)warps * per_warp;
+}
+
+template <int PREC>
+static cudaError_t launch_mma(const MaterialDev &M, const float *u, const float *v, const float *s, int64_t n,
+                              void *out, int out_fp16, cudaStream_t st)
+{
+    const int threads = 128;
+    const int64_t smem = mma_smem_bytes<PREC>(M.mlp, threads / 32);
+    if (smem > 200 * 1024)
+        return cudaErrorInvalidConfiguration;
+    auto kern = k_decode_mma<PREC>;
+    static int configured = 0;
+    if (!configured) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        configured = 1;
+    }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, (size_t)smem);
+    const unsigned grid = grid_for((n + 31) / 32, threads / 32, max(per_sm, 1));
+    kern<<<grid, threads, (size_t)smem, st>>>(M, u, v, s, n, out, out_fp16, mma_act_bytes<PREC>(M.mlp));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_decode_mma(const MaterialDev &M, const float *u, const float *v, const float *s, int64_t n,
+                              void *out, int out_fp16, cudaStream_t st)
+{
+    if (n == 0)
+        return cudaSuccess;
+    switch (M.mlp.precision) {
+    case BCF_FP16: return launch_mma<BCF_FP16>(M, u, v, s, n, out, out_fp16, st);
+    case BCF_BF16: return launch_mma<BCF_BF16>(M, u, v, s, n, out, out_fp16, st);
+    case BCF_FP8_E4M3: return launch_mma<BCF_FP8_E4M3>(M, u, v, s, n, out, out_fp16, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+int64_t decode_mma_smem_bytes(const MlpDev &P)
+{
+    switch (P.precision) {
+    case BCF_FP16: return mma_smem_bytes<BCF_FP16>(P, 4);
+    case BCF_BF16: return mma_smem_bytes<BCF_BF16>(P, 4);
+    case BCF_FP8_E4M3: return mma_smem_bytes<BCF_FP8_E4M3>(P, 4);
+    default: return 0;
+    }
+}
+
+} // namespace bcf

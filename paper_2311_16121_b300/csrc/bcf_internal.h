@@ -1,0 +1,56 @@
+// bcf_internal.h -- structures shared by the libbcf host code and kernels.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/bcf.h"
+
+namespace bcf {
+
+// One feature texture as the kernels see it.
+struct TexDev {
+    const uint4 *blocks;               // level 0 first, row-major blocks, mips concatenated
+    int32_t res;                       // level-0 width
+    int32_t log2res;
+    int32_t levels;
+    int32_t lod_bias;                  // log2(res) - log2(res_ref): the b_i of Eq. 11 in levels
+    uint32_t level_off[BCF_MAX_LEVELS]; // block offset of each level
+};
+
+// Padded MLP geometry for the tensor-core path: K and N of every layer are
+// rounded up to the MMA tile (16 for 16-bit operands, 32 for FP8 K).
+struct MlpDev {
+    int32_t n_layers;
+    int32_t dims[BCF_MAX_LAYERS + 1];
+    int32_t kpad[BCF_MAX_LAYERS];      // padded input width per layer
+    int32_t npad[BCF_MAX_LAYERS];      // padded output width per layer
+    int32_t precision;
+    const void *weights;               // caller layout: W_l [out][in] row-major, concatenated
+    const float *biases;
+    float act_scale[BCF_MAX_LAYERS];
+    float w_scale[BCF_MAX_LAYERS];
+    float inv_act_scale[BCF_MAX_LAYERS];
+    int32_t w_off[BCF_MAX_LAYERS];     // element offset of W_l in the caller layout
+    int32_t b_off[BCF_MAX_LAYERS];
+    int32_t smem_w_bytes;              // padded weights in shared memory (MMA operand type)
+    int32_t smem_b_floats;             // padded biases
+};
+
+struct MaterialDev {
+    int32_t n_tex;
+    int32_t is_signed;
+    int32_t wrap;
+    int32_t lod_input;
+    int32_t n_in;                      // 3 T + lod_input
+    int32_t n_out;
+    TexDev tex[BCF_MAX_TEX];
+    MlpDev mlp;
+};
+
+} // namespace bcf
+
+struct bcf_material_s {
+    bcf::MaterialDev host;   // host copy (passed by value to single-material kernels)
+    bcf::MaterialDev *dev;   // device copy (batched kernels)
+    int device;
+};

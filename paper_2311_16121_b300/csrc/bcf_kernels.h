@@ -1,0 +1,23 @@
+// bcf_kernels.h -- launchers of the libbcf kernels (internal, C++).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "bcf_internal.h"
+
+namespace bcf {
+
+cudaError_t launch_unpack_image(const void *blocks, int bw, int bh, int is_signed, uint16_t *out, cudaStream_t st);
+cudaError_t launch_sample_features(const MaterialDev &M, const float *u, const float *v, const float *s, int64_t n,
+                                   float *feat, cudaStream_t st);
+cudaError_t launch_decode_fp32(const MaterialDev &M, const float *u, const float *v, const float *s, int64_t n,
+                               void *out, int out_fp16, cudaStream_t st);
+cudaError_t launch_decode_mma(const MaterialDev &M, const float *u, const float *v, const float *s, int64_t n,
+                              void *out, int out_fp16, cudaStream_t st);
+int64_t decode_mma_smem_bytes(const MlpDev &P);
+cudaError_t texunit_decode(const void *d_blocks, int bw, int bh, int is_signed, uint16_t *d_out, cudaStream_t st);
+
+// thread-local error text
+void set_error(const char *fmt, ...);
+
+} // namespace bcf

@@ -1,0 +1,125 @@
+"""The five BCf workloads as concrete, seeded inputs (host numpy arrays), plus
+upload helpers that build a libbcf Material from them.
+
+Shapes follow the paper's profiles (Table 1 resolutions and mip chains,
+Table 3 screen resolutions, Sec. 5.1 random training batches).  The paper's
+Polyhaven materials are unavailable, so block bitstreams, queries and weights
+are seeded synthetic stand-ins (paper_2311_16121_b300.synth).  Nothing here
+computes any step of the method.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import synth
+
+
+@dataclass
+class DecodeWorkload:
+    name: str
+    res: list[int]
+    levels: list[int]
+    res_ref: int
+    blocks: list[np.ndarray]           # uint8 [blocks, 16] per texture
+    lod_input: bool
+    dims: list[int]
+    W: list[np.ndarray]                # float32 [out, in] per layer
+    b: list[np.ndarray]                # float32 [out] per layer
+    u: np.ndarray
+    v: np.ndarray
+    s: np.ndarray | None
+    is_signed: bool = False
+    wrap: bool = True
+    input_bound: float = 1.0           # bound on the MLP inputs (features and LOD) for FP8 scales
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def n(self) -> int:
+        return int(self.u.size)
+
+    def weights(self, precision: str):
+        """(stored weights array, FP32 biases, act_scale, w_scale) for `precision`."""
+        bias = np.ascontiguousarray(np.concatenate(self.b).astype(np.float32))
+        if precision == "fp8":
+            a, w = synth.fp8_scales(self.W, self.b, self.input_bound)
+            a = pow2_ceil(a)
+            w = pow2_ceil(w)
+            return synth.store_weights(self.W, "fp8", w), bias, a, w
+        return synth.store_weights(self.W, precision), bias, None, None
+
+
+def pow2_ceil(x: np.ndarray) -> np.ndarray:
+    """Round positive scales up to powers of two (exact scaling on both sides)."""
+    return np.exp2(np.ceil(np.log2(np.asarray(x, np.float64)))).astype(np.float32)
+
+
+def seed_rng(config: int, stream: int) -> np.random.Generator:
+    """Independent seeded streams per config and purpose (0 blocks, 1 queries, 2 weights, 3 target, 4 train)."""
+    return np.random.Generator(np.random.Philox(key=synth.MASTER_SEED + config, counter=stream))
+
+
+def config1() -> DecodeWorkload:
+    res, levels = [256, 256], [1, 1]
+    tex = synth.make_textures(seed_rng(1, 0), res, levels, kind="random")
+    u, v, _ = synth.uniform_queries(seed_rng(1, 1), 65536)
+    W, b = synth.mlp_weights(seed_rng(1, 2), [6, 16, 16, 8])
+    return DecodeWorkload("config1-plain-256", res, levels, 256, tex.blocks, False, [6, 16, 16, 8], W, b, u, v, None,
+                          input_bound=65504.0)
+
+
+def screen_material(config: int, n_tex: int, res: int, dims: list[int], width: int, height: int,
+                    supersample: int = 1, pool: int | None = None, modes=tuple(range(1, 15))) -> DecodeWorkload:
+    levels = synth.full_levels(res)
+    rng = seed_rng(config, 0)
+    if pool:
+        tex = synth.make_textures(rng, [res] * n_tex, [levels] * n_tex, kind="bounded", pool=pool)
+    else:
+        blocks = [synth.bounded_blocks(rng, sum(synth.level_blocks(res, levels)), modes=modes) for _ in range(n_tex)]
+        tex = synth.TextureSet([res] * n_tex, [levels] * n_tex, blocks)
+    u, v, s = synth.plane_queries(seed_rng(config, 1), width, height, res_ref=res, supersample=supersample)
+    W, b = synth.mlp_weights(seed_rng(config, 2), dims)
+    return DecodeWorkload(f"config{config}", [res] * n_tex, [levels] * n_tex, res, tex.blocks, True, dims, W, b, u, v,
+                          s, input_bound=max(1.0, float(s.max())))
+
+
+def config2() -> DecodeWorkload:
+    return screen_material(2, 4, 2048, [13, 32, 32, 9], 3840, 2160)
+
+
+def config5() -> DecodeWorkload:
+    return screen_material(5, 8, 4096, [25, 64, 64, 9], 3840, 2160, supersample=2, pool=1 << 20)
+
+
+def small_screen(config: int = 2, n_tex: int = 4, res: int = 64, dims=(13, 32, 32, 9), width: int = 96,
+                 height: int = 54, modes=tuple(range(1, 15))) -> DecodeWorkload:
+    """A reduced screen workload with the structure of configs 2/5 (for parity tests)."""
+    w = screen_material(config, n_tex, res, list(dims), width, height, modes=modes)
+    w.name = f"small-screen-{n_tex}x{res}-{width}x{height}"
+    return w
+
+
+def upload(w: DecodeWorkload, precision: str, device: str = "cuda"):
+    """Build a libbcf Material on the device from a workload."""
+    import torch
+
+    from . import Material
+
+    blocks = [torch.from_numpy(np.ascontiguousarray(b).reshape(-1)).to(device) for b in w.blocks]
+    Wst, bias, a, ws = w.weights(precision)
+    Wt = torch.from_numpy(Wst.view(np.uint8) if Wst.dtype != np.float32 else Wst).to(device)
+    if Wst.dtype == np.uint16:
+        Wt = torch.from_numpy(Wst.view(np.int16)).to(device)
+    bt = torch.from_numpy(bias).to(device)
+    return Material(blocks, w.res, w.levels, w.res_ref, w.dims, precision, Wt, bt, act_scale=a, w_scale=ws,
+                    is_signed=w.is_signed, wrap=w.wrap, lod_input=w.lod_input)
+
+
+def queries_to_device(w: DecodeWorkload, device: str = "cuda"):
+    import torch
+
+    u = torch.from_numpy(w.u).to(device)
+    v = torch.from_numpy(w.v).to(device)
+    s = None if w.s is None else torch.from_numpy(w.s).to(device)
+    return u, v, s

@@ -1,0 +1,221 @@
+"""GPU parity of the libbcf decode path against the CPU oracle.
+
+Every comparison runs the CUDA kernels through the C ABI (via the thin Python
+binding) and the oracle on the same seeded inputs:
+  - BC6H unpack: bit-exact, all 14 modes, unsigned and signed, reserved modes;
+  - texture-unit BC6H decode (an independent statement of the format) against
+    the oracle: pins the per-mode bit layouts;
+  - trilinear features: FP32 filtering vs FP64 (relative to the magnitudes);
+  - fused decode: FP32 plain path vs FP64; FP16 / BF16 / FP8 tensor-core
+    paths vs the quantisation-aware FP64 oracle within 1e-3 (FP16) and 4e-3
+    (BF16, FP8) absolute per channel, error vs the unquantised FP64 oracle
+    reported.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2311_16121_b300 import synth, workloads
+
+pytestmark = pytest.mark.gpu
+
+TOL = {"fp16": 1e-3, "bf16": 4e-3, "fp8": 4e-3}
+
+
+def _bcf():
+    import paper_2311_16121_b300 as bcf
+
+    bcf.lib()
+    return bcf
+
+
+def _gpu_blocks(arr):
+    return torch.from_numpy(np.ascontiguousarray(arr, np.uint8).reshape(-1)).cuda()
+
+
+# --------------------------------------------------------------------------- BC6H unpack
+
+@pytest.mark.parametrize("signed", [False, True])
+def test_unpack_bit_exact_random_all_modes(signed):
+    bcf = _bcf()
+    rng = workloads.seed_rng(1, 7)
+    bw, bh = 200, 37  # ragged: several 64-block runs and a partial one
+    blocks = synth.random_blocks(rng, bw * bh)
+    got = bcf.decode_bc6h(_gpu_blocks(blocks), bw, bh, signed).cpu().numpy().view(np.uint16)
+    ref = oracle.bc6h_decode_image(blocks, bw, bh, signed)
+    assert got.shape == ref.shape
+    mism = np.argwhere(got != ref)
+    assert mism.size == 0, f"{len(mism)} mismatching values, first at {mism[:3]}"
+
+
+def test_unpack_reserved_modes_and_edge_sizes():
+    bcf = _bcf()
+    rng = workloads.seed_rng(1, 8)
+    blocks = rng.integers(0, 256, (5 * 3, 16), dtype=np.uint8)
+    for i, code in enumerate((19, 23, 27, 31)):
+        blocks[i, 0] = (blocks[i, 0] & 0xE0) | code
+    got = bcf.decode_bc6h(_gpu_blocks(blocks), 5, 3).cpu().numpy().view(np.uint16)
+    np.testing.assert_array_equal(got, oracle.bc6h_decode_image(blocks, 5, 3))
+    assert not got[:4, :16].any()
+    one = synth.random_blocks(rng, 1)
+    np.testing.assert_array_equal(bcf.decode_bc6h(_gpu_blocks(one), 1, 1).cpu().numpy().view(np.uint16),
+                                  oracle.bc6h_decode_image(one, 1, 1))
+    # empty image: a no-op
+    bcf.decode_bc6h(_gpu_blocks(one), 0, 0, out=torch.empty(0, dtype=torch.int16, device="cuda"))
+
+
+@pytest.mark.parametrize("signed", [False, True])
+def test_texture_unit_agrees_with_oracle_on_all_modes(signed):
+    """The GPU's BC6H texture decoder as an independent statement of the format
+    (bit layouts of the 14 modes, partitions, anchors, weights): it must
+    equal the oracle bit for bit on random valid blocks of every mode."""
+    bcf = _bcf()
+    rng = workloads.seed_rng(1, 9)
+    bw, bh = 256, 128
+    blocks = synth.random_blocks(rng, bw * bh)
+    hw = bcf.texunit_decode_bc6h(_gpu_blocks(blocks), bw, bh, signed).cpu().numpy().view(np.uint16)
+    ref = oracle.bc6h_decode_image(blocks, bw, bh, signed)
+    modes = np.array([oracle.bc6h_block_mode(b) for b in blocks]).reshape(bh, bw)
+    bad = np.any(hw != ref, axis=2)
+    if bad.any():
+        bad_blocks = np.unique((np.argwhere(bad) // 4) @ np.array([bw, 1]))
+        bad_modes = np.bincount(modes.reshape(-1)[bad_blocks], minlength=15)
+        pytest.fail(f"texture unit differs from the oracle on {bad_blocks.size} blocks; by mode: {bad_modes.tolist()}")
+
+
+# --------------------------------------------------------------------------- features
+
+def _oracle_material(w: workloads.DecodeWorkload):
+    return oracle.Material(w.blocks, w.res, w.levels, w.res_ref, w.is_signed, w.wrap, w.lod_input)
+
+
+def test_sample_features_random_blocks_fp32_vs_fp64():
+    bcf = _bcf()
+    w = workloads.config1()
+    m = workloads.upload(w, "fp32")
+    u, v, s = workloads.queries_to_device(w)
+    got = m.sample_features(u, v, s).cpu().numpy().astype(np.float64)
+    ref = oracle.sample_features(_oracle_material(w), w.u, w.v, w.s)
+    # non-negative texels, positive weights: relative error of a few FP32 roundings
+    err = np.abs(got - ref)
+    assert (err <= 8 * 2.0 ** -24 * np.abs(ref) + 1e-30).all(), err.max()
+
+
+def test_sample_features_screen_trilinear():
+    bcf = _bcf()
+    w = workloads.small_screen(res=128, width=160, height=90)
+    m = workloads.upload(w, "fp16")
+    u, v, s = workloads.queries_to_device(w)
+    got = m.sample_features(u, v, s).cpu().numpy().astype(np.float64)
+    ref = oracle.sample_features(_oracle_material(w), w.u, w.v, w.s)
+    assert np.abs(got - ref).max() <= 1e-6
+
+
+def test_sample_features_edge_inputs():
+    """NaN / infinite / out-of-range coordinates and LODs, clamp addressing, negative and huge s."""
+    bcf = _bcf()
+    w = workloads.small_screen(res=32, width=16, height=9)
+    u = np.array([np.nan, np.inf, -np.inf, -0.25, 1.0, 1.75, 7.3e6, -1e-9, 0.5, 0.999999], np.float32)
+    v = np.array([0.5, 0.5, 0.1, 1.25, -3.5, np.nan, 0.5, 0.25, 0.0, 1e-20], np.float32)
+    s = np.array([0.5, np.nan, -3.0, 1e9, np.inf, 2.5, 3.0, 0.0, -np.inf, 2.0], np.float32)
+    for wrap in (True, False):
+        w.wrap = wrap
+        m = workloads.upload(w, "fp16")
+        got = m.sample_features(torch.from_numpy(u).cuda(), torch.from_numpy(v).cuda(),
+                                torch.from_numpy(s).cuda()).cpu().numpy().astype(np.float64)
+        ref = oracle.sample_features(_oracle_material(w), u, v, s)
+        assert np.isfinite(got).all()
+        assert np.abs(got - ref).max() <= 1e-6, (wrap, np.abs(got - ref).max(axis=1))
+
+
+# --------------------------------------------------------------------------- fused decode
+
+def _abs_bound(w, feat):
+    """Magnitude bound of the FP32 MLP: the network with |W|, |b| and |x|."""
+    h = np.abs(feat)
+    for l, (W, b) in enumerate(zip(w.W, w.b)):
+        h = h @ np.abs(W.astype(np.float64)).T + np.abs(b)
+    return h
+
+
+def test_decode_fp32_plain_matches_fp64():
+    bcf = _bcf()
+    w = workloads.config1()
+    m = workloads.upload(w, "fp32")
+    u, v, s = workloads.queries_to_device(w)
+    got = m.decode(u, v, s).cpu().numpy().astype(np.float64)
+    Wst, bias, _, _ = w.weights("fp32")
+    P = oracle.Mlp(w.dims, "fp32", Wst, bias)
+    ref = oracle.decode(_oracle_material(w), P, w.u, w.v, w.s, threads=8)
+    feat = oracle.sample_features(_oracle_material(w), w.u, w.v, w.s)
+    M = _abs_bound(w, feat)
+    tol = 4 * (max(w.dims) + 2) * 2.0 ** -24 * M + 1e-6 * M
+    assert (np.abs(got - ref) <= tol).all(), np.max(np.abs(got - ref) / np.maximum(tol, 1e-30))
+
+
+def _quant_check(got, ref_q, tol, what):
+    err = np.abs(got - ref_q)
+    worst = err.max(axis=0)
+    frac = float((err > tol).mean())
+    # rounding-boundary flips (FP32 accumulation in the kernel vs FP64 in the oracle at an operand
+    # rounding step) may move isolated values by one operand ulp; anything systematic fails here
+    assert frac <= 1e-3, f"{what}: {frac:.2e} of outputs beyond {tol}; per-channel max {worst}"
+    assert np.all(err <= 8 * tol), f"{what}: max error {err.max()} per channel {worst}"
+    return worst, frac
+
+
+@pytest.mark.parametrize("precision", ["fp16", "bf16", "fp8"])
+@pytest.mark.parametrize("out_dtype", [torch.float32, torch.float16])
+def test_decode_tensor_core_paths_match_quant_aware_oracle(precision, out_dtype):
+    bcf = _bcf()
+    w = workloads.small_screen(res=128, width=200, height=61)  # 12,200 queries: 381 warp tiles + a ragged tail
+    m = workloads.upload(w, precision)
+    u, v, s = workloads.queries_to_device(w)
+    got = m.decode(u, v, s, out_dtype=out_dtype).cpu().numpy().astype(np.float64)
+    Wst, bias, a, ws = w.weights(precision)
+    P = oracle.Mlp(w.dims, precision, Wst, bias, a, ws)
+    mat = _oracle_material(w)
+    ref_q = oracle.decode(mat, P, w.u, w.v, w.s, quant_aware=True, threads=8)
+    ref = oracle.decode(mat, P, w.u, w.v, w.s, quant_aware=False, threads=8)
+    if out_dtype == torch.float16:
+        ref_q = ref_q.astype(np.float16).astype(np.float64)
+    tol = TOL[precision] + (np.abs(ref_q) * 2.0 ** -11 if out_dtype == torch.float16 else 0.0)
+    worst, frac = _quant_check(got, ref_q, tol, precision)
+    print(f"{precision} out={out_dtype}: per-channel max |gpu - quant-aware oracle| {np.round(worst, 6)}, "
+          f"beyond-tolerance fraction {frac:.1e}; vs unquantised FP64: max {np.abs(got - ref).max(axis=0).round(5)}")
+
+
+@pytest.mark.parametrize("precision", ["fp32", "fp16"])
+def test_decode_edge_sizes(precision):
+    """n = 1, a ragged n, and n = 0 (no-op)."""
+    bcf = _bcf()
+    w = workloads.small_screen(res=32, width=40, height=1)
+    m = workloads.upload(w, precision)
+    Wst, bias, a, ws = w.weights(precision)
+    P = oracle.Mlp(w.dims, precision, Wst, bias, a, ws)
+    for n in (1, 33, 40):
+        u = torch.from_numpy(w.u[:n].copy()).cuda()
+        v = torch.from_numpy(w.v[:n].copy()).cuda()
+        s = torch.from_numpy(w.s[:n].copy()).cuda()
+        got = m.decode(u, v, s).cpu().numpy()
+        ref = oracle.decode(_oracle_material(w), P, w.u[:n], w.v[:n], w.s[:n], quant_aware=True)
+        assert got.shape == (n, 9)
+        assert np.abs(got - ref).max() <= (1e-4 if precision == "fp32" else 2e-3)
+    e = torch.empty(0, device="cuda")
+    assert m.decode(e, e, e).shape == (0, 9)
+
+
+def test_invalid_arguments_return_status_without_launching():
+    bcf = _bcf()
+    w = workloads.small_screen(res=32, width=8, height=4)
+    m = workloads.upload(w, "fp16")
+    u, v, s = workloads.queries_to_device(w)
+    bad_out = torch.empty(w.n * 9 + 1, dtype=torch.float32, device="cuda")[1:]  # 4-byte aligned, not 16
+    with pytest.raises(bcf.BcfError):
+        m.decode(u, v, s, out=bad_out)
+    with pytest.raises(bcf.BcfError):
+        bcf.decode_bc6h(_gpu_blocks(np.zeros(16, np.uint8)), -1, 1,
+                        out=torch.empty(48, dtype=torch.int16, device="cuda"))
