@@ -1,0 +1,294 @@
+"""Benchmark of the BCf decode hot path (BC6H unpack + trilinear filter + MLP) on B300.
+
+One step = one full decode of the screen workload through ``bcf_decode_material``:
+4 BC6H feature textures of 2048^2 with full mip chains (value-bounded random
+blocks over all 14 modes), 3840x2160 queries of a perspective-viewed tiled
+plane (uv and LOD from the per-pixel screen Jacobian), MLP 13-32-32-9 on the
+tensor cores.  ``value`` is the whole-job decode throughput in Gsamples/s with
+inputs resident in HBM; ``e2e`` is the same metric through the C ABI with the
+queries in pinned host memory and the decoded channels read back every step.
+
+Extra keys report the FP32 SIMT plain path and the FP8 path on the same frame,
+the roofline of the dominant kernel, and the CPU oracle on a bounded sample.
+
+Multi-GPU: the decode shards by queries with no exchange step; each rank
+decodes its own full frame (replicas, weak scaling), and rank 0 reports the
+total samples of all ranks over the slowest rank's time.
+
+``--impl reference`` times the CPU oracle (the only reference implementation
+of this method) on the same workload and metric, a bounded sample per step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Gsamples/s BCf decode (BC6H+filter+MLP) low-prec vs FP32 plain; train steps/s"
+HEADLINE_PRECISION = "fp16"
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), float(p["bf16_tflops"]), "measured"
+    except Exception:
+        return 6400.0, 1800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _cpu_baseline(w, precision, seconds=12.0):
+    """The oracle (plain FP64 C, all host cores) on a seeded uniform sample of the frame's queries."""
+    import oracle
+
+    mat = oracle.Material(w.blocks, w.res, w.levels, w.res_ref, w.is_signed, w.wrap, w.lod_input)
+    Wst, bias, a, ws = w.weights(precision)
+    P = oracle.Mlp(w.dims, precision, Wst, bias, a, ws)
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(7)
+    n0 = 1 << 14
+    idx = rng.integers(0, w.n, n0)
+    t = time.perf_counter()
+    oracle.decode(mat, P, w.u[idx], w.v[idx], w.s[idx], quant_aware=True, threads=cores)
+    rate = n0 / max(time.perf_counter() - t, 1e-6)
+    n = int(min(max(rate * seconds, n0), w.n))
+    idx = rng.integers(0, w.n, n)
+    t = time.perf_counter()
+    oracle.decode(mat, P, w.u[idx], w.v[idx], w.s[idx], quant_aware=True, threads=cores)
+    dt = time.perf_counter() - t
+    return {"value": n / dt / 1e9, "unit": "Gsamples/s", "cores": cores, "kind": "oracle",
+            "sample": f"{n} queries drawn uniformly (seed 7) from the {w.n}-query frame, {precision} "
+                      f"quantisation-aware FP64 decode, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """The CPU oracle as the reference arm (bounded sample per step)."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    from paper_2311_16121_b300 import workloads
+
+    w = workloads.config2()
+    mat = oracle.Material(w.blocks, w.res, w.levels, w.res_ref, w.is_signed, w.wrap, w.lod_input)
+    Wst, bias, a, ws = w.weights(HEADLINE_PRECISION)
+    P = oracle.Mlp(w.dims, HEADLINE_PRECISION, Wst, bias, a, ws)
+    cores = os.cpu_count() or 1
+    rng = np.random.default_rng(11)
+    per_step = 1 << 16
+    total_q, total_t = 0, 0.0
+    for step in range(args.warmup + args.steps):
+        idx = rng.integers(0, w.n, per_step)
+        t = time.perf_counter()
+        oracle.decode(mat, P, w.u[idx], w.v[idx], w.s[idx], quant_aware=True, threads=cores)
+        dt = time.perf_counter() - t
+        if step >= args.warmup:
+            total_q += per_step
+            total_t += dt
+    value = total_q / total_t / 1e9
+    sample = f"{per_step} queries per step drawn uniformly from the {w.n}-query frame (FP64 oracle, {cores} threads)"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Gsamples/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_t / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name + ": " + "4x BC6H 2048^2 full mips, 3840x2160 plane "
+                                                                        "queries, MLP 13-32-32-9", "sample": sample},
+            "cpu_baseline": {"value": value, "unit": "Gsamples/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "Gsamples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    import paper_2311_16121_b300 as bcf
+    from paper_2311_16121_b300 import workloads
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    bcf.lib()
+    assert args.warmup >= 3, "at least 3 warm-up steps"
+
+    w = workloads.config2()
+    u, v, s = workloads.queries_to_device(w)
+    mats = {p: workloads.upload(w, p) for p in (HEADLINE_PRECISION, "fp32", "fp8")}
+    out = torch.empty((w.n, 9), dtype=torch.float16, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 126 MB L2
+    stream = torch.cuda.current_stream()
+
+    def timed(mat, steps, warmup):
+        for _ in range(warmup):
+            mat.decode(u, v, s, out=out)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        total = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            mat.decode(u, v, s, out=out)
+            b.record(stream)
+            b.synchronize()
+            total += a.elapsed_time(b)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        return total
+
+    # headline: low-precision path
+    with ClockSampler(local) as clk:
+        head_ms = timed(mats[HEADLINE_PRECISION], args.steps, args.warmup)
+    clocks = clk.summary()
+    t = torch.tensor([head_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    head_ms_max = float(t.item())
+    value = w.n * world * args.steps / (head_ms_max * 1e-3) / 1e9
+
+    # the plain FP32 path and FP8 on the same frame
+    k_extra = max(3, args.steps // 4)
+    fp32_ms = timed(mats["fp32"], k_extra, 3) / k_extra
+    fp8_ms = timed(mats["fp8"], k_extra, 3) / k_extra
+
+    # end to end through the C ABI with host buffers
+    uh, vh, sh = (torch.from_numpy(a).pin_memory() for a in (w.u, w.v, w.s))
+    oh = torch.empty((w.n, 9), dtype=torch.float16).pin_memory()
+    ud, vd, sd = torch.empty_like(u), torch.empty_like(v), torch.empty_like(s)
+    m = mats[HEADLINE_PRECISION]
+    e2e_total = 0.0
+    for i in range(3 + k_extra):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ud.copy_(uh, non_blocking=True)
+        vd.copy_(vh, non_blocking=True)
+        sd.copy_(sh, non_blocking=True)
+        m.decode(ud, vd, sd, out=out)
+        oh.copy_(out, non_blocking=True)
+        b.record(stream)
+        b.synchronize()
+        if i >= 3:
+            e2e_total += a.elapsed_time(b)
+    e2e_value = w.n * world * k_extra / (e2e_total * 1e-3) / 1e9
+
+    hbm_peak, bf16_peak, peak_kind = _peaks()
+    tex_bytes = sum(int(b.size) for b in w.blocks)
+    alg_bytes = w.n * (12 + 18) + tex_bytes  # queries in, FP16 channels out, the texture set once
+    achieved = alg_bytes / (head_ms / args.steps * 1e-3) / 1e9
+
+    if rank == 0:
+        cpu = None
+        if not args.no_cpu_baseline and world == 1:
+            cpu = _cpu_baseline(w, HEADLINE_PRECISION)
+        line = {
+            "metric": METRIC, "value": value, "unit": "Gsamples/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": head_ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": HEADLINE_PRECISION, "data": "synthetic",
+            "config": {"workload": "screen decode: 4x BC6H 2048^2 full mips (value-bounded, all 14 modes), "
+                                   "3840x2160 perspective-plane queries, MLP 13-32-32-9",
+                       "queries_per_step": w.n, "precision": HEADLINE_PRECISION, "out": "fp16 [N][9]",
+                       "l2": "256 MB buffer written between timed steps",
+                       "parallelism": f"replicas x{world}"},
+            "fp32_plain": {"value": w.n / (fp32_ms * 1e-3) / 1e9, "unit": "Gsamples/s", "ms_per_step": fp32_ms},
+            "fp8": {"value": w.n / (fp8_ms * 1e-3) / 1e9, "unit": "Gsamples/s", "ms_per_step": fp8_ms},
+            "speedup_vs_fp32_plain": fp32_ms / (head_ms / args.steps),
+            "e2e": {"value": e2e_value, "unit": "Gsamples/s", "h2d_bytes_per_step": 12 * w.n,
+                    "d2h_bytes_per_step": 18 * w.n},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                         "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                         "kernel": f"k_decode_mma<{HEADLINE_PRECISION}>",
+                         "algorithmic_bytes_per_launch": alg_bytes},
+            "cpu_baseline": cpu,
+            "clocks": clocks,
+            "gpu_launches": args.steps,
+        }
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
