@@ -170,6 +170,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-headline", action="store_true",
+                    help="time only the headline decode (for profiler captures); prints a reduced line")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -227,6 +229,13 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     head_ms_max = float(t.item())
     value = w.n * world * args.steps / (head_ms_max * 1e-3) / 1e9
+
+    if args.only_headline:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": "Gsamples/s", "n_gpus": world,
+                              "steps": args.steps, "warmup": args.warmup, "ms_per_step": head_ms_max / args.steps,
+                              "note": "headline decode only"}))
+        return
 
     # the plain FP32 path and FP8 on the same frame
     k_extra = max(3, args.steps // 4)

@@ -167,6 +167,19 @@ bcf_status bcf_sample_features(bcf_material mat, const float *d_u, const float *
 bcf_status bcf_decode_material(bcf_material mat, const float *d_u, const float *d_v, const float *d_s, int64_t n,
                                void *d_out, bcf_precision out_precision, bcf_stream stream);
 
+/*
+ * bcf_set_decode_variant -- choose the kernel bcf_decode_material uses for a
+ * tensor-core (FP16 / BF16 / FP8) material.  0 (default): tile-cooperative
+ * decode -- 256 screen-coherent queries share one decode of each BC6H block
+ * their footprints touch (blocks mode-sorted, texels staged in shared
+ * memory); falls back per tile to 1 when the tile's blocks do not fit.
+ * 1: per-lane decode -- every query decodes the blocks of its own
+ * footprints.  Both compute the same values.  FP32 materials always use the
+ * per-lane SIMT path.  Errors: BCF_ERR_INVALID_ARG for a null material or
+ * another variant.
+ */
+bcf_status bcf_set_decode_variant(bcf_material mat, int32_t variant);
+
 #ifdef __cplusplus
 }
 #endif

@@ -65,6 +65,8 @@ def lib() -> ctypes.CDLL:
         L.bcf_destroy_material.argtypes = [c_void_p]
         L.bcf_sample_features.restype = c_int
         L.bcf_sample_features.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p]
+        L.bcf_set_decode_variant.restype = c_int
+        L.bcf_set_decode_variant.argtypes = [c_void_p, c_int32]
         L.bcf_decode_material.restype = c_int
         L.bcf_decode_material.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_int, c_void_p]
         _lib = L
@@ -145,6 +147,10 @@ class Material:
         self.dims = list(dims)
         self.n_tex = len(blocks)
         self.precision = precision
+
+    def set_decode_variant(self, variant: int) -> None:
+        """bcf_set_decode_variant: 0 tile-cooperative (default), 1 per-lane."""
+        _check(lib().bcf_set_decode_variant(self.handle, int(variant)), "bcf_set_decode_variant")
 
     def close(self) -> None:
         if self.handle:

@@ -359,3 +359,96 @@ __device__ __forceinline__ Bc6hBlock load_block(const uint4 *p)
 }
 
 } // namespace bcf
+
+namespace bcf {
+
+// All 16 texels of a decoded block, written through `store(t, rgb_lo, b)`
+// with rgb_lo = R | G << 16 and b = B (half bit patterns).  The partition
+// mask, anchor and index stream are read once for the block; indices are
+// consumed from a running shift of the upper 64-bit word.
+template <class Store>
+__device__ __forceinline__ void bc6h_all_texels(const Bc6hBlock &blk, const Bc6hHeader &H, bool sgn, Store store)
+{
+    uint64_t idx;
+    uint32_t pmask = 0;
+    int a2 = 16;
+    if (H.two) {
+        pmask = partition_mask(H.partition);
+        a2 = anchor2_of(H.partition);
+        idx = blk.hi >> 18; // index bits start at bit 82
+    } else {
+        idx = blk.hi >> 1;  // index bits start at bit 65
+    }
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+        int w;
+        if (H.two) {
+            const int nb = (t == 0 || t == a2) ? 2 : 3;
+            w = weight3((int)(idx & ((1u << nb) - 1)));
+            idx >>= nb;
+        } else {
+            const int nb = t == 0 ? 3 : 4;
+            w = weight4((int)(idx & ((1u << nb) - 1)));
+            idx >>= nb;
+        }
+        const int region = (int)((pmask >> t) & 1);
+        const int *ea = region ? H.e[2] : H.e[0];
+        const int *eb = region ? H.e[3] : H.e[1];
+        const int vr = (ea[0] * (64 - w) + eb[0] * w + 32) >> 6;
+        const int vg = (ea[1] * (64 - w) + eb[1] * w + 32) >> 6;
+        const int vb = (ea[2] * (64 - w) + eb[2] * w + 32) >> 6;
+        const uint32_t r = H.valid ? finish(vr, sgn) : 0u;
+        const uint32_t g = H.valid ? finish(vg, sgn) : 0u;
+        const uint32_t b = H.valid ? finish(vb, sgn) : 0u;
+        store(t, r | (g << 16), b);
+    }
+}
+
+} // namespace bcf
+
+namespace bcf {
+
+// Texels 8 * half .. 8 * half + 7 of a decoded block (as bc6h_all_texels).
+template <class Store>
+__device__ __forceinline__ void bc6h_half_texels(const Bc6hBlock &blk, const Bc6hHeader &H, bool sgn, int half,
+                                                 Store store)
+{
+    uint64_t idx;
+    uint32_t pmask = 0;
+    int a2 = 16;
+    if (H.two) {
+        pmask = partition_mask(H.partition);
+        a2 = anchor2_of(H.partition);
+        // texels 0..7 hold 24 index bits minus one for texel 0 and one if the second anchor is among them
+        idx = blk.hi >> (18 + (half ? 23 - (a2 < 8) : 0));
+    } else {
+        idx = blk.hi >> (1 + (half ? 31 : 0));
+    }
+    const int t0 = 8 * half;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const int t = t0 + j;
+        int w;
+        if (H.two) {
+            const int nb = (t == 0 || t == a2) ? 2 : 3;
+            w = weight3((int)(idx & ((1u << nb) - 1)));
+            idx >>= nb;
+        } else {
+            const int nb = t == 0 ? 3 : 4;
+            w = weight4((int)(idx & ((1u << nb) - 1)));
+            idx >>= nb;
+        }
+        const int region = (int)((pmask >> t) & 1);
+        const int *ea = region ? H.e[2] : H.e[0];
+        const int *eb = region ? H.e[3] : H.e[1];
+        const int vr = (ea[0] * (64 - w) + eb[0] * w + 32) >> 6;
+        const int vg = (ea[1] * (64 - w) + eb[1] * w + 32) >> 6;
+        const int vb = (ea[2] * (64 - w) + eb[2] * w + 32) >> 6;
+        const uint32_t r = H.valid ? finish(vr, sgn) : 0u;
+        const uint32_t g = H.valid ? finish(vg, sgn) : 0u;
+        const uint32_t b = H.valid ? finish(vb, sgn) : 0u;
+        store(t, r | (g << 16), b);
+    }
+}
+
+} // namespace bcf

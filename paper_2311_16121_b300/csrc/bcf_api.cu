@@ -186,7 +186,7 @@ bcf_status bcf_create_material(const bcf_material_desc *d, bcf_material *out)
     M.n_out = P.dims[P.n_layers];
     if (d->precision != BCF_FP32) {
         P.smem_w_bytes = 0;
-        if (decode_mma_smem_bytes(P) > 200 * 1024)
+        if (decode_mma_smem_bytes(P) > 200 * 1024 || decode_tiled_smem_bytes(P) > 227 * 1024)
             return fail(BCF_ERR_UNSUPPORTED, "MLP too large for the shared-memory tensor-core path");
     }
     bcf_material m = new (std::nothrow) bcf_material_s;
@@ -194,6 +194,7 @@ bcf_status bcf_create_material(const bcf_material_desc *d, bcf_material *out)
         return fail(BCF_ERR_OOM, "host allocation failed");
     m->host = M;
     m->dev = nullptr;
+    m->variant = 0;
     cudaGetDevice(&m->device);
     cudaError_t e = cudaMalloc(&m->dev, sizeof(MaterialDev));
     if (e != cudaSuccess) {
@@ -207,6 +208,14 @@ bcf_status bcf_create_material(const bcf_material_desc *d, bcf_material *out)
         return cuda_status(e, "cudaMemcpy(material metadata)");
     }
     *out = m;
+    return BCF_OK;
+}
+
+bcf_status bcf_set_decode_variant(bcf_material m, int32_t variant)
+{
+    if (!m || variant < 0 || variant > 1)
+        return fail(BCF_ERR_INVALID_ARG, "bcf_set_decode_variant: null material or variant not in {0, 1}");
+    m->variant = variant;
     return BCF_OK;
 }
 
@@ -246,9 +255,13 @@ bcf_status bcf_decode_material(bcf_material m, const float *d_u, const float *d_
         (d_s && !aligned(d_s, 4)))
         return fail(BCF_ERR_INVALID_ARG, "bcf_decode_material: null or misaligned pointer");
     const int fp16 = out_precision == BCF_FP16;
-    cudaError_t e = m->host.mlp.precision == BCF_FP32
-                        ? launch_decode_fp32(m->host, d_u, d_v, d_s, n, d_out, fp16, (cudaStream_t)stream)
-                        : launch_decode_mma(m->host, d_u, d_v, d_s, n, d_out, fp16, (cudaStream_t)stream);
+    cudaError_t e;
+    if (m->host.mlp.precision == BCF_FP32)
+        e = launch_decode_fp32(m->host, d_u, d_v, d_s, n, d_out, fp16, (cudaStream_t)stream);
+    else if (m->variant == 1)
+        e = launch_decode_mma(m->host, d_u, d_v, d_s, n, d_out, fp16, (cudaStream_t)stream);
+    else
+        e = launch_decode_tiled(m->host, d_u, d_v, d_s, n, d_out, fp16, (cudaStream_t)stream);
     return cuda_status(e, "bcf_decode_material launch");
 }
 

@@ -1,0 +1,598 @@
+// bcf_decode_tiled.cu -- tile-cooperative fused decode (Eq. 3 with Eq. 10 / 11
+// filtering over BC6H features).
+//
+// A CTA takes 256 consecutive queries (one per thread).  Screen queries are
+// spatially coherent, so their bilinear footprints share BC6H blocks.  Instead
+// of every lane decoding the blocks its own footprint touches, the CTA:
+//   1. finds, per texture, the mip levels its queries use and, per level, the
+//      box of blocks their footprints touch (warp reductions + shared atomics,
+//      block coordinates taken relative to the first query so that boxes
+//      straddling the repeat seam stay compact);
+//   2. groups the textures into rounds whose boxes fit the shared-memory
+//      arena; per round it loads each block once (16-byte loads, kept in
+//      registers), counting-sorts the blocks by BC6H mode (warp-aggregated
+//      shared atomics) so that a warp decodes blocks of (mostly) one mode, and
+//      decodes all 16 texels of every block into the arena (8 bytes per texel,
+//      texel slots XOR-swizzled by the block index to spread banks);
+//   3. lets every query filter its 2 x 2 footprints trilinearly from the arena
+//      in FP32 (exact weights, Eq. 10) and write its quantised feature row
+//      straight into its warp's MLP input tile;
+//   4. runs the MLP on the tensor cores per warp (register-chained layers for
+//      the common 3-layer shapes) and stores the channels coalesced.
+// A texture whose boxes alone exceed the arena, or that spans more than three
+// levels in the tile, is filtered by the per-lane decode instead.
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+
+#include "bc6h_unpack.cuh"
+#include "bcf_kernels.h"
+#include "bcf_mlp.cuh"
+#include "bcf_sample.cuh"
+
+namespace bcf {
+
+constexpr int kTileQ = 256;    // queries per CTA tile, one per thread
+constexpr int kMaxLv = 3;      // mip levels per texture held per tile
+constexpr int kBoxes = BCF_MAX_TEX * kMaxLv;
+constexpr int kBins = 15;      // 14 modes + reserved
+
+struct TileMeta {
+    float u0, v0;
+    int smin_bits, smax_bits; // tile LOD range (order-preserving integer images of the floats)
+    int nrounds;
+    int lmin[BCF_MAX_TEX];
+    int lmax[BCF_MAX_TEX];
+    int direct[BCF_MAX_TEX];     // 1: this texture is filtered by the per-lane decode
+    int bb[kBoxes][4];           // min x, max x, min y, max y of the box (relative block coordinates)
+    int base[kBoxes];            // first arena block of each box within its round
+    int bw[kBoxes];              // box width in blocks
+    int rtex[BCF_MAX_TEX + 1];   // textures [rtex[r], rtex[r+1]) form round r
+    int rtotal[BCF_MAX_TEX];     // blocks of round r
+    int hist[16];
+    int offs[16];
+};
+
+// LOD of texture T for query LOD s: level floor(s_t), whether floor(s_t) + 1
+// is also sampled, and the lerp fraction (identical arithmetic everywhere).
+struct Lod {
+    int l0, nlev;
+    float lam;
+};
+
+__device__ __forceinline__ Lod lod_of(const TexDev &T, float s)
+{
+    float st = (isnan(s) ? 0.0f : s) + (float)T.lod_bias;
+    st = fminf(fmaxf(st, 0.0f), (float)(T.levels - 1));
+    const float fl = floorf(st);
+    Lod L;
+    L.l0 = (int)fl;
+    L.lam = st - fl;
+    L.nlev = (L.lam > 0.0f && L.l0 + 1 < T.levels) ? 2 : 1;
+    return L;
+}
+
+// Order-preserving map float -> int (for atomicMin / atomicMax on floats).
+__device__ __forceinline__ int f2ord(float f)
+{
+    const int i = __float_as_int(f);
+    return i >= 0 ? i : i ^ 0x7FFFFFFF;
+}
+__device__ __forceinline__ float ord2f(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7FFFFFFF); }
+
+__device__ __forceinline__ int wraprel(int b, int rb, int wb)
+{
+    const int h = wb >> 1;
+    return ((b - rb + h) & (wb - 1)) - h;
+}
+
+// Block coordinate (relative to the tile reference for repeat addressing,
+// absolute for clamp) of texel column / row i, given the footprint's first
+// column i0 and the reference block rb.
+__device__ __forceinline__ int rel_block(int i, int i0, int rb, int W, int wrap)
+{
+    if (wrap)
+        return wraprel(i0 >> 2, rb, W >> 2) + ((i >> 2) - (i0 >> 2));
+    return min(max(i, 0), W - 1) >> 2;
+}
+
+__device__ __forceinline__ int texel_col(int i, int W, int wrap) { return wrap ? (i & 3) : (min(max(i, 0), W - 1) & 3); }
+
+__device__ __forceinline__ int ref_block(float c0, int W) { return ((int)floorf(c0 * (float)W - 0.5f)) >> 2; }
+
+// Arena slot of texel t of arena block b (XOR swizzle spreads the 8-byte
+// texels of different blocks over the banks).
+__device__ __forceinline__ int arena_slot(int b, int t) { return b * 16 + (t ^ (b & 15)); }
+
+template <int PREC>
+__device__ __forceinline__ void store_feature(unsigned char *row, int col, float x, float inv_scale)
+{
+    if constexpr (PREC == BCF_FP8_E4M3) {
+        row[col] = (unsigned char)__nv_cvt_float_to_fp8(x * inv_scale, __NV_SATFINITE, __NV_E4M3);
+    } else if constexpr (PREC == BCF_BF16) {
+        *(__nv_bfloat16 *)(row + 2 * col) = __float2bfloat16_rn(x);
+    } else {
+        *(__half *)(row + 2 * col) = __float2half_rn(x);
+    }
+}
+
+// Shared memory layout of the kernel (host and device agree through this).
+struct TiledLayout {
+    int w_bytes, b_bytes, meta, sraw, sidx, arena, per_warp, act0, act1, tmp8, ost, total;
+};
+
+template <int PREC>
+__host__ __device__ inline TiledLayout tiled_layout(const MlpDev &P, int cap, bool generic_mlp)
+{
+    TiledLayout L;
+    const int C = P.dims[P.n_layers];
+    int off = 0;
+    L.w_bytes = mlp_smem_weight_bytes<PREC>(P);
+    off += L.w_bytes;
+    L.b_bytes = off;
+    off += (mlp_smem_bias_floats(P) * 4 + 15) & ~15;
+    L.meta = off;
+    off += (int)((sizeof(TileMeta) + 15) & ~15);
+    L.sraw = off;
+    off += cap * 16;
+    L.sidx = off;
+    off += (cap * 2 + 15) & ~15;
+    L.arena = off;
+    off += cap * 16 * 8;
+    // per warp: input tile, (generic MLP: second activation tile), FP8 chaining tile, output staging
+    int act = 0;
+    for (int l = 0; l < P.n_layers; ++l)
+        act = act > 32 * tile_stride_bytes<PREC>(P.kpad[l]) ? act : 32 * tile_stride_bytes<PREC>(P.kpad[l]);
+    act = (act + 15) & ~15;
+    int maxn = 0;
+    for (int l = 0; l < P.n_layers; ++l)
+        maxn = maxn > P.npad[l] ? maxn : P.npad[l];
+    const int tmp = PREC == BCF_FP8_E4M3 ? ((16 * (maxn + 16) + 15) & ~15) : 0;
+    const int ostb = (32 * C * 4 + 15) & ~15;
+    L.act0 = 0;
+    if (generic_mlp) {
+        L.act1 = act;
+        L.tmp8 = 2 * act;
+        L.ost = L.tmp8 + tmp;
+        L.per_warp = L.ost + ostb;
+    } else {
+        // The register-chained MLP loads the A fragments of rows 0-15 of the input tile, writes those rows'
+        // outputs, then loads rows 16-31.  The output staging may share the input tile when the outputs of
+        // rows 0-15 (16 * C floats) end before input row 16 begins.
+        const int in_stride = tile_stride_bytes<PREC>(P.kpad[0]);
+        const int in0 = (32 * in_stride + 15) & ~15;
+        const bool alias = 16 * C * 4 <= 16 * in_stride;
+        const int a0 = alias ? (in0 > ostb ? in0 : ostb) : in0 + ostb;
+        L.act1 = 0;
+        L.ost = alias ? 0 : in0;
+        L.tmp8 = a0;
+        L.per_warp = a0 + tmp;
+    }
+    L.total = off + (kTileQ / 32) * L.per_warp;
+    return L;
+}
+
+// K0 = 0: generic MLP (any layer count, shared-memory chaining); otherwise
+// the register-chained 3-layer MLP with padded widths K0 -> N1 -> N2 -> NO.
+template <int PREC, int CAP, int K0, int N1, int N2, int NO>
+__global__ void __launch_bounds__(kTileQ, 3) k_decode_tiled(MaterialDev M, const float *__restrict__ qu,
+                                                         const float *__restrict__ qv,
+                                                         const float *__restrict__ qs, int64_t n,
+                                                         void *__restrict__ out, int out_fp16)
+{
+    static_assert(CAP <= 2 * kTileQ, "blocks are held two per thread while sorting");
+    extern __shared__ __align__(16) unsigned char smem[];
+    const MlpDev &P = M.mlp;
+    const TiledLayout LY = tiled_layout<PREC>(P, CAP, K0 == 0);
+    unsigned char *sw = smem;
+    float *sb = (float *)(smem + LY.b_bytes);
+    TileMeta &TM = *(TileMeta *)(smem + LY.meta);
+    uint4 *sraw = (uint4 *)(smem + LY.sraw);
+    uint16_t *sidx = (uint16_t *)(smem + LY.sidx);
+    uint2 *arena = (uint2 *)(smem + LY.arena);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char *wbase = smem + LY.total - (kTileQ / 32 - warp) * LY.per_warp;
+    unsigned char *act0 = wbase + LY.act0;
+    unsigned char *act1 = wbase + LY.act1;
+    unsigned char *tmp8 = wbase + LY.tmp8;
+    float *ost = (float *)(wbase + LY.ost);
+    const int C = P.dims[P.n_layers];
+    const int row_stride = tile_stride_bytes<PREC>(P.kpad[0]);
+    unsigned char *myrow = act0 + lane * row_stride;
+    const float inv0 = PREC == BCF_FP8_E4M3 ? P.inv_act_scale[0] : 1.0f;
+    const int nt = M.n_tex;
+    const int wrap = M.wrap;
+    const bool sgn = M.is_signed != 0;
+    const unsigned lanes_lt = (1u << lane) - 1u;
+
+    load_mlp_smem<PREC>(P, sw, sb);
+
+    const int64_t tiles = (n + kTileQ - 1) / kTileQ;
+    // queries of the next tile are loaded one tile ahead
+    float nu = 0.0f, nv = 0.0f, ns = 0.0f;
+    {
+        const int64_t q = (int64_t)blockIdx.x * kTileQ + threadIdx.x;
+        if (blockIdx.x < tiles && q < n) {
+            nu = qu[q];
+            nv = qv[q];
+            ns = qs ? qs[q] : 0.0f;
+        }
+    }
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int64_t q = tile * kTileQ + threadIdx.x;
+        const bool active = q < n;
+        const float u = active ? sanitize(nu, wrap) : 0.0f;
+        const float v = active ? sanitize(nv, wrap) : 0.0f;
+        const float s = active ? ns : 0.0f;
+        {
+            const int64_t qn = (tile + gridDim.x) * kTileQ + threadIdx.x;
+            if (tile + gridDim.x < tiles && qn < n) {
+                nu = qu[qn];
+                nv = qv[qn];
+                ns = qs ? qs[qn] : 0.0f;
+            }
+        }
+        // ---- reset the tile metadata
+        if (threadIdx.x == 0) {
+            TM.u0 = u;
+            TM.v0 = v;
+            TM.smin_bits = INT_MAX;
+            TM.smax_bits = INT_MIN;
+        }
+        for (int i = threadIdx.x; i < kBoxes; i += kTileQ) {
+            TM.bb[i][0] = TM.bb[i][2] = INT_MAX;
+            TM.bb[i][1] = TM.bb[i][3] = INT_MIN;
+        }
+        __syncthreads(); // (also orders the weight load before the first tile's MLP)
+
+        // ---- 1a. LOD range of the tile (NaN reads as 0, as in lod_of)
+        {
+            const float sl = isnan(s) ? 0.0f : s;
+            const int lo = __reduce_min_sync(0xffffffffu, active ? f2ord(sl) : INT_MAX);
+            const int hi = __reduce_max_sync(0xffffffffu, active ? f2ord(sl) : INT_MIN);
+            if (lane == 0 && lo != INT_MAX) {
+                atomicMin(&TM.smin_bits, lo);
+                atomicMax(&TM.smax_bits, hi);
+            }
+        }
+        __syncthreads();
+        // per texture: every l0 lies in [lod(smin).l0, lod(smax).l0] and the upper level adds at most one
+        if (threadIdx.x < nt) {
+            const TexDev &T = M.tex[threadIdx.x];
+            const Lod a = lod_of(T, ord2f(TM.smin_bits)), b = lod_of(T, ord2f(TM.smax_bits));
+            TM.lmin[threadIdx.x] = a.l0;
+            TM.lmax[threadIdx.x] = min(b.l0 + 1, T.levels - 1);
+        }
+        __syncthreads();
+        // ---- 1b. block box per (texture, level)
+        const float u0 = TM.u0, v0 = TM.v0;
+        for (int t = 0; t < nt; ++t) {
+            const TexDev &T = M.tex[t];
+            const int lmin = TM.lmin[t];
+            if (TM.lmax[t] - lmin + 1 > kMaxLv)
+                continue; // this texture is filtered per lane
+            const Lod L = lod_of(T, s);
+            int bx[2][2], by[2][2]; // [side][lo/hi]
+            int slot[2] = {-1, -1};
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                bx[side][0] = bx[side][1] = by[side][0] = by[side][1] = 0;
+                if (active && side < L.nlev) {
+                    const int level = L.l0 + side;
+                    const int W = T.res >> level;
+                    const int i0 = (int)floorf(u * (float)W - 0.5f), j0 = (int)floorf(v * (float)W - 0.5f);
+                    const int rbx = wrap ? ref_block(u0, W) : 0, rby = wrap ? ref_block(v0, W) : 0;
+                    bx[side][0] = rel_block(i0, i0, rbx, W, wrap);
+                    bx[side][1] = rel_block(i0 + 1, i0, rbx, W, wrap);
+                    by[side][0] = rel_block(j0, j0, rby, W, wrap);
+                    by[side][1] = rel_block(j0 + 1, j0, rby, W, wrap);
+                    slot[side] = level - lmin;
+                }
+            }
+#pragma unroll
+            for (int ls = 0; ls < kMaxLv; ++ls) {
+                const int sd = slot[0] == ls ? 0 : (slot[1] == ls ? 1 : -1);
+                const int mnx = __reduce_min_sync(0xffffffffu, sd >= 0 ? bx[sd][0] : INT_MAX);
+                const int mxx = __reduce_max_sync(0xffffffffu, sd >= 0 ? bx[sd][1] : INT_MIN);
+                const int mny = __reduce_min_sync(0xffffffffu, sd >= 0 ? by[sd][0] : INT_MAX);
+                const int mxy = __reduce_max_sync(0xffffffffu, sd >= 0 ? by[sd][1] : INT_MIN);
+                if (lane == 0 && mnx != INT_MAX) {
+                    int *bb = TM.bb[t * kMaxLv + ls];
+                    atomicMin(&bb[0], mnx);
+                    atomicMax(&bb[1], mxx);
+                    atomicMin(&bb[2], mny);
+                    atomicMax(&bb[3], mxy);
+                }
+            }
+        }
+        __syncthreads();
+        // ---- 1c. arena rounds: consecutive textures whose boxes fit together
+        if (threadIdx.x == 0) {
+            int r = 0, acc = 0;
+            TM.rtex[0] = 0;
+            for (int t = 0; t < nt; ++t) {
+                int tt = 0;
+                const bool fits_levels = TM.lmax[t] - TM.lmin[t] + 1 <= kMaxLv;
+                for (int ls = 0; ls < kMaxLv; ++ls) {
+                    const int k = t * kMaxLv + ls;
+                    const int *bb = TM.bb[k];
+                    TM.bw[k] = bb[0] != INT_MAX ? bb[1] - bb[0] + 1 : 0;
+                    tt += bb[0] != INT_MAX ? TM.bw[k] * (bb[3] - bb[2] + 1) : 0;
+                }
+                TM.direct[t] = !fits_levels || tt > CAP;
+                if (TM.direct[t])
+                    tt = 0;
+                if (acc + tt > CAP) { // close the current round
+                    TM.rtotal[r] = acc;
+                    ++r;
+                    TM.rtex[r] = t;
+                    acc = 0;
+                }
+                for (int ls = 0; ls < kMaxLv; ++ls) {
+                    const int k = t * kMaxLv + ls;
+                    TM.base[k] = acc;
+                    if (!TM.direct[t] && TM.bb[k][0] != INT_MAX)
+                        acc += TM.bw[k] * (TM.bb[k][3] - TM.bb[k][2] + 1);
+                }
+            }
+            TM.rtotal[r] = acc;
+            TM.rtex[r + 1] = nt;
+            TM.nrounds = r + 1;
+        }
+        __syncthreads();
+        const int nrounds = TM.nrounds;
+        for (int r = 0; r < nrounds; ++r) {
+            const int t_beg = TM.rtex[r], t_end = TM.rtex[r + 1], total = TM.rtotal[r];
+            if (total > 0) {
+                // ---- 2. load each block once (two per thread), histogram the modes
+                if (threadIdx.x < 16)
+                    TM.hist[threadIdx.x] = 0;
+                __syncthreads();
+                uint4 blk[2];
+                int bin[2], bidx[2];
+#pragma unroll
+                for (int it = 0; it < 2; ++it) {
+                    const int b = it * kTileQ + threadIdx.x;
+                    const bool valid = b < total;
+                    bin[it] = kBins + lane; // unique per lane when invalid: no aggregation
+                    bidx[it] = b;
+                    blk[it] = make_uint4(0, 0, 0, 0);
+                    if (valid) {
+                        int k = t_beg * kMaxLv;
+                        while (TM.bw[k] == 0 || TM.direct[k / kMaxLv] ||
+                               b >= TM.base[k] + TM.bw[k] * (TM.bb[k][3] - TM.bb[k][2] + 1))
+                            ++k;
+                        const int t = k / kMaxLv;
+                        const TexDev &T = M.tex[t];
+                        const int level = TM.lmin[t] + (k - t * kMaxLv);
+                        const int local = b - TM.base[k];
+                        const int bwk = TM.bw[k];
+                        const int ry = local / bwk;
+                        const int rx = TM.bb[k][0] + (local - ry * bwk);
+                        const int W = T.res >> level, wb = W >> 2;
+                        int bxa = rx, bya = TM.bb[k][2] + ry;
+                        if (wrap) {
+                            bxa = (ref_block(u0, W) + bxa) & (wb - 1);
+                            bya = (ref_block(v0, W) + bya) & (wb - 1);
+                        }
+                        blk[it] = __ldg(T.blocks + level_offset((uint32_t)(T.res >> 2), level) +
+                                        (uint32_t)bya * (uint32_t)wb + (uint32_t)bxa);
+                        const int mi = mode_index(blk[it].x);
+                        bin[it] = mi < 0 ? kBins - 1 : mi;
+                    }
+                    const unsigned peers = __match_any_sync(0xffffffffu, bin[it]);
+                    if (valid && (peers & lanes_lt) == 0)
+                        atomicAdd(&TM.hist[bin[it]], __popc(peers));
+                }
+                __syncthreads();
+                if (threadIdx.x == 0) {
+                    int acc = 0;
+                    for (int i = 0; i < kBins; ++i) {
+                        TM.offs[i] = acc;
+                        acc += TM.hist[i];
+                    }
+                }
+                __syncthreads();
+                // ---- 3. scatter into mode-sorted order
+#pragma unroll
+                for (int it = 0; it < 2; ++it) {
+                    const bool valid = bidx[it] < total;
+                    const unsigned peers = __match_any_sync(0xffffffffu, bin[it]);
+                    const int leader = __ffs(peers) - 1;
+                    int pos = 0;
+                    if (valid && lane == leader)
+                        pos = atomicAdd(&TM.offs[bin[it]], __popc(peers));
+                    pos = __shfl_sync(0xffffffffu, pos, leader) + __popc(peers & lanes_lt);
+                    if (valid) {
+                        sraw[pos] = blk[it];
+                        sidx[pos] = (uint16_t)bidx[it];
+                    }
+                }
+                __syncthreads();
+                // ---- 4. decode the sorted blocks into the texel arena: two threads per block (the header is
+                // decoded by both, each then writes 8 texels); neighbouring lanes take the same block
+                for (int i = threadIdx.x; i < 2 * total; i += kTileQ) {
+                    const int e = i >> 1, half = i & 1;
+                    const uint4 rr = sraw[e];
+                    const int b = sidx[e];
+                    Bc6hBlock bk;
+                    bk.lo = (uint64_t)rr.x | ((uint64_t)rr.y << 32);
+                    bk.hi = (uint64_t)rr.z | ((uint64_t)rr.w << 32);
+                    Bc6hHeader H;
+                    bc6h_header(bk, sgn, H);
+                    bc6h_half_texels(bk, H, sgn, half, [&](int t, uint32_t rg, uint32_t bb) {
+                        arena[arena_slot(b, t)] = make_uint2(rg, bb);
+                    });
+                }
+                __syncthreads();
+            }
+            // ---- 5. filter the round's textures (per lane where a texture did not fit)
+            for (int t = t_beg; t < t_end; ++t) {
+                const TexDev &T = M.tex[t];
+                float f0 = 0.0f, f1 = 0.0f, f2 = 0.0f;
+                if (active) {
+                    if (!TM.direct[t]) {
+                        const Lod L = lod_of(T, s);
+                        for (int side = 0; side < L.nlev; ++side) {
+                            const int level = L.l0 + side;
+                            const float scale = L.nlev == 1 ? 1.0f : (side ? L.lam : 1.0f - L.lam);
+                            const int W = T.res >> level;
+                            const float x = u * (float)W - 0.5f, y = v * (float)W - 0.5f;
+                            const float fx0 = floorf(x), fy0 = floorf(y);
+                            const float fx = x - fx0, fy = y - fy0;
+                            const int i0 = (int)fx0, j0 = (int)fy0;
+                            const int k = t * kMaxLv + level - TM.lmin[t];
+                            const int rbx = wrap ? ref_block(u0, W) : 0, rby = wrap ? ref_block(v0, W) : 0;
+                            const int bwk = TM.bw[k], basek = TM.base[k];
+                            const int bhk = TM.bb[k][3] - TM.bb[k][2] + 1;
+                            // the box was built from the same integer coordinates, so these are inside
+                            // it; the clamps only guarantee in-bounds shared-memory reads
+                            const int bxl = min(max(rel_block(i0, i0, rbx, W, wrap) - TM.bb[k][0], 0), bwk - 1);
+                            const int bxh = min(max(rel_block(i0 + 1, i0, rbx, W, wrap) - TM.bb[k][0], 0), bwk - 1);
+                            const int byl = min(max(rel_block(j0, j0, rby, W, wrap) - TM.bb[k][2], 0), bhk - 1);
+                            const int byh = min(max(rel_block(j0 + 1, j0, rby, W, wrap) - TM.bb[k][2], 0), bhk - 1);
+                            const int cl = texel_col(i0, W, wrap), ch = texel_col(i0 + 1, W, wrap);
+                            const int rl = texel_col(j0, W, wrap) * 4, rh = texel_col(j0 + 1, W, wrap) * 4;
+                            const int b00 = basek + byl * bwk + bxl, b10 = basek + byl * bwk + bxh;
+                            const int b01 = basek + byh * bwk + bxl, b11 = basek + byh * bwk + bxh;
+                            const uint2 t00 = arena[arena_slot(b00, rl + cl)];
+                            const uint2 t10 = arena[arena_slot(b10, rl + ch)];
+                            const uint2 t01 = arena[arena_slot(b01, rh + cl)];
+                            const uint2 t11 = arena[arena_slot(b11, rh + ch)];
+                            const float w00 = (1.0f - fx) * (1.0f - fy) * scale, w10 = fx * (1.0f - fy) * scale;
+                            const float w01 = (1.0f - fx) * fy * scale, w11 = fx * fy * scale;
+#define BCF_ACC(tx, w)                                                                                             \
+    {                                                                                                              \
+        const float2 rg = __half22float2(*reinterpret_cast<const __half2 *>(&tx.x));                               \
+        f0 = fmaf(w, rg.x, f0);                                                                                    \
+        f1 = fmaf(w, rg.y, f1);                                                                                    \
+        f2 = fmaf(w, __half2float(__ushort_as_half((unsigned short)tx.y)), f2);                                    \
+    }
+                            BCF_ACC(t00, w00) BCF_ACC(t10, w10) BCF_ACC(t01, w01) BCF_ACC(t11, w11)
+#undef BCF_ACC
+                        }
+                    } else {
+                        const float3 f = sample_texture(T, wrap, sgn, u, v, s);
+                        f0 = f.x;
+                        f1 = f.y;
+                        f2 = f.z;
+                    }
+                }
+                store_feature<PREC>(myrow, 3 * t, f0, inv0);
+                store_feature<PREC>(myrow, 3 * t + 1, f1, inv0);
+                store_feature<PREC>(myrow, 3 * t + 2, f2, inv0);
+            }
+            __syncthreads(); // the arena is refilled by the next round / tile
+        }
+        {
+            int col = 3 * nt;
+            if (M.lod_input) {
+                store_feature<PREC>(myrow, col, active ? (isnan(s) ? 0.0f : fmaxf(s, 0.0f)) : 0.0f, inv0);
+                ++col;
+            }
+            for (; col < P.kpad[0]; ++col)
+                store_feature<PREC>(myrow, col, 0.0f, inv0);
+        }
+        __syncwarp();
+        // ---- 6. MLP on the tensor cores, coalesced store
+        if constexpr (K0 == 0)
+            warp_mlp<PREC>(P, sw, sb, act0, act1, ost);
+        else
+            warp_mlp3<PREC, K0, N1, N2, NO>(P, sw, sb, act0, row_stride, tmp8,
+                                            tile_stride_bytes<BCF_FP8_E4M3>(N1 > N2 ? N1 : N2), ost, C);
+        __syncwarp();
+        const int64_t q0 = tile * kTileQ + warp * 32;
+        if (q0 < n) {
+            const int rows = (int)min((int64_t)32, n - q0);
+            const int tot = rows * C;
+            if (out_fp16) {
+                __half *o = (__half *)out + q0 * C;
+                for (int i = lane; i < tot; i += 32)
+                    o[i] = __float2half_rn(ost[i]);
+            } else {
+                float *o = (float *)out + q0 * C;
+                for (int i = lane; i < tot; i += 32)
+                    o[i] = ost[i];
+            }
+        }
+        __syncwarp();
+    }
+}
+
+// ---------------------------------------------------------------- launcher
+
+constexpr int kArenaCap = 320;
+
+static int tiled_sms()
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0)
+            sms = 148;
+    }
+    return sms;
+}
+
+template <int PREC, int K0, int N1, int N2, int NO>
+static cudaError_t launch_tiled_shape(const MaterialDev &M, const float *u, const float *v, const float *s, int64_t n,
+                                      void *out, int out_fp16, cudaStream_t st)
+{
+    const int64_t smem = tiled_layout<PREC>(M.mlp, kArenaCap, K0 == 0).total;
+    if (smem > 227 * 1024)
+        return cudaErrorInvalidConfiguration;
+    auto kern = k_decode_tiled<PREC, kArenaCap, K0, N1, N2, NO>;
+    static int configured = 0;
+    if (!configured) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        configured = 1;
+    }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTileQ, (size_t)smem);
+    const int64_t tiles = (n + kTileQ - 1) / kTileQ;
+    const int64_t grid = min(tiles, (int64_t)tiled_sms() * max(per_sm, 1));
+    kern<<<(unsigned)grid, kTileQ, (size_t)smem, st>>>(M, u, v, s, n, out, out_fp16);
+    return cudaGetLastError();
+}
+
+template <int PREC>
+static cudaError_t launch_tiled_prec(const MaterialDev &M, const float *u, const float *v, const float *s, int64_t n,
+                                     void *out, int out_fp16, cudaStream_t st)
+{
+    const MlpDev &P = M.mlp;
+    if (P.n_layers == 3) {
+        const int k0 = P.kpad[0], n1 = P.npad[0], n2 = P.npad[1], no = P.npad[2];
+        constexpr int kq = PREC == BCF_FP8_E4M3 ? 32 : 16;
+        if (k0 == kq && n1 == 32 && n2 == 32 && no == 16)
+            return launch_tiled_shape<PREC, kq, 32, 32, 16>(M, u, v, s, n, out, out_fp16, st);
+        if (k0 == 32 && n1 == 64 && n2 == 64 && no == 16)
+            return launch_tiled_shape<PREC, 32, 64, 64, 16>(M, u, v, s, n, out, out_fp16, st);
+    }
+    return launch_tiled_shape<PREC, 0, 0, 0, 0>(M, u, v, s, n, out, out_fp16, st);
+}
+
+cudaError_t launch_decode_tiled(const MaterialDev &M, const float *u, const float *v, const float *s, int64_t n,
+                                void *out, int out_fp16, cudaStream_t st)
+{
+    if (n == 0)
+        return cudaSuccess;
+    switch (M.mlp.precision) {
+    case BCF_FP16: return launch_tiled_prec<BCF_FP16>(M, u, v, s, n, out, out_fp16, st);
+    case BCF_BF16: return launch_tiled_prec<BCF_BF16>(M, u, v, s, n, out, out_fp16, st);
+    case BCF_FP8_E4M3: return launch_tiled_prec<BCF_FP8_E4M3>(M, u, v, s, n, out, out_fp16, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+int64_t decode_tiled_smem_bytes(const MlpDev &P)
+{
+    switch (P.precision) {
+    case BCF_FP16: return tiled_layout<BCF_FP16>(P, kArenaCap, true).total;
+    case BCF_BF16: return tiled_layout<BCF_BF16>(P, kArenaCap, true).total;
+    case BCF_FP8_E4M3: return tiled_layout<BCF_FP8_E4M3>(P, kArenaCap, true).total;
+    default: return 0;
+    }
+}
+
+} // namespace bcf

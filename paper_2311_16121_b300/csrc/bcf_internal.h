@@ -53,4 +53,5 @@ struct bcf_material_s {
     bcf::MaterialDev host;   // host copy (passed by value to single-material kernels)
     bcf::MaterialDev *dev;   // device copy (batched kernels)
     int device;
+    int variant;             // tensor-core decode: 0 tile-cooperative, 1 per-lane
 };

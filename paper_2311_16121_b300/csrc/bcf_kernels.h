@@ -15,6 +15,9 @@ cudaError_t launch_decode_fp32(const MaterialDev &M, const float *u, const float
 cudaError_t launch_decode_mma(const MaterialDev &M, const float *u, const float *v, const float *s, int64_t n,
                               void *out, int out_fp16, cudaStream_t st);
 int64_t decode_mma_smem_bytes(const MlpDev &P);
+cudaError_t launch_decode_tiled(const MaterialDev &M, const float *u, const float *v, const float *s, int64_t n,
+                                void *out, int out_fp16, cudaStream_t st);
+int64_t decode_tiled_smem_bytes(const MlpDev &P);
 cudaError_t texunit_decode(const void *d_blocks, int bw, int bh, int is_signed, uint16_t *d_out, cudaStream_t st);
 
 // thread-local error text

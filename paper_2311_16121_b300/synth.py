@@ -159,10 +159,13 @@ def random_blocks(rng: np.random.Generator, n: int) -> np.ndarray:
     return out
 
 
-def bounded_blocks(rng: np.random.Generator, n: int, modes=tuple(range(1, 15)), frac: float = 0.48) -> np.ndarray:
-    """n BC6H (unsigned) blocks whose endpoints all lie in the lowest `frac` of their mode's range, so every
-    decoded texel is at most 1.0 for frac <= 0.48.  Mode uniform over `modes`; partitions and indices random;
-    delta-coded modes get deltas drawn inside both the delta field's range and the endpoint bound."""
+def bounded_blocks(rng: np.random.Generator, n: int, modes=tuple(range(1, 15)), frac: float = 0.48,
+                   signed: bool = False) -> np.ndarray:
+    """n BC6H blocks whose endpoints all lie in the lowest `frac` of their mode's range, so every decoded
+    texel is at most 1.0 in magnitude for frac <= 0.48.  Unsigned: endpoints in [0, frac 2^epb].  Signed:
+    endpoints in [-frac 2^(epb-1), frac 2^(epb-1)], stored as two's complement.  Mode uniform over `modes`;
+    partitions and indices random; delta-coded modes get deltas inside both the delta field's range and the
+    endpoint bound."""
     out = np.zeros((n, 16), np.uint8)
     mode_of = rng.choice(np.asarray(modes), n)
     for m in modes:
@@ -171,21 +174,22 @@ def bounded_blocks(rng: np.random.Generator, n: int, modes=tuple(range(1, 15)), 
         if k == 0:
             continue
         epb, dbits, regions, delta = MODE_PREC[m]
-        emax = int(frac * (1 << epb))
+        emax = int(frac * (1 << (epb - 1 if signed else epb)))
+        emin = -emax if signed else 0
         ep = np.zeros((k, 4, 3), np.int64)
         n_ep = 2 * regions
         for c in range(3):
-            e0 = rng.integers(0, emax + 1, k)
-            ep[:, 0, c] = e0
+            e0 = rng.integers(emin, emax + 1, k)
+            ep[:, 0, c] = e0 & ((1 << epb) - 1)
             for i in range(1, n_ep):
                 if delta:
                     d = dbits[c]
-                    lo_d = np.maximum(-(1 << (d - 1)), -e0)
+                    lo_d = np.maximum(-(1 << (d - 1)), emin - e0)
                     hi_d = np.minimum((1 << (d - 1)) - 1, emax - e0)
                     dv = lo_d + np.floor(rng.random(k) * (hi_d - lo_d + 1)).astype(np.int64)
                     ep[:, i, c] = dv & ((1 << d) - 1)
                 else:
-                    ep[:, i, c] = rng.integers(0, emax + 1, k)
+                    ep[:, i, c] = rng.integers(emin, emax + 1, k) & ((1 << epb) - 1)
         part = rng.integers(0, 32, k)
         ib = 3 if regions == 2 else 4
         idx = rng.integers(0, 1 << ib, (k, 16))
@@ -240,15 +244,26 @@ def uniform_queries(rng: np.random.Generator, n: int, s_range=None):
     return u, v, s
 
 
+def tile_order(w: int, h: int, tile: int) -> np.ndarray:
+    """Permutation of a row-major w x h pixel grid into tile x tile screen tiles (tiles row-major, pixels
+    row-major inside a tile, partial tiles at the right / bottom edges), the layout GPU render targets use."""
+    ys, xs = np.meshgrid(np.arange(h), np.arange(w), indexing="ij")
+    tiles_x = (w + tile - 1) // tile
+    key = ((ys // tile) * tiles_x + xs // tile) * (tile * tile) + (ys % tile) * tile + (xs % tile)
+    return np.argsort(key.ravel(), kind="stable")
+
+
 def plane_queries(rng: np.random.Generator, width: int, height: int, res_ref: int, uv_scale: float = 0.5,
-                  x0: int = 0, y0: int = 0, w: int | None = None, h: int | None = None, supersample: int = 1):
+                  x0: int = 0, y0: int = 0, w: int | None = None, h: int | None = None, supersample: int = 1,
+                  tile: int = 16):
     """1-spp G-buffer of a perspective-viewed tiled plane.
 
     Camera 1 unit above the plane z = 0, pitch ~ U[45, 55] degrees below the horizon, yaw ~ U[0, 360),
     vertical FOV 60 degrees, aspect width/height; per-pixel jitter ~ U[-0.5, 0.5]^2.  uv = world_xy * uv_scale
     (repeat addressing wraps it).  s = log2(max(|d uv/dx|, |d uv/dy|) * res_ref) from the FP64 screen
     Jacobian, clamped at 0 (magnification).  An optional sub-rectangle (x0, y0, w, h) of the screen is returned;
-    `supersample` renders a (width*ss) x (height*ss) grid.  Returns float32 u, v, s in row-major pixel order."""
+    `supersample` renders a (width*ss) x (height*ss) grid.  Returns float32 u, v, s in 16 x 16 screen-tile
+    order (`tile`; 0 = row-major pixel order)."""
     W, H = width * supersample, height * supersample
     w = W if w is None else w
     h = H if h is None else h
@@ -287,7 +302,11 @@ def plane_queries(rng: np.random.Generator, width: int, height: int, res_ref: in
     s = np.maximum(s, 0.0)
     u = u - np.floor(u)
     v = v - np.floor(v)
-    return (u.astype(np.float32).ravel(), v.astype(np.float32).ravel(), s.astype(np.float32).ravel())
+    u, v, s = u.astype(np.float32).ravel(), v.astype(np.float32).ravel(), s.astype(np.float32).ravel()
+    if tile:
+        perm = tile_order(w, h, tile)
+        u, v, s = u[perm], v[perm], s[perm]
+    return u, v, s
 
 
 # --------------------------------------------------------------------------- MLP weights

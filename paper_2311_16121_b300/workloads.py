@@ -70,7 +70,8 @@ def config1() -> DecodeWorkload:
 
 
 def screen_material(config: int, n_tex: int, res: int, dims: list[int], width: int, height: int,
-                    supersample: int = 1, pool: int | None = None, modes=tuple(range(1, 15))) -> DecodeWorkload:
+                    supersample: int = 1, pool: int | None = None, modes=tuple(range(1, 15)),
+                    tile: int = 16) -> DecodeWorkload:
     levels = synth.full_levels(res)
     rng = seed_rng(config, 0)
     if pool:
@@ -78,7 +79,8 @@ def screen_material(config: int, n_tex: int, res: int, dims: list[int], width: i
     else:
         blocks = [synth.bounded_blocks(rng, sum(synth.level_blocks(res, levels)), modes=modes) for _ in range(n_tex)]
         tex = synth.TextureSet([res] * n_tex, [levels] * n_tex, blocks)
-    u, v, s = synth.plane_queries(seed_rng(config, 1), width, height, res_ref=res, supersample=supersample)
+    u, v, s = synth.plane_queries(seed_rng(config, 1), width, height, res_ref=res, supersample=supersample,
+                                  tile=tile)
     W, b = synth.mlp_weights(seed_rng(config, 2), dims)
     return DecodeWorkload(f"config{config}", [res] * n_tex, [levels] * n_tex, res, tex.blocks, True, dims, W, b, u, v,
                           s, input_bound=max(1.0, float(s.max())))
@@ -93,9 +95,9 @@ def config5() -> DecodeWorkload:
 
 
 def small_screen(config: int = 2, n_tex: int = 4, res: int = 64, dims=(13, 32, 32, 9), width: int = 96,
-                 height: int = 54, modes=tuple(range(1, 15))) -> DecodeWorkload:
+                 height: int = 54, modes=tuple(range(1, 15)), tile: int = 16) -> DecodeWorkload:
     """A reduced screen workload with the structure of configs 2/5 (for parity tests)."""
-    w = screen_material(config, n_tex, res, list(dims), width, height, modes=modes)
+    w = screen_material(config, n_tex, res, list(dims), width, height, modes=modes, tile=tile)
     w.name = f"small-screen-{n_tex}x{res}-{width}x{height}"
     return w
 

@@ -219,3 +219,55 @@ def test_invalid_arguments_return_status_without_launching():
     with pytest.raises(bcf.BcfError):
         bcf.decode_bc6h(_gpu_blocks(np.zeros(16, np.uint8)), -1, 1,
                         out=torch.empty(48, dtype=torch.int16, device="cuda"))
+
+
+# --------------------------------------------------------------------------- tile-cooperative kernel
+
+def _decode_both(w, precision, u=None, v=None, s=None, out_dtype=torch.float32):
+    m = workloads.upload(w, precision)
+    if u is None:
+        u, v, s = workloads.queries_to_device(w)
+    m.set_decode_variant(0)
+    a = m.decode(u, v, s, out_dtype=out_dtype).cpu().numpy()
+    m.set_decode_variant(1)
+    b = m.decode(u, v, s, out_dtype=out_dtype).cpu().numpy()
+    return a, b
+
+
+@pytest.mark.parametrize("precision", ["fp16", "bf16", "fp8"])
+def test_tiled_equals_per_lane_bit_for_bit(precision):
+    """The tile-cooperative kernel filters the same texel values with the same
+    FP32 operation order as the per-lane kernel: identical outputs."""
+    _bcf()
+    w = workloads.small_screen(res=256, width=230, height=77)  # 17,710 queries: 70 tiles, ragged last tile
+    a, b = _decode_both(w, precision)
+    np.testing.assert_array_equal(a, b)
+
+
+@pytest.mark.parametrize("case", ["row_order", "random_uv", "wide_lod", "clamp", "signed"])
+def test_tiled_fallbacks_and_addressing_match_oracle(case):
+    """Incoherent tiles (arena overflow), tiles spanning more than three
+    levels, clamp addressing, signed textures and row-major query order."""
+    _bcf()
+    kw = {}
+    if case == "row_order":
+        kw["tile"] = 0
+    w = workloads.small_screen(res=128, width=120, height=40, **kw)
+    rng = workloads.seed_rng(2, 99)
+    if case == "random_uv":
+        w.u = rng.random(w.n, dtype=np.float32)
+        w.v = rng.random(w.n, dtype=np.float32)
+    elif case == "wide_lod":
+        w.s = rng.uniform(-1.0, 7.0, w.n).astype(np.float32)
+    elif case == "clamp":
+        w.wrap = False
+        w.u = (w.u * 1.3 - 0.15).astype(np.float32)
+    elif case == "signed":
+        w.is_signed = True
+        w.blocks = [synth.bounded_blocks(rng, b.shape[0], signed=True) for b in w.blocks]
+    a, b = _decode_both(w, "fp16")
+    np.testing.assert_array_equal(a, b)
+    Wst, bias, _, _ = w.weights("fp16")
+    ref_q = oracle.decode(_oracle_material(w), oracle.Mlp(w.dims, "fp16", Wst, bias), w.u, w.v, w.s,
+                          quant_aware=True, threads=8)
+    _quant_check(a.astype(np.float64), ref_q, TOL["fp16"], case)
