@@ -409,6 +409,10 @@ __device__ __forceinline__ void bc6h_all_texels(const Bc6hBlock &blk, const Bc6h
 namespace bcf {
 
 // Texels 8 * half .. 8 * half + 7 of a decoded block (as bc6h_all_texels).
+// Each region's channels are kept as (64 a + 32, b - a), so a texel channel
+// is (64 a + 32 + (b - a) w) >> 6 -- the same integer as
+// (a (64 - w) + b w + 32) >> 6.  Reserved modes have all endpoints zero,
+// which decodes to zero texels.
 template <class Store>
 __device__ __forceinline__ void bc6h_half_texels(const Bc6hBlock &blk, const Bc6hHeader &H, bool sgn, int half,
                                                  Store store)
@@ -424,6 +428,14 @@ __device__ __forceinline__ void bc6h_half_texels(const Bc6hBlock &blk, const Bc6
     } else {
         idx = blk.hi >> (1 + (half ? 31 : 0));
     }
+    int base0[3], del0[3], base1[3], del1[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        base0[c] = 64 * H.e[0][c] + 32;
+        del0[c] = H.e[1][c] - H.e[0][c];
+        base1[c] = 64 * H.e[2][c] + 32;
+        del1[c] = H.e[3][c] - H.e[2][c];
+    }
     const int t0 = 8 * half;
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
@@ -438,15 +450,10 @@ __device__ __forceinline__ void bc6h_half_texels(const Bc6hBlock &blk, const Bc6
             w = weight4((int)(idx & ((1u << nb) - 1)));
             idx >>= nb;
         }
-        const int region = (int)((pmask >> t) & 1);
-        const int *ea = region ? H.e[2] : H.e[0];
-        const int *eb = region ? H.e[3] : H.e[1];
-        const int vr = (ea[0] * (64 - w) + eb[0] * w + 32) >> 6;
-        const int vg = (ea[1] * (64 - w) + eb[1] * w + 32) >> 6;
-        const int vb = (ea[2] * (64 - w) + eb[2] * w + 32) >> 6;
-        const uint32_t r = H.valid ? finish(vr, sgn) : 0u;
-        const uint32_t g = H.valid ? finish(vg, sgn) : 0u;
-        const uint32_t b = H.valid ? finish(vb, sgn) : 0u;
+        const bool r1 = (pmask >> t) & 1;
+        const uint32_t r = finish(((r1 ? base1[0] : base0[0]) + (r1 ? del1[0] : del0[0]) * w) >> 6, sgn);
+        const uint32_t g = finish(((r1 ? base1[1] : base0[1]) + (r1 ? del1[1] : del0[1]) * w) >> 6, sgn);
+        const uint32_t b = finish(((r1 ? base1[2] : base0[2]) + (r1 ? del1[2] : del0[2]) * w) >> 6, sgn);
         store(t, r | (g << 16), b);
     }
 }

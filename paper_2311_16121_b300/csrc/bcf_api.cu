@@ -138,6 +138,16 @@ bcf_status bcf_create_material(const bcf_material_desc *d, bcf_material *out)
         }
     }
     M.n_in = 3 * M.n_tex + M.lod_input;
+    M.n_groups = 0;
+    for (int t = 0; t < M.n_tex; ++t) {
+        int g = 0;
+        while (g < M.n_groups && !(M.tex[M.group_first[g]].res == M.tex[t].res &&
+                                   M.tex[M.group_first[g]].levels == M.tex[t].levels))
+            ++g;
+        if (g == M.n_groups)
+            M.group_first[M.n_groups++] = t;
+        M.tex_group[t] = g;
+    }
     MlpDev &P = M.mlp;
     if (d->n_layers < 1 || d->n_layers > BCF_MAX_LAYERS)
         return fail(BCF_ERR_INVALID_ARG, "n_layers %d not in [1, %d]", d->n_layers, BCF_MAX_LAYERS);

@@ -38,16 +38,18 @@ constexpr int kBins = 15;      // 14 modes + reserved
 
 struct TileMeta {
     float u0, v0;
-    int smin_bits, smax_bits; // tile LOD range (order-preserving integer images of the floats)
+    int smin_bits, smax_bits;  // tile LOD range (order-preserving integer images of the floats)
     int nrounds;
-    int lmin[BCF_MAX_TEX];
+    int lmin[BCF_MAX_TEX];     // per geometry group: levels [lmin, lmax] hold the tile's footprints
     int lmax[BCF_MAX_TEX];
-    int direct[BCF_MAX_TEX];     // 1: this texture is filtered by the per-lane decode
-    int bb[kBoxes][4];           // min x, max x, min y, max y of the box (relative block coordinates)
-    int base[kBoxes];            // first arena block of each box within its round
-    int bw[kBoxes];              // box width in blocks
-    int rtex[BCF_MAX_TEX + 1];   // textures [rtex[r], rtex[r+1]) form round r
-    int rtotal[BCF_MAX_TEX];     // blocks of round r
+    int direct[BCF_MAX_TEX];   // per group: 1 = filtered by the per-lane decode
+    int gtotal[BCF_MAX_TEX];   // per group: blocks of one texture's boxes
+    int bb[kBoxes][4];         // per (group, level slot): min x, max x, min y, max y (relative block coordinates)
+    int bw[kBoxes];            // box width in blocks
+    int boff[kBoxes];          // offset of the box inside one texture's block set
+    int tbase[BCF_MAX_TEX];    // per texture: first arena block of its block set within its round
+    int rtex[BCF_MAX_TEX + 1]; // textures [rtex[r], rtex[r+1]) form round r
+    int rtotal[BCF_MAX_TEX];   // blocks of round r
     int hist[16];
     int offs[16];
 };
@@ -146,7 +148,7 @@ __host__ __device__ inline TiledLayout tiled_layout(const MlpDev &P, int cap, bo
     int maxn = 0;
     for (int l = 0; l < P.n_layers; ++l)
         maxn = maxn > P.npad[l] ? maxn : P.npad[l];
-    const int tmp = PREC == BCF_FP8_E4M3 ? ((16 * (maxn + 16) + 15) & ~15) : 0;
+    const int tmp = PREC == BCF_FP8_E4M3 ? ((16 * (maxn + 16) + 15) & ~15) : 0; // one 16-row pass (MlpRows)
     const int ostb = (32 * C * 4 + 15) & ~15;
     L.act0 = 0;
     if (generic_mlp) {
@@ -155,8 +157,8 @@ __host__ __device__ inline TiledLayout tiled_layout(const MlpDev &P, int cap, bo
         L.ost = L.tmp8 + tmp;
         L.per_warp = L.ost + ostb;
     } else {
-        // The register-chained MLP loads the A fragments of rows 0-15 of the input tile, writes those rows'
-        // outputs, then loads rows 16-31.  The output staging may share the input tile when the outputs of
+        // The register-chained MLP loads the A fragments of all rows of a pass (16 or 32 rows) before it
+        // writes that pass's outputs.  The output staging may share the input tile when the outputs of
         // rows 0-15 (16 * C floats) end before input row 16 begins.
         const int in_stride = tile_stride_bytes<PREC>(P.kpad[0]);
         const int in0 = (32 * in_stride + 15) & ~15;
@@ -200,6 +202,7 @@ __global__ void __launch_bounds__(kTileQ, 3) k_decode_tiled(MaterialDev M, const
     unsigned char *myrow = act0 + lane * row_stride;
     const float inv0 = PREC == BCF_FP8_E4M3 ? P.inv_act_scale[0] : 1.0f;
     const int nt = M.n_tex;
+    const int ng = M.n_groups;
     const int wrap = M.wrap;
     const bool sgn = M.is_signed != 0;
     const unsigned lanes_lt = (1u << lane) - 1u;
@@ -255,21 +258,21 @@ __global__ void __launch_bounds__(kTileQ, 3) k_decode_tiled(MaterialDev M, const
             }
         }
         __syncthreads();
-        // per texture: every l0 lies in [lod(smin).l0, lod(smax).l0] and the upper level adds at most one
-        if (threadIdx.x < nt) {
-            const TexDev &T = M.tex[threadIdx.x];
-            const Lod a = lod_of(T, ord2f(TM.smin_bits)), b = lod_of(T, ord2f(TM.smax_bits));
-            TM.lmin[threadIdx.x] = a.l0;
-            TM.lmax[threadIdx.x] = min(b.l0 + 1, T.levels - 1);
+        // per geometry group: every l0 lies in [lod(smin).l0, lod(smax).l0] and the upper level adds at most one
+        if (threadIdx.x < ng) {
+            const TexDev &T = M.tex[M.group_first[threadIdx.x]];
+            const Lod lo = lod_of(T, ord2f(TM.smin_bits)), hi = lod_of(T, ord2f(TM.smax_bits));
+            TM.lmin[threadIdx.x] = lo.l0;
+            TM.lmax[threadIdx.x] = min(hi.l0 + 1, T.levels - 1);
         }
         __syncthreads();
-        // ---- 1b. block box per (texture, level)
+        // ---- 1b. block box per (group, level)
         const float u0 = TM.u0, v0 = TM.v0;
-        for (int t = 0; t < nt; ++t) {
-            const TexDev &T = M.tex[t];
-            const int lmin = TM.lmin[t];
-            if (TM.lmax[t] - lmin + 1 > kMaxLv)
-                continue; // this texture is filtered per lane
+        for (int g = 0; g < ng; ++g) {
+            const TexDev &T = M.tex[M.group_first[g]];
+            const int lmin = TM.lmin[g];
+            if (TM.lmax[g] - lmin + 1 > kMaxLv)
+                continue; // this group is filtered per lane
             const Lod L = lod_of(T, s);
             int bx[2][2], by[2][2]; // [side][lo/hi]
             int slot[2] = {-1, -1};
@@ -296,7 +299,7 @@ __global__ void __launch_bounds__(kTileQ, 3) k_decode_tiled(MaterialDev M, const
                 const int mny = __reduce_min_sync(0xffffffffu, sd >= 0 ? by[sd][0] : INT_MAX);
                 const int mxy = __reduce_max_sync(0xffffffffu, sd >= 0 ? by[sd][1] : INT_MIN);
                 if (lane == 0 && mnx != INT_MAX) {
-                    int *bb = TM.bb[t * kMaxLv + ls];
+                    int *bb = TM.bb[g * kMaxLv + ls];
                     atomicMin(&bb[0], mnx);
                     atomicMax(&bb[1], mxx);
                     atomicMin(&bb[2], mny);
@@ -305,34 +308,32 @@ __global__ void __launch_bounds__(kTileQ, 3) k_decode_tiled(MaterialDev M, const
             }
         }
         __syncthreads();
-        // ---- 1c. arena rounds: consecutive textures whose boxes fit together
+        // ---- 1c. per-group block sets and arena rounds of consecutive textures
         if (threadIdx.x == 0) {
-            int r = 0, acc = 0;
-            TM.rtex[0] = 0;
-            for (int t = 0; t < nt; ++t) {
+            for (int g = 0; g < ng; ++g) {
                 int tt = 0;
-                const bool fits_levels = TM.lmax[t] - TM.lmin[t] + 1 <= kMaxLv;
                 for (int ls = 0; ls < kMaxLv; ++ls) {
-                    const int k = t * kMaxLv + ls;
+                    const int k = g * kMaxLv + ls;
                     const int *bb = TM.bb[k];
+                    TM.boff[k] = tt;
                     TM.bw[k] = bb[0] != INT_MAX ? bb[1] - bb[0] + 1 : 0;
                     tt += bb[0] != INT_MAX ? TM.bw[k] * (bb[3] - bb[2] + 1) : 0;
                 }
-                TM.direct[t] = !fits_levels || tt > CAP;
-                if (TM.direct[t])
-                    tt = 0;
+                TM.direct[g] = TM.lmax[g] - TM.lmin[g] + 1 > kMaxLv || tt > CAP;
+                TM.gtotal[g] = TM.direct[g] ? 0 : tt;
+            }
+            int r = 0, acc = 0;
+            TM.rtex[0] = 0;
+            for (int t = 0; t < nt; ++t) {
+                const int tt = TM.gtotal[M.tex_group[t]];
                 if (acc + tt > CAP) { // close the current round
                     TM.rtotal[r] = acc;
                     ++r;
                     TM.rtex[r] = t;
                     acc = 0;
                 }
-                for (int ls = 0; ls < kMaxLv; ++ls) {
-                    const int k = t * kMaxLv + ls;
-                    TM.base[k] = acc;
-                    if (!TM.direct[t] && TM.bb[k][0] != INT_MAX)
-                        acc += TM.bw[k] * (TM.bb[k][3] - TM.bb[k][2] + 1);
-                }
+                TM.tbase[t] = acc;
+                acc += tt;
             }
             TM.rtotal[r] = acc;
             TM.rtex[r + 1] = nt;
@@ -357,19 +358,21 @@ __global__ void __launch_bounds__(kTileQ, 3) k_decode_tiled(MaterialDev M, const
                     bidx[it] = b;
                     blk[it] = make_uint4(0, 0, 0, 0);
                     if (valid) {
-                        int k = t_beg * kMaxLv;
-                        while (TM.bw[k] == 0 || TM.direct[k / kMaxLv] ||
-                               b >= TM.base[k] + TM.bw[k] * (TM.bb[k][3] - TM.bb[k][2] + 1))
+                        int t = t_beg;
+                        while (b >= TM.tbase[t] + TM.gtotal[M.tex_group[t]])
+                            ++t;
+                        const int g = M.tex_group[t];
+                        const int local0 = b - TM.tbase[t];
+                        int k = g * kMaxLv;
+                        while (TM.bw[k] == 0 || local0 >= TM.boff[k] + TM.bw[k] * (TM.bb[k][3] - TM.bb[k][2] + 1))
                             ++k;
-                        const int t = k / kMaxLv;
                         const TexDev &T = M.tex[t];
-                        const int level = TM.lmin[t] + (k - t * kMaxLv);
-                        const int local = b - TM.base[k];
+                        const int level = TM.lmin[g] + (k - g * kMaxLv);
+                        const int local = local0 - TM.boff[k];
                         const int bwk = TM.bw[k];
                         const int ry = local / bwk;
-                        const int rx = TM.bb[k][0] + (local - ry * bwk);
                         const int W = T.res >> level, wb = W >> 2;
-                        int bxa = rx, bya = TM.bb[k][2] + ry;
+                        int bxa = TM.bb[k][0] + (local - ry * bwk), bya = TM.bb[k][2] + ry;
                         if (wrap) {
                             bxa = (ref_block(u0, W) + bxa) & (wb - 1);
                             bya = (ref_block(v0, W) + bya) & (wb - 1);
@@ -413,75 +416,99 @@ __global__ void __launch_bounds__(kTileQ, 3) k_decode_tiled(MaterialDev M, const
                 for (int i = threadIdx.x; i < 2 * total; i += kTileQ) {
                     const int e = i >> 1, half = i & 1;
                     const uint4 rr = sraw[e];
-                    const int b = sidx[e];
+                    const int bi = sidx[e];
                     Bc6hBlock bk;
                     bk.lo = (uint64_t)rr.x | ((uint64_t)rr.y << 32);
                     bk.hi = (uint64_t)rr.z | ((uint64_t)rr.w << 32);
                     Bc6hHeader H;
                     bc6h_header(bk, sgn, H);
                     bc6h_half_texels(bk, H, sgn, half, [&](int t, uint32_t rg, uint32_t bb) {
-                        arena[arena_slot(b, t)] = make_uint2(rg, bb);
+                        arena[arena_slot(bi, t)] = make_uint2(rg, bb);
                     });
                 }
                 __syncthreads();
-            }
-            // ---- 5. filter the round's textures (per lane where a texture did not fit)
-            for (int t = t_beg; t < t_end; ++t) {
-                const TexDev &T = M.tex[t];
-                float f0 = 0.0f, f1 = 0.0f, f2 = 0.0f;
-                if (active) {
-                    if (!TM.direct[t]) {
+                // ---- 5. filter: per group, the footprint geometry once; per texture, 4 arena texels per level
+                for (int g = 0; g < ng; ++g) {
+                    if (TM.direct[g])
+                        continue;
+                    const TexDev &T = M.tex[M.group_first[g]];
+                    int ofs[2][4], tex_i[2][4];
+                    float wgt[2][4];
+                    int nlev = 0;
+                    if (active) {
                         const Lod L = lod_of(T, s);
-                        for (int side = 0; side < L.nlev; ++side) {
-                            const int level = L.l0 + side;
+                        nlev = L.nlev;
+#pragma unroll
+                        for (int side = 0; side < 2; ++side) {
+                            const int level = L.l0 + (side < L.nlev ? side : 0);
                             const float scale = L.nlev == 1 ? 1.0f : (side ? L.lam : 1.0f - L.lam);
                             const int W = T.res >> level;
                             const float x = u * (float)W - 0.5f, y = v * (float)W - 0.5f;
                             const float fx0 = floorf(x), fy0 = floorf(y);
                             const float fx = x - fx0, fy = y - fy0;
                             const int i0 = (int)fx0, j0 = (int)fy0;
-                            const int k = t * kMaxLv + level - TM.lmin[t];
+                            const int k = g * kMaxLv + level - TM.lmin[g];
                             const int rbx = wrap ? ref_block(u0, W) : 0, rby = wrap ? ref_block(v0, W) : 0;
-                            const int bwk = TM.bw[k], basek = TM.base[k];
-                            const int bhk = TM.bb[k][3] - TM.bb[k][2] + 1;
-                            // the box was built from the same integer coordinates, so these are inside
-                            // it; the clamps only guarantee in-bounds shared-memory reads
+                            const int bwk = TM.bw[k], bhk = TM.bb[k][3] - TM.bb[k][2] + 1;
+                            // the box was built from the same integer coordinates, so these are inside it; the
+                            // clamps only guarantee in-bounds shared-memory reads
                             const int bxl = min(max(rel_block(i0, i0, rbx, W, wrap) - TM.bb[k][0], 0), bwk - 1);
                             const int bxh = min(max(rel_block(i0 + 1, i0, rbx, W, wrap) - TM.bb[k][0], 0), bwk - 1);
                             const int byl = min(max(rel_block(j0, j0, rby, W, wrap) - TM.bb[k][2], 0), bhk - 1);
                             const int byh = min(max(rel_block(j0 + 1, j0, rby, W, wrap) - TM.bb[k][2], 0), bhk - 1);
                             const int cl = texel_col(i0, W, wrap), ch = texel_col(i0 + 1, W, wrap);
                             const int rl = texel_col(j0, W, wrap) * 4, rh = texel_col(j0 + 1, W, wrap) * 4;
-                            const int b00 = basek + byl * bwk + bxl, b10 = basek + byl * bwk + bxh;
-                            const int b01 = basek + byh * bwk + bxl, b11 = basek + byh * bwk + bxh;
-                            const uint2 t00 = arena[arena_slot(b00, rl + cl)];
-                            const uint2 t10 = arena[arena_slot(b10, rl + ch)];
-                            const uint2 t01 = arena[arena_slot(b01, rh + cl)];
-                            const uint2 t11 = arena[arena_slot(b11, rh + ch)];
-                            const float w00 = (1.0f - fx) * (1.0f - fy) * scale, w10 = fx * (1.0f - fy) * scale;
-                            const float w01 = (1.0f - fx) * fy * scale, w11 = fx * fy * scale;
-#define BCF_ACC(tx, w)                                                                                             \
-    {                                                                                                              \
-        const float2 rg = __half22float2(*reinterpret_cast<const __half2 *>(&tx.x));                               \
-        f0 = fmaf(w, rg.x, f0);                                                                                    \
-        f1 = fmaf(w, rg.y, f1);                                                                                    \
-        f2 = fmaf(w, __half2float(__ushort_as_half((unsigned short)tx.y)), f2);                                    \
-    }
-                            BCF_ACC(t00, w00) BCF_ACC(t10, w10) BCF_ACC(t01, w01) BCF_ACC(t11, w11)
-#undef BCF_ACC
+                            const int o = TM.boff[k];
+                            ofs[side][0] = o + byl * bwk + bxl;
+                            ofs[side][1] = o + byl * bwk + bxh;
+                            ofs[side][2] = o + byh * bwk + bxl;
+                            ofs[side][3] = o + byh * bwk + bxh;
+                            tex_i[side][0] = rl + cl;
+                            tex_i[side][1] = rl + ch;
+                            tex_i[side][2] = rh + cl;
+                            tex_i[side][3] = rh + ch;
+                            wgt[side][0] = (1.0f - fx) * (1.0f - fy) * scale;
+                            wgt[side][1] = fx * (1.0f - fy) * scale;
+                            wgt[side][2] = (1.0f - fx) * fy * scale;
+                            wgt[side][3] = fx * fy * scale;
                         }
-                    } else {
-                        const float3 f = sample_texture(T, wrap, sgn, u, v, s);
-                        f0 = f.x;
-                        f1 = f.y;
-                        f2 = f.z;
+                    }
+                    for (int t = t_beg; t < t_end; ++t) {
+                        if (M.tex_group[t] != g)
+                            continue;
+                        float f0 = 0.0f, f1 = 0.0f, f2 = 0.0f;
+                        const int tb = TM.tbase[t];
+#pragma unroll
+                        for (int side = 0; side < 2; ++side) {
+                            if (side < nlev) {
+#pragma unroll
+                                for (int c = 0; c < 4; ++c) {
+                                    const uint2 tx = arena[arena_slot(tb + ofs[side][c], tex_i[side][c])];
+                                    const float2 rg = __half22float2(*reinterpret_cast<const __half2 *>(&tx.x));
+                                    f0 = fmaf(wgt[side][c], rg.x, f0);
+                                    f1 = fmaf(wgt[side][c], rg.y, f1);
+                                    f2 = fmaf(wgt[side][c], __half2float(__ushort_as_half((unsigned short)tx.y)), f2);
+                                }
+                            }
+                        }
+                        store_feature<PREC>(myrow, 3 * t, f0, inv0);
+                        store_feature<PREC>(myrow, 3 * t + 1, f1, inv0);
+                        store_feature<PREC>(myrow, 3 * t + 2, f2, inv0);
                     }
                 }
-                store_feature<PREC>(myrow, 3 * t, f0, inv0);
-                store_feature<PREC>(myrow, 3 * t + 1, f1, inv0);
-                store_feature<PREC>(myrow, 3 * t + 2, f2, inv0);
             }
             __syncthreads(); // the arena is refilled by the next round / tile
+        }
+        // ---- 5b. textures of groups that did not fit: per-lane decode
+        for (int t = 0; t < nt; ++t) {
+            if (!TM.direct[M.tex_group[t]])
+                continue;
+            float3 f = make_float3(0.f, 0.f, 0.f);
+            if (active)
+                f = sample_texture(M.tex[t], wrap, sgn, u, v, s);
+            store_feature<PREC>(myrow, 3 * t, f.x, inv0);
+            store_feature<PREC>(myrow, 3 * t + 1, f.y, inv0);
+            store_feature<PREC>(myrow, 3 * t + 2, f.z, inv0);
         }
         {
             int col = 3 * nt;

@@ -43,6 +43,11 @@ struct MaterialDev {
     int32_t lod_input;
     int32_t n_in;                      // 3 T + lod_input
     int32_t n_out;
+    // textures with the same resolution and level count sample the same texel
+    // footprints: they form one geometry group
+    int32_t n_groups;
+    int32_t tex_group[BCF_MAX_TEX];    // group of each texture
+    int32_t group_first[BCF_MAX_TEX];  // a texture of each group (its geometry)
     TexDev tex[BCF_MAX_TEX];
     MlpDev mlp;
 };

@@ -289,20 +289,25 @@ __device__ __forceinline__ void load_a(const unsigned char *A, int stride, int r
     a[3] = lds32(p1 + kc + kh);
 }
 
-// Dense layer on one 16-row tile: D[NP/8][4] = A(16 x KP) * W^T.
-template <int PREC, int KP, int NP>
-__device__ __forceinline__ void mma_layer(const uint32_t (&a)[KP / Op<PREC>::kK][4], const unsigned char *W, int stride,
-                                          int g, int t, float (&d)[NP / 8][4])
+// Dense layer on MT 16-row tiles: D[m][NP/8][4] = A_m(16 x KP) * W^T; each B
+// fragment is loaded once and used for all MT row tiles.
+template <int PREC, int MT, int KP, int NP>
+__device__ __forceinline__ void mma_layer(const uint32_t (&a)[MT][KP / Op<PREC>::kK][4], const unsigned char *W,
+                                          int stride, int g, int t, float (&d)[MT][NP / 8][4])
 {
     constexpr int KK = Op<PREC>::kK, EB = Op<PREC>::kBytes;
 #pragma unroll
     for (int nt = 0; nt < NP / 8; ++nt) {
-        d[nt][0] = d[nt][1] = d[nt][2] = d[nt][3] = 0.0f;
+#pragma unroll
+        for (int m = 0; m < MT; ++m)
+            d[m][nt][0] = d[m][nt][1] = d[m][nt][2] = d[m][nt][3] = 0.0f;
 #pragma unroll
         for (int kt = 0; kt < KP / KK; ++kt) {
             uint32_t b[2];
             load_b<EB, KK>(W, stride, kt * KK, nt * 8, g, t, b);
-            Op<PREC>::mma(d[nt], a[kt], b);
+#pragma unroll
+            for (int m = 0; m < MT; ++m)
+                Op<PREC>::mma(d[m][nt], a[m][kt], b);
         }
     }
 }
@@ -310,50 +315,66 @@ __device__ __forceinline__ void mma_layer(const uint32_t (&a)[KP / Op<PREC>::kK]
 // Hidden epilogue for 16-bit operands: bias + ReLU, rounded straight into the
 // next layer's A fragments (D tile columns 8 nt + 2 t map onto A fragment
 // nt / 2, registers 0/1 for even nt and 2/3 for odd nt).
-template <int PREC, int NP>
-__device__ __forceinline__ void hidden_to_a16(const float (&d)[NP / 8][4], const float *bias, int t,
-                                              uint32_t (&a)[NP / 16][4])
+template <int PREC, int MT, int NP>
+__device__ __forceinline__ void hidden_to_a16(const float (&d)[MT][NP / 8][4], const float *bias, int t,
+                                              uint32_t (&a)[MT][NP / 16][4])
 {
 #pragma unroll
     for (int nt = 0; nt < NP / 8; ++nt) {
         const float b0 = bias[nt * 8 + 2 * t], b1 = bias[nt * 8 + 2 * t + 1];
-        const uint32_t lo = Op<PREC>::pack2(fmaxf(d[nt][0] + b0, 0.f), fmaxf(d[nt][1] + b1, 0.f));
-        const uint32_t hi = Op<PREC>::pack2(fmaxf(d[nt][2] + b0, 0.f), fmaxf(d[nt][3] + b1, 0.f));
-        a[nt >> 1][(nt & 1) * 2 + 0] = lo;
-        a[nt >> 1][(nt & 1) * 2 + 1] = hi;
+#pragma unroll
+        for (int m = 0; m < MT; ++m) {
+            a[m][nt >> 1][(nt & 1) * 2 + 0] =
+                Op<PREC>::pack2(fmaxf(d[m][nt][0] + b0, 0.f), fmaxf(d[m][nt][1] + b1, 0.f));
+            a[m][nt >> 1][(nt & 1) * 2 + 1] =
+                Op<PREC>::pack2(fmaxf(d[m][nt][2] + b0, 0.f), fmaxf(d[m][nt][3] + b1, 0.f));
+        }
     }
 }
 
 // Hidden epilogue for FP8: bias + ReLU after the scale, divided by the next
-// layer's activation scale, rounded to E4M3 into a 16-row byte tile, from
-// which the next layer's (K = 32) A fragments are loaded.
-template <int NP>
-__device__ __forceinline__ void hidden_to_tile8(const float (&d)[NP / 8][4], const float *bias, float oscale,
+// layer's activation scale, rounded to E4M3 into a byte tile (16 MT rows),
+// from which the next layer's (K = 32) A fragments are loaded.
+template <int MT, int NP>
+__device__ __forceinline__ void hidden_to_tile8(const float (&d)[MT][NP / 8][4], const float *bias, float oscale,
                                                 float next_inv, int g, int t, unsigned char *tile, int stride)
 {
 #pragma unroll
     for (int nt = 0; nt < NP / 8; ++nt) {
         const int c = nt * 8 + 2 * t;
         const float b0 = bias[c], b1 = bias[c + 1];
-        const uint32_t lo = Op<BCF_FP8_E4M3>::pack2(fmaxf(d[nt][0] * oscale + b0, 0.f) * next_inv,
-                                                    fmaxf(d[nt][1] * oscale + b1, 0.f) * next_inv);
-        const uint32_t hi = Op<BCF_FP8_E4M3>::pack2(fmaxf(d[nt][2] * oscale + b0, 0.f) * next_inv,
-                                                    fmaxf(d[nt][3] * oscale + b1, 0.f) * next_inv);
-        *reinterpret_cast<uint16_t *>(tile + g * stride + c) = (uint16_t)lo;
-        *reinterpret_cast<uint16_t *>(tile + (g + 8) * stride + c) = (uint16_t)hi;
+#pragma unroll
+        for (int m = 0; m < MT; ++m) {
+            const uint32_t lo = Op<BCF_FP8_E4M3>::pack2(fmaxf(d[m][nt][0] * oscale + b0, 0.f) * next_inv,
+                                                        fmaxf(d[m][nt][1] * oscale + b1, 0.f) * next_inv);
+            const uint32_t hi = Op<BCF_FP8_E4M3>::pack2(fmaxf(d[m][nt][2] * oscale + b0, 0.f) * next_inv,
+                                                        fmaxf(d[m][nt][3] * oscale + b1, 0.f) * next_inv);
+            *reinterpret_cast<uint16_t *>(tile + (m * 16 + g) * stride + c) = (uint16_t)lo;
+            *reinterpret_cast<uint16_t *>(tile + (m * 16 + g + 8) * stride + c) = (uint16_t)hi;
+        }
     }
 }
 
-// K0 -> N1 -> N2 -> NO (all padded) MLP for the warp's 32 rows, one 16-row
-// tile at a time.  in: the quantised input tile [32][K0] (row stride
-// in_stride bytes).  The FP32 outputs go to ost[32][C].  tmp8: FP8 scratch
-// tile (16 rows, stride tmp_stride) for the FP8 layer chaining.
+// Rows processed together by warp_mlp3.  One 16-row tile per pass: two
+// tiles would let each weight fragment feed two MMAs, but under the decode
+// kernel's 80-register budget the extra accumulators spill.
+template <int N1, int N2>
+struct MlpRows {
+    static constexpr int kMT = 1;
+};
+
+// K0 -> N1 -> N2 -> NO (all padded) MLP for the warp's 32 rows.  in: the
+// quantised input tile [32][K0] (row stride in_stride bytes).  The FP32
+// outputs go to ost[32][C]; all A fragments of a pass are loaded before its
+// outputs are written.  tmp8: FP8 scratch tile (16 kMT rows, stride
+// tmp_stride) for the FP8 layer chaining.
 template <int PREC, int K0, int N1, int N2, int NO>
 __device__ __forceinline__ void warp_mlp3(const MlpDev &P, const unsigned char *sw, const float *sb,
                                           const unsigned char *in, int in_stride, unsigned char *tmp8,
                                           int tmp_stride, float *ost, int C)
 {
     constexpr int KK = Op<PREC>::kK, EB = Op<PREC>::kBytes;
+    constexpr int MT = MlpRows<N1, N2>::kMT;
     const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
     const int s0 = tile_stride_bytes<PREC>(K0), s1 = tile_stride_bytes<PREC>(N1), s2 = tile_stride_bytes<PREC>(N2);
     const unsigned char *W0 = sw;
@@ -369,50 +390,59 @@ __device__ __forceinline__ void warp_mlp3(const MlpDev &P, const unsigned char *
         in2 = P.inv_act_scale[2];
     }
 #pragma unroll 1
-    for (int m = 0; m < 2; ++m) {
-        uint32_t a0[K0 / KK][4];
+    for (int m0 = 0; m0 < 2; m0 += MT) {
+        uint32_t a0[MT][K0 / KK][4];
 #pragma unroll
-        for (int kt = 0; kt < K0 / KK; ++kt)
-            load_a<EB, KK>(in, in_stride, m * 16, kt * KK, g, t, a0[kt]);
-        float d1[N1 / 8][4];
-        mma_layer<PREC, K0, N1>(a0, W0, s0, g, t, d1);
-        uint32_t a1[N1 / KK][4];
+        for (int m = 0; m < MT; ++m)
+#pragma unroll
+            for (int kt = 0; kt < K0 / KK; ++kt)
+                load_a<EB, KK>(in, in_stride, (m0 + m) * 16, kt * KK, g, t, a0[m][kt]);
+        float d1[MT][N1 / 8][4];
+        mma_layer<PREC, MT, K0, N1>(a0, W0, s0, g, t, d1);
+        uint32_t a1[MT][N1 / KK][4];
         if constexpr (PREC == BCF_FP8_E4M3) {
-            hidden_to_tile8<N1>(d1, b0, sc0, in1, g, t, tmp8, tmp_stride);
+            hidden_to_tile8<MT, N1>(d1, b0, sc0, in1, g, t, tmp8, tmp_stride);
             __syncwarp();
 #pragma unroll
-            for (int kt = 0; kt < N1 / KK; ++kt)
-                load_a<EB, KK>(tmp8, tmp_stride, 0, kt * KK, g, t, a1[kt]);
+            for (int m = 0; m < MT; ++m)
+#pragma unroll
+                for (int kt = 0; kt < N1 / KK; ++kt)
+                    load_a<EB, KK>(tmp8, tmp_stride, m * 16, kt * KK, g, t, a1[m][kt]);
             __syncwarp();
         } else {
-            hidden_to_a16<PREC, N1>(d1, b0, t, a1);
+            hidden_to_a16<PREC, MT, N1>(d1, b0, t, a1);
         }
-        float d2[N2 / 8][4];
-        mma_layer<PREC, N1, N2>(a1, W1, s1, g, t, d2);
-        uint32_t a2[N2 / KK][4];
+        float d2[MT][N2 / 8][4];
+        mma_layer<PREC, MT, N1, N2>(a1, W1, s1, g, t, d2);
+        uint32_t a2[MT][N2 / KK][4];
         if constexpr (PREC == BCF_FP8_E4M3) {
-            hidden_to_tile8<N2>(d2, b1, sc1, in2, g, t, tmp8, tmp_stride);
+            hidden_to_tile8<MT, N2>(d2, b1, sc1, in2, g, t, tmp8, tmp_stride);
             __syncwarp();
 #pragma unroll
-            for (int kt = 0; kt < N2 / KK; ++kt)
-                load_a<EB, KK>(tmp8, tmp_stride, 0, kt * KK, g, t, a2[kt]);
+            for (int m = 0; m < MT; ++m)
+#pragma unroll
+                for (int kt = 0; kt < N2 / KK; ++kt)
+                    load_a<EB, KK>(tmp8, tmp_stride, m * 16, kt * KK, g, t, a2[m][kt]);
             __syncwarp();
         } else {
-            hidden_to_a16<PREC, N2>(d2, b1, t, a2);
+            hidden_to_a16<PREC, MT, N2>(d2, b1, t, a2);
         }
-        float d3[NO / 8][4];
-        mma_layer<PREC, N2, NO>(a2, W2, s2, g, t, d3);
+        float d3[MT][NO / 8][4];
+        mma_layer<PREC, MT, N2, NO>(a2, W2, s2, g, t, d3);
 #pragma unroll
         for (int nt = 0; nt < NO / 8; ++nt) {
             const int c = nt * 8 + 2 * t;
-            const int r0 = m * 16 + g, r1 = r0 + 8;
-            if (c < C) {
-                ost[r0 * C + c] = d3[nt][0] * sc2 + b2[c];
-                ost[r1 * C + c] = d3[nt][2] * sc2 + b2[c];
-            }
-            if (c + 1 < C) {
-                ost[r0 * C + c + 1] = d3[nt][1] * sc2 + b2[c + 1];
-                ost[r1 * C + c + 1] = d3[nt][3] * sc2 + b2[c + 1];
+#pragma unroll
+            for (int m = 0; m < MT; ++m) {
+                const int r0 = (m0 + m) * 16 + g, r1 = r0 + 8;
+                if (c < C) {
+                    ost[r0 * C + c] = d3[m][nt][0] * sc2 + b2[c];
+                    ost[r1 * C + c] = d3[m][nt][2] * sc2 + b2[c];
+                }
+                if (c + 1 < C) {
+                    ost[r0 * C + c + 1] = d3[m][nt][1] * sc2 + b2[c + 1];
+                    ost[r1 * C + c + 1] = d3[m][nt][3] * sc2 + b2[c + 1];
+                }
             }
         }
     }
