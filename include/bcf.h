@@ -167,6 +167,120 @@ bcf_status bcf_sample_features(bcf_material mat, const float *d_u, const float *
 bcf_status bcf_decode_material(bcf_material mat, const float *d_u, const float *d_v, const float *d_s, int64_t n,
                                void *d_out, bcf_precision out_precision, bcf_stream stream);
 
+/* ----------------------------------------------------------------- training */
+
+/*
+ * Training of a block-compressed neural material (Sec. 4.1-4.3, Sec. 5.1,
+ * Eq. 4-9): per-block parameters theta (Eq. 6) and the MLP eta are fitted to
+ * a filtered reference F(M) with the MSE of Eq. 5 and Adam (Sec. 6.1).
+ *
+ * Block parameter layout (one 128-byte record per block, mips concatenated
+ * from level 0, blocks row-major per level), 32 floats:
+ *   [0..2]  e1 RGB, [3..5] e2 RGB   endpoints of region 0, in 6-bit units [0, 63]
+ *   [6..7]  unused (kept 0)
+ *   [8..10] e3 RGB, [11..13] e4 RGB endpoints of region 1
+ *   [14..15] unused (kept 0)
+ *   [16..31] x_1..x_16             per-texel positions on the segment, [0, 1]
+ * plus one partition id k in [0, 31] per block (uint8, fixed during training).
+ *
+ * Forward (the emulated BC6 decompression of Sec. 4.2 at the exported
+ * precision of Sec. 5.2, i.e. BC6H mode 10): endpoints and x are rounded to
+ * the 6-bit / 3-bit lattice (straight-through), unquantised, interpolated
+ * with the 3-bit weights and scaled by 31/64 exactly as the BC6H decoder
+ * does, and the 15-bit result is read as a half float (Eq. 9), so the
+ * forward equals the decode of the exported block bit for bit.  Backward:
+ * the exact derivatives of the relaxed pipeline (Eq. 7 slope 1024 per
+ * endpoint unit, Eq. 8 linear in w/64 ~ x, 31/64, slope of Eq. 9) at the
+ * rounded forward values; zero outside [0, 63] / [0, 1].
+ * The MLP evaluates with weights and layer inputs rounded to bfloat16 and
+ * FP32 accumulation; its backward is FP32 with respect to those rounded
+ * values.
+ *
+ * Reference material F(M) (Sec. 5.1): 9 channels, FP16, a mip chain from
+ * target_res down to 4 x 4 (level l is target_res >> l), channels 0..7
+ * interleaved [texels][8] and channel 8 in its own array [texels]; sampled
+ * with Catmull-Rom bicubic filtering on levels floor(s) and floor(s) + 1,
+ * lerped, repeat addressing.
+ */
+typedef struct bcf_trainer_s *bcf_trainer;
+
+typedef struct {
+    int32_t num_textures;                   /* T */
+    int32_t res[BCF_MAX_TEX];
+    int32_t levels[BCF_MAX_TEX];
+    int32_t res_ref;                        /* query LOD s is in units of res_ref (the reference's resolution) */
+    int32_t lod_input;                      /* 1: max(s, 0) is the last MLP input */
+    float *d_params[BCF_MAX_TEX];           /* [blocks][32] block parameters, updated in place by the optimiser */
+    const uint8_t *d_partition[BCF_MAX_TEX]; /* [blocks] partition ids */
+    float *d_grad[BCF_MAX_TEX];             /* [blocks][32] gradient accumulators (zeroed by the optimiser) */
+    float *d_adam_m[BCF_MAX_TEX];           /* [blocks][32] Adam first moments */
+    float *d_adam_v[BCF_MAX_TEX];           /* [blocks][32] Adam second moments */
+    int32_t n_layers;                       /* 1 <= n <= BCF_MAX_LAYERS, widths <= 64 */
+    int32_t dims[BCF_MAX_LAYERS + 1];       /* dims[0] = 3 T + lod_input */
+    float *d_W, *d_b;                       /* FP32 master weights (layers concatenated, W_l [out][in]) */
+    float *d_W_grad, *d_b_grad;             /* their gradient accumulators */
+    float *d_W_m, *d_W_v, *d_b_m, *d_b_v;   /* Adam moments */
+    int32_t target_res, target_levels;
+    const uint16_t *d_target8;              /* FP16 channels 0..7 of the reference, [texels][8] */
+    const uint16_t *d_target1;              /* FP16 channel 8, [texels] */
+    float lr_features, lr_mlp;              /* initial learning rates (Sec. 6.1: 1e-2 and 1e-3) */
+    float gamma;                            /* exponential decay per step (Sec. 6.1: 0.9999) */
+    float beta1, beta2, eps;                /* Adam constants */
+    float s_max;                            /* batch draws: s ~ U[0, s_max) in res_ref units */
+} bcf_trainer_desc;
+
+/*
+ * bcf_trainer_create -- validate a trainer (sizes, alignment: every array
+ * 16-byte aligned) and copy its metadata to the device (a small allocation
+ * freed by bcf_trainer_destroy).  All parameter, gradient, moment and
+ * target arrays stay caller-owned.  Errors: BCF_ERR_INVALID_ARG,
+ * BCF_ERR_UNSUPPORTED (a layer wider than 64, a target not 9 channels),
+ * BCF_ERR_OOM / BCF_ERR_CUDA.
+ */
+bcf_status bcf_trainer_create(const bcf_trainer_desc *desc, bcf_trainer *out);
+bcf_status bcf_trainer_destroy(bcf_trainer tr);
+
+/*
+ * bcf_train_step -- one optimisation step (Eq. 5 on one batch, then Adam):
+ *   queries: (d_u, d_v, d_s) of length `batch` if given, otherwise drawn with
+ *   Philox4x32-10: counter (q, step low, step high, q high), key (seed low,
+ *   seed high); u, v, s = top 24 bits of output words 0, 1, 2 times 2^-24
+ *   (s also times s_max);
+ *   loss: mean over batch and channels of (G - F(M))^2, written to
+ *   d_loss_out (one float, device; overwritten);
+ *   gradients accumulated into the trainer's grad arrays, then Adam with
+ *   lr_t = lr0 gamma^step, bias correction with step + 1, endpoints clamped
+ *   to [0, 63] and x to [0, 1]; gradients are zeroed afterwards.
+ * batch == 0 only runs the optimiser on zero gradients.  Errors:
+ * BCF_ERR_INVALID_ARG for batch < 0, step < 0 or a null loss pointer.
+ */
+bcf_status bcf_train_step(bcf_trainer tr, int64_t batch, uint64_t seed, int64_t step, const float *d_u,
+                          const float *d_v, const float *d_s, float *d_loss_out, bcf_stream stream);
+
+/*
+ * bcf_train_forward -- G(u, v, s) of the current parameters for n queries
+ * (the emulated forward above), d_out [n][C] FP32.
+ * bcf_train_backward -- given dL/dG [n][C] FP32 for the same queries,
+ * accumulate dL/dtheta and dL/deta into the trainer's gradient arrays
+ * (nothing is zeroed and no optimiser step is taken).
+ * Together they are the forward / backward of a torch.autograd.Function.
+ */
+bcf_status bcf_train_forward(bcf_trainer tr, const float *d_u, const float *d_v, const float *d_s, int64_t n,
+                             float *d_out, bcf_stream stream);
+bcf_status bcf_train_backward(bcf_trainer tr, const float *d_u, const float *d_v, const float *d_s, int64_t n,
+                              const float *d_grad_out, bcf_stream stream);
+
+/*
+ * bcf_train_export -- write the trained features as BC6H mode-10 blocks
+ * (Sec. 5.2: endpoints rounded to 6 bits, indices to 3 bits; where a
+ * region's anchor texel would need the top index bit, the region's
+ * endpoints are swapped and its indices mirrored, which keeps every texel
+ * value) and the MLP weights as FP16 (biases stay FP32 in d_b).
+ * d_blocks_out[t]: [blocks][16] bytes per texture, 16-byte aligned;
+ * d_weights_fp16: [sum of W_l sizes] (may be NULL).
+ */
+bcf_status bcf_train_export(bcf_trainer tr, void *const *d_blocks_out, uint16_t *d_weights_fp16, bcf_stream stream);
+
 /*
  * bcf_set_decode_variant -- choose the kernel bcf_decode_material uses for a
  * tensor-core (FP16 / BF16 / FP8) material.  0 (default): tile-cooperative

@@ -130,6 +130,12 @@ def lib():
         L.oracle_train_loss_grad.restype = c_double
         L.oracle_train_loss_grad.argtypes = [POINTER(_TrainFeatures), POINTER(_TrainMlp), POINTER(_Target), c_int64,
                                              c_void_p, c_void_p, c_void_p, c_int, c_void_p]
+        L.oracle_train_outputs.restype = None
+        L.oracle_train_outputs.argtypes = [POINTER(_TrainFeatures), POINTER(_TrainMlp), c_int64, c_void_p, c_void_p,
+                                           c_void_p, c_void_p]
+        L.oracle_train_backward_given.restype = None
+        L.oracle_train_backward_given.argtypes = [POINTER(_TrainFeatures), POINTER(_TrainMlp), c_int64, c_void_p,
+                                                  c_void_p, c_void_p, c_void_p, c_void_p]
         L.oracle_texture_blocks.restype = c_int64
         L.oracle_texture_blocks.argtypes = [c_int, c_int]
         L.oracle_train_export_block.restype = None
@@ -453,3 +459,31 @@ def train_export_block(p: np.ndarray, k: int) -> np.ndarray:
     out = np.zeros(16, np.uint8)
     lib().oracle_train_export_block(_ptr(p), int(k), _ptr(out))
     return out
+
+
+def train_outputs(F: TrainFeatures, P: TrainMlp, u, v, s) -> np.ndarray:
+    u = np.ascontiguousarray(u, np.float32)
+    v = np.ascontiguousarray(v, np.float32)
+    s = np.ascontiguousarray(s, np.float32)
+    out = np.zeros((u.size, P.dims[-1]), np.float64)
+    lib().oracle_train_outputs(ctypes.byref(F.c), ctypes.byref(P.c), u.size, _ptr(u), _ptr(v), _ptr(s), _ptr(out))
+    return out
+
+
+def train_backward_given(F: TrainFeatures, P: TrainMlp, u, v, s, grad_out):
+    """Gradients (feature grads per texture [blocks, 28], W grad, b grad) for a given dL/dG [n][C]."""
+    u = np.ascontiguousarray(u, np.float32)
+    v = np.ascontiguousarray(v, np.float32)
+    s = np.ascontiguousarray(s, np.float32)
+    go = np.ascontiguousarray(grad_out, np.float64)
+    gf = [np.zeros_like(p) for p in F._p]
+    gW = np.zeros(P._W.size, np.float64)
+    gb = np.zeros(P._b.size, np.float64)
+    G = _TrainGrads()
+    for t, g in enumerate(gf):
+        G.feat_grad[t] = g.ctypes.data
+    G.W_grad = gW.ctypes.data
+    G.b_grad = gb.ctypes.data
+    lib().oracle_train_backward_given(ctypes.byref(F.c), ctypes.byref(P.c), u.size, _ptr(u), _ptr(v), _ptr(s),
+                                      _ptr(go), ctypes.byref(G))
+    return [g.reshape(-1, 28) for g in gf], gW, gb

@@ -1126,8 +1126,22 @@ static double rnd_t(const oracle_train_mlp *P, double x) { return P->bf16 ? orac
 /* Forward and backward of one query; returns the query's squared error
  * summed over channels.  Gradients of the mean loss (gscale = 2 / (B C))
  * are accumulated into G when G != NULL. */
+static double train_query_ext(const oracle_train_features *F, const oracle_train_mlp *P, const oracle_target *Tg, float u,
+                              float v, float s, int relaxed, double gscale, oracle_train_grads *G, const double *dy_ext,
+                              double *y_out);
+
 static double train_query(const oracle_train_features *F, const oracle_train_mlp *P, const oracle_target *Tg, float u, float v,
                           float s, int relaxed, double gscale, oracle_train_grads *G)
+{
+    return train_query_ext(F, P, Tg, u, v, s, relaxed, gscale, G, NULL, NULL);
+}
+
+/* One query: forward; then either the MSE gradient against the reference
+ * (dy_ext == NULL) or the given output gradient dy_ext; y_out receives the
+ * MLP outputs when non-NULL. */
+static double train_query_ext(const oracle_train_features *F, const oracle_train_mlp *P, const oracle_target *Tg, float u,
+                              float v, float s, int relaxed, double gscale, oracle_train_grads *G, const double *dy_ext,
+                              double *y_out)
 {
     tap_list L;
     train_taps(F, u, v, s, &L);
@@ -1174,15 +1188,23 @@ static double train_query(const oracle_train_features *F, const oracle_train_mlp
         woff += (int64_t)ni * no;
         boff += no;
     }
-    double tgt[9];
-    oracle_target_sample(Tg, u, v, s, tgt);
     int nout = P->dims[P->n_layers];
+    if (y_out)
+        for (int c = 0; c < nout; ++c)
+            y_out[c] = act[P->n_layers][c];
     double err = 0.0;
     double dy[64];
-    for (int c = 0; c < nout; ++c) {
-        double d = act[P->n_layers][c] - tgt[c];
-        err += d * d;
-        dy[c] = gscale * d;
+    if (dy_ext) {
+        for (int c = 0; c < nout; ++c)
+            dy[c] = dy_ext[c];
+    } else if (Tg) {
+        double tgt[9];
+        oracle_target_sample(Tg, u, v, s, tgt);
+        for (int c = 0; c < nout; ++c) {
+            double d = act[P->n_layers][c] - tgt[c];
+            err += d * d;
+            dy[c] = gscale * d;
+        }
     }
     if (!G)
         return err;
@@ -1296,4 +1318,23 @@ void oracle_train_export_block(const double *p, int k, uint8_t blk[16])
         for (int c = 0; c < 3; ++c)
             raw[e * 3 + c] = q[e][c];
     oracle_bc6h_encode_fields(10, raw, k, idx, blk);
+}
+
+/* MLP outputs of the block-parameterised material for explicit queries
+ * (out[n][C]), and the gradients for a given output gradient grad_out[n][C]
+ * accumulated into G (the forward / backward pair of an autograd function). */
+void oracle_train_outputs(const oracle_train_features *F, const oracle_train_mlp *P, int64_t n, const float *u, const float *v,
+                          const float *s, double *out)
+{
+    int nout = P->dims[P->n_layers];
+    for (int64_t q = 0; q < n; ++q)
+        train_query_ext(F, P, NULL, u[q], v[q], s[q], 0, 0.0, NULL, NULL, out + q * nout);
+}
+
+void oracle_train_backward_given(const oracle_train_features *F, const oracle_train_mlp *P, int64_t n, const float *u,
+                                 const float *v, const float *s, const double *grad_out, oracle_train_grads *G)
+{
+    int nout = P->dims[P->n_layers];
+    for (int64_t q = 0; q < n; ++q)
+        train_query_ext(F, P, NULL, u[q], v[q], s[q], 0, 0.0, G, grad_out + q * nout, NULL);
 }

@@ -40,6 +40,18 @@ class _MaterialDesc(ctypes.Structure):
                 ("act_scale", c_float * MAX_LAYERS), ("w_scale", c_float * MAX_LAYERS)]
 
 
+class _TrainerDesc(ctypes.Structure):
+    _fields_ = [("num_textures", c_int32), ("res", c_int32 * MAX_TEX), ("levels", c_int32 * MAX_TEX),
+                ("res_ref", c_int32), ("lod_input", c_int32), ("d_params", c_void_p * MAX_TEX),
+                ("d_partition", c_void_p * MAX_TEX), ("d_grad", c_void_p * MAX_TEX), ("d_adam_m", c_void_p * MAX_TEX),
+                ("d_adam_v", c_void_p * MAX_TEX), ("n_layers", c_int32), ("dims", c_int32 * (MAX_LAYERS + 1)),
+                ("d_W", c_void_p), ("d_b", c_void_p), ("d_W_grad", c_void_p), ("d_b_grad", c_void_p),
+                ("d_W_m", c_void_p), ("d_W_v", c_void_p), ("d_b_m", c_void_p), ("d_b_v", c_void_p),
+                ("target_res", c_int32), ("target_levels", c_int32), ("d_target8", c_void_p), ("d_target1", c_void_p),
+                ("lr_features", c_float), ("lr_mlp", c_float), ("gamma", c_float), ("beta1", c_float),
+                ("beta2", c_float), ("eps", c_float), ("s_max", c_float)]
+
+
 _lib = None
 
 
@@ -69,6 +81,19 @@ def lib() -> ctypes.CDLL:
         L.bcf_set_decode_variant.argtypes = [c_void_p, c_int32]
         L.bcf_decode_material.restype = c_int
         L.bcf_decode_material.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_int, c_void_p]
+        L.bcf_trainer_create.restype = c_int
+        L.bcf_trainer_create.argtypes = [POINTER(_TrainerDesc), POINTER(c_void_p)]
+        L.bcf_trainer_destroy.restype = c_int
+        L.bcf_trainer_destroy.argtypes = [c_void_p]
+        L.bcf_train_step.restype = c_int
+        L.bcf_train_step.argtypes = [c_void_p, c_int64, ctypes.c_uint64, c_int64, c_void_p, c_void_p, c_void_p,
+                                     c_void_p, c_void_p]
+        L.bcf_train_forward.restype = c_int
+        L.bcf_train_forward.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p]
+        L.bcf_train_backward.restype = c_int
+        L.bcf_train_backward.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p]
+        L.bcf_train_export.restype = c_int
+        L.bcf_train_export.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
         _lib = L
     return _lib
 
@@ -183,3 +208,110 @@ class Material:
         _check(lib().bcf_decode_material(self.handle, _ptr(u), _ptr(v), _ptr(s), n, _ptr(out), prec, _stream()),
                "bcf_decode_material")
         return out
+
+
+# --------------------------------------------------------------------------- training
+
+class Trainer:
+    """A bcf_trainer: block parameters [blocks, 32] per texture (updated in place), partition ids, the FP32 MLP,
+    the FP16 reference mip chain and the Adam state.  Gradient and moment buffers are allocated here (torch)."""
+
+    def __init__(self, params: list[torch.Tensor], partition: list[torch.Tensor], res: list[int], levels: list[int],
+                 res_ref: int, dims: list[int], W: torch.Tensor, b: torch.Tensor, target8: torch.Tensor,
+                 target1: torch.Tensor, target_res: int, target_levels: int, lr_features: float = 1e-2,
+                 lr_mlp: float = 1e-3, gamma: float = 0.9999, beta1: float = 0.9, beta2: float = 0.999,
+                 eps: float = 1e-8, s_max: float | None = None, lod_input: bool = True):
+        z = torch.zeros_like
+        self.params, self.partition = list(params), list(partition)
+        self.grads = [z(p) for p in params]
+        self.m = [z(p) for p in params]
+        self.v = [z(p) for p in params]
+        self.W, self.b = W, b
+        self.W_grad, self.b_grad = z(W), z(b)
+        self.W_m, self.W_v, self.b_m, self.b_v = z(W), z(W), z(b), z(b)
+        self.target = (target8, target1)
+        d = _TrainerDesc()
+        d.num_textures = len(params)
+        for t in range(len(params)):
+            d.res[t], d.levels[t] = int(res[t]), int(levels[t])
+            d.d_params[t] = _ptr(params[t])
+            d.d_partition[t] = _ptr(partition[t])
+            d.d_grad[t] = _ptr(self.grads[t])
+            d.d_adam_m[t] = _ptr(self.m[t])
+            d.d_adam_v[t] = _ptr(self.v[t])
+        d.res_ref = int(res_ref)
+        d.lod_input = int(lod_input)
+        d.n_layers = len(dims) - 1
+        for i, x in enumerate(dims):
+            d.dims[i] = int(x)
+        for name, t in (("d_W", W), ("d_b", b), ("d_W_grad", self.W_grad), ("d_b_grad", self.b_grad),
+                        ("d_W_m", self.W_m), ("d_W_v", self.W_v), ("d_b_m", self.b_m), ("d_b_v", self.b_v)):
+            setattr(d, name, _ptr(t))
+        d.target_res, d.target_levels = int(target_res), int(target_levels)
+        d.d_target8, d.d_target1 = _ptr(target8), _ptr(target1)
+        d.lr_features, d.lr_mlp, d.gamma = lr_features, lr_mlp, gamma
+        d.beta1, d.beta2, d.eps = beta1, beta2, eps
+        d.s_max = float(target_levels - 1 if s_max is None else s_max)
+        h = c_void_p()
+        _check(lib().bcf_trainer_create(ctypes.byref(d), ctypes.byref(h)), "bcf_trainer_create")
+        self.handle = h
+        self.dims = list(dims)
+        self.loss = torch.zeros(1, dtype=torch.float32, device=W.device)
+
+    def close(self):
+        if self.handle:
+            _check(lib().bcf_trainer_destroy(self.handle), "bcf_trainer_destroy")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def step(self, batch: int, seed: int, step: int, u=None, v=None, s=None) -> torch.Tensor:
+        """bcf_train_step; returns the (device) loss of the batch."""
+        _check(lib().bcf_train_step(self.handle, int(batch), int(seed), int(step), _ptr(u), _ptr(v), _ptr(s),
+                                    _ptr(self.loss), _stream()), "bcf_train_step")
+        return self.loss
+
+    def forward(self, u, v, s) -> torch.Tensor:
+        out = torch.empty((u.numel(), self.dims[-1]), dtype=torch.float32, device=u.device)
+        _check(lib().bcf_train_forward(self.handle, _ptr(u), _ptr(v), _ptr(s), u.numel(), _ptr(out), _stream()),
+               "bcf_train_forward")
+        return out
+
+    def backward(self, u, v, s, grad_out: torch.Tensor) -> None:
+        _check(lib().bcf_train_backward(self.handle, _ptr(u), _ptr(v), _ptr(s), u.numel(),
+                                        _ptr(grad_out.contiguous()), _stream()), "bcf_train_backward")
+
+    def zero_grad(self) -> None:
+        for g in self.grads + [self.W_grad, self.b_grad]:
+            g.zero_()
+
+    def export(self):
+        """bcf_train_export -> (BC6H mode-10 blocks per texture as uint8 [blocks*16], FP16 weights as int16)."""
+        blocks = [torch.empty(p.shape[0] * 16, dtype=torch.uint8, device=p.device) for p in self.params]
+        arr = (c_void_p * MAX_TEX)(*[b.data_ptr() for b in blocks])
+        w16 = torch.empty(self.W.numel(), dtype=torch.int16, device=self.W.device)
+        _check(lib().bcf_train_export(self.handle, arr, _ptr(w16), _stream()), "bcf_train_export")
+        return blocks, w16
+
+
+class BCfTrainFn(torch.autograd.Function):
+    """G(u, v, s) of a trainer's block-compressed material as a differentiable function of its block parameters
+    and MLP weights: forward = bcf_train_forward, backward = bcf_train_backward (hand-written kernels)."""
+
+    @staticmethod
+    def forward(ctx, trainer: Trainer, u, v, s, W, b, *params):
+        ctx.trainer = trainer
+        ctx.save_for_backward(u, v, s)
+        return trainer.forward(u, v, s)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        tr = ctx.trainer
+        u, v, s = ctx.saved_tensors
+        tr.zero_grad()
+        tr.backward(u, v, s, grad_out.float())
+        return (None, None, None, None, tr.W_grad.clone(), tr.b_grad.clone(), *[g.clone() for g in tr.grads])

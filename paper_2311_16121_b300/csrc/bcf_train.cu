@@ -1,0 +1,650 @@
+// bcf_train.cu -- training of a block-compressed neural material through the
+// emulated BC6 decompression (Sec. 4.1-4.3, Eq. 5-9) and its optimiser.
+//
+// k_train: one persistent kernel for forward / backward / full step.  Per
+// query (one thread): Philox batch draw or given (u, v, s); trilinear taps
+// (Eq. 10, Eq. 11 bias) over the block parameters with the straight-through
+// mode-10 emulation; MLP forward with BF16-rounded weights and inputs (FP32
+// accumulation); Catmull-Rom reference F(M); MSE; FP32 backward through the
+// MLP; tap gradients scattered with vector atomics.  MLP weight gradients are
+// reduced per CTA: the tile's layer inputs and output gradients are staged in
+// shared memory and contracted over the tile's queries, accumulated in
+// shared memory across the CTA's tiles, and added to the global gradients
+// once at the end.
+// k_adam: Adam with exponentially decayed learning rate, box projection of
+// the block parameters, and zeroing of the gradients.
+// k_export: trained blocks -> BC6H mode-10 bitstreams, weights -> FP16.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <math.h>
+#include <string.h>
+
+#include "bc6h_unpack.cuh"
+#include "bcf_kernels.h"
+#include "bcf_train.h"
+
+namespace bcf {
+
+// ------------------------------------------------------------ Philox4x32-10
+
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
+        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+// --------------------------------------------------- emulated BC6 mode 10
+
+// One texel of the block-based features: value (half reinterpretation of the
+// exact integer decode of the rounded parameters, Eq. 9) and the partials of
+// the relaxed pipeline at that point.
+struct SteTexel {
+    float v[3];
+    float dea[3], deb[3], dx[3];
+    int region;
+    int ina[3], inb[3], inx;
+};
+
+__device__ __forceinline__ int unq6(float e)
+{
+    const int q = (int)rintf(fminf(fmaxf(e, 0.0f), 63.0f));
+    return q == 0 ? 0 : (q == 63 ? 0xFFFF : q * 1024 + 512);
+}
+
+__device__ __forceinline__ void ste_texel(const float *p, int k, int t, SteTexel &o)
+{
+    const int r = (int)((partition_mask(k) >> t) & 1);
+    o.region = r;
+    const float4 a4 = *reinterpret_cast<const float4 *>(p + 8 * r);
+    const float2 b2 = *reinterpret_cast<const float2 *>(p + 8 * r + 4);
+    const float ea[3] = {a4.x, a4.y, a4.z}, eb[3] = {a4.w, b2.x, b2.y};
+    const float x = p[16 + t];
+    o.inx = x >= 0.0f && x <= 1.0f;
+    const int w = weight3((int)rintf(7.0f * fminf(fmaxf(x, 0.0f), 1.0f)));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        o.ina[c] = ea[c] >= 0.0f && ea[c] <= 63.0f;
+        o.inb[c] = eb[c] >= 0.0f && eb[c] <= 63.0f;
+        const int ua = unq6(ea[c]), ub = unq6(eb[c]);
+        const int yi = (64 * ua + 32 + (ub - ua) * w) >> 6;
+        const int y = (yi * 31) >> 6;
+        o.v[c] = __half2float(__ushort_as_half((unsigned short)y));
+        // slope of Eq. 9: 2^(h - 14) / 1024 with h = max(floor((y - 1) / 1024) - 1, 0); times 31/64
+        const int h = max(((y - 1) >> 10) - 1, 0);
+        const float dy = ldexpf(31.0f, h - 30);
+        o.dea[c] = dy * (float)((64 - w) * 16);
+        o.deb[c] = dy * (float)(w * 16);
+        o.dx[c] = dy * (float)(ub - ua);
+    }
+}
+
+__device__ __forceinline__ void red_add_v4(float *p, float a, float b, float c, float d)
+{
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
+__device__ __forceinline__ void red_add_v2(float *p, float a, float b)
+{
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
+}
+
+// Trilinear taps of texture T at (u, v, s): per side (level floor(s_t) and
+// the next, weights 1 - lambda and lambda) the 2 x 2 bilinear footprint.
+struct Tap {
+    int64_t block;
+    int texel;
+    float weight;
+};
+
+template <class F>
+__device__ __forceinline__ void for_each_tap(const TrainTexDev &T, float u, float v, float s, F f)
+{
+    float st = (isnan(s) ? 0.0f : s) + (float)T.lod_bias;
+    st = fminf(fmaxf(st, 0.0f), (float)(T.levels - 1));
+    const float fl = floorf(st);
+    const int l0 = (int)fl;
+    const int l1 = min(l0 + 1, T.levels - 1);
+    const float lam = st - fl;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const int level = side ? l1 : l0;
+        const float lw = side ? lam : 1.0f - lam;
+        if (lw == 0.0f)
+            continue;
+        const int W = T.res >> level, wb = W >> 2;
+        const int64_t lbase = (int64_t)((((uint32_t)(T.res >> 2) * (uint32_t)(T.res >> 2)) -
+                                         ((uint32_t)wb * (uint32_t)wb)) * 4u / 3u);
+        const float x = u * (float)W - 0.5f, y = v * (float)W - 0.5f;
+        const float fx0 = floorf(x), fy0 = floorf(y);
+        const float fx = x - fx0, fy = y - fy0;
+        const int i0 = (int)fx0, j0 = (int)fy0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int i = (i0 + (c & 1)) & (W - 1), j = (j0 + (c >> 1)) & (W - 1);
+            const float bw = ((c & 1) ? fx : 1.0f - fx) * ((c >> 1) ? fy : 1.0f - fy);
+            Tap tp;
+            tp.block = lbase + (int64_t)(j >> 2) * wb + (i >> 2);
+            tp.texel = ((j & 3) << 2) | (i & 3);
+            tp.weight = lw * bw;
+            f(tp);
+        }
+    }
+}
+
+// ----------------------------------------------------- reference material
+
+__device__ __forceinline__ void catmull_rom(float f, float w[4])
+{
+    const float f2 = f * f, f3 = f2 * f;
+    w[0] = 0.5f * (-f3 + 2.0f * f2 - f);
+    w[1] = 0.5f * (3.0f * f3 - 5.0f * f2 + 2.0f);
+    w[2] = 0.5f * (-3.0f * f3 + 4.0f * f2 + f);
+    w[3] = 0.5f * (f3 - f2);
+}
+
+__device__ __forceinline__ void target_level(const TrainDev &D, int level, float u, float v, float scale, float out[9])
+{
+    const int W = D.tres >> level;
+    int64_t base = 0;
+    for (int l = 0; l < level; ++l)
+        base += (int64_t)(D.tres >> l) * (D.tres >> l);
+    const float x = u * (float)W - 0.5f, y = v * (float)W - 0.5f;
+    const float fx0 = floorf(x), fy0 = floorf(y);
+    float wx[4], wy[4];
+    catmull_rom(x - fx0, wx);
+    catmull_rom(y - fy0, wy);
+    const int i0 = (int)fx0, j0 = (int)fy0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const int j = (j0 - 1 + b) & (W - 1);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int i = (i0 - 1 + a) & (W - 1);
+            const int64_t idx = base + (int64_t)j * W + i;
+            const float wgt = wx[a] * wy[b] * scale;
+            const uint4 c8 = __ldg(reinterpret_cast<const uint4 *>(D.t8) + idx);
+            const uint32_t w4[4] = {c8.x, c8.y, c8.z, c8.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w4[q]));
+                out[2 * q] = fmaf(wgt, f.x, out[2 * q]);
+                out[2 * q + 1] = fmaf(wgt, f.y, out[2 * q + 1]);
+            }
+            out[8] = fmaf(wgt, __half2float(__ushort_as_half(__ldg(D.t1 + idx))), out[8]);
+        }
+    }
+}
+
+__device__ __forceinline__ void target_sample(const TrainDev &D, float u, float v, float s, float out[9])
+{
+    float sq = isnan(s) ? 0.0f : s;
+    sq = fminf(fmaxf(sq, 0.0f), (float)(D.tlevels - 1));
+    const float fl = floorf(sq);
+    const int l0 = (int)fl;
+    const int l1 = min(l0 + 1, D.tlevels - 1);
+    const float lam = sq - fl;
+#pragma unroll
+    for (int c = 0; c < 9; ++c)
+        out[c] = 0.0f;
+    if (l1 != l0 && lam > 0.0f) {
+        target_level(D, l0, u, v, 1.0f - lam, out);
+        target_level(D, l1, u, v, lam, out);
+    } else {
+        target_level(D, l0, u, v, 1.0f, out);
+    }
+}
+
+// ------------------------------------------------------------ the kernel
+
+enum { kModeForward = 0, kModeBackward = 1, kModeStep = 2 };
+constexpr int kTrainThreads = 128;
+
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+struct TrainSmem {
+    float *Wbf, *bias, *dW, *db;
+    float *act[BCF_MAX_LAYERS];  // layer inputs A[l] [threads][stride]
+    float *grd[BCF_MAX_LAYERS];  // dL/d(output of layer l) [threads][stride]
+    int stride[BCF_MAX_LAYERS + 1];
+};
+
+__host__ __device__ inline int64_t train_smem_floats(const TrainDev &D)
+{
+    int64_t f = 2 * (int64_t)(D.w_total + D.b_total);
+    for (int l = 0; l <= D.n_layers; ++l) {
+        const int st = D.dims[l] | 1; // odd row stride: conflict-free column access
+        if (l < D.n_layers)
+            f += (int64_t)kTrainThreads * st; // act[l]
+        if (l > 0)
+            f += (int64_t)kTrainThreads * st; // grd[l-1]
+    }
+    return f;
+}
+
+__global__ void __launch_bounds__(kTrainThreads) k_train(TrainDev D, int mode, int64_t batch, uint32_t seed_lo,
+                                                         uint32_t seed_hi, uint32_t step_lo, uint32_t step_hi,
+                                                         const float *__restrict__ qu, const float *__restrict__ qv,
+                                                         const float *__restrict__ qs, float *__restrict__ out,
+                                                         const float *__restrict__ grad_out, float *loss,
+                                                         float gscale)
+{
+    extern __shared__ __align__(16) float tsm[];
+    const int L = D.n_layers;
+    TrainSmem S;
+    {
+        float *p = tsm;
+        S.Wbf = p;
+        p += D.w_total;
+        S.bias = p;
+        p += D.b_total;
+        S.dW = p;
+        p += D.w_total;
+        S.db = p;
+        p += D.b_total;
+        for (int l = 0; l <= L; ++l)
+            S.stride[l] = D.dims[l] | 1;
+        for (int l = 0; l < L; ++l) {
+            S.act[l] = p;
+            p += kTrainThreads * S.stride[l];
+        }
+        for (int l = 0; l < L; ++l) {
+            S.grd[l] = p;
+            p += kTrainThreads * S.stride[l + 1];
+        }
+    }
+    for (int i = threadIdx.x; i < D.w_total; i += blockDim.x) {
+        S.Wbf[i] = bf16r(D.W[i]);
+        S.dW[i] = 0.0f;
+    }
+    for (int i = threadIdx.x; i < D.b_total; i += blockDim.x) {
+        S.bias[i] = D.b[i];
+        S.db[i] = 0.0f;
+    }
+    __syncthreads();
+    const int tid = threadIdx.x;
+    const int nout = D.dims[L];
+    float loss_acc = 0.0f;
+    const int64_t tiles = (batch + kTrainThreads - 1) / kTrainThreads;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int64_t q = tile * kTrainThreads + tid;
+        const bool active = q < batch;
+        float u = 0.0f, v = 0.0f, s = 0.0f;
+        if (active) {
+            if (qu) {
+                u = qu[q];
+                v = qv[q];
+                s = qs[q];
+            } else {
+                uint32_t c[4] = {(uint32_t)q, step_lo, step_hi, (uint32_t)((uint64_t)q >> 32)};
+                philox4x32_10(c, seed_lo, seed_hi);
+                u = (float)(c[0] >> 8) * 0x1p-24f;
+                v = (float)(c[1] >> 8) * 0x1p-24f;
+                s = ((float)(c[2] >> 8) * 0x1p-24f) * D.s_max;
+            }
+            u = isfinite(u) ? u - floorf(u) : 0.0f;
+            v = isfinite(v) ? v - floorf(v) : 0.0f;
+        }
+        // ---- features (emulated BC6 + trilinear), rounded MLP input row
+        float *a0 = S.act[0] + tid * S.stride[0];
+        for (int t = 0; t < D.n_tex; ++t) {
+            float f[3] = {0.0f, 0.0f, 0.0f};
+            if (active) {
+                const TrainTexDev &T = D.tex[t];
+                for_each_tap(T, u, v, s, [&](const Tap &tp) {
+                    SteTexel tx;
+                    ste_texel(T.params + tp.block * 32, T.part[tp.block], tp.texel, tx);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c)
+                        f[c] = fmaf(tp.weight, tx.v[c], f[c]);
+                });
+            }
+            a0[3 * t] = bf16r(f[0]);
+            a0[3 * t + 1] = bf16r(f[1]);
+            a0[3 * t + 2] = bf16r(f[2]);
+        }
+        if (D.lod_input)
+            a0[3 * D.n_tex] = bf16r(active ? (isnan(s) ? 0.0f : fmaxf(s, 0.0f)) : 0.0f);
+        // ---- MLP forward (hidden: ReLU then BF16 rounding; output: FP32)
+        float y[64];
+        for (int l = 0; l < L; ++l) {
+            const int ni = D.dims[l], no = D.dims[l + 1];
+            const float *W = S.Wbf + D.w_off[l];
+            const float *b = S.bias + D.b_off[l];
+            const float *xin = S.act[l] + tid * S.stride[l];
+            float *xout = l + 1 < L ? S.act[l + 1] + tid * S.stride[l + 1] : nullptr;
+            for (int o = 0; o < no; ++o) {
+                float acc = 0.0f;
+                for (int i = 0; i < ni; ++i)
+                    acc = fmaf(W[o * ni + i], xin[i], acc);
+                acc += b[o];
+                if (xout)
+                    xout[o] = bf16r(fmaxf(acc, 0.0f));
+                else
+                    y[o] = acc;
+            }
+        }
+        if (mode == kModeForward) {
+            if (active)
+                for (int o = 0; o < nout; ++o)
+                    out[q * nout + o] = y[o];
+            continue;
+        }
+        // ---- output gradient: given, or from the MSE against the reference (Eq. 5, mean over batch x C)
+        float *gL = S.grd[L - 1] + tid * S.stride[L];
+        if (mode == kModeBackward) {
+            for (int o = 0; o < nout; ++o)
+                gL[o] = active ? grad_out[q * nout + o] : 0.0f;
+        } else {
+            float tg[9];
+            if (active)
+                target_sample(D, u, v, s, tg);
+            for (int o = 0; o < nout; ++o) {
+                const float d = active ? y[o] - tg[o] : 0.0f;
+                loss_acc = fmaf(d, d, loss_acc);
+                gL[o] = gscale * d;
+            }
+        }
+        // ---- MLP backward: grd[l-1] = (act[l] > 0) * W_l^T grd[l]
+        for (int l = L - 1; l >= 1; --l) {
+            const int ni = D.dims[l], no = D.dims[l + 1];
+            const float *W = S.Wbf + D.w_off[l];
+            const float *g = S.grd[l] + tid * S.stride[l + 1];
+            const float *a = S.act[l] + tid * S.stride[l];
+            float *gp = S.grd[l - 1] + tid * S.stride[l];
+            for (int i = 0; i < ni; ++i) {
+                float acc = 0.0f;
+                if (a[i] > 0.0f)
+                    for (int o = 0; o < no; ++o)
+                        acc = fmaf(W[o * ni + i], g[o], acc);
+                gp[i] = acc;
+            }
+        }
+        __syncthreads();
+        // ---- weight gradients of the tile: dW_l += sum_q grd[l][q] (x) act[l][q], db_l += sum_q grd[l][q]
+        for (int l = 0; l < L; ++l) {
+            const int ni = D.dims[l], no = D.dims[l + 1];
+            const int sa = S.stride[l], sg = S.stride[l + 1];
+            for (int e = tid; e < no * (ni + 1); e += kTrainThreads) {
+                const int o = e / (ni + 1), i = e - o * (ni + 1);
+                float acc = 0.0f;
+                const float *g = S.grd[l] + o;
+                if (i < ni) {
+                    const float *a = S.act[l] + i;
+                    for (int r = 0; r < kTrainThreads; ++r)
+                        acc = fmaf(g[r * sg], a[r * sa], acc);
+                    S.dW[D.w_off[l] + o * ni + i] += acc;
+                } else {
+                    for (int r = 0; r < kTrainThreads; ++r)
+                        acc += g[r * sg];
+                    S.db[D.b_off[l] + o] += acc;
+                }
+            }
+        }
+        // ---- input gradient and the scatter into the block parameters
+        if (active) {
+            const float *g1 = S.grd[0] + tid * S.stride[1];
+            const float *W0 = S.Wbf + D.w_off[0];
+            const int n1 = D.dims[1], n0 = D.dims[0];
+            for (int t = 0; t < D.n_tex; ++t) {
+                float dxf[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    float acc = 0.0f;
+                    for (int o = 0; o < n1; ++o)
+                        acc = fmaf(W0[o * n0 + 3 * t + c], g1[o], acc);
+                    dxf[c] = acc;
+                }
+                const TrainTexDev &T = D.tex[t];
+                for_each_tap(T, u, v, s, [&](const Tap &tp) {
+                    const float *p = T.params + tp.block * 32;
+                    SteTexel tx;
+                    ste_texel(p, T.part[tp.block], tp.texel, tx);
+                    float *gp = T.grad + tp.block * 32;
+                    float ga[3], gb[3], gx = 0.0f;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        const float dv = dxf[c] * tp.weight;
+                        ga[c] = tx.ina[c] ? dv * tx.dea[c] : 0.0f;
+                        gb[c] = tx.inb[c] ? dv * tx.deb[c] : 0.0f;
+                        gx = fmaf(dv, tx.dx[c], gx);
+                    }
+                    red_add_v4(gp + 8 * tx.region, ga[0], ga[1], ga[2], gb[0]);
+                    red_add_v2(gp + 8 * tx.region + 4, gb[1], gb[2]);
+                    if (tx.inx)
+                        atomicAdd(gp + 16 + tp.texel, gx);
+                });
+            }
+        }
+        __syncthreads(); // the staged rows are rewritten by the next tile
+    }
+    // ---- flush the CTA's weight gradients and loss
+    if (mode != kModeForward) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < D.w_total; i += blockDim.x)
+            if (S.dW[i] != 0.0f)
+                atomicAdd(D.Wg + i, S.dW[i]);
+        for (int i = threadIdx.x; i < D.b_total; i += blockDim.x)
+            if (S.db[i] != 0.0f)
+                atomicAdd(D.bg + i, S.db[i]);
+    }
+    if (mode == kModeStep) {
+        for (int off = 16; off > 0; off >>= 1)
+            loss_acc += __shfl_xor_sync(0xffffffffu, loss_acc, off);
+        if ((threadIdx.x & 31) == 0 && loss_acc != 0.0f)
+            atomicAdd(loss, loss_acc * (gscale * 0.5f));
+    }
+}
+
+// ------------------------------------------------------------------ Adam
+
+struct AdamSeg {
+    float *p, *g, *m, *v;
+    int64_t n;
+    float lr;
+    int blocks_layout; // 1: block parameters (clamp endpoints to [0, 63], x to [0, 1], skip unused)
+};
+
+struct AdamArgs {
+    AdamSeg seg[BCF_MAX_TEX + 2];
+    int64_t chunk_start[BCF_MAX_TEX + 3];
+    int nseg;
+    float beta1, beta2, eps, bc1, bc2;
+};
+
+constexpr int kAdamChunk = 4096;
+
+__global__ void __launch_bounds__(256) k_adam(AdamArgs A)
+{
+    int k = 0;
+    while (k + 1 < A.nseg && (int64_t)blockIdx.x >= A.chunk_start[k + 1])
+        ++k;
+    const AdamSeg &S = A.seg[k];
+    const int64_t i0 = ((int64_t)blockIdx.x - A.chunk_start[k]) * kAdamChunk;
+    const int64_t i1 = min(i0 + kAdamChunk, S.n);
+    for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
+        const float g = S.g[i];
+        S.g[i] = 0.0f;
+        if (S.blocks_layout) {
+            const int e = (int)(i & 31);
+            if (e == 6 || e == 7 || e == 14 || e == 15)
+                continue;
+        }
+        const float m = A.beta1 * S.m[i] + (1.0f - A.beta1) * g;
+        const float v = A.beta2 * S.v[i] + (1.0f - A.beta2) * g * g;
+        S.m[i] = m;
+        S.v[i] = v;
+        float p = S.p[i] - S.lr * (m / A.bc1) / (sqrtf(v / A.bc2) + A.eps);
+        if (S.blocks_layout)
+            p = (i & 31) < 16 ? fminf(fmaxf(p, 0.0f), 63.0f) : fminf(fmaxf(p, 0.0f), 1.0f);
+        S.p[i] = p;
+    }
+}
+
+// ---------------------------------------------------------------- export
+
+// BC6H mode 10 writer (the field order the decoder reads back).
+struct BitWriter {
+    uint64_t lo = 0, hi = 0;
+    int pos = 0;
+    __device__ void put(uint32_t v, int lsb, int n)
+    {
+        for (int j = 0; j < n; ++j, ++pos) {
+            const uint64_t bit = (v >> (lsb + j)) & 1u;
+            if (pos < 64)
+                lo |= bit << pos;
+            else
+                hi |= bit << (pos - 64);
+        }
+    }
+};
+
+__global__ void k_export_blocks(const float *__restrict__ params, const uint8_t *__restrict__ part, int64_t nblocks,
+                                uint4 *__restrict__ out)
+{
+    const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (b >= nblocks)
+        return;
+    const float *p = params + b * 32;
+    const int k = part[b];
+    int q[4][3], idx[16];
+#pragma unroll
+    for (int e = 0; e < 4; ++e)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+            q[e][c] = (int)rintf(fminf(fmaxf(p[(e >> 1) * 8 + (e & 1) * 3 + c], 0.0f), 63.0f));
+#pragma unroll
+    for (int t = 0; t < 16; ++t)
+        idx[t] = (int)rintf(7.0f * fminf(fmaxf(p[16 + t], 0.0f), 1.0f));
+    const uint32_t pm = partition_mask(k);
+    const int anchors[2] = {0, anchor2_of(k)};
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        if (idx[anchors[r]] >= 4) { // the anchor index must fit 2 bits: swap the region's endpoints
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const int tmp = q[2 * r][c];
+                q[2 * r][c] = q[2 * r + 1][c];
+                q[2 * r + 1][c] = tmp;
+            }
+#pragma unroll
+            for (int t = 0; t < 16; ++t)
+                if ((int)((pm >> t) & 1) == r)
+                    idx[t] = 7 - idx[t];
+        }
+    }
+    const uint32_t r0 = q[0][0], g0 = q[0][1], b0 = q[0][2], r1 = q[1][0], g1 = q[1][1], b1 = q[1][2];
+    const uint32_t r2 = q[2][0], g2 = q[2][1], b2 = q[2][2], r3 = q[3][0], g3 = q[3][1], b3 = q[3][2];
+    BitWriter w;
+    w.put(30u, 0, 5); // mode field 11110
+    w.put(r0, 0, 6); w.put(g3, 4, 1); w.put(b3, 0, 1); w.put(b3, 1, 1); w.put(b2, 4, 1);
+    w.put(g0, 0, 6); w.put(g2, 5, 1); w.put(b2, 5, 1); w.put(b3, 2, 1); w.put(g2, 4, 1);
+    w.put(b0, 0, 6); w.put(g3, 5, 1); w.put(b3, 3, 1); w.put(b3, 5, 1); w.put(b3, 4, 1);
+    w.put(r1, 0, 6); w.put(g2, 0, 4); w.put(g1, 0, 6); w.put(g3, 0, 4); w.put(b1, 0, 6);
+    w.put(b2, 0, 4); w.put(r2, 0, 6); w.put(r3, 0, 6); w.put((uint32_t)k, 0, 5);
+#pragma unroll
+    for (int t = 0; t < 16; ++t)
+        w.put((uint32_t)idx[t], 0, (t == 0 || t == anchors[1]) ? 2 : 3);
+    out[b] = make_uint4((uint32_t)w.lo, (uint32_t)(w.lo >> 32), (uint32_t)w.hi, (uint32_t)(w.hi >> 32));
+}
+
+__global__ void k_export_weights(const float *__restrict__ W, int64_t n, uint16_t *__restrict__ out)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i < n)
+        out[i] = __half_as_ushort(__float2half_rn(W[i]));
+}
+
+// -------------------------------------------------------------- launchers
+
+static int train_sms()
+{
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (sms <= 0)
+            sms = 148;
+    }
+    return sms;
+}
+
+int64_t train_smem_bytes(const TrainDev &D) { return train_smem_floats(D) * 4; }
+
+cudaError_t launch_train(const TrainDev &D, int mode, int64_t batch, uint64_t seed, int64_t step, const float *u,
+                         const float *v, const float *s, float *out, const float *grad_out, float *loss,
+                         cudaStream_t st)
+{
+    if (batch <= 0)
+        return cudaSuccess;
+    const int64_t smem = train_smem_bytes(D);
+    static int configured = 0;
+    if (!configured) {
+        cudaFuncSetAttribute(k_train, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        configured = 1;
+    }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_train, kTrainThreads, (size_t)smem);
+    const int64_t tiles = (batch + kTrainThreads - 1) / kTrainThreads;
+    const int64_t grid = min(tiles, (int64_t)train_sms() * max(per_sm, 1));
+    const float gscale = 2.0f / ((float)batch * (float)D.dims[D.n_layers]);
+    k_train<<<(unsigned)grid, kTrainThreads, (size_t)smem, st>>>(
+        D, mode, batch, (uint32_t)seed, (uint32_t)(seed >> 32), (uint32_t)step, (uint32_t)((uint64_t)step >> 32), u, v,
+        s, out, grad_out, loss, gscale);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam(const TrainDev &D, const TrainHyper &H, int64_t step, cudaStream_t st)
+{
+    AdamArgs A;
+    memset(&A, 0, sizeof A);
+    const double decay = pow((double)H.gamma, (double)step);
+    int k = 0;
+    for (int t = 0; t < D.n_tex; ++t) {
+        A.seg[k] = {D.tex[t].params, D.tex[t].grad, D.tex[t].m, D.tex[t].v, D.tex[t].blocks * 32,
+                    (float)(H.lr_features * decay), 1};
+        ++k;
+    }
+    A.seg[k++] = {D.W, D.Wg, D.Wm, D.Wv, D.w_total, (float)(H.lr_mlp * decay), 0};
+    A.seg[k++] = {D.b, D.bg, D.bm, D.bv, D.b_total, (float)(H.lr_mlp * decay), 0};
+    A.nseg = k;
+    int64_t chunks = 0;
+    for (int i = 0; i < k; ++i) {
+        A.chunk_start[i] = chunks;
+        chunks += (A.seg[i].n + kAdamChunk - 1) / kAdamChunk;
+    }
+    A.chunk_start[k] = chunks;
+    A.beta1 = H.beta1;
+    A.beta2 = H.beta2;
+    A.eps = H.eps;
+    A.bc1 = (float)(1.0 - pow((double)H.beta1, (double)(step + 1)));
+    A.bc2 = (float)(1.0 - pow((double)H.beta2, (double)(step + 1)));
+    if (chunks == 0)
+        return cudaSuccess;
+    k_adam<<<(unsigned)chunks, 256, 0, st>>>(A);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_export(const TrainDev &D, void *const *blocks_out, uint16_t *weights_fp16, cudaStream_t st)
+{
+    for (int t = 0; t < D.n_tex; ++t) {
+        const int64_t nb = D.tex[t].blocks;
+        k_export_blocks<<<(unsigned)((nb + 127) / 128), 128, 0, st>>>(D.tex[t].params, D.tex[t].part, nb,
+                                                                      (uint4 *)blocks_out[t]);
+    }
+    if (weights_fp16)
+        k_export_weights<<<(unsigned)((D.w_total + 255) / 256), 256, 0, st>>>(D.W, D.w_total, weights_fp16);
+    return cudaGetLastError();
+}
+
+} // namespace bcf

@@ -1,0 +1,47 @@
+// bcf_train.h -- trainer structures shared by the training kernels and the C ABI.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/bcf.h"
+
+namespace bcf {
+
+struct TrainTexDev {
+    float *params;        // [blocks][32]
+    float *grad;          // [blocks][32]
+    float *m, *v;         // Adam moments
+    const uint8_t *part;  // [blocks]
+    int32_t res, levels, lod_bias;
+    int64_t blocks;
+};
+
+struct TrainDev {
+    int32_t n_tex, lod_input, n_layers;
+    int32_t dims[BCF_MAX_LAYERS + 1];
+    int32_t w_off[BCF_MAX_LAYERS], b_off[BCF_MAX_LAYERS];
+    int32_t w_total, b_total;
+    TrainTexDev tex[BCF_MAX_TEX];
+    float *W, *b, *Wg, *bg, *Wm, *Wv, *bm, *bv;
+    int32_t tres, tlevels;
+    const uint16_t *t8, *t1;
+    float s_max;
+};
+
+struct TrainHyper {
+    float lr_features, lr_mlp, gamma, beta1, beta2, eps;
+};
+
+int64_t train_smem_bytes(const TrainDev &D);
+cudaError_t launch_train(const TrainDev &D, int mode, int64_t batch, uint64_t seed, int64_t step, const float *u,
+                         const float *v, const float *s, float *out, const float *grad_out, float *loss,
+                         cudaStream_t st);
+cudaError_t launch_adam(const TrainDev &D, const TrainHyper &H, int64_t step, cudaStream_t st);
+cudaError_t launch_export(const TrainDev &D, void *const *blocks_out, uint16_t *weights_fp16, cudaStream_t st);
+
+} // namespace bcf
+
+struct bcf_trainer_s {
+    bcf::TrainDev dev;
+    bcf::TrainHyper hyper;
+};

@@ -125,3 +125,73 @@ def queries_to_device(w: DecodeWorkload, device: str = "cuda"):
     v = torch.from_numpy(w.v).to(device)
     s = None if w.s is None else torch.from_numpy(w.s).to(device)
     return u, v, s
+
+
+# --------------------------------------------------------------------------- training (config 3)
+
+@dataclass
+class TrainWorkload:
+    name: str
+    res: list[int]
+    levels: list[int]
+    params: list[np.ndarray]      # float32 [blocks, 32] (device layout: region r's endpoints at 8 r, x at 16)
+    partition: list[np.ndarray]   # uint8 [blocks]
+    dims: list[int]
+    W: np.ndarray                 # float32, layers concatenated
+    b: np.ndarray
+    target8: np.ndarray           # float16 [texels, 8]
+    target1: np.ndarray           # float16 [texels]
+    target_res: int
+    target_levels: int
+    batch: int
+
+    @property
+    def res_ref(self) -> int:
+        return self.target_res
+
+
+def params28_to_32(p28: np.ndarray) -> np.ndarray:
+    """[blocks, 28] (e1..e4 RGB, x1..x16) -> the 32-float device record."""
+    out = np.zeros((p28.shape[0], 32), np.float32)
+    out[:, 0:6] = p28[:, 0:6]
+    out[:, 8:14] = p28[:, 6:12]
+    out[:, 16:32] = p28[:, 12:28]
+    return out
+
+
+def params32_to_28(p32: np.ndarray) -> np.ndarray:
+    return np.concatenate([p32[:, 0:6], p32[:, 8:14], p32[:, 16:32]], axis=1)
+
+
+def train_workload(res=(1024, 1024, 1024, 1024), target_res: int = 2048, batch: int = 1 << 20,
+                   dims=(13, 32, 32, 9), config: int = 3) -> TrainWorkload:
+    levels = [synth.full_levels(r) for r in res]
+    rng = seed_rng(config, 4)
+    params, part = [], []
+    for r, l in zip(res, levels):
+        p28, k = synth.train_block_params(rng, sum(synth.level_blocks(r, l)))
+        p28 = np.concatenate([p28[:, :12], p28[:, 12:]], axis=1)
+        params.append(params28_to_32(p28))
+        part.append(k)
+    tl = synth.full_levels(target_res)
+    img = synth.pbr_target(seed_rng(config, 3), target_res)
+    t8, t1 = synth.target_mips(img, tl)
+    Ws, bs = synth.mlp_weights(seed_rng(config, 2), list(dims))
+    W = np.concatenate([w.ravel() for w in Ws]).astype(np.float32)
+    b = np.concatenate(bs).astype(np.float32)
+    return TrainWorkload(f"train-{len(res)}x{res[0]}-target{target_res}", list(res), levels, params, part, list(dims),
+                         W, b, t8, t1, target_res, tl, batch)
+
+
+def upload_trainer(w: TrainWorkload, device: str = "cuda", **hyper):
+    import torch
+
+    from . import Trainer
+
+    P = [torch.from_numpy(p.copy()).to(device) for p in w.params]
+    K = [torch.from_numpy(k.copy()).to(device) for k in w.partition]
+    W = torch.from_numpy(w.W.copy()).to(device)
+    b = torch.from_numpy(w.b.copy()).to(device)
+    t8 = torch.from_numpy(w.target8.view(np.int16).copy()).to(device)
+    t1 = torch.from_numpy(w.target1.view(np.int16).copy()).to(device)
+    return Trainer(P, K, w.res, w.levels, w.res_ref, w.dims, W, b, t8, t1, w.target_res, w.target_levels, **hyper)

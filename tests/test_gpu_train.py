@@ -1,0 +1,195 @@
+"""GPU parity of the training path (emulated BC6 mode 10 + MLP + reference
+sampling + Adam) against the CPU oracle, export round trip, the autograd
+function, and a training sanity check."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2311_16121_b300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def _bcf():
+    import paper_2311_16121_b300 as bcf
+
+    bcf.lib()
+    return bcf
+
+
+def _oracle_parts(w, params32=None, W=None, b=None):
+    p32 = w.params if params32 is None else params32
+    F = oracle.TrainFeatures([workloads.params32_to_28(p).astype(np.float64) for p in p32], w.partition, w.res,
+                             w.levels, w.res_ref, lod_input=True)
+    P = oracle.TrainMlp(w.dims, w.W if W is None else W, w.b if b is None else b, bf16=True)
+    T = oracle.Target(w.target8, w.target1, w.target_res, w.target_levels)
+    return F, P, T
+
+
+SMALL = dict(res=(16, 8), target_res=32, batch=384, dims=(7, 8, 8, 9))
+MEDIUM = dict(res=(64, 64, 64, 64), target_res=128, batch=600, dims=(13, 32, 32, 9))
+
+
+def _queries(n, s_max, seed=3):
+    rng = np.random.default_rng(seed)
+    u = rng.random(n, dtype=np.float32)
+    v = rng.random(n, dtype=np.float32)
+    s = rng.uniform(0, s_max, n).astype(np.float32)
+    return u, v, s
+
+
+def _close_fraction(got, ref, rtol, atol_frac):
+    scale = np.abs(ref).max() + 1e-30
+    bad = np.abs(got - ref) > rtol * np.abs(ref) + atol_frac * scale
+    return bad.mean(), np.abs(got - ref).max() / scale
+
+
+@pytest.mark.parametrize("shape", ["small", "medium"])
+def test_train_forward_matches_oracle(shape):
+    _bcf()
+    w = workloads.train_workload(**(SMALL if shape == "small" else MEDIUM))
+    tr = workloads.upload_trainer(w)
+    u, v, s = _queries(w.batch, w.target_levels - 1)
+    got = tr.forward(*(torch.from_numpy(a).cuda() for a in (u, v, s))).cpu().numpy().astype(np.float64)
+    F, P, _ = _oracle_parts(w)
+    ref = oracle.train_outputs(F, P, u, v, s)
+    err = np.abs(got - ref)
+    # BF16-rounded MLP on both sides; FP32 vs FP64 accumulation may flip isolated BF16 roundings
+    assert (err > 4e-3).mean() <= 2e-3 and err.max() < 0.05, (err.max(), (err > 4e-3).mean())
+
+
+@pytest.mark.parametrize("shape", ["small", "medium"])
+def test_train_backward_matches_oracle_gradient(shape):
+    _bcf()
+    w = workloads.train_workload(**(SMALL if shape == "small" else MEDIUM))
+    tr = workloads.upload_trainer(w)
+    u, v, s = _queries(w.batch, w.target_levels - 1, seed=4)
+    go = np.random.default_rng(5).standard_normal((w.batch, 9)).astype(np.float32) * 1e-2
+    tr.zero_grad()
+    tr.backward(*(torch.from_numpy(a).cuda() for a in (u, v, s)), torch.from_numpy(go).cuda())
+    F, P, _ = _oracle_parts(w)
+    gf, gW, gb = oracle.train_backward_given(F, P, u, v, s, go.astype(np.float64))
+    for name, got, ref in [("W", tr.W_grad.cpu().numpy(), gW), ("b", tr.b_grad.cpu().numpy(), gb)] + [
+            (f"features{t}", workloads.params32_to_28(tr.grads[t].cpu().numpy()), gf[t]) for t in range(len(gf))]:
+        frac, worst = _close_fraction(got.astype(np.float64), ref, 1e-3, 1e-4)
+        assert frac <= 5e-3 and worst < 5e-2, (name, frac, worst)
+    # the unused slots of the parameter records receive nothing
+    for g in tr.grads:
+        assert not g[:, [6, 7, 14, 15]].any()
+
+
+def test_train_step_loss_with_philox_draws_and_adam_update():
+    bcf = _bcf()
+    w = workloads.train_workload(**MEDIUM)
+    tr = workloads.upload_trainer(w, lr_features=1e-2, lr_mlp=1e-3, gamma=0.9999)
+    seed, step = 1234567, 0
+    loss = float(tr.step(w.batch, seed, step).item())
+    u, v, s = oracle.train_queries(seed, step, w.batch, float(w.target_levels - 1))
+    F, P, T = _oracle_parts(w)
+    ref_loss, gf, gW, gb = oracle.train_loss_grad(F, P, T, u, v, s)
+    assert loss == pytest.approx(ref_loss, rel=2e-3)
+    # first Adam step: p -= lr * g / (|g| + eps) (bias-corrected), projected to the box; compare where |g| is
+    # clearly non-zero (sign-like updates), everything else must stay within one learning-rate step
+    newW = tr.W.cpu().numpy().astype(np.float64)
+    pW, mW, vW = w.W.astype(np.float64).copy(), np.zeros(gW.size), np.zeros(gW.size)
+    oracle.adam(pW, gW.copy(), mW, vW, step, 1e-3, 0.9999)
+    big = np.abs(gW) > 1e-3 * np.abs(gW).max()
+    np.testing.assert_allclose(newW[big], pW[big], rtol=0, atol=2e-6)
+    assert np.abs(newW - pW).max() <= 2.0e-3 + 1e-6
+    for t in range(len(gf)):
+        p28 = workloads.params32_to_28(tr.params[t].cpu().numpy()).astype(np.float64)
+        o28 = workloads.params32_to_28(w.params[t]).astype(np.float64)
+        ends, xs = o28[:, :12].copy(), o28[:, 12:].copy()
+        ge, gx = gf[t][:, :12].copy(), gf[t][:, 12:].copy()
+        oracle.adam(ends.reshape(-1), ge.reshape(-1).copy(), np.zeros(ends.size), np.zeros(ends.size), step, 1e-2,
+                    0.9999, lo=0.0, hi=63.0)
+        oracle.adam(xs.reshape(-1), gx.reshape(-1).copy(), np.zeros(xs.size), np.zeros(xs.size), step, 1e-2, 0.9999,
+                    lo=0.0, hi=1.0)
+        ref = np.concatenate([ends, xs], axis=1)
+        g = np.concatenate([ge, gx], axis=1)
+        big = np.abs(g) > 1e-3 * np.abs(g).max()
+        np.testing.assert_allclose(p28[big], ref[big], rtol=0, atol=2e-5)
+        assert np.abs(p28 - ref).max() <= 2e-2 + 1e-5
+    # gradients were zeroed by the optimiser
+    assert not tr.W_grad.any() and not any(g.any() for g in tr.grads)
+
+
+def test_export_is_bit_exact_and_decodes_to_the_emulated_features():
+    bcf = _bcf()
+    w = workloads.train_workload(**SMALL)
+    # include lattice extremes and anchor swaps
+    w.params[0][:4, 0:6] = [[0, 63, 0.49, 62.5, 31.5, 7]] * 4
+    tr = workloads.upload_trainer(w)
+    blocks, w16 = tr.export()
+    for t, blk in enumerate(blocks):
+        got = blk.cpu().numpy().reshape(-1, 16)
+        p28 = workloads.params32_to_28(w.params[t]).astype(np.float64)
+        ref = np.stack([oracle.train_export_block(p28[i], int(w.partition[t][i])) for i in range(p28.shape[0])])
+        np.testing.assert_array_equal(got, ref)
+        # the exported blocks decode (GPU unpack) to the emulated texel values (oracle emulation)
+        off = 0
+        for l in range(w.levels[t]):
+            W = w.res[t] >> l
+            nb = (W // 4) ** 2
+            img = bcf.decode_bc6h(blk[off * 16:(off + nb) * 16].contiguous(), W // 4, W // 4).cpu().numpy()
+            img = img.view(np.uint16).view(np.float16).astype(np.float64)
+            for bi in range(nb):
+                k = int(w.partition[t][off + bi])
+                by, bx = divmod(bi, W // 4)
+                for tx in range(16):
+                    for c in range(3):
+                        assert img[4 * by + tx // 4, 4 * bx + tx % 4, c] == oracle.train_texel(p28[off + bi], k, tx, c)
+            off += nb
+    np.testing.assert_array_equal(w16.cpu().numpy().view(np.float16), w.W.astype(np.float16))
+
+
+def test_autograd_function_matches_trainer_backward():
+    bcf = _bcf()
+    w = workloads.train_workload(**SMALL)
+    tr = workloads.upload_trainer(w)
+    u, v, s = (torch.from_numpy(a).cuda() for a in _queries(200, w.target_levels - 1, seed=9))
+    W = tr.W.clone().requires_grad_(True)
+    b = tr.b.clone().requires_grad_(True)
+    ps = [p.clone().requires_grad_(True) for p in tr.params]
+    y = bcf.BCfTrainFn.apply(tr, u, v, s, W, b, *ps)
+    wts = torch.randn_like(y)
+    (y * wts).sum().backward()
+    tr.zero_grad()
+    tr.backward(u, v, s, wts)
+    torch.testing.assert_close(W.grad, tr.W_grad)
+    torch.testing.assert_close(b.grad, tr.b_grad)
+    for p, g in zip(ps, tr.grads):
+        torch.testing.assert_close(p.grad, g)
+    torch.testing.assert_close(y, tr.forward(u, v, s))
+
+
+def test_training_reduces_loss_and_beats_linear_decoder():
+    """Training sanity: the loss falls, and on held-out queries the trained
+    MLP beats both its step-0 state and the best (least-squares) linear
+    decoder of the same trained features -- what the network adds over the
+    features alone."""
+    bcf = _bcf()
+    w = workloads.train_workload(res=(32, 32, 32, 32), target_res=64, batch=8192, dims=(13, 32, 32, 9))
+    tr = workloads.upload_trainer(w, lr_features=1e-2, lr_mlp=3e-3, gamma=0.9995)
+    hu, hv, hs = _queries(4096, w.target_levels - 1, seed=77)
+    T = oracle.Target(w.target8, w.target1, w.target_res, w.target_levels)
+    tgt = np.stack([oracle.target_sample(T, float(a), float(b_), float(c)) for a, b_, c in zip(hu, hv, hs)])
+    hq = [torch.from_numpy(a).cuda() for a in (hu, hv, hs)]
+    mse0 = float(((tr.forward(*hq).cpu().numpy() - tgt) ** 2).mean())
+    losses = [float(tr.step(w.batch, 42, i).item()) for i in range(400)]
+    torch.cuda.synchronize()
+    mse1 = float(((tr.forward(*hq).cpu().numpy() - tgt) ** 2).mean())
+    assert np.mean(losses[-20:]) < 0.5 * np.mean(losses[:5])
+    assert mse1 < 0.5 * mse0
+    # features of the trained textures: export, then the decode path's feature sampling
+    blocks, _ = tr.export()
+    zW = torch.zeros(13 * 16 + 16 * 9, dtype=torch.float16, device="cuda")
+    zb = torch.zeros(16 + 9, dtype=torch.float32, device="cuda")
+    mat = bcf.Material(blocks, w.res, w.levels, w.res_ref, [13, 16, 9], "fp16", zW, zb)
+    feat = mat.sample_features(*hq).cpu().numpy().astype(np.float64)
+    X = np.concatenate([feat, hs[:, None].astype(np.float64), np.ones((hs.size, 1))], axis=1)
+    coef, *_ = np.linalg.lstsq(X, tgt, rcond=None)
+    mse_lin = float(((X @ coef - tgt) ** 2).mean())
+    assert mse1 < mse_lin, (mse1, mse_lin)
+    print(f"held-out MSE: step 0 {mse0:.4g}, trained {mse1:.4g}, linear decoder on trained features {mse_lin:.4g}")
