@@ -271,6 +271,36 @@ bcf_status bcf_train_backward(bcf_trainer tr, const float *d_u, const float *d_v
                               const float *d_grad_out, bcf_stream stream);
 
 /*
+ * bcf_train_step_noalloc -- bcf_train_step for callers that cannot allocate
+ * device memory: engines and real-time hosts that own every device byte
+ * through their own budgeted allocator, or whose frame loop must not call
+ * cudaMalloc (it can synchronise the device and fails once the budget is
+ * reached).  The paper has no counterpart; this is a property of the
+ * library's interface.
+ *
+ * It computes the same step as bcf_train_step (same arguments, same loss,
+ * parameter, weight and moment updates), but the gradient accumulators --
+ * scratch that lives only between the gradient kernel and the optimiser
+ * kernel -- are kept in one library-owned device array of
+ * BCF_NOALLOC_MAX_GRAD_FLOATS floats (4 MiB) that every GPU which loads
+ * the library holds until the process exits.  The trainer's own gradient
+ * arrays are neither read nor written.  Nothing is allocated: the array's
+ * device address is looked up once per device (cudaGetSymbolAddress) on the
+ * first call made with that device current, so make that first call before
+ * any stream capture.  Every call zeroes the part of the array it uses
+ * before accumulating (the array keeps the last call's contents).  All calls
+ * on a device share the one array: calls whose work overlaps on the GPU
+ * (different streams, or different threads) race and give wrong results.
+ * Errors: those of bcf_train_step; BCF_ERR_UNSUPPORTED when the trainer has
+ * more gradient values than the array holds (each texture's block records
+ * and the weights and biases, each rounded up to 32 floats); BCF_ERR_CUDA
+ * when the address lookup fails.
+ */
+#define BCF_NOALLOC_MAX_GRAD_FLOATS (1 << 20)
+bcf_status bcf_train_step_noalloc(bcf_trainer tr, int64_t batch, uint64_t seed, int64_t step, const float *d_u,
+                                  const float *d_v, const float *d_s, float *d_loss_out, bcf_stream stream);
+
+/*
  * bcf_train_export -- write the trained features as BC6H mode-10 blocks
  * (Sec. 5.2: endpoints rounded to 6 bits, indices to 3 bits; where a
  * region's anchor texel would need the top index bit, the region's

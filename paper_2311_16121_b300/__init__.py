@@ -88,6 +88,9 @@ def lib() -> ctypes.CDLL:
         L.bcf_train_step.restype = c_int
         L.bcf_train_step.argtypes = [c_void_p, c_int64, ctypes.c_uint64, c_int64, c_void_p, c_void_p, c_void_p,
                                      c_void_p, c_void_p]
+        L.bcf_train_step_noalloc.restype = c_int
+        L.bcf_train_step_noalloc.argtypes = [c_void_p, c_int64, ctypes.c_uint64, c_int64, c_void_p, c_void_p,
+                                             c_void_p, c_void_p, c_void_p]
         L.bcf_train_forward.restype = c_int
         L.bcf_train_forward.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p]
         L.bcf_train_backward.restype = c_int
@@ -273,6 +276,12 @@ class Trainer:
         """bcf_train_step; returns the (device) loss of the batch."""
         _check(lib().bcf_train_step(self.handle, int(batch), int(seed), int(step), _ptr(u), _ptr(v), _ptr(s),
                                     _ptr(self.loss), _stream()), "bcf_train_step")
+        return self.loss
+
+    def step_noalloc(self, batch: int, seed: int, step: int, u=None, v=None, s=None) -> torch.Tensor:
+        """bcf_train_step_noalloc: the same step with the gradient scratch in the library's device array."""
+        _check(lib().bcf_train_step_noalloc(self.handle, int(batch), int(seed), int(step), _ptr(u), _ptr(v),
+                                            _ptr(s), _ptr(self.loss), _stream()), "bcf_train_step_noalloc")
         return self.loss
 
     def forward(self, u, v, s) -> torch.Tensor:
