@@ -263,6 +263,25 @@ def main():
             e2e_total += a.elapsed_time(b)
     e2e_value = w.n * world * k_extra / (e2e_total * 1e-3) / 1e9
 
+    # training steps/s: 4 block-parameterised 1024^2 textures with mips, 2048^2 9-channel reference,
+    # batch 2^20 Philox draws, MLP 13-32-32-9 (BF16 operands), Adam
+    tw = workloads.train_workload()
+    tr = workloads.upload_trainer(tw)
+    for i in range(3):
+        tr.step(tw.batch, 7, i)
+    torch.cuda.synchronize()
+    k_train = max(3, args.steps // 2)
+    ta = torch.cuda.Event(enable_timing=True)
+    tb = torch.cuda.Event(enable_timing=True)
+    ta.record(stream)
+    for i in range(k_train):
+        tr.step(tw.batch, 7, 3 + i)
+    tb.record(stream)
+    tb.synchronize()
+    train_ms = ta.elapsed_time(tb) / k_train
+    train_loss = float(tr.loss.item())
+    del tr
+
     hbm_peak, bf16_peak, peak_kind = _peaks()
     tex_bytes = sum(int(b.size) for b in w.blocks)
     alg_bytes = w.n * (12 + 18) + tex_bytes  # queries in, FP16 channels out, the texture set once
@@ -284,6 +303,10 @@ def main():
             "fp32_plain": {"value": w.n / (fp32_ms * 1e-3) / 1e9, "unit": "Gsamples/s", "ms_per_step": fp32_ms},
             "fp8": {"value": w.n / (fp8_ms * 1e-3) / 1e9, "unit": "Gsamples/s", "ms_per_step": fp8_ms},
             "speedup_vs_fp32_plain": fp32_ms / (head_ms / args.steps),
+            "train": {"metric": "train steps/s", "value": 1000.0 / train_ms, "unit": "steps/s",
+                      "ms_per_step": train_ms, "batch": tw.batch, "samples_per_s": tw.batch * 1000.0 / train_ms,
+                      "workload": "4x block-parameterised 1024^2 (9 levels), 2048^2 9-ch reference, "
+                                  "MLP 13-32-32-9 BF16 operands, Adam", "last_loss": train_loss},
             "e2e": {"value": e2e_value, "unit": "Gsamples/s", "h2d_bytes_per_step": 12 * w.n,
                     "d2h_bytes_per_step": 18 * w.n},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",

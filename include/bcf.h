@@ -167,6 +167,60 @@ bcf_status bcf_sample_features(bcf_material mat, const float *d_u, const float *
 bcf_status bcf_decode_material(bcf_material mat, const float *d_u, const float *d_v, const float *d_s, int64_t n,
                                void *d_out, bcf_precision out_precision, bcf_stream stream);
 
+/* ------------------------------------------------------------ material sets */
+
+/*
+ * A material set decodes many materials in one launch (Sec. 5.2: several
+ * materials' networks in one buffer, indexed by material id).  All
+ * materials of a set must share the MLP (precision, layer count and
+ * widths, LOD input) and the texture count; textures may differ in
+ * resolution and levels.  At most BCF_MAX_SET materials.
+ */
+#define BCF_MAX_SET 256
+typedef struct bcf_material_set_s *bcf_material_set;
+
+/*
+ * bcf_create_material_set -- copy the materials' metadata into one device
+ * table and allocate the set's work counter (freed by
+ * bcf_destroy_material_set; synchronous).  The materials must outlive the
+ * set.  Errors: BCF_ERR_INVALID_ARG (n out of [1, BCF_MAX_SET], null
+ * materials, materials that do not share the MLP / texture count),
+ * BCF_ERR_UNSUPPORTED (FP32 materials: the set path is the tensor-core
+ * path), BCF_ERR_OOM / BCF_ERR_CUDA.
+ */
+bcf_status bcf_create_material_set(const bcf_material *mats, int32_t n, bcf_material_set *out);
+bcf_status bcf_destroy_material_set(bcf_material_set set);
+
+/*
+ * bcf_decode_material_set -- bcf_decode_material for every material of the
+ * set in one persistent launch.  The queries of all materials are
+ * concatenated: material m's queries are [d_offsets[m], d_offsets[m+1]) of
+ * d_u / d_v / d_s (and of the rows of d_out [n_queries][C]).  d_offsets:
+ * n + 1 non-decreasing int64 on the device (entries are clipped to
+ * [0, n_queries]).  Queries are processed in tiles of 256 taken from an
+ * atomic work counter that a memset before the launch resets, so the call
+ * can be captured into a CUDA graph and replayed.  Calls on one set must
+ * not overlap on the GPU (they share the counter).  Errors as
+ * bcf_decode_material.
+ */
+bcf_status bcf_decode_material_set(bcf_material_set set, const int64_t *d_offsets, const float *d_u, const float *d_v,
+                                   const float *d_s, int64_t n_queries, void *d_out, bcf_precision out_precision,
+                                   bcf_stream stream);
+
+/*
+ * bcf_autotune_material_set -- time the set-decode launch configurations
+ * (shared-memory block arena 256 / 320 blocks, 1-3 persistent CTAs per SM,
+ * 1 / 2 / 4 / 8 tiles per work-counter grab) on the given workload with
+ * CUDA events (synchronises the stream; the output is overwritten), keep the
+ * fastest for the set, and return it in *cap, *ctas_per_sm, *chunk (any may
+ * be NULL).  bcf_material_set_config reads the current configuration.
+ */
+bcf_status bcf_autotune_material_set(bcf_material_set set, const int64_t *d_offsets, const float *d_u,
+                                     const float *d_v, const float *d_s, int64_t n_queries, void *d_out,
+                                     bcf_precision out_precision, bcf_stream stream, int32_t *cap,
+                                     int32_t *ctas_per_sm, int32_t *chunk);
+bcf_status bcf_material_set_config(bcf_material_set set, int32_t *cap, int32_t *ctas_per_sm, int32_t *chunk);
+
 /* ----------------------------------------------------------------- training */
 
 /*

@@ -81,6 +81,18 @@ def lib() -> ctypes.CDLL:
         L.bcf_set_decode_variant.argtypes = [c_void_p, c_int32]
         L.bcf_decode_material.restype = c_int
         L.bcf_decode_material.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_int, c_void_p]
+        L.bcf_create_material_set.restype = c_int
+        L.bcf_create_material_set.argtypes = [c_void_p, c_int32, POINTER(c_void_p)]
+        L.bcf_destroy_material_set.restype = c_int
+        L.bcf_destroy_material_set.argtypes = [c_void_p]
+        L.bcf_decode_material_set.restype = c_int
+        L.bcf_decode_material_set.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p,
+                                              c_int, c_void_p]
+        L.bcf_autotune_material_set.restype = c_int
+        L.bcf_autotune_material_set.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p,
+                                                c_int, c_void_p, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32)]
+        L.bcf_material_set_config.restype = c_int
+        L.bcf_material_set_config.argtypes = [c_void_p, POINTER(c_int32), POINTER(c_int32), POINTER(c_int32)]
         L.bcf_trainer_create.restype = c_int
         L.bcf_trainer_create.argtypes = [POINTER(_TrainerDesc), POINTER(c_void_p)]
         L.bcf_trainer_destroy.restype = c_int
@@ -211,6 +223,56 @@ class Material:
         _check(lib().bcf_decode_material(self.handle, _ptr(u), _ptr(v), _ptr(s), n, _ptr(out), prec, _stream()),
                "bcf_decode_material")
         return out
+
+
+# --------------------------------------------------------------------------- material sets
+
+class MaterialSet:
+    """A bcf_material_set: several materials sharing the MLP shape, decoded in one persistent launch."""
+
+    def __init__(self, materials: list[Material]):
+        arr = (c_void_p * len(materials))(*[m.handle.value for m in materials])
+        h = c_void_p()
+        _check(lib().bcf_create_material_set(arr, len(materials), ctypes.byref(h)), "bcf_create_material_set")
+        self.handle = h
+        self.materials = list(materials)
+        self.dims = materials[0].dims
+
+    def close(self):
+        if self.handle:
+            _check(lib().bcf_destroy_material_set(self.handle), "bcf_destroy_material_set")
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def decode(self, offsets: torch.Tensor, u, v, s, out_dtype=torch.float16, out: torch.Tensor | None = None):
+        """bcf_decode_material_set: offsets int64 [n_materials + 1] on the device; queries concatenated."""
+        n = u.numel()
+        if out is None:
+            out = torch.empty((n, self.dims[-1]), dtype=out_dtype, device=u.device)
+        prec = FP16 if out.dtype == torch.float16 else FP32
+        _check(lib().bcf_decode_material_set(self.handle, _ptr(offsets), _ptr(u), _ptr(v), _ptr(s), n, _ptr(out),
+                                             prec, _stream()), "bcf_decode_material_set")
+        return out
+
+    def autotune(self, offsets, u, v, s, out: torch.Tensor) -> tuple[int, int, int]:
+        """bcf_autotune_material_set -> (arena blocks, CTAs per SM, tiles per grab)."""
+        a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        prec = FP16 if out.dtype == torch.float16 else FP32
+        _check(lib().bcf_autotune_material_set(self.handle, _ptr(offsets), _ptr(u), _ptr(v), _ptr(s), u.numel(),
+                                               _ptr(out), prec, _stream(), ctypes.byref(a), ctypes.byref(b),
+                                               ctypes.byref(c)), "bcf_autotune_material_set")
+        return a.value, b.value, c.value
+
+    def config(self) -> tuple[int, int, int]:
+        a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(lib().bcf_material_set_config(self.handle, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+               "bcf_material_set_config")
+        return a.value, b.value, c.value
 
 
 # --------------------------------------------------------------------------- training

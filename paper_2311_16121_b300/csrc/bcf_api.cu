@@ -275,4 +275,170 @@ bcf_status bcf_decode_material(bcf_material m, const float *d_u, const float *d_
     return cuda_status(e, "bcf_decode_material launch");
 }
 
+// ------------------------------------------------------------ material sets
+
+} // extern "C"
+
+struct bcf_material_set_s {
+    int n;
+    bcf::MaterialDev first; // host copy of material 0 (MLP shape and layout of the set)
+    bcf::MaterialDev *table; // device table
+    int *counter;            // device work counter
+    bcf::SetConfig cfg;
+};
+
+extern "C" {
+
+bcf_status bcf_create_material_set(const bcf_material *mats, int32_t n, bcf_material_set *out)
+{
+    if (!mats || !out || n < 1 || n > BCF_MAX_SET)
+        return fail(BCF_ERR_INVALID_ARG, "bcf_create_material_set: null argument or n = %d not in [1, %d]", n,
+                    BCF_MAX_SET);
+    *out = nullptr;
+    for (int m = 0; m < n; ++m) {
+        if (!mats[m])
+            return fail(BCF_ERR_INVALID_ARG, "bcf_create_material_set: material %d is null", m);
+        const MaterialDev &A = mats[0]->host, &B = mats[m]->host;
+        bool same = A.n_tex == B.n_tex && A.lod_input == B.lod_input && A.mlp.n_layers == B.mlp.n_layers &&
+                    A.mlp.precision == B.mlp.precision;
+        for (int l = 0; same && l <= A.mlp.n_layers; ++l)
+            same = A.mlp.dims[l] == B.mlp.dims[l];
+        if (!same)
+            return fail(BCF_ERR_INVALID_ARG, "bcf_create_material_set: material %d does not share the MLP / textures",
+                        m);
+    }
+    if (mats[0]->host.mlp.precision == BCF_FP32)
+        return fail(BCF_ERR_UNSUPPORTED, "bcf_create_material_set: FP32 materials use bcf_decode_material");
+    bcf_material_set set = new (std::nothrow) bcf_material_set_s;
+    if (!set)
+        return fail(BCF_ERR_OOM, "host allocation failed");
+    set->n = n;
+    set->first = mats[0]->host;
+    set->table = nullptr;
+    set->counter = nullptr;
+    set->cfg = {320, 3, 2};
+    MaterialDev *host = new (std::nothrow) MaterialDev[n];
+    if (!host) {
+        delete set;
+        return fail(BCF_ERR_OOM, "host allocation failed");
+    }
+    for (int m = 0; m < n; ++m)
+        host[m] = mats[m]->host;
+    cudaError_t e = cudaMalloc(&set->table, sizeof(MaterialDev) * n);
+    if (e == cudaSuccess)
+        e = cudaMalloc(&set->counter, sizeof(int));
+    if (e == cudaSuccess)
+        e = cudaMemcpy(set->table, host, sizeof(MaterialDev) * n, cudaMemcpyHostToDevice);
+    delete[] host;
+    if (e != cudaSuccess) {
+        cudaFree(set->table);
+        cudaFree(set->counter);
+        delete set;
+        return fail(BCF_ERR_OOM, "bcf_create_material_set: %s", cudaGetErrorString(e));
+    }
+    *out = set;
+    return BCF_OK;
+}
+
+bcf_status bcf_destroy_material_set(bcf_material_set set)
+{
+    if (!set)
+        return BCF_OK;
+    cudaError_t e = cudaFree(set->table);
+    cudaError_t e2 = cudaFree(set->counter);
+    delete set;
+    return cuda_status(e != cudaSuccess ? e : e2, "bcf_destroy_material_set");
+}
+
+static bcf_status check_set_args(bcf_material_set set, const int64_t *d_offsets, const float *d_u, const float *d_v,
+                                 const float *d_s, int64_t n, void *d_out, bcf_precision out_precision)
+{
+    if (!set || n < 0 || !d_offsets)
+        return fail(BCF_ERR_INVALID_ARG, "material set decode: null set / offsets or n < 0");
+    if (out_precision != BCF_FP32 && out_precision != BCF_FP16)
+        return fail(BCF_ERR_INVALID_ARG, "material set decode: out_precision must be FP32 or FP16");
+    if (n > 0 && (!d_u || !d_v || !d_out || !aligned(d_u, 4) || !aligned(d_v, 4) || !aligned(d_out, 16) ||
+                  (d_s && !aligned(d_s, 4)) || !aligned(d_offsets, 8)))
+        return fail(BCF_ERR_INVALID_ARG, "material set decode: null or misaligned pointer");
+    return BCF_OK;
+}
+
+bcf_status bcf_decode_material_set(bcf_material_set set, const int64_t *d_offsets, const float *d_u, const float *d_v,
+                                   const float *d_s, int64_t n_queries, void *d_out, bcf_precision out_precision,
+                                   bcf_stream stream)
+{
+    bcf_status st = check_set_args(set, d_offsets, d_u, d_v, d_s, n_queries, d_out, out_precision);
+    if (st != BCF_OK || n_queries == 0)
+        return st;
+    return cuda_status(launch_decode_set(set->first, set->table, set->n, d_offsets, d_u, d_v, d_s, n_queries, d_out,
+                                         out_precision == BCF_FP16, set->counter, set->cfg, (cudaStream_t)stream),
+                       "bcf_decode_material_set launch");
+}
+
+bcf_status bcf_material_set_config(bcf_material_set set, int32_t *cap, int32_t *ctas_per_sm, int32_t *chunk)
+{
+    if (!set)
+        return fail(BCF_ERR_INVALID_ARG, "bcf_material_set_config: null set");
+    if (cap)
+        *cap = set->cfg.cap;
+    if (ctas_per_sm)
+        *ctas_per_sm = set->cfg.ctas_per_sm;
+    if (chunk)
+        *chunk = set->cfg.chunk;
+    return BCF_OK;
+}
+
+bcf_status bcf_autotune_material_set(bcf_material_set set, const int64_t *d_offsets, const float *d_u,
+                                     const float *d_v, const float *d_s, int64_t n_queries, void *d_out,
+                                     bcf_precision out_precision, bcf_stream stream, int32_t *cap,
+                                     int32_t *ctas_per_sm, int32_t *chunk)
+{
+    bcf_status st = check_set_args(set, d_offsets, d_u, d_v, d_s, n_queries, d_out, out_precision);
+    if (st != BCF_OK)
+        return st;
+    cudaStream_t cs = (cudaStream_t)stream;
+    if (n_queries > 0) {
+        cudaEvent_t a = nullptr, b = nullptr;
+        cudaError_t e = cudaEventCreate(&a);
+        if (e == cudaSuccess)
+            e = cudaEventCreate(&b);
+        float best = 1e30f;
+        SetConfig best_cfg = set->cfg;
+        const int caps[2] = {256, 320}, ctas[3] = {1, 2, 3}, chunks[4] = {1, 2, 4, 8};
+        for (int ic = 0; e == cudaSuccess && ic < 2; ++ic)
+            for (int ir = 0; e == cudaSuccess && ir < 3; ++ir)
+                for (int ik = 0; e == cudaSuccess && ik < 4; ++ik) {
+                    const SetConfig cfg = {caps[ic], ctas[ir], chunks[ik]};
+                    float ms = 0.0f;
+                    for (int rep = 0; e == cudaSuccess && rep < 3; ++rep) { // first run warms up
+                        e = cudaEventRecord(a, cs);
+                        if (e == cudaSuccess)
+                            e = launch_decode_set(set->first, set->table, set->n, d_offsets, d_u, d_v, d_s, n_queries,
+                                                  d_out, out_precision == BCF_FP16, set->counter, cfg, cs);
+                        if (e == cudaSuccess)
+                            e = cudaEventRecord(b, cs);
+                        if (e == cudaSuccess)
+                            e = cudaEventSynchronize(b);
+                        float t = 0.0f;
+                        if (e == cudaSuccess)
+                            e = cudaEventElapsedTime(&t, a, b);
+                        if (rep > 0)
+                            ms += t;
+                    }
+                    if (e == cudaSuccess && ms < best) {
+                        best = ms;
+                        best_cfg = cfg;
+                    }
+                }
+        if (a)
+            cudaEventDestroy(a);
+        if (b)
+            cudaEventDestroy(b);
+        if (e != cudaSuccess)
+            return cuda_status(e, "bcf_autotune_material_set");
+        set->cfg = best_cfg;
+    }
+    return bcf_material_set_config(set, cap, ctas_per_sm, chunk);
+}
+
 } // extern "C"

@@ -35,6 +35,9 @@ constexpr int kTileQ = 256;    // queries per CTA tile, one per thread
 constexpr int kMaxLv = 3;      // mip levels per texture held per tile
 constexpr int kBoxes = BCF_MAX_TEX * kMaxLv;
 constexpr int kBins = 15;      // 14 modes + reserved
+#ifndef BCF_MAX_SET
+#define BCF_MAX_SET 256        // materials per material set
+#endif
 
 struct TileMeta {
     float u0, v0;
@@ -173,31 +176,58 @@ __host__ __device__ inline TiledLayout tiled_layout(const MlpDev &P, int cap, bo
     return L;
 }
 
-// K0 = 0: generic MLP (any layer count, shared-memory chaining); otherwise
-// the register-chained 3-layer MLP with padded widths K0 -> N1 -> N2 -> NO.
-template <int PREC, int CAP, int K0, int N1, int N2, int NO>
-__global__ void __launch_bounds__(kTileQ, 3) k_decode_tiled(MaterialDev M, const float *__restrict__ qu,
-                                                         const float *__restrict__ qv,
-                                                         const float *__restrict__ qs, int64_t n,
-                                                         void *__restrict__ out, int out_fp16)
+// Shared-memory pointers of one CTA (carved from the dynamic shared memory
+// by carve()).
+struct TileCtx {
+    TileMeta *TM;
+    uint4 *sraw;
+    uint16_t *sidx;
+    uint2 *arena;
+    unsigned char *sw;
+    float *sb;
+    unsigned char *act0, *act1, *tmp8;
+    float *ost;
+};
+
+template <int PREC>
+__device__ __forceinline__ TileCtx carve(unsigned char *smem, const MlpDev &P, int cap, bool generic)
 {
-    static_assert(CAP <= 2 * kTileQ, "blocks are held two per thread while sorting");
-    extern __shared__ __align__(16) unsigned char smem[];
-    const MlpDev &P = M.mlp;
-    const TiledLayout LY = tiled_layout<PREC>(P, CAP, K0 == 0);
-    unsigned char *sw = smem;
-    float *sb = (float *)(smem + LY.b_bytes);
-    TileMeta &TM = *(TileMeta *)(smem + LY.meta);
-    uint4 *sraw = (uint4 *)(smem + LY.sraw);
-    uint16_t *sidx = (uint16_t *)(smem + LY.sidx);
-    uint2 *arena = (uint2 *)(smem + LY.arena);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const TiledLayout LY = tiled_layout<PREC>(P, cap, generic);
+    TileCtx C;
+    C.sw = smem;
+    C.sb = (float *)(smem + LY.b_bytes);
+    C.TM = (TileMeta *)(smem + LY.meta);
+    C.sraw = (uint4 *)(smem + LY.sraw);
+    C.sidx = (uint16_t *)(smem + LY.sidx);
+    C.arena = (uint2 *)(smem + LY.arena);
+    const int warp = threadIdx.x >> 5;
     unsigned char *wbase = smem + LY.total - (kTileQ / 32 - warp) * LY.per_warp;
-    unsigned char *act0 = wbase + LY.act0;
-    unsigned char *act1 = wbase + LY.act1;
-    unsigned char *tmp8 = wbase + LY.tmp8;
-    float *ost = (float *)(wbase + LY.ost);
-    const int C = P.dims[P.n_layers];
+    C.act0 = wbase + LY.act0;
+    C.act1 = wbase + LY.act1;
+    C.tmp8 = wbase + LY.tmp8;
+    C.ost = (float *)(wbase + LY.ost);
+    return C;
+}
+
+// One tile of 256 queries [q_first, q_first + 256) clipped to q_end; this
+// thread's query is (u, v, s) (already sanitised; zeros when inactive).
+// Every thread of the CTA calls it (it synchronises the CTA).
+template <int PREC, int CAP, int K0, int N1, int N2, int NO>
+__device__ __forceinline__ void decode_tile(const MaterialDev &M, const TileCtx &C, int64_t q_first, int64_t q_end,
+                                            const float u, const float v, const float s, void *__restrict__ out,
+                                            int out_fp16)
+{
+    const MlpDev &P = M.mlp;
+    TileMeta &TM = *C.TM;
+    uint4 *sraw = C.sraw;
+    uint16_t *sidx = C.sidx;
+    uint2 *arena = C.arena;
+    unsigned char *sw = C.sw;
+    float *sb = C.sb;
+    unsigned char *act0 = C.act0, *act1 = C.act1, *tmp8 = C.tmp8;
+    float *ost = C.ost;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int Cn = P.dims[P.n_layers];
     const int row_stride = tile_stride_bytes<PREC>(P.kpad[0]);
     unsigned char *myrow = act0 + lane * row_stride;
     const float inv0 = PREC == BCF_FP8_E4M3 ? P.inv_act_scale[0] : 1.0f;
@@ -206,34 +236,8 @@ __global__ void __launch_bounds__(kTileQ, 3) k_decode_tiled(MaterialDev M, const
     const int wrap = M.wrap;
     const bool sgn = M.is_signed != 0;
     const unsigned lanes_lt = (1u << lane) - 1u;
-
-    load_mlp_smem<PREC>(P, sw, sb);
-
-    const int64_t tiles = (n + kTileQ - 1) / kTileQ;
-    // queries of the next tile are loaded one tile ahead
-    float nu = 0.0f, nv = 0.0f, ns = 0.0f;
-    {
-        const int64_t q = (int64_t)blockIdx.x * kTileQ + threadIdx.x;
-        if (blockIdx.x < tiles && q < n) {
-            nu = qu[q];
-            nv = qv[q];
-            ns = qs ? qs[q] : 0.0f;
-        }
-    }
-    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
-        const int64_t q = tile * kTileQ + threadIdx.x;
-        const bool active = q < n;
-        const float u = active ? sanitize(nu, wrap) : 0.0f;
-        const float v = active ? sanitize(nv, wrap) : 0.0f;
-        const float s = active ? ns : 0.0f;
-        {
-            const int64_t qn = (tile + gridDim.x) * kTileQ + threadIdx.x;
-            if (tile + gridDim.x < tiles && qn < n) {
-                nu = qu[qn];
-                nv = qv[qn];
-                ns = qs ? qs[qn] : 0.0f;
-            }
-        }
+    const int64_t q = q_first + threadIdx.x;
+    const bool active = q < q_end;
         // ---- reset the tile metadata
         if (threadIdx.x == 0) {
             TM.u0 = u;
@@ -525,23 +529,141 @@ __global__ void __launch_bounds__(kTileQ, 3) k_decode_tiled(MaterialDev M, const
             warp_mlp<PREC>(P, sw, sb, act0, act1, ost);
         else
             warp_mlp3<PREC, K0, N1, N2, NO>(P, sw, sb, act0, row_stride, tmp8,
-                                            tile_stride_bytes<BCF_FP8_E4M3>(N1 > N2 ? N1 : N2), ost, C);
+                                            tile_stride_bytes<BCF_FP8_E4M3>(N1 > N2 ? N1 : N2), ost, Cn);
         __syncwarp();
-        const int64_t q0 = tile * kTileQ + warp * 32;
-        if (q0 < n) {
-            const int rows = (int)min((int64_t)32, n - q0);
-            const int tot = rows * C;
+        const int64_t q0 = q_first + warp * 32;
+        if (q0 < q_end) {
+            const int rows = (int)min((int64_t)32, q_end - q0);
+            const int tot = rows * Cn;
             if (out_fp16) {
-                __half *o = (__half *)out + q0 * C;
+                __half *o = (__half *)out + q0 * Cn;
                 for (int i = lane; i < tot; i += 32)
                     o[i] = __float2half_rn(ost[i]);
             } else {
-                float *o = (float *)out + q0 * C;
+                float *o = (float *)out + q0 * Cn;
                 for (int i = lane; i < tot; i += 32)
                     o[i] = ost[i];
             }
         }
         __syncwarp();
+}
+
+// Single material: the material is a kernel parameter; tiles are assigned
+// round-robin to the persistent CTAs, queries are loaded one tile ahead.
+template <int PREC, int CAP, int K0, int N1, int N2, int NO>
+__global__ void __launch_bounds__(kTileQ, 3) k_decode_tiled(MaterialDev M, const float *__restrict__ qu,
+                                                            const float *__restrict__ qv,
+                                                            const float *__restrict__ qs, int64_t n,
+                                                            void *__restrict__ out, int out_fp16)
+{
+    static_assert(CAP <= 2 * kTileQ, "blocks are held two per thread while sorting");
+    extern __shared__ __align__(16) unsigned char smem[];
+    const TileCtx C = carve<PREC>(smem, M.mlp, CAP, K0 == 0);
+    const int wrap = M.wrap;
+    load_mlp_smem<PREC>(M.mlp, C.sw, C.sb);
+    const int64_t tiles = (n + kTileQ - 1) / kTileQ;
+    float nu = 0.0f, nv = 0.0f, ns = 0.0f;
+    {
+        const int64_t q = (int64_t)blockIdx.x * kTileQ + threadIdx.x;
+        if (blockIdx.x < tiles && q < n) {
+            nu = qu[q];
+            nv = qv[q];
+            ns = qs ? qs[q] : 0.0f;
+        }
+    }
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int64_t q = tile * kTileQ + threadIdx.x;
+        const bool active = q < n;
+        const float u = active ? sanitize(nu, wrap) : 0.0f;
+        const float v = active ? sanitize(nv, wrap) : 0.0f;
+        const float s = active ? ns : 0.0f;
+        {
+            const int64_t qn = (tile + gridDim.x) * kTileQ + threadIdx.x;
+            if (tile + gridDim.x < tiles && qn < n) {
+                nu = qu[qn];
+                nv = qv[qn];
+                ns = qs ? qs[qn] : 0.0f;
+            }
+        }
+        decode_tile<PREC, CAP, K0, N1, N2, NO>(M, C, tile * kTileQ, n, u, v, s, out, out_fp16);
+    }
+}
+
+// Material set: materials in a device table, material m's queries are
+// [offsets[m], offsets[m+1]) of the concatenated arrays.  Tiles are numbered
+// material by material; CTAs take `chunk` consecutive tiles at a time from an
+// atomic work counter (zeroed before the launch) and reload the material's
+// metadata and MLP weights into shared memory when a tile belongs to a new
+// material.  Offsets are clipped to [0, n], so malformed ranges cannot
+// address outside the query and output arrays.
+template <int PREC, int CAP, int K0, int N1, int N2, int NO>
+__global__ void __launch_bounds__(kTileQ, 3) k_decode_set(const MaterialDev *__restrict__ mats, int nmat,
+                                                          const int64_t *__restrict__ offsets, const float *__restrict__ qu,
+                                                          const float *__restrict__ qv, const float *__restrict__ qs,
+                                                          int64_t n, void *__restrict__ out, int out_fp16,
+                                                          int *__restrict__ counter, int chunk)
+{
+    static_assert(CAP <= 2 * kTileQ, "blocks are held two per thread while sorting");
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ MaterialDev Ms;
+    __shared__ int64_t tile_first[BCF_MAX_SET + 1];
+    __shared__ int grab;
+    // every material shares the MLP shape (checked when the set is created), so the layout is that of material 0
+    const TileCtx C = carve<PREC>(smem, mats[0].mlp, CAP, K0 == 0);
+    if (threadIdx.x == 0) {
+        int64_t acc = 0;
+        for (int m = 0; m < nmat; ++m) {
+            tile_first[m] = acc;
+            const int64_t a = min(max(offsets[m], (int64_t)0), n), b = min(max(offsets[m + 1], (int64_t)0), n);
+            acc += b > a ? (b - a + kTileQ - 1) / kTileQ : 0;
+        }
+        tile_first[nmat] = acc;
+    }
+    __syncthreads();
+    const int64_t total = tile_first[nmat];
+    int cur = -1;
+    for (;;) {
+        if (threadIdx.x == 0)
+            grab = atomicAdd(counter, chunk);
+        __syncthreads();
+        const int64_t base = grab;
+        __syncthreads(); // everyone has read `grab` before thread 0 may overwrite it
+        if (base >= total)
+            break;
+        for (int j = 0; j < chunk && base + j < total; ++j) {
+            const int64_t tile = base + j;
+            int lo = 0, hi = nmat - 1; // last m with tile_first[m] <= tile
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (tile_first[mid] <= tile)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            const int m = lo;
+            if (m != cur) {
+                __syncthreads(); // the previous tile's MLP may still read the weights being replaced
+                const int words = (int)(sizeof(MaterialDev) / 4);
+                for (int i = threadIdx.x; i < words; i += kTileQ)
+                    reinterpret_cast<int *>(&Ms)[i] = reinterpret_cast<const int *>(mats + m)[i];
+                __syncthreads();
+                load_mlp_smem<PREC>(Ms.mlp, C.sw, C.sb);
+                cur = m;
+                // (the first __syncthreads of decode_tile orders the loads before their use)
+            }
+            const int64_t a = min(max(offsets[m], (int64_t)0), n), b = min(max(offsets[m + 1], (int64_t)0), n);
+            const int64_t q0 = a + (tile - tile_first[m]) * kTileQ;
+            const int64_t q = q0 + threadIdx.x;
+            const bool active = q < b;
+            const int wrap = Ms.wrap;
+            float u = 0.0f, v = 0.0f, s = 0.0f;
+            if (active) {
+                u = sanitize(qu[q], wrap);
+                v = sanitize(qv[q], wrap);
+                s = qs ? qs[q] : 0.0f;
+            }
+            decode_tile<PREC, CAP, K0, N1, N2, NO>(Ms, C, q0, b, u, v, s, out, out_fp16);
+        }
     }
 }
 
@@ -608,6 +730,73 @@ cudaError_t launch_decode_tiled(const MaterialDev &M, const float *u, const floa
     case BCF_FP16: return launch_tiled_prec<BCF_FP16>(M, u, v, s, n, out, out_fp16, st);
     case BCF_BF16: return launch_tiled_prec<BCF_BF16>(M, u, v, s, n, out, out_fp16, st);
     case BCF_FP8_E4M3: return launch_tiled_prec<BCF_FP8_E4M3>(M, u, v, s, n, out, out_fp16, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+// ------------------------------------------------------ material sets
+
+template <int PREC, int CAP, int K0, int N1, int N2, int NO>
+static cudaError_t launch_set_shape(const MaterialDev &M0, const MaterialDev *mats, int nmat, const int64_t *offsets,
+                                    const float *u, const float *v, const float *s, int64_t n, void *out,
+                                    int out_fp16, int *counter, const SetConfig &cfg, cudaStream_t st)
+{
+    const int64_t smem = tiled_layout<PREC>(M0.mlp, CAP, K0 == 0).total;
+    if (smem > 200 * 1024)
+        return cudaErrorInvalidConfiguration;
+    auto kern = k_decode_set<PREC, CAP, K0, N1, N2, NO>;
+    static int configured = 0;
+    if (!configured) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        configured = 1;
+    }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTileQ, (size_t)smem);
+    per_sm = max(1, min(per_sm, cfg.ctas_per_sm));
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+    if (e != cudaSuccess)
+        return e;
+    kern<<<(unsigned)(tiled_sms() * per_sm), kTileQ, (size_t)smem, st>>>(mats, nmat, offsets, u, v, s, n, out,
+                                                                           out_fp16, counter, max(cfg.chunk, 1));
+    return cudaGetLastError();
+}
+
+template <int PREC, int CAP>
+static cudaError_t launch_set_cap(const MaterialDev &M0, const MaterialDev *mats, int nmat, const int64_t *offsets,
+                                  const float *u, const float *v, const float *s, int64_t n, void *out, int out_fp16,
+                                  int *counter, const SetConfig &cfg, cudaStream_t st)
+{
+    const MlpDev &P = M0.mlp;
+    if (P.n_layers == 3) {
+        const int k0 = P.kpad[0], n1 = P.npad[0], n2 = P.npad[1], no = P.npad[2];
+        constexpr int kq = PREC == BCF_FP8_E4M3 ? 32 : 16;
+        if (k0 == kq && n1 == 32 && n2 == 32 && no == 16)
+            return launch_set_shape<PREC, CAP, kq, 32, 32, 16>(M0, mats, nmat, offsets, u, v, s, n, out, out_fp16,
+                                                                counter, cfg, st);
+    }
+    return launch_set_shape<PREC, CAP, 0, 0, 0, 0>(M0, mats, nmat, offsets, u, v, s, n, out, out_fp16, counter, cfg,
+                                                   st);
+}
+
+template <int PREC>
+static cudaError_t launch_set_prec(const MaterialDev &M0, const MaterialDev *mats, int nmat, const int64_t *offsets,
+                                   const float *u, const float *v, const float *s, int64_t n, void *out, int out_fp16,
+                                   int *counter, const SetConfig &cfg, cudaStream_t st)
+{
+    if (cfg.cap == 256)
+        return launch_set_cap<PREC, 256>(M0, mats, nmat, offsets, u, v, s, n, out, out_fp16, counter, cfg, st);
+    return launch_set_cap<PREC, 320>(M0, mats, nmat, offsets, u, v, s, n, out, out_fp16, counter, cfg, st);
+}
+
+cudaError_t launch_decode_set(const MaterialDev &M0, const MaterialDev *mats, int nmat, const int64_t *offsets,
+                              const float *u, const float *v, const float *s, int64_t n, void *out, int out_fp16,
+                              int *counter, const SetConfig &cfg, cudaStream_t st)
+{
+    switch (M0.mlp.precision) {
+    case BCF_FP16: return launch_set_prec<BCF_FP16>(M0, mats, nmat, offsets, u, v, s, n, out, out_fp16, counter, cfg, st);
+    case BCF_BF16: return launch_set_prec<BCF_BF16>(M0, mats, nmat, offsets, u, v, s, n, out, out_fp16, counter, cfg, st);
+    case BCF_FP8_E4M3:
+        return launch_set_prec<BCF_FP8_E4M3>(M0, mats, nmat, offsets, u, v, s, n, out, out_fp16, counter, cfg, st);
     default: return cudaErrorInvalidValue;
     }
 }

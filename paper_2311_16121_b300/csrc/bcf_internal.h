@@ -54,6 +54,10 @@ struct MaterialDev {
 
 } // namespace bcf
 
+#ifndef BCF_MAX_SET
+#define BCF_MAX_SET 256 // materials per material set
+#endif
+
 struct bcf_material_s {
     bcf::MaterialDev host;   // host copy (passed by value to single-material kernels)
     bcf::MaterialDev *dev;   // device copy (batched kernels)

@@ -18,6 +18,16 @@ int64_t decode_mma_smem_bytes(const MlpDev &P);
 cudaError_t launch_decode_tiled(const MaterialDev &M, const float *u, const float *v, const float *s, int64_t n,
                                 void *out, int out_fp16, cudaStream_t st);
 int64_t decode_tiled_smem_bytes(const MlpDev &P);
+
+// Launch configuration of a material-set decode (picked by the autotuner).
+struct SetConfig {
+    int cap;          // shared-memory block arena (256 or 320 blocks)
+    int ctas_per_sm;  // persistent CTAs per SM (capped by occupancy)
+    int chunk;        // consecutive tiles taken per work-counter grab
+};
+cudaError_t launch_decode_set(const MaterialDev &M0, const MaterialDev *mats, int nmat, const int64_t *offsets,
+                              const float *u, const float *v, const float *s, int64_t n, void *out, int out_fp16,
+                              int *counter, const SetConfig &cfg, cudaStream_t st);
 cudaError_t texunit_decode(const void *d_blocks, int bw, int bh, int is_signed, uint16_t *d_out, cudaStream_t st);
 
 // thread-local error text

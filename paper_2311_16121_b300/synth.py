@@ -271,34 +271,31 @@ def plane_queries(rng: np.random.Generator, width: int, height: int, res_ref: in
     yaw = rng.uniform(0.0, 2 * math.pi)
     tan_half = math.tan(math.radians(30.0))
     aspect = W / H
-    ys, xs = np.meshgrid(np.arange(y0, y0 + h, dtype=np.float64), np.arange(x0, x0 + w, dtype=np.float64),
-                         indexing="ij")
-    jx = rng.uniform(-0.5, 0.5, xs.shape)
-    jy = rng.uniform(-0.5, 0.5, ys.shape)
-    px, py = xs + 0.5 + jx, ys + 0.5 + jy
     # camera basis: forward tilted down by `pitch`, rotated by `yaw` about z
     cf, sf = math.cos(pitch), math.sin(pitch)
     cy, sy = math.cos(yaw), math.sin(yaw)
     fwd = np.array([cf * cy, cf * sy, -sf])
     right = np.array([sy, -cy, 0.0])
     up = np.cross(right, fwd)
-
-    def hit(px, py):
-        nx = (2.0 * px / W - 1.0) * tan_half * aspect
-        ny = (1.0 - 2.0 * py / H) * tan_half
-        d = fwd[:, None, None] + nx[None] * right[:, None, None] + ny[None] * up[:, None, None]
-        t = 1.0 / -d[2]
-        return d[0] * t * uv_scale, d[1] * t * uv_scale
-
-    u, v = hit(px, py)
-    e = 1e-3
-    ux1, vx1 = hit(px + e, py)
-    ux0, vx0 = hit(px - e, py)
-    uy1, vy1 = hit(px, py + e)
-    uy0, vy0 = hit(px, py - e)
-    dx = np.hypot((ux1 - ux0) / (2 * e), (vx1 - vx0) / (2 * e))
-    dy = np.hypot((uy1 - uy0) / (2 * e), (vy1 - vy0) / (2 * e))
-    s = np.log2(np.maximum(dx, dy) * res_ref)
+    px = np.arange(x0, x0 + w, dtype=np.float64)[None, :] + 0.5 + rng.uniform(-0.5, 0.5, (h, w))
+    py = np.arange(y0, y0 + h, dtype=np.float64)[:, None] + 0.5 + rng.uniform(-0.5, 0.5, (h, w))
+    # ray d = fwd + nx right + ny up hits z = 0 from height 1 at t = -1 / d_z: world = t (d_x, d_y)
+    ax, ay = 2.0 * tan_half * aspect / W, -2.0 * tan_half / H  # d nx / d px, d ny / d py
+    nx = px * ax - tan_half * aspect
+    ny = py * ay + tan_half
+    dx_ = fwd[0] + nx * right[0] + ny * up[0]
+    dy_ = fwd[1] + nx * right[1] + ny * up[1]
+    dz_ = fwd[2] + nx * right[2] + ny * up[2]
+    t = -1.0 / dz_
+    u = dx_ * t * uv_scale
+    v = dy_ * t * uv_scale
+    # exact screen Jacobian of (u, v) = uv_scale * (d_x, d_y) / (-d_z)
+    def grad(e):  # e: direction derivative per pixel step (3-vector)
+        dt = t * t * e[2]
+        return uv_scale * (dt * dx_ + t * e[0]), uv_scale * (dt * dy_ + t * e[1])
+    gux, gvx = grad(right * ax)
+    guy, gvy = grad(up * ay)
+    s = np.log2(np.maximum(np.hypot(gux, gvx), np.hypot(guy, gvy)) * res_ref)
     s = np.maximum(s, 0.0)
     u = u - np.floor(u)
     v = v - np.floor(v)

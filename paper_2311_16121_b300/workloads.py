@@ -90,6 +90,54 @@ def config2() -> DecodeWorkload:
     return screen_material(2, 4, 2048, [13, 32, 32, 9], 3840, 2160)
 
 
+@dataclass
+class SetWorkload:
+    """Several materials and their concatenated queries (material m: rows offsets[m]..offsets[m+1])."""
+    name: str
+    materials: list[DecodeWorkload]   # each with its own queries in u, v, s
+    offsets: np.ndarray               # int64 [n + 1]
+
+    @property
+    def n(self) -> int:
+        return int(self.offsets[-1])
+
+    def concat(self):
+        u = np.concatenate([m.u for m in self.materials])
+        v = np.concatenate([m.v for m in self.materials])
+        s = np.concatenate([m.s for m in self.materials])
+        return u, v, s
+
+
+def config4(n_materials: int = 64, q_range=(1e4, 4e6), res_choices=(256, 512, 1024, 2048, 4096),
+            dims=(13, 32, 32, 9), pool: int = 1 << 20, config: int = 4) -> SetWorkload:
+    """64 materials: resolution uniform over res_choices (4 value-bounded BC6H textures each, full mips),
+    query count log-uniform in q_range, each material's queries a contiguous 16:9 patch of the
+    perspective-plane screen generator (res_ref = the material's resolution), own MLP weights."""
+    rng = seed_rng(config, 0)
+    pool_blocks = synth.bounded_blocks(rng, pool)
+    mats = []
+    offsets = [0]
+    rq = seed_rng(config, 1)
+    rw = seed_rng(config, 2)
+    for m in range(n_materials):
+        res = int(rng.choice(np.asarray(res_choices)))
+        levels = synth.full_levels(res)
+        nb = sum(synth.level_blocks(res, levels))
+        blocks = [pool_blocks[rng.integers(0, pool, nb)] for _ in range(4)]
+        nq = int(np.floor(np.exp(rng.uniform(np.log(q_range[0]), np.log(q_range[1])))))
+        w = int(np.ceil(np.sqrt(nq * 16 / 9)))
+        h = int(np.ceil(nq / w))
+        x0 = int(rq.integers(0, max(1, 3840 - w)))
+        y0 = int(rq.integers(0, max(1, 2160 - h)))
+        u, v, s = synth.plane_queries(rq, 3840, 2160, res_ref=res, x0=x0, y0=y0, w=w, h=h)
+        u, v, s = u[:nq], v[:nq], s[:nq]
+        W, b = synth.mlp_weights(rw, list(dims))
+        mats.append(DecodeWorkload(f"material{m}-{res}", [res] * 4, [levels] * 4, res, blocks, True, list(dims), W, b,
+                                   u, v, s, input_bound=max(1.0, float(s.max()))))
+        offsets.append(offsets[-1] + nq)
+    return SetWorkload(f"config{config}-{n_materials}-materials", mats, np.asarray(offsets, np.int64))
+
+
 def config5() -> DecodeWorkload:
     return screen_material(5, 8, 4096, [25, 64, 64, 9], 3840, 2160, supersample=2, pool=1 << 20)
 

@@ -1,0 +1,105 @@
+"""Batched multi-material decode (bcf_decode_material_set): one persistent
+launch over many materials of different resolutions and query counts."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2311_16121_b300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def _bcf():
+    import paper_2311_16121_b300 as bcf
+
+    bcf.lib()
+    return bcf
+
+
+def _small_set(precision="fp16", n_materials=7, seed_config=41):
+    sw = workloads.config4(n_materials=n_materials, q_range=(300, 6000), res_choices=(32, 64, 128, 256),
+                           pool=1 << 14, config=seed_config)
+    mats = [workloads.upload(m, precision) for m in sw.materials]
+    return sw, mats
+
+
+def _set_inputs(sw):
+    u, v, s = (torch.from_numpy(a).cuda() for a in sw.concat())
+    off = torch.from_numpy(sw.offsets).cuda()
+    return off, u, v, s
+
+
+@pytest.mark.parametrize("precision", ["fp16", "fp8"])
+def test_set_decode_equals_per_material_decodes(precision):
+    bcf = _bcf()
+    sw, mats = _small_set(precision)
+    S = bcf.MaterialSet(mats)
+    off, u, v, s = _set_inputs(sw)
+    got = S.decode(off, u, v, s).cpu().numpy()
+    for m, w in enumerate(sw.materials):
+        a, b = int(sw.offsets[m]), int(sw.offsets[m + 1])
+        one = mats[m].decode(u[a:b], v[a:b], s[a:b], out_dtype=torch.float16).cpu().numpy()
+        np.testing.assert_array_equal(got[a:b], one)
+
+
+def test_set_decode_matches_oracle():
+    bcf = _bcf()
+    sw, mats = _small_set("fp16", n_materials=3, seed_config=43)
+    S = bcf.MaterialSet(mats)
+    off, u, v, s = _set_inputs(sw)
+    got = S.decode(off, u, v, s, out_dtype=torch.float32).cpu().numpy().astype(np.float64)
+    for m, w in enumerate(sw.materials):
+        a, b = int(sw.offsets[m]), int(sw.offsets[m + 1])
+        Wst, bias, _, _ = w.weights("fp16")
+        ref = oracle.decode(oracle.Material(w.blocks, w.res, w.levels, w.res_ref, False, True, True),
+                            oracle.Mlp(w.dims, "fp16", Wst, bias), w.u, w.v, w.s, quant_aware=True, threads=8)
+        err = np.abs(got[a:b] - ref)
+        assert (err > 1e-3).mean() <= 1e-3 and err.max() <= 8e-3, (m, err.max())
+
+
+def test_set_decode_in_a_cuda_graph_and_autotune():
+    bcf = _bcf()
+    sw, mats = _small_set("fp16", seed_config=44)
+    S = bcf.MaterialSet(mats)
+    off, u, v, s = _set_inputs(sw)
+    ref = S.decode(off, u, v, s).clone()
+    cfg = S.autotune(off, u, v, s, torch.empty_like(ref))
+    assert cfg[0] in (256, 320) and 1 <= cfg[1] <= 3 and cfg[2] in (1, 2, 4, 8)
+    assert S.config() == cfg
+    out = torch.zeros_like(ref)
+    stream = torch.cuda.Stream()
+    stream.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(stream):
+        S.decode(off, u, v, s, out=out)  # warm-up outside the capture
+    torch.cuda.current_stream().wait_stream(stream)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        S.decode(off, u, v, s, out=out)
+    for _ in range(2):  # the work counter is reset inside the graph: replays are repeatable
+        out.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        torch.testing.assert_close(out, ref, rtol=0, atol=0)
+
+
+def test_set_decode_empty_and_clipped_ranges():
+    bcf = _bcf()
+    sw, mats = _small_set("fp16", n_materials=4, seed_config=45)
+    S = bcf.MaterialSet(mats)
+    _, u, v, s = _set_inputs(sw)
+    n = u.numel()
+    # material 1 has no queries; the last offset runs past the end (clipped to n)
+    offs = sw.offsets.copy()
+    offs[2] = offs[1]
+    offs[-1] = n + 1000
+    got = S.decode(torch.from_numpy(offs).cuda(), u, v, s).cpu().numpy()
+    for m in (0, 2, 3):
+        a, b = int(offs[m]), min(int(offs[m + 1]), n)
+        one = mats[m].decode(u[a:b], v[a:b], s[a:b], out_dtype=torch.float16).cpu().numpy()
+        np.testing.assert_array_equal(got[a:b], one)
+    # sets reject mixed MLP shapes
+    w2 = workloads.small_screen(res=32, width=8, height=8, dims=(13, 16, 16, 9))
+    other = workloads.upload(w2, "fp16")
+    with pytest.raises(bcf.BcfError):
+        bcf.MaterialSet([mats[0], other])
