@@ -298,6 +298,10 @@ __device__ __forceinline__ void bc6h_header(const Bc6hBlock &blk, bool sgn, Bc6h
         H.e[0][c] = unquantize(base, epb, sgn);
 #pragma unroll
         for (int i = 1; i < 4; ++i) {
+            if (i >= 2 && !two) {
+                H.e[i][c] = 0;
+                continue;
+            }
             int v = raw[i][c];
             if (sgn || xf)
                 v = sext(v, xf ? dbits[c] : epb);
@@ -408,13 +412,15 @@ __device__ __forceinline__ void bc6h_all_texels(const Bc6hBlock &blk, const Bc6h
 
 namespace bcf {
 
-// Texels 8 * half .. 8 * half + 7 of a decoded block (as bc6h_all_texels).
-// Each region's channels are kept as (64 a + 32, b - a), so a texel channel
-// is (64 a + 32 + (b - a) w) >> 6 -- the same integer as
-// (a (64 - w) + b w + 32) >> 6.  Reserved modes have all endpoints zero,
-// which decodes to zero texels.
+// Texels [t0, t0 + nt) of a decoded block (t0 + nt <= 16), as
+// bc6h_all_texels.  The index stream is entered at texel t0: the indices of
+// texels 0 .. t0-1 occupy q t0 bits, minus one for texel 0 and one for the
+// second anchor when it lies among them.  Each region's channels are kept as
+// (64 a + 32, b - a), so a texel channel is (64 a + 32 + (b - a) w) >> 6 --
+// the same integer as (a (64 - w) + b w + 32) >> 6.  Reserved modes have all
+// endpoints zero, which decodes to zero texels.
 template <class Store>
-__device__ __forceinline__ void bc6h_half_texels(const Bc6hBlock &blk, const Bc6hHeader &H, bool sgn, int half,
+__device__ __forceinline__ void bc6h_texel_range(const Bc6hBlock &blk, const Bc6hHeader &H, bool sgn, int t0, int nt,
                                                  Store store)
 {
     uint64_t idx;
@@ -423,10 +429,9 @@ __device__ __forceinline__ void bc6h_half_texels(const Bc6hBlock &blk, const Bc6
     if (H.two) {
         pmask = partition_mask(H.partition);
         a2 = anchor2_of(H.partition);
-        // texels 0..7 hold 24 index bits minus one for texel 0 and one if the second anchor is among them
-        idx = blk.hi >> (18 + (half ? 23 - (a2 < 8) : 0));
+        idx = blk.hi >> (18 + 3 * t0 - (t0 > 0) - (a2 < t0));
     } else {
-        idx = blk.hi >> (1 + (half ? 31 : 0));
+        idx = blk.hi >> (1 + 4 * t0 - (t0 > 0));
     }
     int base0[3], del0[3], base1[3], del1[3];
 #pragma unroll
@@ -436,10 +441,8 @@ __device__ __forceinline__ void bc6h_half_texels(const Bc6hBlock &blk, const Bc6
         base1[c] = 64 * H.e[2][c] + 32;
         del1[c] = H.e[3][c] - H.e[2][c];
     }
-    const int t0 = 8 * half;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const int t = t0 + j;
+#pragma unroll 1
+    for (int t = t0; t < t0 + nt; ++t) {
         int w;
         if (H.two) {
             const int nb = (t == 0 || t == a2) ? 2 : 3;
@@ -455,6 +458,84 @@ __device__ __forceinline__ void bc6h_half_texels(const Bc6hBlock &blk, const Bc6
         const uint32_t g = finish(((r1 ? base1[1] : base0[1]) + (r1 ? del1[1] : del0[1]) * w) >> 6, sgn);
         const uint32_t b = finish(((r1 ? base1[2] : base0[2]) + (r1 ? del1[2] : del0[2]) * w) >> 6, sgn);
         store(t, r | (g << 16), b);
+    }
+}
+
+} // namespace bcf
+
+namespace bcf {
+
+// Per-block texel stage: the index stream normalised to a fixed field per
+// texel (the anchors' implicit zero bit inserted), the region mask, and each
+// region's channels as (64 a + 32, b - a).
+struct Bc6hTexels {
+    uint64_t stream; // index of texel t in bits [q t, q t + q)
+    uint32_t pmask;  // region of texel t in bit t
+    int q;           // 3 (two regions) or 4 (one region)
+    int base[2][3], del[2][3];
+};
+
+__device__ __forceinline__ void bc6h_prepare_texels(const Bc6hBlock &blk, const Bc6hHeader &H, Bc6hTexels &X)
+{
+    if (H.two) {
+        const uint64_t raw = blk.hi >> 18;                 // 46 index bits from bit 82
+        const uint64_t s1 = ((raw >> 2) << 3) | (raw & 3); // texel 0: 2 stored bits -> a 3-bit field
+        const int p = 3 * anchor2_of(H.partition) + 2;     // top bit of the second anchor's field
+        X.stream = ((s1 >> p) << (p + 1)) | (s1 & ((1ull << p) - 1));
+        X.pmask = partition_mask(H.partition);
+        X.q = 3;
+    } else {
+        const uint64_t raw = blk.hi >> 1;                  // 63 index bits from bit 65
+        X.stream = ((raw >> 3) << 4) | (raw & 7);          // texel 0: 3 stored bits -> a 4-bit field
+        X.pmask = 0;
+        X.q = 4;
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        X.base[0][c] = 64 * H.e[0][c] + 32;
+        X.del[0][c] = H.e[1][c] - H.e[0][c];
+        X.base[1][c] = 64 * H.e[2][c] + 32;
+        X.del[1][c] = H.e[3][c] - H.e[2][c];
+    }
+}
+
+// Texels t0 .. t0 + N - 1.  Weights: round(64 i / 7) = (146 i + 8) >> 4 for
+// 3-bit indices and round(64 i / 15) = (273 i + 32) >> 6 for 4-bit indices
+// (exact over the index ranges).  Unsigned scaling by 31/64 as one high
+// multiply: (v 31) >> 6 = umulhi(v, 31 << 26) for 0 <= v < 2^16.
+template <int N, int Q, bool SGN, class Store>
+__device__ __forceinline__ void bc6h_texels_n(const Bc6hTexels &X, int t0, Store store)
+{
+    const uint64_t s = X.stream >> (Q * t0);
+    const uint32_t pm = X.pmask >> t0;
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        const int i = (int)(s >> (Q * j)) & ((1 << Q) - 1);
+        const int w = Q == 3 ? (146 * i + 8) >> 4 : (273 * i + 32) >> 6;
+        const bool r1 = Q == 3 && ((pm >> j) & 1);
+        uint32_t ch[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const int v = ((r1 ? X.base[1][c] : X.base[0][c]) + (r1 ? X.del[1][c] : X.del[0][c]) * w) >> 6;
+            ch[c] = SGN ? finish(v, true) : __umulhi((uint32_t)v, 31u << 26);
+        }
+        store(t0 + j, ch[0] | (ch[1] << 16), ch[2]);
+    }
+}
+
+template <int N, class Store>
+__device__ __forceinline__ void bc6h_texels(const Bc6hTexels &X, bool sgn, int t0, Store store)
+{
+    if (sgn) {
+        if (X.q == 3)
+            bc6h_texels_n<N, 3, true>(X, t0, store);
+        else
+            bc6h_texels_n<N, 4, true>(X, t0, store);
+    } else {
+        if (X.q == 3)
+            bc6h_texels_n<N, 3, false>(X, t0, store);
+        else
+            bc6h_texels_n<N, 4, false>(X, t0, store);
     }
 }
 

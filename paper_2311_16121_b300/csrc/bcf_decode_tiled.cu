@@ -53,8 +53,7 @@ struct TileMeta {
     int tbase[BCF_MAX_TEX];    // per texture: first arena block of its block set within its round
     int rtex[BCF_MAX_TEX + 1]; // textures [rtex[r], rtex[r+1]) form round r
     int rtotal[BCF_MAX_TEX];   // blocks of round r
-    int hist[16];
-    int offs[16];
+    int hist[16];              // blocks per mode bin of the current round
 };
 
 // LOD of texture T for query LOD s: level floor(s_t), whether floor(s_t) + 1
@@ -136,7 +135,7 @@ __host__ __device__ inline TiledLayout tiled_layout(const MlpDev &P, int cap, bo
     L.b_bytes = off;
     off += (mlp_smem_bias_floats(P) * 4 + 15) & ~15;
     L.meta = off;
-    off += (int)((sizeof(TileMeta) + 15) & ~15);
+    off += (int)((2 * sizeof(TileMeta) + 15) & ~15); // double-buffered across tiles
     L.sraw = off;
     off += cap * 16;
     L.sidx = off;
@@ -179,7 +178,8 @@ __host__ __device__ inline TiledLayout tiled_layout(const MlpDev &P, int cap, bo
 // Shared-memory pointers of one CTA (carved from the dynamic shared memory
 // by carve()).
 struct TileCtx {
-    TileMeta *TM;
+    TileMeta *TM;      // this tile's metadata
+    TileMeta *TMnext;  // the other buffer (the next tile's)
     uint4 *sraw;
     uint16_t *sidx;
     uint2 *arena;
@@ -197,6 +197,7 @@ __device__ __forceinline__ TileCtx carve(unsigned char *smem, const MlpDev &P, i
     C.sw = smem;
     C.sb = (float *)(smem + LY.b_bytes);
     C.TM = (TileMeta *)(smem + LY.meta);
+    C.TMnext = C.TM + 1;
     C.sraw = (uint4 *)(smem + LY.sraw);
     C.sidx = (uint16_t *)(smem + LY.sidx);
     C.arena = (uint2 *)(smem + LY.arena);
@@ -207,6 +208,28 @@ __device__ __forceinline__ TileCtx carve(unsigned char *smem, const MlpDev &P, i
     C.tmp8 = wbase + LY.tmp8;
     C.ost = (float *)(wbase + LY.ost);
     return C;
+}
+
+// Reset the fields a tile accumulates into (LOD range, boxes, mode histogram).
+__device__ __forceinline__ void reset_tile_meta(TileMeta &T)
+{
+    if (threadIdx.x == 0) {
+        T.smin_bits = INT_MAX;
+        T.smax_bits = INT_MIN;
+    }
+    if (threadIdx.x < 16)
+        T.hist[threadIdx.x] = 0;
+    for (int i = threadIdx.x; i < kBoxes; i += kTileQ) {
+        T.bb[i][0] = T.bb[i][2] = INT_MAX;
+        T.bb[i][1] = T.bb[i][3] = INT_MIN;
+    }
+}
+
+__device__ __forceinline__ void swap_meta(TileCtx &C)
+{
+    TileMeta *t = C.TM;
+    C.TM = C.TMnext;
+    C.TMnext = t;
 }
 
 // One tile of 256 queries [q_first, q_first + 256) clipped to q_end; this
@@ -238,18 +261,13 @@ __device__ __forceinline__ void decode_tile(const MaterialDev &M, const TileCtx 
     const unsigned lanes_lt = (1u << lane) - 1u;
     const int64_t q = q_first + threadIdx.x;
     const bool active = q < q_end;
-        // ---- reset the tile metadata
+        // ---- this tile's metadata was reset during the previous tile (or before the first); reset the other
+        // buffer for the next tile now: its last readers (the previous tile's phases) are behind a barrier
+        reset_tile_meta(*C.TMnext);
         if (threadIdx.x == 0) {
             TM.u0 = u;
             TM.v0 = v;
-            TM.smin_bits = INT_MAX;
-            TM.smax_bits = INT_MIN;
         }
-        for (int i = threadIdx.x; i < kBoxes; i += kTileQ) {
-            TM.bb[i][0] = TM.bb[i][2] = INT_MAX;
-            TM.bb[i][1] = TM.bb[i][3] = INT_MIN;
-        }
-        __syncthreads(); // (also orders the weight load before the first tile's MLP)
 
         // ---- 1a. LOD range of the tile (NaN reads as 0, as in lod_of)
         {
@@ -262,20 +280,19 @@ __device__ __forceinline__ void decode_tile(const MaterialDev &M, const TileCtx 
             }
         }
         __syncthreads();
-        // per geometry group: every l0 lies in [lod(smin).l0, lod(smax).l0] and the upper level adds at most one
-        if (threadIdx.x < ng) {
-            const TexDev &T = M.tex[M.group_first[threadIdx.x]];
-            const Lod lo = lod_of(T, ord2f(TM.smin_bits)), hi = lod_of(T, ord2f(TM.smax_bits));
-            TM.lmin[threadIdx.x] = lo.l0;
-            TM.lmax[threadIdx.x] = min(hi.l0 + 1, T.levels - 1);
-        }
-        __syncthreads();
         // ---- 1b. block box per (group, level)
         const float u0 = TM.u0, v0 = TM.v0;
+        const float smin = ord2f(TM.smin_bits), smax = ord2f(TM.smax_bits);
         for (int g = 0; g < ng; ++g) {
             const TexDev &T = M.tex[M.group_first[g]];
-            const int lmin = TM.lmin[g];
-            if (TM.lmax[g] - lmin + 1 > kMaxLv)
+            // every l0 of the tile lies in [lod(smin).l0, lod(smax).l0]; the upper level adds at most one
+            const int lmin = lod_of(T, smin).l0;
+            const int lmax = min(lod_of(T, smax).l0 + 1, T.levels - 1);
+            if (threadIdx.x == 0) {
+                TM.lmin[g] = lmin;
+                TM.lmax[g] = lmax;
+            }
+            if (lmax - lmin + 1 > kMaxLv)
                 continue; // this group is filtered per lane
             const Lod L = lod_of(T, s);
             int bx[2][2], by[2][2]; // [side][lo/hi]
@@ -312,8 +329,60 @@ __device__ __forceinline__ void decode_tile(const MaterialDev &M, const TileCtx 
             }
         }
         __syncthreads();
-        // ---- 1c. per-group block sets and arena rounds of consecutive textures
-        if (threadIdx.x == 0) {
+        // ---- 1c. per-group block sets and arena rounds of consecutive textures.  Warp 0: lane k sizes box k,
+        // per-group totals and per-texture bases by shuffles; when everything fits the arena (the common case)
+        // that is one round; otherwise thread 0 packs the rounds.
+        bool fits = false;
+        if (warp == 0 && ng * kMaxLv <= 32) {
+            const int nbox = ng * kMaxLv;
+            int size = 0;
+            if (lane < nbox) {
+                const int *bb = TM.bb[lane];
+                const int bw = bb[0] != INT_MAX ? bb[1] - bb[0] + 1 : 0;
+                TM.bw[lane] = bw;
+                size = bw ? bw * (bb[3] - bb[2] + 1) : 0;
+            }
+            // inclusive scan of the box sizes within each group of kMaxLv lanes
+            int incl = size;
+#pragma unroll
+            for (int d = 1; d < kMaxLv; d <<= 1) {
+                const int o = __shfl_up_sync(0xffffffffu, incl, d);
+                if (lane % kMaxLv >= d)
+                    incl += o;
+            }
+            if (lane < nbox)
+                TM.boff[lane] = incl - size;
+            const int gt = __shfl_sync(0xffffffffu, incl, lane < ng ? lane * kMaxLv + kMaxLv - 1 : 0);
+            int direct = 0;
+            if (lane < ng) {
+                direct = TM.lmax[lane] - TM.lmin[lane] + 1 > kMaxLv || gt > CAP;
+                TM.direct[lane] = direct;
+                TM.gtotal[lane] = direct ? 0 : gt;
+            }
+            __syncwarp();
+            // per-texture bases: exclusive scan of the group totals over the textures
+            const int tt = lane < nt ? TM.gtotal[M.tex_group[lane]] : 0;
+            int ti = tt;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const int o = __shfl_up_sync(0xffffffffu, ti, d);
+                if (lane >= d)
+                    ti += o;
+            }
+            const int grand = __shfl_sync(0xffffffffu, ti, 31);
+            fits = grand <= CAP;
+            if (fits) {
+                if (lane < nt)
+                    TM.tbase[lane] = ti - tt;
+                if (lane == 0) {
+                    TM.rtex[0] = 0;
+                    TM.rtex[1] = nt;
+                    TM.rtotal[0] = grand;
+                    TM.nrounds = 1;
+                }
+            }
+        }
+        if (warp == 0 && lane == 0 && !fits) {
             for (int g = 0; g < ng; ++g) {
                 int tt = 0;
                 for (int ls = 0; ls < kMaxLv; ++ls) {
@@ -348,12 +417,10 @@ __device__ __forceinline__ void decode_tile(const MaterialDev &M, const TileCtx 
         for (int r = 0; r < nrounds; ++r) {
             const int t_beg = TM.rtex[r], t_end = TM.rtex[r + 1], total = TM.rtotal[r];
             if (total > 0) {
-                // ---- 2. load each block once (two per thread), histogram the modes
-                if (threadIdx.x < 16)
-                    TM.hist[threadIdx.x] = 0;
-                __syncthreads();
+                // ---- 2. load each block once (two per thread); its rank among the blocks of its mode comes
+                // from the (warp-aggregated) histogram atomic
                 uint4 blk[2];
-                int bin[2], bidx[2];
+                int bin[2], bidx[2], rank[2];
 #pragma unroll
                 for (int it = 0; it < 2; ++it) {
                     const int b = it * kTileQ + threadIdx.x;
@@ -387,38 +454,34 @@ __device__ __forceinline__ void decode_tile(const MaterialDev &M, const TileCtx 
                         bin[it] = mi < 0 ? kBins - 1 : mi;
                     }
                     const unsigned peers = __match_any_sync(0xffffffffu, bin[it]);
-                    if (valid && (peers & lanes_lt) == 0)
-                        atomicAdd(&TM.hist[bin[it]], __popc(peers));
+                    const int leader = __ffs(peers) - 1;
+                    int base = 0;
+                    if (valid && lane == leader)
+                        base = atomicAdd(&TM.hist[bin[it]], __popc(peers));
+                    rank[it] = __shfl_sync(0xffffffffu, base, leader) + __popc(peers & lanes_lt);
                 }
                 __syncthreads();
-                if (threadIdx.x == 0) {
-                    int acc = 0;
-                    for (int i = 0; i < kBins; ++i) {
-                        TM.offs[i] = acc;
-                        acc += TM.hist[i];
-                    }
-                }
-                __syncthreads();
-                // ---- 3. scatter into mode-sorted order
+                // ---- 3. scatter into mode-sorted order: position = blocks of smaller modes + rank
 #pragma unroll
                 for (int it = 0; it < 2; ++it) {
-                    const bool valid = bidx[it] < total;
-                    const unsigned peers = __match_any_sync(0xffffffffu, bin[it]);
-                    const int leader = __ffs(peers) - 1;
-                    int pos = 0;
-                    if (valid && lane == leader)
-                        pos = atomicAdd(&TM.offs[bin[it]], __popc(peers));
-                    pos = __shfl_sync(0xffffffffu, pos, leader) + __popc(peers & lanes_lt);
-                    if (valid) {
+                    if (bidx[it] < total) {
+                        int pos = rank[it];
+                        for (int i = 0; i < bin[it]; ++i)
+                            pos += TM.hist[i];
                         sraw[pos] = blk[it];
                         sidx[pos] = (uint16_t)bidx[it];
                     }
                 }
                 __syncthreads();
-                // ---- 4. decode the sorted blocks into the texel arena: two threads per block (the header is
-                // decoded by both, each then writes 8 texels); neighbouring lanes take the same block
-                for (int i = threadIdx.x; i < 2 * total; i += kTileQ) {
-                    const int e = i >> 1, half = i & 1;
+                if (threadIdx.x < 16)
+                    TM.hist[threadIdx.x] = 0; // for the next round (read again only after the decode barrier)
+                // ---- 4. decode the sorted blocks into the texel arena.  The phase's length is one thread's
+                // chain (header + its texels), so a block is split over 1, 2 or 4 threads (each decodes the
+                // header and 16, 8 or 4 texels), the most that keeps all parts in one pass of the CTA;
+                // neighbouring lanes take parts of the same block.
+                const int lk = total <= 64 ? 2 : total <= 128 ? 1 : 0;
+                for (int i = threadIdx.x; i < (total << lk); i += kTileQ) {
+                    const int e = i >> lk, part = i & ((1 << lk) - 1);
                     const uint4 rr = sraw[e];
                     const int bi = sidx[e];
                     Bc6hBlock bk;
@@ -426,9 +489,15 @@ __device__ __forceinline__ void decode_tile(const MaterialDev &M, const TileCtx 
                     bk.hi = (uint64_t)rr.z | ((uint64_t)rr.w << 32);
                     Bc6hHeader H;
                     bc6h_header(bk, sgn, H);
-                    bc6h_half_texels(bk, H, sgn, half, [&](int t, uint32_t rg, uint32_t bb) {
-                        arena[arena_slot(bi, t)] = make_uint2(rg, bb);
-                    });
+                    Bc6hTexels X;
+                    bc6h_prepare_texels(bk, H, X);
+                    const auto put = [&](int t, uint32_t rg, uint32_t bb) { arena[arena_slot(bi, t)] = make_uint2(rg, bb); };
+                    if (lk == 0)
+                        bc6h_texels<16>(X, sgn, 0, put);
+                    else if (lk == 1)
+                        bc6h_texels<8>(X, sgn, part * 8, put);
+                    else
+                        bc6h_texels<4>(X, sgn, part * 4, put);
                 }
                 __syncthreads();
                 // ---- 5. filter: per group, the footprint geometry once; per texture, 4 arena texels per level
@@ -558,9 +627,11 @@ __global__ void __launch_bounds__(kTileQ, 3) k_decode_tiled(MaterialDev M, const
 {
     static_assert(CAP <= 2 * kTileQ, "blocks are held two per thread while sorting");
     extern __shared__ __align__(16) unsigned char smem[];
-    const TileCtx C = carve<PREC>(smem, M.mlp, CAP, K0 == 0);
+    TileCtx C = carve<PREC>(smem, M.mlp, CAP, K0 == 0);
     const int wrap = M.wrap;
     load_mlp_smem<PREC>(M.mlp, C.sw, C.sb);
+    reset_tile_meta(*C.TM);
+    __syncthreads();
     const int64_t tiles = (n + kTileQ - 1) / kTileQ;
     float nu = 0.0f, nv = 0.0f, ns = 0.0f;
     {
@@ -586,6 +657,7 @@ __global__ void __launch_bounds__(kTileQ, 3) k_decode_tiled(MaterialDev M, const
             }
         }
         decode_tile<PREC, CAP, K0, N1, N2, NO>(M, C, tile * kTileQ, n, u, v, s, out, out_fp16);
+        swap_meta(C);
     }
 }
 
@@ -609,7 +681,8 @@ __global__ void __launch_bounds__(kTileQ, 3) k_decode_set(const MaterialDev *__r
     __shared__ int64_t tile_first[BCF_MAX_SET + 1];
     __shared__ int grab;
     // every material shares the MLP shape (checked when the set is created), so the layout is that of material 0
-    const TileCtx C = carve<PREC>(smem, mats[0].mlp, CAP, K0 == 0);
+    TileCtx C = carve<PREC>(smem, mats[0].mlp, CAP, K0 == 0);
+    reset_tile_meta(*C.TM);
     if (threadIdx.x == 0) {
         int64_t acc = 0;
         for (int m = 0; m < nmat; ++m) {
@@ -663,6 +736,7 @@ __global__ void __launch_bounds__(kTileQ, 3) k_decode_set(const MaterialDev *__r
                 s = qs ? qs[q] : 0.0f;
             }
             decode_tile<PREC, CAP, K0, N1, N2, NO>(Ms, C, q0, b, u, v, s, out, out_fp16);
+            swap_meta(C);
         }
     }
 }
