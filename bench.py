@@ -9,7 +9,11 @@ inputs resident in HBM; ``e2e`` is the same metric through the C ABI with the
 queries in pinned host memory and the decoded channels read back every step.
 
 Extra keys report the FP32 SIMT plain path and the FP8 path on the same frame,
-the roofline of the dominant kernel, and the CPU oracle on a bounded sample.
+the batched 64-material launch, the 8x4096^2 frame (FP8 / FP16 / FP32), the
+small 2x256^2 launch, training steps/s, the roofline of the dominant kernel
+(HBM, with the issue and tensor co-bounds), the measured FP8 and derived FP32
+peaks, the CPU oracle on a bounded sample and, from the same oracle run, the
+per-channel error of every path against the exact FP64 decode.
 
 Multi-GPU: the decode shards by queries with no exchange step; each rank
 decodes its own full frame (replicas, weak scaling), and rank 0 reports the
@@ -45,6 +49,44 @@ def _peaks():
         return float(p["hbm_gbs"]), float(p["bf16_tflops"]), "measured"
     except Exception:
         return 6400.0, 1800.0, "fallback"
+
+
+# DRAM traffic and executed warp instructions of one launch of the headline kernel, from the full ncu
+# capture summarised in profiles/k_decode_tiled_screen2048_fp16.md.  They are reported only while the
+# kernel's sources hash to the value the capture was taken on; after any change they read as null.
+KERNEL_SOURCES = ["bcf_decode_tiled.cu", "bc6h_unpack.cuh", "bcf_sample.cuh", "bcf_mlp.cuh", "bcf_internal.h"]
+NCU_CAPTURE = {"source_sha256": "fb9af4a4c39d52dd", "dram_bytes": 121182208 + 104522240, "warp_inst": 703194424}
+SM_COUNT, SMSP_PER_SM, FP32_LANES_PER_SM = 148, 4, 128
+
+
+def _kernel_sha():
+    import hashlib
+
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2311_16121_b300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _fp8_tflops(torch, n=8192, iters=20):
+    """Dense FP8 E4M3 peak of this GPU, measured with the library GEMM (burst, like the BF16 figure)."""
+    try:
+        a = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn)
+        b = torch.randn(n, n, device="cuda").to(torch.float8_e4m3fn).t()
+        one = torch.ones((), device="cuda")
+        for _ in range(3):
+            torch._scaled_mm(a, b, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(iters):
+            torch._scaled_mm(a, b, scale_a=one, scale_b=one, out_dtype=torch.bfloat16)
+        e1.record()
+        e1.synchronize()
+        return 2.0 * n ** 3 * iters / (e0.elapsed_time(e1) * 1e-3) / 1e12
+    except Exception:
+        return None
 
 
 class ClockSampler:
@@ -102,8 +144,14 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def _cpu_baseline(w, precision, seconds=12.0):
-    """The oracle (plain FP64 C, all host cores) on a seeded uniform sample of the frame's queries."""
+def _cpu_baseline(w, precision, gpu_out, seconds=12.0):
+    """The oracle (plain FP64 C, all host cores) on a seeded uniform sample of the frame's queries.
+
+    The same run also gives the accuracy of the GPU outputs: ``gpu_out`` maps a
+    precision to a callable returning that path's FP32 outputs at given query
+    indices.  Each path is compared with the exact FP64 decode (FP32 master
+    weights, no rounding anywhere) on the first 2^16 sampled queries, and the
+    timed path with the quantisation-aware oracle on the whole sample."""
     import oracle
 
     mat = oracle.Material(w.blocks, w.res, w.levels, w.res_ref, w.is_signed, w.wrap, w.lod_input)
@@ -122,11 +170,29 @@ def _cpu_baseline(w, precision, seconds=12.0):
     n = int(min(max(rate * seconds, 1 << 16), w.n))
     idx = rng.integers(0, w.n, n)
     t = time.perf_counter()
-    oracle.decode(mat, P, w.u[idx], w.v[idx], w.s[idx], quant_aware=True, threads=cores)
+    ref_q = oracle.decode(mat, P, w.u[idx], w.v[idx], w.s[idx], quant_aware=True, threads=cores)
     dt = time.perf_counter() - t
-    return {"value": n / dt / 1e9, "unit": "Gsamples/s", "cores": cores, "kind": "oracle",
-            "sample": f"{n} queries drawn uniformly (seed 7) from the {w.n}-query frame, {precision} "
-                      f"quantisation-aware FP64 decode, {dt:.1f} s"}
+    cpu = {"value": n / dt / 1e9, "unit": "Gsamples/s", "cores": cores, "kind": "oracle",
+           "sample": f"{n} queries drawn uniformly (seed 7) from the {w.n}-query frame, {precision} "
+                     f"quantisation-aware FP64 decode, {dt:.1f} s"}
+
+    # accuracy
+    W32, b32, _, _ = w.weights("fp32")
+    exact = oracle.decode(mat, oracle.Mlp(w.dims, "fp32", W32, b32), w.u[idx[:1 << 16]], w.v[idx[:1 << 16]],
+                          w.s[idx[:1 << 16]], quant_aware=False, threads=cores)
+
+    def stats(d):
+        return {"max_abs": [float(f"{x:.3g}") for x in np.abs(d).max(axis=0)],
+                "rms": [float(f"{x:.3g}") for x in np.sqrt((d * d).mean(axis=0))]}
+
+    acc = {"reference": "exact FP64 decode with the FP32 master weights, 65536 sampled queries, per channel"}
+    for prec, get in gpu_out.items():
+        acc[prec] = stats(get(idx[:1 << 16]).astype(np.float64) - exact)
+    d = gpu_out[precision](idx).astype(np.float64) - ref_q
+    acc[f"{precision}_vs_quantisation_aware_oracle"] = {
+        "queries": n, "max_abs": float(f"{np.abs(d).max():.3g}"),
+        "frac_above_1e-3": float(f"{(np.abs(d) > 1e-3).mean():.3g}")}
+    return cpu, acc
 
 
 def run_reference(args):
@@ -166,6 +232,24 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def _train_bench(torch, workloads, stream, k_train):
+    """Training steps/s: 4 block-parameterised 1024^2 textures with mips, 2048^2 9-channel reference,
+    batch 2^20 Philox draws, MLP 13-32-32-9 (BF16 operands), Adam.  Returns (ms/step, last loss, batch)."""
+    tw = workloads.train_workload()
+    tr = workloads.upload_trainer(tw)
+    for i in range(3):
+        tr.step(tw.batch, 7, i)
+    torch.cuda.synchronize()
+    ta = torch.cuda.Event(enable_timing=True)
+    tb = torch.cuda.Event(enable_timing=True)
+    ta.record(stream)
+    for i in range(k_train):
+        tr.step(tw.batch, 7, 3 + i)
+    tb.record(stream)
+    tb.synchronize()
+    return ta.elapsed_time(tb) / k_train, float(tr.loss.item()), tw.batch
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -173,6 +257,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only-train", action="store_true",
+                    help="time only the training step (for profiler captures); prints a reduced line")
     ap.add_argument("--only-headline", action="store_true",
                     help="time only the headline decode (for profiler captures); prints a reduced line")
     args = ap.parse_args()
@@ -195,14 +281,24 @@ def main():
     bcf.lib()
     assert args.warmup >= 3, "at least 3 warm-up steps"
 
+    stream = torch.cuda.current_stream()
+    if args.only_train:
+        ms, loss, batch = _train_bench(torch, workloads, stream, args.steps)
+        if rank == 0:
+            print(json.dumps({"metric": "train steps/s", "value": 1000.0 / ms, "unit": "steps/s", "n_gpus": world,
+                              "steps": args.steps, "warmup": 3, "ms_per_step": ms, "batch": batch,
+                              "last_loss": loss, "note": "training step only"}))
+        return
+
     w = workloads.config2()
     u, v, s = workloads.queries_to_device(w)
     mats = {p: workloads.upload(w, p) for p in (HEADLINE_PRECISION, "fp32", "fp8")}
     out = torch.empty((w.n, 9), dtype=torch.float16, device="cuda")
+    out32 = torch.empty((w.n, 9), dtype=torch.float32, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 126 MB L2
     stream = torch.cuda.current_stream()
 
-    def timed(mat, steps, warmup):
+    def timed(mat, steps, warmup, out=out):
         for _ in range(warmup):
             mat.decode(u, v, s, out=out)
         torch.cuda.synchronize()
@@ -242,8 +338,31 @@ def main():
 
     # the plain FP32 path and FP8 on the same frame
     k_extra = max(3, args.steps // 4)
-    fp32_ms = timed(mats["fp32"], k_extra, 3) / k_extra
+    fp32_ms = timed(mats["fp32"], k_extra, 3, out=out32) / k_extra
     fp8_ms = timed(mats["fp8"], k_extra, 3) / k_extra
+
+    def gathered(prec):
+        """Outputs of one untimed decode of `prec` (in the timed path's output type) at query indices."""
+        o = torch.empty_like(out32 if prec == "fp32" else out)
+        mats[prec].decode(u, v, s, out=o)
+        return lambda idx: o[torch.from_numpy(idx).cuda()].float().cpu().numpy()
+
+    # small: 2x 256^2 random all-mode textures, 65,536 uniform queries, bilinear at level 0, MLP 6-16-16-8 FP32
+    w1 = workloads.config1()
+    m1 = workloads.upload(w1, "fp32")
+    u1, v1, _ = workloads.queries_to_device(w1)
+    o1 = torch.empty((w1.n, 8), dtype=torch.float32, device="cuda")
+    for _ in range(5):
+        m1.decode(u1, v1, None, out=o1)
+    torch.cuda.synchronize()
+    a1, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a1.record(stream)
+    for _ in range(100):
+        m1.decode(u1, v1, None, out=o1)
+    b1.record(stream)
+    b1.synchronize()
+    small_us = a1.elapsed_time(b1) * 10.0
+    del m1, u1, v1, o1
 
     # end to end through the C ABI with host buffers
     uh, vh, sh = (torch.from_numpy(a).pin_memory() for a in (w.u, w.v, w.s))
@@ -266,24 +385,7 @@ def main():
             e2e_total += a.elapsed_time(b)
     e2e_value = w.n * world * k_extra / (e2e_total * 1e-3) / 1e9
 
-    # training steps/s: 4 block-parameterised 1024^2 textures with mips, 2048^2 9-channel reference,
-    # batch 2^20 Philox draws, MLP 13-32-32-9 (BF16 operands), Adam
-    tw = workloads.train_workload()
-    tr = workloads.upload_trainer(tw)
-    for i in range(3):
-        tr.step(tw.batch, 7, i)
-    torch.cuda.synchronize()
-    k_train = max(3, args.steps // 2)
-    ta = torch.cuda.Event(enable_timing=True)
-    tb = torch.cuda.Event(enable_timing=True)
-    ta.record(stream)
-    for i in range(k_train):
-        tr.step(tw.batch, 7, 3 + i)
-    tb.record(stream)
-    tb.synchronize()
-    train_ms = ta.elapsed_time(tb) / k_train
-    train_loss = float(tr.loss.item())
-    del tr
+    train_ms, train_loss, train_batch = _train_bench(torch, workloads, stream, max(3, args.steps // 2))
 
     # batched multi-material decode: 64 materials, one persistent graph-captured launch, autotuned
     sw = workloads.config4()
@@ -362,14 +464,31 @@ def main():
     del u5, v5, s5, out5, w5
 
     hbm_peak, bf16_peak, peak_kind = _peaks()
+    fp8_peak = _fp8_tflops(torch)
+    sm_clock_ghz = (clocks.get("sm_max_mhz") or 2032.0) / 1e3
+    fp32_simt_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_clock_ghz / 1e3  # TFLOP/s, one FMA per lane per clock
+    issue_peak = SM_COUNT * SMSP_PER_SM * sm_clock_ghz  # G warp-instructions/s, one issue per partition per clock
     tex_bytes = sum(int(b.size) for b in w.blocks)
     alg_bytes = w.n * (12 + 18) + tex_bytes  # queries in, FP16 channels out, the texture set once
-    achieved = alg_bytes / (head_ms / args.steps * 1e-3) / 1e9
+    head_launch_s = head_ms / args.steps * 1e-3
+    achieved = alg_bytes / head_launch_s / 1e9
+    counters_valid = _kernel_sha() == NCU_CAPTURE["source_sha256"] and HEADLINE_PRECISION == "fp16"
+    mlp_flops = 2 * sum(a * b for a, b in zip(w.dims[:-1], w.dims[1:]))  # 3,456 per query for 13-32-32-9
+
+    # large frame: tensor roofline of the MLP (25-64-64-9, 12,544 flop/query) and HBM bytes per path
+    flops5 = 2 * (25 * 64 + 64 * 64 + 64 * 9)
+    tex5 = 8 * 22369616  # 8 x 4096^2 with full mips, 16 B per 4x4 block
+    for prec, peak_tf in (("fp8", fp8_peak), ("fp16", bf16_peak), ("fp32", fp32_simt_peak)):
+        t5 = cfg5[prec]["ms_per_step"] * 1e-3
+        tf = flops5 * n5 / t5 / 1e12
+        cfg5[prec]["tensor" if prec != "fp32" else "fp32_simt"] = {
+            "achieved_tflops": tf, "peak_tflops": peak_tf, "frac": (tf / peak_tf) if peak_tf else None}
+        cfg5[prec]["hbm_frac"] = (n5 * (12 + 18) + tex5) / t5 / 1e9 / hbm_peak
 
     if rank == 0:
-        cpu = None
+        cpu, acc = None, None
         if not args.no_cpu_baseline and world == 1:
-            cpu = _cpu_baseline(w, HEADLINE_PRECISION)
+            cpu, acc = _cpu_baseline(w, HEADLINE_PRECISION, {p: gathered(p) for p in ("fp16", "fp8", "fp32")})
         line = {
             "metric": METRIC, "value": value, "unit": "Gsamples/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": head_ms_max / args.steps, "higher_is_better": True,
@@ -379,7 +498,11 @@ def main():
                        "queries_per_step": w.n, "precision": HEADLINE_PRECISION, "out": "fp16 [N][9]",
                        "l2": "256 MB buffer written between timed steps",
                        "parallelism": f"replicas x{world}"},
-            "fp32_plain": {"value": w.n / (fp32_ms * 1e-3) / 1e9, "unit": "Gsamples/s", "ms_per_step": fp32_ms},
+            "fp32_plain": {"value": w.n / (fp32_ms * 1e-3) / 1e9, "unit": "Gsamples/s", "ms_per_step": fp32_ms,
+                           "out": "fp32 [N][9]", "kernel": "k_decode_fp32 (plain FP32 SIMT, per-lane)",
+                           "fp32_simt": {"achieved_tflops": mlp_flops * w.n / (fp32_ms * 1e-3) / 1e12,
+                                         "peak_tflops": fp32_simt_peak, "peak_kind": "derived: 148 SMs x 128 "
+                                         "lanes x 2 flop x max SM clock"}},
             "fp8": {"value": w.n / (fp8_ms * 1e-3) / 1e9, "unit": "Gsamples/s", "ms_per_step": fp8_ms},
             "speedup_vs_fp32_plain": fp32_ms / (head_ms / args.steps),
             "batched": {"value": set_n / (set_ms * 1e-3) / 1e9, "unit": "Gsamples/s", "ms_per_step": set_ms,
@@ -389,17 +512,37 @@ def main():
                                       "tiles_per_grab": set_cfg[2]},
                         "sequential_64_launches": {"value": set_n / (seq_ms * 1e-3) / 1e9, "unit": "Gsamples/s",
                                                    "ms_per_step": seq_ms}},
-            "large_8x4096": {"queries": n5, "mlp": "25-64-64-9", **cfg5},
+            "large_8x4096": {"queries": n5, "mlp": "25-64-64-9", "flop_per_query": flops5, **cfg5},
+            "small_2x256": {"queries": 65536, "mlp": "6-16-16-8 fp32", "us_per_launch": small_us,
+                            "value": 65536 / (small_us * 1e-6) / 1e9, "unit": "Gsamples/s",
+                            "note": "launch-latency bound: 100 back-to-back launches, no flush"},
             "train": {"metric": "train steps/s", "value": 1000.0 / train_ms, "unit": "steps/s",
-                      "ms_per_step": train_ms, "batch": tw.batch, "samples_per_s": tw.batch * 1000.0 / train_ms,
+                      "ms_per_step": train_ms, "batch": train_batch,
+                      "samples_per_s": train_batch * 1000.0 / train_ms,
                       "workload": "4x block-parameterised 1024^2 (9 levels), 2048^2 9-ch reference, "
                                   "MLP 13-32-32-9 BF16 operands, Adam", "last_loss": train_loss},
             "e2e": {"value": e2e_value, "unit": "Gsamples/s", "h2d_bytes_per_step": 12 * w.n,
                     "d2h_bytes_per_step": 18 * w.n},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": achieved / hbm_peak, "traffic": None, "peak_kind": peak_kind,
+                         "frac": achieved / hbm_peak,
+                         "traffic": NCU_CAPTURE["dram_bytes"] if counters_valid else None, "peak_kind": peak_kind,
                          "kernel": f"k_decode_tiled<{HEADLINE_PRECISION}> (tile-cooperative decode)",
-                         "algorithmic_bytes_per_launch": alg_bytes},
+                         "algorithmic_bytes_per_launch": alg_bytes,
+                         "co_bound": {"bound": "issue", "unit": "G warp-instructions/s",
+                                      "achieved": (NCU_CAPTURE["warp_inst"] / head_launch_s / 1e9
+                                                   if counters_valid else None),
+                                      "peak": issue_peak,
+                                      "frac": (NCU_CAPTURE["warp_inst"] / head_launch_s / 1e9 / issue_peak
+                                               if counters_valid else None),
+                                      "note": "executed (not algorithmic) instructions per launch from ncu; "
+                                              "peak = 148 SMs x 4 partitions x 1 issue/clock at the max SM clock"},
+                         "tensor": {"achieved_tflops": mlp_flops * w.n / head_launch_s / 1e12,
+                                    "peak_tflops": bf16_peak,
+                                    "frac": mlp_flops * w.n / head_launch_s / 1e12 / bf16_peak}},
+            "peaks": {"hbm_gbs": hbm_peak, "bf16_tflops": bf16_peak, "kind": peak_kind,
+                      "fp8_tflops": fp8_peak, "fp8_kind": "measured here: torch._scaled_mm 8192^3 e4m3, burst",
+                      "fp32_simt_tflops": fp32_simt_peak, "fp32_simt_kind": "derived from unit counts and clock"},
+            "accuracy": acc,
             "cpu_baseline": cpu,
             "clocks": clocks,
             "gpu_launches": args.steps,

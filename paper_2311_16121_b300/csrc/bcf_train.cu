@@ -461,8 +461,29 @@ struct AdamArgs {
     float beta1, beta2, eps, bc1, bc2;
 };
 
-constexpr int kAdamChunk = 4096;
+constexpr int kAdamChunk = 4096;  // elements per CTA: 256 threads x 4 float4 groups
+constexpr int kAdamVec = kAdamChunk / (256 * 4);
 
+__device__ __forceinline__ float adam_one(const AdamArgs &A, float lr, float &p, float g, float &m, float &v)
+{
+    m = A.beta1 * m + (1.0f - A.beta1) * g;
+    v = A.beta2 * v + (1.0f - A.beta2) * g * g;
+    p = p - lr * (m / A.bc1) / (sqrtf(v / A.bc2) + A.eps);
+    return p;
+}
+
+// Block-parameter records: element e of a 32-float record is an endpoint channel (e < 16, box [0, 63]) or an
+// index coordinate (e >= 16, box [0, 1]); elements 6, 7, 14, 15 are padding and are left untouched.
+__device__ __forceinline__ bool record_pad(int e) { return e == 6 || e == 7 || e == 14 || e == 15; }
+__device__ __forceinline__ float record_clamp(int e, float p)
+{
+    return e < 16 ? fminf(fmaxf(p, 0.0f), 63.0f) : fminf(fmaxf(p, 0.0f), 1.0f);
+}
+
+// One Adam step over the segments (feature records of every texture, MLP weights, MLP biases), with the
+// learning rate lr_0 gamma^step and the gradients zeroed for the next step.  Each CTA streams a 4096-element
+// chunk of one segment with 16-byte accesses, all four of a thread's groups loaded before any is written so
+// that 16 loads per thread are in flight; ragged or unaligned segments take the scalar path.
 __global__ void __launch_bounds__(256) k_adam(AdamArgs A)
 {
     int k = 0;
@@ -471,22 +492,55 @@ __global__ void __launch_bounds__(256) k_adam(AdamArgs A)
     const AdamSeg &S = A.seg[k];
     const int64_t i0 = ((int64_t)blockIdx.x - A.chunk_start[k]) * kAdamChunk;
     const int64_t i1 = min(i0 + kAdamChunk, S.n);
+    const bool aligned = ((reinterpret_cast<uintptr_t>(S.p) | reinterpret_cast<uintptr_t>(S.g) |
+                           reinterpret_cast<uintptr_t>(S.m) | reinterpret_cast<uintptr_t>(S.v)) & 15) == 0;
+    if (aligned && i1 - i0 == kAdamChunk) {
+        float4 *__restrict__ P = reinterpret_cast<float4 *>(S.p + i0);
+        float4 *__restrict__ G = reinterpret_cast<float4 *>(S.g + i0);
+        float4 *__restrict__ M = reinterpret_cast<float4 *>(S.m + i0);
+        float4 *__restrict__ V = reinterpret_cast<float4 *>(S.v + i0);
+        float4 p[kAdamVec], g[kAdamVec], m[kAdamVec], v[kAdamVec];
+#pragma unroll
+        for (int j = 0; j < kAdamVec; ++j) {
+            const int x = threadIdx.x + 256 * j;
+            g[j] = G[x];
+            m[j] = __ldcs(M + x);
+            v[j] = __ldcs(V + x);
+            p[j] = P[x];
+        }
+#pragma unroll
+        for (int j = 0; j < kAdamVec; ++j) {
+            const int x = threadIdx.x + 256 * j;
+            float *pp = &p[j].x, *gg = &g[j].x, *mm = &m[j].x, *vv = &v[j].x;
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                const int e = (4 * x + c) & 31;
+                if (S.blocks_layout && record_pad(e))
+                    continue;
+                float pn = pp[c], mn = mm[c], vn = vv[c];
+                adam_one(A, S.lr, pn, gg[c], mn, vn);
+                pp[c] = S.blocks_layout ? record_clamp(e, pn) : pn;
+                mm[c] = mn;
+                vv[c] = vn;
+            }
+            G[x] = make_float4(0.0f, 0.0f, 0.0f, 0.0f); // parameters and gradients stay in L2 for the next
+            P[x] = p[j];                               // step; the moments stream
+            __stcs(M + x, m[j]);
+            __stcs(V + x, v[j]);
+        }
+        return;
+    }
     for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) {
         const float g = S.g[i];
         S.g[i] = 0.0f;
-        if (S.blocks_layout) {
-            const int e = (int)(i & 31);
-            if (e == 6 || e == 7 || e == 14 || e == 15)
-                continue;
-        }
-        const float m = A.beta1 * S.m[i] + (1.0f - A.beta1) * g;
-        const float v = A.beta2 * S.v[i] + (1.0f - A.beta2) * g * g;
+        const int e = (int)(i & 31);
+        if (S.blocks_layout && record_pad(e))
+            continue;
+        float p = S.p[i], m = S.m[i], v = S.v[i];
+        adam_one(A, S.lr, p, g, m, v);
         S.m[i] = m;
         S.v[i] = v;
-        float p = S.p[i] - S.lr * (m / A.bc1) / (sqrtf(v / A.bc2) + A.eps);
-        if (S.blocks_layout)
-            p = (i & 31) < 16 ? fminf(fmaxf(p, 0.0f), 63.0f) : fminf(fmaxf(p, 0.0f), 1.0f);
-        S.p[i] = p;
+        S.p[i] = S.blocks_layout ? record_clamp(e, p) : p;
     }
 }
 
