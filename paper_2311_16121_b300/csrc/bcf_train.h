@@ -36,6 +36,10 @@ int64_t train_smem_bytes(const TrainDev &D);
 cudaError_t launch_train(const TrainDev &D, int mode, int64_t batch, uint64_t seed, int64_t step, const float *u,
                          const float *v, const float *s, float *out, const float *grad_out, float *loss,
                          cudaStream_t st);
+bool train_mma_supported(const TrainDev &D);
+cudaError_t launch_train_mma(const TrainDev &D, int mode, int64_t batch, uint64_t seed, int64_t step,
+                             const float *u, const float *v, const float *s, float *out, const float *grad_out,
+                             float *loss, int sms, cudaStream_t st);
 cudaError_t launch_adam(const TrainDev &D, const TrainHyper &H, int64_t step, cudaStream_t st);
 cudaError_t launch_export(const TrainDev &D, void *const *blocks_out, uint16_t *weights_fp16, cudaStream_t st);
 

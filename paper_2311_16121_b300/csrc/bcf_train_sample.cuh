@@ -1,0 +1,210 @@
+// bcf_train_sample.cuh -- per-query pieces of the training step shared by the
+// training kernels: the Philox4x32-10 batch draw, the straight-through mode-10
+// texel (Sec. 4.2, Eq. 7-9), the trilinear taps over the block parameters
+// (Eq. 10, Eq. 11 bias), the Catmull-Rom reference sample, and vector atomics.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <math.h>
+
+#include "bc6h_unpack.cuh"
+#include "bcf_train.h"
+
+namespace bcf {
+
+enum { kModeForward = 0, kModeBackward = 1, kModeStep = 2 };
+
+// ------------------------------------------------------------ Philox4x32-10
+
+__device__ __forceinline__ void philox4x32_10(uint32_t c[4], uint32_t k0, uint32_t k1)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c[0]), lo0 = 0xD2511F53u * c[0];
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c[2]), lo1 = 0xCD9E8D57u * c[2];
+        const uint32_t n0 = hi1 ^ c[1] ^ k0, n2 = hi0 ^ c[3] ^ k1;
+        c[0] = n0;
+        c[1] = lo1;
+        c[2] = n2;
+        c[3] = lo0;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+}
+
+// --------------------------------------------------- emulated BC6 mode 10
+
+// One texel of the block-based features: value (half reinterpretation of the
+// exact integer decode of the rounded parameters, Eq. 9) and the partials of
+// the relaxed pipeline at that point.
+struct SteTexel {
+    float v[3];
+    float dea[3], deb[3], dx[3];
+    int region;
+    int ina[3], inb[3], inx;
+};
+
+__device__ __forceinline__ int unq6(float e)
+{
+    const int q = (int)rintf(fminf(fmaxf(e, 0.0f), 63.0f));
+    return q == 0 ? 0 : (q == 63 ? 0xFFFF : q * 1024 + 512);
+}
+
+__device__ __forceinline__ void ste_texel(const float *p, int k, int t, SteTexel &o)
+{
+    const int r = (int)((partition_mask(k) >> t) & 1);
+    o.region = r;
+    const float4 a4 = *reinterpret_cast<const float4 *>(p + 8 * r);
+    const float2 b2 = *reinterpret_cast<const float2 *>(p + 8 * r + 4);
+    const float ea[3] = {a4.x, a4.y, a4.z}, eb[3] = {a4.w, b2.x, b2.y};
+    const float x = p[16 + t];
+    o.inx = x >= 0.0f && x <= 1.0f;
+    const int w = weight3((int)rintf(7.0f * fminf(fmaxf(x, 0.0f), 1.0f)));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        o.ina[c] = ea[c] >= 0.0f && ea[c] <= 63.0f;
+        o.inb[c] = eb[c] >= 0.0f && eb[c] <= 63.0f;
+        const int ua = unq6(ea[c]), ub = unq6(eb[c]);
+        const int yi = (64 * ua + 32 + (ub - ua) * w) >> 6;
+        const int y = (yi * 31) >> 6;
+        o.v[c] = __half2float(__ushort_as_half((unsigned short)y));
+        // slope of Eq. 9: 2^(h - 14) / 1024 with h = max(floor((y - 1) / 1024) - 1, 0); times 31/64
+        const int h = max(((y - 1) >> 10) - 1, 0);
+        const float dy = ldexpf(31.0f, h - 30);
+        o.dea[c] = dy * (float)((64 - w) * 16);
+        o.deb[c] = dy * (float)(w * 16);
+        o.dx[c] = dy * (float)(ub - ua);
+    }
+}
+
+__device__ __forceinline__ void red_add_v4(float *p, float a, float b, float c, float d)
+{
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
+                 : "memory");
+}
+__device__ __forceinline__ void red_add_v2(float *p, float a, float b)
+{
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
+}
+
+// Trilinear taps of texture T at (u, v, s): per side (level floor(s_t) and
+// the next, weights 1 - lambda and lambda) the 2 x 2 bilinear footprint.
+struct Tap {
+    int64_t block;
+    int texel;
+    float weight;
+};
+
+template <class F>
+__device__ __forceinline__ void for_each_tap(const TrainTexDev &T, float u, float v, float s, F f)
+{
+    float st = (isnan(s) ? 0.0f : s) + (float)T.lod_bias;
+    st = fminf(fmaxf(st, 0.0f), (float)(T.levels - 1));
+    const float fl = floorf(st);
+    const int l0 = (int)fl;
+    const int l1 = min(l0 + 1, T.levels - 1);
+    const float lam = st - fl;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        const int level = side ? l1 : l0;
+        const float lw = side ? lam : 1.0f - lam;
+        if (lw == 0.0f)
+            continue;
+        const int W = T.res >> level, wb = W >> 2;
+        const int64_t lbase = (int64_t)((((uint32_t)(T.res >> 2) * (uint32_t)(T.res >> 2)) -
+                                         ((uint32_t)wb * (uint32_t)wb)) * 4u / 3u);
+        const float x = u * (float)W - 0.5f, y = v * (float)W - 0.5f;
+        const float fx0 = floorf(x), fy0 = floorf(y);
+        const float fx = x - fx0, fy = y - fy0;
+        const int i0 = (int)fx0, j0 = (int)fy0;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int i = (i0 + (c & 1)) & (W - 1), j = (j0 + (c >> 1)) & (W - 1);
+            const float bw = ((c & 1) ? fx : 1.0f - fx) * ((c >> 1) ? fy : 1.0f - fy);
+            Tap tp;
+            tp.block = lbase + (int64_t)(j >> 2) * wb + (i >> 2);
+            tp.texel = ((j & 3) << 2) | (i & 3);
+            tp.weight = lw * bw;
+            f(tp);
+        }
+    }
+}
+
+// ----------------------------------------------------- reference material
+
+__device__ __forceinline__ void catmull_rom(float f, float w[4])
+{
+    const float f2 = f * f, f3 = f2 * f;
+    w[0] = 0.5f * (-f3 + 2.0f * f2 - f);
+    w[1] = 0.5f * (3.0f * f3 - 5.0f * f2 + 2.0f);
+    w[2] = 0.5f * (-3.0f * f3 + 4.0f * f2 + f);
+    w[3] = 0.5f * (f3 - f2);
+}
+
+__device__ __forceinline__ void target_level(const TrainDev &D, int level, float u, float v, float scale, float out[9])
+{
+    const int W = D.tres >> level;
+    int64_t base = 0;
+    for (int l = 0; l < level; ++l)
+        base += (int64_t)(D.tres >> l) * (D.tres >> l);
+    const float x = u * (float)W - 0.5f, y = v * (float)W - 0.5f;
+    const float fx0 = floorf(x), fy0 = floorf(y);
+    float wx[4], wy[4];
+    catmull_rom(x - fx0, wx);
+    catmull_rom(y - fy0, wy);
+    const int i0 = (int)fx0, j0 = (int)fy0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+        const int j = (j0 - 1 + b) & (W - 1);
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            const int i = (i0 - 1 + a) & (W - 1);
+            const int64_t idx = base + (int64_t)j * W + i;
+            const float wgt = wx[a] * wy[b] * scale;
+            const uint4 c8 = __ldg(reinterpret_cast<const uint4 *>(D.t8) + idx);
+            const uint32_t w4[4] = {c8.x, c8.y, c8.z, c8.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(&w4[q]));
+                out[2 * q] = fmaf(wgt, f.x, out[2 * q]);
+                out[2 * q + 1] = fmaf(wgt, f.y, out[2 * q + 1]);
+            }
+            out[8] = fmaf(wgt, __half2float(__ushort_as_half(__ldg(D.t1 + idx))), out[8]);
+        }
+    }
+}
+
+__device__ __forceinline__ void target_sample(const TrainDev &D, float u, float v, float s, float out[9])
+{
+    float sq = isnan(s) ? 0.0f : s;
+    sq = fminf(fmaxf(sq, 0.0f), (float)(D.tlevels - 1));
+    const float fl = floorf(sq);
+    const int l0 = (int)fl;
+    const int l1 = min(l0 + 1, D.tlevels - 1);
+    const float lam = sq - fl;
+#pragma unroll
+    for (int c = 0; c < 9; ++c)
+        out[c] = 0.0f;
+    if (l1 != l0 && lam > 0.0f) {
+        target_level(D, l0, u, v, 1.0f - lam, out);
+        target_level(D, l1, u, v, lam, out);
+    } else {
+        target_level(D, l0, u, v, 1.0f, out);
+    }
+}
+
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+
+// One batch draw (u, v, s) of query q at the given step: Philox4x32-10 with the
+// counter (q, step, q >> 32) and the seed as key; 24-bit uniforms.
+__device__ __forceinline__ void draw_query(int64_t q, uint32_t seed_lo, uint32_t seed_hi, uint32_t step_lo,
+                                           uint32_t step_hi, float s_max, float &u, float &v, float &s)
+{
+    uint32_t c[4] = {(uint32_t)q, step_lo, step_hi, (uint32_t)((uint64_t)q >> 32)};
+    philox4x32_10(c, seed_lo, seed_hi);
+    u = (float)(c[0] >> 8) * 0x1p-24f;
+    v = (float)(c[1] >> 8) * 0x1p-24f;
+    s = ((float)(c[2] >> 8) * 0x1p-24f) * s_max;
+}
+
+} // namespace bcf
