@@ -32,6 +32,10 @@ constexpr int K0P = 16, N1 = 32, N2 = 32, NOP = 16;
 constexpr int S16 = 24, S32 = 40; // row strides (BF16) of [n][k] tiles with K = 16 / 32: 12 / 20 words
 constexpr int kRowF = NOP + 1;    // FP32 staging row stride
 constexpr int kMaxW = N1 * K0P + N2 * N1 + NOP * N2, kMaxB = N1 + N2 + NOP;
+// The coarsest levels (at most 16 x 16 texels: 16 + 4 + 1 blocks) of the first textures collect the gradient
+// contributions of most queries on a handful of blocks; they are accumulated in shared memory per CTA
+// instead of by contended global atomics, and added to the global gradients once at the end.
+constexpr int kCoarseTex = 4, kCoarseBlocks = 21;
 
 typedef __nv_bfloat16 bf16;
 
@@ -42,7 +46,21 @@ struct MmaSmem {
     float dW[kMaxW], db[kMaxB];
     bf16 X[kWarps][32 * S16]; // the warp's BF16 input rows
     float R[kWarps][32 * kRowF]; // row <-> fragment staging: outputs, output gradients, input gradients
+    float coarse[kCoarseTex][kCoarseBlocks * 32];
 };
+
+// First block of the coarse tail (levels of at most 16 x 16 texels) of a texture's block array.
+__device__ __forceinline__ int64_t coarse_start(const TrainTexDev &T)
+{
+    int lg = 0;
+    while ((2 << lg) <= T.res)
+        ++lg;
+    const int lc = max(lg - 4, 0);
+    if (lc >= T.levels)
+        return T.blocks;
+    const uint32_t wb0 = (uint32_t)(T.res >> 2), wbl = (uint32_t)((T.res >> lc) >> 2);
+    return (int64_t)((wb0 * wb0 - wbl * wbl) * 4u / 3u);
+}
 
 __device__ __forceinline__ uint32_t ld32(const bf16 *p) { return *reinterpret_cast<const uint32_t *>(p); }
 
@@ -219,7 +237,7 @@ __device__ __forceinline__ void weight_grad(const uint32_t (&ghi)[2][MT][4], con
             }
 }
 
-__global__ void __launch_bounds__(kThreads) k_train_mma(TrainDev D, int mode, int64_t batch, uint32_t seed_lo,
+__global__ void __launch_bounds__(kThreads, 4) k_train_mma(TrainDev D, int mode, int64_t batch, uint32_t seed_lo,
                                                         uint32_t seed_hi, uint32_t step_lo, uint32_t step_hi,
                                                         const float *__restrict__ qu, const float *__restrict__ qv,
                                                         const float *__restrict__ qs, float *__restrict__ out,
@@ -257,6 +275,8 @@ __global__ void __launch_bounds__(kThreads) k_train_mma(TrainDev D, int mode, in
     }
     for (int e = threadIdx.x; e < kMaxW; e += kThreads)
         S.dW[e] = 0.0f;
+    for (int e = threadIdx.x; e < kCoarseTex * kCoarseBlocks * 32; e += kThreads)
+        (&S.coarse[0][0])[e] = 0.0f;
     __syncthreads();
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
@@ -476,6 +496,7 @@ __global__ void __launch_bounds__(kThreads) k_train_mma(TrainDev D, int mode, in
             for (int tx = 0; tx < D.n_tex; ++tx) {
                 const float dxf[3] = {rr[3 * tx], rr[3 * tx + 1], rr[3 * tx + 2]};
                 const TrainTexDev &T = D.tex[tx];
+                const int64_t cst = tx < kCoarseTex ? coarse_start(T) : T.blocks;
                 for_each_tap(T, u, v, s, [&](const Tap &tp) {
                     const float *p = T.params + tp.block * 32;
                     SteTexel tt;
@@ -488,6 +509,17 @@ __global__ void __launch_bounds__(kThreads) k_train_mma(TrainDev D, int mode, in
                         ga[c] = tt.ina[c] ? dv * tt.dea[c] : 0.0f;
                         gb[c] = tt.inb[c] ? dv * tt.deb[c] : 0.0f;
                         gx = fmaf(dv, tt.dx[c], gx);
+                    }
+                    if (tp.block >= cst) {
+                        float *cp = S.coarse[tx] + (tp.block - cst) * 32 + 8 * tt.region;
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            atomicAdd(cp + c, ga[c]);
+                            atomicAdd(cp + 3 + c, gb[c]);
+                        }
+                        if (tt.inx)
+                            atomicAdd(S.coarse[tx] + (tp.block - cst) * 32 + 16 + tp.texel, gx);
+                        return;
                     }
                     red_add_v4(gp + 8 * tt.region, ga[0], ga[1], ga[2], gb[0]);
                     red_add_v2(gp + 8 * tt.region + 4, gb[1], gb[2]);
@@ -508,6 +540,13 @@ __global__ void __launch_bounds__(kThreads) k_train_mma(TrainDev D, int mode, in
         for (int i = threadIdx.x; i < N1 + N2 + C; i += kThreads)
             if (S.db[i] != 0.0f)
                 atomicAdd(D.bg + i, S.db[i]);
+        for (int tx = 0; tx < min(D.n_tex, kCoarseTex); ++tx) {
+            const TrainTexDev &T = D.tex[tx];
+            const int64_t cst = coarse_start(T);
+            for (int i = threadIdx.x; i < (int)(T.blocks - cst) * 32; i += kThreads)
+                if (S.coarse[tx][i] != 0.0f)
+                    atomicAdd(T.grad + cst * 32 + i, S.coarse[tx][i]);
+        }
     }
     if (mode == kModeStep) {
         for (int off = 16; off > 0; off >>= 1)
