@@ -305,12 +305,15 @@ __global__ void __launch_bounds__(kThreads, 4) k_train_mma(TrainDev D, int mode,
             float f[3] = {0.0f, 0.0f, 0.0f};
             if (active) {
                 const TrainTexDev &T = D.tex[tx];
-                for_each_tap(T, u, v, s, [&](const Tap &tp) {
-                    SteTexel tt;
-                    ste_texel(T.params + tp.block * 32, T.part[tp.block], tp.texel, tt);
+                for_each_side(T, u, v, s, [&](const Tap(&tp)[4], const TexelParams(&P)[4]) {
 #pragma unroll
-                    for (int c = 0; c < 3; ++c)
-                        f[c] = fmaf(tp.weight, tt.v[c], f[c]);
+                    for (int j = 0; j < 4; ++j) {
+                        SteTexel tt;
+                        ste_from(P[j], tt);
+#pragma unroll
+                        for (int c = 0; c < 3; ++c)
+                            f[c] = fmaf(tp[j].weight, tt.v[c], f[c]);
+                    }
                 });
             }
 #pragma unroll
@@ -497,34 +500,37 @@ __global__ void __launch_bounds__(kThreads, 4) k_train_mma(TrainDev D, int mode,
                 const float dxf[3] = {rr[3 * tx], rr[3 * tx + 1], rr[3 * tx + 2]};
                 const TrainTexDev &T = D.tex[tx];
                 const int64_t cst = tx < kCoarseTex ? coarse_start(T) : T.blocks;
-                for_each_tap(T, u, v, s, [&](const Tap &tp) {
-                    const float *p = T.params + tp.block * 32;
-                    SteTexel tt;
-                    ste_texel(p, T.part[tp.block], tp.texel, tt);
-                    float *gp = T.grad + tp.block * 32;
-                    float ga[3], gb[3], gx = 0.0f;
+                for_each_side(T, u, v, s, [&](const Tap(&tps)[4], const TexelParams(&P)[4]) {
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const float dv = dxf[c] * tp.weight;
-                        ga[c] = tt.ina[c] ? dv * tt.dea[c] : 0.0f;
-                        gb[c] = tt.inb[c] ? dv * tt.deb[c] : 0.0f;
-                        gx = fmaf(dv, tt.dx[c], gx);
-                    }
-                    if (tp.block >= cst) {
-                        float *cp = S.coarse[tx] + (tp.block - cst) * 32 + 8 * tt.region;
+                    for (int j = 0; j < 4; ++j) {
+                        const Tap &tp = tps[j];
+                        SteTexel tt;
+                        ste_from(P[j], tt);
+                        float ga[3], gb[3], gx = 0.0f;
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
-                            atomicAdd(cp + c, ga[c]);
-                            atomicAdd(cp + 3 + c, gb[c]);
+                            const float dv = dxf[c] * tp.weight;
+                            ga[c] = tt.ina[c] ? dv * tt.dea[c] : 0.0f;
+                            gb[c] = tt.inb[c] ? dv * tt.deb[c] : 0.0f;
+                            gx = fmaf(dv, tt.dx[c], gx);
                         }
-                        if (tt.inx)
-                            atomicAdd(S.coarse[tx] + (tp.block - cst) * 32 + 16 + tp.texel, gx);
-                        return;
+                        if (tp.block >= cst) {
+                            float *cp = S.coarse[tx] + (tp.block - cst) * 32;
+#pragma unroll
+                            for (int c = 0; c < 3; ++c) {
+                                atomicAdd(cp + 8 * tt.region + c, ga[c]);
+                                atomicAdd(cp + 8 * tt.region + 3 + c, gb[c]);
+                            }
+                            if (tt.inx)
+                                atomicAdd(cp + 16 + tp.texel, gx);
+                        } else {
+                            float *gp = T.grad + tp.block * 32;
+                            red_add_v4(gp + 8 * tt.region, ga[0], ga[1], ga[2], gb[0]);
+                            red_add_v2(gp + 8 * tt.region + 4, gb[1], gb[2]);
+                            if (tt.inx)
+                                atomicAdd(gp + 16 + tp.texel, gx);
+                        }
                     }
-                    red_add_v4(gp + 8 * tt.region, ga[0], ga[1], ga[2], gb[0]);
-                    red_add_v2(gp + 8 * tt.region + 4, gb[1], gb[2]);
-                    if (tt.inx)
-                        atomicAdd(gp + 16 + tp.texel, gx);
                 });
             }
         }

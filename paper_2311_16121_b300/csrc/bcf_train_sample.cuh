@@ -50,14 +50,27 @@ __device__ __forceinline__ int unq6(float e)
     return q == 0 ? 0 : (q == 63 ? 0xFFFF : q * 1024 + 512);
 }
 
-__device__ __forceinline__ void ste_texel(const float *p, int k, int t, SteTexel &o)
+// The parameters one texel reads: its region's endpoints (e_a, e_b) and its index coordinate x.
+struct TexelParams {
+    float4 a; // e_a RGB, e_b R
+    float2 b; // e_b G, B
+    float x;
+    int region;
+};
+
+__device__ __forceinline__ void load_texel(const float *p, int k, int t, TexelParams &P)
 {
-    const int r = (int)((partition_mask(k) >> t) & 1);
-    o.region = r;
-    const float4 a4 = *reinterpret_cast<const float4 *>(p + 8 * r);
-    const float2 b2 = *reinterpret_cast<const float2 *>(p + 8 * r + 4);
-    const float ea[3] = {a4.x, a4.y, a4.z}, eb[3] = {a4.w, b2.x, b2.y};
-    const float x = p[16 + t];
+    P.region = (int)((partition_mask(k) >> t) & 1);
+    P.a = *reinterpret_cast<const float4 *>(p + 8 * P.region);
+    P.b = *reinterpret_cast<const float2 *>(p + 8 * P.region + 4);
+    P.x = p[16 + t];
+}
+
+__device__ __forceinline__ void ste_from(const TexelParams &P, SteTexel &o)
+{
+    o.region = P.region;
+    const float ea[3] = {P.a.x, P.a.y, P.a.z}, eb[3] = {P.a.w, P.b.x, P.b.y};
+    const float x = P.x;
     o.inx = x >= 0.0f && x <= 1.0f;
     const int w = weight3((int)rintf(7.0f * fminf(fmaxf(x, 0.0f), 1.0f)));
 #pragma unroll
@@ -77,14 +90,22 @@ __device__ __forceinline__ void ste_texel(const float *p, int k, int t, SteTexel
     }
 }
 
+__device__ __forceinline__ void ste_texel(const float *p, int k, int t, SteTexel &o)
+{
+    TexelParams P;
+    load_texel(p, k, t, P);
+    ste_from(P, o);
+}
+
+// Fire-and-forget vector reductions into the gradient arrays.  The kernels never read a gradient they add
+// to, so the reductions carry no memory clobber: later parameter loads may be issued ahead of them.
 __device__ __forceinline__ void red_add_v4(float *p, float a, float b, float c, float d)
 {
-    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d)
-                 : "memory");
+    asm volatile("red.global.add.v4.f32 [%0], {%1, %2, %3, %4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d));
 }
 __device__ __forceinline__ void red_add_v2(float *p, float a, float b)
 {
-    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b) : "memory");
+    asm volatile("red.global.add.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(a), "f"(b));
 }
 
 // Trilinear taps of texture T at (u, v, s): per side (level floor(s_t) and
@@ -127,6 +148,50 @@ __device__ __forceinline__ void for_each_tap(const TrainTexDev &T, float u, floa
             tp.weight = lw * bw;
             f(tp);
         }
+    }
+}
+
+// The same taps grouped by side: f(taps[4]) once per side with a non-zero weight.  The four partition bytes
+// and then the four parameter records of a side are loaded together (two memory latencies per side).
+template <class F>
+__device__ __forceinline__ void for_each_side(const TrainTexDev &T, float u, float v, float s, F f)
+{
+    float st = (isnan(s) ? 0.0f : s) + (float)T.lod_bias;
+    st = fminf(fmaxf(st, 0.0f), (float)(T.levels - 1));
+    const float fl = floorf(st);
+    const int l0 = (int)fl;
+    const int l1 = min(l0 + 1, T.levels - 1);
+    const float lam = st - fl;
+#pragma unroll 1 // one copy of the side body (instruction-fetch bound kernels)
+    for (int side = 0; side < 2; ++side) {
+        const int level = side ? l1 : l0;
+        const float lw = side ? lam : 1.0f - lam;
+        if (lw == 0.0f)
+            continue;
+        const int W = T.res >> level, wb = W >> 2;
+        const int64_t lbase = (int64_t)((((uint32_t)(T.res >> 2) * (uint32_t)(T.res >> 2)) -
+                                         ((uint32_t)wb * (uint32_t)wb)) * 4u / 3u);
+        const float x = u * (float)W - 0.5f, y = v * (float)W - 0.5f;
+        const float fx0 = floorf(x), fy0 = floorf(y);
+        const float fx = x - fx0, fy = y - fy0;
+        const int i0 = (int)fx0, j0 = (int)fy0;
+        Tap tp[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int i = (i0 + (c & 1)) & (W - 1), j = (j0 + (c >> 1)) & (W - 1);
+            tp[c].block = lbase + (int64_t)(j >> 2) * wb + (i >> 2);
+            tp[c].texel = ((j & 3) << 2) | (i & 3);
+            tp[c].weight = lw * ((c & 1) ? fx : 1.0f - fx) * ((c >> 1) ? fy : 1.0f - fy);
+        }
+        int k[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            k[c] = T.part[tp[c].block];
+        TexelParams P[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c)
+            load_texel(T.params + tp[c].block * 32, k[c], tp[c].texel, P[c]);
+        f(tp, P);
     }
 }
 
@@ -185,12 +250,10 @@ __device__ __forceinline__ void target_sample(const TrainDev &D, float u, float 
 #pragma unroll
     for (int c = 0; c < 9; ++c)
         out[c] = 0.0f;
-    if (l1 != l0 && lam > 0.0f) {
-        target_level(D, l0, u, v, 1.0f - lam, out);
-        target_level(D, l1, u, v, lam, out);
-    } else {
-        target_level(D, l0, u, v, 1.0f, out);
-    }
+    const int nside = (l1 != l0 && lam > 0.0f) ? 2 : 1;
+#pragma unroll 1 // one copy of the 16-tap body: the kernels that inline it are instruction-fetch bound
+    for (int side = 0; side < nside; ++side)
+        target_level(D, side ? l1 : l0, u, v, nside == 1 ? 1.0f : (side ? lam : 1.0f - lam), out);
 }
 
 __device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
