@@ -33,7 +33,7 @@ def build(force: bool = False) -> str:
     """Compile the oracle with gcc into ``oracle/liboracle.so``."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".tmp{os.getpid()}"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-fPIC", "-shared", "-o", tmp, _SRC,
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-D_GNU_SOURCE", "-ffp-contract=off", "-fPIC", "-shared", "-o", tmp, _SRC,
                                "-lm", "-lpthread"])
         os.replace(tmp, _LIB)
     return _LIB
@@ -140,6 +140,10 @@ def lib():
         L.oracle_texture_blocks.argtypes = [c_int, c_int]
         L.oracle_train_export_block.restype = None
         L.oracle_train_export_block.argtypes = [c_void_p, c_int, c_void_p]
+        L.oracle_encode_mode10_block.restype = None
+        L.oracle_encode_mode10_block.argtypes = [c_void_p, c_void_p, POINTER(c_int), POINTER(c_float), c_void_p]
+        L.oracle_encode_mode10_texture.restype = None
+        L.oracle_encode_mode10_texture.argtypes = [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]
         L.oracle_adam.restype = None
         L.oracle_adam.argtypes = [c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_double, c_double, c_double,
                                   c_double, c_double, c_double, c_double]
@@ -487,3 +491,29 @@ def train_backward_given(F: TrainFeatures, P: TrainMlp, u, v, s, grad_out):
     lib().oracle_train_backward_given(ctypes.byref(F.c), ctypes.byref(P.c), u.size, _ptr(u), _ptr(v), _ptr(s),
                                       _ptr(go), ctypes.byref(G))
     return [g.reshape(-1, 28) for g in gf], gW, gb
+
+
+# --------------------------------------------------------------------------- mode-10 encoder
+
+def encode_mode10_block(v: np.ndarray) -> tuple[np.ndarray, int, float, np.ndarray]:
+    """Encode one 4x4 block of RGB targets (v[16][3], texel t = 4 row + column): block parameters
+    (training layout, 28 values), partition, its total error, and the total error of all 32 partitions."""
+    v = np.ascontiguousarray(v, dtype=np.float32).reshape(48)
+    params = np.zeros(28, np.float64)
+    k = ctypes.c_int(0)
+    err = ctypes.c_float(0.0)
+    errs = np.zeros(32, np.float32)
+    lib().oracle_encode_mode10_block(_ptr(v), _ptr(params), ctypes.byref(k), ctypes.byref(err), _ptr(errs))
+    return params, int(k.value), float(err.value), errs
+
+
+def encode_mode10_texture(texels: np.ndarray, res: int, levels: int) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """Encode a mipmapped RGB texture (levels concatenated from level 0, each [W][W][3] float32): block
+    parameters [blocks][28], partitions [blocks], errors [blocks]."""
+    texels = np.ascontiguousarray(texels, dtype=np.float32).reshape(-1)
+    nb = texture_blocks(res, levels)
+    params = np.zeros((nb, 28), np.float64)
+    part = np.zeros(nb, np.uint8)
+    err = np.zeros(nb, np.float32)
+    lib().oracle_encode_mode10_texture(_ptr(texels), int(res), int(levels), _ptr(params), _ptr(part), _ptr(err))
+    return params, part, err

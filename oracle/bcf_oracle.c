@@ -11,7 +11,10 @@
  * here, in its own notation, from the public format definition.
  *
  * Arithmetic: FP64 for every floating-point step, integers for the BC6H
- * bitstream, which the format defines exactly.
+ * bitstream, which the format defines exactly -- except the mode-10 block
+ * encoder (partition selection), whose every floating-point quantity decides
+ * an integer and is computed in IEEE single precision in a fixed order, the
+ * precision of the GPU encoder (see its section).
  *
  * What each part follows:
  *   - IEEE-754 binary16 / bfloat16 / OCP E4M3 codecs: the format definitions.
@@ -33,6 +36,10 @@
  *     bicubic reference sampling of Sec. 5.1, the MSE loss of Eq. 5 and an
  *     Adam step (Sec. 6.1).
  *   - Philox4x32-10 (Salmon et al., SC'11) for the training batch draws.
+ *   - BC6H mode-10 block encoder for partition selection and the initial
+ *     block parameters (Sec. 4.4: compress unconstrained features with the
+ *     BC6 algorithm): per-partition principal-axis line fit, 6-bit / 3-bit
+ *     quantisation, minimum-error partition.
  *
  * Parity unpinned: the bicubic kernel choice (Catmull-Rom) for the
  * reference sampling and the LOD-input convention are readings of text the
@@ -1337,4 +1344,241 @@ void oracle_train_backward_given(const oracle_train_features *F, const oracle_tr
     int nout = P->dims[P->n_layers];
     for (int64_t q = 0; q < n; ++q)
         train_query_ext(F, P, NULL, u[q], v[q], s[q], 0, 0.0, G, grad_out + q * nout, NULL);
+}
+
+/* ------------------------------------------------------------------------- */
+/* BC6H mode-10 block encoder: partition selection and initial block         */
+/* parameters from free per-texel features (Sec. 4.4)                         */
+/* ------------------------------------------------------------------------- */
+/*
+ * The paper initialises the block parameters and fixes the partitions by
+ * compressing a quickly trained set of unconstrained features with the BC6
+ * algorithm.  The encoder here, per block and for each of the 32 two-region
+ * partitions:
+ *   1. maps the 16 target texels to the integer domain in which the format
+ *      interpolates (the binary16 bit pattern of the value, 0 .. 0x7BFF);
+ *   2. fits a line to each region there: the region's mean, its 3 x 3
+ *      scatter matrix, the principal axis by 8 power iterations started from
+ *      the scatter column of the largest diagonal entry, and the segment
+ *      spanned by the smallest and largest projections onto the axis;
+ *   3. quantises both segment ends to 6-bit endpoints by inverting the
+ *      unquantise (1024 e + 512) and finish (x 31/64) steps;
+ *   4. gives each texel the 3-bit index whose decoded value is closest
+ *      (squared error over RGB in value space);
+ * and keeps the partition with the smallest total error.
+ *
+ * Precision: the method fixes none for this heuristic.  Every value that
+ * decides an integer here (a quantised endpoint, an index, the partition)
+ * is computed in IEEE single precision with one fixed order of operations
+ * and no fused multiply-add, which is also how the GPU encoder computes
+ * them, so both take the same decisions; ties go to the smaller index and
+ * the smaller partition number.
+ */
+
+/* binary16 bit pattern of a non-negative, representable half value */
+static uint16_t half_bits_of(double h)
+{
+    if (h <= 0.0)
+        return 0;
+    int e = (int)floor(log2(h));
+    if (e < -14)
+        return (uint16_t)nearbyint(h / ldexp(1.0, -24));
+    /* guard the exact powers of two against log2 rounding */
+    if (ldexp(1.0, e) > h)
+        --e;
+    if (ldexp(1.0, e + 1) <= h)
+        ++e;
+    return (uint16_t)(((e + 15) << 10) | (int)nearbyint((h / ldexp(1.0, e) - 1.0) * 1024.0));
+}
+
+/* the interpolation-domain coordinate of a target value: its half bit pattern, 0 for v <= 0 or NaN,
+ * 0x7BFF (the largest finite half) above the range */
+static float enc_coord(float v)
+{
+    if (!(v > 0.0f))
+        return 0.0f;
+    double h = oracle_round_half((double)v);
+    if (!(h <= 65504.0))
+        return 31743.0f;
+    return (float)half_bits_of(h);
+}
+
+/* decoded value of a mode-10 texel with 6-bit endpoints a, b (one channel) and 3-bit index i */
+static float enc_texel_value(int a, int b, int i)
+{
+    int ua = bc6h_unquantize(a, 6, 0), ub = bc6h_unquantize(b, 6, 0);
+    int w = k_weights3[i];
+    return (float)oracle_half_to_double(bc6h_finish(floor_div64(ua * (64 - w) + ub * w + 32), 0));
+}
+
+static int enc_quantise(float y)
+{
+    const float scale = 64.0f / 31.0f;
+    float q = rintf((y * scale - 512.0f) / 1024.0f);
+    return q < 0.0f ? 0 : (q > 63.0f ? 63 : (int)q);
+}
+
+/* line fit of one region of partition k; e[0] = segment start, e[1] = segment end (6-bit, RGB) */
+static void enc_fit_region(const float y[16][3], int k, int r, int e[2][3])
+{
+    float sum[3] = {0.0f, 0.0f, 0.0f};
+    int n = 0;
+    for (int t = 0; t < 16; ++t)
+        if (oracle_bc6h_partition_region(k, t) == r) {
+            for (int c = 0; c < 3; ++c)
+                sum[c] = sum[c] + y[t][c];
+            ++n;
+        }
+    float m[3];
+    for (int c = 0; c < 3; ++c)
+        m[c] = n ? sum[c] / (float)n : 0.0f;
+    float C[3][3] = {{0.0f}};
+    for (int t = 0; t < 16; ++t)
+        if (oracle_bc6h_partition_region(k, t) == r) {
+            float d[3];
+            for (int c = 0; c < 3; ++c)
+                d[c] = y[t][c] - m[c];
+            for (int i = 0; i < 3; ++i)
+                for (int j = i; j < 3; ++j) {
+                    float p = d[i] * d[j];
+                    C[i][j] = C[i][j] + p;
+                }
+        }
+    C[1][0] = C[0][1];
+    C[2][0] = C[0][2];
+    C[2][1] = C[1][2];
+    int jm = 0;
+    if (C[1][1] > C[jm][jm])
+        jm = 1;
+    if (C[2][2] > C[jm][jm])
+        jm = 2;
+    float A[3], B[3];
+    if (C[jm][jm] > 0.0f) {
+        float a[3] = {C[0][jm], C[1][jm], C[2][jm]};
+        for (int it = 0; it < 8; ++it) {
+            float b[3];
+            for (int i = 0; i < 3; ++i) {
+                float p0 = C[i][0] * a[0], p1 = C[i][1] * a[1], p2 = C[i][2] * a[2];
+                b[i] = (p0 + p1) + p2;
+            }
+            float s = fabsf(b[0]);
+            if (fabsf(b[1]) > s)
+                s = fabsf(b[1]);
+            if (fabsf(b[2]) > s)
+                s = fabsf(b[2]);
+            if (!(s > 0.0f))
+                break;
+            for (int i = 0; i < 3; ++i)
+                a[i] = b[i] / s;
+        }
+        float q0 = a[0] * a[0], q1 = a[1] * a[1], q2 = a[2] * a[2];
+        float aa = (q0 + q1) + q2;
+        float pmin = INFINITY, pmax = -INFINITY;
+        for (int t = 0; t < 16; ++t)
+            if (oracle_bc6h_partition_region(k, t) == r) {
+                float d0 = y[t][0] - m[0], d1 = y[t][1] - m[1], d2 = y[t][2] - m[2];
+                float p0 = d0 * a[0], p1 = d1 * a[1], p2 = d2 * a[2];
+                float p = (p0 + p1) + p2;
+                if (p < pmin)
+                    pmin = p;
+                if (p > pmax)
+                    pmax = p;
+            }
+        float s0 = pmin / aa, s1 = pmax / aa;
+        for (int c = 0; c < 3; ++c) {
+            float o0 = s0 * a[c], o1 = s1 * a[c];
+            A[c] = m[c] + o0;
+            B[c] = m[c] + o1;
+        }
+    } else {
+        for (int c = 0; c < 3; ++c)
+            A[c] = B[c] = m[c];
+    }
+    for (int c = 0; c < 3; ++c) {
+        e[0][c] = enc_quantise(A[c]);
+        e[1][c] = enc_quantise(B[c]);
+    }
+}
+
+/* squared error (RGB, value space) of texel t's target against index i of the segment e */
+static float enc_texel_error(const int e[2][3], int i, const float *v)
+{
+    float d[3];
+    for (int c = 0; c < 3; ++c)
+        d[c] = enc_texel_value(e[0][c], e[1][c], i) - v[c];
+    float q0 = d[0] * d[0], q1 = d[1] * d[1], q2 = d[2] * d[2];
+    return (q0 + q1) + q2;
+}
+
+/* Encode one block: v[3 t + c] = target of texel t (row-major in the block), channel c.  Outputs the block
+ * parameters in the training layout (e1, e2 = region-0 segment, e3, e4 = region-1 segment, RGB each, then
+ * x_t = index / 7), the partition, its total error and the total error of every partition. */
+void oracle_encode_mode10_block(const float *v, double params[28], int *k_out, float *err_out, float errs[32])
+{
+    float y[16][3];
+    for (int t = 0; t < 16; ++t)
+        for (int c = 0; c < 3; ++c)
+            y[t][c] = enc_coord(v[3 * t + c]);
+    float best = INFINITY;
+    int best_k = 0, best_e[2][2][3] = {{{0}}}, best_idx[16] = {0};
+    for (int k = 0; k < 32; ++k) {
+        int e[2][2][3];
+        enc_fit_region(y, k, 0, e[0]);
+        enc_fit_region(y, k, 1, e[1]);
+        float total = 0.0f;
+        int idx[16];
+        for (int t = 0; t < 16; ++t) {
+            int r = oracle_bc6h_partition_region(k, t);
+            float be = INFINITY;
+            int bi = 0;
+            for (int i = 0; i < 8; ++i) {
+                float err = enc_texel_error((const int(*)[3])e[r], i, v + 3 * t);
+                if (err < be) {
+                    be = err;
+                    bi = i;
+                }
+            }
+            idx[t] = bi;
+            total = total + be;
+        }
+        if (errs)
+            errs[k] = total;
+        float key = isnan(total) ? INFINITY : total; /* a NaN total never wins over a number */
+        if (key < best || k == 0) {
+            best = key;
+            *err_out = total;
+            best_k = k;
+            memcpy(best_e, e, sizeof e);
+            memcpy(best_idx, idx, sizeof idx);
+        }
+    }
+    for (int r = 0; r < 2; ++r)
+        for (int s = 0; s < 2; ++s)
+            for (int c = 0; c < 3; ++c)
+                params[(2 * r + s) * 3 + c] = (double)best_e[r][s][c];
+    for (int t = 0; t < 16; ++t)
+        params[12 + t] = best_idx[t] / 7.0;
+    *k_out = best_k;
+}
+
+/* Encode a mipmapped texture: texels[level][W][W][3] (levels concatenated from level 0), blocks in the
+ * training order (per level, row-major).  params[blocks][28], part[blocks], err[blocks]. */
+void oracle_encode_mode10_texture(const float *texels, int res, int levels, double *params, uint8_t *part, float *err)
+{
+    int64_t toff = 0, b = 0;
+    for (int l = 0; l < levels; ++l) {
+        int W = res >> l, wb = W / 4;
+        for (int by = 0; by < wb; ++by)
+            for (int bx = 0; bx < wb; ++bx, ++b) {
+                float v[48];
+                for (int j = 0; j < 4; ++j)
+                    for (int i = 0; i < 4; ++i)
+                        for (int c = 0; c < 3; ++c)
+                            v[3 * (4 * j + i) + c] = texels[toff + ((int64_t)(4 * by + j) * W + (4 * bx + i)) * 3 + c];
+                int k;
+                oracle_encode_mode10_block(v, params + b * 28, &k, err + b, NULL);
+                part[b] = (uint8_t)k;
+            }
+        toff += (int64_t)W * W * 3;
+    }
 }

@@ -728,3 +728,78 @@ def test_adam_first_step_closed_form_and_torch():
     p = np.full(4, 62.999)
     oracle.adam(p, np.full(4, -1.0), np.zeros(4), np.zeros(4), 0, 1.0, 1.0, lo=0.0, hi=63.0)
     assert (p == 63.0).all()
+
+
+# --------------------------------------------------------------------------- mode-10 encoder (Sec. 4.4)
+
+def _decoded_block(p, k):
+    """Values of a mode-10 block through the format decoder (export, then decode): [16][3]."""
+    mode, tex = oracle.bc6h_decode_block(oracle.train_export_block(p, k))
+    assert mode == 10
+    return np.array([[oracle.half_to_double(int(tex[t, c])) for c in range(3)] for t in range(16)])
+
+
+def _exact_block(rng, k):
+    """Random mode-10 lattice block whose regions each use index 0 and index 7 (a segment the encoder's line
+    fit can see end to end), endpoints at least 8 lattice steps apart in some channel."""
+    p = np.zeros(28)
+    while True:
+        e = rng.integers(0, 64, (4, 3))
+        if all(np.abs(e[2 * r] - e[2 * r + 1]).max() >= 8 for r in range(2)):
+            break
+    p[:12] = e.reshape(-1)
+    idx = rng.integers(0, 8, 16)
+    for r in range(2):
+        ts = [t for t in range(16) if oracle.bc6h_partition_region(k, t) == r]
+        i0, i1 = rng.choice(ts, 2, replace=False)
+        idx[i0], idx[i1] = 0, 7
+    p[12:] = idx / 7.0
+    return p
+
+
+def test_encoder_recovers_exactly_encodable_blocks():
+    """A block that is itself a mode-10 encoding is reproduced with zero error: the decoded texels of the
+    encoder's output (through the format decoder) equal the targets bit for bit."""
+    rng = np.random.default_rng(101)
+    for b in range(96):
+        k0 = b % 32
+        target = _decoded_block(_exact_block(rng, k0), k0)
+        p, k, err, errs = oracle.encode_mode10_block(target.astype(np.float32))
+        assert err == 0.0 and errs[k] == 0.0 and errs.min() == 0.0, (b, err)
+        assert np.array_equal(_decoded_block(p, k), target), b
+        if (errs == 0.0).sum() == 1:  # the generating partition is the only exact one
+            assert k == k0
+
+
+def test_encoder_constant_block_and_ties():
+    """A constant block of a decodable value: every partition is exact, the first one is chosen."""
+    for e in (0, 17, 63):
+        p0 = np.zeros(28)
+        p0[:12] = e
+        target = _decoded_block(p0, 0)
+        p, k, err, errs = oracle.encode_mode10_block(target.astype(np.float32))
+        assert k == 0 and err == 0.0 and not errs.any()
+        assert np.array_equal(_decoded_block(p, k), target)
+
+
+def test_encoder_error_is_the_decoded_error_and_indices_are_optimal():
+    """On arbitrary targets the reported error is the squared error of the block the format decoder
+    reconstructs from the encoder's output, every index is the best of the 8 for its endpoints, and the
+    chosen partition has the smallest error of the 32."""
+    rng = np.random.default_rng(102)
+    for b in range(40):
+        target = (rng.random((16, 3)) * rng.choice([0.05, 1.0, 30.0])).astype(np.float32)
+        p, k, err, errs = oracle.encode_mode10_block(target)
+        dec = _decoded_block(p, k)
+        ref = ((dec - target.astype(np.float64)) ** 2).sum()
+        assert err == pytest.approx(ref, rel=2e-6, abs=1e-12)
+        assert errs[k] == err and err == errs.min() and k == int(np.argmin(errs))
+        for t in range(16):
+            best = None
+            for i in range(8):
+                q = p.copy()
+                q[12 + t] = i / 7.0
+                e_t = ((_decoded_block(q, k)[t] - target[t].astype(np.float64)) ** 2).sum()
+                best = e_t if best is None else min(best, e_t)
+            got = ((dec[t] - target[t].astype(np.float64)) ** 2).sum()
+            assert got <= best * (1 + 1e-6) + 1e-12, (b, t)
