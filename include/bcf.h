@@ -365,6 +365,43 @@ bcf_status bcf_train_step_noalloc(bcf_trainer tr, int64_t batch, uint64_t seed, 
  */
 bcf_status bcf_train_export(bcf_trainer tr, void *const *d_blocks_out, uint16_t *d_weights_fp16, bcf_stream stream);
 
+/* ---------------------------------------------- partition selection encoder */
+
+/*
+ * bcf_encode_mode10 -- compress a mipmapped RGB feature texture into BC6H
+ * mode-10 block parameters (Sec. 4.4: after a short training of unconstrained
+ * features, compressing them with the BC6 algorithm fixes each block's
+ * partition and initialises its endpoints and indices).
+ *
+ * Per block, every one of the 32 two-region partitions is tried: a line is
+ * fitted to each region in the format's interpolation domain (the half bit
+ * pattern of the value; principal axis of the region's scatter matrix, the
+ * segment between the extreme projections), its ends are quantised to 6-bit
+ * endpoints, every texel takes the 3-bit index with the smallest squared RGB
+ * error of the decoded value, and the partition with the smallest total
+ * error is kept (ties: the smaller partition number).  All decisions are
+ * computed in IEEE single precision in a fixed order, so the result is
+ * reproducible.
+ *
+ * d_texels : level 0 .. levels-1 concatenated, each [W][W][3] float32 with
+ *            W = res >> level (RGB per texel, row-major), 16-byte aligned.
+ * res      : level-0 width, a power of two in [4, 32768]; levels in
+ *            [1, log2(res) - 1] (down to at most one 4 x 4 block).
+ * d_params : [blocks][32] float32, the block-parameter record of
+ *            bcf_trainer_desc ([0..5] region-0 endpoints e_a RGB, e_b RGB,
+ *            [8..13] region 1, [16..31] index / 7 per texel, pads 0);
+ *            blocks = sum over levels of (W / 4)^2, in the trainer's order
+ *            (per level, row-major).  16-byte aligned.
+ * d_partitions: [blocks] partition numbers (0..31).
+ * d_errors : [blocks] float32 total squared error of the chosen encoding,
+ *            or NULL.
+ * Caller-owned buffers; asynchronous on `stream`; no allocation.
+ * Errors: BCF_ERR_INVALID_ARG for an invalid size or level count, or a null
+ * or misaligned pointer.
+ */
+bcf_status bcf_encode_mode10(const float *d_texels, int32_t res, int32_t levels, float *d_params,
+                             uint8_t *d_partitions, float *d_errors, bcf_stream stream);
+
 /*
  * bcf_set_decode_variant -- choose the kernel bcf_decode_material uses for a
  * tensor-core (FP16 / BF16 / FP8) material.  0 (default): tile-cooperative

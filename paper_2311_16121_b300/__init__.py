@@ -109,6 +109,8 @@ def lib() -> ctypes.CDLL:
         L.bcf_train_backward.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p]
         L.bcf_train_export.restype = c_int
         L.bcf_train_export.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
+        L.bcf_encode_mode10.restype = c_int
+        L.bcf_encode_mode10.argtypes = [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]
         _lib = L
     return _lib
 
@@ -143,6 +145,31 @@ def decode_bc6h(blocks: torch.Tensor, blocks_w: int, blocks_h: int, is_signed: b
     _check(lib().bcf_decode_bc6h(_ptr(blocks), blocks_w, blocks_h, int(is_signed), _ptr(out), _stream()),
            "bcf_decode_bc6h")
     return out
+
+
+def texture_blocks(res: int, levels: int) -> int:
+    """Blocks of a mipmapped texture of `levels` levels from res x res (sum of (W / 4)^2)."""
+    return sum(((res >> l) // 4) ** 2 for l in range(levels))
+
+
+def encode_mode10(texels: torch.Tensor, res: int, levels: int, params: torch.Tensor | None = None,
+                  partitions: torch.Tensor | None = None, errors: torch.Tensor | None = None):
+    """bcf_encode_mode10: RGB texels (levels concatenated, float32) -> block parameters [blocks][32],
+    partitions [blocks] uint8 and per-block squared errors [blocks]."""
+    nb = texture_blocks(res, levels)
+    n_tex = sum(3 * (res >> l) ** 2 for l in range(levels))
+    if texels.dtype != torch.float32 or texels.numel() < n_tex:
+        raise ValueError(f"encode_mode10: texels must be float32 with at least {n_tex} values")
+    for t, shape_n, dt in ((params, nb * 32, torch.float32), (partitions, nb, torch.uint8), (errors, nb, torch.float32)):
+        if t is not None and (t.dtype != dt or t.numel() < shape_n):
+            raise ValueError(f"encode_mode10: output of {shape_n} {dt} values expected")
+    dev = texels.device
+    params = torch.empty((nb, 32), dtype=torch.float32, device=dev) if params is None else params
+    partitions = torch.empty(nb, dtype=torch.uint8, device=dev) if partitions is None else partitions
+    errors = torch.empty(nb, dtype=torch.float32, device=dev) if errors is None else errors
+    _check(lib().bcf_encode_mode10(_ptr(texels), int(res), int(levels), _ptr(params), _ptr(partitions),
+                                   _ptr(errors), _stream()), "bcf_encode_mode10")
+    return params, partitions, errors
 
 
 def texunit_decode_bc6h(blocks: torch.Tensor, blocks_w: int, blocks_h: int, is_signed: bool = False) -> torch.Tensor:

@@ -1,0 +1,130 @@
+"""GPU parity of the BC6H mode-10 partition-selection encoder (Sec. 4.4)
+against the CPU oracle: block parameters, partitions and errors are
+compared bit for bit (both take every decision in IEEE single precision in
+the same order)."""
+import zlib
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def _bcf():
+    import paper_2311_16121_b300 as bcf
+
+    bcf.lib()
+    return bcf
+
+
+def _level_texels(rng, W, kind):
+    if kind == "noise":
+        return rng.random((W, W, 3), dtype=np.float32)
+    if kind == "smooth":
+        y, x = np.meshgrid(np.arange(W), np.arange(W), indexing="ij")
+        f = [np.sin(x * a + y * b + c) for a, b, c in rng.uniform(0.05, 0.6, (3, 3))]
+        return (0.5 + 0.4 * np.stack(f, -1)).astype(np.float32)
+    if kind == "wide":  # values across the half range, zeros, negatives, above the range
+        v = np.exp(rng.uniform(-12, 11.5, (W, W, 3))).astype(np.float32)
+        v[rng.random((W, W, 3)) < 0.05] = 0.0
+        v[rng.random((W, W, 3)) < 0.05] *= -1.0
+        v[rng.random((W, W, 3)) < 0.01] = 70000.0
+        return v
+    if kind == "exact":  # every block a mode-10 lattice block (the encoder reproduces them exactly)
+        out = np.zeros((W, W, 3), np.float32)
+        for by in range(W // 4):
+            for bx in range(W // 4):
+                k = int(rng.integers(0, 32))
+                while True:  # both segment ends used in each region, ends apart: the line fit sees the segment
+                    e = rng.integers(0, 64, (4, 3))
+                    if all(np.abs(e[2 * r] - e[2 * r + 1]).max() >= 8 for r in range(2)):
+                        break
+                idx = rng.integers(0, 8, 16)
+                for r in range(2):
+                    ts = [t for t in range(16) if oracle.bc6h_partition_region(k, t) == r]
+                    i0, i1 = rng.choice(ts, 2, replace=False)
+                    idx[i0], idx[i1] = 0, 7
+                p = np.concatenate([e.reshape(-1), idx / 7.0])
+                mode, tex = oracle.bc6h_decode_block(oracle.train_export_block(p, k))
+                vals = np.array([[oracle.half_to_double(int(tex[t, c])) for c in range(3)] for t in range(16)])
+                out[4 * by:4 * by + 4, 4 * bx:4 * bx + 4] = vals.reshape(4, 4, 3)
+        return out
+    if kind == "constant":
+        return np.full((W, W, 3), rng.random(3, dtype=np.float32), np.float32)
+    raise ValueError(kind)
+
+
+def _texture(rng, res, levels, kinds):
+    return np.concatenate([_level_texels(rng, res >> l, kinds[l % len(kinds)]).reshape(-1) for l in range(levels)])
+
+
+def _compare(bcf, tex, res, levels):
+    p, part, err = bcf.encode_mode10(torch.from_numpy(tex).cuda(), res, levels)
+    p, part, err = p.cpu().numpy(), part.cpu().numpy(), err.cpu().numpy()
+    rp, rpart, rerr = oracle.encode_mode10_texture(tex, res, levels)
+    np.testing.assert_array_equal(part, rpart)
+    np.testing.assert_array_equal(err, rerr)
+    got28 = np.concatenate([p[:, 0:6], p[:, 8:14], p[:, 16:32]], axis=1)
+    np.testing.assert_array_equal(got28, rp.astype(np.float32))
+    assert not p[:, [6, 7, 14, 15]].any()
+    return part, err
+
+
+@pytest.mark.parametrize("kinds", [("noise",), ("smooth", "wide"), ("exact", "constant", "noise")])
+def test_encoder_matches_oracle_bit_for_bit(kinds):
+    bcf = _bcf()
+    rng = np.random.default_rng(zlib.crc32("/".join(kinds).encode()))
+    res, levels = 64, 5
+    tex = _texture(rng, res, levels, kinds)
+    part, err = _compare(bcf, tex, res, levels)
+    if kinds[0] == "exact":  # level 0 is all exact blocks: zero error everywhere there
+        assert not err[:256].any()
+
+
+def test_encoder_edge_sizes():
+    bcf = _bcf()
+    rng = np.random.default_rng(7)
+    for res, levels in ((4, 1), (8, 1), (8, 2), (16, 3)):
+        _compare(bcf, _texture(rng, res, levels, ("noise", "smooth")), res, levels)
+
+
+def test_encoder_full_size_sampled():
+    """4 x 1024^2 with 9 levels (87,381 blocks per texture): sampled blocks against the oracle."""
+    bcf = _bcf()
+    rng = np.random.default_rng(8)
+    res, levels = 1024, 9
+    tex = _texture(rng, res, levels, ("smooth", "noise"))
+    p, part, err = (a.cpu().numpy() for a in bcf.encode_mode10(torch.from_numpy(tex).cuda(), res, levels))
+    nb = oracle.texture_blocks(res, levels)
+    assert p.shape == (nb, 32)
+    # level offsets of the blocks and of the texels
+    boffs, toffs, b, t = [], [], 0, 0
+    for l in range(levels):
+        W = res >> l
+        boffs.append(b)
+        toffs.append(t)
+        b += (W // 4) ** 2
+        t += W * W * 3
+    for bi in rng.choice(nb, 600, replace=False):
+        l = max(i for i in range(levels) if boffs[i] <= bi)
+        W = res >> l
+        by, bx = divmod(int(bi - boffs[l]), W // 4)
+        img = tex[toffs[l]:toffs[l] + W * W * 3].reshape(W, W, 3)
+        blk = img[4 * by:4 * by + 4, 4 * bx:4 * bx + 4].reshape(16, 3)
+        rp, rk, rerr, _ = oracle.encode_mode10_block(blk)
+        assert part[bi] == rk and err[bi] == np.float32(rerr), bi
+        np.testing.assert_array_equal(np.concatenate([p[bi, 0:6], p[bi, 8:14], p[bi, 16:32]]), rp.astype(np.float32))
+
+
+def test_encoder_rejects_bad_arguments():
+    bcf = _bcf()
+    tex = torch.zeros(2 * 64 * 64 * 3, device="cuda")
+    with pytest.raises(bcf.BcfError):
+        bcf.encode_mode10(tex, 64, 6)  # 64 -> at most 5 levels
+    with pytest.raises(bcf.BcfError):
+        bcf.encode_mode10(tex[1:], 64, 1)  # misaligned
+    with pytest.raises(ValueError):
+        bcf.encode_mode10(tex[:100], 64, 1)  # too few texels
