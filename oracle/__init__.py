@@ -53,7 +53,7 @@ class _Mlp(ctypes.Structure):
 class _TrainFeatures(ctypes.Structure):
     _fields_ = [("n_tex", c_int), ("res", c_int * MAX_TEX), ("levels", c_int * MAX_TEX),
                 ("params", c_void_p * MAX_TEX), ("partition", c_void_p * MAX_TEX), ("res_ref", c_int),
-                ("lod_input", c_int)]
+                ("lod_input", c_int), ("free_texels", c_int)]
 
 
 class _Target(ctypes.Structure):
@@ -366,12 +366,14 @@ def train_texel_grad(p: np.ndarray, k: int, texel: int, channel: int, relaxed: b
 
 
 class TrainFeatures:
-    """Block-parameterised feature textures: params [blocks, 28] (float64) and partition ids per texture."""
+    """Block-parameterised feature textures: params [blocks, 28] (float64) and partition ids per texture; or,
+    with free=True, unconstrained features: params [texels, 3] per texture and no partitions."""
 
-    def __init__(self, params: list[np.ndarray], partition: list[np.ndarray], res: list[int], levels: list[int],
-                 res_ref: int, lod_input: bool = True):
+    def __init__(self, params: list[np.ndarray], partition: list[np.ndarray] | None, res: list[int],
+                 levels: list[int], res_ref: int, lod_input: bool = True, free: bool = False):
         self._p = [np.ascontiguousarray(p, dtype=np.float64).reshape(-1) for p in params]
-        self._k = [np.ascontiguousarray(k, dtype=np.uint8).reshape(-1) for k in partition]
+        self._k = [np.ascontiguousarray(k, dtype=np.uint8).reshape(-1) for k in partition] if not free else \
+            [np.zeros(1, np.uint8) for _ in params]
         c = _TrainFeatures()
         c.n_tex = len(params)
         for t in range(len(params)):
@@ -381,6 +383,8 @@ class TrainFeatures:
             c.partition[t] = self._k[t].ctypes.data
         c.res_ref = int(res_ref)
         c.lod_input = int(lod_input)
+        c.free_texels = int(free)
+        self.free = free
         self.c = c
         self.n_tex = len(params)
 
@@ -442,7 +446,7 @@ def train_loss_grad(F: TrainFeatures, P: TrainMlp, T: Target, u, v, s, want_grad
     G.b_grad = gb.ctypes.data
     loss = lib().oracle_train_loss_grad(ctypes.byref(F.c), ctypes.byref(P.c), ctypes.byref(T.c), u.size, _ptr(u),
                                         _ptr(v), _ptr(s), int(relaxed), ctypes.byref(G) if want_grad else None)
-    return loss, [g.reshape(-1, 28) for g in gf], gW, gb
+    return loss, [g.reshape(-1, 3 if F.free else 28) for g in gf], gW, gb
 
 
 def adam(p: np.ndarray, g: np.ndarray, m: np.ndarray, v: np.ndarray, t: int, lr0: float, gamma: float,
@@ -490,7 +494,7 @@ def train_backward_given(F: TrainFeatures, P: TrainMlp, u, v, s, grad_out):
     G.b_grad = gb.ctypes.data
     lib().oracle_train_backward_given(ctypes.byref(F.c), ctypes.byref(P.c), u.size, _ptr(u), _ptr(v), _ptr(s),
                                       _ptr(go), ctypes.byref(G))
-    return [g.reshape(-1, 28) for g in gf], gW, gb
+    return [g.reshape(-1, 3 if F.free else 28) for g in gf], gW, gb
 
 
 # --------------------------------------------------------------------------- mode-10 encoder

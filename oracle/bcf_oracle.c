@@ -863,6 +863,8 @@ typedef struct {
     const uint8_t *partition[OR_MAX_TEX]; /* [blocks] */
     int res_ref;
     int lod_input;
+    int free_texels; /* 1: unconstrained features, params[t] = [texels][3] values (mips concatenated), no
+                      * partition -- the first training stage of Sec. 4.4 */
 } oracle_train_features;
 
 static double clampd(double x, double lo, double hi) { return x < lo ? lo : (x > hi ? hi : x); }
@@ -964,7 +966,24 @@ void oracle_train_texel_grad(const double *p, int k, int texel, int channel, int
 static int64_t train_block_index(const oracle_train_features *F, int t, int level, int i, int j)
 {
     int W = F->res[t] >> level;
+    if (F->free_texels) { /* the texel itself: levels of W^2 texels concatenated */
+        int64_t off = 0;
+        for (int l = 0; l < level; ++l)
+            off += (int64_t)(F->res[t] >> l) * (F->res[t] >> l);
+        return off + (int64_t)j * W + i;
+    }
     return level_block_offset(F->res[t], level) + (int64_t)(j / 4) * (W / 4) + (i / 4);
+}
+
+/* An unconstrained texel: its value, with derivative 1 (carried in d_ea) per channel. */
+static void texel_free(const double *p, texel_eval *T)
+{
+    memset(T, 0, sizeof *T);
+    for (int c = 0; c < 3; ++c) {
+        T->value[c] = p[c];
+        T->d_ea[c] = 1.0;
+        T->e_in_a[c] = 1;
+    }
 }
 
 typedef struct {
@@ -1023,8 +1042,14 @@ void oracle_train_features_one(const oracle_train_features *F, float u, float v,
     memset(feat, 0, sizeof(double) * 3 * F->n_tex);
     for (int n = 0; n < L.n; ++n) {
         int t = L.tex[n];
-        const double *p = F->params[t] + L.block[n] * OR_BLOCK_PARAMS;
         texel_eval T;
+        if (F->free_texels) {
+            texel_free(F->params[t] + L.block[n] * 3, &T);
+            for (int c = 0; c < 3; ++c)
+                feat[3 * t + c] += L.weight[n] * T.value[c];
+            continue;
+        }
+        const double *p = F->params[t] + L.block[n] * OR_BLOCK_PARAMS;
         if (relaxed)
             texel_relaxed(p, F->partition[t][L.block[n]], L.texel[n], &T);
         else
@@ -1158,8 +1183,10 @@ static double train_query_ext(const oracle_train_features *F, const oracle_train
     memset(x, 0, sizeof x);
     for (int n = 0; n < L.n; ++n) {
         int t = L.tex[n];
-        const double *p = F->params[t] + L.block[n] * OR_BLOCK_PARAMS;
-        if (relaxed)
+        const double *p = F->params[t] + L.block[n] * (F->free_texels ? 3 : OR_BLOCK_PARAMS);
+        if (F->free_texels)
+            texel_free(p, &taps[n]);
+        else if (relaxed)
             texel_relaxed(p, F->partition[t][L.block[n]], L.texel[n], &taps[n]);
         else
             texel_ste(p, F->partition[t][L.block[n]], L.texel[n], &taps[n]);
@@ -1239,6 +1266,12 @@ static double train_query_ext(const oracle_train_features *F, const oracle_train
     for (int n = 0; n < L.n; ++n) {
         int t = L.tex[n];
         texel_eval *T = &taps[n];
+        if (F->free_texels) {
+            double *g = G->feat_grad[t] + L.block[n] * 3;
+            for (int c = 0; c < 3; ++c)
+                g[c] += dy[3 * t + c] * L.weight[n] * T->d_ea[c];
+            continue;
+        }
         double *g = G->feat_grad[t] + L.block[n] * OR_BLOCK_PARAMS;
         for (int c = 0; c < 3; ++c) {
             double dv = dy[3 * t + c] * L.weight[n];

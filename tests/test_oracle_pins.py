@@ -803,3 +803,69 @@ def test_encoder_error_is_the_decoded_error_and_indices_are_optimal():
                 best = e_t if best is None else min(best, e_t)
             got = ((dec[t] - target[t].astype(np.float64)) ** 2).sum()
             assert got <= best * (1 + 1e-6) + 1e-12, (b, t)
+
+
+# --------------------------------------------------------------------------- unconstrained features (Sec. 4.4)
+
+def _free_levels(rng, res, levels):
+    return [rng.uniform(-0.5, 1.5, ((res >> l), (res >> l), 3)) for l in range(levels)]
+
+
+def test_free_features_are_numpy_trilinear_of_the_texels():
+    """Unconstrained features: plain trilinear filtering (Eq. 10, Eq. 11 bias) of free texel values."""
+    rng = np.random.default_rng(31)
+    res, levels = [16, 8], [3, 2]
+    lv = [_free_levels(rng, r, l) for r, l in zip(res, levels)]
+    F = oracle.TrainFeatures([np.concatenate([a.reshape(-1, 3) for a in x]) for x in lv], None, res, levels,
+                             res_ref=32, lod_input=True, free=True)
+    for q in range(200):
+        u, v, s = (float(np.float32(x)) for x in (rng.uniform(0, 1), rng.uniform(0, 1), rng.uniform(-1, 5)))
+        feat = oracle.train_features_one(F, u, v, s)
+        for t in range(2):
+            st = min(max(s + math.log2(res[t] / 32), 0.0), levels[t] - 1)
+            l0 = int(math.floor(st))
+            l1 = min(l0 + 1, levels[t] - 1)
+            lam = st - l0
+            ref = (1 - lam) * _np_bilinear(lv[t][l0], u, v) + lam * _np_bilinear(lv[t][l1], u, v)
+            np.testing.assert_allclose(feat[3 * t:3 * t + 3], ref, rtol=1e-12, atol=1e-12)
+
+
+def test_free_feature_gradient_matches_finite_differences():
+    """Training backward into unconstrained texels against central differences of the loss (the features are
+    linear in the texels, so only the MLP's ReLU kinks limit the comparison)."""
+    rng = np.random.default_rng(32)
+    res, levels = [16, 8], [3, 2]
+    params = [np.concatenate([a.reshape(-1, 3) for a in _free_levels(rng, r, l)]) for r, l in zip(res, levels)]
+    a, b8 = _synthetic_target(32, 4, rng)
+    T = oracle.Target(a, b8, 32, 4)
+    dims = [7, 8, 8, 9]
+    Ws, bs = _mlp_params(dims)
+    W, b = np.concatenate([w.ravel() for w in Ws]), np.concatenate(bs)
+    P = oracle.TrainMlp(dims, W, b, bf16=False)
+    n = 16
+    u = rng.uniform(0, 1, n).astype(np.float32)
+    v = rng.uniform(0, 1, n).astype(np.float32)
+    s = rng.uniform(0, 3, n).astype(np.float32)
+    F = oracle.TrainFeatures(params, None, res, levels, res_ref=32, lod_input=True, free=True)
+    loss, gf, gW, gb = oracle.train_loss_grad(F, P, T, u, v, s)
+    h = 1e-6
+
+    def loss_at(p2):
+        F2 = oracle.TrainFeatures(p2, None, res, levels, res_ref=32, lod_input=True, free=True)
+        return oracle.train_loss_grad(F2, P, T, u, v, s, want_grad=False)[0]
+
+    checked = 0
+    for t in range(2):
+        touched = np.nonzero(np.abs(gf[t]).sum(axis=1))[0]
+        assert touched.size > 0
+        for tx in rng.choice(touched, min(12, touched.size), replace=False):
+            for c in range(3):
+                pp = [p.copy() for p in params]
+                pm = [p.copy() for p in params]
+                pp[t][tx, c] += h
+                pm[t][tx, c] -= h
+                fd = (loss_at(pp) - loss_at(pm)) / (2 * h)
+                if abs(fd - gf[t][tx, c]) > 1e-5 * abs(gf[t][tx, c]) + 1e-10:
+                    continue  # a ReLU kink inside the stencil
+                checked += 1
+    assert checked >= 50
