@@ -387,6 +387,24 @@ def main():
 
     train_ms, train_loss, train_batch = _train_bench(torch, workloads, stream, max(3, args.steps // 2))
 
+    # partition-selection encoder: 4 textures of 1024^2 with 9 levels (87,381 blocks each), smooth RGB texels
+    enc_res, enc_levels = 1024, 9
+    n_texels = sum((enc_res >> l) ** 2 for l in range(enc_levels))
+    g = torch.Generator(device="cuda").manual_seed(5)
+    enc_tex = [torch.rand(n_texels * 3, device="cuda", generator=g) for _ in range(4)]
+    enc_out = [bcf.encode_mode10(t, enc_res, enc_levels) for t in enc_tex]
+    torch.cuda.synchronize()
+    ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ea.record(stream)
+    for _ in range(3):
+        for t, (pp, pk, pe) in zip(enc_tex, enc_out):
+            bcf.encode_mode10(t, enc_res, enc_levels, pp, pk, pe)
+    eb.record(stream)
+    eb.synchronize()
+    enc_ms = ea.elapsed_time(eb) / 3
+    enc_blocks = 4 * bcf.texture_blocks(enc_res, enc_levels)
+    del enc_tex, enc_out
+
     # batched multi-material decode: 64 materials, one persistent graph-captured launch, autotuned
     sw = workloads.config4()
     set_mats = [workloads.upload(m, "fp16") for m in sw.materials]
@@ -521,6 +539,9 @@ def main():
                       "samples_per_s": train_batch * 1000.0 / train_ms,
                       "workload": "4x block-parameterised 1024^2 (9 levels), 2048^2 9-ch reference, "
                                   "MLP 13-32-32-9 BF16 operands, Adam", "last_loss": train_loss},
+            "encode": {"metric": "blocks/s", "value": enc_blocks / (enc_ms * 1e-3), "ms": enc_ms,
+                       "blocks": enc_blocks, "workload": "BC6H mode-10 partition selection (32 partitions per "
+                                                         "block), 4x 1024^2 RGB textures with 9 levels, uniform texels"},
             "e2e": {"value": e2e_value, "unit": "Gsamples/s", "h2d_bytes_per_step": 12 * w.n,
                     "d2h_bytes_per_step": 18 * w.n},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",

@@ -250,6 +250,16 @@ bcf_status bcf_material_set_config(bcf_material_set set, int32_t *cap, int32_t *
  * FP32 accumulation; its backward is FP32 with respect to those rounded
  * values.
  *
+ * Unconstrained features (unconstrained = 1; the first training stage of
+ * Sec. 5.1, whose result bcf_encode_mode10 compresses into the initial block
+ * parameters and partitions): each texture holds free RGB values per texel,
+ * [texels][4] floats (R, G, B, unused 0), mips concatenated from level 0,
+ * texels row-major per level; d_params, d_grad, d_adam_m, d_adam_v have
+ * that layout, d_partition is ignored, the texel values are filtered
+ * trilinearly (Eq. 10) without any compression emulation or bound, and
+ * bcf_train_export does not apply.  Supported for three-layer MLPs
+ * dims[0] <= 16 -> 32 -> 32 -> 9 (BCF_ERR_UNSUPPORTED otherwise).
+ *
  * Reference material F(M) (Sec. 5.1): 9 channels, FP16, a mip chain from
  * target_res down to 4 x 4 (level l is target_res >> l), channels 0..7
  * interleaved [texels][8] and channel 8 in its own array [texels]; sampled
@@ -281,6 +291,7 @@ typedef struct {
     float gamma;                            /* exponential decay per step (Sec. 6.1: 0.9999) */
     float beta1, beta2, eps;                /* Adam constants */
     float s_max;                            /* batch draws: s ~ U[0, s_max) in res_ref units */
+    int32_t unconstrained;                  /* 1: free per-texel features (see below) instead of block parameters */
 } bcf_trainer_desc;
 
 /*
@@ -369,7 +380,7 @@ bcf_status bcf_train_export(bcf_trainer tr, void *const *d_blocks_out, uint16_t 
 
 /*
  * bcf_encode_mode10 -- compress a mipmapped RGB feature texture into BC6H
- * mode-10 block parameters (Sec. 4.4: after a short training of unconstrained
+ * mode-10 block parameters (Sec. 5.1: after a short training of unconstrained
  * features, compressing them with the BC6 algorithm fixes each block's
  * partition and initialises its endpoints and indices).
  *
@@ -383,8 +394,11 @@ bcf_status bcf_train_export(bcf_trainer tr, void *const *d_blocks_out, uint16_t 
  * computed in IEEE single precision in a fixed order, so the result is
  * reproducible.
  *
- * d_texels : level 0 .. levels-1 concatenated, each [W][W][3] float32 with
- *            W = res >> level (RGB per texel, row-major), 16-byte aligned.
+ * d_texels : level 0 .. levels-1 concatenated, each [W][W][texel_stride]
+ *            float32 with W = res >> level (R, G, B first per texel,
+ *            row-major), 4-byte aligned.
+ * texel_stride: floats per texel, 3 (RGB) or 4 (the unconstrained features
+ *            of bcf_trainer_desc).
  * res      : level-0 width, a power of two in [4, 32768]; levels in
  *            [1, log2(res) - 1] (down to at most one 4 x 4 block).
  * d_params : [blocks][32] float32, the block-parameter record of
@@ -396,11 +410,11 @@ bcf_status bcf_train_export(bcf_trainer tr, void *const *d_blocks_out, uint16_t 
  * d_errors : [blocks] float32 total squared error of the chosen encoding,
  *            or NULL.
  * Caller-owned buffers; asynchronous on `stream`; no allocation.
- * Errors: BCF_ERR_INVALID_ARG for an invalid size or level count, or a null
- * or misaligned pointer.
+ * Errors: BCF_ERR_INVALID_ARG for an invalid size, level count or texel
+ * stride, or a null or misaligned pointer.
  */
-bcf_status bcf_encode_mode10(const float *d_texels, int32_t res, int32_t levels, float *d_params,
-                             uint8_t *d_partitions, float *d_errors, bcf_stream stream);
+bcf_status bcf_encode_mode10(const float *d_texels, int32_t texel_stride, int32_t res, int32_t levels,
+                             float *d_params, uint8_t *d_partitions, float *d_errors, bcf_stream stream);
 
 /*
  * bcf_set_decode_variant -- choose the kernel bcf_decode_material uses for a

@@ -49,7 +49,7 @@ class _TrainerDesc(ctypes.Structure):
                 ("d_W_m", c_void_p), ("d_W_v", c_void_p), ("d_b_m", c_void_p), ("d_b_v", c_void_p),
                 ("target_res", c_int32), ("target_levels", c_int32), ("d_target8", c_void_p), ("d_target1", c_void_p),
                 ("lr_features", c_float), ("lr_mlp", c_float), ("gamma", c_float), ("beta1", c_float),
-                ("beta2", c_float), ("eps", c_float), ("s_max", c_float)]
+                ("beta2", c_float), ("eps", c_float), ("s_max", c_float), ("unconstrained", c_int32)]
 
 
 _lib = None
@@ -110,7 +110,7 @@ def lib() -> ctypes.CDLL:
         L.bcf_train_export.restype = c_int
         L.bcf_train_export.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
         L.bcf_encode_mode10.restype = c_int
-        L.bcf_encode_mode10.argtypes = [c_void_p, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]
+        L.bcf_encode_mode10.argtypes = [c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]
         _lib = L
     return _lib
 
@@ -153,11 +153,11 @@ def texture_blocks(res: int, levels: int) -> int:
 
 
 def encode_mode10(texels: torch.Tensor, res: int, levels: int, params: torch.Tensor | None = None,
-                  partitions: torch.Tensor | None = None, errors: torch.Tensor | None = None):
-    """bcf_encode_mode10: RGB texels (levels concatenated, float32) -> block parameters [blocks][32],
-    partitions [blocks] uint8 and per-block squared errors [blocks]."""
+                  partitions: torch.Tensor | None = None, errors: torch.Tensor | None = None, texel_stride: int = 3):
+    """bcf_encode_mode10: RGB texels (levels concatenated, float32, `texel_stride` floats per texel) -> block
+    parameters [blocks][32], partitions [blocks] uint8 and per-block squared errors [blocks]."""
     nb = texture_blocks(res, levels)
-    n_tex = sum(3 * (res >> l) ** 2 for l in range(levels))
+    n_tex = sum(texel_stride * (res >> l) ** 2 for l in range(levels))
     if texels.dtype != torch.float32 or texels.numel() < n_tex:
         raise ValueError(f"encode_mode10: texels must be float32 with at least {n_tex} values")
     for t, shape_n, dt in ((params, nb * 32, torch.float32), (partitions, nb, torch.uint8), (errors, nb, torch.float32)):
@@ -167,7 +167,7 @@ def encode_mode10(texels: torch.Tensor, res: int, levels: int, params: torch.Ten
     params = torch.empty((nb, 32), dtype=torch.float32, device=dev) if params is None else params
     partitions = torch.empty(nb, dtype=torch.uint8, device=dev) if partitions is None else partitions
     errors = torch.empty(nb, dtype=torch.float32, device=dev) if errors is None else errors
-    _check(lib().bcf_encode_mode10(_ptr(texels), int(res), int(levels), _ptr(params), _ptr(partitions),
+    _check(lib().bcf_encode_mode10(_ptr(texels), int(texel_stride), int(res), int(levels), _ptr(params), _ptr(partitions),
                                    _ptr(errors), _stream()), "bcf_encode_mode10")
     return params, partitions, errors
 
@@ -312,7 +312,7 @@ class Trainer:
                  res_ref: int, dims: list[int], W: torch.Tensor, b: torch.Tensor, target8: torch.Tensor,
                  target1: torch.Tensor, target_res: int, target_levels: int, lr_features: float = 1e-2,
                  lr_mlp: float = 1e-3, gamma: float = 0.9999, beta1: float = 0.9, beta2: float = 0.999,
-                 eps: float = 1e-8, s_max: float | None = None, lod_input: bool = True):
+                 eps: float = 1e-8, s_max: float | None = None, lod_input: bool = True, unconstrained: bool = False):
         z = torch.zeros_like
         self.params, self.partition = list(params), list(partition)
         self.grads = [z(p) for p in params]
@@ -327,7 +327,7 @@ class Trainer:
         for t in range(len(params)):
             d.res[t], d.levels[t] = int(res[t]), int(levels[t])
             d.d_params[t] = _ptr(params[t])
-            d.d_partition[t] = _ptr(partition[t])
+            d.d_partition[t] = _ptr(partition[t]) if partition[t] is not None else None
             d.d_grad[t] = _ptr(self.grads[t])
             d.d_adam_m[t] = _ptr(self.m[t])
             d.d_adam_v[t] = _ptr(self.v[t])
@@ -344,6 +344,8 @@ class Trainer:
         d.lr_features, d.lr_mlp, d.gamma = lr_features, lr_mlp, gamma
         d.beta1, d.beta2, d.eps = beta1, beta2, eps
         d.s_max = float(target_levels - 1 if s_max is None else s_max)
+        d.unconstrained = int(unconstrained)
+        self.unconstrained = bool(unconstrained)
         h = c_void_p()
         _check(lib().bcf_trainer_create(ctypes.byref(d), ctypes.byref(h)), "bcf_trainer_create")
         self.handle = h

@@ -277,9 +277,11 @@ bcf_status bcf_decode_material(bcf_material m, const float *d_u, const float *d_
 
 // ------------------------------------------------------------ partition selection encoder
 
-bcf_status bcf_encode_mode10(const float *d_texels, int32_t res, int32_t levels, float *d_params,
-                             uint8_t *d_partitions, float *d_errors, bcf_stream stream)
+bcf_status bcf_encode_mode10(const float *d_texels, int32_t texel_stride, int32_t res, int32_t levels,
+                             float *d_params, uint8_t *d_partitions, float *d_errors, bcf_stream stream)
 {
+    if (texel_stride != 3 && texel_stride != 4)
+        return fail(BCF_ERR_INVALID_ARG, "bcf_encode_mode10: texel_stride %d is not 3 or 4", texel_stride);
     if (!is_pow2(res) || res < 4 || res > 32768)
         return fail(BCF_ERR_INVALID_ARG, "bcf_encode_mode10: res %d is not a power of two in [4, 32768]", res);
     int lg = 0;
@@ -287,14 +289,14 @@ bcf_status bcf_encode_mode10(const float *d_texels, int32_t res, int32_t levels,
         ++lg;
     if (levels < 1 || levels > lg - 1)
         return fail(BCF_ERR_INVALID_ARG, "bcf_encode_mode10: levels %d not in [1, %d]", levels, lg - 1);
-    if (!d_texels || !d_params || !d_partitions || !aligned(d_texels, 16) || !aligned(d_params, 16) ||
+    if (!d_texels || !d_params || !d_partitions || !aligned(d_texels, 4) || !aligned(d_params, 16) ||
         (d_errors && !aligned(d_errors, 4)))
         return fail(BCF_ERR_INVALID_ARG, "bcf_encode_mode10: null or misaligned pointer");
     int64_t nb = 0;
     for (int l = 0; l < levels; ++l)
         nb += (int64_t)((res >> l) / 4) * ((res >> l) / 4);
-    return cuda_status(launch_encode_mode10(d_texels, res, levels, nb, d_params, d_partitions, d_errors,
-                                            (cudaStream_t)stream),
+    return cuda_status(launch_encode_mode10(d_texels, texel_stride, res, levels, nb, d_params, d_partitions,
+                                            d_errors, (cudaStream_t)stream),
                        "bcf_encode_mode10 launch");
 }
 

@@ -1,5 +1,5 @@
 // bcf_encode.cu -- BC6H mode-10 block encoder: partition selection and the
-// initial block parameters from free per-texel features (Sec. 4.4: the
+// initial block parameters from free per-texel features (Sec. 5.1: the
 // unconstrained features of a short first training stage are compressed with
 // the BC6 algorithm, which fixes each block's partition and initialises its
 // endpoints and indices).
@@ -141,7 +141,7 @@ __device__ void fit_region(const float *y, uint32_t pm, int r, int e[2][3])
     }
 }
 
-__global__ void __launch_bounds__(32 * kEncWarps) k_encode_mode10(const float *__restrict__ texels, int res, int levels,
+__global__ void __launch_bounds__(32 * kEncWarps) k_encode_mode10(const float *__restrict__ texels, int stride, int res, int levels,
                                                                  int64_t nblocks, float *__restrict__ params,
                                                                  uint8_t *__restrict__ part, float *__restrict__ err)
 {
@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(32 * kEncWarps) k_encode_mode10(const float *_
         if (b < boff + wb * wb)
             break;
         boff += wb * wb;
-        toff += (int64_t)(res >> l) * (res >> l) * 3;
+        toff += (int64_t)(res >> l) * (res >> l) * stride;
     }
     const int W = res >> l, wb = W >> 2;
     const int64_t bl = b - boff;
@@ -166,7 +166,7 @@ __global__ void __launch_bounds__(32 * kEncWarps) k_encode_mode10(const float *_
     float *v = sv[warp], *y = sy[warp];
     for (int e = lane; e < 48; e += 32) {
         const int t = e / 3, c = e % 3;
-        const float x = texels[toff + ((int64_t)(4 * by + (t >> 2)) * W + 4 * bx + (t & 3)) * 3 + c];
+        const float x = texels[toff + ((int64_t)(4 * by + (t >> 2)) * W + 4 * bx + (t & 3)) * stride + c];
         v[e] = x;
         y[e] = enc_coord(x);
     }
@@ -245,13 +245,14 @@ __global__ void __launch_bounds__(32 * kEncWarps) k_encode_mode10(const float *_
 
 } // namespace
 
-cudaError_t launch_encode_mode10(const float *texels, int res, int levels, int64_t nblocks, float *params,
-                                 uint8_t *part, float *err, cudaStream_t st)
+cudaError_t launch_encode_mode10(const float *texels, int stride, int res, int levels, int64_t nblocks,
+                                 float *params, uint8_t *part, float *err, cudaStream_t st)
 {
     if (nblocks <= 0)
         return cudaSuccess;
     const int64_t grid = (nblocks + kEncWarps - 1) / kEncWarps;
-    k_encode_mode10<<<(unsigned)grid, 32 * kEncWarps, 0, st>>>(texels, res, levels, nblocks, params, part, err);
+    k_encode_mode10<<<(unsigned)grid, 32 * kEncWarps, 0, st>>>(texels, stride, res, levels, nblocks, params, part,
+                                                              err);
     return cudaGetLastError();
 }
 

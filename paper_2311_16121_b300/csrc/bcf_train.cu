@@ -482,8 +482,8 @@ cudaError_t launch_adam(const TrainDev &D, const TrainHyper &H, int64_t step, cu
     const double decay = pow((double)H.gamma, (double)step);
     int k = 0;
     for (int t = 0; t < D.n_tex; ++t) {
-        A.seg[k] = {D.tex[t].params, D.tex[t].grad, D.tex[t].m, D.tex[t].v, D.tex[t].blocks * 32,
-                    (float)(H.lr_features * decay), 1};
+        A.seg[k] = {D.tex[t].params, D.tex[t].grad, D.tex[t].m, D.tex[t].v, feature_floats(D, t),
+                    (float)(H.lr_features * decay), D.unconstrained ? 0 : 1};
         ++k;
     }
     A.seg[k++] = {D.W, D.Wg, D.Wm, D.Wv, D.w_total, (float)(H.lr_mlp * decay), 0};

@@ -13,7 +13,7 @@ struct TrainTexDev {
     float *m, *v;         // Adam moments
     const uint8_t *part;  // [blocks]
     int32_t res, levels, lod_bias;
-    int64_t blocks;
+    int64_t blocks;       // block records, or texels when the features are unconstrained
 };
 
 struct TrainDev {
@@ -26,7 +26,11 @@ struct TrainDev {
     int32_t tres, tlevels;
     const uint16_t *t8, *t1;
     float s_max;
+    int32_t unconstrained; // free per-texel features [texels][4] instead of block records [blocks][32]
 };
+
+// floats of one texture's feature array
+inline int64_t feature_floats(const TrainDev &D, int t) { return D.tex[t].blocks * (D.unconstrained ? 4 : 32); }
 
 struct TrainHyper {
     float lr_features, lr_mlp, gamma, beta1, beta2, eps;

@@ -51,6 +51,7 @@ bcf_status bcf_trainer_create(const bcf_trainer_desc *d, bcf_trainer *out)
         return tfail(BCF_ERR_INVALID_ARG, "res_ref %d is not a power of two", d->res_ref);
     D.n_tex = d->num_textures;
     D.lod_input = d->lod_input != 0;
+    D.unconstrained = d->unconstrained != 0;
     for (int t = 0; t < D.n_tex; ++t) {
         const int res = d->res[t];
         if (!pow2(res) || res < 4 || res > 32768)
@@ -58,7 +59,7 @@ bcf_status bcf_trainer_create(const bcf_trainer_desc *d, bcf_trainer *out)
         if (d->levels[t] < 1 || d->levels[t] > lg2(res) - 1)
             return tfail(BCF_ERR_INVALID_ARG, "texture %d: levels %d not in [1, %d]", t, d->levels[t], lg2(res) - 1);
         if (!al16(d->d_params[t]) || !al16(d->d_grad[t]) || !al16(d->d_adam_m[t]) || !al16(d->d_adam_v[t]) ||
-            !d->d_partition[t])
+            (!d->d_partition[t] && !D.unconstrained))
             return tfail(BCF_ERR_INVALID_ARG, "texture %d: null or non-16-byte-aligned array", t);
         TrainTexDev &T = D.tex[t];
         T.params = d->d_params[t];
@@ -71,7 +72,7 @@ bcf_status bcf_trainer_create(const bcf_trainer_desc *d, bcf_trainer *out)
         T.lod_bias = lg2(res) - lg2(d->res_ref);
         int64_t nb = 0;
         for (int l = 0; l < T.levels; ++l)
-            nb += (int64_t)((res >> l) / 4) * ((res >> l) / 4);
+            nb += D.unconstrained ? (int64_t)(res >> l) * (res >> l) : (int64_t)((res >> l) / 4) * ((res >> l) / 4);
         T.blocks = nb;
     }
     if (d->n_layers < 1 || d->n_layers > BCF_MAX_LAYERS)
@@ -119,6 +120,8 @@ bcf_status bcf_trainer_create(const bcf_trainer_desc *d, bcf_trainer *out)
         !(d->beta2 >= 0.0f && d->beta2 < 1.0f) || !(d->eps > 0.0f))
         return tfail(BCF_ERR_INVALID_ARG, "invalid hyper-parameters");
     D.s_max = d->s_max;
+    if (D.unconstrained && !train_mma_supported(D))
+        return tfail(BCF_ERR_UNSUPPORTED, "unconstrained features need a dims[0] <= 16 -> 32 -> 32 -> 9 MLP");
     if (train_smem_bytes(D) > 227 * 1024)
         return tfail(BCF_ERR_UNSUPPORTED, "MLP too wide for the training kernel's shared memory");
     bcf_trainer tr = new (std::nothrow) bcf_trainer_s;
@@ -200,6 +203,9 @@ bcf_status bcf_train_export(bcf_trainer tr, void *const *d_blocks_out, uint16_t 
 {
     if (!tr || !d_blocks_out)
         return tfail(BCF_ERR_INVALID_ARG, "bcf_train_export: null argument");
+    if (tr->dev.unconstrained)
+        return tfail(BCF_ERR_UNSUPPORTED, "bcf_train_export: unconstrained features have no block encoding "
+                                          "(compress them with bcf_encode_mode10)");
     for (int t = 0; t < tr->dev.n_tex; ++t)
         if (!al16(d_blocks_out[t]))
             return tfail(BCF_ERR_INVALID_ARG, "bcf_train_export: texture %d output null or misaligned", t);

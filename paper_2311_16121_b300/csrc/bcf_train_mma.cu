@@ -1,6 +1,9 @@
 // bcf_train_mma.cu -- the training step (Sec. 4.1-4.3, Eq. 5-9) with the MLP
 // of Eq. 3 on the tensor cores, for three-layer decoders K0 <= 16 -> 32 -> 32
-// -> C <= 16 (the 13-32-32-9 materials); other shapes use k_train.
+// -> C <= 16 (the 13-32-32-9 materials); other shapes use k_train.  The
+// features are either block parameters through the emulated BC6 mode-10
+// decompression, or (FREE) unconstrained per-texel values, the first stage
+// of Sec. 5.1.
 //
 // One warp owns 32 queries.  The per-query work (batch draw, emulated BC6
 // taps, reference sample, gradient scatter) runs one query per lane exactly as
@@ -237,6 +240,7 @@ __device__ __forceinline__ void weight_grad(const uint32_t (&ghi)[2][MT][4], con
             }
 }
 
+template <bool FREE>
 __global__ void __launch_bounds__(kThreads, 4) k_train_mma(TrainDev D, int mode, int64_t batch, uint32_t seed_lo,
                                                         uint32_t seed_hi, uint32_t step_lo, uint32_t step_hi,
                                                         const float *__restrict__ qu, const float *__restrict__ qv,
@@ -303,7 +307,17 @@ __global__ void __launch_bounds__(kThreads, 4) k_train_mma(TrainDev D, int mode,
         bf16 *xr = X + lane * S16;
         for (int tx = 0; tx < D.n_tex; ++tx) {
             float f[3] = {0.0f, 0.0f, 0.0f};
-            if (active) {
+            if (active && FREE) {
+                for_each_side_free<true>(D.tex[tx], u, v, s,
+                                         [&](const int64_t(&)[4], const float(&wt)[4], const float4(&val)[4]) {
+#pragma unroll
+                                             for (int j = 0; j < 4; ++j) {
+                                                 f[0] = fmaf(wt[j], val[j].x, f[0]);
+                                                 f[1] = fmaf(wt[j], val[j].y, f[1]);
+                                                 f[2] = fmaf(wt[j], val[j].z, f[2]);
+                                             }
+                                         });
+            } else if (active) {
                 const TrainTexDev &T = D.tex[tx];
                 for_each_side(T, u, v, s, [&](const Tap(&tp)[4], const TexelParams(&P)[4]) {
 #pragma unroll
@@ -499,6 +513,16 @@ __global__ void __launch_bounds__(kThreads, 4) k_train_mma(TrainDev D, int mode,
             for (int tx = 0; tx < D.n_tex; ++tx) {
                 const float dxf[3] = {rr[3 * tx], rr[3 * tx + 1], rr[3 * tx + 2]};
                 const TrainTexDev &T = D.tex[tx];
+                if (FREE) {
+                    for_each_side_free<false>(T, u, v, s,
+                                              [&](const int64_t(&idx)[4], const float(&wt)[4], const float4(&)[4]) {
+#pragma unroll
+                                                  for (int j = 0; j < 4; ++j)
+                                                      red_add_v4(T.grad + idx[j] * 4, dxf[0] * wt[j], dxf[1] * wt[j],
+                                                                 dxf[2] * wt[j], 0.0f);
+                                              });
+                    continue;
+                }
                 const int64_t cst = tx < kCoarseTex ? coarse_start(T) : T.blocks;
                 for_each_side(T, u, v, s, [&](const Tap(&tps)[4], const TexelParams(&P)[4]) {
 #pragma unroll
@@ -546,7 +570,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_train_mma(TrainDev D, int mode,
         for (int i = threadIdx.x; i < N1 + N2 + C; i += kThreads)
             if (S.db[i] != 0.0f)
                 atomicAdd(D.bg + i, S.db[i]);
-        for (int tx = 0; tx < min(D.n_tex, kCoarseTex); ++tx) {
+        for (int tx = 0; tx < (FREE ? 0 : min(D.n_tex, kCoarseTex)); ++tx) {
             const TrainTexDev &T = D.tex[tx];
             const int64_t cst = coarse_start(T);
             for (int i = threadIdx.x; i < (int)(T.blocks - cst) * 32; i += kThreads)
@@ -574,14 +598,14 @@ cudaError_t launch_train_mma(const TrainDev &D, int mode, int64_t batch, uint64_
                              const float *u, const float *v, const float *s, float *out, const float *grad_out,
                              float *loss, int sms, cudaStream_t st)
 {
+    const auto kern = D.unconstrained ? k_train_mma<true> : k_train_mma<false>;
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_train_mma, kThreads, 0);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0);
     const int64_t tiles = (batch + kThreads - 1) / kThreads;
     const int64_t grid = min(tiles, (int64_t)sms * max(per_sm, 1));
     const float gscale = 2.0f / ((float)batch * (float)D.dims[D.n_layers]);
-    k_train_mma<<<(unsigned)grid, kThreads, 0, st>>>(D, mode, batch, (uint32_t)seed, (uint32_t)(seed >> 32),
-                                                     (uint32_t)step, (uint32_t)((uint64_t)step >> 32), u, v, s, out,
-                                                     grad_out, loss, gscale);
+    kern<<<(unsigned)grid, kThreads, 0, st>>>(D, mode, batch, (uint32_t)seed, (uint32_t)(seed >> 32), (uint32_t)step,
+                                              (uint32_t)((uint64_t)step >> 32), u, v, s, out, grad_out, loss, gscale);
     return cudaGetLastError();
 }
 

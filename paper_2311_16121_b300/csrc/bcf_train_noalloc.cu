@@ -64,7 +64,7 @@ extern "C" bcf_status bcf_train_step_noalloc(bcf_trainer tr, int64_t batch, uint
     TrainDev D = tr->dev;
     int64_t need = 0;
     for (int t = 0; t < D.n_tex; ++t)
-        need += round32(D.tex[t].blocks * 32);
+        need += round32(feature_floats(D, t));
     need += round32(D.w_total) + round32(D.b_total);
     if (need > BCF_NOALLOC_MAX_GRAD_FLOATS) {
         set_error("bcf_train_step_noalloc: %lld gradient values exceed the %d of the library's scratch array",
@@ -80,7 +80,7 @@ extern "C" bcf_status bcf_train_step_noalloc(bcf_trainer tr, int64_t batch, uint
     int64_t off = 0;
     for (int t = 0; t < D.n_tex; ++t) {
         D.tex[t].grad = base + off;
-        off += round32(D.tex[t].blocks * 32);
+        off += round32(feature_floats(D, t));
     }
     D.Wg = base + off;
     off += round32(D.w_total);

@@ -195,6 +195,47 @@ __device__ __forceinline__ void for_each_side(const TrainTexDev &T, float u, flo
     }
 }
 
+// Unconstrained features ([texels][4], levels concatenated): per side with a non-zero weight,
+// f(texel indices[4], tap weights[4], texel values[4]); the values are loaded only when LOAD is set.
+template <bool LOAD, class F>
+__device__ __forceinline__ void for_each_side_free(const TrainTexDev &T, float u, float v, float s, F f)
+{
+    float st = (isnan(s) ? 0.0f : s) + (float)T.lod_bias;
+    st = fminf(fmaxf(st, 0.0f), (float)(T.levels - 1));
+    const float fl = floorf(st);
+    const int l0 = (int)fl;
+    const int l1 = min(l0 + 1, T.levels - 1);
+    const float lam = st - fl;
+#pragma unroll 1
+    for (int side = 0; side < 2; ++side) {
+        const int level = side ? l1 : l0;
+        const float lw = side ? lam : 1.0f - lam;
+        if (lw == 0.0f)
+            continue;
+        const int W = T.res >> level;
+        const int64_t lbase = (int64_t)(((uint64_t)T.res * (uint64_t)T.res - (uint64_t)W * (uint64_t)W) * 4u / 3u);
+        const float x = u * (float)W - 0.5f, y = v * (float)W - 0.5f;
+        const float fx0 = floorf(x), fy0 = floorf(y);
+        const float fx = x - fx0, fy = y - fy0;
+        const int i0 = (int)fx0, j0 = (int)fy0;
+        int64_t idx[4];
+        float wt[4];
+        float4 val[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const int i = (i0 + (c & 1)) & (W - 1), j = (j0 + (c >> 1)) & (W - 1);
+            idx[c] = lbase + (int64_t)j * W + i;
+            wt[c] = lw * ((c & 1) ? fx : 1.0f - fx) * ((c >> 1) ? fy : 1.0f - fy);
+        }
+        if (LOAD) {
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+                val[c] = *reinterpret_cast<const float4 *>(T.params + idx[c] * 4);
+        }
+        f(idx, wt, val);
+    }
+}
+
 // ----------------------------------------------------- reference material
 
 __device__ __forceinline__ void catmull_rom(float f, float w[4])

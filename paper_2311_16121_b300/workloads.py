@@ -243,3 +243,32 @@ def upload_trainer(w: TrainWorkload, device: str = "cuda", **hyper):
     t8 = torch.from_numpy(w.target8.view(np.int16).copy()).to(device)
     t1 = torch.from_numpy(w.target1.view(np.int16).copy()).to(device)
     return Trainer(P, K, w.res, w.levels, w.res_ref, w.dims, W, b, t8, t1, w.target_res, w.target_levels, **hyper)
+
+
+def free_texels(w: TrainWorkload, config: int = 3) -> list[np.ndarray]:
+    """Initial unconstrained features for the first training stage: [texels][4] float32 per texture (R, G, B,
+    unused 0), values ~ U[0, 0.5), mips concatenated."""
+    rng = seed_rng(config, 5)
+    out = []
+    for r, l in zip(w.res, w.levels):
+        n = sum((r >> i) ** 2 for i in range(l))
+        a = np.zeros((n, 4), np.float32)
+        a[:, :3] = rng.random((n, 3), dtype=np.float32) * 0.5
+        out.append(a)
+    return out
+
+
+def upload_free_trainer(w: TrainWorkload, texels: list[np.ndarray] | None = None, device: str = "cuda", **hyper):
+    """A trainer over unconstrained per-texel features (the MLP, reference and sizes of `w`)."""
+    import torch
+
+    from . import Trainer
+
+    tex = free_texels(w) if texels is None else texels
+    P = [torch.from_numpy(np.ascontiguousarray(t, np.float32).copy()).to(device) for t in tex]
+    W = torch.from_numpy(w.W.copy()).to(device)
+    b = torch.from_numpy(w.b.copy()).to(device)
+    t8 = torch.from_numpy(w.target8.view(np.int16).copy()).to(device)
+    t1 = torch.from_numpy(w.target1.view(np.int16).copy()).to(device)
+    return Trainer(P, [None] * len(P), w.res, w.levels, w.res_ref, w.dims, W, b, t8, t1, w.target_res,
+                   w.target_levels, unconstrained=True, **hyper)

@@ -76,13 +76,14 @@ def test_host_validation_rejects_bad_arguments():
 
 def test_encoder_host_validation():
     bcf, L = _lib()
-    L.bcf_encode_mode10.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_void_p,
-                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
-    assert L.bcf_encode_mode10(4096, 48, 1, 4096, 4096, None, None) == 1  # not a power of two
+    L.bcf_encode_mode10.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    assert L.bcf_encode_mode10(4096, 3, 48, 1, 4096, 4096, None, None) == 1  # not a power of two
     assert b"power of two" in L.bcf_last_error()
-    assert L.bcf_encode_mode10(4096, 64, 6, 4096, 4096, None, None) == 1  # 64 -> at most 5 levels (64 .. 4)
-    assert L.bcf_encode_mode10(4096, 64, 0, 4096, 4096, None, None) == 1
-    assert L.bcf_encode_mode10(None, 64, 4, 4096, 4096, None, None) == 1  # null texels
-    assert L.bcf_encode_mode10(4104, 64, 4, 4096, 4096, None, None) == 1  # misaligned texels
+    assert L.bcf_encode_mode10(4096, 3, 64, 6, 4096, 4096, None, None) == 1  # 64 -> at most 5 levels (64 .. 4)
+    assert L.bcf_encode_mode10(4096, 3, 64, 0, 4096, 4096, None, None) == 1
+    assert L.bcf_encode_mode10(4096, 5, 64, 4, 4096, 4096, None, None) == 1  # texel stride
+    assert L.bcf_encode_mode10(None, 3, 64, 4, 4096, 4096, None, None) == 1  # null texels
+    assert L.bcf_encode_mode10(4098, 3, 64, 4, 4096, 4096, None, None) == 1  # misaligned texels
     assert b"misaligned" in L.bcf_last_error()
     assert bcf.texture_blocks(64, 4) == 256 + 64 + 16 + 4

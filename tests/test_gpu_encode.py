@@ -1,4 +1,4 @@
-"""GPU parity of the BC6H mode-10 partition-selection encoder (Sec. 4.4)
+"""GPU parity of the BC6H mode-10 partition-selection encoder (Sec. 5.1)
 against the CPU oracle: block parameters, partitions and errors are
 compared bit for bit (both take every decision in IEEE single precision in
 the same order)."""
@@ -84,6 +84,18 @@ def test_encoder_matches_oracle_bit_for_bit(kinds):
         assert not err[:256].any()
 
 
+def test_encoder_texel_stride_4():
+    """The unconstrained training features' layout ([texels][4]) encodes like the packed RGB one."""
+    bcf = _bcf()
+    rng = np.random.default_rng(9)
+    tex3 = _texture(rng, 32, 4, ("smooth", "noise"))
+    tex4 = np.concatenate([tex3.reshape(-1, 3), np.full((tex3.size // 3, 1), 7.0, np.float32)], axis=1)
+    a = bcf.encode_mode10(torch.from_numpy(tex3).cuda(), 32, 4)
+    b = bcf.encode_mode10(torch.from_numpy(tex4.reshape(-1)).cuda(), 32, 4, texel_stride=4)
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+
+
 def test_encoder_edge_sizes():
     bcf = _bcf()
     rng = np.random.default_rng(7)
@@ -125,6 +137,6 @@ def test_encoder_rejects_bad_arguments():
     with pytest.raises(bcf.BcfError):
         bcf.encode_mode10(tex, 64, 6)  # 64 -> at most 5 levels
     with pytest.raises(bcf.BcfError):
-        bcf.encode_mode10(tex[1:], 64, 1)  # misaligned
+        bcf.encode_mode10(tex, 64, 1, texel_stride=5)
     with pytest.raises(ValueError):
         bcf.encode_mode10(tex[:100], 64, 1)  # too few texels

@@ -730,7 +730,7 @@ def test_adam_first_step_closed_form_and_torch():
     assert (p == 63.0).all()
 
 
-# --------------------------------------------------------------------------- mode-10 encoder (Sec. 4.4)
+# --------------------------------------------------------------------------- mode-10 encoder (Sec. 5.1)
 
 def _decoded_block(p, k):
     """Values of a mode-10 block through the format decoder (export, then decode): [16][3]."""
@@ -805,7 +805,7 @@ def test_encoder_error_is_the_decoded_error_and_indices_are_optimal():
             assert got <= best * (1 + 1e-6) + 1e-12, (b, t)
 
 
-# --------------------------------------------------------------------------- unconstrained features (Sec. 4.4)
+# --------------------------------------------------------------------------- unconstrained features (Sec. 5.1)
 
 def _free_levels(rng, res, levels):
     return [rng.uniform(-0.5, 1.5, ((res >> l), (res >> l), 3)) for l in range(levels)]
