@@ -53,7 +53,7 @@ class _Mlp(ctypes.Structure):
 class _TrainFeatures(ctypes.Structure):
     _fields_ = [("n_tex", c_int), ("res", c_int * MAX_TEX), ("levels", c_int * MAX_TEX),
                 ("params", c_void_p * MAX_TEX), ("partition", c_void_p * MAX_TEX), ("res_ref", c_int),
-                ("lod_input", c_int), ("free_texels", c_int)]
+                ("lod_input", c_int), ("free_texels", c_int), ("is_signed", c_int), ("literal", c_int)]
 
 
 class _Target(ctypes.Structure):
@@ -138,6 +138,12 @@ def lib():
                                                   c_void_p, c_void_p, c_void_p, c_void_p]
         L.oracle_texture_blocks.restype = c_int64
         L.oracle_texture_blocks.argtypes = [c_int, c_int]
+        L.oracle_train_texel_v.restype = c_double
+        L.oracle_train_texel_v.argtypes = [c_void_p, c_int, c_int, c_int, c_int, c_int, c_int]
+        L.oracle_train_texel_grad_v.restype = None
+        L.oracle_train_texel_grad_v.argtypes = [c_void_p, c_int, c_int, c_int, c_int, c_int, c_int, c_void_p]
+        L.oracle_train_export_block_v.restype = None
+        L.oracle_train_export_block_v.argtypes = [c_void_p, c_int, c_int, c_void_p]
         L.oracle_train_export_block.restype = None
         L.oracle_train_export_block.argtypes = [c_void_p, c_int, c_void_p]
         L.oracle_encode_mode10_block.restype = None
@@ -370,7 +376,8 @@ class TrainFeatures:
     with free=True, unconstrained features: params [texels, 3] per texture and no partitions."""
 
     def __init__(self, params: list[np.ndarray], partition: list[np.ndarray] | None, res: list[int],
-                 levels: list[int], res_ref: int, lod_input: bool = True, free: bool = False):
+                 levels: list[int], res_ref: int, lod_input: bool = True, free: bool = False, is_signed: bool = False,
+                 literal: bool = False):
         self._p = [np.ascontiguousarray(p, dtype=np.float64).reshape(-1) for p in params]
         self._k = [np.ascontiguousarray(k, dtype=np.uint8).reshape(-1) for k in partition] if not free else \
             [np.zeros(1, np.uint8) for _ in params]
@@ -384,6 +391,8 @@ class TrainFeatures:
         c.res_ref = int(res_ref)
         c.lod_input = int(lod_input)
         c.free_texels = int(free)
+        c.is_signed = int(is_signed)
+        c.literal = int(literal)
         self.free = free
         self.c = c
         self.n_tex = len(params)
@@ -461,12 +470,29 @@ def texture_blocks(res: int, levels: int) -> int:
     return int(lib().oracle_texture_blocks(int(res), int(levels)))
 
 
-def train_export_block(p: np.ndarray, k: int) -> np.ndarray:
-    """Mode-10 BC6H block of trained block parameters (with the anchor fix-up)."""
+def train_export_block(p: np.ndarray, k: int, is_signed: bool = False) -> np.ndarray:
+    """Mode-10 BC6H block of trained block parameters (with the anchor fix-up); SF16 when is_signed."""
     p = np.ascontiguousarray(p, dtype=np.float64).reshape(28)
     out = np.zeros(16, np.uint8)
-    lib().oracle_train_export_block(_ptr(p), int(k), _ptr(out))
+    lib().oracle_train_export_block_v(_ptr(p), int(k), int(is_signed), _ptr(out))
     return out
+
+
+def train_texel_v(p: np.ndarray, k: int, texel: int, channel: int, is_signed: bool = False, literal: bool = False,
+                  relaxed: bool = False) -> float:
+    """One emulated texel channel: UF16 or SF16, the format's exact steps or Eq. 7-8 as printed, STE or relaxed."""
+    p = np.ascontiguousarray(p, dtype=np.float64).reshape(28)
+    return lib().oracle_train_texel_v(_ptr(p), int(k), int(texel), int(channel), int(is_signed), int(literal),
+                                      int(relaxed))
+
+
+def train_texel_grad_v(p: np.ndarray, k: int, texel: int, channel: int, is_signed: bool = False,
+                       literal: bool = False, relaxed: bool = False) -> np.ndarray:
+    p = np.ascontiguousarray(p, dtype=np.float64).reshape(28)
+    g = np.zeros(28, np.float64)
+    lib().oracle_train_texel_grad_v(_ptr(p), int(k), int(texel), int(channel), int(is_signed), int(literal),
+                                    int(relaxed), _ptr(g))
+    return g
 
 
 def train_outputs(F: TrainFeatures, P: TrainMlp, u, v, s) -> np.ndarray:

@@ -37,7 +37,7 @@
  *     Adam step (Sec. 6.1).
  *   - Philox4x32-10 (Salmon et al., SC'11) for the training batch draws.
  *   - BC6H mode-10 block encoder for partition selection and the initial
- *     block parameters (Sec. 4.4: compress unconstrained features with the
+ *     block parameters (Sec. 5.1: compress unconstrained features with the
  *     BC6 algorithm): per-partition principal-axis line fit, 6-bit / 3-bit
  *     quantisation, minimum-error partition.
  *
@@ -864,7 +864,9 @@ typedef struct {
     int res_ref;
     int lod_input;
     int free_texels; /* 1: unconstrained features, params[t] = [texels][3] values (mips concatenated), no
-                      * partition -- the first training stage of Sec. 4.4 */
+                      * partition -- the first training stage of Sec. 5.1 */
+    int is_signed;   /* block features: BC6H signed (SF16) emulation */
+    int literal;     /* block features: Eq. 7 and Eq. 8 as printed instead of the format's exact steps */
 } oracle_train_features;
 
 static double clampd(double x, double lo, double hi) { return x < lo ? lo : (x > hi ? hi : x); }
@@ -881,12 +883,23 @@ typedef struct {
 
 /* Emulated decompression (Sec. 4.2), straight-through form: endpoints and
  * index quantised to the exported mode-10 lattice (6-bit endpoints, 3-bit
- * indices, Sec. 5.2), then the exact integer unquantise / interpolate /
- * finish steps of the format, then Eq. 9.  The partials are those of the
- * relaxed pipeline (Eq. 7 slope 2^16 / 2^6 per endpoint unit, linear
- * interpolation in w / 64 with w / 64 standing for x, final 31/64, slope of
- * Eq. 9) evaluated at the quantised forward values. */
-static void texel_ste(const double *p, int k, int texel, texel_eval *T)
+ * indices, Sec. 5.2), then the value.  Variants:
+ *   sgn = 0: BC6H unsigned (UF16): endpoints in [0, 63], a = 31/64;
+ *   sgn = 1: BC6H signed (SF16): endpoints are 6-bit two's complement
+ *            values in [-32, 31], a = 31/32, the value carries the sign and
+ *            Eq. 9 acts on its magnitude;
+ *   lit = 0: the format's exact integer steps (unquantise with its special
+ *            cases for 0 and the largest code, interpolate with the >> 6
+ *            floor, finish with a), so the value equals the decode of the
+ *            exported block bit for bit;
+ *   lit = 1: Eq. 7 and Eq. 8 as printed ("paper_literal"): the real
+ *            unquantisation (a 2^16 e + 2^15) / 2^6 with no special cases,
+ *            real interpolation with weight w / 64, no floors, then Eq. 9 on
+ *            the real result.
+ * The partials are those of the relaxed pipeline (Eq. 7 slope a 2^16 / 2^6
+ * per endpoint unit, interpolation linear in w / 64 with w / 64 standing for
+ * x, slope of Eq. 9) evaluated at the quantised forward values. */
+static void texel_ste_v(const double *p, int k, int texel, int sgn, int lit, texel_eval *T)
 {
     int region = oracle_bc6h_partition_region(k, texel);
     T->region = region;
@@ -894,42 +907,98 @@ static void texel_ste(const double *p, int k, int texel, texel_eval *T)
     T->x_in = x >= 0.0 && x <= 1.0;
     int idx = (int)nearbyint(7.0 * clampd(x, 0.0, 1.0));
     int w = k_weights3[idx];
+    double lo = sgn ? -32.0 : 0.0, hi = sgn ? 31.0 : 63.0;
+    double a = sgn ? 31.0 / 32.0 : 31.0 / 64.0;
     for (int c = 0; c < 3; ++c) {
         double ea = p[(2 * region) * 3 + c], eb = p[(2 * region + 1) * 3 + c];
-        T->e_in_a[c] = ea >= 0.0 && ea <= 63.0;
-        T->e_in_b[c] = eb >= 0.0 && eb <= 63.0;
-        int ua = bc6h_unquantize((int)nearbyint(clampd(ea, 0.0, 63.0)), 6, 0);
-        int ub = bc6h_unquantize((int)nearbyint(clampd(eb, 0.0, 63.0)), 6, 0);
-        int yi = floor_div64(ua * (64 - w) + ub * w + 32);
-        int y = bc6h_finish(yi, 0);
-        T->value[c] = oracle_eq9((double)y);
-        double dy = oracle_eq9_slope((double)y) * (31.0 / 64.0);
-        T->d_ea[c] = dy * (64.0 - w) / 64.0 * 1024.0;
-        T->d_eb[c] = dy * w / 64.0 * 1024.0;
-        T->d_x[c] = dy * (double)(ub - ua);
+        T->e_in_a[c] = ea >= lo && ea <= hi;
+        T->e_in_b[c] = eb >= lo && eb <= hi;
+        int qa = (int)nearbyint(clampd(ea, lo, hi)), qb = (int)nearbyint(clampd(eb, lo, hi));
+        double slope, span;
+        if (!lit) {
+            int ua = bc6h_unquantize(qa, 6, sgn), ub = bc6h_unquantize(qb, 6, sgn);
+            int yi = floor_div64(ua * (64 - w) + ub * w + 32);
+            uint16_t bits = bc6h_finish(yi, sgn);
+            T->value[c] = oracle_half_to_double(bits);
+            slope = oracle_eq9_slope((double)(bits & 0x7FFF)) * a;
+            span = (double)(ub - ua);
+        } else {
+            double ua = (a * 65536.0 * qa + 32768.0) / 64.0, ub = (a * 65536.0 * qb + 32768.0) / 64.0;
+            double y = ua + (w / 64.0) * (ub - ua);
+            T->value[c] = oracle_eq9(y);
+            slope = oracle_eq9_slope(y) * a; /* a is inside the unquantisation here */
+            span = (ub - ua) / a;
+        }
+        T->d_ea[c] = slope * (64.0 - w) / 64.0 * 1024.0;
+        T->d_eb[c] = slope * w / 64.0 * 1024.0;
+        T->d_x[c] = slope * span;
     }
 }
 
-/* Relaxed (continuous) texel: no rounding and no floors; unquantise
- * e -> 1024 e + 512, weight w = 64 x, finish 31/64, then Eq. 9; exact
+static void texel_ste(const double *p, int k, int texel, texel_eval *T) { texel_ste_v(p, k, texel, 0, 0, T); }
+
+/* Relaxed (continuous) texel: no rounding and no floors.  Exact form: the
+ * unquantisation e -> 1024 e + 512 (signed: 1024 e + 512 sign(e)), weight
+ * w = 64 x, scale a, then Eq. 9 (on the magnitude, sign restored); literal
+ * form: Eq. 7 and Eq. 8 as printed with the real e and w = 64 x.  Exact
  * partials of that function. */
-static void texel_relaxed(const double *p, int k, int texel, texel_eval *T)
+static void texel_relaxed_v(const double *p, int k, int texel, int sgn, int lit, texel_eval *T)
 {
     int region = oracle_bc6h_partition_region(k, texel);
     T->region = region;
     T->x_in = 1;
     double w = 64.0 * p[12 + texel];
+    double a = sgn ? 31.0 / 32.0 : 31.0 / 64.0;
     for (int c = 0; c < 3; ++c) {
         T->e_in_a[c] = T->e_in_b[c] = 1;
-        double ea = 1024.0 * p[(2 * region) * 3 + c] + 512.0;
-        double eb = 1024.0 * p[(2 * region + 1) * 3 + c] + 512.0;
-        double y = ((64.0 - w) * ea + w * eb) / 64.0 * (31.0 / 64.0);
+        double e0 = p[(2 * region) * 3 + c], e1 = p[(2 * region + 1) * 3 + c];
+        double ea, eb, y, de;
+        if (!lit) {
+            ea = 1024.0 * e0 + 512.0 * (sgn && e0 < 0.0 ? -1.0 : 1.0);
+            eb = 1024.0 * e1 + 512.0 * (sgn && e1 < 0.0 ? -1.0 : 1.0);
+            y = ((64.0 - w) * ea + w * eb) / 64.0 * a;
+            de = 1024.0 * a;
+        } else {
+            ea = (a * 65536.0 * e0 + 32768.0) / 64.0;
+            eb = (a * 65536.0 * e1 + 32768.0) / 64.0;
+            y = ((64.0 - w) * ea + w * eb) / 64.0;
+            de = a * 1024.0;
+        }
         T->value[c] = oracle_eq9(y);
-        double dy = oracle_eq9_slope(y) * (31.0 / 64.0);
-        T->d_ea[c] = dy * (64.0 - w) / 64.0 * 1024.0;
-        T->d_eb[c] = dy * w / 64.0 * 1024.0;
-        T->d_x[c] = dy * (eb - ea);
+        double sl = oracle_eq9_slope(y);
+        T->d_ea[c] = sl * (64.0 - w) / 64.0 * de;
+        T->d_eb[c] = sl * w / 64.0 * de;
+        T->d_x[c] = sl * (lit ? (eb - ea) : (eb - ea) * a);
     }
+}
+
+static void texel_relaxed(const double *p, int k, int texel, texel_eval *T) { texel_relaxed_v(p, k, texel, 0, 0, T); }
+
+double oracle_train_texel_v(const double *p, int k, int texel, int channel, int sgn, int lit, int relaxed)
+{
+    texel_eval T;
+    if (relaxed)
+        texel_relaxed_v(p, k, texel, sgn, lit, &T);
+    else
+        texel_ste_v(p, k, texel, sgn, lit, &T);
+    return T.value[channel];
+}
+
+void oracle_train_texel_grad_v(const double *p, int k, int texel, int channel, int sgn, int lit, int relaxed,
+                               double grad[28])
+{
+    texel_eval T;
+    if (relaxed)
+        texel_relaxed_v(p, k, texel, sgn, lit, &T);
+    else
+        texel_ste_v(p, k, texel, sgn, lit, &T);
+    memset(grad, 0, sizeof(double) * 28);
+    if (T.e_in_a[channel])
+        grad[(2 * T.region) * 3 + channel] = T.d_ea[channel];
+    if (T.e_in_b[channel])
+        grad[(2 * T.region + 1) * 3 + channel] = T.d_eb[channel];
+    if (T.x_in)
+        grad[12 + texel] = T.d_x[channel];
 }
 
 double oracle_train_texel(const double *p, int k, int texel, int channel)
@@ -1051,9 +1120,9 @@ void oracle_train_features_one(const oracle_train_features *F, float u, float v,
         }
         const double *p = F->params[t] + L.block[n] * OR_BLOCK_PARAMS;
         if (relaxed)
-            texel_relaxed(p, F->partition[t][L.block[n]], L.texel[n], &T);
+            texel_relaxed_v(p, F->partition[t][L.block[n]], L.texel[n], F->is_signed, F->literal, &T);
         else
-            texel_ste(p, F->partition[t][L.block[n]], L.texel[n], &T);
+            texel_ste_v(p, F->partition[t][L.block[n]], L.texel[n], F->is_signed, F->literal, &T);
         for (int c = 0; c < 3; ++c)
             feat[3 * t + c] += L.weight[n] * T.value[c];
     }
@@ -1187,9 +1256,9 @@ static double train_query_ext(const oracle_train_features *F, const oracle_train
         if (F->free_texels)
             texel_free(p, &taps[n]);
         else if (relaxed)
-            texel_relaxed(p, F->partition[t][L.block[n]], L.texel[n], &taps[n]);
+            texel_relaxed_v(p, F->partition[t][L.block[n]], L.texel[n], F->is_signed, F->literal, &taps[n]);
         else
-            texel_ste(p, F->partition[t][L.block[n]], L.texel[n], &taps[n]);
+            texel_ste_v(p, F->partition[t][L.block[n]], L.texel[n], F->is_signed, F->literal, &taps[n]);
         for (int c = 0; c < 3; ++c)
             x[3 * t + c] += L.weight[n] * taps[n].value[c];
     }
@@ -1332,12 +1401,12 @@ int64_t oracle_texture_blocks(int res, int levels) { return level_block_offset(r
  * index bit, the region's two endpoints are swapped and its indices
  * mirrored (index -> 7 - index), which leaves every texel value unchanged
  * because the 3-bit weights satisfy W(7 - i) = 64 - W(i). */
-void oracle_train_export_block(const double *p, int k, uint8_t blk[16])
+void oracle_train_export_block_v(const double *p, int k, int sgn, uint8_t blk[16])
 {
     int q[4][3], idx[16];
     for (int e = 0; e < 4; ++e)
         for (int c = 0; c < 3; ++c)
-            q[e][c] = (int)nearbyint(clampd(p[e * 3 + c], 0.0, 63.0));
+            q[e][c] = (int)nearbyint(sgn ? clampd(p[e * 3 + c], -32.0, 31.0) : clampd(p[e * 3 + c], 0.0, 63.0));
     for (int t = 0; t < 16; ++t)
         idx[t] = (int)nearbyint(7.0 * clampd(p[12 + t], 0.0, 1.0));
     for (int r = 0; r < 2; ++r) {
@@ -1356,9 +1425,11 @@ void oracle_train_export_block(const double *p, int k, uint8_t blk[16])
     int raw[12];
     for (int e = 0; e < 4; ++e)
         for (int c = 0; c < 3; ++c)
-            raw[e * 3 + c] = q[e][c];
+            raw[e * 3 + c] = q[e][c] & 63; /* 6-bit field (two's complement for SF16) */
     oracle_bc6h_encode_fields(10, raw, k, idx, blk);
 }
+
+void oracle_train_export_block(const double *p, int k, uint8_t blk[16]) { oracle_train_export_block_v(p, k, 0, blk); }
 
 /* MLP outputs of the block-parameterised material for explicit queries
  * (out[n][C]), and the gradients for a given output gradient grad_out[n][C]
@@ -1381,7 +1452,7 @@ void oracle_train_backward_given(const oracle_train_features *F, const oracle_tr
 
 /* ------------------------------------------------------------------------- */
 /* BC6H mode-10 block encoder: partition selection and initial block         */
-/* parameters from free per-texel features (Sec. 4.4)                         */
+/* parameters from free per-texel features (Sec. 5.1)                         */
 /* ------------------------------------------------------------------------- */
 /*
  * The paper initialises the block parameters and fixes the partitions by

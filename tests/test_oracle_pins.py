@@ -869,3 +869,100 @@ def test_free_feature_gradient_matches_finite_differences():
                     continue  # a ReLU kink inside the stencil
                 checked += 1
     assert checked >= 50
+
+
+# --------------------------------------------------------------------------- SF16 and paper-literal emulation
+
+def test_signed_emulated_texels_equal_signed_decode_of_export():
+    """SF16 (Sec. 4.2, a = 31/32): the signed straight-through forward equals the signed BC6H decode of the
+    exported mode-10 block (6-bit two's complement endpoints) bit for bit, including the saturating codes
+    -32, -31 and 31, zero, and index ties."""
+    rng = np.random.default_rng(41)
+    for b in range(300):
+        p = np.zeros(28)
+        p[:12] = rng.uniform(-32, 31, 12)
+        if b % 3 == 0:
+            p[:12] = rng.integers(-32, 32, 12)
+        if b % 7 == 0:
+            p[:12] = rng.choice([-32.0, -31.0, 31.0, 0.0, -0.4, 0.49], 12)
+        p[12:] = rng.uniform(0, 1, 16) if b % 2 else (rng.integers(0, 7, 16) + 0.5) / 7.0
+        k = b % 32
+        mode, tex = oracle.bc6h_decode_block(oracle.train_export_block(p, k, is_signed=True), is_signed=True)
+        assert mode == 10
+        for t in range(16):
+            for c in range(3):
+                v = oracle.train_texel_v(p, k, t, c, is_signed=True)
+                assert v == oracle.half_to_double(int(tex[t, c])), (b, t, c)
+
+
+def _half_coord(v):
+    """The interpolation-domain coordinate of a value through numpy's binary16 table: the bit pattern of the
+    half just below |v| plus the fraction of the way to the next one, signed."""
+    a = abs(v)
+    n = int(np.array([a], np.float16).view(np.uint16)[0])
+    while float(np.array([n], np.uint16).view(np.float16)[0]) > a:
+        n -= 1
+    lo = float(np.array([n], np.uint16).view(np.float16)[0])
+    hi = float(np.array([n + 1], np.uint16).view(np.float16)[0])
+    return math.copysign(n + (a - lo) / (hi - lo), v)
+
+
+@pytest.mark.parametrize("signed", [False, True])
+def test_literal_form_sits_the_unscaled_offset_above_the_format(signed):
+    """Eq. 7 as printed adds 2^15 / 2^6 = 512 after the scale a instead of scaling it: read back through
+    numpy's half table, the literal value of an interior lattice texel lies 512 (1 - a) half-bit units
+    (264 for UF16, 16 for SF16) above the format's decode, within the format's two floor operations."""
+    rng = np.random.default_rng(42 + signed)
+    off = 512 * (1 - (31 / 32 if signed else 31 / 64))
+    for _ in range(300):
+        p = np.zeros(28)
+        p[:12] = rng.integers(1, 31 if signed else 62, 12)  # positive interior codes, no special cases
+        p[12:] = rng.integers(0, 8, 16) / 7.0
+        k, t, c = int(rng.integers(0, 32)), int(rng.integers(0, 16)), int(rng.integers(0, 3))
+        exact = _half_coord(oracle.train_texel_v(p, k, t, c, is_signed=signed))
+        lit = _half_coord(oracle.train_texel_v(p, k, t, c, is_signed=signed, literal=True))
+        assert off - 2.0 <= lit - exact <= off + 1.0, (lit - exact, off)
+
+
+@pytest.mark.parametrize("signed,literal", [(False, True), (True, False), (True, True)])
+def test_variant_relaxed_texel_gradients_match_finite_differences(signed, literal):
+    rng = np.random.default_rng(50 + 2 * signed + literal)
+    h = 1e-6
+    checked = 0
+    for _ in range(150):
+        p = np.zeros(28)
+        lo, hi = (-30.0, 30.0) if signed else (1.0, 62.0)
+        p[:12] = rng.uniform(lo, hi, 12)
+        p[:12][np.abs(p[:12]) < 1.0] += 2.0  # away from the sign switch of the signed unquantisation
+        p[12:] = rng.uniform(0.02, 0.98, 16)
+        k, t, c = int(rng.integers(0, 32)), int(rng.integers(0, 16)), int(rng.integers(0, 3))
+        g = oracle.train_texel_grad_v(p, k, t, c, signed, literal, relaxed=True)
+        for j in np.nonzero(g)[0]:
+            pp, pm = p.copy(), p.copy()
+            pp[j] += h
+            pm[j] -= h
+            fd = (oracle.train_texel_v(pp, k, t, c, signed, literal, True)
+                  - oracle.train_texel_v(pm, k, t, c, signed, literal, True)) / (2 * h)
+            if abs(fd - g[j]) > 1e-5 * abs(g[j]) + 1e-12:
+                continue  # an Eq. 9 kink inside the stencil
+            checked += 1
+    assert checked >= 300
+
+
+def test_literal_ste_is_the_relaxed_form_on_the_lattice():
+    """With no floors in the literal form, its straight-through forward and partials at a lattice point are
+    those of the relaxed literal form there (index weights W3 = round(64 i / 7))."""
+    rng = np.random.default_rng(60)
+    for _ in range(200):
+        p = np.zeros(28)
+        p[:12] = rng.integers(0, 64, 12)
+        idx = rng.integers(0, 8, 16)
+        p[12:] = idx / 7.0
+        q = p.copy()
+        q[12:] = np.array([oracle.bc6h_weight(3, int(i)) for i in idx]) / 64.0
+        k, t, c = int(rng.integers(0, 32)), int(rng.integers(0, 16)), int(rng.integers(0, 3))
+        assert oracle.train_texel_v(p, k, t, c, literal=True) == pytest.approx(
+            oracle.train_texel_v(q, k, t, c, literal=True, relaxed=True), rel=1e-12, abs=1e-300)
+        gs = oracle.train_texel_grad_v(p, k, t, c, literal=True)
+        gr = oracle.train_texel_grad_v(q, k, t, c, literal=True, relaxed=True)
+        np.testing.assert_allclose(gs, gr, rtol=1e-12, atol=0)
