@@ -250,6 +250,19 @@ bcf_status bcf_material_set_config(bcf_material_set set, int32_t *cap, int32_t *
  * FP32 accumulation; its backward is FP32 with respect to those rounded
  * values.
  *
+ * Signed features (is_signed = 1, Sec. 4.2 with a = 31/32): endpoints are
+ * 6-bit two's complement codes in [-32, 31] (the box of the optimiser),
+ * unquantised and finished as the BC6H signed format does (sign carried,
+ * Eq. 9 on the magnitude), exported as SF16 mode-10 blocks.
+ *
+ * Literal emulation (literal = 1): the forward evaluates Eq. 7 and Eq. 8
+ * exactly as printed on the rounded codes -- unquantisation
+ * (a 2^16 e + 2^15) / 2^6 with no special cases for the smallest and
+ * largest codes, real interpolation with weight w / 64, no floors -- and
+ * Eq. 9 on that real value; the backward is that function's derivative.
+ * It differs from the decode of the exported block (the 2^15 term is not
+ * scaled by a), which is why the exact form is the default.
+ *
  * Unconstrained features (unconstrained = 1; the first training stage of
  * Sec. 5.1, whose result bcf_encode_mode10 compresses into the initial block
  * parameters and partitions): each texture holds free RGB values per texel,
@@ -292,6 +305,8 @@ typedef struct {
     float beta1, beta2, eps;                /* Adam constants */
     float s_max;                            /* batch draws: s ~ U[0, s_max) in res_ref units */
     int32_t unconstrained;                  /* 1: free per-texel features (see below) instead of block parameters */
+    int32_t is_signed;                      /* 1: BC6H signed (SF16) features: endpoints in [-32, 31], a = 31/32 */
+    int32_t literal;                        /* 1: Eq. 7-8 as printed instead of the format's exact steps (below) */
 } bcf_trainer_desc;
 
 /*

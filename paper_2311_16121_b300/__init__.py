@@ -49,7 +49,8 @@ class _TrainerDesc(ctypes.Structure):
                 ("d_W_m", c_void_p), ("d_W_v", c_void_p), ("d_b_m", c_void_p), ("d_b_v", c_void_p),
                 ("target_res", c_int32), ("target_levels", c_int32), ("d_target8", c_void_p), ("d_target1", c_void_p),
                 ("lr_features", c_float), ("lr_mlp", c_float), ("gamma", c_float), ("beta1", c_float),
-                ("beta2", c_float), ("eps", c_float), ("s_max", c_float), ("unconstrained", c_int32)]
+                ("beta2", c_float), ("eps", c_float), ("s_max", c_float), ("unconstrained", c_int32),
+                ("is_signed", c_int32), ("literal", c_int32)]
 
 
 _lib = None
@@ -312,7 +313,8 @@ class Trainer:
                  res_ref: int, dims: list[int], W: torch.Tensor, b: torch.Tensor, target8: torch.Tensor,
                  target1: torch.Tensor, target_res: int, target_levels: int, lr_features: float = 1e-2,
                  lr_mlp: float = 1e-3, gamma: float = 0.9999, beta1: float = 0.9, beta2: float = 0.999,
-                 eps: float = 1e-8, s_max: float | None = None, lod_input: bool = True, unconstrained: bool = False):
+                 eps: float = 1e-8, s_max: float | None = None, lod_input: bool = True, unconstrained: bool = False,
+                 is_signed: bool = False, literal: bool = False):
         z = torch.zeros_like
         self.params, self.partition = list(params), list(partition)
         self.grads = [z(p) for p in params]
@@ -345,6 +347,7 @@ class Trainer:
         d.beta1, d.beta2, d.eps = beta1, beta2, eps
         d.s_max = float(target_levels - 1 if s_max is None else s_max)
         d.unconstrained = int(unconstrained)
+        d.is_signed, d.literal = int(is_signed), int(literal)
         self.unconstrained = bool(unconstrained)
         h = c_void_p()
         _check(lib().bcf_trainer_create(ctypes.byref(d), ctypes.byref(h)), "bcf_trainer_create")

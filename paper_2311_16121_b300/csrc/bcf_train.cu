@@ -92,6 +92,7 @@ __global__ void __launch_bounds__(kTrainThreads) k_train(TrainDev D, int mode, i
     __syncthreads();
     const int tid = threadIdx.x;
     const int nout = D.dims[L];
+    const int emu = emulation_variant(D);
     float loss_acc = 0.0f;
     const int64_t tiles = (batch + kTrainThreads - 1) / kTrainThreads;
     for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
@@ -117,7 +118,7 @@ __global__ void __launch_bounds__(kTrainThreads) k_train(TrainDev D, int mode, i
                 const TrainTexDev &T = D.tex[t];
                 for_each_tap(T, u, v, s, [&](const Tap &tp) {
                     SteTexel tx;
-                    ste_texel(T.params + tp.block * 32, T.part[tp.block], tp.texel, tx);
+                    ste_texel_v(T.params + tp.block * 32, T.part[tp.block], tp.texel, emu, tx);
 #pragma unroll
                     for (int c = 0; c < 3; ++c)
                         f[c] = fmaf(tp.weight, tx.v[c], f[c]);
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(kTrainThreads) k_train(TrainDev D, int mode, i
                 for_each_tap(T, u, v, s, [&](const Tap &tp) {
                     const float *p = T.params + tp.block * 32;
                     SteTexel tx;
-                    ste_texel(p, T.part[tp.block], tp.texel, tx);
+                    ste_texel_v(p, T.part[tp.block], tp.texel, emu, tx);
                     float *gp = T.grad + tp.block * 32;
                     float ga[3], gb[3], gx = 0.0f;
 #pragma unroll
@@ -266,7 +267,8 @@ struct AdamSeg {
     float *p, *g, *m, *v;
     int64_t n;
     float lr;
-    int blocks_layout; // 1: block parameters (clamp endpoints to [0, 63], x to [0, 1], skip unused)
+    int blocks_layout; // 1: block parameters (clamp endpoints to [elo, ehi], x to [0, 1], skip unused)
+    float elo, ehi;
 };
 
 struct AdamArgs {
@@ -290,9 +292,9 @@ __device__ __forceinline__ float adam_one(const AdamArgs &A, float lr, float &p,
 // Block-parameter records: element e of a 32-float record is an endpoint channel (e < 16, box [0, 63]) or an
 // index coordinate (e >= 16, box [0, 1]); elements 6, 7, 14, 15 are padding and are left untouched.
 __device__ __forceinline__ bool record_pad(int e) { return e == 6 || e == 7 || e == 14 || e == 15; }
-__device__ __forceinline__ float record_clamp(int e, float p)
+__device__ __forceinline__ float record_clamp(int e, float p, float elo, float ehi)
 {
-    return e < 16 ? fminf(fmaxf(p, 0.0f), 63.0f) : fminf(fmaxf(p, 0.0f), 1.0f);
+    return e < 16 ? fminf(fmaxf(p, elo), ehi) : fminf(fmaxf(p, 0.0f), 1.0f);
 }
 
 // One Adam step over the segments (feature records of every texture, MLP weights, MLP biases), with the
@@ -334,7 +336,7 @@ __global__ void __launch_bounds__(256) k_adam(AdamArgs A)
                     continue;
                 float pn = pp[c], mn = mm[c], vn = vv[c];
                 adam_one(A, S.lr, pn, gg[c], mn, vn);
-                pp[c] = S.blocks_layout ? record_clamp(e, pn) : pn;
+                pp[c] = S.blocks_layout ? record_clamp(e, pn, S.elo, S.ehi) : pn;
                 mm[c] = mn;
                 vv[c] = vn;
             }
@@ -355,7 +357,7 @@ __global__ void __launch_bounds__(256) k_adam(AdamArgs A)
         adam_one(A, S.lr, p, g, m, v);
         S.m[i] = m;
         S.v[i] = v;
-        S.p[i] = S.blocks_layout ? record_clamp(e, p) : p;
+        S.p[i] = S.blocks_layout ? record_clamp(e, p, S.elo, S.ehi) : p;
     }
 }
 
@@ -378,7 +380,7 @@ struct BitWriter {
 };
 
 __global__ void k_export_blocks(const float *__restrict__ params, const uint8_t *__restrict__ part, int64_t nblocks,
-                                uint4 *__restrict__ out)
+                                int is_signed, uint4 *__restrict__ out)
 {
     const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (b >= nblocks)
@@ -390,7 +392,8 @@ __global__ void k_export_blocks(const float *__restrict__ params, const uint8_t 
     for (int e = 0; e < 4; ++e)
 #pragma unroll
         for (int c = 0; c < 3; ++c)
-            q[e][c] = (int)rintf(fminf(fmaxf(p[(e >> 1) * 8 + (e & 1) * 3 + c], 0.0f), 63.0f));
+            q[e][c] = (int)rintf(fminf(fmaxf(p[(e >> 1) * 8 + (e & 1) * 3 + c], is_signed ? -32.0f : 0.0f),
+                                       is_signed ? 31.0f : 63.0f)); // SF16: the low 6 bits hold the two's complement
 #pragma unroll
     for (int t = 0; t < 16; ++t)
         idx[t] = (int)rintf(7.0f * fminf(fmaxf(p[16 + t], 0.0f), 1.0f));
@@ -483,11 +486,12 @@ cudaError_t launch_adam(const TrainDev &D, const TrainHyper &H, int64_t step, cu
     int k = 0;
     for (int t = 0; t < D.n_tex; ++t) {
         A.seg[k] = {D.tex[t].params, D.tex[t].grad, D.tex[t].m, D.tex[t].v, feature_floats(D, t),
-                    (float)(H.lr_features * decay), D.unconstrained ? 0 : 1};
+                    (float)(H.lr_features * decay), D.unconstrained ? 0 : 1, D.is_signed ? -32.0f : 0.0f,
+                    D.is_signed ? 31.0f : 63.0f};
         ++k;
     }
-    A.seg[k++] = {D.W, D.Wg, D.Wm, D.Wv, D.w_total, (float)(H.lr_mlp * decay), 0};
-    A.seg[k++] = {D.b, D.bg, D.bm, D.bv, D.b_total, (float)(H.lr_mlp * decay), 0};
+    A.seg[k++] = {D.W, D.Wg, D.Wm, D.Wv, D.w_total, (float)(H.lr_mlp * decay), 0, 0.0f, 0.0f};
+    A.seg[k++] = {D.b, D.bg, D.bm, D.bv, D.b_total, (float)(H.lr_mlp * decay), 0, 0.0f, 0.0f};
     A.nseg = k;
     int64_t chunks = 0;
     for (int i = 0; i < k; ++i) {
@@ -511,7 +515,7 @@ cudaError_t launch_export(const TrainDev &D, void *const *blocks_out, uint16_t *
     for (int t = 0; t < D.n_tex; ++t) {
         const int64_t nb = D.tex[t].blocks;
         k_export_blocks<<<(unsigned)((nb + 127) / 128), 128, 0, st>>>(D.tex[t].params, D.tex[t].part, nb,
-                                                                      (uint4 *)blocks_out[t]);
+                                                                      D.is_signed, (uint4 *)blocks_out[t]);
     }
     if (weights_fp16)
         k_export_weights<<<(unsigned)((D.w_total + 255) / 256), 256, 0, st>>>(D.W, D.w_total, weights_fp16);

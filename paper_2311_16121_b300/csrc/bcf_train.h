@@ -27,7 +27,12 @@ struct TrainDev {
     const uint16_t *t8, *t1;
     float s_max;
     int32_t unconstrained; // free per-texel features [texels][4] instead of block records [blocks][32]
+    int32_t is_signed;     // SF16 block features (endpoints in [-32, 31], a = 31/32)
+    int32_t literal;       // Eq. 7-8 as printed instead of the format's exact steps
 };
+
+// emulation variant of the block features: bit 0 signed, bit 1 literal
+__host__ __device__ inline int emulation_variant(const TrainDev &D) { return (D.is_signed ? 1 : 0) | (D.literal ? 2 : 0); }
 
 // floats of one texture's feature array
 inline int64_t feature_floats(const TrainDev &D, int t) { return D.tex[t].blocks * (D.unconstrained ? 4 : 32); }

@@ -52,6 +52,10 @@ bcf_status bcf_trainer_create(const bcf_trainer_desc *d, bcf_trainer *out)
     D.n_tex = d->num_textures;
     D.lod_input = d->lod_input != 0;
     D.unconstrained = d->unconstrained != 0;
+    D.is_signed = d->is_signed != 0;
+    D.literal = d->literal != 0;
+    if (D.unconstrained && (D.is_signed || D.literal))
+        return tfail(BCF_ERR_INVALID_ARG, "unconstrained features have no BC6 emulation variant");
     for (int t = 0; t < D.n_tex; ++t) {
         const int res = d->res[t];
         if (!pow2(res) || res < 4 || res > 32768)

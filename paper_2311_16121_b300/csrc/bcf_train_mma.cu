@@ -240,7 +240,7 @@ __device__ __forceinline__ void weight_grad(const uint32_t (&ghi)[2][MT][4], con
             }
 }
 
-template <bool FREE>
+template <bool FREE, int EMU>
 __global__ void __launch_bounds__(kThreads, 4) k_train_mma(TrainDev D, int mode, int64_t batch, uint32_t seed_lo,
                                                         uint32_t seed_hi, uint32_t step_lo, uint32_t step_hi,
                                                         const float *__restrict__ qu, const float *__restrict__ qv,
@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_train_mma(TrainDev D, int mode,
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         SteTexel tt;
-                        ste_from(P[j], tt);
+                        ste_from_v<EMU>(P[j], tt);
 #pragma unroll
                         for (int c = 0; c < 3; ++c)
                             f[c] = fmaf(tp[j].weight, tt.v[c], f[c]);
@@ -529,7 +529,7 @@ __global__ void __launch_bounds__(kThreads, 4) k_train_mma(TrainDev D, int mode,
                     for (int j = 0; j < 4; ++j) {
                         const Tap &tp = tps[j];
                         SteTexel tt;
-                        ste_from(P[j], tt);
+                        ste_from_v<EMU>(P[j], tt);
                         float ga[3], gb[3], gx = 0.0f;
 #pragma unroll
                         for (int c = 0; c < 3; ++c) {
@@ -598,7 +598,11 @@ cudaError_t launch_train_mma(const TrainDev &D, int mode, int64_t batch, uint64_
                              const float *u, const float *v, const float *s, float *out, const float *grad_out,
                              float *loss, int sms, cudaStream_t st)
 {
-    const auto kern = D.unconstrained ? k_train_mma<true> : k_train_mma<false>;
+    static void (*const kernels[5])(TrainDev, int, int64_t, uint32_t, uint32_t, uint32_t, uint32_t, const float *,
+                                    const float *, const float *, float *, const float *, float *, float) = {
+        k_train_mma<false, 0>, k_train_mma<false, 1>, k_train_mma<false, 2>, k_train_mma<false, 3>,
+        k_train_mma<true, 0>};
+    const auto kern = kernels[D.unconstrained ? 4 : emulation_variant(D)];
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0);
     const int64_t tiles = (batch + kThreads - 1) / kThreads;

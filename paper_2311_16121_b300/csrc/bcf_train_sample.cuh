@@ -66,8 +66,38 @@ __device__ __forceinline__ void load_texel(const float *p, int k, int t, TexelPa
     P.x = p[16 + t];
 }
 
-__device__ __forceinline__ void ste_from(const TexelParams &P, SteTexel &o)
+// SF16 unquantisation of a 6-bit two's complement code (sign carried, saturating at |e| >= 31)
+__device__ __forceinline__ int unq6s(int q)
 {
+    const int m = q < 0 ? -q : q;
+    const int u = m == 0 ? 0 : (m >= 31 ? 0x7FFF : m * 1024 + 512);
+    return q < 0 ? -u : u;
+}
+
+// Eq. 9 on a real coordinate (sign carried): 2^(h - 14) (|y| / 1024 - h), h = max(floor((|y| - 1) / 1024) - 1, 0);
+// its slope 2^(h - 24) through `slope`
+__device__ __forceinline__ float eq9_real(float y, float &slope)
+{
+    const float a = fabsf(y);
+    const int h = max((int)floorf((a - 1.0f) * (1.0f / 1024.0f)) - 1, 0);
+    slope = ldexpf(1.0f, h - 24);
+    const float w = ldexpf(a * (1.0f / 1024.0f) - (float)h, h - 14);
+    return y < 0.0f ? -w : w;
+}
+
+// The emulated texel (Sec. 4.2) for the four variants EMU = signed (bit 0) | literal (bit 1):
+//  exact:   the format's integer steps on the rounded codes (UF16: unquantise 1024 e + 512 with 0 and 63
+//           special, >> 6 interpolation, x 31/64; SF16: sign-magnitude, saturating, x 31/32), the result read
+//           as a half (Eq. 9 on the integer), so the value is the decode of the exported block;
+//  literal: Eq. 7-8 as printed on the rounded codes ((a 2^16 e + 2^15) / 2^6, real interpolation), Eq. 9 on
+//           the real result.
+// Partials: the relaxed pipeline's (a 1024 per endpoint unit times the interpolation weight, the index
+// coordinate through w / 64, the slope of Eq. 9) at the forward values.
+template <int EMU>
+__device__ __forceinline__ void ste_from_v(const TexelParams &P, SteTexel &o)
+{
+    constexpr bool SGN = (EMU & 1) != 0, LIT = (EMU & 2) != 0;
+    constexpr float lo = SGN ? -32.0f : 0.0f, hi = SGN ? 31.0f : 63.0f;
     o.region = P.region;
     const float ea[3] = {P.a.x, P.a.y, P.a.z}, eb[3] = {P.a.w, P.b.x, P.b.y};
     const float x = P.x;
@@ -75,26 +105,57 @@ __device__ __forceinline__ void ste_from(const TexelParams &P, SteTexel &o)
     const int w = weight3((int)rintf(7.0f * fminf(fmaxf(x, 0.0f), 1.0f)));
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        o.ina[c] = ea[c] >= 0.0f && ea[c] <= 63.0f;
-        o.inb[c] = eb[c] >= 0.0f && eb[c] <= 63.0f;
-        const int ua = unq6(ea[c]), ub = unq6(eb[c]);
-        const int yi = (64 * ua + 32 + (ub - ua) * w) >> 6;
-        const int y = (yi * 31) >> 6;
-        o.v[c] = __half2float(__ushort_as_half((unsigned short)y));
-        // slope of Eq. 9: 2^(h - 14) / 1024 with h = max(floor((y - 1) / 1024) - 1, 0); times 31/64
-        const int h = max(((y - 1) >> 10) - 1, 0);
-        const float dy = ldexpf(31.0f, h - 30);
-        o.dea[c] = dy * (float)((64 - w) * 16);
-        o.deb[c] = dy * (float)(w * 16);
-        o.dx[c] = dy * (float)(ub - ua);
+        o.ina[c] = ea[c] >= lo && ea[c] <= hi;
+        o.inb[c] = eb[c] >= lo && eb[c] <= hi;
+        const int qa = (int)rintf(fminf(fmaxf(ea[c], lo), hi)), qb = (int)rintf(fminf(fmaxf(eb[c], lo), hi));
+        float slope, span;
+        if (!LIT) {
+            const int ua = SGN ? unq6s(qa) : (qa == 0 ? 0 : (qa == 63 ? 0xFFFF : qa * 1024 + 512));
+            const int ub = SGN ? unq6s(qb) : (qb == 0 ? 0 : (qb == 63 ? 0xFFFF : qb * 1024 + 512));
+            const int yi = (64 * ua + 32 + (ub - ua) * w) >> 6; // arithmetic shift: floor for SF16 too
+            const bool neg = SGN && yi < 0;
+            const int mag = SGN ? (((neg ? -yi : yi) * 31) >> 5) : ((yi * 31) >> 6);
+            const float v = __half2float(__ushort_as_half((unsigned short)mag));
+            o.v[c] = neg && mag ? -v : v;
+            // slope of Eq. 9 at the integer magnitude, times a
+            const int h = max(((mag - 1) >> 10) - 1, 0);
+            slope = ldexpf(31.0f, h - (SGN ? 29 : 30));
+            span = (float)(ub - ua);
+        } else {
+            constexpr float a = SGN ? 31.0f / 32.0f : 31.0f / 64.0f;
+            const float ua = a * 1024.0f * (float)qa + 512.0f, ub = a * 1024.0f * (float)qb + 512.0f;
+            const float y = ua + ((float)w * (1.0f / 64.0f)) * (ub - ua);
+            float s9;
+            o.v[c] = eq9_real(y, s9);
+            slope = s9 * a;
+            span = (ub - ua) * (1.0f / a);
+        }
+        o.dea[c] = slope * (float)((64 - w) * 16);
+        o.deb[c] = slope * (float)(w * 16);
+        o.dx[c] = slope * span;
     }
 }
+
+__device__ __forceinline__ void ste_from(const TexelParams &P, SteTexel &o) { ste_from_v<0>(P, o); }
 
 __device__ __forceinline__ void ste_texel(const float *p, int k, int t, SteTexel &o)
 {
     TexelParams P;
     load_texel(p, k, t, P);
     ste_from(P, o);
+}
+
+// runtime-selected variant (the SIMT training kernel)
+__device__ __forceinline__ void ste_texel_v(const float *p, int k, int t, int emu, SteTexel &o)
+{
+    TexelParams P;
+    load_texel(p, k, t, P);
+    switch (emu) {
+    case 1: ste_from_v<1>(P, o); break;
+    case 2: ste_from_v<2>(P, o); break;
+    case 3: ste_from_v<3>(P, o); break;
+    default: ste_from_v<0>(P, o); break;
+    }
 }
 
 // Fire-and-forget vector reductions into the gradient arrays.  The kernels never read a gradient they add

@@ -64,6 +64,26 @@ def eval_psnr(tr: Trainer, w: wl.TrainWorkload, max_queries: int = 1 << 22) -> t
     return psnr(float(np.mean(mses))), [psnr(m) for m in mses]
 
 
+def eval_psnr_exported(tr: Trainer, w: wl.TrainWorkload, is_signed: bool = False,
+                       max_queries: int = 1 << 22) -> tuple[float, list[float]]:
+    """The same PSNR for what a renderer sees: the trainer's export (BC6H mode-10 blocks and FP16 weights)
+    decoded by the decode path (bcf_decode_material, plain FP32 evaluation of the FP16 weights)."""
+    from . import Material
+
+    blocks, w16 = tr.export()
+    Wf = w16.view(torch.float16).float().contiguous()
+    mat = Material(blocks, w.res, w.levels, w.res_ref, w.dims, "fp32", Wf, tr.b.contiguous(), is_signed=is_signed)
+
+    class _Decoded:
+        W = tr.W
+
+        @staticmethod
+        def forward(u, v, s):
+            return mat.decode(u, v, s, out_dtype=torch.float32)
+
+    return eval_psnr(_Decoded, w, max_queries)
+
+
 def _run(tr: Trainer, w: wl.TrainWorkload, name: str, steps: int, batch: int, seed: int, step0: int,
          eval_queries: int) -> StageLog:
     first = float(tr.step(batch, seed, step0).item()) if steps else float("nan")
@@ -79,8 +99,9 @@ def _run(tr: Trainer, w: wl.TrainWorkload, name: str, steps: int, batch: int, se
 
 
 def three_stage(w: wl.TrainWorkload, warmup_steps: int = 5000, bc_steps: int = 20000, finetune_steps: int = 1000,
-                batch: int | None = None, seed: int = 11, eval_queries: int = 1 << 22):
-    """Runs the schedule; returns (block trainer after stage 3, partitions, stage logs)."""
+                batch: int | None = None, seed: int = 11, eval_queries: int = 1 << 22, literal: bool = False):
+    """Runs the schedule; returns (block trainer after stage 3, partitions, stage logs).  `literal` trains the
+    block stages with Eq. 7-8 as printed instead of the format's exact steps."""
     batch = w.batch if batch is None else batch
     logs = []
     # stage 1: unconstrained features (lr 5e-2 / 1e-3, decay 0.9995)
@@ -97,11 +118,11 @@ def three_stage(w: wl.TrainWorkload, warmup_steps: int = 5000, bc_steps: int = 2
     del tr0
     # stage 2: block parameters through the emulated BC6 decompression (lr 1e-2 / 1e-3, decay 0.9999)
     tr1 = Trainer(params, parts, w.res, w.levels, w.res_ref, w.dims, W, b, t8, t1, w.target_res, w.target_levels,
-                  lr_features=1e-2, lr_mlp=1e-3, gamma=0.9999)
+                  lr_features=1e-2, lr_mlp=1e-3, gamma=0.9999, literal=literal)
     logs.append(_run(tr1, w, "block", bc_steps, batch, seed, warmup_steps, eval_queries))
     # stage 3: features frozen (on the lattice by construction), MLP fine-tuned
     tr2 = Trainer(tr1.params, parts, w.res, w.levels, w.res_ref, w.dims, tr1.W, tr1.b, t8, t1, w.target_res,
-                  w.target_levels, lr_features=0.0, lr_mlp=1e-3, gamma=0.9999)
+                  w.target_levels, lr_features=0.0, lr_mlp=1e-3, gamma=0.9999, literal=literal)
     logs.append(_run(tr2, w, "finetune", finetune_steps, batch, seed, warmup_steps + bc_steps, eval_queries))
     return tr2, parts, logs
 
