@@ -438,9 +438,20 @@ bcf_status bcf_encode_mode10(const float *d_texels, int32_t texel_stride, int32_
  * their footprints touch (blocks mode-sorted, texels staged in shared
  * memory); falls back per tile to 1 when the tile's blocks do not fit.
  * 1: per-lane decode -- every query decodes the blocks of its own
- * footprints.  Both compute the same values.  FP32 materials always use the
- * per-lane SIMT path.  Errors: BCF_ERR_INVALID_ARG for a null material or
- * another variant.
+ * footprints.  Both compute the same values.
+ * 2: texture unit -- the render-time design of Sec. 5.2: the feature
+ * textures are sampled through BC6H texture objects with hardware trilinear
+ * filtering (mipmapped CUDA arrays; the hardware decodes the blocks), then
+ * the same tensor-core MLP.  The hardware's filter and LOD weights are
+ * low-precision fixed point, so its outputs differ from variants 0 and 1 by
+ * a bounded filtering error: a comparison path, not a parity one.  Setting
+ * variant 2 allocates the mipmapped arrays and copies the blocks into them
+ * (synchronously, once per material; later changes of the caller's block
+ * arrays are not seen by this variant); they are freed with the material.
+ * FP32 materials always use the per-lane SIMT path.
+ * Errors: BCF_ERR_INVALID_ARG for a null material or another variant;
+ * BCF_ERR_UNSUPPORTED for variant 2 on an FP32 material; BCF_ERR_CUDA if the
+ * texture objects cannot be created.
  */
 bcf_status bcf_set_decode_variant(bcf_material mat, int32_t variant);
 

@@ -217,7 +217,7 @@ class Material:
         self.precision = precision
 
     def set_decode_variant(self, variant: int) -> None:
-        """bcf_set_decode_variant: 0 tile-cooperative (default), 1 per-lane."""
+        """bcf_set_decode_variant: 0 tile-cooperative (default), 1 per-lane, 2 texture unit (hardware trilinear)."""
         _check(lib().bcf_set_decode_variant(self.handle, int(variant)), "bcf_set_decode_variant")
 
     def close(self) -> None:

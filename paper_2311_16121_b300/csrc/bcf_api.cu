@@ -205,6 +205,10 @@ bcf_status bcf_create_material(const bcf_material_desc *d, bcf_material *out)
     m->host = M;
     m->dev = nullptr;
     m->variant = 0;
+    m->hw = TexUnitObjs{};
+    for (int t = 0; t < BCF_MAX_TEX; ++t)
+        m->hw_arrays[t] = nullptr;
+    m->hw_ready = 0;
     cudaGetDevice(&m->device);
     cudaError_t e = cudaMalloc(&m->dev, sizeof(MaterialDev));
     if (e != cudaSuccess) {
@@ -223,8 +227,19 @@ bcf_status bcf_create_material(const bcf_material_desc *d, bcf_material *out)
 
 bcf_status bcf_set_decode_variant(bcf_material m, int32_t variant)
 {
-    if (!m || variant < 0 || variant > 1)
-        return fail(BCF_ERR_INVALID_ARG, "bcf_set_decode_variant: null material or variant not in {0, 1}");
+    if (!m || variant < 0 || variant > 2)
+        return fail(BCF_ERR_INVALID_ARG, "bcf_set_decode_variant: null material or variant not in {0, 1, 2}");
+    if (variant == 2) {
+        if (m->host.mlp.precision == BCF_FP32)
+            return fail(BCF_ERR_UNSUPPORTED, "bcf_set_decode_variant: the texture-unit variant needs a tensor-core "
+                                             "(FP16 / BF16 / FP8) material");
+        if (!m->hw_ready) {
+            cudaError_t e = texunit_create(m->host, m->hw, m->hw_arrays);
+            if (e != cudaSuccess)
+                return cuda_status(e, "bcf_set_decode_variant: texture-unit textures");
+            m->hw_ready = 1;
+        }
+    }
     m->variant = variant;
     return BCF_OK;
 }
@@ -233,6 +248,8 @@ bcf_status bcf_destroy_material(bcf_material m)
 {
     if (!m)
         return BCF_OK;
+    if (m->hw_ready)
+        texunit_destroy(m->hw, m->hw_arrays, m->host.n_tex);
     cudaError_t e = cudaFree(m->dev);
     delete m;
     return cuda_status(e, "cudaFree(material metadata)");
@@ -270,6 +287,8 @@ bcf_status bcf_decode_material(bcf_material m, const float *d_u, const float *d_
         e = launch_decode_fp32(m->host, d_u, d_v, d_s, n, d_out, fp16, (cudaStream_t)stream);
     else if (m->variant == 1)
         e = launch_decode_mma(m->host, d_u, d_v, d_s, n, d_out, fp16, (cudaStream_t)stream);
+    else if (m->variant == 2)
+        e = launch_decode_texunit(m->host, m->hw, d_u, d_v, d_s, n, d_out, fp16, (cudaStream_t)stream);
     else
         e = launch_decode_tiled(m->host, d_u, d_v, d_s, n, d_out, fp16, (cudaStream_t)stream);
     return cuda_status(e, "bcf_decode_material launch");

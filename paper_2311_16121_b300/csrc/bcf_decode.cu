@@ -154,8 +154,8 @@ __host__ __device__ inline int mma_per_warp_bytes(int act_bytes, int C, int n_in
 // One warp per tile of 32 queries: per-lane unpack + filter of its query,
 // the quantised feature row goes to the warp's activation tile, the MLP runs
 // on the tensor cores, the [32][C] result is staged and stored coalesced.
-template <int PREC>
-__global__ void __launch_bounds__(128) k_decode_mma(MaterialDev M, const float *__restrict__ u,
+template <int PREC, bool HW>
+__global__ void __launch_bounds__(128) k_decode_mma(MaterialDev M, TexUnitObjs T, const float *__restrict__ u,
                                                     const float *__restrict__ v, const float *__restrict__ s,
                                                     int64_t n, void *__restrict__ out, int out_fp16, int act_bytes)
 {
@@ -184,7 +184,10 @@ __global__ void __launch_bounds__(128) k_decode_mma(MaterialDev M, const float *
     for (int64_t tile = blockIdx.x * (int64_t)(blockDim.x >> 5) + warp; tile < tiles; tile += warps_total) {
         const int64_t q = tile * 32 + lane;
         if (q < n) {
-            query_features(M, u[q], v[q], s ? s[q] : 0.0f, frow);
+            if (HW)
+                query_features_hw(M, T, u[q], v[q], s ? s[q] : 0.0f, frow);
+            else
+                query_features(M, u[q], v[q], s ? s[q] : 0.0f, frow);
         } else {
             for (int i = 0; i < M.n_in; ++i)
                 frow[i] = 0.0f;
@@ -293,15 +296,15 @@ int64_t mma_smem_bytes(const MlpDev &P, int warps)
            (int64_t)warps * per_warp;
 }
 
-template <int PREC>
-static cudaError_t launch_mma(const MaterialDev &M, const float *u, const float *v, const float *s, int64_t n,
-                              void *out, int out_fp16, cudaStream_t st)
+template <int PREC, bool HW>
+static cudaError_t launch_mma(const MaterialDev &M, const TexUnitObjs &T, const float *u, const float *v,
+                              const float *s, int64_t n, void *out, int out_fp16, cudaStream_t st)
 {
     const int threads = 128;
     const int64_t smem = mma_smem_bytes<PREC>(M.mlp, threads / 32);
     if (smem > 200 * 1024)
         return cudaErrorInvalidConfiguration;
-    auto kern = k_decode_mma<PREC>;
+    auto kern = k_decode_mma<PREC, HW>;
     static int configured = 0;
     if (!configured) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -310,7 +313,7 @@ static cudaError_t launch_mma(const MaterialDev &M, const float *u, const float 
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, threads, (size_t)smem);
     const unsigned grid = grid_for((n + 31) / 32, threads / 32, max(per_sm, 1));
-    kern<<<grid, threads, (size_t)smem, st>>>(M, u, v, s, n, out, out_fp16, mma_act_bytes<PREC>(M.mlp));
+    kern<<<grid, threads, (size_t)smem, st>>>(M, T, u, v, s, n, out, out_fp16, mma_act_bytes<PREC>(M.mlp));
     return cudaGetLastError();
 }
 
@@ -319,10 +322,24 @@ cudaError_t launch_decode_mma(const MaterialDev &M, const float *u, const float 
 {
     if (n == 0)
         return cudaSuccess;
+    const TexUnitObjs none = {};
     switch (M.mlp.precision) {
-    case BCF_FP16: return launch_mma<BCF_FP16>(M, u, v, s, n, out, out_fp16, st);
-    case BCF_BF16: return launch_mma<BCF_BF16>(M, u, v, s, n, out, out_fp16, st);
-    case BCF_FP8_E4M3: return launch_mma<BCF_FP8_E4M3>(M, u, v, s, n, out, out_fp16, st);
+    case BCF_FP16: return launch_mma<BCF_FP16, false>(M, none, u, v, s, n, out, out_fp16, st);
+    case BCF_BF16: return launch_mma<BCF_BF16, false>(M, none, u, v, s, n, out, out_fp16, st);
+    case BCF_FP8_E4M3: return launch_mma<BCF_FP8_E4M3, false>(M, none, u, v, s, n, out, out_fp16, st);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_decode_texunit(const MaterialDev &M, const TexUnitObjs &T, const float *u, const float *v,
+                                  const float *s, int64_t n, void *out, int out_fp16, cudaStream_t st)
+{
+    if (n == 0)
+        return cudaSuccess;
+    switch (M.mlp.precision) {
+    case BCF_FP16: return launch_mma<BCF_FP16, true>(M, T, u, v, s, n, out, out_fp16, st);
+    case BCF_BF16: return launch_mma<BCF_BF16, true>(M, T, u, v, s, n, out, out_fp16, st);
+    case BCF_FP8_E4M3: return launch_mma<BCF_FP8_E4M3, true>(M, T, u, v, s, n, out, out_fp16, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -36,6 +36,12 @@ struct MlpDev {
     int32_t smem_b_floats;             // padded biases
 };
 
+// Texture objects of a material's feature textures for the texture-unit decode: BC6H views of mipmapped
+// CUDA arrays, hardware trilinear filtering (cudaTextureObject_t values).
+struct TexUnitObjs {
+    unsigned long long tex[BCF_MAX_TEX];
+};
+
 struct MaterialDev {
     int32_t n_tex;
     int32_t is_signed;
@@ -62,5 +68,8 @@ struct bcf_material_s {
     bcf::MaterialDev host;   // host copy (passed by value to single-material kernels)
     bcf::MaterialDev *dev;   // device copy (batched kernels)
     int device;
-    int variant;             // tensor-core decode: 0 tile-cooperative, 1 per-lane
+    int variant;             // tensor-core decode: 0 tile-cooperative, 1 per-lane, 2 texture unit
+    bcf::TexUnitObjs hw;     // variant 2: BC6H texture objects with hardware trilinear filtering
+    void *hw_arrays[BCF_MAX_TEX];
+    int hw_ready;
 };

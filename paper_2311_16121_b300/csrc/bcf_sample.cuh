@@ -99,4 +99,24 @@ __device__ __forceinline__ void query_features(const MaterialDev &M, float u, fl
         row[3 * M.n_tex] = isnan(s) ? 0.0f : fmaxf(s, 0.0f);
 }
 
+// The same features through the texture unit (the render-time design of Sec. 5.2): hardware trilinear
+// filtering of the BC6H textures at the per-texture LOD of Eq. 11.  The hardware's filter weights are low-
+// precision fixed point, so these features differ from query_features by a bounded filtering error.
+__device__ __forceinline__ void query_features_hw(const MaterialDev &M, const TexUnitObjs &T, float u, float v,
+                                                  float s, float *row)
+{
+    const float uu = sanitize(u, M.wrap), vv = sanitize(v, M.wrap);
+    const float sq = isnan(s) ? 0.0f : s;
+#pragma unroll 1
+    for (int t = 0; t < M.n_tex; ++t) {
+        const float lod = fminf(fmaxf(sq + (float)M.tex[t].lod_bias, 0.0f), (float)(M.tex[t].levels - 1));
+        const float4 f = tex2DLod<float4>((cudaTextureObject_t)T.tex[t], uu, vv, lod);
+        row[3 * t] = f.x;
+        row[3 * t + 1] = f.y;
+        row[3 * t + 2] = f.z;
+    }
+    if (M.lod_input)
+        row[3 * M.n_tex] = isnan(s) ? 0.0f : fmaxf(s, 0.0f);
+}
+
 } // namespace bcf

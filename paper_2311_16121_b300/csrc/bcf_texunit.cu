@@ -1,8 +1,13 @@
-// bcf_texunit.cu -- BC6H decode by the GPU texture unit: the blocks are
-// copied into a CUDA array of 16-byte elements and viewed as a BC6H texture
-// (a resource view with a block-compressed format), then every texel centre
-// is fetched with point filtering.  An independent statement of the format,
-// used to check the integer decoder and the CPU oracle; not a hot path.
+// bcf_texunit.cu -- the GPU texture unit on BC6H data: the blocks are copied
+// into CUDA arrays of 16-byte elements and viewed as BC6H textures (resource
+// views with a block-compressed format).
+//  * texunit_decode: every texel centre fetched with point filtering -- an
+//    independent statement of the format, used to check the integer decoder
+//    and the CPU oracle; not a hot path.
+//  * texunit_create: a material's feature textures as mipmapped CUDA arrays
+//    of the BC6H channel format with hardware trilinear filtering (the
+//    render-time design of Sec. 5.2), sampled by the texture-unit decode
+//    variant.
 #include <cuda_fp16.h>
 
 #include "bcf_kernels.h"
@@ -67,6 +72,77 @@ cudaError_t texunit_decode(const void *d_blocks, int bw, int bh, int is_signed, 
         cudaDestroyTextureObject(tex);
     if (arr)
         cudaFreeArray(arr);
+    return e;
+}
+
+void texunit_destroy(TexUnitObjs &T, void **arrays, int n_tex)
+{
+    for (int t = 0; t < n_tex; ++t) {
+        if (T.tex[t])
+            cudaDestroyTextureObject((cudaTextureObject_t)T.tex[t]);
+        if (arrays[t])
+            cudaFreeMipmappedArray((cudaMipmappedArray_t)arrays[t]);
+        T.tex[t] = 0;
+        arrays[t] = nullptr;
+    }
+}
+
+cudaError_t texunit_create(const MaterialDev &M, TexUnitObjs &T, void **arrays)
+{
+    for (int t = 0; t < BCF_MAX_TEX; ++t) {
+        T.tex[t] = 0;
+        arrays[t] = nullptr;
+    }
+    // arrays of the BC6H channel format itself (texels as the extent): the texture unit filters them as floats
+    const cudaChannelFormatDesc cd = cudaCreateChannelDesc(
+        16, 16, 16, 0,
+        M.is_signed ? cudaChannelFormatKindSignedBlockCompressed6H : cudaChannelFormatKindUnsignedBlockCompressed6H);
+    cudaError_t e = cudaSuccess;
+    for (int t = 0; t < M.n_tex && e == cudaSuccess; ++t) {
+        const TexDev &X = M.tex[t];
+        const int wb0 = X.res / 4;
+        cudaMipmappedArray_t mip = nullptr;
+        e = cudaMallocMipmappedArray(&mip, &cd, make_cudaExtent((size_t)X.res, (size_t)X.res, 0), (unsigned)X.levels);
+        if (e != cudaSuccess) {
+            set_error("cudaMallocMipmappedArray: %s", cudaGetErrorString(e));
+            break;
+        }
+        arrays[t] = mip;
+        for (int l = 0; l < X.levels && e == cudaSuccess; ++l) {
+            cudaArray_t lvl = nullptr;
+            e = cudaGetMipmappedArrayLevel(&lvl, mip, (unsigned)l);
+            const size_t wb = (size_t)max(wb0 >> l, 1);
+            // block-compressed arrays are copied as rows of blocks: 16 bytes per block, one row per 4 texel rows
+            if (e == cudaSuccess)
+                e = cudaMemcpy2DToArray(lvl, 0, 0, X.blocks + X.level_off[l], wb * 16, wb * 16, wb,
+                                        cudaMemcpyDeviceToDevice);
+            if (e != cudaSuccess)
+                set_error("texture level %d of texture %d: %s", l, t, cudaGetErrorString(e));
+        }
+        if (e != cudaSuccess)
+            break;
+        cudaResourceDesc rd = {};
+        rd.resType = cudaResourceTypeMipmappedArray;
+        rd.res.mipmap.mipmap = mip;
+        cudaTextureDesc td = {};
+        const cudaTextureAddressMode am = M.wrap ? cudaAddressModeWrap : cudaAddressModeClamp;
+        td.addressMode[0] = td.addressMode[1] = am;
+        td.filterMode = cudaFilterModeLinear;
+        td.mipmapFilterMode = cudaFilterModeLinear;
+        td.readMode = cudaReadModeElementType;
+        td.normalizedCoords = 1;
+        td.minMipmapLevelClamp = 0.0f;
+        td.maxMipmapLevelClamp = (float)(X.levels - 1);
+        cudaTextureObject_t tex = 0;
+        e = cudaCreateTextureObject(&tex, &rd, &td, nullptr);
+        if (e != cudaSuccess) {
+            set_error("cudaCreateTextureObject (mipmapped BC6H): %s", cudaGetErrorString(e));
+            break;
+        }
+        T.tex[t] = (unsigned long long)tex;
+    }
+    if (e != cudaSuccess)
+        texunit_destroy(T, arrays, M.n_tex);
     return e;
 }
 
