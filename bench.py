@@ -55,7 +55,7 @@ def _peaks():
 # capture summarised in profiles/k_decode_tiled_screen2048_fp16.md.  They are reported only while the
 # kernel's sources hash to the value the capture was taken on; after any change they read as null.
 KERNEL_SOURCES = ["bcf_decode_tiled.cu", "bc6h_unpack.cuh", "bcf_sample.cuh", "bcf_mlp.cuh", "bcf_internal.h"]
-NCU_CAPTURE = {"source_sha256": "fb9af4a4c39d52dd", "dram_bytes": 121182208 + 104522240, "warp_inst": 703194424}
+NCU_CAPTURE = {"source_sha256": "4f1d3eff1fd60344", "dram_bytes": 121091328 + 104757248, "warp_inst": 703194380}
 SM_COUNT, SMSP_PER_SM, FP32_LANES_PER_SM = 148, 4, 128
 
 
@@ -341,6 +341,16 @@ def main():
     fp32_ms = timed(mats["fp32"], k_extra, 3, out=out32) / k_extra
     fp8_ms = timed(mats["fp8"], k_extra, 3) / k_extra
 
+    # the texture-unit comparator (decode variant 2: hardware trilinear filtering of BC6H texture objects)
+    m_hw = workloads.upload(w, HEADLINE_PRECISION)
+    m_hw.set_decode_variant(2)
+    hw_out = torch.empty_like(out)
+    hw_ms = timed(m_hw, k_extra, 3, out=hw_out) / k_extra
+    mats[HEADLINE_PRECISION].decode(u, v, s, out=out)
+    hw_err = (hw_out.float() - out.float()).abs()
+    hw_stats = {"mean_abs_vs_software": float(hw_err.mean()), "max_abs_vs_software": float(hw_err.max())}
+    del m_hw, hw_out, hw_err
+
     def gathered(prec):
         """Outputs of one untimed decode of `prec` (in the timed path's output type) at query indices."""
         o = torch.empty_like(out32 if prec == "fp32" else out)
@@ -386,6 +396,21 @@ def main():
     e2e_value = w.n * world * k_extra / (e2e_total * 1e-3) / 1e9
 
     train_ms, train_loss, train_batch = _train_bench(torch, workloads, stream, max(3, args.steps // 2))
+    # first training stage (unconstrained per-texel features), same sizes and batch
+    tw0 = workloads.train_workload()
+    tr0 = workloads.upload_free_trainer(tw0, lr_features=5e-2, lr_mlp=1e-3, gamma=0.9995)
+    for i in range(3):
+        tr0.step(tw0.batch, 7, i)
+    torch.cuda.synchronize()
+    fa, fb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    fa.record(stream)
+    k_free = max(3, args.steps // 2)
+    for i in range(k_free):
+        tr0.step(tw0.batch, 7, 3 + i)
+    fb.record(stream)
+    fb.synchronize()
+    free_ms = fa.elapsed_time(fb) / k_free
+    del tr0, tw0
 
     # partition-selection encoder: 4 textures of 1024^2 with 9 levels (87,381 blocks each), smooth RGB texels
     enc_res, enc_levels = 1024, 9
@@ -539,6 +564,12 @@ def main():
                       "samples_per_s": train_batch * 1000.0 / train_ms,
                       "workload": "4x block-parameterised 1024^2 (9 levels), 2048^2 9-ch reference, "
                                   "MLP 13-32-32-9 BF16 operands, Adam", "last_loss": train_loss},
+            "texunit": {"value": w.n / (hw_ms * 1e-3) / 1e9, "unit": "Gsamples/s", "ms_per_step": hw_ms,
+                        "precision": HEADLINE_PRECISION, "kernel": "decode variant 2: hardware trilinear filtering of "
+                        "mipmapped BC6H texture objects + tensor-core MLP (per-lane)", **hw_stats},
+            "train_unconstrained": {"metric": "train steps/s", "value": 1000.0 / free_ms, "unit": "steps/s",
+                                    "ms_per_step": free_ms, "batch": train_batch,
+                                    "workload": "first stage: free per-texel features, 4x 1024^2 with 9 levels"},
             "encode": {"metric": "blocks/s", "value": enc_blocks / (enc_ms * 1e-3), "ms": enc_ms,
                        "blocks": enc_blocks, "workload": "BC6H mode-10 partition selection (32 partitions per "
                                                          "block), 4x 1024^2 RGB textures with 9 levels, uniform texels"},
