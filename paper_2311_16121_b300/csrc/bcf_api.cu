@@ -227,9 +227,9 @@ bcf_status bcf_create_material(const bcf_material_desc *d, bcf_material *out)
 
 bcf_status bcf_set_decode_variant(bcf_material m, int32_t variant)
 {
-    if (!m || variant < 0 || variant > 2)
-        return fail(BCF_ERR_INVALID_ARG, "bcf_set_decode_variant: null material or variant not in {0, 1, 2}");
-    if (variant == 2) {
+    if (!m || variant < 0 || variant > 3)
+        return fail(BCF_ERR_INVALID_ARG, "bcf_set_decode_variant: null material or variant not in {0, 1, 2, 3}");
+    if (variant >= 2) {
         if (m->host.mlp.precision == BCF_FP32)
             return fail(BCF_ERR_UNSUPPORTED, "bcf_set_decode_variant: the texture-unit variant needs a tensor-core "
                                              "(FP16 / BF16 / FP8) material");
@@ -287,8 +287,9 @@ bcf_status bcf_decode_material(bcf_material m, const float *d_u, const float *d_
         e = launch_decode_fp32(m->host, d_u, d_v, d_s, n, d_out, fp16, (cudaStream_t)stream);
     else if (m->variant == 1)
         e = launch_decode_mma(m->host, d_u, d_v, d_s, n, d_out, fp16, (cudaStream_t)stream);
-    else if (m->variant == 2)
-        e = launch_decode_texunit(m->host, m->hw, d_u, d_v, d_s, n, d_out, fp16, (cudaStream_t)stream);
+    else if (m->variant >= 2)
+        e = launch_decode_texunit(m->host, m->hw, m->variant == 3, d_u, d_v, d_s, n, d_out, fp16,
+                                  (cudaStream_t)stream);
     else
         e = launch_decode_tiled(m->host, d_u, d_v, d_s, n, d_out, fp16, (cudaStream_t)stream);
     return cuda_status(e, "bcf_decode_material launch");

@@ -146,15 +146,25 @@ __global__ void __launch_bounds__(128) k_decode_fp32_generic(MaterialDev M, cons
 
 // ------------------------------------------------ fused decode, tensor cores
 
-__host__ __device__ inline int mma_per_warp_bytes(int act_bytes, int C, int n_in)
+__host__ __device__ inline int mma_per_warp_bytes(int act_bytes, int act1_bytes, int C, int n_in)
 {
-    return 2 * act_bytes + ((32 * C + 3) & ~3) * 4 + 32 * (n_in + 1) * 4;
+    return act_bytes + act1_bytes + ((32 * C + 3) & ~3) * 4 + 32 * (n_in + 1) * 4;
+}
+
+// Second activation buffer of a warp: the generic MLP ping-pongs two full tiles; the register-chained one
+// (three layers, K0 > 0) needs only FP8's 16-row re-quantisation tile, 16-bit operands none.
+template <int PREC, int K0, int N1, int N2>
+__host__ __device__ inline int mma_act1_bytes(int act_bytes)
+{
+    if (K0 == 0)
+        return act_bytes;
+    return PREC == BCF_FP8_E4M3 ? 16 * tile_stride_bytes<BCF_FP8_E4M3>(N1 > N2 ? N1 : N2) : 0;
 }
 
 // One warp per tile of 32 queries: per-lane unpack + filter of its query,
 // the quantised feature row goes to the warp's activation tile, the MLP runs
 // on the tensor cores, the [32][C] result is staged and stored coalesced.
-template <int PREC, bool HW>
+template <int PREC, int HW, int K0, int N1, int N2, int NO>
 __global__ void __launch_bounds__(128) k_decode_mma(MaterialDev M, TexUnitObjs T, const float *__restrict__ u,
                                                     const float *__restrict__ v, const float *__restrict__ s,
                                                     int64_t n, void *__restrict__ out, int out_fp16, int act_bytes)
@@ -169,10 +179,11 @@ __global__ void __launch_bounds__(128) k_decode_mma(MaterialDev M, TexUnitObjs T
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int C = P.dims[P.n_layers];
     // per warp: act0, act1 (act_bytes each), output staging [32][C] floats, feature rows [32][n_in + 1]
-    const int per_warp = mma_per_warp_bytes(act_bytes, C, M.n_in);
+    const int act1_bytes = mma_act1_bytes<PREC, K0, N1, N2>(act_bytes);
+    const int per_warp = mma_per_warp_bytes(act_bytes, act1_bytes, C, M.n_in);
     unsigned char *act0 = wbase + warp * per_warp;
     unsigned char *act1 = act0 + act_bytes;
-    float *ost = (float *)(act1 + act_bytes);
+    float *ost = (float *)(act1 + act1_bytes);
     float *frow = ost + ((32 * C + 3) & ~3) + lane * (M.n_in + 1);
 
     load_mlp_smem<PREC>(P, sw, sb);
@@ -184,8 +195,10 @@ __global__ void __launch_bounds__(128) k_decode_mma(MaterialDev M, TexUnitObjs T
     for (int64_t tile = blockIdx.x * (int64_t)(blockDim.x >> 5) + warp; tile < tiles; tile += warps_total) {
         const int64_t q = tile * 32 + lane;
         if (q < n) {
-            if (HW)
+            if (HW == 1)
                 query_features_hw(M, T, u[q], v[q], s ? s[q] : 0.0f, frow);
+            else if (HW == 2)
+                query_features_hwpoint(M, T, u[q], v[q], s ? s[q] : 0.0f, frow);
             else
                 query_features(M, u[q], v[q], s ? s[q] : 0.0f, frow);
         } else {
@@ -194,7 +207,11 @@ __global__ void __launch_bounds__(128) k_decode_mma(MaterialDev M, TexUnitObjs T
         }
         store_input_row<PREC>(P, frow, M.n_in, act0 + lane * row_stride);
         __syncwarp();
-        warp_mlp<PREC>(P, sw, sb, act0, act1, ost);
+        if constexpr (K0 == 0)
+            warp_mlp<PREC>(P, sw, sb, act0, act1, ost);
+        else // the common shapes: layers chained through registers (act1 is the FP8 re-quantisation tile)
+            warp_mlp3<PREC, K0, N1, N2, NO>(P, sw, sb, act0, row_stride, act1,
+                                            tile_stride_bytes<BCF_FP8_E4M3>(N1 > N2 ? N1 : N2), ost, C);
         __syncwarp();
         // coalesced store of the warp's rows [tile*32, tile*32 + rows)
         const int rows = (int)min((int64_t)32, n - tile * 32);
@@ -287,24 +304,25 @@ static int mma_act_bytes(const MlpDev &P)
     return (mx + 15) & ~15;
 }
 
-template <int PREC>
+template <int PREC, int K0 = 0, int N1 = 0, int N2 = 0>
 int64_t mma_smem_bytes(const MlpDev &P, int warps)
 {
     const int C = P.dims[P.n_layers];
-    const int per_warp = mma_per_warp_bytes(mma_act_bytes<PREC>(P), C, P.dims[0]);
+    const int act = mma_act_bytes<PREC>(P);
+    const int per_warp = mma_per_warp_bytes(act, mma_act1_bytes<PREC, K0, N1, N2>(act), C, P.dims[0]);
     return (int64_t)mlp_smem_weight_bytes<PREC>(P) + ((mlp_smem_bias_floats(P) * 4 + 15) & ~15) +
            (int64_t)warps * per_warp;
 }
 
-template <int PREC, bool HW>
-static cudaError_t launch_mma(const MaterialDev &M, const TexUnitObjs &T, const float *u, const float *v,
-                              const float *s, int64_t n, void *out, int out_fp16, cudaStream_t st)
+template <int PREC, int HW, int K0, int N1, int N2, int NO>
+static cudaError_t launch_mma_shape(const MaterialDev &M, const TexUnitObjs &T, const float *u, const float *v,
+                                    const float *s, int64_t n, void *out, int out_fp16, cudaStream_t st)
 {
     const int threads = 128;
-    const int64_t smem = mma_smem_bytes<PREC>(M.mlp, threads / 32);
+    const int64_t smem = mma_smem_bytes<PREC, K0, N1, N2>(M.mlp, threads / 32);
     if (smem > 200 * 1024)
         return cudaErrorInvalidConfiguration;
-    auto kern = k_decode_mma<PREC, HW>;
+    auto kern = k_decode_mma<PREC, HW, K0, N1, N2, NO>;
     static int configured = 0;
     if (!configured) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -317,6 +335,22 @@ static cudaError_t launch_mma(const MaterialDev &M, const TexUnitObjs &T, const 
     return cudaGetLastError();
 }
 
+template <int PREC, int HW>
+static cudaError_t launch_mma(const MaterialDev &M, const TexUnitObjs &T, const float *u, const float *v,
+                              const float *s, int64_t n, void *out, int out_fp16, cudaStream_t st)
+{
+    const MlpDev &P = M.mlp;
+    if (P.n_layers == 3) {
+        const int k0 = P.kpad[0], n1 = P.npad[0], n2 = P.npad[1], no = P.npad[2];
+        constexpr int kq = PREC == BCF_FP8_E4M3 ? 32 : 16;
+        if (k0 == kq && n1 == 32 && n2 == 32 && no == 16)
+            return launch_mma_shape<PREC, HW, kq, 32, 32, 16>(M, T, u, v, s, n, out, out_fp16, st);
+        if (k0 == 32 && n1 == 64 && n2 == 64 && no == 16)
+            return launch_mma_shape<PREC, HW, 32, 64, 64, 16>(M, T, u, v, s, n, out, out_fp16, st);
+    }
+    return launch_mma_shape<PREC, HW, 0, 0, 0, 0>(M, T, u, v, s, n, out, out_fp16, st);
+}
+
 cudaError_t launch_decode_mma(const MaterialDev &M, const float *u, const float *v, const float *s, int64_t n,
                               void *out, int out_fp16, cudaStream_t st)
 {
@@ -324,22 +358,25 @@ cudaError_t launch_decode_mma(const MaterialDev &M, const float *u, const float 
         return cudaSuccess;
     const TexUnitObjs none = {};
     switch (M.mlp.precision) {
-    case BCF_FP16: return launch_mma<BCF_FP16, false>(M, none, u, v, s, n, out, out_fp16, st);
-    case BCF_BF16: return launch_mma<BCF_BF16, false>(M, none, u, v, s, n, out, out_fp16, st);
-    case BCF_FP8_E4M3: return launch_mma<BCF_FP8_E4M3, false>(M, none, u, v, s, n, out, out_fp16, st);
+    case BCF_FP16: return launch_mma<BCF_FP16, 0>(M, none, u, v, s, n, out, out_fp16, st);
+    case BCF_BF16: return launch_mma<BCF_BF16, 0>(M, none, u, v, s, n, out, out_fp16, st);
+    case BCF_FP8_E4M3: return launch_mma<BCF_FP8_E4M3, 0>(M, none, u, v, s, n, out, out_fp16, st);
     default: return cudaErrorInvalidValue;
     }
 }
 
-cudaError_t launch_decode_texunit(const MaterialDev &M, const TexUnitObjs &T, const float *u, const float *v,
-                                  const float *s, int64_t n, void *out, int out_fp16, cudaStream_t st)
+cudaError_t launch_decode_texunit(const MaterialDev &M, const TexUnitObjs &T, int exact_filter, const float *u,
+                                  const float *v, const float *s, int64_t n, void *out, int out_fp16, cudaStream_t st)
 {
     if (n == 0)
         return cudaSuccess;
-    switch (M.mlp.precision) {
-    case BCF_FP16: return launch_mma<BCF_FP16, true>(M, T, u, v, s, n, out, out_fp16, st);
-    case BCF_BF16: return launch_mma<BCF_BF16, true>(M, T, u, v, s, n, out, out_fp16, st);
-    case BCF_FP8_E4M3: return launch_mma<BCF_FP8_E4M3, true>(M, T, u, v, s, n, out, out_fp16, st);
+    switch (M.mlp.precision * 2 + (exact_filter ? 1 : 0)) {
+    case BCF_FP16 * 2: return launch_mma<BCF_FP16, 1>(M, T, u, v, s, n, out, out_fp16, st);
+    case BCF_FP16 * 2 + 1: return launch_mma<BCF_FP16, 2>(M, T, u, v, s, n, out, out_fp16, st);
+    case BCF_BF16 * 2: return launch_mma<BCF_BF16, 1>(M, T, u, v, s, n, out, out_fp16, st);
+    case BCF_BF16 * 2 + 1: return launch_mma<BCF_BF16, 2>(M, T, u, v, s, n, out, out_fp16, st);
+    case BCF_FP8_E4M3 * 2: return launch_mma<BCF_FP8_E4M3, 1>(M, T, u, v, s, n, out, out_fp16, st);
+    case BCF_FP8_E4M3 * 2 + 1: return launch_mma<BCF_FP8_E4M3, 2>(M, T, u, v, s, n, out, out_fp16, st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -36,10 +36,12 @@ struct MlpDev {
     int32_t smem_b_floats;             // padded biases
 };
 
-// Texture objects of a material's feature textures for the texture-unit decode: BC6H views of mipmapped
-// CUDA arrays, hardware trilinear filtering (cudaTextureObject_t values).
+// Texture objects of a material's feature textures for the texture-unit decodes: mipmapped CUDA arrays of
+// the BC6H format (cudaTextureObject_t values); `tex` filters trilinearly in hardware, `texp` samples single
+// texels (point filtering at texel centres: the hardware's exact BC6H decode).
 struct TexUnitObjs {
     unsigned long long tex[BCF_MAX_TEX];
+    unsigned long long texp[BCF_MAX_TEX];
 };
 
 struct MaterialDev {
@@ -68,7 +70,8 @@ struct bcf_material_s {
     bcf::MaterialDev host;   // host copy (passed by value to single-material kernels)
     bcf::MaterialDev *dev;   // device copy (batched kernels)
     int device;
-    int variant;             // tensor-core decode: 0 tile-cooperative, 1 per-lane, 2 texture unit
+    int variant;             // tensor-core decode: 0 tile-cooperative, 1 per-lane, 2 texture unit (hardware
+                             // trilinear), 3 texture-unit texels with the exact FP32 filter
     bcf::TexUnitObjs hw;     // variant 2: BC6H texture objects with hardware trilinear filtering
     void *hw_arrays[BCF_MAX_TEX];
     int hw_ready;

@@ -9,8 +9,8 @@ namespace bcf {
 
 cudaError_t launch_encode_mode10(const float *texels, int stride, int res, int levels, int64_t nblocks,
                                  float *params, uint8_t *part, float *err, cudaStream_t st);
-cudaError_t launch_decode_texunit(const MaterialDev &M, const TexUnitObjs &T, const float *u, const float *v,
-                                  const float *s, int64_t n, void *out, int out_fp16, cudaStream_t st);
+cudaError_t launch_decode_texunit(const MaterialDev &M, const TexUnitObjs &T, int exact_filter, const float *u,
+                                  const float *v, const float *s, int64_t n, void *out, int out_fp16, cudaStream_t st);
 cudaError_t texunit_create(const MaterialDev &M, TexUnitObjs &T, void **arrays);
 void texunit_destroy(TexUnitObjs &T, void **arrays, int n_tex);
 cudaError_t launch_unpack_image(const void *blocks, int bw, int bh, int is_signed, uint16_t *out, cudaStream_t st);

@@ -119,4 +119,60 @@ __device__ __forceinline__ void query_features_hw(const MaterialDev &M, const Te
         row[3 * M.n_tex] = isnan(s) ? 0.0f : fmaxf(s, 0.0f);
 }
 
+// The exact features with the texels decoded by the texture unit: each footprint texel is fetched with point
+// filtering at its centre (the hardware BC6H decoder, bit-exact with bc6h_texel) and filtered here with the
+// same FP32 operations in the same order as sample_texture, so the features are identical to it.
+__device__ __forceinline__ float3 sample_texture_hwpoint(const TexDev &T, unsigned long long tex, int wrap, float u,
+                                                         float v, float s)
+{
+    float st = (isnan(s) ? 0.0f : s) + (float)T.lod_bias;
+    st = fminf(fmaxf(st, 0.0f), (float)(T.levels - 1));
+    const float fl = floorf(st);
+    const int l0 = (int)fl;
+    const float lam = st - fl;
+    const int nlev = (lam > 0.0f && l0 + 1 < T.levels) ? 2 : 1;
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
+#pragma unroll 1
+    for (int side = 0; side < nlev; ++side) {
+        const int level = l0 + side;
+        const float scale = nlev == 1 ? 1.0f : (side ? lam : 1.0f - lam);
+        const int W = T.res >> level;
+        const float x = u * (float)W - 0.5f, y = v * (float)W - 0.5f;
+        const float fx0 = floorf(x), fy0 = floorf(y);
+        const float fx = x - fx0, fy = y - fy0;
+        const int i0 = (int)fx0, j0 = (int)fy0;
+        const int ia = address(i0, W, wrap), ib = address(i0 + 1, W, wrap);
+        const int ja = address(j0, W, wrap), jb = address(j0 + 1, W, wrap);
+        const float rw = 1.0f / (float)W; // exact: W is a power of two
+        float4 c4[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) // texel centres (i + 1/2) / W are exact in FP32
+            c4[c] = tex2DLod<float4>((cudaTextureObject_t)tex, ((float)((c & 1) ? ib : ia) + 0.5f) * rw,
+                                     ((float)((c & 2) ? jb : ja) + 0.5f) * rw, (float)level);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            const float w = ((c & 1) ? fx : 1.0f - fx) * ((c & 2) ? fy : 1.0f - fy) * scale;
+            a0 = fmaf(w, c4[c].x, a0);
+            a1 = fmaf(w, c4[c].y, a1);
+            a2 = fmaf(w, c4[c].z, a2);
+        }
+    }
+    return make_float3(a0, a1, a2);
+}
+
+__device__ __forceinline__ void query_features_hwpoint(const MaterialDev &M, const TexUnitObjs &T, float u, float v,
+                                                       float s, float *row)
+{
+    const float uu = sanitize(u, M.wrap), vv = sanitize(v, M.wrap);
+#pragma unroll 1
+    for (int t = 0; t < M.n_tex; ++t) {
+        const float3 f = sample_texture_hwpoint(M.tex[t], T.texp[t], M.wrap, uu, vv, s);
+        row[3 * t] = f.x;
+        row[3 * t + 1] = f.y;
+        row[3 * t + 2] = f.z;
+    }
+    if (M.lod_input)
+        row[3 * M.n_tex] = isnan(s) ? 0.0f : fmaxf(s, 0.0f);
+}
+
 } // namespace bcf

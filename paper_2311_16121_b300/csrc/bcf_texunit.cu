@@ -80,6 +80,9 @@ void texunit_destroy(TexUnitObjs &T, void **arrays, int n_tex)
     for (int t = 0; t < n_tex; ++t) {
         if (T.tex[t])
             cudaDestroyTextureObject((cudaTextureObject_t)T.tex[t]);
+        if (T.texp[t])
+            cudaDestroyTextureObject((cudaTextureObject_t)T.texp[t]);
+        T.texp[t] = 0;
         if (arrays[t])
             cudaFreeMipmappedArray((cudaMipmappedArray_t)arrays[t]);
         T.tex[t] = 0;
@@ -91,6 +94,7 @@ cudaError_t texunit_create(const MaterialDev &M, TexUnitObjs &T, void **arrays)
 {
     for (int t = 0; t < BCF_MAX_TEX; ++t) {
         T.tex[t] = 0;
+        T.texp[t] = 0;
         arrays[t] = nullptr;
     }
     // arrays of the BC6H channel format itself (texels as the extent): the texture unit filters them as floats
@@ -140,6 +144,16 @@ cudaError_t texunit_create(const MaterialDev &M, TexUnitObjs &T, void **arrays)
             break;
         }
         T.tex[t] = (unsigned long long)tex;
+        // the same arrays sampled texel by texel: point filtering, point mip selection (integer LODs)
+        td.filterMode = cudaFilterModePoint;
+        td.mipmapFilterMode = cudaFilterModePoint;
+        tex = 0;
+        e = cudaCreateTextureObject(&tex, &rd, &td, nullptr);
+        if (e != cudaSuccess) {
+            set_error("cudaCreateTextureObject (mipmapped BC6H, point): %s", cudaGetErrorString(e));
+            break;
+        }
+        T.texp[t] = (unsigned long long)tex;
     }
     if (e != cudaSuccess)
         texunit_destroy(T, arrays, M.n_tex);

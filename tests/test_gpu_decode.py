@@ -167,12 +167,14 @@ def _quant_check(got, ref_q, tol, what):
     return worst, frac
 
 
+@pytest.mark.parametrize("variant", [0, 3])
 @pytest.mark.parametrize("precision", ["fp16", "bf16", "fp8"])
 @pytest.mark.parametrize("out_dtype", [torch.float32, torch.float16])
-def test_decode_tensor_core_paths_match_quant_aware_oracle(precision, out_dtype):
+def test_decode_tensor_core_paths_match_quant_aware_oracle(precision, out_dtype, variant):
     bcf = _bcf()
     w = workloads.small_screen(res=128, width=200, height=61)  # 12,200 queries: 381 warp tiles + a ragged tail
     m = workloads.upload(w, precision)
+    m.set_decode_variant(variant)
     u, v, s = workloads.queries_to_device(w)
     got = m.decode(u, v, s, out_dtype=out_dtype).cpu().numpy().astype(np.float64)
     Wst, bias, a, ws = w.weights(precision)
@@ -300,3 +302,43 @@ def test_texture_unit_variant_within_hardware_filter_error(precision):
     with pytest.raises(bcf.BcfError) as e:
         m32.set_decode_variant(2)
     assert e.value.status == 2
+
+
+@pytest.mark.parametrize("precision,signed", [("fp16", False), ("fp8", False), ("fp16", True)])
+def test_texture_unit_texels_with_exact_filter_equal_the_software_decode(precision, signed):
+    """Variant 3 fetches every footprint texel from the texture unit with point filtering (the hardware's BC6H
+    decoder, bit-exact with the software one) and filters it with the same FP32 operations as the per-lane
+    software path (variant 1): the outputs are identical bit for bit."""
+    bcf = _bcf()
+    w = workloads.small_screen(res=128, width=200, height=61)
+    if signed:
+        w.is_signed = True
+        rng = np.random.default_rng(5)
+        w.blocks = [synth.bounded_blocks(rng, b.size // 16, tuple(range(1, 15)), signed=True) for b in w.blocks]
+    m = workloads.upload(w, precision)
+    u, v, s = workloads.queries_to_device(w)
+    m.set_decode_variant(1)
+    ref = m.decode(u, v, s, out_dtype=torch.float32)
+    m.set_decode_variant(3)
+    got = m.decode(u, v, s, out_dtype=torch.float32)
+    assert torch.equal(got, ref)
+
+
+@pytest.mark.parametrize("variant", [0, 3])
+def test_full_size_screen_decode_sampled_against_oracle(variant):
+    """The 4 x 2048^2 / 3840x2160 FP16 workload in the launch configuration the benchmark times (whole frame,
+    FP16 output), checked on 20,000 sampled queries against the quantisation-aware oracle."""
+    bcf = _bcf()
+    w = workloads.config2()
+    m = workloads.upload(w, "fp16")
+    m.set_decode_variant(variant)
+    u, v, s = workloads.queries_to_device(w)
+    out = torch.empty((w.n, 9), dtype=torch.float16, device="cuda")
+    m.decode(u, v, s, out=out)
+    idx = np.random.default_rng(17).choice(w.n, 20000, replace=False)
+    got = out[torch.from_numpy(idx).cuda()].float().cpu().numpy().astype(np.float64)
+    Wst, bias, a, ws = w.weights("fp16")
+    ref_q = oracle.decode(_oracle_material(w), oracle.Mlp(w.dims, "fp16", Wst, bias, a, ws), w.u[idx], w.v[idx],
+                          w.s[idx], quant_aware=True, threads=8).astype(np.float16).astype(np.float64)
+    tol = TOL["fp16"] + np.abs(ref_q) * 2.0 ** -11
+    worst, frac = _quant_check(got, ref_q, tol, "fp16")
