@@ -146,9 +146,11 @@ __global__ void __launch_bounds__(128) k_decode_fp32_generic(MaterialDev M, cons
 
 // ------------------------------------------------ fused decode, tensor cores
 
-__host__ __device__ inline int mma_per_warp_bytes(int act_bytes, int act1_bytes, int C, int n_in)
+// per warp: act0, act1, the output staging [32][C] floats and (generic MLP only) FP32 feature rows
+// [32][n_in + 1]; the register-chained MLP's features go straight into act0
+__host__ __device__ inline int mma_per_warp_bytes(int act_bytes, int act1_bytes, int C, int n_in, bool rows)
 {
-    return act_bytes + act1_bytes + ((32 * C + 3) & ~3) * 4 + 32 * (n_in + 1) * 4;
+    return act_bytes + act1_bytes + ((32 * C + 3) & ~3) * 4 + (rows ? 32 * (n_in + 1) * 4 : 0);
 }
 
 // Second activation buffer of a warp: the generic MLP ping-pongs two full tiles; the register-chained one
@@ -180,7 +182,7 @@ __global__ void __launch_bounds__(128) k_decode_mma(MaterialDev M, TexUnitObjs T
     const int C = P.dims[P.n_layers];
     // per warp: act0, act1 (act_bytes each), output staging [32][C] floats, feature rows [32][n_in + 1]
     const int act1_bytes = mma_act1_bytes<PREC, K0, N1, N2>(act_bytes);
-    const int per_warp = mma_per_warp_bytes(act_bytes, act1_bytes, C, M.n_in);
+    const int per_warp = mma_per_warp_bytes(act_bytes, act1_bytes, C, M.n_in, K0 == 0);
     unsigned char *act0 = wbase + warp * per_warp;
     unsigned char *act1 = act0 + act_bytes;
     float *ost = (float *)(act1 + act1_bytes);
@@ -194,18 +196,47 @@ __global__ void __launch_bounds__(128) k_decode_mma(MaterialDev M, TexUnitObjs T
     const int row_stride = tile_stride_bytes<PREC>(P.kpad[0]);
     for (int64_t tile = blockIdx.x * (int64_t)(blockDim.x >> 5) + warp; tile < tiles; tile += warps_total) {
         const int64_t q = tile * 32 + lane;
-        if (q < n) {
-            if (HW == 1)
-                query_features_hw(M, T, u[q], v[q], s ? s[q] : 0.0f, frow);
-            else if (HW == 2)
-                query_features_hwpoint(M, T, u[q], v[q], s ? s[q] : 0.0f, frow);
-            else
-                query_features(M, u[q], v[q], s ? s[q] : 0.0f, frow);
+        if constexpr (K0 != 0) {
+            // features straight into the lane's operand row, zero-padded to K0
+            unsigned char *row = act0 + lane * row_stride;
+            const float inv0 = PREC == BCF_FP8_E4M3 ? P.inv_act_scale[0] : 1.0f;
+            const bool live = q < n;
+            const float sq = live && s ? s[q] : 0.0f;
+            const float uu = sanitize(live ? u[q] : 0.0f, M.wrap), vv = sanitize(live ? v[q] : 0.0f, M.wrap);
+#pragma unroll 1
+            for (int t = 0; t < M.n_tex; ++t) {
+                float3 f = make_float3(0.0f, 0.0f, 0.0f);
+                if (live) {
+                    if (HW == 1)
+                        f = texture_trilinear_hw(M.tex[t], T.tex[t], uu, vv, sq);
+                    else if (HW == 2)
+                        f = sample_texture_hwpoint(M.tex[t], T.texp[t], M.wrap, uu, vv, sq);
+                    else
+                        f = sample_texture(M.tex[t], M.wrap, M.is_signed != 0, uu, vv, sq);
+                }
+                store_feature<PREC>(row, 3 * t, f.x, inv0);
+                store_feature<PREC>(row, 3 * t + 1, f.y, inv0);
+                store_feature<PREC>(row, 3 * t + 2, f.z, inv0);
+            }
+            int col = 3 * M.n_tex;
+            if (M.lod_input)
+                store_feature<PREC>(row, col++, live ? (isnan(sq) ? 0.0f : fmaxf(sq, 0.0f)) : 0.0f, inv0);
+            for (; col < K0; ++col)
+                store_feature<PREC>(row, col, 0.0f, inv0);
         } else {
-            for (int i = 0; i < M.n_in; ++i)
-                frow[i] = 0.0f;
+            if (q < n) {
+                if (HW == 1)
+                    query_features_hw(M, T, u[q], v[q], s ? s[q] : 0.0f, frow);
+                else if (HW == 2)
+                    query_features_hwpoint(M, T, u[q], v[q], s ? s[q] : 0.0f, frow);
+                else
+                    query_features(M, u[q], v[q], s ? s[q] : 0.0f, frow);
+            } else {
+                for (int i = 0; i < M.n_in; ++i)
+                    frow[i] = 0.0f;
+            }
+            store_input_row<PREC>(P, frow, M.n_in, act0 + lane * row_stride);
         }
-        store_input_row<PREC>(P, frow, M.n_in, act0 + lane * row_stride);
         __syncwarp();
         if constexpr (K0 == 0)
             warp_mlp<PREC>(P, sw, sb, act0, act1, ost);
@@ -309,7 +340,7 @@ int64_t mma_smem_bytes(const MlpDev &P, int warps)
 {
     const int C = P.dims[P.n_layers];
     const int act = mma_act_bytes<PREC>(P);
-    const int per_warp = mma_per_warp_bytes(act, mma_act1_bytes<PREC, K0, N1, N2>(act), C, P.dims[0]);
+    const int per_warp = mma_per_warp_bytes(act, mma_act1_bytes<PREC, K0, N1, N2>(act), C, P.dims[0], K0 == 0);
     return (int64_t)mlp_smem_weight_bytes<PREC>(P) + ((mlp_smem_bias_floats(P) * 4 + 15) & ~15) +
            (int64_t)warps * per_warp;
 }

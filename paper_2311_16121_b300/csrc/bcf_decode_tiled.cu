@@ -107,17 +107,6 @@ __device__ __forceinline__ int ref_block(float c0, int W) { return ((int)floorf(
 // texels of different blocks over the banks).
 __device__ __forceinline__ int arena_slot(int b, int t) { return b * 16 + (t ^ (b & 15)); }
 
-template <int PREC>
-__device__ __forceinline__ void store_feature(unsigned char *row, int col, float x, float inv_scale)
-{
-    if constexpr (PREC == BCF_FP8_E4M3) {
-        row[col] = (unsigned char)__nv_cvt_float_to_fp8(x * inv_scale, __NV_SATFINITE, __NV_E4M3);
-    } else if constexpr (PREC == BCF_BF16) {
-        *(__nv_bfloat16 *)(row + 2 * col) = __float2bfloat16_rn(x);
-    } else {
-        *(__half *)(row + 2 * col) = __float2half_rn(x);
-    }
-}
 
 // Shared memory layout of the kernel (host and device agree through this).
 struct TiledLayout {

@@ -239,6 +239,19 @@ __device__ __forceinline__ void store_input_row(const MlpDev &P, const float *x,
     }
 }
 
+// One MLP input feature written in the operand format (FP8: scaled by the layer's inverse activation scale).
+template <int PREC>
+__device__ __forceinline__ void store_feature(unsigned char *row, int col, float x, float inv_scale)
+{
+    if constexpr (PREC == BCF_FP8_E4M3) {
+        row[col] = (unsigned char)__nv_cvt_float_to_fp8(x * inv_scale, __NV_SATFINITE, __NV_E4M3);
+    } else if constexpr (PREC == BCF_BF16) {
+        *(__nv_bfloat16 *)(row + 2 * col) = __float2bfloat16_rn(x);
+    } else {
+        *(__half *)(row + 2 * col) = __float2half_rn(x);
+    }
+}
+
 // ----------------------------------------------------------- FP32 SIMT MLP
 
 // Fully unrolled dense layer y = W x + b (W row-major [NO][NI] in shared

@@ -102,15 +102,21 @@ __device__ __forceinline__ void query_features(const MaterialDev &M, float u, fl
 // The same features through the texture unit (the render-time design of Sec. 5.2): hardware trilinear
 // filtering of the BC6H textures at the per-texture LOD of Eq. 11.  The hardware's filter weights are low-
 // precision fixed point, so these features differ from query_features by a bounded filtering error.
+__device__ __forceinline__ float3 texture_trilinear_hw(const TexDev &X, unsigned long long tex, float u, float v,
+                                                       float s)
+{
+    const float lod = fminf(fmaxf((isnan(s) ? 0.0f : s) + (float)X.lod_bias, 0.0f), (float)(X.levels - 1));
+    const float4 f = tex2DLod<float4>((cudaTextureObject_t)tex, u, v, lod);
+    return make_float3(f.x, f.y, f.z);
+}
+
 __device__ __forceinline__ void query_features_hw(const MaterialDev &M, const TexUnitObjs &T, float u, float v,
                                                   float s, float *row)
 {
     const float uu = sanitize(u, M.wrap), vv = sanitize(v, M.wrap);
-    const float sq = isnan(s) ? 0.0f : s;
 #pragma unroll 1
     for (int t = 0; t < M.n_tex; ++t) {
-        const float lod = fminf(fmaxf(sq + (float)M.tex[t].lod_bias, 0.0f), (float)(M.tex[t].levels - 1));
-        const float4 f = tex2DLod<float4>((cudaTextureObject_t)T.tex[t], uu, vv, lod);
+        const float3 f = texture_trilinear_hw(M.tex[t], T.tex[t], uu, vv, s);
         row[3 * t] = f.x;
         row[3 * t + 1] = f.y;
         row[3 * t + 2] = f.z;
@@ -131,30 +137,41 @@ __device__ __forceinline__ float3 sample_texture_hwpoint(const TexDev &T, unsign
     const int l0 = (int)fl;
     const float lam = st - fl;
     const int nlev = (lam > 0.0f && l0 + 1 < T.levels) ? 2 : 1;
+    // both levels' eight texels are fetched before any is used (the fetch latency is paid once)
+    float fxs[2], fys[2];
+    float4 c4[2][4];
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+        if (side < nlev) {
+            const int level = l0 + side;
+            const int W = T.res >> level;
+            const float x = u * (float)W - 0.5f, y = v * (float)W - 0.5f;
+            const float fx0 = floorf(x), fy0 = floorf(y);
+            fxs[side] = x - fx0;
+            fys[side] = y - fy0;
+            const int i0 = (int)fx0, j0 = (int)fy0;
+            const int ia = address(i0, W, wrap), ib = address(i0 + 1, W, wrap);
+            const int ja = address(j0, W, wrap), jb = address(j0 + 1, W, wrap);
+            const float rw = 1.0f / (float)W; // exact: W is a power of two
+#pragma unroll
+            for (int c = 0; c < 4; ++c) // texel centres (i + 1/2) / W are exact in FP32
+                c4[side][c] = tex2DLod<float4>((cudaTextureObject_t)tex, ((float)((c & 1) ? ib : ia) + 0.5f) * rw,
+                                               ((float)((c & 2) ? jb : ja) + 0.5f) * rw, (float)level);
+        }
+    }
     float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
-#pragma unroll 1
-    for (int side = 0; side < nlev; ++side) {
-        const int level = l0 + side;
-        const float scale = nlev == 1 ? 1.0f : (side ? lam : 1.0f - lam);
-        const int W = T.res >> level;
-        const float x = u * (float)W - 0.5f, y = v * (float)W - 0.5f;
-        const float fx0 = floorf(x), fy0 = floorf(y);
-        const float fx = x - fx0, fy = y - fy0;
-        const int i0 = (int)fx0, j0 = (int)fy0;
-        const int ia = address(i0, W, wrap), ib = address(i0 + 1, W, wrap);
-        const int ja = address(j0, W, wrap), jb = address(j0 + 1, W, wrap);
-        const float rw = 1.0f / (float)W; // exact: W is a power of two
-        float4 c4[4];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) // texel centres (i + 1/2) / W are exact in FP32
-            c4[c] = tex2DLod<float4>((cudaTextureObject_t)tex, ((float)((c & 1) ? ib : ia) + 0.5f) * rw,
-                                     ((float)((c & 2) ? jb : ja) + 0.5f) * rw, (float)level);
+    for (int side = 0; side < 2; ++side) {
+        if (side < nlev) {
+            const float scale = nlev == 1 ? 1.0f : (side ? lam : 1.0f - lam);
+            const float fx = fxs[side], fy = fys[side];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const float w = ((c & 1) ? fx : 1.0f - fx) * ((c & 2) ? fy : 1.0f - fy) * scale;
-            a0 = fmaf(w, c4[c].x, a0);
-            a1 = fmaf(w, c4[c].y, a1);
-            a2 = fmaf(w, c4[c].z, a2);
+            for (int c = 0; c < 4; ++c) {
+                const float w = ((c & 1) ? fx : 1.0f - fx) * ((c & 2) ? fy : 1.0f - fy) * scale;
+                a0 = fmaf(w, c4[side][c].x, a0);
+                a1 = fmaf(w, c4[side][c].y, a1);
+                a2 = fmaf(w, c4[side][c].z, a2);
+            }
         }
     }
     return make_float3(a0, a1, a2);
