@@ -183,7 +183,14 @@ typedef struct bcf_material_set_s *bcf_material_set;
  * bcf_create_material_set -- copy the materials' metadata into one device
  * table and allocate the set's work counter (freed by
  * bcf_destroy_material_set; synchronous).  The materials must outlive the
- * set.  Errors: BCF_ERR_INVALID_ARG (n out of [1, BCF_MAX_SET], null
+ * set.  When every material is on decode variant 3 at creation (see
+ * bcf_set_decode_variant) and the MLP is one of the register-chained shapes
+ * (three layers, K0 <= 16 (FP8: 32) -> 32 -> 32 -> C <= 16, or
+ * K0 <= 32 -> 64 -> 64 -> C <= 16), the set decodes through the texture unit
+ * the same way (texture-unit texels, exact FP32 filter) with a persistent
+ * kernel over 256-query tiles, and bcf_autotune_material_set has nothing to
+ * tune; otherwise it uses the tile-cooperative software decode.
+ * Errors: BCF_ERR_INVALID_ARG (n out of [1, BCF_MAX_SET], null
  * materials, materials that do not share the MLP / texture count),
  * BCF_ERR_UNSUPPORTED (FP32 materials: the set path is the tensor-core
  * path), BCF_ERR_OOM / BCF_ERR_CUDA.

@@ -330,6 +330,8 @@ struct bcf_material_set_s {
     bcf::MaterialDev *table; // device table
     int *counter;            // device work counter
     bcf::SetConfig cfg;
+    bcf::TexUnitObjs *tex_table; // device table of the materials' texture objects (texture-unit sets)
+    int texunit;             // 1: every material was on decode variant 3 at creation
 };
 
 extern "C" {
@@ -362,6 +364,10 @@ bcf_status bcf_create_material_set(const bcf_material *mats, int32_t n, bcf_mate
     set->table = nullptr;
     set->counter = nullptr;
     set->cfg = {320, 3, 2};
+    set->tex_table = nullptr;
+    set->texunit = set_tex_supported(mats[0]->host);
+    for (int m = 0; m < n; ++m)
+        set->texunit = set->texunit && mats[m]->hw_ready && mats[m]->variant == 3;
     MaterialDev *host = new (std::nothrow) MaterialDev[n];
     if (!host) {
         delete set;
@@ -375,9 +381,22 @@ bcf_status bcf_create_material_set(const bcf_material *mats, int32_t n, bcf_mate
     if (e == cudaSuccess)
         e = cudaMemcpy(set->table, host, sizeof(MaterialDev) * n, cudaMemcpyHostToDevice);
     delete[] host;
+    if (e == cudaSuccess && set->texunit) {
+        TexUnitObjs *th = new (std::nothrow) TexUnitObjs[n];
+        if (!th)
+            e = cudaErrorMemoryAllocation;
+        for (int m = 0; th && m < n; ++m)
+            th[m] = mats[m]->hw;
+        if (e == cudaSuccess)
+            e = cudaMalloc(&set->tex_table, sizeof(TexUnitObjs) * n);
+        if (e == cudaSuccess)
+            e = cudaMemcpy(set->tex_table, th, sizeof(TexUnitObjs) * n, cudaMemcpyHostToDevice);
+        delete[] th;
+    }
     if (e != cudaSuccess) {
         cudaFree(set->table);
         cudaFree(set->counter);
+        cudaFree(set->tex_table);
         delete set;
         return fail(BCF_ERR_OOM, "bcf_create_material_set: %s", cudaGetErrorString(e));
     }
@@ -391,6 +410,7 @@ bcf_status bcf_destroy_material_set(bcf_material_set set)
         return BCF_OK;
     cudaError_t e = cudaFree(set->table);
     cudaError_t e2 = cudaFree(set->counter);
+    cudaFree(set->tex_table);
     delete set;
     return cuda_status(e != cudaSuccess ? e : e2, "bcf_destroy_material_set");
 }
@@ -415,6 +435,11 @@ bcf_status bcf_decode_material_set(bcf_material_set set, const int64_t *d_offset
     bcf_status st = check_set_args(set, d_offsets, d_u, d_v, d_s, n_queries, d_out, out_precision);
     if (st != BCF_OK || n_queries == 0)
         return st;
+    if (set->texunit)
+        return cuda_status(launch_decode_set_tex(set->first, set->table, set->tex_table, set->n, d_offsets, d_u, d_v,
+                                                 d_s, n_queries, d_out, out_precision == BCF_FP16, set->counter,
+                                                 (cudaStream_t)stream),
+                           "bcf_decode_material_set launch");
     return cuda_status(launch_decode_set(set->first, set->table, set->n, d_offsets, d_u, d_v, d_s, n_queries, d_out,
                                          out_precision == BCF_FP16, set->counter, set->cfg, (cudaStream_t)stream),
                        "bcf_decode_material_set launch");
@@ -441,6 +466,8 @@ bcf_status bcf_autotune_material_set(bcf_material_set set, const int64_t *d_offs
     bcf_status st = check_set_args(set, d_offsets, d_u, d_v, d_s, n_queries, d_out, out_precision);
     if (st != BCF_OK)
         return st;
+    if (set->texunit) // the texture-unit set kernel has no tunable configuration
+        return bcf_material_set_config(set, cap, ctas_per_sm, chunk);
     cudaStream_t cs = (cudaStream_t)stream;
     if (n_queries > 0) {
         cudaEvent_t a = nullptr, b = nullptr;

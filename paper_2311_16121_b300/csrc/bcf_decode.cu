@@ -260,6 +260,121 @@ __global__ void __launch_bounds__(128) k_decode_mma(MaterialDev M, TexUnitObjs T
     }
 }
 
+// Material sets through the texture unit: a persistent CTA of 8 warps grabs 256-query tiles of a work list over
+// the materials (tiles never straddle two materials); when the material changes, its description, texture
+// objects and MLP weights replace the previous ones in shared memory; every warp then decodes its 32 queries as
+// variant 3 does (texture-unit texels, exact FP32 filter, register-chained tensor-core MLP).
+constexpr int kSetTexWarps = 8;
+
+template <int PREC, int K0, int N1, int N2, int NO>
+__global__ void __launch_bounds__(32 * kSetTexWarps) k_decode_set_tex(
+    const MaterialDev *__restrict__ mats, const TexUnitObjs *__restrict__ texs, int nmat,
+    const int64_t *__restrict__ offsets, const float *__restrict__ qu, const float *__restrict__ qv,
+    const float *__restrict__ qs, int64_t n, void *__restrict__ out, int out_fp16, int *__restrict__ counter,
+    int act_bytes)
+{
+    constexpr int kTile = 32 * kSetTexWarps;
+    extern __shared__ __align__(16) unsigned char smem[];
+    __shared__ MaterialDev Ms;
+    __shared__ unsigned long long Tp[BCF_MAX_TEX];
+    __shared__ int64_t tile_first[BCF_MAX_SET + 1];
+    __shared__ int grab;
+    const MlpDev &P0 = mats[0].mlp; // every material shares the MLP shape (checked when the set is created)
+    const int wbytes = mlp_smem_weight_bytes<PREC>(P0);
+    unsigned char *sw = smem;
+    float *sb = (float *)(smem + wbytes);
+    unsigned char *wbase = smem + wbytes + ((mlp_smem_bias_floats(P0) * 4 + 15) & ~15);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int C = P0.dims[P0.n_layers];
+    const int act1_bytes = mma_act1_bytes<PREC, K0, N1, N2>(act_bytes);
+    const int per_warp = mma_per_warp_bytes(act_bytes, act1_bytes, C, 0, false);
+    unsigned char *act0 = wbase + warp * per_warp;
+    unsigned char *act1 = act0 + act_bytes;
+    float *ost = (float *)(act1 + act1_bytes);
+    const int row_stride = tile_stride_bytes<PREC>(K0);
+    if (threadIdx.x == 0) {
+        int64_t acc = 0;
+        for (int m = 0; m < nmat; ++m) {
+            tile_first[m] = acc;
+            const int64_t a = min(max(offsets[m], (int64_t)0), n), b = min(max(offsets[m + 1], (int64_t)0), n);
+            acc += b > a ? (b - a + kTile - 1) / kTile : 0;
+        }
+        tile_first[nmat] = acc;
+    }
+    __syncthreads();
+    const int64_t total = tile_first[nmat];
+    int cur = -1;
+    for (;;) {
+        if (threadIdx.x == 0)
+            grab = atomicAdd(counter, 1);
+        __syncthreads();
+        const int64_t tile = grab;
+        __syncthreads(); // everyone has read `grab` before thread 0 may overwrite it
+        if (tile >= total)
+            break;
+        int lo = 0, hi = nmat - 1; // last m with tile_first[m] <= tile
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (tile_first[mid] <= tile)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        const int m = lo;
+        if (m != cur) { // (the barriers above ordered the previous tile's MLP reads before these writes)
+            const int words = (int)(sizeof(MaterialDev) / 4);
+            for (int i = threadIdx.x; i < words; i += kTile)
+                reinterpret_cast<int *>(&Ms)[i] = reinterpret_cast<const int *>(mats + m)[i];
+            if (threadIdx.x < BCF_MAX_TEX)
+                Tp[threadIdx.x] = texs[m].texp[threadIdx.x];
+            __syncthreads();
+            load_mlp_smem<PREC>(Ms.mlp, sw, sb);
+            __syncthreads();
+            cur = m;
+        }
+        const int64_t a = min(max(offsets[m], (int64_t)0), n), b = min(max(offsets[m + 1], (int64_t)0), n);
+        const int64_t q0w = a + (tile - tile_first[m]) * kTile + warp * 32;
+        if (q0w < b) { // warp-uniform
+            const int64_t q = q0w + lane;
+            const bool live = q < b;
+            unsigned char *row = act0 + lane * row_stride;
+            const float inv0 = PREC == BCF_FP8_E4M3 ? Ms.mlp.inv_act_scale[0] : 1.0f;
+            const float sq = live && qs ? qs[q] : 0.0f;
+            const float uu = sanitize(live ? qu[q] : 0.0f, Ms.wrap), vv = sanitize(live ? qv[q] : 0.0f, Ms.wrap);
+#pragma unroll 1
+            for (int t = 0; t < Ms.n_tex; ++t) {
+                float3 f = make_float3(0.0f, 0.0f, 0.0f);
+                if (live)
+                    f = sample_texture_hwpoint(Ms.tex[t], Tp[t], Ms.wrap, uu, vv, sq);
+                store_feature<PREC>(row, 3 * t, f.x, inv0);
+                store_feature<PREC>(row, 3 * t + 1, f.y, inv0);
+                store_feature<PREC>(row, 3 * t + 2, f.z, inv0);
+            }
+            int col = 3 * Ms.n_tex;
+            if (Ms.lod_input)
+                store_feature<PREC>(row, col++, live ? (isnan(sq) ? 0.0f : fmaxf(sq, 0.0f)) : 0.0f, inv0);
+            for (; col < K0; ++col)
+                store_feature<PREC>(row, col, 0.0f, inv0);
+            __syncwarp();
+            warp_mlp3<PREC, K0, N1, N2, NO>(Ms.mlp, sw, sb, act0, row_stride, act1,
+                                            tile_stride_bytes<BCF_FP8_E4M3>(N1 > N2 ? N1 : N2), ost, C);
+            __syncwarp();
+            const int rows = (int)min((int64_t)32, b - q0w);
+            const int tot = rows * C;
+            if (out_fp16) {
+                __half *o = (__half *)out + q0w * C;
+                for (int i = lane; i < tot; i += 32)
+                    o[i] = __float2half_rn(ost[i]);
+            } else {
+                float *o = (float *)out + q0w * C;
+                for (int i = lane; i < tot; i += 32)
+                    o[i] = ost[i];
+            }
+            __syncwarp();
+        }
+    }
+}
+
 // ---------------------------------------------------------------- launchers
 
 static int sm_count()
@@ -420,6 +535,69 @@ int64_t decode_mma_smem_bytes(const MlpDev &P)
     case BCF_FP8_E4M3: return mma_smem_bytes<BCF_FP8_E4M3>(P, 4);
     default: return 0;
     }
+}
+
+
+template <int PREC, int K0, int N1, int N2, int NO>
+static cudaError_t launch_set_tex_shape(const MaterialDev &M0, const MaterialDev *mats, const TexUnitObjs *texs,
+                                        int nmat, const int64_t *offsets, const float *u, const float *v,
+                                        const float *s, int64_t n, void *out, int out_fp16, int *counter,
+                                        cudaStream_t st)
+{
+    const MlpDev &P = M0.mlp;
+    const int act = mma_act_bytes<PREC>(P);
+    const int per_warp = mma_per_warp_bytes(act, mma_act1_bytes<PREC, K0, N1, N2>(act), P.dims[P.n_layers], 0,
+                                            false);
+    const int64_t smem = (int64_t)mlp_smem_weight_bytes<PREC>(P) + ((mlp_smem_bias_floats(P) * 4 + 15) & ~15) +
+                         (int64_t)kSetTexWarps * per_warp;
+    if (smem > 160 * 1024)
+        return cudaErrorInvalidConfiguration;
+    auto kern = k_decode_set_tex<PREC, K0, N1, N2, NO>;
+    static int configured = 0;
+    if (!configured) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 160 * 1024);
+        configured = 1;
+    }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kSetTexWarps, (size_t)smem);
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+    if (e != cudaSuccess)
+        return e;
+    kern<<<(unsigned)(sm_count() * max(per_sm, 1)), 32 * kSetTexWarps, (size_t)smem, st>>>(
+        mats, texs, nmat, offsets, u, v, s, n, out, out_fp16, counter, act);
+    return cudaGetLastError();
+}
+
+bool set_tex_supported(const MaterialDev &M0)
+{
+    const MlpDev &P = M0.mlp;
+    if (P.n_layers != 3 || P.precision == BCF_FP32)
+        return false;
+    const int kq = P.precision == BCF_FP8_E4M3 ? 32 : 16;
+    return (P.kpad[0] == kq && P.npad[0] == 32 && P.npad[1] == 32 && P.npad[2] == 16) ||
+           (P.kpad[0] == 32 && P.npad[0] == 64 && P.npad[1] == 64 && P.npad[2] == 16);
+}
+
+cudaError_t launch_decode_set_tex(const MaterialDev &M0, const MaterialDev *mats, const TexUnitObjs *texs, int nmat,
+                                  const int64_t *offsets, const float *u, const float *v, const float *s, int64_t n,
+                                  void *out, int out_fp16, int *counter, cudaStream_t st)
+{
+    if (n == 0)
+        return cudaSuccess;
+    const MlpDev &P = M0.mlp;
+    const bool wide = P.kpad[0] == 32 && P.npad[0] == 64;
+#define BCF_SET_TEX(PR, KQ)                                                                                          \
+    return wide ? launch_set_tex_shape<PR, 32, 64, 64, 16>(M0, mats, texs, nmat, offsets, u, v, s, n, out, out_fp16, \
+                                                           counter, st)                                              \
+                : launch_set_tex_shape<PR, KQ, 32, 32, 16>(M0, mats, texs, nmat, offsets, u, v, s, n, out, out_fp16, \
+                                                           counter, st)
+    switch (P.precision) {
+    case BCF_FP16: BCF_SET_TEX(BCF_FP16, 16);
+    case BCF_BF16: BCF_SET_TEX(BCF_BF16, 16);
+    case BCF_FP8_E4M3: BCF_SET_TEX(BCF_FP8_E4M3, 32);
+    default: return cudaErrorInvalidValue;
+    }
+#undef BCF_SET_TEX
 }
 
 } // namespace bcf

@@ -30,10 +30,15 @@ def _set_inputs(sw):
     return off, u, v, s
 
 
+@pytest.mark.parametrize("variant", [0, 3])
 @pytest.mark.parametrize("precision", ["fp16", "fp8"])
-def test_set_decode_equals_per_material_decodes(precision):
+def test_set_decode_equals_per_material_decodes(precision, variant):
+    """One launch over the set equals the per-material decodes bit for bit: the tile-cooperative software decode
+    (materials on variant 0) and the texture-unit decode (materials on variant 3)."""
     bcf = _bcf()
     sw, mats = _small_set(precision)
+    for m in mats:
+        m.set_decode_variant(variant)
     S = bcf.MaterialSet(mats)
     off, u, v, s = _set_inputs(sw)
     got = S.decode(off, u, v, s).cpu().numpy()
@@ -58,9 +63,12 @@ def test_set_decode_matches_oracle():
         assert (err > 1e-3).mean() <= 1e-3 and err.max() <= 8e-3, (m, err.max())
 
 
-def test_set_decode_in_a_cuda_graph_and_autotune():
+@pytest.mark.parametrize("variant", [0, 3])
+def test_set_decode_in_a_cuda_graph_and_autotune(variant):
     bcf = _bcf()
     sw, mats = _small_set("fp16", seed_config=44)
+    for m in mats:
+        m.set_decode_variant(variant)
     S = bcf.MaterialSet(mats)
     off, u, v, s = _set_inputs(sw)
     ref = S.decode(off, u, v, s).clone()
