@@ -167,6 +167,29 @@ bcf_status bcf_sample_features(bcf_material mat, const float *d_u, const float *
 bcf_status bcf_decode_material(bcf_material mat, const float *d_u, const float *d_v, const float *d_s, int64_t n,
                                void *d_out, bcf_precision out_precision, bcf_stream stream);
 
+/*
+ * bcf_decode_material_host -- bcf_decode_material for queries and outputs in
+ * host memory (page-locked memory gives overlapped copies; pageable memory
+ * works but serialises).  The n queries are processed in chunks through two
+ * alternating buffers carved from the caller's device scratch; the upload of
+ * the next chunk, the decode of the current one and the download of the
+ * previous one run concurrently on three library streams, ordered after the
+ * work already on `stream`, and `stream` waits for the last download, so the
+ * call is asynchronous like the others (h_out is complete once `stream`
+ * reaches that point).  Each chunk is a multiple of 256 queries: a chunk needs
+ * 2 x (8 + 4 [with s] + C x out bytes) per query plus 1 KB of alignment, and
+ * the chunk size is chosen so the call runs in at least about four chunks.
+ * h_u, h_v, h_s (may be NULL when the material has no LOD input): n floats;
+ * h_out: [n][C] in out_precision.  No allocation besides the streams and
+ * events, which are released when their work completes.
+ * Errors: BCF_ERR_INVALID_ARG for null pointers, scratch not 256-byte aligned
+ * or too small for one 256-query chunk; the errors of bcf_decode_material;
+ * BCF_ERR_CUDA.
+ */
+bcf_status bcf_decode_material_host(bcf_material mat, const float *h_u, const float *h_v, const float *h_s, int64_t n,
+                                    void *h_out, bcf_precision out_precision, void *d_scratch, int64_t scratch_bytes,
+                                    bcf_stream stream);
+
 /* ------------------------------------------------------------ material sets */
 
 /*

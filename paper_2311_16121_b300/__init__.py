@@ -110,6 +110,9 @@ def lib() -> ctypes.CDLL:
         L.bcf_train_backward.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p]
         L.bcf_train_export.restype = c_int
         L.bcf_train_export.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p]
+        L.bcf_decode_material_host.restype = c_int
+        L.bcf_decode_material_host.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_int,
+                                               c_void_p, c_int64, c_void_p]
         L.bcf_encode_mode10.restype = c_int
         L.bcf_encode_mode10.argtypes = [c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]
         _lib = L
@@ -215,6 +218,21 @@ class Material:
         self.dims = list(dims)
         self.n_tex = len(blocks)
         self.precision = precision
+
+    def decode_host(self, u: torch.Tensor, v: torch.Tensor, s: torch.Tensor | None, out: torch.Tensor,
+                    scratch: torch.Tensor) -> torch.Tensor:
+        """bcf_decode_material_host: queries and `out` in (preferably pinned) host memory, pipelined through the
+        device `scratch` (uint8, 256-byte aligned)."""
+        for t in (u, v, s, out):
+            if t is not None and (t.is_cuda or not t.is_contiguous()):
+                raise ValueError("decode_host takes contiguous host tensors")
+        prec = {torch.float32: 0, torch.float16: 1}[out.dtype]
+        if out.numel() < u.numel() * self.dims[-1]:
+            raise ValueError("decode_host: output too small")
+        _check(lib().bcf_decode_material_host(self.handle, u.data_ptr(), v.data_ptr(),
+                                              None if s is None else s.data_ptr(), u.numel(), out.data_ptr(), prec,
+                                              _ptr(scratch), scratch.numel(), _stream()), "bcf_decode_material_host")
+        return out
 
     def set_decode_variant(self, variant: int) -> None:
         """bcf_set_decode_variant: 0 tile-cooperative (default), 1 per-lane, 2 texture unit (hardware trilinear)."""

@@ -2,6 +2,7 @@
 // material metadata and the kernel launches.  No entry point allocates on
 // the decode path; bcf_create_material allocates the small device metadata.
 #include <math.h>
+#include <algorithm>
 #include <new>
 #include <stdarg.h>
 #include <stdio.h>
@@ -293,6 +294,98 @@ bcf_status bcf_decode_material(bcf_material m, const float *d_u, const float *d_
     else
         e = launch_decode_tiled(m->host, d_u, d_v, d_s, n, d_out, fp16, (cudaStream_t)stream);
     return cuda_status(e, "bcf_decode_material launch");
+}
+
+// ------------------------------------------------------------ host-resident queries
+
+// The decode of queries and outputs that live in host memory, pipelined in chunks over three streams: the
+// upload of chunk i + 1, the decode of chunk i and the download of chunk i - 1 overlap.  Two chunk buffers
+// alternate in the caller's device scratch; per buffer an event marks when its download has finished so the
+// next upload into it may start.
+bcf_status bcf_decode_material_host(bcf_material m, const float *h_u, const float *h_v, const float *h_s, int64_t n,
+                                    void *h_out, bcf_precision out_precision, void *d_scratch, int64_t scratch_bytes,
+                                    bcf_stream stream)
+{
+    if (!m || n < 0)
+        return fail(BCF_ERR_INVALID_ARG, "bcf_decode_material_host: null material or n < 0");
+    if (out_precision != BCF_FP32 && out_precision != BCF_FP16)
+        return fail(BCF_ERR_INVALID_ARG, "bcf_decode_material_host: out_precision must be FP32 or FP16");
+    if (n == 0)
+        return BCF_OK;
+    if (!h_u || !h_v || !h_out || !d_scratch || !aligned(d_scratch, 256))
+        return fail(BCF_ERR_INVALID_ARG, "bcf_decode_material_host: null pointer or scratch not 256-byte aligned");
+    const int C = m->host.mlp.dims[m->host.mlp.n_layers];
+    const int64_t out_b = (int64_t)C * (out_precision == BCF_FP16 ? 2 : 4);
+    const int64_t per_q = (h_s ? 12 : 8) + out_b;
+    int64_t chunk = (scratch_bytes - 2048) / (2 * per_q) / 256 * 256; // two buffers, each array 256-aligned
+    if (chunk < 256)
+        return fail(BCF_ERR_INVALID_ARG, "bcf_decode_material_host: scratch of %lld bytes holds no 256-query chunk",
+                    (long long)scratch_bytes);
+    chunk = std::min<int64_t>(chunk, std::max<int64_t>(256, (n / 4 + 255) / 256 * 256)); // at least ~4 chunks
+    auto up = [](int64_t b) { return (b + 255) / 256 * 256; };
+    const int64_t buf = up(chunk * 4) * (h_s ? 3 : 2) + up(chunk * out_b);
+    char *base[2] = {(char *)d_scratch, (char *)d_scratch + buf};
+    cudaStream_t cs = (cudaStream_t)stream, sin = nullptr, scomp = nullptr, sout = nullptr;
+    cudaEvent_t start = nullptr, done = nullptr, in_done[2] = {}, comp_done[2] = {}, free_ev[2] = {};
+    cudaError_t e = cudaStreamCreateWithFlags(&sin, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithFlags(&scomp, cudaStreamNonBlocking);
+    if (e == cudaSuccess)
+        e = cudaStreamCreateWithFlags(&sout, cudaStreamNonBlocking);
+    cudaEvent_t *evs[] = {&start, &done, &in_done[0], &in_done[1], &comp_done[0], &comp_done[1], &free_ev[0],
+                          &free_ev[1]};
+    for (cudaEvent_t *ev : evs)
+        if (e == cudaSuccess)
+            e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+        e = cudaEventRecord(start, cs); // the pipeline starts after the caller's earlier work
+    if (e == cudaSuccess)
+        e = cudaStreamWaitEvent(sin, start, 0);
+    bcf_status st = BCF_OK;
+    const int64_t nchunks = (n + chunk - 1) / chunk;
+    for (int64_t i = 0; i < nchunks && e == cudaSuccess && st == BCF_OK; ++i) {
+        const int b = (int)(i & 1);
+        const int64_t q0 = i * chunk, nq = std::min(chunk, n - q0);
+        float *du = (float *)base[b], *dv = (float *)(base[b] + up(chunk * 4));
+        float *ds = h_s ? (float *)(base[b] + 2 * up(chunk * 4)) : nullptr;
+        void *dout = base[b] + up(chunk * 4) * (h_s ? 3 : 2);
+        if (i >= 2)
+            e = cudaStreamWaitEvent(sin, free_ev[b], 0);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(du, h_u + q0, nq * 4, cudaMemcpyHostToDevice, sin);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(dv, h_v + q0, nq * 4, cudaMemcpyHostToDevice, sin);
+        if (e == cudaSuccess && h_s)
+            e = cudaMemcpyAsync(ds, h_s + q0, nq * 4, cudaMemcpyHostToDevice, sin);
+        if (e == cudaSuccess)
+            e = cudaEventRecord(in_done[b], sin);
+        if (e == cudaSuccess)
+            e = cudaStreamWaitEvent(scomp, in_done[b], 0);
+        if (e == cudaSuccess)
+            st = bcf_decode_material(m, du, dv, ds, nq, dout, out_precision, (bcf_stream)scomp);
+        if (e == cudaSuccess && st == BCF_OK)
+            e = cudaEventRecord(comp_done[b], scomp);
+        if (e == cudaSuccess && st == BCF_OK)
+            e = cudaStreamWaitEvent(sout, comp_done[b], 0);
+        if (e == cudaSuccess && st == BCF_OK)
+            e = cudaMemcpyAsync((char *)h_out + q0 * out_b, dout, nq * out_b, cudaMemcpyDeviceToHost, sout);
+        if (e == cudaSuccess && st == BCF_OK)
+            e = cudaEventRecord(free_ev[b], sout);
+    }
+    if (e == cudaSuccess && st == BCF_OK)
+        e = cudaEventRecord(done, sout);
+    if (e == cudaSuccess && st == BCF_OK)
+        e = cudaStreamWaitEvent(cs, done, 0); // the caller's stream continues after the last download
+    // streams and events are released once their pending work completes
+    for (cudaStream_t x : {sin, scomp, sout})
+        if (x)
+            cudaStreamDestroy(x);
+    for (cudaEvent_t *ev : evs)
+        if (*ev)
+            cudaEventDestroy(*ev);
+    if (st != BCF_OK)
+        return st;
+    return cuda_status(e, "bcf_decode_material_host");
 }
 
 // ------------------------------------------------------------ partition selection encoder

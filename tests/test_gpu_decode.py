@@ -342,3 +342,23 @@ def test_full_size_screen_decode_sampled_against_oracle(variant):
                           w.s[idx], quant_aware=True, threads=8).astype(np.float16).astype(np.float64)
     tol = TOL["fp16"] + np.abs(ref_q) * 2.0 ** -11
     worst, frac = _quant_check(got, ref_q, tol, "fp16")
+
+
+@pytest.mark.parametrize("n,scratch_kb", [(12200, 64), (12200, 4096), (100, 64), (777, 32)])
+def test_host_memory_decode_equals_device_decode(n, scratch_kb):
+    """bcf_decode_material_host: pinned host queries in, host channels out, chunked and pipelined over three
+    streams through the caller's scratch; the result equals the device-resident decode bit for bit."""
+    bcf = _bcf()
+    w = workloads.small_screen(res=128, width=200, height=61)
+    m = workloads.upload(w, "fp16")
+    m.set_decode_variant(3)
+    u, v, s = (torch.from_numpy(a[:n].copy()) for a in (w.u, w.v, w.s))
+    ref = m.decode(u.cuda(), v.cuda(), s.cuda(), out_dtype=torch.float16)
+    uh, vh, sh = (t.pin_memory() for t in (u, v, s))
+    oh = torch.zeros((n, 9), dtype=torch.float16).pin_memory()
+    scratch = torch.empty(scratch_kb * 1024, dtype=torch.uint8, device="cuda")
+    m.decode_host(uh, vh, sh, oh, scratch)
+    torch.cuda.synchronize()
+    assert torch.equal(oh, ref.cpu())
+    with pytest.raises(bcf.BcfError):
+        m.decode_host(uh, vh, sh, oh, scratch[:4096])  # too small for one 256-query chunk
