@@ -281,9 +281,9 @@ def main():
     import paper_2311_16121_b300 as bcf
     from paper_2311_16121_b300 import workloads
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2311_16121_b300 import replicas
+
+    rank, world, local = replicas.rank_env()
     torch.cuda.set_device(local)
     if world > 1:
         dist.init_process_group("nccl")
@@ -313,8 +313,7 @@ def main():
         for _ in range(warmup):
             mat.decode(u, v, s, out=out)
         torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
+        replicas.barrier()
         total = 0.0
         for _ in range(steps):
             flush.zero_()
@@ -326,19 +325,16 @@ def main():
             b.synchronize()
             total += a.elapsed_time(b)
         torch.cuda.synchronize()
-        if world > 1:
-            dist.barrier()
+        replicas.barrier()
         return total
 
     # headline: low-precision path
     with ClockSampler(local) as clk:
         head_ms = timed(mats[HEADLINE_PRECISION], args.steps, args.warmup)
     clocks = clk.summary()
-    t = torch.tensor([head_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    head_ms_max = float(t.item())
-    value = w.n * world * args.steps / (head_ms_max * 1e-3) / 1e9
+    # whole-job throughput: the queries of all replicas over the slowest rank's time
+    head_units, head_ms_max = replicas.aggregate(w.n * args.steps, head_ms, device="cuda")
+    value = head_units / (head_ms_max * 1e-3) / 1e9
 
     if args.only_headline:
         if rank == 0:
