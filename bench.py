@@ -64,7 +64,8 @@ def _peaks():
 # kernel's sources hash to the value the capture was taken on; after any change they read as null.
 KERNEL_SOURCES = ["bcf_decode.cu", "bcf_texunit.cu", "bc6h_unpack.cuh", "bcf_sample.cuh", "bcf_mlp.cuh",
                   "bcf_internal.h"]
-NCU_CAPTURE = {"source_sha256": "b20031f2f06532af", "dram_bytes": 120755712 + 101953792, "warp_inst": 321041160}
+NCU_CAPTURE = {"source_sha256": "b20031f2f06532af", "dram_bytes": 120755712 + 101953792, "warp_inst": 321041160,
+               "tex_pipe_pct": 70.45, "issue_active_pct": 60.96, "tensor_active_pct": 12.61}
 SM_COUNT, SMSP_PER_SM, FP32_LANES_PER_SM = 148, 4, 128
 
 
@@ -425,6 +426,28 @@ def main():
         if i >= 3:
             seq_total += a.elapsed_time(b)
     e2e_sequential = w.n * world * k_extra / (seq_total * 1e-3) / 1e9
+    # the PCIe floor of the same bytes: all uploads and the download concurrently on two streams, no decode
+    s_up, s_down = torch.cuda.Stream(), torch.cuda.Stream()
+    floor_total = 0.0
+    for i in range(3 + k_extra):
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        s_up.wait_stream(stream)
+        s_down.wait_stream(stream)
+        with torch.cuda.stream(s_up):
+            ud.copy_(uh, non_blocking=True)
+            vd.copy_(vh, non_blocking=True)
+            sd.copy_(sh, non_blocking=True)
+        with torch.cuda.stream(s_down):
+            oh.copy_(out, non_blocking=True)
+        stream.wait_stream(s_up)
+        stream.wait_stream(s_down)
+        b.record(stream)
+        b.synchronize()
+        if i >= 3:
+            floor_total += a.elapsed_time(b)
+    e2e_copy_floor = w.n * world * k_extra / (floor_total * 1e-3) / 1e9
     del scratch, ud, vd, sd
 
     train_ms, train_loss, train_batch = _train_bench(torch, workloads, stream, max(3, args.steps // 2))
@@ -638,7 +661,9 @@ def main():
                                                          "block), 4x 1024^2 RGB textures with 9 levels, uniform texels"},
             "e2e": {"value": e2e_value, "unit": "Gsamples/s", "h2d_bytes_per_step": 12 * w.n,
                     "d2h_bytes_per_step": 18 * w.n, "api": "bcf_decode_material_host (pinned host queries and "
-                    "channels, chunked, copies overlapped with the decode)", "sequential_copies": e2e_sequential},
+                    "channels, chunked, copies overlapped with the decode)", "sequential_copies": e2e_sequential,
+                    "copy_floor": e2e_copy_floor, "copy_floor_note": "the same bytes copied concurrently "
+                    "(uploads and download on two streams) with no decode: the PCIe bound of e2e"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak,
                          "traffic": NCU_CAPTURE["dram_bytes"] if counters_valid else None, "peak_kind": peak_kind,
@@ -652,6 +677,12 @@ def main():
                                                if counters_valid else None),
                                       "note": "executed (not algorithmic) instructions per launch from ncu; "
                                               "peak = 148 SMs x 4 partitions x 1 issue/clock at the max SM clock"},
+                         "limiter": {"unit": "texture data pipe, pct of peak (ncu l1tex__data_pipe_tex_wavefronts)",
+                                     "value": NCU_CAPTURE["tex_pipe_pct"] if counters_valid else None,
+                                     "note": "the busiest unit of the headline kernel: 32 point-sampled texel "
+                                             "fetches per query; issue active and tensor pipe " +
+                                             (f"{NCU_CAPTURE['issue_active_pct']}% / {NCU_CAPTURE['tensor_active_pct']}%"
+                                              if counters_valid else "n/a")},
                          "tensor": {"achieved_tflops": mlp_flops * w.n / head_launch_s / 1e12,
                                     "peak_tflops": bf16_peak,
                                     "frac": mlp_flops * w.n / head_launch_s / 1e12 / bf16_peak}},
