@@ -474,14 +474,20 @@ bcf_status bcf_encode_mode10(const float *d_texels, int32_t texel_stride, int32_
  * filtering (mipmapped CUDA arrays; the hardware decodes the blocks), then
  * the same tensor-core MLP.  The hardware's filter and LOD weights are
  * low-precision fixed point, so its outputs differ from variants 0 and 1 by
- * a bounded filtering error: a comparison path, not a parity one.  Setting
- * variant 2 allocates the mipmapped arrays and copies the blocks into them
- * (synchronously, once per material; later changes of the caller's block
- * arrays are not seen by this variant); they are freed with the material.
- * FP32 materials always use the per-lane SIMT path.
+ * a bounded filtering error: a comparison path, not a parity one.
+ * 3: texture-unit texels with the exact filter -- every footprint texel is
+ * fetched from the same BC6H texture objects with point filtering at its
+ * centre (the hardware's BC6H decoder, bit-exact with the software one) and
+ * filtered in FP32 with the software path's operations in the same order:
+ * the outputs equal those of variants 0 and 1 bit for bit.  The fastest
+ * exact variant.
+ * Setting variant 2 or 3 allocates the mipmapped arrays and copies the
+ * blocks into them (synchronously, once per material; later changes of the
+ * caller's block arrays are not seen by these variants); they are freed
+ * with the material.  FP32 materials always use the per-lane SIMT path.
  * Errors: BCF_ERR_INVALID_ARG for a null material or another variant;
- * BCF_ERR_UNSUPPORTED for variant 2 on an FP32 material; BCF_ERR_CUDA if the
- * texture objects cannot be created.
+ * BCF_ERR_UNSUPPORTED for variant 2 or 3 on an FP32 material; BCF_ERR_CUDA
+ * if the texture objects cannot be created.
  */
 bcf_status bcf_set_decode_variant(bcf_material mat, int32_t variant);
 
