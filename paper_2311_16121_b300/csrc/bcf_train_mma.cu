@@ -525,34 +525,65 @@ __global__ void __launch_bounds__(kThreads, 4) k_train_mma(TrainDev D, int mode,
                 }
                 const int64_t cst = tx < kCoarseTex ? coarse_start(T) : T.blocks;
                 for_each_side(T, u, v, s, [&](const Tap(&tps)[4], const TexelParams(&P)[4]) {
+                    // per tap: the region's endpoint gradients (6) and the index gradient
+                    float g[4][6], gx[4];
+                    int reg[4];
+                    bool inx[4];
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        SteTexel tt;
+                        ste_from_v<EMU>(P[j], tt);
+                        reg[j] = tt.region;
+                        inx[j] = tt.inx;
+                        gx[j] = 0.0f;
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            const float dv = dxf[c] * tps[j].weight;
+                            g[j][c] = tt.ina[c] ? dv * tt.dea[c] : 0.0f;
+                            g[j][3 + c] = tt.inb[c] ? dv * tt.deb[c] : 0.0f;
+                            gx[j] = fmaf(dv, tt.dx[c], gx[j]);
+                        }
+                    }
+                    // taps of the footprint in the same block and region share one endpoint update
+                    bool own[4] = {true, true, true, true};
+#pragma unroll
+                    for (int j = 1; j < 4; ++j)
+#pragma unroll
+                        for (int k = 0; k < j; ++k)
+                            if (own[j] && own[k] && tps[k].block == tps[j].block && reg[k] == reg[j]) {
+#pragma unroll
+                                for (int c = 0; c < 6; ++c)
+                                    g[k][c] += g[j][c];
+                                own[j] = false;
+                            }
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         const Tap &tp = tps[j];
-                        SteTexel tt;
-                        ste_from_v<EMU>(P[j], tt);
-                        float ga[3], gb[3], gx = 0.0f;
-#pragma unroll
-                        for (int c = 0; c < 3; ++c) {
-                            const float dv = dxf[c] * tp.weight;
-                            ga[c] = tt.ina[c] ? dv * tt.dea[c] : 0.0f;
-                            gb[c] = tt.inb[c] ? dv * tt.deb[c] : 0.0f;
-                            gx = fmaf(dv, tt.dx[c], gx);
-                        }
+                        // horizontal neighbours in one block with an even first texel: one 8-byte index update
+                        const bool pair_lo = (j == 0 || j == 2) && tps[j + (j < 3 ? 1 : 0)].block == tp.block &&
+                                             tps[j + (j < 3 ? 1 : 0)].texel == tp.texel + 1 && (tp.texel & 1) == 0;
+                        const bool pair_hi = (j == 1 || j == 3) && tps[j - 1].block == tp.block &&
+                                             tp.texel == tps[j - 1].texel + 1 && (tps[j - 1].texel & 1) == 0;
                         if (tp.block >= cst) {
                             float *cp = S.coarse[tx] + (tp.block - cst) * 32;
+                            if (own[j]) {
 #pragma unroll
-                            for (int c = 0; c < 3; ++c) {
-                                atomicAdd(cp + 8 * tt.region + c, ga[c]);
-                                atomicAdd(cp + 8 * tt.region + 3 + c, gb[c]);
+                                for (int c = 0; c < 6; ++c)
+                                    atomicAdd(cp + 8 * reg[j] + c, g[j][c]);
                             }
-                            if (tt.inx)
-                                atomicAdd(cp + 16 + tp.texel, gx);
+                            if (inx[j])
+                                atomicAdd(cp + 16 + tp.texel, gx[j]);
                         } else {
                             float *gp = T.grad + tp.block * 32;
-                            red_add_v4(gp + 8 * tt.region, ga[0], ga[1], ga[2], gb[0]);
-                            red_add_v2(gp + 8 * tt.region + 4, gb[1], gb[2]);
-                            if (tt.inx)
-                                atomicAdd(gp + 16 + tp.texel, gx);
+                            if (own[j]) {
+                                red_add_v4(gp + 8 * reg[j], g[j][0], g[j][1], g[j][2], g[j][3]);
+                                red_add_v2(gp + 8 * reg[j] + 4, g[j][4], g[j][5]);
+                            }
+                            if (pair_lo)
+                                red_add_v2(gp + 16 + tp.texel, inx[j] ? gx[j] : 0.0f,
+                                           inx[j + 1] ? gx[j + 1] : 0.0f);
+                            else if (!pair_hi && inx[j])
+                                atomicAdd(gp + 16 + tp.texel, gx[j]);
                         }
                     }
                 });
