@@ -347,6 +347,11 @@ def main():
     # the plain FP32 path and FP8 on the same frame
     k_extra = max(3, args.steps // 4)
     fp32_ms = timed(mats["fp32"], k_extra, 3, out=out32) / k_extra
+    # the FP32 MLP on the texture unit's texels (variant 3): the same precision gap with the same texel path
+    m32t = workloads.upload(w, "fp32")
+    m32t.set_decode_variant(HEADLINE_VARIANT)
+    fp32t_ms = timed(m32t, k_extra, 3, out=out32) / k_extra
+    del m32t
     fp8_ms = timed(mats["fp8"], k_extra, 3) / k_extra
 
     # the texture-unit comparator (decode variant 2: hardware trilinear filtering of BC6H texture objects)
@@ -626,7 +631,12 @@ def main():
                                          "peak_tflops": fp32_simt_peak, "peak_kind": "derived: 148 SMs x 128 "
                                          "lanes x 2 flop x max SM clock"}},
             "fp8": {"value": w.n / (fp8_ms * 1e-3) / 1e9, "unit": "Gsamples/s", "ms_per_step": fp8_ms},
+            "fp32_texunit_texels": {"value": w.n / (fp32t_ms * 1e-3) / 1e9, "unit": "Gsamples/s",
+                                    "ms_per_step": fp32t_ms, "out": "fp32 [N][9]",
+                                    "kernel": "k_decode_fp32 on decode variant 3 (texture-unit texels, exact filter, "
+                                              "FP32 SIMT MLP)"},
             "speedup_vs_fp32_plain": fp32_ms / (head_ms / args.steps),
+            "speedup_vs_fp32_same_texels": fp32t_ms / (head_ms / args.steps),
             "batched": {"value": set_n / (set_ms * 1e-3) / 1e9, "unit": "Gsamples/s", "ms_per_step": set_ms,
                         "queries": set_n, "materials": 64, "precision": "fp16",
                         "launch": "one persistent launch replayed from a CUDA graph",

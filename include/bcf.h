@@ -484,10 +484,12 @@ bcf_status bcf_encode_mode10(const float *d_texels, int32_t texel_stride, int32_
  * Setting variant 2 or 3 allocates the mipmapped arrays and copies the
  * blocks into them (synchronously, once per material; later changes of the
  * caller's block arrays are not seen by these variants); they are freed
- * with the material.  FP32 materials always use the per-lane SIMT path.
+ * with the material.  FP32 materials use the per-lane SIMT MLP; on variant 3
+ * their texels come from the texture unit as above (same features), on the
+ * other variants from the software decoder.
  * Errors: BCF_ERR_INVALID_ARG for a null material or another variant;
- * BCF_ERR_UNSUPPORTED for variant 2 or 3 on an FP32 material; BCF_ERR_CUDA
- * if the texture objects cannot be created.
+ * BCF_ERR_UNSUPPORTED for variant 2 on an FP32 material; BCF_ERR_CUDA if the
+ * texture objects cannot be created.
  */
 bcf_status bcf_set_decode_variant(bcf_material mat, int32_t variant);
 

@@ -231,9 +231,9 @@ bcf_status bcf_set_decode_variant(bcf_material m, int32_t variant)
     if (!m || variant < 0 || variant > 3)
         return fail(BCF_ERR_INVALID_ARG, "bcf_set_decode_variant: null material or variant not in {0, 1, 2, 3}");
     if (variant >= 2) {
-        if (m->host.mlp.precision == BCF_FP32)
-            return fail(BCF_ERR_UNSUPPORTED, "bcf_set_decode_variant: the texture-unit variant needs a tensor-core "
-                                             "(FP16 / BF16 / FP8) material");
+        if (m->host.mlp.precision == BCF_FP32 && variant == 2)
+            return fail(BCF_ERR_UNSUPPORTED, "bcf_set_decode_variant: the hardware-trilinear variant needs a "
+                                             "tensor-core (FP16 / BF16 / FP8) material");
         if (!m->hw_ready) {
             cudaError_t e = texunit_create(m->host, m->hw, m->hw_arrays);
             if (e != cudaSuccess)
@@ -285,7 +285,9 @@ bcf_status bcf_decode_material(bcf_material m, const float *d_u, const float *d_
     const int fp16 = out_precision == BCF_FP16;
     cudaError_t e;
     if (m->host.mlp.precision == BCF_FP32)
-        e = launch_decode_fp32(m->host, d_u, d_v, d_s, n, d_out, fp16, (cudaStream_t)stream);
+        e = m->variant == 3 ? launch_decode_fp32_texunit(m->host, m->hw, d_u, d_v, d_s, n, d_out, fp16,
+                                                          (cudaStream_t)stream)
+                            : launch_decode_fp32(m->host, d_u, d_v, d_s, n, d_out, fp16, (cudaStream_t)stream);
     else if (m->variant == 1)
         e = launch_decode_mma(m->host, d_u, d_v, d_s, n, d_out, fp16, (cudaStream_t)stream);
     else if (m->variant >= 2)

@@ -73,8 +73,8 @@ __global__ void __launch_bounds__(128) k_sample_features(MaterialDev M, const fl
 
 // The plain evaluation: one thread per query, per-query BC6H unpack of the
 // texels it filters, FP32 SIMT MLP with weights broadcast from shared memory.
-template <int D0, int D1, int D2, int D3>
-__global__ void __launch_bounds__(128) k_decode_fp32(MaterialDev M, const float *__restrict__ u,
+template <int D0, int D1, int D2, int D3, bool HW = false>
+__global__ void __launch_bounds__(128) k_decode_fp32(MaterialDev M, TexUnitObjs T, const float *__restrict__ u,
                                                      const float *__restrict__ v, const float *__restrict__ s,
                                                      int64_t n, void *__restrict__ out, int out_fp16)
 {
@@ -90,7 +90,10 @@ __global__ void __launch_bounds__(128) k_decode_fp32(MaterialDev M, const float 
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n; q += (int64_t)gridDim.x * blockDim.x) {
         float x[D0];
         float *row = sX + threadIdx.x * D0;
-        query_features(M, u[q], v[q], s ? s[q] : 0.0f, row);
+        if (HW) // the texture unit's texels, the same exact filter (variant 3)
+            query_features_hwpoint(M, T, u[q], v[q], s ? s[q] : 0.0f, row);
+        else
+            query_features(M, u[q], v[q], s ? s[q] : 0.0f, row);
 #pragma unroll
         for (int i = 0; i < D0; ++i)
             x[i] = row[i];
@@ -422,7 +425,8 @@ cudaError_t launch_sample_features(const MaterialDev &M, const float *u, const f
 
 #define BCF_FP32_CASE(D0, D1, D2, D3)                                                                              \
     if (P.n_layers == 3 && P.dims[0] == D0 && P.dims[1] == D1 && P.dims[2] == D2 && P.dims[3] == D3) {             \
-        k_decode_fp32<D0, D1, D2, D3><<<grid, 128, 0, st>>>(M, u, v, s, n, out, out_fp16);                         \
+        const TexUnitObjs none = {};                                                                               \
+        k_decode_fp32<D0, D1, D2, D3><<<grid, 128, 0, st>>>(M, none, u, v, s, n, out, out_fp16);                   \
         return cudaGetLastError();                                                                                 \
     }
 
@@ -439,6 +443,28 @@ cudaError_t launch_decode_fp32(const MaterialDev &M, const float *u, const float
     BCF_FP32_CASE(25, 64, 64, 9)
     k_decode_fp32_generic<<<grid, 128, 0, st>>>(M, u, v, s, n, out, out_fp16);
     return cudaGetLastError();
+}
+
+// FP32 materials on variant 3: the texture unit's texels and the same exact filter, then the plain FP32 MLP
+// (the common three-layer shapes; others keep the software texels)
+#define BCF_FP32_HW_CASE(D0, D1, D2, D3)                                                                           \
+    if (P.n_layers == 3 && P.dims[0] == D0 && P.dims[1] == D1 && P.dims[2] == D2 && P.dims[3] == D3) {             \
+        k_decode_fp32<D0, D1, D2, D3, true><<<grid, 128, 0, st>>>(M, T, u, v, s, n, out, out_fp16);                 \
+        return cudaGetLastError();                                                                                 \
+    }
+
+cudaError_t launch_decode_fp32_texunit(const MaterialDev &M, const TexUnitObjs &T, const float *u, const float *v,
+                                       const float *s, int64_t n, void *out, int out_fp16, cudaStream_t st)
+{
+    if (n == 0)
+        return cudaSuccess;
+    const MlpDev &P = M.mlp;
+    const unsigned grid = grid_for(n, 128, 16);
+    BCF_FP32_HW_CASE(6, 16, 16, 8)
+    BCF_FP32_HW_CASE(13, 32, 32, 9)
+    BCF_FP32_HW_CASE(12, 16, 16, 9)
+    BCF_FP32_HW_CASE(25, 64, 64, 9)
+    return launch_decode_fp32(M, u, v, s, n, out, out_fp16, st);
 }
 
 template <int PREC>

@@ -9,6 +9,8 @@ namespace bcf {
 
 cudaError_t launch_encode_mode10(const float *texels, int stride, int res, int levels, int64_t nblocks,
                                  float *params, uint8_t *part, float *err, cudaStream_t st);
+cudaError_t launch_decode_fp32_texunit(const MaterialDev &M, const TexUnitObjs &T, const float *u, const float *v,
+                                       const float *s, int64_t n, void *out, int out_fp16, cudaStream_t st);
 bool set_tex_supported(const MaterialDev &M0);
 cudaError_t launch_decode_set_tex(const MaterialDev &M0, const MaterialDev *mats, const TexUnitObjs *texs, int nmat,
                                   const int64_t *offsets, const float *u, const float *v, const float *s, int64_t n,

@@ -304,7 +304,7 @@ def test_texture_unit_variant_within_hardware_filter_error(precision):
     assert e.value.status == 2
 
 
-@pytest.mark.parametrize("precision,signed", [("fp16", False), ("fp8", False), ("fp16", True)])
+@pytest.mark.parametrize("precision,signed", [("fp16", False), ("fp8", False), ("fp16", True), ("fp32", False)])
 def test_texture_unit_texels_with_exact_filter_equal_the_software_decode(precision, signed):
     """Variant 3 fetches every footprint texel from the texture unit with point filtering (the hardware's BC6H
     decoder, bit-exact with the software one) and filters it with the same FP32 operations as the per-lane
