@@ -190,12 +190,14 @@ def test_decode_tensor_core_paths_match_quant_aware_oracle(precision, out_dtype,
           f"beyond-tolerance fraction {frac:.1e}; vs unquantised FP64: max {np.abs(got - ref).max(axis=0).round(5)}")
 
 
+@pytest.mark.parametrize("variant", [0, 3])
 @pytest.mark.parametrize("precision", ["fp32", "fp16"])
-def test_decode_edge_sizes(precision):
+def test_decode_edge_sizes(precision, variant):
     """n = 1, a ragged n, and n = 0 (no-op)."""
     bcf = _bcf()
     w = workloads.small_screen(res=32, width=40, height=1)
     m = workloads.upload(w, precision)
+    m.set_decode_variant(variant)
     Wst, bias, a, ws = w.weights(precision)
     P = oracle.Mlp(w.dims, precision, Wst, bias, a, ws)
     for n in (1, 33, 40):
@@ -225,7 +227,7 @@ def test_invalid_arguments_return_status_without_launching():
 
 # --------------------------------------------------------------------------- tile-cooperative kernel
 
-def _decode_both(w, precision, u=None, v=None, s=None, out_dtype=torch.float32):
+def _decode_both(w, precision, u=None, v=None, s=None, out_dtype=torch.float32, also_texunit=False):
     m = workloads.upload(w, precision)
     if u is None:
         u, v, s = workloads.queries_to_device(w)
@@ -233,6 +235,10 @@ def _decode_both(w, precision, u=None, v=None, s=None, out_dtype=torch.float32):
     a = m.decode(u, v, s, out_dtype=out_dtype).cpu().numpy()
     m.set_decode_variant(1)
     b = m.decode(u, v, s, out_dtype=out_dtype).cpu().numpy()
+    if also_texunit:  # the texture-unit texels with the exact filter (variant 3) give the same values
+        m.set_decode_variant(3)
+        c = m.decode(u, v, s, out_dtype=out_dtype).cpu().numpy()
+        np.testing.assert_array_equal(c, b)
     return a, b
 
 
@@ -249,7 +255,8 @@ def test_tiled_equals_per_lane_bit_for_bit(precision):
 @pytest.mark.parametrize("case", ["row_order", "random_uv", "wide_lod", "clamp", "signed"])
 def test_tiled_fallbacks_and_addressing_match_oracle(case):
     """Incoherent tiles (arena overflow), tiles spanning more than three
-    levels, clamp addressing, signed textures and row-major query order."""
+    levels, clamp addressing, signed textures and row-major query order, for
+    the software decoders and the texture-unit texels (bit-identical)."""
     _bcf()
     kw = {}
     if case == "row_order":
@@ -267,7 +274,7 @@ def test_tiled_fallbacks_and_addressing_match_oracle(case):
     elif case == "signed":
         w.is_signed = True
         w.blocks = [synth.bounded_blocks(rng, b.shape[0], signed=True) for b in w.blocks]
-    a, b = _decode_both(w, "fp16")
+    a, b = _decode_both(w, "fp16", also_texunit=True)
     np.testing.assert_array_equal(a, b)
     Wst, bias, _, _ = w.weights("fp16")
     ref_q = oracle.decode(_oracle_material(w), oracle.Mlp(w.dims, "fp16", Wst, bias), w.u, w.v, w.s,
