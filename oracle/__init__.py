@@ -117,6 +117,9 @@ def lib():
         L.oracle_train_query.restype = None
         L.oracle_train_query.argtypes = [c_uint64, c_uint64, c_int64, c_float, POINTER(c_float), POINTER(c_float),
                                          POINTER(c_float)]
+        L.oracle_train_query_grid.restype = None
+        L.oracle_train_query_grid.argtypes = [c_uint64, c_uint64, c_int64, c_int, c_float, POINTER(c_float),
+                                              POINTER(c_float), POINTER(c_float)]
         L.oracle_train_texel.restype = c_double
         L.oracle_train_texel.argtypes = [c_void_p, c_int, c_int, c_int]
         L.oracle_train_texel_relaxed.restype = c_double
@@ -339,14 +342,21 @@ def philox4x32_10(ctr: list[int], key: list[int]) -> list[int]:
     return [int(x) for x in o]
 
 
-def train_queries(seed: int, step: int, batch: int, s_max: float) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+def train_queries(seed: int, step: int, batch: int, s_max: float,
+                  grid: int = 0) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """The step's batch draws: independent (u, v, s) per query, or (grid > 0) a grid x grid uv grid with one
+    offset and one s per batch."""
     u = np.zeros(batch, np.float32)
     v = np.zeros(batch, np.float32)
     s = np.zeros(batch, np.float32)
     L = lib()
     cu, cv, cs = c_float(), c_float(), c_float()
     for q in range(batch):
-        L.oracle_train_query(seed, step, q, s_max, ctypes.byref(cu), ctypes.byref(cv), ctypes.byref(cs))
+        if grid:
+            L.oracle_train_query_grid(seed, step, q, grid, s_max, ctypes.byref(cu), ctypes.byref(cv),
+                                      ctypes.byref(cs))
+        else:
+            L.oracle_train_query(seed, step, q, s_max, ctypes.byref(cu), ctypes.byref(cv), ctypes.byref(cs))
         u[q], v[q], s[q] = cu.value, cv.value, cs.value
     return u, v, s
 

@@ -834,6 +834,26 @@ void oracle_philox4x32_10(const uint32_t ctr_in[4], const uint32_t key_in[2], ui
 /* Training batch draw for query q of step t: counter (q, t_lo, t_hi, 0),
  * key (seed_lo, seed_hi); u, v in [0, 1) and s in [0, s_max) from the top
  * 24 bits of the first three output words. */
+/* The paper's batch form (Sec. 5.1: a uniformly sampled uv grid with one scale per batch): query q of a
+ * grid x grid batch sits at ((i + o_u) / grid, (j + o_v) / grid), i = q mod grid, j = q / grid, with one
+ * offset (o_u, o_v) and one s per step, drawn from the Philox counter (2^32 - 1, step, 2^32 - 1), which no
+ * per-query draw uses.  Single-precision arithmetic, as on the device. */
+void oracle_train_query_grid(uint64_t seed, uint64_t step, int64_t q, int grid, float s_max, float *u, float *v,
+                             float *s)
+{
+    uint32_t ctr[4] = {0xFFFFFFFFu, (uint32_t)step, (uint32_t)(step >> 32), 0xFFFFFFFFu};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t o[4];
+    oracle_philox4x32_10(ctr, key, o);
+    float ou = (float)ldexp((double)(o[0] >> 8), -24), ov = (float)ldexp((double)(o[1] >> 8), -24);
+    int i = (int)(q % grid), j = (int)(q / grid);
+    float inv = 1.0f / (float)grid;
+    float xu = (float)i + ou, xv = (float)j + ov;
+    *u = xu * inv;
+    *v = xv * inv;
+    *s = (float)(ldexp((double)(o[2] >> 8), -24) * (double)s_max);
+}
+
 void oracle_train_query(uint64_t seed, uint64_t step, int64_t q, float s_max, float *u, float *v, float *s)
 {
     uint32_t ctr[4] = {(uint32_t)q, (uint32_t)step, (uint32_t)(step >> 32), (uint32_t)((uint64_t)q >> 32)};

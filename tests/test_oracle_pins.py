@@ -966,3 +966,17 @@ def test_literal_ste_is_the_relaxed_form_on_the_lattice():
         gs = oracle.train_texel_grad_v(p, k, t, c, literal=True)
         gr = oracle.train_texel_grad_v(q, k, t, c, literal=True, relaxed=True)
         np.testing.assert_allclose(gs, gr, rtol=1e-12, atol=0)
+
+
+def test_grid_batches_are_a_jittered_grid_with_one_scale():
+    """The paper's batch form (Sec. 5.1): a grid x grid uv grid shifted by one offset in [0, 1)^2 per step, one s
+    per step in [0, s_max); consecutive steps draw different offsets."""
+    G = 16
+    u, v, s = oracle.train_queries(9, 4, G * G, 7.0, grid=G)
+    assert np.all(s == s[0]) and 0.0 <= s[0] < 7.0
+    i, j = np.arange(G * G) % G, np.arange(G * G) // G
+    ou, ov = u * G - i, v * G - j
+    assert np.allclose(ou, ou[0], atol=1e-5) and np.allclose(ov, ov[0], atol=1e-5)
+    assert 0.0 <= ou[0] < 1.0 and 0.0 <= ov[0] < 1.0
+    u2, _, s2 = oracle.train_queries(9, 5, G * G, 7.0, grid=G)
+    assert u2[0] != u[0] and s2[0] != s[0]
