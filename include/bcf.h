@@ -337,6 +337,7 @@ typedef struct {
     int32_t unconstrained;                  /* 1: free per-texel features (see below) instead of block parameters */
     int32_t is_signed;                      /* 1: BC6H signed (SF16) features: endpoints in [-32, 31], a = 31/32 */
     int32_t literal;                        /* 1: Eq. 7-8 as printed instead of the format's exact steps (below) */
+    int32_t batch_grid;                     /* > 0: step batches are batch_grid^2 uv grids (below); 0: random */
 } bcf_trainer_desc;
 
 /*
@@ -355,14 +356,19 @@ bcf_status bcf_trainer_destroy(bcf_trainer tr);
  *   queries: (d_u, d_v, d_s) of length `batch` if given, otherwise drawn with
  *   Philox4x32-10: counter (q, step low, step high, q high), key (seed low,
  *   seed high); u, v, s = top 24 bits of output words 0, 1, 2 times 2^-24
- *   (s also times s_max);
+ *   (s also times s_max).  With batch_grid = G > 0 (the paper's batches,
+ *   Sec. 5.1: a uniformly sampled uv grid with one scale per batch) the batch
+ *   must be G^2 and query q = j G + i sits at ((i + o_u) / G, (j + o_v) / G)
+ *   with one (o_u, o_v, s) per step from the counter (2^32 - 1, step low,
+ *   step high, 2^32 - 1), single-precision arithmetic;
  *   loss: mean over batch and channels of (G - F(M))^2, written to
  *   d_loss_out (one float, device; overwritten);
  *   gradients accumulated into the trainer's grad arrays, then Adam with
  *   lr_t = lr0 gamma^step, bias correction with step + 1, endpoints clamped
  *   to [0, 63] and x to [0, 1]; gradients are zeroed afterwards.
  * batch == 0 only runs the optimiser on zero gradients.  Errors:
- * BCF_ERR_INVALID_ARG for batch < 0, step < 0 or a null loss pointer.
+ * BCF_ERR_INVALID_ARG for batch < 0, step < 0, a null loss pointer, or a
+ * grid trainer's batch other than G^2.
  */
 bcf_status bcf_train_step(bcf_trainer tr, int64_t batch, uint64_t seed, int64_t step, const float *d_u,
                           const float *d_v, const float *d_s, float *d_loss_out, bcf_stream stream);

@@ -50,7 +50,7 @@ class _TrainerDesc(ctypes.Structure):
                 ("target_res", c_int32), ("target_levels", c_int32), ("d_target8", c_void_p), ("d_target1", c_void_p),
                 ("lr_features", c_float), ("lr_mlp", c_float), ("gamma", c_float), ("beta1", c_float),
                 ("beta2", c_float), ("eps", c_float), ("s_max", c_float), ("unconstrained", c_int32),
-                ("is_signed", c_int32), ("literal", c_int32)]
+                ("is_signed", c_int32), ("literal", c_int32), ("batch_grid", c_int32)]
 
 
 _lib = None
@@ -332,7 +332,7 @@ class Trainer:
                  target1: torch.Tensor, target_res: int, target_levels: int, lr_features: float = 1e-2,
                  lr_mlp: float = 1e-3, gamma: float = 0.9999, beta1: float = 0.9, beta2: float = 0.999,
                  eps: float = 1e-8, s_max: float | None = None, lod_input: bool = True, unconstrained: bool = False,
-                 is_signed: bool = False, literal: bool = False):
+                 is_signed: bool = False, literal: bool = False, batch_grid: int = 0):
         z = torch.zeros_like
         self.params, self.partition = list(params), list(partition)
         self.grads = [z(p) for p in params]
@@ -366,6 +366,7 @@ class Trainer:
         d.s_max = float(target_levels - 1 if s_max is None else s_max)
         d.unconstrained = int(unconstrained)
         d.is_signed, d.literal = int(is_signed), int(literal)
+        d.batch_grid = int(batch_grid)
         self.unconstrained = bool(unconstrained)
         h = c_void_p()
         _check(lib().bcf_trainer_create(ctypes.byref(d), ctypes.byref(h)), "bcf_trainer_create")

@@ -105,7 +105,10 @@ __global__ void __launch_bounds__(kTrainThreads) k_train(TrainDev D, int mode, i
                 v = qv[q];
                 s = qs[q];
             } else {
-                draw_query(q, seed_lo, seed_hi, step_lo, step_hi, D.s_max, u, v, s);
+                if (D.batch_grid > 0)
+                    draw_query_grid(q, D.batch_grid, seed_lo, seed_hi, step_lo, step_hi, D.s_max, u, v, s);
+                else
+                    draw_query(q, seed_lo, seed_hi, step_lo, step_hi, D.s_max, u, v, s);
             }
             u = isfinite(u) ? u - floorf(u) : 0.0f;
             v = isfinite(v) ? v - floorf(v) : 0.0f;

@@ -29,6 +29,7 @@ struct TrainDev {
     int32_t unconstrained; // free per-texel features [texels][4] instead of block records [blocks][32]
     int32_t is_signed;     // SF16 block features (endpoints in [-32, 31], a = 31/32)
     int32_t literal;       // Eq. 7-8 as printed instead of the format's exact steps
+    int32_t batch_grid;    // > 0: batches are batch_grid x batch_grid uv grids with one scale (the paper's form)
 };
 
 // emulation variant of the block features: bit 0 signed, bit 1 literal

@@ -54,6 +54,9 @@ bcf_status bcf_trainer_create(const bcf_trainer_desc *d, bcf_trainer *out)
     D.unconstrained = d->unconstrained != 0;
     D.is_signed = d->is_signed != 0;
     D.literal = d->literal != 0;
+    if (d->batch_grid < 0 || d->batch_grid > 65535)
+        return tfail(BCF_ERR_INVALID_ARG, "batch_grid %d not in [0, 65535]", d->batch_grid);
+    D.batch_grid = d->batch_grid;
     if (D.unconstrained && (D.is_signed || D.literal))
         return tfail(BCF_ERR_INVALID_ARG, "unconstrained features have no BC6 emulation variant");
     for (int t = 0; t < D.n_tex; ++t) {
@@ -159,6 +162,9 @@ bcf_status bcf_train_step(bcf_trainer tr, int64_t batch, uint64_t seed, int64_t 
         return tfail(BCF_ERR_INVALID_ARG, "bcf_train_step: null trainer / loss, or negative batch / step");
     if ((d_u != nullptr) != (d_v != nullptr) || (d_u != nullptr) != (d_s != nullptr))
         return tfail(BCF_ERR_INVALID_ARG, "bcf_train_step: give all of u, v, s or none");
+    if (!d_u && tr->dev.batch_grid > 0 && batch != (int64_t)tr->dev.batch_grid * tr->dev.batch_grid)
+        return tfail(BCF_ERR_INVALID_ARG, "bcf_train_step: grid batches need batch = %d^2",
+                     tr->dev.batch_grid);
     cudaStream_t st = (cudaStream_t)stream;
     cudaError_t e = cudaMemsetAsync(d_loss_out, 0, sizeof(float), st);
     if (e == cudaSuccess)

@@ -372,4 +372,21 @@ __device__ __forceinline__ void draw_query(int64_t q, uint32_t seed_lo, uint32_t
     s = ((float)(c[2] >> 8) * 0x1p-24f) * s_max;
 }
 
+// The paper's batch form (Sec. 5.1): query q of a grid x grid batch at ((i + o_u) / grid, (j + o_v) / grid),
+// i = q mod grid, j = q / grid, with one offset and one s per step from the Philox counter
+// (2^32 - 1, step, 2^32 - 1), which no per-query draw uses.
+__device__ __forceinline__ void draw_query_grid(int64_t q, int grid, uint32_t seed_lo, uint32_t seed_hi,
+                                                uint32_t step_lo, uint32_t step_hi, float s_max, float &u, float &v,
+                                                float &s)
+{
+    uint32_t c[4] = {0xFFFFFFFFu, step_lo, step_hi, 0xFFFFFFFFu};
+    philox4x32_10(c, seed_lo, seed_hi);
+    const float ou = (float)(c[0] >> 8) * 0x1p-24f, ov = (float)(c[1] >> 8) * 0x1p-24f;
+    const int i = (int)(q % grid), j = (int)(q / grid);
+    const float inv = 1.0f / (float)grid;
+    u = __fmul_rn(__fadd_rn((float)i, ou), inv);
+    v = __fmul_rn(__fadd_rn((float)j, ov), inv);
+    s = ((float)(c[2] >> 8) * 0x1p-24f) * s_max;
+}
+
 } // namespace bcf

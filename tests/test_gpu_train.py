@@ -367,3 +367,19 @@ def test_literal_emulation_against_the_exact_default_after_export():
     assert abs(res[False][0] - res[False][1]) < 0.2  # exact: the export decodes to the trained features
     # literal: about 1 dB lost at export (measured: 28.31 dB emulated, 27.31 dB exported; exact 28.39 dB)
     assert res[True][1] < res[True][0] - 0.5 and res[True][1] < res[False][1] - 0.5
+
+
+def test_grid_batches_loss_and_step_match_oracle():
+    """The paper's batch form (Sec. 5.1): a 32 x 32 jittered uv grid with one scale per step."""
+    bcf = _bcf()
+    w = workloads.train_workload(**MEDIUM)
+    G = 32
+    tr = workloads.upload_trainer(w, lr_features=1e-2, lr_mlp=1e-3, gamma=0.9999, batch_grid=G)
+    seed, step = 4242, 3
+    loss = float(tr.step(G * G, seed, step).item())
+    u, v, s = oracle.train_queries(seed, step, G * G, float(w.target_levels - 1), grid=G)
+    F, P, T = _oracle_parts(w)
+    ref_loss, _, _, _ = oracle.train_loss_grad(F, P, T, u, v, s)
+    assert loss == pytest.approx(ref_loss, rel=2e-3)
+    with pytest.raises(bcf.BcfError):
+        tr.step(G * G + 1, seed, step)
