@@ -559,6 +559,29 @@ def main():
     set_n = sw.n
     del graph, S, set_mats, su, sv, ss, sout, seq_out, seq_q
 
+    # the paper's own decode configuration (Table 1 BCf-1K, decoder 12-16-9) at 3840x2160, FP16, variant 3
+    wp = workloads.paper_bcf1k()
+    up_, vp_, sp_ = workloads.queries_to_device(wp)
+    mp_ = workloads.upload(wp, "fp16")
+    mp_.set_decode_variant(HEADLINE_VARIANT)
+    outp = torch.empty((wp.n, 9), dtype=torch.float16, device="cuda")
+    for _ in range(3):
+        mp_.decode(up_, vp_, sp_, out=outp)
+    torch.cuda.synchronize()
+    tot = 0.0
+    for _ in range(k_extra):
+        flush.zero_()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        mp_.decode(up_, vp_, sp_, out=outp)
+        b.record(stream)
+        b.synchronize()
+        tot += a.elapsed_time(b)
+    paper_ms = tot / k_extra
+    paper_n = wp.n
+    del mp_, up_, vp_, sp_, outp, wp
+
     # large deferred decode: 8 x 4096^2, 7680x4320 queries, MLP 25-64-64-9 (FP8, FP16, FP32)
     w5 = workloads.config5()
     u5, v5, s5 = workloads.queries_to_device(w5)
@@ -647,6 +670,12 @@ def main():
                                                           "tiles_per_grab": set_cfg[2]}},
                         "sequential_64_launches": {"value": set_n / (seq_ms * 1e-3) / 1e9, "unit": "Gsamples/s",
                                                    "ms_per_step": seq_ms}},
+            "paper_bcf1k_2160p": {"value": paper_n / (paper_ms * 1e-3) / 1e9, "unit": "Gsamples/s",
+                                  "ms_per_step": paper_ms, "queries": paper_n,
+                                  "workload": "BC6H 1024/512/256/128 with 9/8/7/6 levels, MLP 12-16-9, FP16, "
+                                              "variant 3, 3840x2160 plane queries",
+                                  "context": "the paper's neural overhead at 2160p: 0.640 ms on an RTX 2070 "
+                                             "(hardware trilinear, graphics pipeline)"},
             "large_8x4096": {"queries": n5, "mlp": "25-64-64-9", "flop_per_query": flops5, **cfg5},
             "small_2x256": {"queries": 65536, "mlp": "6-16-16-8 fp32", "us_per_launch": small_us,
                             "value": 65536 / (small_us * 1e-6) / 1e9, "unit": "Gsamples/s",

@@ -243,6 +243,8 @@ __global__ void __launch_bounds__(128) k_decode_mma(MaterialDev M, TexUnitObjs T
         __syncwarp();
         if constexpr (K0 == 0)
             warp_mlp<PREC>(P, sw, sb, act0, act1, ost);
+        else if constexpr (N2 == 0) // one hidden layer (the paper's decoder shape)
+            warp_mlp2<PREC, K0, N1, NO>(sw, sb, act0, row_stride, ost, C);
         else // the common shapes: layers chained through registers (act1 is the FP8 re-quantisation tile)
             warp_mlp3<PREC, K0, N1, N2, NO>(P, sw, sb, act0, row_stride, act1,
                                             tile_stride_bytes<BCF_FP8_E4M3>(N1 > N2 ? N1 : N2), ost, C);
@@ -359,7 +361,10 @@ __global__ void __launch_bounds__(32 * kSetTexWarps) k_decode_set_tex(
             for (; col < K0; ++col)
                 store_feature<PREC>(row, col, 0.0f, inv0);
             __syncwarp();
-            warp_mlp3<PREC, K0, N1, N2, NO>(Ms.mlp, sw, sb, act0, row_stride, act1,
+            if constexpr (N2 == 0)
+                warp_mlp2<PREC, K0, N1, NO>(sw, sb, act0, row_stride, ost, C);
+            else
+                warp_mlp3<PREC, K0, N1, N2, NO>(Ms.mlp, sw, sb, act0, row_stride, act1,
                                             tile_stride_bytes<BCF_FP8_E4M3>(N1 > N2 ? N1 : N2), ost, C);
             __syncwarp();
             const int rows = (int)min((int64_t)32, b - q0w);
@@ -520,6 +525,9 @@ static cudaError_t launch_mma(const MaterialDev &M, const TexUnitObjs &T, const 
         if (k0 == 32 && n1 == 64 && n2 == 64 && no == 16)
             return launch_mma_shape<PREC, HW, 32, 64, 64, 16>(M, T, u, v, s, n, out, out_fp16, st);
     }
+    if constexpr (PREC != BCF_FP8_E4M3)
+        if (P.n_layers == 2 && P.kpad[0] == 16 && P.npad[0] == 16 && P.npad[1] == 16)
+            return launch_mma_shape<PREC, HW, 16, 16, 0, 16>(M, T, u, v, s, n, out, out_fp16, st);
     return launch_mma_shape<PREC, HW, 0, 0, 0, 0>(M, T, u, v, s, n, out, out_fp16, st);
 }
 
@@ -594,14 +602,25 @@ static cudaError_t launch_set_tex_shape(const MaterialDev &M0, const MaterialDev
     return cudaGetLastError();
 }
 
+static bool set_tex_two_layer(const MlpDev &P);
+
 bool set_tex_supported(const MaterialDev &M0)
 {
     const MlpDev &P = M0.mlp;
-    if (P.n_layers != 3 || P.precision == BCF_FP32)
+    if (P.precision == BCF_FP32)
+        return false;
+    if (set_tex_two_layer(P))
+        return true;
+    if (P.n_layers != 3)
         return false;
     const int kq = P.precision == BCF_FP8_E4M3 ? 32 : 16;
     return (P.kpad[0] == kq && P.npad[0] == 32 && P.npad[1] == 32 && P.npad[2] == 16) ||
            (P.kpad[0] == 32 && P.npad[0] == 64 && P.npad[1] == 64 && P.npad[2] == 16);
+}
+
+static bool set_tex_two_layer(const MlpDev &P)
+{
+    return P.n_layers == 2 && P.precision != BCF_FP8_E4M3 && P.kpad[0] == 16 && P.npad[0] == 16 && P.npad[1] == 16;
 }
 
 cudaError_t launch_decode_set_tex(const MaterialDev &M0, const MaterialDev *mats, const TexUnitObjs *texs, int nmat,
@@ -612,6 +631,13 @@ cudaError_t launch_decode_set_tex(const MaterialDev &M0, const MaterialDev *mats
         return cudaSuccess;
     const MlpDev &P = M0.mlp;
     const bool wide = P.kpad[0] == 32 && P.npad[0] == 64;
+    if (set_tex_two_layer(P)) {
+        if (P.precision == BCF_BF16)
+            return launch_set_tex_shape<BCF_BF16, 16, 16, 0, 16>(M0, mats, texs, nmat, offsets, u, v, s, n, out,
+                                                                  out_fp16, counter, st);
+        return launch_set_tex_shape<BCF_FP16, 16, 16, 0, 16>(M0, mats, texs, nmat, offsets, u, v, s, n, out,
+                                                              out_fp16, counter, st);
+    }
 #define BCF_SET_TEX(PR, KQ)                                                                                          \
     return wide ? launch_set_tex_shape<PR, 32, 64, 64, 16>(M0, mats, texs, nmat, offsets, u, v, s, n, out, out_fp16, \
                                                            counter, st)                                              \

@@ -585,6 +585,8 @@ __device__ __forceinline__ void decode_tile(const MaterialDev &M, const TileCtx 
         // ---- 6. MLP on the tensor cores, coalesced store
         if constexpr (K0 == 0)
             warp_mlp<PREC>(P, sw, sb, act0, act1, ost);
+        else if constexpr (N2 == 0) // one hidden layer
+            warp_mlp2<PREC, K0, N1, NO>(sw, sb, act0, row_stride, ost, Cn);
         else
             warp_mlp3<PREC, K0, N1, N2, NO>(P, sw, sb, act0, row_stride, tmp8,
                                             tile_stride_bytes<BCF_FP8_E4M3>(N1 > N2 ? N1 : N2), ost, Cn);
@@ -781,6 +783,9 @@ static cudaError_t launch_tiled_prec(const MaterialDev &M, const float *u, const
         if (k0 == 32 && n1 == 64 && n2 == 64 && no == 16)
             return launch_tiled_shape<PREC, 32, 64, 64, 16>(M, u, v, s, n, out, out_fp16, st);
     }
+    if constexpr (PREC != BCF_FP8_E4M3)
+        if (P.n_layers == 2 && P.kpad[0] == 16 && P.npad[0] == 16 && P.npad[1] == 16)
+            return launch_tiled_shape<PREC, 16, 16, 0, 16>(M, u, v, s, n, out, out_fp16, st);
     return launch_tiled_shape<PREC, 0, 0, 0, 0>(M, u, v, s, n, out, out_fp16, st);
 }
 

@@ -461,4 +461,45 @@ __device__ __forceinline__ void warp_mlp3(const MlpDev &P, const unsigned char *
     }
 }
 
+// K0 -> N1 -> NO (padded) MLP with one hidden layer -- the paper's decoder shape (12 inputs, one hidden layer
+// of 16, Sec. 5.1) -- for 16-bit operands, layers chained through registers as in warp_mlp3.
+template <int PREC, int K0, int N1, int NO>
+__device__ __forceinline__ void warp_mlp2(const unsigned char *sw, const float *sb, const unsigned char *in,
+                                          int in_stride, float *ost, int C)
+{
+    static_assert(PREC != BCF_FP8_E4M3, "FP8 pads the hidden layer's K to 32: the generic MLP covers it");
+    constexpr int KK = Op<PREC>::kK, EB = Op<PREC>::kBytes;
+    const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+    const int s0 = tile_stride_bytes<PREC>(K0), s1 = tile_stride_bytes<PREC>(N1);
+    const unsigned char *W0 = sw;
+    const unsigned char *W1 = W0 + N1 * s0;
+    const float *b0 = sb, *b1 = sb + N1;
+#pragma unroll 1
+    for (int m0 = 0; m0 < 2; ++m0) {
+        uint32_t a0[1][K0 / KK][4];
+#pragma unroll
+        for (int kt = 0; kt < K0 / KK; ++kt)
+            load_a<EB, KK>(in, in_stride, m0 * 16, kt * KK, g, t, a0[0][kt]);
+        float d1[1][N1 / 8][4];
+        mma_layer<PREC, 1, K0, N1>(a0, W0, s0, g, t, d1);
+        uint32_t a1[1][N1 / KK][4];
+        hidden_to_a16<PREC, 1, N1>(d1, b0, t, a1);
+        float d2[1][NO / 8][4];
+        mma_layer<PREC, 1, N1, NO>(a1, W1, s1, g, t, d2);
+#pragma unroll
+        for (int nt = 0; nt < NO / 8; ++nt) {
+            const int c = nt * 8 + 2 * t;
+            const int r0 = m0 * 16 + g, r1 = r0 + 8;
+            if (c < C) {
+                ost[r0 * C + c] = d2[0][nt][0] + b1[c];
+                ost[r1 * C + c] = d2[0][nt][2] + b1[c];
+            }
+            if (c + 1 < C) {
+                ost[r0 * C + c + 1] = d2[0][nt][1] + b1[c + 1];
+                ost[r1 * C + c + 1] = d2[0][nt][3] + b1[c + 1];
+            }
+        }
+    }
+}
+
 } // namespace bcf

@@ -82,8 +82,9 @@ def screen_material(config: int, n_tex: int, res: int, dims: list[int], width: i
     u, v, s = synth.plane_queries(seed_rng(config, 1), width, height, res_ref=res, supersample=supersample,
                                   tile=tile)
     W, b = synth.mlp_weights(seed_rng(config, 2), dims)
-    return DecodeWorkload(f"config{config}", [res] * n_tex, [levels] * n_tex, res, tex.blocks, True, dims, W, b, u, v,
-                          s, input_bound=max(1.0, float(s.max())))
+    lod_input = dims[0] == 3 * n_tex + 1  # the paper's own network reads the 3 T features only
+    return DecodeWorkload(f"config{config}", [res] * n_tex, [levels] * n_tex, res, tex.blocks, lod_input, dims, W, b,
+                          u, v, s, input_bound=max(1.0, float(s.max())))
 
 
 def config2() -> DecodeWorkload:
@@ -272,3 +273,18 @@ def upload_free_trainer(w: TrainWorkload, texels: list[np.ndarray] | None = None
     t1 = torch.from_numpy(w.target1.view(np.int16).copy()).to(device)
     return Trainer(P, [None] * len(P), w.res, w.levels, w.res_ref, w.dims, W, b, t8, t1, w.target_res,
                    w.target_levels, unconstrained=True, **hyper)
+
+
+def paper_bcf1k(width: int = 3840, height: int = 2160, config: int = 6) -> DecodeWorkload:
+    """The paper's decode configuration (Table 1 BCf-1K, Table 3): four value-bounded BC6H feature textures of
+    1024^2, 512^2, 256^2, 128^2 with 9 / 8 / 7 / 6 levels, the paper's decoder (12 inputs, one hidden layer of
+    16, 9 outputs, no LOD input), one sample per pixel of the perspective-plane screen with LODs in units of a
+    2048^2 material."""
+    res = [1024, 512, 256, 128]
+    levels = [synth.full_levels(r) for r in res]
+    tex = synth.make_textures(seed_rng(config, 0), res, levels, kind="bounded")
+    u, v, s = synth.plane_queries(seed_rng(config, 1), width, height, res_ref=2048)
+    dims = [12, 16, 9]
+    W, b = synth.mlp_weights(seed_rng(config, 2), dims)
+    return DecodeWorkload(f"paper-bcf1k-{width}x{height}", res, levels, 2048, tex.blocks, False, dims, W, b, u, v,
+                          s, input_bound=1.0)

@@ -369,3 +369,19 @@ def test_host_memory_decode_equals_device_decode(n, scratch_kb):
     assert torch.equal(oh, ref.cpu())
     with pytest.raises(bcf.BcfError):
         m.decode_host(uh, vh, sh, oh, scratch[:4096])  # too small for one 256-query chunk
+
+
+@pytest.mark.parametrize("precision", ["fp16", "bf16", "fp8"])
+def test_paper_decoder_shape_12_16_9(precision):
+    """The paper's own decoder: 12 inputs (4 textures, no LOD input), one hidden layer of 16 (Sec. 5.1).  The
+    16-bit precisions take the register-chained one-hidden-layer MLP; every variant agrees bit for bit and with
+    the oracle."""
+    _bcf()
+    w = workloads.small_screen(res=128, width=200, height=61, dims=(12, 16, 9))
+    assert not w.lod_input
+    a, b = _decode_both(w, precision, also_texunit=True)
+    np.testing.assert_array_equal(a, b)
+    Wst, bias, sa, ws = w.weights(precision)
+    ref_q = oracle.decode(_oracle_material(w), oracle.Mlp(w.dims, precision, Wst, bias, sa, ws), w.u, w.v, w.s,
+                          quant_aware=True, threads=8)
+    _quant_check(a.astype(np.float64), ref_q, TOL[precision], precision)
