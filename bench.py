@@ -193,7 +193,8 @@ def _cpu_baseline(w, precision, gpu_out, seconds=12.0):
 
     def stats(d):
         return {"max_abs": [float(f"{x:.3g}") for x in np.abs(d).max(axis=0)],
-                "rms": [float(f"{x:.3g}") for x in np.sqrt((d * d).mean(axis=0))]}
+                "rms": [float(f"{x:.3g}") for x in np.sqrt((d * d).mean(axis=0))],
+                "p99.9_abs": [float(f"{x:.3g}") for x in np.quantile(np.abs(d), 0.999, axis=0)]}
 
     acc = {"reference": "exact FP64 decode with the FP32 master weights, 65536 sampled queries, per channel"}
     for prec, get in gpu_out.items():
@@ -456,6 +457,22 @@ def main():
     del scratch, ud, vd, sd
 
     train_ms, train_loss, train_batch = _train_bench(torch, workloads, stream, max(3, args.steps // 2))
+    # FP32 atomic-add rate of this GPU for scattered updates into a buffer of the trainer's size (torch
+    # index_add_, one atomic per element): the reference for the training scatter's reduction rate
+    gbuf = torch.zeros(9_786_368, device="cuda")
+    gidx = torch.randint(0, gbuf.numel(), (1 << 24,), device="cuda")
+    gval = torch.rand(1 << 24, device="cuda")
+    for _ in range(2):
+        gbuf.index_add_(0, gidx, gval)
+    torch.cuda.synchronize()
+    ga, gb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ga.record(stream)
+    for _ in range(5):
+        gbuf.index_add_(0, gidx, gval)
+    gb.record(stream)
+    gb.synchronize()
+    atomic_rate = 5 * (1 << 24) / (ga.elapsed_time(gb) * 1e-3)
+    del gbuf, gidx, gval
     # first training stage (unconstrained per-texel features), same sizes and batch
     tw0 = workloads.train_workload()
     tr0 = workloads.upload_free_trainer(tw0, lr_features=5e-2, lr_mlp=1e-3, gamma=0.9995)
@@ -684,7 +701,11 @@ def main():
                       "ms_per_step": train_ms, "batch": train_batch,
                       "samples_per_s": train_batch * 1000.0 / train_ms,
                       "workload": "4x block-parameterised 1024^2 (9 levels), 2048^2 9-ch reference, "
-                                  "MLP 13-32-32-9 BF16 operands, Adam", "last_loss": train_loss},
+                                  "MLP 13-32-32-9 BF16 operands, Adam", "last_loss": train_loss,
+                      "atomic_microbenchmark": {"value": atomic_rate, "unit": "FP32 atomic adds/s",
+                                                "workload": "torch index_add_ of 2^24 random updates into "
+                                                            "9.79 M floats"},
+                      "adam_algorithmic_bytes_per_step": 313_000_000},
             "software_decode": {"value": w.n / (sw_ms * 1e-3) / 1e9, "unit": "Gsamples/s", "ms_per_step": sw_ms,
                                 "precision": HEADLINE_PRECISION, "kernel": "k_decode_tiled (decode variant 0: "
                                 "tile-cooperative software BC6H decode into shared memory)",
