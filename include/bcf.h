@@ -72,6 +72,33 @@ const char *bcf_last_error(void);
 /* Library version as major * 10000 + minor * 100 + patch. */
 int bcf_version(void);
 
+/*
+ * Device-side checks.  Some conditions can only be seen by the kernels, on
+ * data that lives on the device: those kernels set a bit of a 32-bit check
+ * word (one per device, created with the first material set or trainer)
+ * with an atomic OR, take the documented safe reading of the data and carry
+ * on.  Nothing is reported until the caller asks:
+ *
+ *   BCF_CHECK_PARTITION  a training block's partition id (d_partition) is
+ *                        above 31; the block is read, trained and exported
+ *                        with id & 31.
+ *   BCF_CHECK_OFFSETS    material-set query offsets decrease
+ *                        (d_offsets[m+1] < d_offsets[m]); that material's
+ *                        range is decoded as empty.
+ */
+#define BCF_CHECK_PARTITION 0x1u
+#define BCF_CHECK_OFFSETS 0x2u
+
+/*
+ * bcf_device_check -- wait for all work on the current device (every
+ * stream), then read and clear its check word.  Returns BCF_OK if no check
+ * fired, else BCF_ERR_DEVICE_CHECK with bcf_last_error() naming the checks.
+ * h_word (may be NULL) receives the word.  Like cudaDeviceSynchronize, this
+ * blocks the host; launches made by other host threads while it runs may
+ * land on either side of the read.
+ */
+bcf_status bcf_device_check(uint32_t *h_word);
+
 /* ------------------------------------------------------------ BC6H unpack */
 
 /*
@@ -227,7 +254,7 @@ bcf_status bcf_destroy_material_set(bcf_material_set set);
  * concatenated: material m's queries are [d_offsets[m], d_offsets[m+1]) of
  * d_u / d_v / d_s (and of the rows of d_out [n_queries][C]).  d_offsets:
  * n + 1 non-decreasing int64 on the device (entries are clipped to
- * [0, n_queries]).  Queries are processed in tiles of 256 taken from an
+ * [0, n_queries]; a decreasing pair sets BCF_CHECK_OFFSETS).  Queries are processed in tiles of 256 taken from an
  * atomic work counter that a memset before the launch resets, so the call
  * can be captured into a CUDA graph and replayed.  Calls on one set must
  * not overlap on the GPU (they share the counter).  Errors as
@@ -265,7 +292,8 @@ bcf_status bcf_material_set_config(bcf_material_set set, int32_t *cap, int32_t *
  *   [8..10] e3 RGB, [11..13] e4 RGB endpoints of region 1
  *   [14..15] unused (kept 0)
  *   [16..31] x_1..x_16             per-texel positions on the segment, [0, 1]
- * plus one partition id k in [0, 31] per block (uint8, fixed during training).
+ * plus one partition id k in [0, 31] per block (uint8, fixed during training;
+ * a larger id sets BCF_CHECK_PARTITION and reads as k & 31).
  *
  * Forward (the emulated BC6 decompression of Sec. 4.2 at the exported
  * precision of Sec. 5.2, i.e. BC6H mode 10): endpoints and x are rounded to

@@ -23,6 +23,7 @@ MAX_LAYERS = 8
 MAX_WIDTH = 128
 
 FP32, FP16, BF16, FP8_E4M3 = 0, 1, 2, 3
+CHECK_PARTITION, CHECK_OFFSETS = 0x1, 0x2  # bits of the device check word
 PRECISION = {"fp32": FP32, "fp16": FP16, "bf16": BF16, "fp8": FP8_E4M3}
 
 
@@ -115,6 +116,8 @@ def lib() -> ctypes.CDLL:
                                                c_void_p, c_int64, c_void_p]
         L.bcf_encode_mode10.restype = c_int
         L.bcf_encode_mode10.argtypes = [c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]
+        L.bcf_device_check.restype = c_int
+        L.bcf_device_check.argtypes = [POINTER(ctypes.c_uint32)]
         _lib = L
     return _lib
 
@@ -140,6 +143,17 @@ def _stream() -> int:
 
 
 # --------------------------------------------------------------------------- BC6H
+
+def device_check(raise_on_failure: bool = True) -> int:
+    """bcf_device_check: wait for all work on the current device, read and clear its check word
+    (CHECK_PARTITION, CHECK_OFFSETS) and return it; raises BcfError naming the checks when a bit is set and
+    raise_on_failure holds."""
+    word = ctypes.c_uint32(0)
+    status = lib().bcf_device_check(ctypes.byref(word))
+    if status != 0 and (raise_on_failure or word.value == 0):
+        _check(status, "bcf_device_check")
+    return word.value
+
 
 def decode_bc6h(blocks: torch.Tensor, blocks_w: int, blocks_h: int, is_signed: bool = False,
                 out: torch.Tensor | None = None) -> torch.Tensor:
@@ -373,6 +387,28 @@ class Trainer:
         self.handle = h
         self.dims = list(dims)
         self.loss = torch.zeros(1, dtype=torch.float32, device=W.device)
+
+    def state_dict(self) -> dict:
+        """Checkpoint of the trainable state: block parameters (or free texels), partitions, MLP weights and both
+        Adam moments, as CPU copies.  The step counter is the caller's (bcf_train_step takes it per call), and
+        the batch draws are a function of (seed, step), so a run resumed at step t draws what it would have."""
+        cpu = lambda xs: [x.detach().cpu().clone() for x in xs]
+        return {"params": cpu(self.params), "m": cpu(self.m), "v": cpu(self.v),
+                "partition": [None if k is None else k.detach().cpu().clone() for k in self.partition],
+                "W": self.W.detach().cpu().clone(), "b": self.b.detach().cpu().clone(),
+                "W_m": self.W_m.detach().cpu().clone(), "W_v": self.W_v.detach().cpu().clone(),
+                "b_m": self.b_m.detach().cpu().clone(), "b_v": self.b_v.detach().cpu().clone()}
+
+    def load_state_dict(self, state: dict) -> None:
+        """Restore a state_dict() into this trainer's buffers in place (same sizes); gradients are zeroed."""
+        for dst, src in zip(self.params + self.m + self.v, state["params"] + state["m"] + state["v"]):
+            dst.copy_(src)
+        for dst, src in zip(self.partition, state["partition"]):
+            if dst is not None:
+                dst.copy_(src)
+        for name in ("W", "b", "W_m", "W_v", "b_m", "b_v"):
+            getattr(self, name).copy_(state[name])
+        self.zero_grad()
 
     def close(self):
         if self.handle:

@@ -3,6 +3,7 @@
 // the decode path; bcf_create_material allocates the small device metadata.
 #include <math.h>
 #include <algorithm>
+#include <mutex>
 #include <new>
 #include <stdarg.h>
 #include <stdio.h>
@@ -49,6 +50,30 @@ static int ilog2(int64_t v)
 static bool aligned(const void *p, int a) { return ((uintptr_t)p % (uintptr_t)a) == 0; }
 static int round_up(int v, int m) { return (v + m - 1) / m * m; }
 
+constexpr int kMaxDevices = 64;
+static std::mutex g_check_mu;
+static unsigned *g_check[kMaxDevices];
+
+unsigned *check_word()
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+        return nullptr;
+    std::lock_guard<std::mutex> lock(g_check_mu);
+    if (!g_check[dev]) {
+        unsigned *p = nullptr;
+        const unsigned zero = 0;
+        if (cudaMalloc(&p, sizeof(unsigned)) != cudaSuccess)
+            return nullptr;
+        if (cudaMemcpy(p, &zero, sizeof zero, cudaMemcpyHostToDevice) != cudaSuccess) { // synchronous
+            cudaFree(p);
+            return nullptr;
+        }
+        g_check[dev] = p;
+    }
+    return g_check[dev];
+}
+
 } // namespace bcf
 
 using namespace bcf;
@@ -72,6 +97,33 @@ const char *bcf_status_string(bcf_status s)
 const char *bcf_last_error(void) { return g_err; }
 
 int bcf_version(void) { return 100; }
+
+bcf_status bcf_device_check(uint32_t *h_word)
+{
+    if (h_word)
+        *h_word = 0;
+    unsigned *w = check_word();
+    if (!w)
+        return fail(BCF_ERR_OOM, "bcf_device_check: the device check word could not be created");
+    unsigned h = 0;
+    cudaError_t e = cudaDeviceSynchronize(); // every stream: no kernel can set a bit between the read and the clear
+    if (e == cudaSuccess)
+        e = cudaMemcpy(&h, w, sizeof h, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess)
+        e = cudaMemset(w, 0, sizeof h);
+    if (e == cudaSuccess)
+        e = cudaDeviceSynchronize();
+    if (e != cudaSuccess)
+        return cuda_status(e, "bcf_device_check");
+    if (h_word)
+        *h_word = h;
+    if (!h)
+        return BCF_OK;
+    return fail(BCF_ERR_DEVICE_CHECK, "device checks fired (word 0x%x):%s%s", h,
+                (h & BCF_CHECK_PARTITION) ? " a training block's partition id is above 31 (read as id & 31);" : "",
+                (h & BCF_CHECK_OFFSETS) ? " material-set query offsets decrease (that range was decoded as empty);"
+                                        : "");
+}
 
 bcf_status bcf_decode_bc6h(const void *d_blocks, int32_t blocks_w, int32_t blocks_h, int32_t is_signed, uint16_t *d_out,
                            bcf_stream stream)
@@ -427,6 +479,7 @@ struct bcf_material_set_s {
     bcf::SetConfig cfg;
     bcf::TexUnitObjs *tex_table; // device table of the materials' texture objects (texture-unit sets)
     int texunit;             // 1: every material was on decode variant 3 at creation
+    unsigned *check;         // the device's check word (BCF_CHECK_OFFSETS)
 };
 
 extern "C" {
@@ -470,7 +523,8 @@ bcf_status bcf_create_material_set(const bcf_material *mats, int32_t n, bcf_mate
     }
     for (int m = 0; m < n; ++m)
         host[m] = mats[m]->host;
-    cudaError_t e = cudaMalloc(&set->table, sizeof(MaterialDev) * n);
+    set->check = check_word();
+    cudaError_t e = set->check ? cudaMalloc(&set->table, sizeof(MaterialDev) * n) : cudaErrorMemoryAllocation;
     if (e == cudaSuccess)
         e = cudaMalloc(&set->counter, sizeof(int));
     if (e == cudaSuccess)
@@ -533,10 +587,11 @@ bcf_status bcf_decode_material_set(bcf_material_set set, const int64_t *d_offset
     if (set->texunit)
         return cuda_status(launch_decode_set_tex(set->first, set->table, set->tex_table, set->n, d_offsets, d_u, d_v,
                                                  d_s, n_queries, d_out, out_precision == BCF_FP16, set->counter,
-                                                 (cudaStream_t)stream),
+                                                 set->check, (cudaStream_t)stream),
                            "bcf_decode_material_set launch");
     return cuda_status(launch_decode_set(set->first, set->table, set->n, d_offsets, d_u, d_v, d_s, n_queries, d_out,
-                                         out_precision == BCF_FP16, set->counter, set->cfg, (cudaStream_t)stream),
+                                         out_precision == BCF_FP16, set->counter, set->check, set->cfg,
+                                         (cudaStream_t)stream),
                        "bcf_decode_material_set launch");
 }
 
@@ -581,7 +636,7 @@ bcf_status bcf_autotune_material_set(bcf_material_set set, const int64_t *d_offs
                         e = cudaEventRecord(a, cs);
                         if (e == cudaSuccess)
                             e = launch_decode_set(set->first, set->table, set->n, d_offsets, d_u, d_v, d_s, n_queries,
-                                                  d_out, out_precision == BCF_FP16, set->counter, cfg, cs);
+                                                  d_out, out_precision == BCF_FP16, set->counter, set->check, cfg, cs);
                         if (e == cudaSuccess)
                             e = cudaEventRecord(b, cs);
                         if (e == cudaSuccess)

@@ -276,7 +276,7 @@ __global__ void __launch_bounds__(32 * kSetTexWarps) k_decode_set_tex(
     const MaterialDev *__restrict__ mats, const TexUnitObjs *__restrict__ texs, int nmat,
     const int64_t *__restrict__ offsets, const float *__restrict__ qu, const float *__restrict__ qv,
     const float *__restrict__ qs, int64_t n, void *__restrict__ out, int out_fp16, int *__restrict__ counter,
-    int act_bytes)
+    unsigned *__restrict__ check, int act_bytes)
 {
     constexpr int kTile = 32 * kSetTexWarps;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -303,6 +303,8 @@ __global__ void __launch_bounds__(32 * kSetTexWarps) k_decode_set_tex(
             tile_first[m] = acc;
             const int64_t a = min(max(offsets[m], (int64_t)0), n), b = min(max(offsets[m + 1], (int64_t)0), n);
             acc += b > a ? (b - a + kTile - 1) / kTile : 0;
+            if (blockIdx.x == 0 && offsets[m + 1] < offsets[m] && check)
+                atomicOr(check, BCF_CHECK_OFFSETS);
         }
         tile_first[nmat] = acc;
     }
@@ -576,7 +578,7 @@ template <int PREC, int K0, int N1, int N2, int NO>
 static cudaError_t launch_set_tex_shape(const MaterialDev &M0, const MaterialDev *mats, const TexUnitObjs *texs,
                                         int nmat, const int64_t *offsets, const float *u, const float *v,
                                         const float *s, int64_t n, void *out, int out_fp16, int *counter,
-                                        cudaStream_t st)
+                                        unsigned *check, cudaStream_t st)
 {
     const MlpDev &P = M0.mlp;
     const int act = mma_act_bytes<PREC>(P);
@@ -598,7 +600,7 @@ static cudaError_t launch_set_tex_shape(const MaterialDev &M0, const MaterialDev
     if (e != cudaSuccess)
         return e;
     kern<<<(unsigned)(sm_count() * max(per_sm, 1)), 32 * kSetTexWarps, (size_t)smem, st>>>(
-        mats, texs, nmat, offsets, u, v, s, n, out, out_fp16, counter, act);
+        mats, texs, nmat, offsets, u, v, s, n, out, out_fp16, counter, check, act);
     return cudaGetLastError();
 }
 
@@ -625,7 +627,7 @@ static bool set_tex_two_layer(const MlpDev &P)
 
 cudaError_t launch_decode_set_tex(const MaterialDev &M0, const MaterialDev *mats, const TexUnitObjs *texs, int nmat,
                                   const int64_t *offsets, const float *u, const float *v, const float *s, int64_t n,
-                                  void *out, int out_fp16, int *counter, cudaStream_t st)
+                                  void *out, int out_fp16, int *counter, unsigned *check, cudaStream_t st)
 {
     if (n == 0)
         return cudaSuccess;
@@ -634,15 +636,15 @@ cudaError_t launch_decode_set_tex(const MaterialDev &M0, const MaterialDev *mats
     if (set_tex_two_layer(P)) {
         if (P.precision == BCF_BF16)
             return launch_set_tex_shape<BCF_BF16, 16, 16, 0, 16>(M0, mats, texs, nmat, offsets, u, v, s, n, out,
-                                                                  out_fp16, counter, st);
+                                                                  out_fp16, counter, check, st);
         return launch_set_tex_shape<BCF_FP16, 16, 16, 0, 16>(M0, mats, texs, nmat, offsets, u, v, s, n, out,
-                                                              out_fp16, counter, st);
+                                                              out_fp16, counter, check, st);
     }
 #define BCF_SET_TEX(PR, KQ)                                                                                          \
     return wide ? launch_set_tex_shape<PR, 32, 64, 64, 16>(M0, mats, texs, nmat, offsets, u, v, s, n, out, out_fp16, \
-                                                           counter, st)                                              \
+                                                           counter, check, st)                                              \
                 : launch_set_tex_shape<PR, KQ, 32, 32, 16>(M0, mats, texs, nmat, offsets, u, v, s, n, out, out_fp16, \
-                                                           counter, st)
+                                                           counter, check, st)
     switch (P.precision) {
     case BCF_FP16: BCF_SET_TEX(BCF_FP16, 16);
     case BCF_BF16: BCF_SET_TEX(BCF_BF16, 16);

@@ -658,13 +658,15 @@ __global__ void __launch_bounds__(kTileQ, 3) k_decode_tiled(MaterialDev M, const
 // atomic work counter (zeroed before the launch) and reload the material's
 // metadata and MLP weights into shared memory when a tile belongs to a new
 // material.  Offsets are clipped to [0, n], so malformed ranges cannot
-// address outside the query and output arrays.
+// address outside the query and output arrays; a decreasing pair sets the
+// offsets check bit (its range is empty).
 template <int PREC, int CAP, int K0, int N1, int N2, int NO>
 __global__ void __launch_bounds__(kTileQ, 3) k_decode_set(const MaterialDev *__restrict__ mats, int nmat,
                                                           const int64_t *__restrict__ offsets, const float *__restrict__ qu,
                                                           const float *__restrict__ qv, const float *__restrict__ qs,
                                                           int64_t n, void *__restrict__ out, int out_fp16,
-                                                          int *__restrict__ counter, int chunk)
+                                                          int *__restrict__ counter, unsigned *__restrict__ check,
+                                                          int chunk)
 {
     static_assert(CAP <= 2 * kTileQ, "blocks are held two per thread while sorting");
     extern __shared__ __align__(16) unsigned char smem[];
@@ -680,6 +682,8 @@ __global__ void __launch_bounds__(kTileQ, 3) k_decode_set(const MaterialDev *__r
             tile_first[m] = acc;
             const int64_t a = min(max(offsets[m], (int64_t)0), n), b = min(max(offsets[m + 1], (int64_t)0), n);
             acc += b > a ? (b - a + kTileQ - 1) / kTileQ : 0;
+            if (blockIdx.x == 0 && offsets[m + 1] < offsets[m] && check)
+                atomicOr(check, BCF_CHECK_OFFSETS);
         }
         tile_first[nmat] = acc;
     }
@@ -807,7 +811,7 @@ cudaError_t launch_decode_tiled(const MaterialDev &M, const float *u, const floa
 template <int PREC, int CAP, int K0, int N1, int N2, int NO>
 static cudaError_t launch_set_shape(const MaterialDev &M0, const MaterialDev *mats, int nmat, const int64_t *offsets,
                                     const float *u, const float *v, const float *s, int64_t n, void *out,
-                                    int out_fp16, int *counter, const SetConfig &cfg, cudaStream_t st)
+                                    int out_fp16, int *counter, unsigned *check, const SetConfig &cfg, cudaStream_t st)
 {
     const int64_t smem = tiled_layout<PREC>(M0.mlp, CAP, K0 == 0).total;
     if (smem > 200 * 1024)
@@ -825,14 +829,14 @@ static cudaError_t launch_set_shape(const MaterialDev &M0, const MaterialDev *ma
     if (e != cudaSuccess)
         return e;
     kern<<<(unsigned)(tiled_sms() * per_sm), kTileQ, (size_t)smem, st>>>(mats, nmat, offsets, u, v, s, n, out,
-                                                                           out_fp16, counter, max(cfg.chunk, 1));
+                                                                           out_fp16, counter, check, max(cfg.chunk, 1));
     return cudaGetLastError();
 }
 
 template <int PREC, int CAP>
 static cudaError_t launch_set_cap(const MaterialDev &M0, const MaterialDev *mats, int nmat, const int64_t *offsets,
                                   const float *u, const float *v, const float *s, int64_t n, void *out, int out_fp16,
-                                  int *counter, const SetConfig &cfg, cudaStream_t st)
+                                  int *counter, unsigned *check, const SetConfig &cfg, cudaStream_t st)
 {
     const MlpDev &P = M0.mlp;
     if (P.n_layers == 3) {
@@ -840,31 +844,34 @@ static cudaError_t launch_set_cap(const MaterialDev &M0, const MaterialDev *mats
         constexpr int kq = PREC == BCF_FP8_E4M3 ? 32 : 16;
         if (k0 == kq && n1 == 32 && n2 == 32 && no == 16)
             return launch_set_shape<PREC, CAP, kq, 32, 32, 16>(M0, mats, nmat, offsets, u, v, s, n, out, out_fp16,
-                                                                counter, cfg, st);
+                                                                counter, check, cfg, st);
     }
-    return launch_set_shape<PREC, CAP, 0, 0, 0, 0>(M0, mats, nmat, offsets, u, v, s, n, out, out_fp16, counter, cfg,
-                                                   st);
+    return launch_set_shape<PREC, CAP, 0, 0, 0, 0>(M0, mats, nmat, offsets, u, v, s, n, out, out_fp16, counter, check,
+                                                   cfg, st);
 }
 
 template <int PREC>
 static cudaError_t launch_set_prec(const MaterialDev &M0, const MaterialDev *mats, int nmat, const int64_t *offsets,
                                    const float *u, const float *v, const float *s, int64_t n, void *out, int out_fp16,
-                                   int *counter, const SetConfig &cfg, cudaStream_t st)
+                                   int *counter, unsigned *check, const SetConfig &cfg, cudaStream_t st)
 {
     if (cfg.cap == 256)
-        return launch_set_cap<PREC, 256>(M0, mats, nmat, offsets, u, v, s, n, out, out_fp16, counter, cfg, st);
-    return launch_set_cap<PREC, 320>(M0, mats, nmat, offsets, u, v, s, n, out, out_fp16, counter, cfg, st);
+        return launch_set_cap<PREC, 256>(M0, mats, nmat, offsets, u, v, s, n, out, out_fp16, counter, check, cfg, st);
+    return launch_set_cap<PREC, 320>(M0, mats, nmat, offsets, u, v, s, n, out, out_fp16, counter, check, cfg, st);
 }
 
 cudaError_t launch_decode_set(const MaterialDev &M0, const MaterialDev *mats, int nmat, const int64_t *offsets,
                               const float *u, const float *v, const float *s, int64_t n, void *out, int out_fp16,
-                              int *counter, const SetConfig &cfg, cudaStream_t st)
+                              int *counter, unsigned *check, const SetConfig &cfg, cudaStream_t st)
 {
     switch (M0.mlp.precision) {
-    case BCF_FP16: return launch_set_prec<BCF_FP16>(M0, mats, nmat, offsets, u, v, s, n, out, out_fp16, counter, cfg, st);
-    case BCF_BF16: return launch_set_prec<BCF_BF16>(M0, mats, nmat, offsets, u, v, s, n, out, out_fp16, counter, cfg, st);
+    case BCF_FP16:
+        return launch_set_prec<BCF_FP16>(M0, mats, nmat, offsets, u, v, s, n, out, out_fp16, counter, check, cfg, st);
+    case BCF_BF16:
+        return launch_set_prec<BCF_BF16>(M0, mats, nmat, offsets, u, v, s, n, out, out_fp16, counter, check, cfg, st);
     case BCF_FP8_E4M3:
-        return launch_set_prec<BCF_FP8_E4M3>(M0, mats, nmat, offsets, u, v, s, n, out, out_fp16, counter, cfg, st);
+        return launch_set_prec<BCF_FP8_E4M3>(M0, mats, nmat, offsets, u, v, s, n, out, out_fp16, counter, check, cfg,
+                                             st);
     default: return cudaErrorInvalidValue;
     }
 }

@@ -60,6 +60,10 @@ struct MaterialDev {
     MlpDev mlp;
 };
 
+// The current device's check word (include/bcf.h, BCF_CHECK_*), created on the first call; nullptr if that
+// allocation failed.  Kernels set its bits with atomicOr; bcf_device_check reads and clears it.
+unsigned *check_word();
+
 } // namespace bcf
 
 #ifndef BCF_MAX_SET

@@ -14,7 +14,7 @@ cudaError_t launch_decode_fp32_texunit(const MaterialDev &M, const TexUnitObjs &
 bool set_tex_supported(const MaterialDev &M0);
 cudaError_t launch_decode_set_tex(const MaterialDev &M0, const MaterialDev *mats, const TexUnitObjs *texs, int nmat,
                                   const int64_t *offsets, const float *u, const float *v, const float *s, int64_t n,
-                                  void *out, int out_fp16, int *counter, cudaStream_t st);
+                                  void *out, int out_fp16, int *counter, unsigned *check, cudaStream_t st);
 cudaError_t launch_decode_texunit(const MaterialDev &M, const TexUnitObjs &T, int exact_filter, const float *u,
                                   const float *v, const float *s, int64_t n, void *out, int out_fp16, cudaStream_t st);
 cudaError_t texunit_create(const MaterialDev &M, TexUnitObjs &T, void **arrays);
@@ -39,7 +39,7 @@ struct SetConfig {
 };
 cudaError_t launch_decode_set(const MaterialDev &M0, const MaterialDev *mats, int nmat, const int64_t *offsets,
                               const float *u, const float *v, const float *s, int64_t n, void *out, int out_fp16,
-                              int *counter, const SetConfig &cfg, cudaStream_t st);
+                              int *counter, unsigned *check, const SetConfig &cfg, cudaStream_t st);
 cudaError_t texunit_decode(const void *d_blocks, int bw, int bh, int is_signed, uint16_t *d_out, cudaStream_t st);
 
 // thread-local error text

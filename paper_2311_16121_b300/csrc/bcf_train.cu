@@ -121,7 +121,7 @@ __global__ void __launch_bounds__(kTrainThreads) k_train(TrainDev D, int mode, i
                 const TrainTexDev &T = D.tex[t];
                 for_each_tap(T, u, v, s, [&](const Tap &tp) {
                     SteTexel tx;
-                    ste_texel_v(T.params + tp.block * 32, T.part[tp.block], tp.texel, emu, tx);
+                    ste_texel_v(T.params + tp.block * 32, read_partition(T, tp.block), tp.texel, emu, tx);
 #pragma unroll
                     for (int c = 0; c < 3; ++c)
                         f[c] = fmaf(tp.weight, tx.v[c], f[c]);
@@ -227,7 +227,7 @@ __global__ void __launch_bounds__(kTrainThreads) k_train(TrainDev D, int mode, i
                 for_each_tap(T, u, v, s, [&](const Tap &tp) {
                     const float *p = T.params + tp.block * 32;
                     SteTexel tx;
-                    ste_texel_v(p, T.part[tp.block], tp.texel, emu, tx);
+                    ste_texel_v(p, read_partition(T, tp.block), tp.texel, emu, tx);
                     float *gp = T.grad + tp.block * 32;
                     float ga[3], gb[3], gx = 0.0f;
 #pragma unroll
@@ -383,13 +383,18 @@ struct BitWriter {
 };
 
 __global__ void k_export_blocks(const float *__restrict__ params, const uint8_t *__restrict__ part, int64_t nblocks,
-                                int is_signed, uint4 *__restrict__ out)
+                                int is_signed, unsigned *__restrict__ check, uint4 *__restrict__ out)
 {
     const int64_t b = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (b >= nblocks)
         return;
     const float *p = params + b * 32;
-    const int k = part[b];
+    int k = part[b];
+    if (k > 31) { // the same reading as training: id & 31
+        if (check)
+            atomicOr(check, BCF_CHECK_PARTITION);
+        k &= 31;
+    }
     int q[4][3], idx[16];
 #pragma unroll
     for (int e = 0; e < 4; ++e)
@@ -518,7 +523,8 @@ cudaError_t launch_export(const TrainDev &D, void *const *blocks_out, uint16_t *
     for (int t = 0; t < D.n_tex; ++t) {
         const int64_t nb = D.tex[t].blocks;
         k_export_blocks<<<(unsigned)((nb + 127) / 128), 128, 0, st>>>(D.tex[t].params, D.tex[t].part, nb,
-                                                                      D.is_signed, (uint4 *)blocks_out[t]);
+                                                                      D.is_signed, D.tex[t].check,
+                                                                      (uint4 *)blocks_out[t]);
     }
     if (weights_fp16)
         k_export_weights<<<(unsigned)((D.w_total + 255) / 256), 256, 0, st>>>(D.W, D.w_total, weights_fp16);

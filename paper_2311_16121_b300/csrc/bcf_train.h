@@ -12,6 +12,7 @@ struct TrainTexDev {
     float *grad;          // [blocks][32]
     float *m, *v;         // Adam moments
     const uint8_t *part;  // [blocks]
+    unsigned *check;      // the device's check word (BCF_CHECK_PARTITION)
     int32_t res, levels, lod_bias;
     int64_t blocks;       // block records, or texels when the features are unconstrained
 };

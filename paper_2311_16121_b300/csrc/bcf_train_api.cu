@@ -131,6 +131,11 @@ bcf_status bcf_trainer_create(const bcf_trainer_desc *d, bcf_trainer *out)
         return tfail(BCF_ERR_UNSUPPORTED, "unconstrained features need a dims[0] <= 16 -> 32 -> 32 -> 9 MLP");
     if (train_smem_bytes(D) > 227 * 1024)
         return tfail(BCF_ERR_UNSUPPORTED, "MLP too wide for the training kernel's shared memory");
+    unsigned *check = check_word(); // after every argument check: the first call allocates on the device
+    if (!check)
+        return tfail(BCF_ERR_OOM, "bcf_trainer_create: the device check word could not be created");
+    for (int t = 0; t < D.n_tex; ++t)
+        D.tex[t].check = check;
     bcf_trainer tr = new (std::nothrow) bcf_trainer_s;
     if (!tr)
         return tfail(BCF_ERR_OOM, "host allocation failed");

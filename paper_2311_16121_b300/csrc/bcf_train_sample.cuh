@@ -58,6 +58,18 @@ struct TexelParams {
     int region;
 };
 
+// Partition id of block b; an id above 31 sets the partition check bit and reads as id & 31.
+__device__ __forceinline__ int read_partition(const TrainTexDev &T, int64_t b)
+{
+    const int k = T.part[b];
+    if (k > 31) {
+        if (T.check)
+            atomicOr(T.check, BCF_CHECK_PARTITION);
+        return k & 31;
+    }
+    return k;
+}
+
 __device__ __forceinline__ void load_texel(const float *p, int k, int t, TexelParams &P)
 {
     P.region = (int)((partition_mask(k) >> t) & 1);
@@ -247,7 +259,7 @@ __device__ __forceinline__ void for_each_side(const TrainTexDev &T, float u, flo
         int k[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c)
-            k[c] = T.part[tp[c].block];
+            k[c] = read_partition(T, tp[c].block);
         TexelParams P[4];
 #pragma unroll
         for (int c = 0; c < 4; ++c)

@@ -383,3 +383,26 @@ def test_grid_batches_loss_and_step_match_oracle():
     assert loss == pytest.approx(ref_loss, rel=2e-3)
     with pytest.raises(bcf.BcfError):
         tr.step(G * G + 1, seed, step)
+
+
+def test_checkpoint_resume_reproduces_the_run():
+    """state_dict / load_state_dict: training 6 steps straight equals training 3, checkpointing into a fresh
+    trainer, and training 3 more (same draws, since they depend only on seed and step)."""
+    _bcf()
+    w = workloads.train_workload(**MEDIUM)
+    a = workloads.upload_trainer(w, lr_features=1e-2, lr_mlp=1e-3, gamma=0.9999)
+    for i in range(6):
+        a.step(w.batch, 31, i)
+    b = workloads.upload_trainer(w, lr_features=1e-2, lr_mlp=1e-3, gamma=0.9999)
+    for i in range(3):
+        b.step(w.batch, 31, i)
+    state = b.state_dict()
+    c = workloads.upload_trainer(w, lr_features=1e-2, lr_mlp=1e-3, gamma=0.9999)
+    c.load_state_dict(state)
+    for i in range(3, 6):
+        c.step(w.batch, 31, i)
+    torch.cuda.synchronize()
+    # the gradient reductions are atomics (order-free), so compare within the Adam step scale
+    np.testing.assert_allclose(c.W.cpu().numpy(), a.W.cpu().numpy(), rtol=0, atol=3e-3)
+    for pa, pc in zip(a.params, c.params):
+        assert np.abs(pa.cpu().numpy() - pc.cpu().numpy()).max() <= 3e-2
