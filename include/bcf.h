@@ -496,6 +496,27 @@ bcf_status bcf_encode_mode10(const float *d_texels, int32_t texel_stride, int32_
                              float *d_params, uint8_t *d_partitions, float *d_errors, bcf_stream stream);
 
 /*
+ * bcf_pack_mode10 -- write block-parameter records as BC6H mode-10 blocks:
+ * the step bcf_train_export applies to a trainer's features, for any array
+ * of records (with bcf_encode_mode10 in front, a complete mode-10
+ * compressor).  Endpoints are rounded to 6-bit codes (clamped to [0, 63], or
+ * to [-32, 31] two's complement when is_signed), positions to 3-bit indices
+ * (round(7 x), x clamped to [0, 1]); where a region's anchor texel would
+ * need the top index bit, the region's endpoints are swapped and its indices
+ * mirrored, which keeps every texel value (Sec. 5.2).
+ * d_params    : [n_blocks][32] float32 records as in bcf_trainer_desc,
+ *               16-byte aligned.
+ * d_partitions: [n_blocks] ids in [0, 31] (a larger id sets
+ *               BCF_CHECK_PARTITION and reads as id & 31).
+ * d_blocks_out: [n_blocks][16] bytes, 16-byte aligned.
+ * n_blocks = 0 is a no-op.  The first call on a device creates its check
+ * word; otherwise no allocation.  Errors: BCF_ERR_INVALID_ARG for
+ * n_blocks < 0 or a null or misaligned pointer.
+ */
+bcf_status bcf_pack_mode10(const float *d_params, const uint8_t *d_partitions, int64_t n_blocks, int32_t is_signed,
+                           void *d_blocks_out, bcf_stream stream);
+
+/*
  * bcf_set_decode_variant -- choose the kernel bcf_decode_material uses for a
  * tensor-core (FP16 / BF16 / FP8) material.  0 (default): tile-cooperative
  * decode -- 256 screen-coherent queries share one decode of each BC6H block

@@ -116,6 +116,8 @@ def lib() -> ctypes.CDLL:
                                                c_void_p, c_int64, c_void_p]
         L.bcf_encode_mode10.restype = c_int
         L.bcf_encode_mode10.argtypes = [c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]
+        L.bcf_pack_mode10.restype = c_int
+        L.bcf_pack_mode10.argtypes = [c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_void_p]
         L.bcf_device_check.restype = c_int
         L.bcf_device_check.argtypes = [POINTER(ctypes.c_uint32)]
         _lib = L
@@ -188,6 +190,20 @@ def encode_mode10(texels: torch.Tensor, res: int, levels: int, params: torch.Ten
     _check(lib().bcf_encode_mode10(_ptr(texels), int(texel_stride), int(res), int(levels), _ptr(params), _ptr(partitions),
                                    _ptr(errors), _stream()), "bcf_encode_mode10")
     return params, partitions, errors
+
+
+def pack_mode10(params: torch.Tensor, partitions: torch.Tensor, is_signed: bool = False) -> torch.Tensor:
+    """bcf_pack_mode10: block-parameter records [blocks][32] float32 and partition ids [blocks] uint8 -> BC6H
+    mode-10 blocks as uint8 [blocks * 16]."""
+    nb = params.shape[0] if params.dim() == 2 else params.numel() // 32
+    if params.dtype != torch.float32 or params.numel() != nb * 32:
+        raise ValueError("pack_mode10: params must be float32 [blocks, 32]")
+    if partitions.dtype != torch.uint8 or partitions.numel() < nb:
+        raise ValueError(f"pack_mode10: {nb} uint8 partition ids expected")
+    out = torch.empty(nb * 16, dtype=torch.uint8, device=params.device)
+    _check(lib().bcf_pack_mode10(_ptr(params), _ptr(partitions), nb, int(is_signed), _ptr(out), _stream()),
+           "bcf_pack_mode10")
+    return out
 
 
 def texunit_decode_bc6h(blocks: torch.Tensor, blocks_w: int, blocks_h: int, is_signed: bool = False) -> torch.Tensor:

@@ -518,13 +518,22 @@ cudaError_t launch_adam(const TrainDev &D, const TrainHyper &H, int64_t step, cu
     return cudaGetLastError();
 }
 
+cudaError_t launch_export_blocks(const float *params, const uint8_t *part, int64_t nblocks, int is_signed,
+                                 unsigned *check, void *out, cudaStream_t st)
+{
+    if (nblocks > 0)
+        k_export_blocks<<<(unsigned)((nblocks + 127) / 128), 128, 0, st>>>(params, part, nblocks, is_signed, check,
+                                                                           (uint4 *)out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_export(const TrainDev &D, void *const *blocks_out, uint16_t *weights_fp16, cudaStream_t st)
 {
     for (int t = 0; t < D.n_tex; ++t) {
-        const int64_t nb = D.tex[t].blocks;
-        k_export_blocks<<<(unsigned)((nb + 127) / 128), 128, 0, st>>>(D.tex[t].params, D.tex[t].part, nb,
-                                                                      D.is_signed, D.tex[t].check,
-                                                                      (uint4 *)blocks_out[t]);
+        const cudaError_t e = launch_export_blocks(D.tex[t].params, D.tex[t].part, D.tex[t].blocks, D.is_signed,
+                                                   D.tex[t].check, blocks_out[t], st);
+        if (e != cudaSuccess)
+            return e;
     }
     if (weights_fp16)
         k_export_weights<<<(unsigned)((D.w_total + 255) / 256), 256, 0, st>>>(D.W, D.w_total, weights_fp16);

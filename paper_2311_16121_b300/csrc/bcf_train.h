@@ -53,6 +53,8 @@ cudaError_t launch_train_mma(const TrainDev &D, int mode, int64_t batch, uint64_
                              float *loss, int sms, cudaStream_t st);
 cudaError_t launch_adam(const TrainDev &D, const TrainHyper &H, int64_t step, cudaStream_t st);
 cudaError_t launch_export(const TrainDev &D, void *const *blocks_out, uint16_t *weights_fp16, cudaStream_t st);
+cudaError_t launch_export_blocks(const float *params, const uint8_t *part, int64_t nblocks, int is_signed,
+                                 unsigned *check, void *out, cudaStream_t st);
 
 } // namespace bcf
 

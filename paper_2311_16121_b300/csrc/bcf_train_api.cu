@@ -230,4 +230,23 @@ bcf_status bcf_train_export(bcf_trainer tr, void *const *d_blocks_out, uint16_t 
     return BCF_OK;
 }
 
+bcf_status bcf_pack_mode10(const float *d_params, const uint8_t *d_partitions, int64_t n_blocks, int32_t is_signed,
+                           void *d_blocks_out, bcf_stream stream)
+{
+    if (n_blocks < 0)
+        return tfail(BCF_ERR_INVALID_ARG, "bcf_pack_mode10: n_blocks %lld < 0", (long long)n_blocks);
+    if (n_blocks == 0)
+        return BCF_OK;
+    if (!al16(d_params) || !d_partitions || !al16(d_blocks_out))
+        return tfail(BCF_ERR_INVALID_ARG, "bcf_pack_mode10: null or misaligned pointer");
+    unsigned *check = check_word();
+    if (!check)
+        return tfail(BCF_ERR_OOM, "bcf_pack_mode10: the device check word could not be created");
+    cudaError_t e = launch_export_blocks(d_params, d_partitions, n_blocks, is_signed ? 1 : 0, check, d_blocks_out,
+                                         (cudaStream_t)stream);
+    if (e != cudaSuccess)
+        return tfail(BCF_ERR_CUDA, "bcf_pack_mode10: %s", cudaGetErrorString(e));
+    return BCF_OK;
+}
+
 } // extern "C"

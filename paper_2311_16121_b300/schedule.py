@@ -23,7 +23,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
-from . import Trainer, encode_mode10
+from . import Material, Trainer, encode_mode10, pack_mode10, texture_blocks
 from . import workloads as wl
 
 
@@ -68,8 +68,6 @@ def eval_psnr_exported(tr: Trainer, w: wl.TrainWorkload, is_signed: bool = False
                        max_queries: int = 1 << 22) -> tuple[float, list[float]]:
     """The same PSNR for what a renderer sees: the trainer's export (BC6H mode-10 blocks and FP16 weights)
     decoded by the decode path (bcf_decode_material, plain FP32 evaluation of the FP16 weights)."""
-    from . import Material
-
     blocks, w16 = tr.export()
     Wf = w16.view(torch.float16).float().contiguous()
     mat = Material(blocks, w.res, w.levels, w.res_ref, w.dims, "fp32", Wf, tr.b.contiguous(), is_signed=is_signed)
@@ -134,3 +132,47 @@ def random_init(w: wl.TrainWorkload, steps: int, batch: int | None = None, seed:
     batch = w.batch if batch is None else batch
     tr = wl.upload_trainer(w, lr_features=1e-2, lr_mlp=1e-3, gamma=0.9999)
     return tr, _run(tr, w, "random-partitions", steps, batch, seed, 0, eval_queries)
+
+
+def material_bytes(res: list[int], levels: list[int]) -> int:
+    """Storage of BC6H textures with mips: 16 bytes per 4 x 4 block."""
+    return sum(16 * texture_blocks(r, l) for r, l in zip(res, levels))
+
+
+def classic_bc6h(w: wl.TrainWorkload, res: int, eval_queries: int = 1 << 22):
+    """The material without the network: the nine reference channels compressed directly as three BC6H
+    textures -- albedo, the normal stored as n / 2 + 1 / 2 (the unsigned format holds no negative values),
+    roughness / metalness / AO -- at `res` (at most the reference's resolution) with the reference's own box
+    mips from that size down, each compressed by bcf_encode_mode10 + bcf_pack_mode10.  They are decoded by
+    the decode path (BC6H unpack, trilinear filtering at the query LOD) with a single linear output layer that
+    undoes the normal encoding, and scored with the same PSNR as the trained materials.
+    Returns (PSNR, per-level PSNRs, bytes)."""
+    if res > w.target_res or res & (res - 1):
+        raise ValueError("classic_bc6h: res must be a power of two no larger than the reference")
+    dev = torch.device("cuda")
+    lo = int(round(math.log2(w.target_res // res)))
+    levels = w.target_levels - lo
+    start = sum((w.target_res >> l) ** 2 for l in range(lo))
+    ref = np.concatenate([w.target8.astype(np.float32), w.target1.astype(np.float32)[:, None]], axis=1)[start:]
+    ref[:, 3:6] = ref[:, 3:6] * 0.5 + 0.5
+    blocks = []
+    for t in range(3):
+        tex = torch.from_numpy(np.ascontiguousarray(ref[:, 3 * t:3 * t + 3])).to(dev)
+        params, parts, _ = encode_mode10(tex.reshape(-1), res, levels)
+        blocks.append(pack_mode10(params, parts))
+    Wm = torch.eye(9, device=dev)
+    bm = torch.zeros(9, device=dev)
+    Wm[3:6, 3:6] *= 2.0
+    bm[3:6] = -1.0
+    mat = Material(blocks, [res] * 3, [levels] * 3, w.target_res, [9, 9], "fp32", Wm.reshape(-1).contiguous(),
+                   bm, lod_input=False)
+
+    class _Decoded:
+        W = Wm
+
+        @staticmethod
+        def forward(u, v, s):
+            return mat.decode(u, v, s, out_dtype=torch.float32)
+
+    ps, pl = eval_psnr(_Decoded, w, eval_queries)
+    return ps, pl, material_bytes([res] * 3, [levels] * 3)

@@ -140,3 +140,44 @@ def test_encoder_rejects_bad_arguments():
         bcf.encode_mode10(tex, 64, 1, texel_stride=5)
     with pytest.raises(ValueError):
         bcf.encode_mode10(tex[:100], 64, 1)  # too few texels
+
+
+@pytest.mark.parametrize("is_signed", [False, True])
+def test_pack_mode10_matches_oracle_export(is_signed):
+    """bcf_pack_mode10 on arbitrary records (codes beyond the clamp range, positions outside [0, 1], anchors
+    needing the swap) equals the oracle's export bit for bit; unsigned and signed."""
+    bcf = _bcf()
+    rng = np.random.default_rng(61 + is_signed)
+    nb = 3000
+    p28 = np.concatenate([rng.uniform(-40 if is_signed else -5, 68 if not is_signed else 40, (nb, 12)),
+                          rng.uniform(-0.2, 1.2, (nb, 16))], axis=1).astype(np.float32)
+    p32 = np.zeros((nb, 32), np.float32)
+    p32[:, 0:6], p32[:, 8:14], p32[:, 16:32] = p28[:, 0:6], p28[:, 6:12], p28[:, 12:28]
+    k = rng.integers(0, 32, nb).astype(np.uint8)
+    got = bcf.pack_mode10(torch.from_numpy(p32).cuda(), torch.from_numpy(k).cuda(), is_signed=is_signed)
+    got = got.cpu().numpy().reshape(nb, 16)
+    ref = np.stack([oracle.train_export_block(p28[i], int(k[i]), is_signed=is_signed) for i in range(nb)])
+    np.testing.assert_array_equal(got, ref)
+
+
+def test_encode_then_pack_is_a_mode10_compressor():
+    """encode + pack: every block decodes (bcf_decode_bc6h) to the encoder's reported error, computed here from
+    the decoded values against the input texels."""
+    bcf = _bcf()
+    rng = np.random.default_rng(67)
+    res, levels = 32, 3
+    tex = _texture(rng, res, levels, ("smooth", "noise"))
+    p, part, err = bcf.encode_mode10(torch.from_numpy(tex).cuda(), res, levels)
+    blocks = bcf.pack_mode10(p, part)
+    off_b, off_t = 0, 0
+    for lvl in range(levels):
+        W = res >> lvl
+        nb = (W // 4) ** 2
+        dec = bcf.decode_bc6h(blocks[16 * off_b:16 * (off_b + nb)], W // 4, W // 4).cpu().numpy()
+        vals = dec.view(np.float16).astype(np.float32).reshape(W, W, 3)
+        src = tex[off_t:off_t + W * W * 3].reshape(W, W, 3)
+        sq = ((vals - src) ** 2).reshape(W // 4, 4, W // 4, 4, 3).transpose(0, 2, 1, 3, 4).reshape(nb, 48)
+        e = err[off_b:off_b + nb].cpu().numpy()
+        np.testing.assert_allclose(sq.astype(np.float64).sum(1), e, rtol=1e-5, atol=1e-9)
+        off_b += nb
+        off_t += W * W * 3

@@ -281,6 +281,14 @@ def test_three_stage_schedule_runs_and_reports_psnr():
     # Sec. 6.5: partitions and initial blocks from the unconstrained warm-up beat random partitions
     # (measured on this problem: 28.4 dB vs 25.6 dB after 1,400 steps each)
     assert logs[2].psnr > rnd.psnr + 1.0
+    # the method without the network: the nine channels as three plain BC6H textures, at 3/4 and 3x the
+    # bytes of the four 64^2 feature textures
+    bytes_bcf = schedule.material_bytes(w.res, w.levels)
+    for r in (64, 128):
+        ps, pl, nbytes = schedule.classic_bc6h(w, r)
+        print(f"classic BC6H 3x{r}^2 {nbytes} B ({nbytes / bytes_bcf:.2f}x BCf) PSNR {ps:.2f} dB "
+              f"({', '.join(f'{x:.1f}' for x in pl)})")
+        assert math.isfinite(ps) and len(pl) == w.target_levels
 
 
 # --------------------------------------------------------------------------- SF16 and paper-literal emulation
