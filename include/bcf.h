@@ -496,6 +496,29 @@ bcf_status bcf_encode_mode10(const float *d_texels, int32_t texel_stride, int32_
                              float *d_params, uint8_t *d_partitions, float *d_errors, bcf_stream stream);
 
 /*
+ * bcf_compress_bc6h -- compress a mipmapped RGB texture into BC6H UF16
+ * blocks, for storing channels directly (the material without the network,
+ * as a comparison).  Per block two candidates: the mode-10 encoding of
+ * bcf_encode_mode10 (written as bcf_pack_mode10 writes it) and a mode-11
+ * encoding (one region over all sixteen texels: the same line fit, its ends
+ * quantised to 10-bit endpoints, each texel the best of the 16 indices);
+ * the one with the smaller total squared error is written (ties, or a NaN
+ * total: mode 10).  Decisions in IEEE single precision in a fixed order, as
+ * in bcf_encode_mode10.
+ * d_texels, texel_stride, res, levels: as bcf_encode_mode10.
+ * d_blocks : [blocks][16] bytes, levels concatenated (per level,
+ *            row-major), 16-byte aligned -- a texture bcf_create_material
+ *            takes as is.
+ * d_errors : [blocks] float32 total squared error of the written block,
+ *            or NULL.
+ * d_modes  : [blocks] uint8, 10 or 11, or NULL.
+ * Caller-owned buffers; asynchronous on `stream`; no allocation.  Errors:
+ * as bcf_encode_mode10.
+ */
+bcf_status bcf_compress_bc6h(const float *d_texels, int32_t texel_stride, int32_t res, int32_t levels, void *d_blocks,
+                             float *d_errors, uint8_t *d_modes, bcf_stream stream);
+
+/*
  * bcf_pack_mode10 -- write block-parameter records as BC6H mode-10 blocks:
  * the step bcf_train_export applies to a trainer's features, for any array
  * of records (with bcf_encode_mode10 in front, a complete mode-10

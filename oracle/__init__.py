@@ -153,6 +153,12 @@ def lib():
         L.oracle_encode_mode10_block.argtypes = [c_void_p, c_void_p, POINTER(c_int), POINTER(c_float), c_void_p]
         L.oracle_encode_mode10_texture.restype = None
         L.oracle_encode_mode10_texture.argtypes = [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]
+        L.oracle_encode_mode11_block.restype = None
+        L.oracle_encode_mode11_block.argtypes = [c_void_p, c_void_p, c_void_p, POINTER(c_float)]
+        L.oracle_compress_bc6h_block.restype = None
+        L.oracle_compress_bc6h_block.argtypes = [c_void_p, c_void_p, POINTER(c_float), POINTER(c_int)]
+        L.oracle_compress_bc6h_texture.restype = None
+        L.oracle_compress_bc6h_texture.argtypes = [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]
         L.oracle_adam.restype = None
         L.oracle_adam.argtypes = [c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_double, c_double, c_double,
                                   c_double, c_double, c_double, c_double]
@@ -557,3 +563,36 @@ def encode_mode10_texture(texels: np.ndarray, res: int, levels: int) -> tuple[np
     err = np.zeros(nb, np.float32)
     lib().oracle_encode_mode10_texture(_ptr(texels), int(res), int(levels), _ptr(params), _ptr(part), _ptr(err))
     return params, part, err
+
+
+def encode_mode11_block(v: np.ndarray) -> tuple[np.ndarray, np.ndarray, float]:
+    """Mode-11 encoding of one 4x4 block of RGB targets (v[16][3]): endpoints e[2][3] (10-bit codes, segment
+    start and end), indices [16] (4-bit), total squared error."""
+    v = np.ascontiguousarray(v, dtype=np.float32).reshape(48)
+    e = np.zeros((2, 3), np.int32)
+    idx = np.zeros(16, np.int32)
+    err = ctypes.c_float(0.0)
+    lib().oracle_encode_mode11_block(_ptr(v), _ptr(e), _ptr(idx), ctypes.byref(err))
+    return e, idx, float(err.value)
+
+
+def compress_bc6h_block(v: np.ndarray) -> tuple[np.ndarray, float, int]:
+    """The two-mode (10 / 11) BC6H UF16 compression of one block: (16 bytes, error, mode)."""
+    v = np.ascontiguousarray(v, dtype=np.float32).reshape(48)
+    blk = np.zeros(16, np.uint8)
+    err = ctypes.c_float(0.0)
+    mode = ctypes.c_int(0)
+    lib().oracle_compress_bc6h_block(_ptr(v), _ptr(blk), ctypes.byref(err), ctypes.byref(mode))
+    return blk, float(err.value), int(mode.value)
+
+
+def compress_bc6h_texture(texels: np.ndarray, res: int, levels: int) -> tuple[np.ndarray, np.ndarray, np.ndarray]:
+    """The two-mode compression of a mipmapped RGB texture (layout as encode_mode10_texture): blocks
+    [blocks][16] uint8, errors [blocks], modes [blocks] (10 or 11)."""
+    texels = np.ascontiguousarray(texels, dtype=np.float32).reshape(-1)
+    nb = texture_blocks(res, levels)
+    blocks = np.zeros((nb, 16), np.uint8)
+    err = np.zeros(nb, np.float32)
+    modes = np.zeros(nb, np.uint8)
+    lib().oracle_compress_bc6h_texture(_ptr(texels), int(res), int(levels), _ptr(blocks), _ptr(err), _ptr(modes))
+    return blocks, err, modes

@@ -11,8 +11,8 @@
  * here, in its own notation, from the public format definition.
  *
  * Arithmetic: FP64 for every floating-point step, integers for the BC6H
- * bitstream, which the format defines exactly -- except the mode-10 block
- * encoder (partition selection), whose every floating-point quantity decides
+ * bitstream, which the format defines exactly -- except the block encoders
+ * (partition and mode selection), whose every floating-point quantity decides
  * an integer and is computed in IEEE single precision in a fixed order, the
  * precision of the GPU encoder (see its section).
  *
@@ -39,7 +39,11 @@
  *   - BC6H mode-10 block encoder for partition selection and the initial
  *     block parameters (Sec. 5.1: compress unconstrained features with the
  *     BC6 algorithm): per-partition principal-axis line fit, 6-bit / 3-bit
- *     quantisation, minimum-error partition.
+ *     quantisation, minimum-error partition; and a plain two-mode BC6H
+ *     compressor (that mode-10 encoding against a one-region mode-11 fit
+ *     with 10-bit endpoints and 4-bit indices, the smaller error kept) that
+ *     stores a material's channels directly, the comparison without the
+ *     network.
  *
  * Parity unpinned: the bicubic kernel choice (Catmull-Rom) for the
  * reference sampling and the LOD-input convention are readings of text the
@@ -1542,13 +1546,25 @@ static int enc_quantise(float y)
     return q < 0.0f ? 0 : (q > 63.0f ? 63 : (int)q);
 }
 
-/* line fit of one region of partition k; e[0] = segment start, e[1] = segment end (6-bit, RGB) */
-static void enc_fit_region(const float y[16][3], int k, int r, int e[2][3])
+/* 10-bit endpoints (mode 11): the inverse of unquantise 64 e + 32 and finish x 31/64 */
+static int enc_quantise10(float y)
+{
+    const float scale = 64.0f / 31.0f;
+    float q = rintf((y * scale - 32.0f) / 64.0f);
+    return q < 0.0f ? 0 : (q > 1023.0f ? 1023 : (int)q);
+}
+
+/* texel t belongs to the fitted set: region r of partition k, or every texel when k < 0 */
+static int enc_member(int k, int r, int t) { return k < 0 ? 1 : oracle_bc6h_partition_region(k, t) == r; }
+
+/* line fit of one region of partition k (k < 0: all sixteen texels): the segment A (start) .. B (end)
+ * between the extreme projections on the principal axis, in the interpolation domain */
+static void enc_fit_segment(const float y[16][3], int k, int r, float A[3], float B[3])
 {
     float sum[3] = {0.0f, 0.0f, 0.0f};
     int n = 0;
     for (int t = 0; t < 16; ++t)
-        if (oracle_bc6h_partition_region(k, t) == r) {
+        if (enc_member(k, r, t)) {
             for (int c = 0; c < 3; ++c)
                 sum[c] = sum[c] + y[t][c];
             ++n;
@@ -1558,7 +1574,7 @@ static void enc_fit_region(const float y[16][3], int k, int r, int e[2][3])
         m[c] = n ? sum[c] / (float)n : 0.0f;
     float C[3][3] = {{0.0f}};
     for (int t = 0; t < 16; ++t)
-        if (oracle_bc6h_partition_region(k, t) == r) {
+        if (enc_member(k, r, t)) {
             float d[3];
             for (int c = 0; c < 3; ++c)
                 d[c] = y[t][c] - m[c];
@@ -1576,7 +1592,6 @@ static void enc_fit_region(const float y[16][3], int k, int r, int e[2][3])
         jm = 1;
     if (C[2][2] > C[jm][jm])
         jm = 2;
-    float A[3], B[3];
     if (C[jm][jm] > 0.0f) {
         float a[3] = {C[0][jm], C[1][jm], C[2][jm]};
         for (int it = 0; it < 8; ++it) {
@@ -1599,7 +1614,7 @@ static void enc_fit_region(const float y[16][3], int k, int r, int e[2][3])
         float aa = (q0 + q1) + q2;
         float pmin = INFINITY, pmax = -INFINITY;
         for (int t = 0; t < 16; ++t)
-            if (oracle_bc6h_partition_region(k, t) == r) {
+            if (enc_member(k, r, t)) {
                 float d0 = y[t][0] - m[0], d1 = y[t][1] - m[1], d2 = y[t][2] - m[2];
                 float p0 = d0 * a[0], p1 = d1 * a[1], p2 = d2 * a[2];
                 float p = (p0 + p1) + p2;
@@ -1618,6 +1633,13 @@ static void enc_fit_region(const float y[16][3], int k, int r, int e[2][3])
         for (int c = 0; c < 3; ++c)
             A[c] = B[c] = m[c];
     }
+}
+
+/* line fit of one region of partition k quantised to 6-bit endpoints: e[0] = segment start, e[1] = end */
+static void enc_fit_region(const float y[16][3], int k, int r, int e[2][3])
+{
+    float A[3], B[3];
+    enc_fit_segment(y, k, r, A, B);
     for (int c = 0; c < 3; ++c) {
         e[0][c] = enc_quantise(A[c]);
         e[1][c] = enc_quantise(B[c]);
@@ -1683,6 +1705,106 @@ void oracle_encode_mode10_block(const float *v, double params[28], int *k_out, f
     for (int t = 0; t < 16; ++t)
         params[12 + t] = best_idx[t] / 7.0;
     *k_out = best_k;
+}
+
+/* Encode one block in mode 11 (one region, 10-bit endpoints, 4-bit indices): the line fit over all sixteen
+ * texels, its ends quantised to 10 bits, each texel the index of the smallest squared RGB error (ties: the
+ * smaller index).  e[0] / e[1] = segment start / end (RGB), idx[16], the total error in *err_out. */
+void oracle_encode_mode11_block(const float *v, int e[2][3], int idx[16], float *err_out)
+{
+    float y[16][3];
+    for (int t = 0; t < 16; ++t)
+        for (int c = 0; c < 3; ++c)
+            y[t][c] = enc_coord(v[3 * t + c]);
+    float A[3], B[3];
+    enc_fit_segment(y, -1, 0, A, B);
+    for (int c = 0; c < 3; ++c) {
+        e[0][c] = enc_quantise10(A[c]);
+        e[1][c] = enc_quantise10(B[c]);
+    }
+    float total = 0.0f;
+    for (int t = 0; t < 16; ++t) {
+        float be = INFINITY;
+        int bi = 0;
+        for (int i = 0; i < 16; ++i) {
+            float d[3];
+            for (int c = 0; c < 3; ++c) {
+                int ua = bc6h_unquantize(e[0][c], 10, 0), ub = bc6h_unquantize(e[1][c], 10, 0);
+                int w = k_weights4[i];
+                d[c] = (float)oracle_half_to_double(bc6h_finish(floor_div64(ua * (64 - w) + ub * w + 32), 0)) -
+                       v[3 * t + c];
+            }
+            float q0 = d[0] * d[0], q1 = d[1] * d[1], q2 = d[2] * d[2];
+            float err = (q0 + q1) + q2;
+            if (err < be) {
+                be = err;
+                bi = i;
+            }
+        }
+        idx[t] = bi;
+        total = total + be;
+    }
+    *err_out = total;
+}
+
+/* A plain two-mode BC6H UF16 compressor of one block: the mode-10 encoding above (written by the mode-10
+ * export) against the mode-11 encoding; the smaller total error wins (a NaN total counts as infinite; ties
+ * and two NaN totals: mode 10).  blk[16], the written block's error and mode (10 or 11). */
+void oracle_compress_bc6h_block(const float *v, uint8_t blk[16], float *err_out, int *mode_out)
+{
+    double params[28];
+    int k;
+    float err10, err11;
+    oracle_encode_mode10_block(v, params, &k, &err10, NULL);
+    int e[2][3], idx[16];
+    oracle_encode_mode11_block(v, e, idx, &err11);
+    float key10 = isnan(err10) ? INFINITY : err10, key11 = isnan(err11) ? INFINITY : err11;
+    if (!(key11 < key10)) {
+        oracle_train_export_block_v(params, k, 0, blk);
+        *err_out = err10;
+        *mode_out = 10;
+        return;
+    }
+    if (idx[0] >= 8) { /* the anchor index must fit 3 bits: swap the endpoints, mirror the indices */
+        for (int c = 0; c < 3; ++c) {
+            int tmp = e[0][c];
+            e[0][c] = e[1][c];
+            e[1][c] = tmp;
+        }
+        for (int t = 0; t < 16; ++t)
+            idx[t] = 15 - idx[t];
+    }
+    int raw[12] = {0};
+    for (int c = 0; c < 3; ++c) {
+        raw[c] = e[0][c];
+        raw[3 + c] = e[1][c];
+    }
+    oracle_bc6h_encode_fields(11, raw, 0, idx, blk);
+    *err_out = err11;
+    *mode_out = 11;
+}
+
+/* The compressor over a mipmapped texture (layout as oracle_encode_mode10_texture): blocks[blocks][16],
+ * err[blocks], modes[blocks]. */
+void oracle_compress_bc6h_texture(const float *texels, int res, int levels, uint8_t *blocks, float *err,
+                                  uint8_t *modes)
+{
+    int64_t toff = 0, b = 0;
+    for (int l = 0; l < levels; ++l) {
+        int W = res >> l, wb = W / 4;
+        for (int by = 0; by < wb; ++by)
+            for (int bx = 0; bx < wb; ++bx, ++b) {
+                float v[48];
+                for (int j = 0; j < 4; ++j)
+                    for (int i = 0; i < 4; ++i)
+                        for (int c = 0; c < 3; ++c)
+                            v[3 * (4 * j + i) + c] = texels[toff + ((int64_t)(4 * by + j) * W + (4 * bx + i)) * 3 + c];
+                int mode;
+                oracle_compress_bc6h_block(v, blocks + 16 * b, err + b, &mode);
+                modes[b] = (uint8_t)mode;
+            }
+        toff += (int64_t)W * W * 3;
+    }
 }
 
 /* Encode a mipmapped texture: texels[level][W][W][3] (levels concatenated from level 0), blocks in the

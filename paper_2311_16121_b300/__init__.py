@@ -116,6 +116,8 @@ def lib() -> ctypes.CDLL:
                                                c_void_p, c_int64, c_void_p]
         L.bcf_encode_mode10.restype = c_int
         L.bcf_encode_mode10.argtypes = [c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]
+        L.bcf_compress_bc6h.restype = c_int
+        L.bcf_compress_bc6h.argtypes = [c_void_p, c_int32, c_int32, c_int32, c_void_p, c_void_p, c_void_p, c_void_p]
         L.bcf_pack_mode10.restype = c_int
         L.bcf_pack_mode10.argtypes = [c_void_p, c_void_p, c_int64, c_int32, c_void_p, c_void_p]
         L.bcf_device_check.restype = c_int
@@ -190,6 +192,22 @@ def encode_mode10(texels: torch.Tensor, res: int, levels: int, params: torch.Ten
     _check(lib().bcf_encode_mode10(_ptr(texels), int(texel_stride), int(res), int(levels), _ptr(params), _ptr(partitions),
                                    _ptr(errors), _stream()), "bcf_encode_mode10")
     return params, partitions, errors
+
+
+def compress_bc6h(texels: torch.Tensor, res: int, levels: int, texel_stride: int = 3):
+    """bcf_compress_bc6h: RGB texels (levels concatenated, float32) -> BC6H UF16 blocks uint8 [blocks * 16] (the
+    better of a mode-10 and a mode-11 encoding per block), squared errors [blocks] and modes [blocks] (10 / 11)."""
+    nb = texture_blocks(res, levels)
+    n_tex = sum(texel_stride * (res >> l) ** 2 for l in range(levels))
+    if texels.dtype != torch.float32 or texels.numel() < n_tex:
+        raise ValueError(f"compress_bc6h: texels must be float32 with at least {n_tex} values")
+    dev = texels.device
+    blocks = torch.empty(nb * 16, dtype=torch.uint8, device=dev)
+    errors = torch.empty(nb, dtype=torch.float32, device=dev)
+    modes = torch.empty(nb, dtype=torch.uint8, device=dev)
+    _check(lib().bcf_compress_bc6h(_ptr(texels), int(texel_stride), int(res), int(levels), _ptr(blocks),
+                                   _ptr(errors), _ptr(modes), _stream()), "bcf_compress_bc6h")
+    return blocks, errors, modes
 
 
 def pack_mode10(params: torch.Tensor, partitions: torch.Tensor, is_signed: bool = False) -> torch.Tensor:

@@ -467,6 +467,26 @@ bcf_status bcf_encode_mode10(const float *d_texels, int32_t texel_stride, int32_
                        "bcf_encode_mode10 launch");
 }
 
+bcf_status bcf_compress_bc6h(const float *d_texels, int32_t texel_stride, int32_t res, int32_t levels,
+                             void *d_blocks, float *d_errors, uint8_t *d_modes, bcf_stream stream)
+{
+    if (texel_stride != 3 && texel_stride != 4)
+        return fail(BCF_ERR_INVALID_ARG, "bcf_compress_bc6h: texel_stride %d is not 3 or 4", texel_stride);
+    if (!is_pow2(res) || res < 4 || res > 32768)
+        return fail(BCF_ERR_INVALID_ARG, "bcf_compress_bc6h: res %d is not a power of two in [4, 32768]", res);
+    if (levels < 1 || levels > ilog2(res) - 1)
+        return fail(BCF_ERR_INVALID_ARG, "bcf_compress_bc6h: levels %d not in [1, %d]", levels, ilog2(res) - 1);
+    if (!d_texels || !d_blocks || !aligned(d_texels, 4) || !aligned(d_blocks, 16) ||
+        (d_errors && !aligned(d_errors, 4)))
+        return fail(BCF_ERR_INVALID_ARG, "bcf_compress_bc6h: null or misaligned pointer");
+    int64_t nb = 0;
+    for (int l = 0; l < levels; ++l)
+        nb += (int64_t)((res >> l) / 4) * ((res >> l) / 4);
+    return cuda_status(launch_compress_bc6h(d_texels, texel_stride, res, levels, nb, d_blocks, d_errors, d_modes,
+                                            (cudaStream_t)stream),
+                       "bcf_compress_bc6h launch");
+}
+
 // ------------------------------------------------------------ material sets
 
 } // extern "C"

@@ -1,8 +1,12 @@
-// bcf_encode.cu -- BC6H mode-10 block encoder: partition selection and the
-// initial block parameters from free per-texel features (Sec. 5.1: the
-// unconstrained features of a short first training stage are compressed with
-// the BC6 algorithm, which fixes each block's partition and initialises its
-// endpoints and indices).
+// bcf_encode.cu -- BC6H block encoders of RGB textures.
+//
+// k_encode_mode10: partition selection and the initial block parameters from
+// free per-texel features (Sec. 5.1: the unconstrained features of a short
+// first training stage are compressed with the BC6 algorithm, which fixes
+// each block's partition and initialises its endpoints and indices).
+// k_compress_bc6h: the same mode-10 search against a mode-11 candidate, the
+// better one written as a BC6H block -- a plain texture compressor, used to
+// store a material's channels directly (the material without the network).
 //
 // One warp per block, one lane per partition k = 0..31.  Each lane fits a
 // line to each of its two regions in the format's interpolation domain (the
@@ -12,16 +16,19 @@
 // segment ends are quantised to 6-bit endpoints (inverting unquantise
 // 1024 e + 512 and finish x 31/64), each texel takes the 3-bit index whose
 // decoded value is closest (squared RGB error in value space), and the warp
-// keeps the partition with the smallest total error (ties: smaller k).
+// keeps the partition with the smallest total error (ties: smaller k).  The
+// mode-11 candidate fits one line to all sixteen texels, quantises its ends
+// to 10 bits (unquantise 64 e + 32) and picks 4-bit indices the same way.
 //
 // Every floating-point quantity here decides an integer (an endpoint, an
-// index, the partition), so it is computed in IEEE single precision with
-// explicitly rounded operations in one fixed order -- no contraction into
-// fused multiply-adds -- which makes the choice reproducible and independent
-// of compiler scheduling.
+// index, the partition, the mode), so it is computed in IEEE single
+// precision with explicitly rounded operations in one fixed order -- no
+// contraction into fused multiply-adds -- which makes the choice
+// reproducible and independent of compiler scheduling.
 #include <cuda_fp16.h>
 #include <math.h>
 
+#include "bc6h_pack.cuh"
 #include "bc6h_unpack.cuh"
 #include "bcf_kernels.h"
 
@@ -47,21 +54,31 @@ __device__ __forceinline__ float enc_coord(float v)
 
 __device__ __forceinline__ int unq6(int e) { return e == 0 ? 0 : (e == 63 ? 0xFFFF : (e << 10) + 512); }
 
-// decoded value of a mode-10 channel from the unquantised endpoints and weight w
-__device__ __forceinline__ float mode10_value(int ua, int ub, int w)
+// decoded UF16 value of a channel (modes 10 and 11) from the unquantised endpoints and weight w
+__device__ __forceinline__ float texel_value(int ua, int ub, int w)
 {
     const int yi = (ua * (64 - w) + ub * w + 32) >> 6;
     return __half2float(__ushort_as_half((unsigned short)((yi * 31) >> 6)));
 }
 
-__device__ __forceinline__ int enc_quantise(float y)
+__device__ __forceinline__ int enc_quantise6(float y)
 {
     const float q = rintf(fdiv(fsub(fmul(y, 64.0f / 31.0f), 512.0f), 1024.0f));
     return q < 0.0f ? 0 : (q > 63.0f ? 63 : (int)q);
 }
 
-// line fit of region r of the partition with texel mask pm (bit t set: texel t in region 1)
-__device__ void fit_region(const float *y, uint32_t pm, int r, int e[2][3])
+// 10-bit endpoints (mode 11): unquantise 64 e + 32, finish x 31/64
+__device__ __forceinline__ int unq10(int e) { return e == 0 ? 0 : (e == 1023 ? 0xFFFF : (e << 6) + 32); }
+
+__device__ __forceinline__ int enc_quantise10(float y)
+{
+    const float q = rintf(fdiv(fsub(fmul(y, 64.0f / 31.0f), 32.0f), 64.0f));
+    return q < 0.0f ? 0 : (q > 1023.0f ? 1023 : (int)q);
+}
+
+// Line fit of region r of the partition with texel mask pm (bit t set: texel t in region 1; pm = 0, r = 0: all
+// sixteen texels): the segment [A, B] between the extreme projections on the principal axis.
+__device__ void fit_segment(const float *y, uint32_t pm, int r, float A[3], float B[3])
 {
     float sum[3] = {0.0f, 0.0f, 0.0f};
     int n = 0;
@@ -93,7 +110,6 @@ __device__ void fit_region(const float *y, uint32_t pm, int r, int e[2][3])
         jm = 1;
     if (C[2][2] > C[jm][jm])
         jm = 2;
-    float A[3], B[3];
     if (C[jm][jm] > 0.0f) {
         float a[3] = {C[0][jm], C[1][jm], C[2][jm]};
         for (int it = 0; it < 8; ++it) {
@@ -134,23 +150,88 @@ __device__ void fit_region(const float *y, uint32_t pm, int r, int e[2][3])
         for (int c = 0; c < 3; ++c)
             A[c] = B[c] = m[c];
     }
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        e[0][c] = enc_quantise(A[c]);
-        e[1][c] = enc_quantise(B[c]);
-    }
 }
 
-__global__ void __launch_bounds__(32 * kEncWarps) k_encode_mode10(const float *__restrict__ texels, int stride, int res, int levels,
-                                                                 int64_t nblocks, float *__restrict__ params,
-                                                                 uint8_t *__restrict__ part, float *__restrict__ err)
+// squared RGB error (value space) of texel target v[0..2] against the value of weight w between ua and ub
+__device__ __forceinline__ float texel_error(const int ua[3], const int ub[3], int w, const float *v)
 {
-    __shared__ float sv[kEncWarps][48], sy[kEncWarps][48];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t b = (int64_t)blockIdx.x * kEncWarps + warp;
-    if (b >= nblocks) // warp-uniform
-        return;
-    // the block's level and position; texel offset of the level
+    float q[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float d = fsub(texel_value(ua[c], ub[c], w), v[c]);
+        q[c] = fmul(d, d);
+    }
+    return fadd(fadd(q[0], q[1]), q[2]);
+}
+
+// Mode-10 candidate of partition k (one lane): 6-bit endpoints e[region][end][c], 3-bit indices (texels 0-7 in
+// idx_lo, 8-15 in idx_hi), total squared error.
+__device__ float mode10_candidate(const float *v, const float *y, int k, int e[2][2][3], uint32_t &idx_lo,
+                                  uint32_t &idx_hi)
+{
+    const uint32_t pm = partition_mask(k);
+    int ua[2][3], ub[2][3];
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        float A[3], B[3];
+        fit_segment(y, pm, r, A, B);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            e[r][0][c] = enc_quantise6(A[c]);
+            e[r][1][c] = enc_quantise6(B[c]);
+            ua[r][c] = unq6(e[r][0][c]);
+            ub[r][c] = unq6(e[r][1][c]);
+        }
+    }
+    float total = 0.0f;
+    idx_lo = idx_hi = 0;
+    for (int t = 0; t < 16; ++t) {
+        const int r = (int)((pm >> t) & 1);
+        float be = INFINITY;
+        int bi = 0;
+        for (int i = 0; i < 8; ++i) {
+            const float er = texel_error(r ? ua[1] : ua[0], r ? ub[1] : ub[0], weight3(i), v + 3 * t);
+            if (er < be) {
+                be = er;
+                bi = i;
+            }
+        }
+        if (t < 8)
+            idx_lo |= (uint32_t)bi << (3 * t);
+        else
+            idx_hi |= (uint32_t)bi << (3 * (t - 8));
+        total = fadd(total, be);
+    }
+    return total;
+}
+
+// smallest key over the warp (a NaN total never wins over a number; ties go to the smaller k)
+__device__ __forceinline__ int warp_best_partition(float total, int k, float &key)
+{
+    key = isnan(total) ? INFINITY : total;
+    int best = k;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const float ok = __shfl_xor_sync(0xffffffffu, key, off);
+        const int obest = __shfl_xor_sync(0xffffffffu, best, off);
+        if (ok < key || (ok == key && obest < best)) {
+            key = ok;
+            best = obest;
+        }
+    }
+    return best;
+}
+
+__device__ __forceinline__ int mode10_index(uint32_t idx_lo, uint32_t idx_hi, int t)
+{
+    return t < 8 ? (int)((idx_lo >> (3 * t)) & 7) : (int)((idx_hi >> (3 * (t - 8))) & 7);
+}
+
+// The block b of a mipmapped texture: its 48 targets (v) and their interpolation-domain coordinates (y) in the
+// warp's shared rows.
+__device__ void load_block(const float *__restrict__ texels, int stride, int res, int levels, int64_t b, float *v,
+                           float *y, int lane)
+{
     int l = 0;
     int64_t boff = 0, toff = 0;
     for (; l < levels - 1; ++l) {
@@ -163,7 +244,6 @@ __global__ void __launch_bounds__(32 * kEncWarps) k_encode_mode10(const float *_
     const int W = res >> l, wb = W >> 2;
     const int64_t bl = b - boff;
     const int by = (int)(bl / wb), bx = (int)(bl % wb);
-    float *v = sv[warp], *y = sy[warp];
     for (int e = lane; e < 48; e += 32) {
         const int t = e / 3, c = e % 3;
         const float x = texels[toff + ((int64_t)(4 * by + (t >> 2)) * W + 4 * bx + (t & 3)) * stride + c];
@@ -171,59 +251,26 @@ __global__ void __launch_bounds__(32 * kEncWarps) k_encode_mode10(const float *_
         y[e] = enc_coord(x);
     }
     __syncwarp();
+}
 
+__global__ void __launch_bounds__(32 * kEncWarps) k_encode_mode10(const float *__restrict__ texels, int stride, int res,
+                                                                 int levels, int64_t nblocks,
+                                                                 float *__restrict__ params,
+                                                                 uint8_t *__restrict__ part, float *__restrict__ err)
+{
+    __shared__ float sv[kEncWarps][48], sy[kEncWarps][48];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t b = (int64_t)blockIdx.x * kEncWarps + warp;
+    if (b >= nblocks) // warp-uniform
+        return;
+    float *v = sv[warp], *y = sy[warp];
+    load_block(texels, stride, res, levels, b, v, y, lane);
     const int k = lane;
-    const uint32_t pm = partition_mask(k);
     int e[2][2][3];
-    fit_region(y, pm, 0, e[0]);
-    fit_region(y, pm, 1, e[1]);
-    int ua[2][3], ub[2][3];
-#pragma unroll
-    for (int r = 0; r < 2; ++r)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            ua[r][c] = unq6(e[r][0][c]);
-            ub[r][c] = unq6(e[r][1][c]);
-        }
-    float total = 0.0f;
-    uint32_t idx_bits = 0, idx_hi = 0; // 3 bits per texel: texels 0-7, 8-15
-    for (int t = 0; t < 16; ++t) {
-        const int r = (int)((pm >> t) & 1);
-        float be = INFINITY;
-        int bi = 0;
-        for (int i = 0; i < 8; ++i) {
-            const int w = weight3(i);
-            float q[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const float d = fsub(mode10_value(r ? ua[1][c] : ua[0][c], r ? ub[1][c] : ub[0][c], w), v[3 * t + c]);
-                q[c] = fmul(d, d);
-            }
-            const float er = fadd(fadd(q[0], q[1]), q[2]);
-            if (er < be) {
-                be = er;
-                bi = i;
-            }
-        }
-        if (t < 8)
-            idx_bits |= (uint32_t)bi << (3 * t);
-        else
-            idx_hi |= (uint32_t)bi << (3 * (t - 8));
-        total = fadd(total, be);
-    }
-    // smallest total error over the warp; a NaN total never wins over a number, ties go to the smaller k
-    float key = isnan(total) ? INFINITY : total;
-    int best = k;
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const float ok = __shfl_xor_sync(0xffffffffu, key, off);
-        const int obest = __shfl_xor_sync(0xffffffffu, best, off);
-        if (ok < key || (ok == key && obest < best)) {
-            key = ok;
-            best = obest;
-        }
-    }
-    if (k != best)
+    uint32_t idx_lo, idx_hi;
+    const float total = mode10_candidate(v, y, k, e, idx_lo, idx_hi);
+    float key;
+    if (warp_best_partition(total, k, key) != k)
         return;
     float *pr = params + b * 32;
 #pragma unroll
@@ -234,13 +281,90 @@ __global__ void __launch_bounds__(32 * kEncWarps) k_encode_mode10(const float *_
             pr[8 * r + 3 + c] = (float)e[r][1][c];
         }
     pr[6] = pr[7] = pr[14] = pr[15] = 0.0f;
-    for (int t = 0; t < 16; ++t) {
-        const int i = t < 8 ? (int)((idx_bits >> (3 * t)) & 7) : (int)((idx_hi >> (3 * (t - 8))) & 7);
-        pr[16 + t] = (float)i / 7.0f;
-    }
+    for (int t = 0; t < 16; ++t)
+        pr[16 + t] = (float)mode10_index(idx_lo, idx_hi, t) / 7.0f;
     part[b] = (uint8_t)k;
     if (err)
         err[b] = total;
+}
+
+// Two-mode compressor: the mode-10 encoding above against a mode-11 encoding (one region over all sixteen
+// texels, 10-bit endpoints, 4-bit indices); the smaller total error is written as a BC6H block (ties and NaN
+// totals: mode 10).  The mode-11 line fit runs on every lane alike; its index search takes texel lane & 15.
+__global__ void __launch_bounds__(32 * kEncWarps) k_compress_bc6h(const float *__restrict__ texels, int stride, int res,
+                                                                 int levels, int64_t nblocks, uint4 *__restrict__ out,
+                                                                 float *__restrict__ err, uint8_t *__restrict__ modes)
+{
+    __shared__ float sv[kEncWarps][48], sy[kEncWarps][48];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int64_t b = (int64_t)blockIdx.x * kEncWarps + warp;
+    if (b >= nblocks) // warp-uniform
+        return;
+    float *v = sv[warp], *y = sy[warp];
+    load_block(texels, stride, res, levels, b, v, y, lane);
+    const int k = lane;
+    int e[2][2][3];
+    uint32_t idx_lo, idx_hi;
+    const float total10 = mode10_candidate(v, y, k, e, idx_lo, idx_hi);
+    float key10;
+    const int best = warp_best_partition(total10, k, key10);
+
+    float A[3], B[3];
+    fit_segment(y, 0u, 0, A, B);
+    int e11[2][3], ua[3], ub[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        e11[0][c] = enc_quantise10(A[c]);
+        e11[1][c] = enc_quantise10(B[c]);
+        ua[c] = unq10(e11[0][c]);
+        ub[c] = unq10(e11[1][c]);
+    }
+    const int tl = lane & 15;
+    float be = INFINITY;
+    int bi = 0;
+    for (int i = 0; i < 16; ++i) {
+        const float er = texel_error(ua, ub, weight4(i), v + 3 * tl);
+        if (er < be) {
+            be = er;
+            bi = i;
+        }
+    }
+    float total11 = 0.0f;
+    int idx11[16];
+#pragma unroll
+    for (int t = 0; t < 16; ++t) { // texel order, as a sequential sum would take it
+        total11 = fadd(total11, __shfl_sync(0xffffffffu, be, t));
+        idx11[t] = __shfl_sync(0xffffffffu, bi, t);
+    }
+    const float key11 = isnan(total11) ? INFINITY : total11;
+    if (key11 < key10) {
+        if (lane == 0) {
+            out[b] = bc6h_pack_mode11(e11, idx11);
+            if (err)
+                err[b] = total11;
+            if (modes)
+                modes[b] = 11;
+        }
+        return;
+    }
+    if (k != best)
+        return;
+    int q[4][3], idx[16];
+#pragma unroll
+    for (int r = 0; r < 2; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            q[2 * r][c] = e[r][0][c];
+            q[2 * r + 1][c] = e[r][1][c];
+        }
+#pragma unroll
+    for (int t = 0; t < 16; ++t)
+        idx[t] = mode10_index(idx_lo, idx_hi, t);
+    out[b] = bc6h_pack_mode10(q, idx, k);
+    if (err)
+        err[b] = total10;
+    if (modes)
+        modes[b] = 10;
 }
 
 } // namespace
@@ -253,6 +377,21 @@ cudaError_t launch_encode_mode10(const float *texels, int stride, int res, int l
     const int64_t grid = (nblocks + kEncWarps - 1) / kEncWarps;
     k_encode_mode10<<<(unsigned)grid, 32 * kEncWarps, 0, st>>>(texels, stride, res, levels, nblocks, params, part,
                                                               err);
+    return cudaGetLastError();
+}
+
+} // namespace bcf
+
+namespace bcf {
+
+cudaError_t launch_compress_bc6h(const float *texels, int stride, int res, int levels, int64_t nblocks, void *out,
+                                 float *err, uint8_t *modes, cudaStream_t st)
+{
+    if (nblocks <= 0)
+        return cudaSuccess;
+    const int64_t grid = (nblocks + kEncWarps - 1) / kEncWarps;
+    k_compress_bc6h<<<(unsigned)grid, 32 * kEncWarps, 0, st>>>(texels, stride, res, levels, nblocks, (uint4 *)out,
+                                                              err, modes);
     return cudaGetLastError();
 }
 

@@ -9,6 +9,8 @@ namespace bcf {
 
 cudaError_t launch_encode_mode10(const float *texels, int stride, int res, int levels, int64_t nblocks,
                                  float *params, uint8_t *part, float *err, cudaStream_t st);
+cudaError_t launch_compress_bc6h(const float *texels, int stride, int res, int levels, int64_t nblocks, void *out,
+                                 float *err, uint8_t *modes, cudaStream_t st);
 cudaError_t launch_decode_fp32_texunit(const MaterialDev &M, const TexUnitObjs &T, const float *u, const float *v,
                                        const float *s, int64_t n, void *out, int out_fp16, cudaStream_t st);
 bool set_tex_supported(const MaterialDev &M0);

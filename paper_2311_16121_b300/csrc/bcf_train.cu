@@ -19,6 +19,7 @@
 #include <math.h>
 #include <string.h>
 
+#include "bc6h_pack.cuh"
 #include "bc6h_unpack.cuh"
 #include "bcf_kernels.h"
 #include "bcf_train.h"
@@ -366,22 +367,6 @@ __global__ void __launch_bounds__(256) k_adam(AdamArgs A)
 
 // ---------------------------------------------------------------- export
 
-// BC6H mode 10 writer (the field order the decoder reads back).
-struct BitWriter {
-    uint64_t lo = 0, hi = 0;
-    int pos = 0;
-    __device__ void put(uint32_t v, int lsb, int n)
-    {
-        for (int j = 0; j < n; ++j, ++pos) {
-            const uint64_t bit = (v >> (lsb + j)) & 1u;
-            if (pos < 64)
-                lo |= bit << pos;
-            else
-                hi |= bit << (pos - 64);
-        }
-    }
-};
-
 __global__ void k_export_blocks(const float *__restrict__ params, const uint8_t *__restrict__ part, int64_t nblocks,
                                 int is_signed, unsigned *__restrict__ check, uint4 *__restrict__ out)
 {
@@ -405,36 +390,7 @@ __global__ void k_export_blocks(const float *__restrict__ params, const uint8_t 
 #pragma unroll
     for (int t = 0; t < 16; ++t)
         idx[t] = (int)rintf(7.0f * fminf(fmaxf(p[16 + t], 0.0f), 1.0f));
-    const uint32_t pm = partition_mask(k);
-    const int anchors[2] = {0, anchor2_of(k)};
-#pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        if (idx[anchors[r]] >= 4) { // the anchor index must fit 2 bits: swap the region's endpoints
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const int tmp = q[2 * r][c];
-                q[2 * r][c] = q[2 * r + 1][c];
-                q[2 * r + 1][c] = tmp;
-            }
-#pragma unroll
-            for (int t = 0; t < 16; ++t)
-                if ((int)((pm >> t) & 1) == r)
-                    idx[t] = 7 - idx[t];
-        }
-    }
-    const uint32_t r0 = q[0][0], g0 = q[0][1], b0 = q[0][2], r1 = q[1][0], g1 = q[1][1], b1 = q[1][2];
-    const uint32_t r2 = q[2][0], g2 = q[2][1], b2 = q[2][2], r3 = q[3][0], g3 = q[3][1], b3 = q[3][2];
-    BitWriter w;
-    w.put(30u, 0, 5); // mode field 11110
-    w.put(r0, 0, 6); w.put(g3, 4, 1); w.put(b3, 0, 1); w.put(b3, 1, 1); w.put(b2, 4, 1);
-    w.put(g0, 0, 6); w.put(g2, 5, 1); w.put(b2, 5, 1); w.put(b3, 2, 1); w.put(g2, 4, 1);
-    w.put(b0, 0, 6); w.put(g3, 5, 1); w.put(b3, 3, 1); w.put(b3, 5, 1); w.put(b3, 4, 1);
-    w.put(r1, 0, 6); w.put(g2, 0, 4); w.put(g1, 0, 6); w.put(g3, 0, 4); w.put(b1, 0, 6);
-    w.put(b2, 0, 4); w.put(r2, 0, 6); w.put(r3, 0, 6); w.put((uint32_t)k, 0, 5);
-#pragma unroll
-    for (int t = 0; t < 16; ++t)
-        w.put((uint32_t)idx[t], 0, (t == 0 || t == anchors[1]) ? 2 : 3);
-    out[b] = make_uint4((uint32_t)w.lo, (uint32_t)(w.lo >> 32), (uint32_t)w.hi, (uint32_t)(w.hi >> 32));
+    out[b] = bc6h_pack_mode10(q, idx, k);
 }
 
 __global__ void k_export_weights(const float *__restrict__ W, int64_t n, uint16_t *__restrict__ out)

@@ -23,7 +23,7 @@ from dataclasses import dataclass, field
 import numpy as np
 import torch
 
-from . import Material, Trainer, encode_mode10, pack_mode10, texture_blocks
+from . import Material, Trainer, compress_bc6h, encode_mode10, pack_mode10, texture_blocks
 from . import workloads as wl
 
 
@@ -139,11 +139,12 @@ def material_bytes(res: list[int], levels: list[int]) -> int:
     return sum(16 * texture_blocks(r, l) for r, l in zip(res, levels))
 
 
-def classic_bc6h(w: wl.TrainWorkload, res: int, eval_queries: int = 1 << 22):
+def classic_bc6h(w: wl.TrainWorkload, res: int, eval_queries: int = 1 << 22, modes: tuple[int, ...] = (10, 11)):
     """The material without the network: the nine reference channels compressed directly as three BC6H
     textures -- albedo, the normal stored as n / 2 + 1 / 2 (the unsigned format holds no negative values),
     roughness / metalness / AO -- at `res` (at most the reference's resolution) with the reference's own box
-    mips from that size down, each compressed by bcf_encode_mode10 + bcf_pack_mode10.  They are decoded by
+    mips from that size down, each compressed by bcf_compress_bc6h (per block the better of a mode-10 and a
+    mode-11 encoding; modes=(10,) keeps mode 10 alone, the features' own mode).  They are decoded by
     the decode path (BC6H unpack, trilinear filtering at the query LOD) with a single linear output layer that
     undoes the normal encoding, and scored with the same PSNR as the trained materials.
     Returns (PSNR, per-level PSNRs, bytes)."""
@@ -158,8 +159,11 @@ def classic_bc6h(w: wl.TrainWorkload, res: int, eval_queries: int = 1 << 22):
     blocks = []
     for t in range(3):
         tex = torch.from_numpy(np.ascontiguousarray(ref[:, 3 * t:3 * t + 3])).to(dev)
-        params, parts, _ = encode_mode10(tex.reshape(-1), res, levels)
-        blocks.append(pack_mode10(params, parts))
+        if tuple(modes) == (10,):
+            params, parts, _ = encode_mode10(tex.reshape(-1), res, levels)
+            blocks.append(pack_mode10(params, parts))
+        else:
+            blocks.append(compress_bc6h(tex.reshape(-1), res, levels)[0])
     Wm = torch.eye(9, device=dev)
     bm = torch.zeros(9, device=dev)
     Wm[3:6, 3:6] *= 2.0

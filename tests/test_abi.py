@@ -87,3 +87,20 @@ def test_encoder_host_validation():
     assert L.bcf_encode_mode10(4098, 3, 64, 4, 4096, 4096, None, None) == 1  # misaligned texels
     assert b"misaligned" in L.bcf_last_error()
     assert bcf.texture_blocks(64, 4) == 256 + 64 + 16 + 4
+
+
+def test_compressor_and_packer_host_validation():
+    _, L = _lib()
+    L.bcf_compress_bc6h.argtypes = [ctypes.c_void_p, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
+                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]
+    assert L.bcf_compress_bc6h(4096, 3, 48, 1, 4096, None, None, None) == 1  # not a power of two
+    assert L.bcf_compress_bc6h(4096, 3, 64, 6, 4096, None, None, None) == 1  # too many levels
+    assert L.bcf_compress_bc6h(4096, 2, 64, 4, 4096, None, None, None) == 1  # texel stride
+    assert L.bcf_compress_bc6h(4096, 3, 64, 4, 4104, None, None, None) == 1  # blocks not 16-byte aligned
+    assert b"misaligned" in L.bcf_last_error()
+    L.bcf_pack_mode10.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32,
+                                  ctypes.c_void_p, ctypes.c_void_p]
+    assert L.bcf_pack_mode10(4096, 4096, -1, 0, 4096, None) == 1
+    assert L.bcf_pack_mode10(4096, 4096, 0, 0, None, None) == 0  # nothing to do
+    assert L.bcf_pack_mode10(4100, 4096, 8, 0, 4096, None) == 1  # params not 16-byte aligned
+    assert L.bcf_pack_mode10(4096, None, 8, 0, 4096, None) == 1  # no partitions

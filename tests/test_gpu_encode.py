@@ -181,3 +181,67 @@ def test_encode_then_pack_is_a_mode10_compressor():
         np.testing.assert_allclose(sq.astype(np.float64).sum(1), e, rtol=1e-5, atol=1e-9)
         off_b += nb
         off_t += W * W * 3
+
+
+def _mode11_level(rng, W):
+    """Every block a mode-11 lattice block (the compressor reproduces them exactly, in mode 11)."""
+    out = np.zeros((W, W, 3), np.float32)
+    for by in range(W // 4):
+        for bx in range(W // 4):
+            while True:
+                e = rng.integers(0, 1024, (2, 3))
+                if np.abs(e[0] - e[1]).max() >= 64:
+                    break
+            idx = rng.integers(0, 16, 16)
+            idx[0] = rng.integers(0, 8)
+            i0, i1 = rng.choice(np.arange(1, 16), 2, replace=False)
+            idx[i0], idx[i1] = 0, 15
+            blk = oracle.bc6h_encode_fields(11, [int(x) for x in e.reshape(-1)] + [0] * 6, 0, [int(i) for i in idx])
+            _, tex = oracle.bc6h_decode_block(blk)
+            vals = np.array([[oracle.half_to_double(int(tex[t, c])) for c in range(3)] for t in range(16)])
+            out[4 * by:4 * by + 4, 4 * bx:4 * bx + 4] = vals.reshape(4, 4, 3)
+    return out
+
+
+@pytest.mark.parametrize("kinds", [("noise",), ("smooth", "wide"), ("exact", "constant", "mode11")])
+def test_compressor_matches_oracle_bit_for_bit(kinds):
+    """bcf_compress_bc6h: blocks, errors and modes equal the oracle's two-mode compressor bit for bit."""
+    bcf = _bcf()
+    rng = np.random.default_rng(zlib.crc32(("c/" + "/".join(kinds)).encode()))
+    res, levels = 32, 4
+    tex = np.concatenate([(_mode11_level(rng, res >> l) if kinds[l % len(kinds)] == "mode11"
+                           else _level_texels(rng, res >> l, kinds[l % len(kinds)])).reshape(-1)
+                          for l in range(levels)])
+    blocks, err, modes = bcf.compress_bc6h(torch.from_numpy(tex).cuda(), res, levels)
+    rb, rerr, rmodes = oracle.compress_bc6h_texture(tex, res, levels)
+    np.testing.assert_array_equal(modes.cpu().numpy(), rmodes)
+    np.testing.assert_array_equal(err.cpu().numpy(), rerr)
+    np.testing.assert_array_equal(blocks.cpu().numpy().reshape(-1, 16), rb)
+    if "mode11" in kinds:  # the mode-11 lattice level is reproduced exactly, in mode 11
+        lv = kinds.index("mode11")
+        a = sum(((res >> l) // 4) ** 2 for l in range(lv))
+        b = a + ((res >> lv) // 4) ** 2
+        assert (rmodes[a:b] == 11).all() and not rerr[a:b].any()
+    assert set(np.unique(rmodes)) <= {10, 11}
+
+
+def test_compressor_output_is_a_texture_the_decoder_takes():
+    """The compressed blocks decode (bcf_decode_bc6h, every level) to values whose squared error against the
+    input is the reported error."""
+    bcf = _bcf()
+    rng = np.random.default_rng(71)
+    res, levels = 16, 3
+    tex = _texture(rng, res, levels, ("smooth", "noise"))
+    blocks, err, _ = bcf.compress_bc6h(torch.from_numpy(tex).cuda(), res, levels)
+    off_b, off_t = 0, 0
+    for lvl in range(levels):
+        W = res >> lvl
+        nb = (W // 4) ** 2
+        dec = bcf.decode_bc6h(blocks[16 * off_b:16 * (off_b + nb)], W // 4, W // 4).cpu().numpy()
+        vals = dec.view(np.float16).astype(np.float32).reshape(W, W, 3)
+        src = tex[off_t:off_t + W * W * 3].reshape(W, W, 3)
+        sq = ((vals - src) ** 2).reshape(W // 4, 4, W // 4, 4, 3).transpose(0, 2, 1, 3, 4).reshape(nb, 48)
+        np.testing.assert_allclose(sq.astype(np.float64).sum(1), err[off_b:off_b + nb].cpu().numpy(), rtol=1e-5,
+                                   atol=1e-9)
+        off_b += nb
+        off_t += W * W * 3

@@ -805,6 +805,100 @@ def test_encoder_error_is_the_decoded_error_and_indices_are_optimal():
             assert got <= best * (1 + 1e-6) + 1e-12, (b, t)
 
 
+# --------------------------------------------------------------------------- two-mode compressor (no network)
+
+def _block_values(blk):
+    """Mode and values [16][3] of a UF16 block through the format decoder."""
+    mode, tex = oracle.bc6h_decode_block(blk)
+    return mode, np.array([[oracle.half_to_double(int(tex[t, c])) for c in range(3)] for t in range(16)])
+
+
+def _mode11_lattice_block(rng):
+    """A random mode-11 block written field by field (10-bit endpoints at least 64 codes apart in some channel,
+    texel 0's index below 8 as the anchor rule requires, indices 0 and 15 both used): its decoded values."""
+    while True:
+        e = rng.integers(0, 1024, (2, 3))
+        if np.abs(e[0] - e[1]).max() >= 64:
+            break
+    idx = rng.integers(0, 16, 16)
+    idx[0] = rng.integers(0, 8)
+    i0, i1 = rng.choice(np.arange(1, 16), 2, replace=False)
+    idx[i0], idx[i1] = 0, 15
+    raw = [int(x) for x in e.reshape(-1)] + [0] * 6
+    mode, vals = _block_values(oracle.bc6h_encode_fields(11, raw, 0, [int(i) for i in idx]))
+    assert mode == 11
+    return vals
+
+
+def test_mode11_encoder_recovers_exactly_encodable_blocks():
+    """A block that is itself a mode-11 encoding is reproduced with zero error, and the compressor then writes
+    a mode-11 block that decodes to the targets bit for bit."""
+    rng = np.random.default_rng(111)
+    for b in range(64):
+        target = _mode11_lattice_block(rng).astype(np.float32)
+        e, idx, err = oracle.encode_mode11_block(target)
+        assert err == 0.0, (b, err)
+        blk, cerr, mode = oracle.compress_bc6h_block(target)
+        assert mode == 11 and cerr == 0.0
+        m, vals = _block_values(blk)
+        assert m == 11 and np.array_equal(vals, target.astype(np.float64)), b
+
+
+def test_compressor_error_is_the_decoded_error_and_the_smaller_candidate():
+    """On arbitrary targets the written block (decoded by the format decoder) has exactly the reported squared
+    error, the mode is the candidate with the smaller error (ties: mode 10), and every mode-11 index is the
+    best of the 16 for its endpoints."""
+    rng = np.random.default_rng(112)
+    y, x = np.meshgrid(np.arange(4), np.arange(4), indexing="ij")
+    seen = set()
+    for b in range(48):
+        if b % 3 == 0:
+            target = rng.random((16, 3)) * rng.choice([0.05, 1.0, 30.0])
+        else:  # smooth ramps, where the finer endpoints of mode 11 pay
+            g = rng.uniform(-0.05, 0.05, (2, 3))
+            target = rng.uniform(0.2, 0.8, 3) + x.reshape(16, 1) * g[0] + y.reshape(16, 1) * g[1]
+        target = target.astype(np.float32)
+        blk, err, mode = oracle.compress_bc6h_block(target)
+        m, vals = _block_values(blk)
+        assert m == mode
+        seen.add(mode)
+        sq = ((vals.astype(np.float32) - target) ** 2).astype(np.float32)
+        ref = np.float32(0.0)
+        for t in range(16):  # the encoder's order: (r + g) + b per texel, texels in order, single precision
+            ref = np.float32(ref + np.float32(np.float32(sq[t, 0] + sq[t, 1]) + sq[t, 2]))
+        assert err == ref, (b, err, ref)
+        _, _, e10, _ = oracle.encode_mode10_block(target)
+        e, idx, e11 = oracle.encode_mode11_block(target)
+        assert err == min(e10, e11) and mode == (11 if e11 < e10 else 10)
+        for t in range(16):  # each index is the best of 16 for the mode-11 endpoints
+            errs = []
+            for i in range(16):
+                raw = [int(v) for v in e.reshape(-1)] + [0] * 6
+                ii = [0] * 16
+                ii[t] = i
+                sw = i >= 8 and t == 0  # texel 0 is the anchor: write the mirrored form
+                if sw:
+                    raw = raw[3:6] + raw[0:3] + [0] * 6
+                    ii = [15 - j for j in ii]
+                _, v2 = _block_values(oracle.bc6h_encode_fields(11, raw, 0, ii))
+                errs.append(((v2[t] - target[t].astype(np.float64)) ** 2).sum())
+            got = ((oracle_mode11_value(e, idx[t]) - target[t].astype(np.float64)) ** 2).sum()
+            assert got <= min(errs) * (1 + 1e-6) + 1e-12, (b, t)
+    assert seen == {10, 11}
+
+
+def oracle_mode11_value(e, i):
+    """Value of index i between 10-bit endpoints e[0], e[1], through the format decoder (a block whose texel 0
+    carries the index; mirrored when the anchor rule requires)."""
+    raw = [int(v) for v in np.asarray(e).reshape(-1)] + [0] * 6
+    ii = [int(i)] + [0] * 15
+    if i >= 8:
+        raw = raw[3:6] + raw[0:3] + [0] * 6
+        ii = [15 - j for j in ii]
+    _, vals = _block_values(oracle.bc6h_encode_fields(11, raw, 0, ii))
+    return vals[0]
+
+
 # --------------------------------------------------------------------------- unconstrained features (Sec. 5.1)
 
 def _free_levels(rng, res, levels):
