@@ -153,6 +153,8 @@ def lib():
         L.oracle_encode_mode10_block.argtypes = [c_void_p, c_void_p, POINTER(c_int), POINTER(c_float), c_void_p]
         L.oracle_encode_mode10_texture.restype = None
         L.oracle_encode_mode10_texture.argtypes = [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]
+        L.oracle_train_loss_mt.restype = c_double
+        L.oracle_train_loss_mt.argtypes = [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_int]
         L.oracle_encode_mode11_block.restype = None
         L.oracle_encode_mode11_block.argtypes = [c_void_p, c_void_p, c_void_p, POINTER(c_float)]
         L.oracle_compress_bc6h_block.restype = None
@@ -472,6 +474,16 @@ def train_loss_grad(F: TrainFeatures, P: TrainMlp, T: Target, u, v, s, want_grad
     loss = lib().oracle_train_loss_grad(ctypes.byref(F.c), ctypes.byref(P.c), ctypes.byref(T.c), u.size, _ptr(u),
                                         _ptr(v), _ptr(s), int(relaxed), ctypes.byref(G) if want_grad else None)
     return loss, [g.reshape(-1, 3 if F.free else 28) for g in gf], gW, gb
+
+
+def train_loss_mt(F: TrainFeatures, P: TrainMlp, T: Target, u, v, s, threads: int | None = None) -> float:
+    """The loss of train_loss_grad without gradients, the queries split over POSIX threads (for full-size
+    batches)."""
+    u = np.ascontiguousarray(u, np.float32)
+    v = np.ascontiguousarray(v, np.float32)
+    s = np.ascontiguousarray(s, np.float32)
+    return lib().oracle_train_loss_mt(ctypes.byref(F.c), ctypes.byref(P.c), ctypes.byref(T.c), u.size, _ptr(u),
+                                      _ptr(v), _ptr(s), int(threads or os.cpu_count() or 1))
 
 
 def adam(p: np.ndarray, g: np.ndarray, m: np.ndarray, v: np.ndarray, t: int, lr0: float, gamma: float,

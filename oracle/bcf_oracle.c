@@ -1393,6 +1393,49 @@ double oracle_train_loss_grad(const oracle_train_features *F, const oracle_train
     return sum / ((double)batch * nout);
 }
 
+typedef struct {
+    const oracle_train_features *F;
+    const oracle_train_mlp *P;
+    const oracle_target *Tg;
+    int64_t q0, q1;
+    const float *u, *v, *s;
+    double sum;
+} loss_job;
+
+static void *loss_worker(void *arg)
+{
+    loss_job *J = (loss_job *)arg;
+    double sum = 0.0;
+    for (int64_t q = J->q0; q < J->q1; ++q)
+        sum += train_query(J->F, J->P, J->Tg, J->u[q], J->v[q], J->s[q], 0, 0.0, NULL);
+    J->sum = sum;
+    return NULL;
+}
+
+/* The loss alone (no gradients) over `threads` POSIX threads, each summing a contiguous range of queries;
+ * the partial sums are added in range order (the same value as the sequential loop up to that order). */
+double oracle_train_loss_mt(const oracle_train_features *F, const oracle_train_mlp *P, const oracle_target *Tg,
+                            int64_t batch, const float *u, const float *v, const float *s, int threads)
+{
+    ensure_layouts();
+    if (threads < 1)
+        threads = 1;
+    if (threads > 512)
+        threads = 512;
+    pthread_t th[512];
+    loss_job jobs[512];
+    for (int i = 0; i < threads; ++i) {
+        jobs[i] = (loss_job){F, P, Tg, batch * i / threads, batch * (i + 1) / threads, u, v, s, 0.0};
+        pthread_create(&th[i], NULL, loss_worker, &jobs[i]);
+    }
+    double sum = 0.0;
+    for (int i = 0; i < threads; ++i) {
+        pthread_join(th[i], NULL);
+        sum += jobs[i].sum;
+    }
+    return sum / ((double)batch * P->dims[P->n_layers]);
+}
+
 /* --- Adam with exponentially decayed learning rate (Sec. 6.1) --- */
 
 /* Step t (0-based): lr_t = lr0 * gamma^t, bias correction with t + 1;

@@ -117,6 +117,26 @@ def test_train_step_loss_with_philox_draws_and_adam_update():
     assert not tr.W_grad.any() and not any(g.any() for g in tr.grads)
 
 
+def test_full_size_step_loss_and_sampled_outputs():
+    """The timed training configuration at full size (four block-parameterised 1024^2 textures with 9 levels,
+    2048^2 reference, batch 2^20, 13-32-32-9 BF16, the bench's launch): outputs of 4,096 sampled queries of the
+    batch match the oracle, and the step's loss equals the oracle's loss over the same 2^20 Philox draws."""
+    _bcf()
+    w = workloads.train_workload()
+    tr = workloads.upload_trainer(w)
+    seed, step = 987654321, 0
+    u, v, s = oracle.train_queries(seed, step, w.batch, float(w.target_levels - 1))
+    F, P, T = _oracle_parts(w)
+    pick = np.sort(np.random.default_rng(8).choice(w.batch, 4096, replace=False))
+    got = tr.forward(*(torch.from_numpy(np.ascontiguousarray(a[pick])).cuda() for a in (u, v, s)))
+    ref = oracle.train_outputs(F, P, u[pick], v[pick], s[pick])
+    err = np.abs(got.cpu().numpy().astype(np.float64) - ref)
+    assert (err > 4e-3).mean() <= 2e-3 and err.max() < 0.05, (err.max(), (err > 4e-3).mean())
+    loss = float(tr.step(w.batch, seed, step).item())
+    ref_loss = oracle.train_loss_mt(F, P, T, u, v, s)
+    assert loss == pytest.approx(ref_loss, rel=2e-3), (loss, ref_loss)
+
+
 def test_export_is_bit_exact_and_decodes_to_the_emulated_features():
     bcf = _bcf()
     w = workloads.train_workload(**SMALL)
