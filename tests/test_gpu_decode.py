@@ -351,6 +351,45 @@ def test_full_size_screen_decode_sampled_against_oracle(variant):
     worst, frac = _quant_check(got, ref_q, tol, "fp16")
 
 
+@pytest.fixture(scope="module")
+def large_frame():
+    return workloads.config5()
+
+
+@pytest.mark.parametrize("precision", ["fp8", "fp16", "fp32"])
+def test_full_size_large_frame_sampled_against_oracle(large_frame, precision):
+    """The 8 x 4096^2 / 7680x4320 workload (MLP 25-64-64-9) at full size in the launch configuration the
+    benchmark times (whole frame, FP16 output; FP8 and FP16 on decode variant 3, FP32 on the plain path),
+    checked on 8,192 sampled queries: the low-precision paths against the quantisation-aware oracle, the FP32
+    path against FP64 within a few FP32 roundings of the network's magnitude bound."""
+    bcf = _bcf()
+    w = large_frame
+    m = workloads.upload(w, precision)
+    if precision != "fp32":
+        m.set_decode_variant(3)
+    u, v, s = workloads.queries_to_device(w)
+    out = torch.empty((w.n, 9), dtype=torch.float16, device="cuda")
+    m.decode(u, v, s, out=out)
+    idx = np.sort(np.random.default_rng(23).choice(w.n, 8192, replace=False))
+    got = out[torch.from_numpy(idx).cuda()].float().cpu().numpy().astype(np.float64)
+    del out, u, v, s, m
+    Wst, bias, a, ws = w.weights(precision)
+    P = oracle.Mlp(w.dims, precision, Wst, bias, a, ws)
+    mat = _oracle_material(w)
+    if precision != "fp32":
+        ref_q = oracle.decode(mat, P, w.u[idx], w.v[idx], w.s[idx], quant_aware=True, threads=8)
+        ref_q = ref_q.astype(np.float16).astype(np.float64)
+        _quant_check(got, ref_q, TOL[precision] + np.abs(ref_q) * 2.0 ** -11, precision)
+        return
+    ref = oracle.decode(mat, P, w.u[idx], w.v[idx], w.s[idx], threads=8)
+    feat = oracle.sample_features(mat, w.u[idx], w.v[idx], w.s[idx])
+    if w.lod_input:
+        feat = np.concatenate([feat, np.maximum(w.s[idx].astype(np.float64), 0.0)[:, None]], axis=1)
+    M = _abs_bound(w, feat)
+    tol = 4 * (max(w.dims) + 2) * 2.0 ** -24 * M + 1e-6 * M + np.abs(ref) * 2.0 ** -11  # FP16 output
+    assert (np.abs(got - ref) <= tol).all(), np.max(np.abs(got - ref) / np.maximum(tol, 1e-30))
+
+
 @pytest.mark.parametrize("n,scratch_kb", [(12200, 64), (12200, 4096), (100, 64), (777, 32)])
 def test_host_memory_decode_equals_device_decode(n, scratch_kb):
     """bcf_decode_material_host: pinned host queries in, host channels out, chunked and pipelined over three
