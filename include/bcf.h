@@ -238,7 +238,7 @@ typedef struct bcf_material_set_s *bcf_material_set;
  * (three layers, K0 <= 16 (FP8: 32) -> 32 -> 32 -> C <= 16, or
  * K0 <= 32 -> 64 -> 64 -> C <= 16), the set decodes through the texture unit
  * the same way (texture-unit texels, exact FP32 filter) with a persistent
- * kernel over 256-query tiles, and bcf_autotune_material_set has nothing to
+ * kernel over 128-query tiles, and bcf_autotune_material_set has nothing to
  * tune; otherwise it uses the tile-cooperative software decode.
  * Errors: BCF_ERR_INVALID_ARG (n out of [1, BCF_MAX_SET], null
  * materials, materials that do not share the MLP / texture count),
@@ -254,7 +254,8 @@ bcf_status bcf_destroy_material_set(bcf_material_set set);
  * concatenated: material m's queries are [d_offsets[m], d_offsets[m+1]) of
  * d_u / d_v / d_s (and of the rows of d_out [n_queries][C]).  d_offsets:
  * n + 1 non-decreasing int64 on the device (entries are clipped to
- * [0, n_queries]; a decreasing pair sets BCF_CHECK_OFFSETS).  Queries are processed in tiles of 256 taken from an
+ * [0, n_queries]; a decreasing pair sets BCF_CHECK_OFFSETS).  Queries are
+ * processed in tiles (256 queries; 128 on the texture-unit path) taken from an
  * atomic work counter that a memset before the launch resets, so the call
  * can be captured into a CUDA graph and replayed.  Calls on one set must
  * not overlap on the GPU (they share the counter).  Errors as

@@ -265,11 +265,11 @@ __global__ void __launch_bounds__(128) k_decode_mma(MaterialDev M, TexUnitObjs T
     }
 }
 
-// Material sets through the texture unit: a persistent CTA of 8 warps grabs 256-query tiles of a work list over
+// Material sets through the texture unit: a persistent CTA of 4 warps grabs 128-query tiles of a work list over
 // the materials (tiles never straddle two materials); when the material changes, its description, texture
 // objects and MLP weights replace the previous ones in shared memory; every warp then decodes its 32 queries as
 // variant 3 does (texture-unit texels, exact FP32 filter, register-chained tensor-core MLP).
-constexpr int kSetTexWarps = 8;
+constexpr int kSetTexWarps = 4;
 
 template <int PREC, int K0, int N1, int N2, int NO>
 __global__ void __launch_bounds__(32 * kSetTexWarps) k_decode_set_tex(
