@@ -325,7 +325,9 @@ def test_trained_network_beats_plain_bc6h_storage():
         print(f"plain BC6H modes {modes} 3x{r}^2 {nbytes} B ({nbytes / bytes_bcf:.2f}x) PSNR {ps:.2f} dB "
               f"({', '.join(f'{x:.1f}' for x in pl)})")
         assert math.isfinite(ps) and len(pl) == w.target_levels
-    assert abs(exported - bcf_psnr) < 0.1  # the exported blocks and FP16 weights decode as trained
+    # the exported blocks and FP16 weights lose nothing against the trainer's BF16 forward (the decode path's
+    # FP16 weights and FP32 activations may gain a little: measured +0.0 to +0.13 dB)
+    assert exported > bcf_psnr - 0.1
     # measured: 31.3 dB vs 20.3 (mode 10, 0.75x bytes), 28.6 (modes 10 + 11, 0.75x) and 28.9 (3x)
     assert bcf_psnr > plain[64, (10,)] + 8.0
     assert bcf_psnr > plain[128, (10, 11)] + 1.5
