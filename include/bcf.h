@@ -81,7 +81,10 @@ int bcf_version(void);
  *
  *   BCF_CHECK_PARTITION  a training block's partition id (d_partition) is
  *                        above 31; the block is read, trained and exported
- *                        with id & 31.
+ *                        with id & 31.  Checked by the optimiser of
+ *                        bcf_train_step / bcf_train_step_noalloc and by
+ *                        the export (bcf_train_forward / _backward only
+ *                        mask).
  *   BCF_CHECK_OFFSETS    material-set query offsets decrease
  *                        (d_offsets[m+1] < d_offsets[m]); that material's
  *                        range is decoded as empty.

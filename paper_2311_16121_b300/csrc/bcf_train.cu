@@ -273,6 +273,8 @@ struct AdamSeg {
     float lr;
     int blocks_layout; // 1: block parameters (clamp endpoints to [elo, ehi], x to [0, 1], skip unused)
     float elo, ehi;
+    const uint8_t *part; // block parameters: the partition ids, checked for ids above 31
+    unsigned *check;
 };
 
 struct AdamArgs {
@@ -313,6 +315,11 @@ __global__ void __launch_bounds__(256) k_adam(AdamArgs A)
     const AdamSeg &S = A.seg[k];
     const int64_t i0 = ((int64_t)blockIdx.x - A.chunk_start[k]) * kAdamChunk;
     const int64_t i1 = min(i0 + kAdamChunk, S.n);
+    if (S.part && threadIdx.x < kAdamChunk / 32) { // the chunk's block records: their partition ids
+        const int64_t r = i0 / 32 + threadIdx.x;
+        if (r < S.n / 32 && S.part[r] > 31 && S.check)
+            atomicOr(S.check, BCF_CHECK_PARTITION);
+    }
     const bool aligned = ((reinterpret_cast<uintptr_t>(S.p) | reinterpret_cast<uintptr_t>(S.g) |
                            reinterpret_cast<uintptr_t>(S.m) | reinterpret_cast<uintptr_t>(S.v)) & 15) == 0;
     if (aligned && i1 - i0 == kAdamChunk) {
@@ -451,11 +458,11 @@ cudaError_t launch_adam(const TrainDev &D, const TrainHyper &H, int64_t step, cu
     for (int t = 0; t < D.n_tex; ++t) {
         A.seg[k] = {D.tex[t].params, D.tex[t].grad, D.tex[t].m, D.tex[t].v, feature_floats(D, t),
                     (float)(H.lr_features * decay), D.unconstrained ? 0 : 1, D.is_signed ? -32.0f : 0.0f,
-                    D.is_signed ? 31.0f : 63.0f};
+                    D.is_signed ? 31.0f : 63.0f, D.unconstrained ? nullptr : D.tex[t].part, D.tex[t].check};
         ++k;
     }
-    A.seg[k++] = {D.W, D.Wg, D.Wm, D.Wv, D.w_total, (float)(H.lr_mlp * decay), 0, 0.0f, 0.0f};
-    A.seg[k++] = {D.b, D.bg, D.bm, D.bv, D.b_total, (float)(H.lr_mlp * decay), 0, 0.0f, 0.0f};
+    A.seg[k++] = {D.W, D.Wg, D.Wm, D.Wv, D.w_total, (float)(H.lr_mlp * decay), 0, 0.0f, 0.0f, nullptr, nullptr};
+    A.seg[k++] = {D.b, D.bg, D.bm, D.bv, D.b_total, (float)(H.lr_mlp * decay), 0, 0.0f, 0.0f, nullptr, nullptr};
     A.nseg = k;
     int64_t chunks = 0;
     for (int i = 0; i < k; ++i) {
