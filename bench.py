@@ -393,6 +393,30 @@ def main():
     sw_identical = bool(torch.equal(out, sw_out))
     del m_hw, sw_out
 
+    # the texel-fetch roofline of the headline: the texture unit's point-fetch rate on the same material's
+    # level-0 texels in screen-coherent order (bcf_texunit_fetch_probe), against the fetches one headline launch
+    # issues -- 4 per texture and sampled level, one level where the LOD is integral or the last one
+    probe_rounds = 8
+    sink = torch.empty(w.n, dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        mats[HEADLINE_PRECISION].texunit_fetch_probe(w.n, probe_rounds, sink=sink)
+    torch.cuda.synchronize()
+    pa, pb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    pa.record(stream)
+    for _ in range(5):
+        mats[HEADLINE_PRECISION].texunit_fetch_probe(w.n, probe_rounds, sink=sink)
+    pb.record(stream)
+    pb.synchronize()
+    probe_rate = 5 * 4 * probe_rounds * w.n / (pa.elapsed_time(pb) * 1e-3)
+    del sink
+    head_fetches = 0
+    s_clean = np.where(np.isnan(w.s), np.float32(0.0), w.s).astype(np.float32)
+    for res_t, lev_t in zip(w.res, w.levels):
+        bias = np.float32(int(round(np.log2(res_t))) - int(round(np.log2(w.res_ref))))
+        st = np.clip(s_clean + bias, np.float32(0.0), np.float32(lev_t - 1))
+        fl = np.floor(st)
+        head_fetches += int(4 * np.where((st - fl > 0) & (fl + 1 < lev_t), 2, 1).sum())
+
     def gathered(prec):
         """Outputs of one untimed decode of `prec` (in the timed path's output type) at query indices."""
         o = torch.empty_like(out32 if prec == "fp32" else out)
@@ -757,6 +781,14 @@ def main():
                                               "peak = 148 SMs x 4 partitions x 1 issue/clock at the max SM clock"},
                          "limiter": {"unit": "texture data pipe, pct of peak (ncu l1tex__data_pipe_tex_wavefronts)",
                                      "value": NCU_CAPTURE["tex_pipe_pct"] if counters_valid else None,
+                                     "texel_fetch": {"unit": "texel fetches/s",
+                                                     "achieved": head_fetches / head_launch_s,
+                                                     "peak": probe_rate,
+                                                     "frac": head_fetches / head_launch_s / probe_rate,
+                                                     "fetches_per_launch": head_fetches,
+                                                     "peak_source": "bcf_texunit_fetch_probe: 2x2 point-fetch "
+                                                                    "footprints of the headline material's level-0 "
+                                                                    "texels, screen-coherent, measured in this run"},
                                      "note": "the busiest unit of the headline kernel: 32 point-sampled texel "
                                              "fetches per query; issue active and tensor pipe " +
                                              (f"{NCU_CAPTURE['issue_active_pct']}% / {NCU_CAPTURE['tensor_active_pct']}%"

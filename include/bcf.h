@@ -575,6 +575,24 @@ bcf_status bcf_pack_mode10(const float *d_params, const uint8_t *d_partitions, i
  */
 bcf_status bcf_set_decode_variant(bcf_material mat, int32_t variant);
 
+/*
+ * bcf_texunit_fetch_probe -- measurement only: the rate at which the texture
+ * unit point-fetches this material's BC6H texels, the path decode variant 3
+ * is bound by.  n_threads threads each fetch, `rounds` times, the 2 x 2
+ * footprint around their own texel of level `level` of feature texture
+ * `texture` (4 x rounds x n_threads fetches in all), the 32 lanes of a warp
+ * on an 8 x 4 patch of neighbouring texels and the patches in row-major
+ * order over the level, as screen-coherent queries access it; the summed
+ * values go to d_sink[n_threads] (float32).  The material must have texture
+ * objects (decode variant 2 or 3 selected).  Asynchronous; no allocation.
+ * Errors: BCF_ERR_INVALID_ARG (texture, level, rounds in [1, 4096],
+ * n_threads in [0, 2^40], null or misaligned sink), BCF_ERR_UNSUPPORTED
+ * (no texture objects).
+ */
+bcf_status bcf_texunit_fetch_probe(bcf_material mat, int32_t texture, int32_t level, int64_t n_threads, int32_t rounds,
+                                   float *d_sink, bcf_stream stream);
+
+
 #ifdef __cplusplus
 }
 #endif

@@ -81,6 +81,8 @@ def lib() -> ctypes.CDLL:
         L.bcf_sample_features.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p]
         L.bcf_set_decode_variant.restype = c_int
         L.bcf_set_decode_variant.argtypes = [c_void_p, c_int32]
+        L.bcf_texunit_fetch_probe.restype = c_int
+        L.bcf_texunit_fetch_probe.argtypes = [c_void_p, c_int32, c_int32, c_int64, c_int32, c_void_p, c_void_p]
         L.bcf_decode_material.restype = c_int
         L.bcf_decode_material.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_int, c_void_p]
         L.bcf_create_material_set.restype = c_int
@@ -283,8 +285,19 @@ class Material:
         return out
 
     def set_decode_variant(self, variant: int) -> None:
-        """bcf_set_decode_variant: 0 tile-cooperative (default), 1 per-lane, 2 texture unit (hardware trilinear)."""
+        """bcf_set_decode_variant: 0 tile-cooperative (default), 1 per-lane, 2 texture unit (hardware trilinear),
+        3 texture-unit texels with the exact FP32 filter."""
         _check(lib().bcf_set_decode_variant(self.handle, int(variant)), "bcf_set_decode_variant")
+
+    def texunit_fetch_probe(self, n_threads: int, rounds: int, texture: int = 0, level: int = 0,
+                            sink: torch.Tensor | None = None) -> torch.Tensor:
+        """bcf_texunit_fetch_probe (measurement only): 4 x rounds x n_threads point fetches of one level's texels
+        in screen-coherent order; returns the float32 sink [n_threads]."""
+        if sink is None:
+            sink = torch.empty(n_threads, dtype=torch.float32, device="cuda")
+        _check(lib().bcf_texunit_fetch_probe(self.handle, int(texture), int(level), int(n_threads), int(rounds),
+                                             _ptr(sink), _stream()), "bcf_texunit_fetch_probe")
+        return sink
 
     def close(self) -> None:
         if self.handle:

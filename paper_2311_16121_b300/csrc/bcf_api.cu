@@ -297,6 +297,21 @@ bcf_status bcf_set_decode_variant(bcf_material m, int32_t variant)
     return BCF_OK;
 }
 
+bcf_status bcf_texunit_fetch_probe(bcf_material m, int32_t texture, int32_t level, int64_t n_threads,
+                                   int32_t rounds, float *d_sink, bcf_stream stream)
+{
+    if (!m || texture < 0 || texture >= m->host.n_tex || level < 0 || level >= m->host.tex[texture].levels ||
+        n_threads < 0 || n_threads > (1ll << 40) || rounds < 1 || rounds > 4096 || (n_threads > 0 && !d_sink) ||
+        !aligned(d_sink, 4))
+        return fail(BCF_ERR_INVALID_ARG, "bcf_texunit_fetch_probe: invalid material, texture, level, size or sink");
+    if (!m->hw_ready)
+        return fail(BCF_ERR_UNSUPPORTED, "bcf_texunit_fetch_probe: the material has no texture objects "
+                                         "(select decode variant 2 or 3 first)");
+    return cuda_status(launch_texfetch_probe(m->hw.texp[texture], m->host.tex[texture].res >> level, level,
+                                             n_threads, rounds, d_sink, (cudaStream_t)stream),
+                       "bcf_texunit_fetch_probe launch");
+}
+
 bcf_status bcf_destroy_material(bcf_material m)
 {
     if (!m)

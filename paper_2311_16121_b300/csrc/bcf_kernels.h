@@ -20,6 +20,8 @@ cudaError_t launch_decode_set_tex(const MaterialDev &M0, const MaterialDev *mats
 cudaError_t launch_decode_texunit(const MaterialDev &M, const TexUnitObjs &T, int exact_filter, const float *u,
                                   const float *v, const float *s, int64_t n, void *out, int out_fp16, cudaStream_t st);
 cudaError_t texunit_create(const MaterialDev &M, TexUnitObjs &T, void **arrays);
+cudaError_t launch_texfetch_probe(unsigned long long tex, int W, int level, int64_t n, int rounds, float *sink,
+                                  cudaStream_t st);
 void texunit_destroy(TexUnitObjs &T, void **arrays, int n_tex);
 cudaError_t launch_unpack_image(const void *blocks, int bw, int bh, int is_signed, uint16_t *out, cudaStream_t st);
 cudaError_t launch_sample_features(const MaterialDev &M, const float *u, const float *v, const float *s, int64_t n,

@@ -160,4 +160,45 @@ cudaError_t texunit_create(const MaterialDev &M, TexUnitObjs &T, void **arrays)
     return e;
 }
 
+// Point-fetch rate probe (measurement only): every lane fetches the 2 x 2 footprint around its own texel of one
+// level, as a query's bilinear taps do, with the 32 lanes of a warp on an 8 x 4 patch of neighbouring texels
+// (a warp of screen-coherent queries) and the warps' patches in row-major order over the level; each of the
+// `rounds` rounds moves the footprint one texel along x.  The fetched values are summed into sink[thread] so
+// that no fetch can be dropped.
+__global__ void __launch_bounds__(128) k_texfetch_probe(cudaTextureObject_t tex, int W, int level, int64_t n,
+                                                        int rounds, float *__restrict__ sink)
+{
+    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= n)
+        return;
+    const int lane = threadIdx.x & 31;
+    const int64_t patch = t >> 5;
+    const int per_row = max(W / 8, 1);
+    const int px = (int)((patch % per_row) * 8) + (lane & 7);
+    const int py = (int)(((patch / per_row) * 4) % W) + (lane >> 3);
+    const float rw = 1.0f / (float)W;
+    const float lod = (float)level;
+    float acc = 0.0f;
+    for (int r = 0; r < rounds; ++r) {
+        const float x0 = (float)((px + r) & (W - 1)) + 0.5f, x1 = (float)((px + r + 1) & (W - 1)) + 0.5f;
+        const float y0 = (float)(py & (W - 1)) + 0.5f, y1 = (float)((py + 1) & (W - 1)) + 0.5f;
+        const float4 a = tex2DLod<float4>(tex, x0 * rw, y0 * rw, lod);
+        const float4 b = tex2DLod<float4>(tex, x1 * rw, y0 * rw, lod);
+        const float4 c = tex2DLod<float4>(tex, x0 * rw, y1 * rw, lod);
+        const float4 d = tex2DLod<float4>(tex, x1 * rw, y1 * rw, lod);
+        acc += (a.x + b.y) + (c.z + d.x);
+    }
+    sink[t] = acc;
+}
+
+cudaError_t launch_texfetch_probe(unsigned long long tex, int W, int level, int64_t n, int rounds, float *sink,
+                                  cudaStream_t st)
+{
+    if (n <= 0)
+        return cudaSuccess;
+    k_texfetch_probe<<<(unsigned)((n + 127) / 128), 128, 0, st>>>((cudaTextureObject_t)tex, W, level, n, rounds,
+                                                                  sink);
+    return cudaGetLastError();
+}
+
 } // namespace bcf

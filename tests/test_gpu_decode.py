@@ -424,3 +424,39 @@ def test_paper_decoder_shape_12_16_9(precision):
     ref_q = oracle.decode(_oracle_material(w), oracle.Mlp(w.dims, precision, Wst, bias, sa, ws), w.u, w.v, w.s,
                           quant_aware=True, threads=8)
     _quant_check(a.astype(np.float64), ref_q, TOL[precision], precision)
+
+
+def test_texunit_fetch_probe_sums_the_decoded_footprints():
+    """bcf_texunit_fetch_probe (the measured texel-fetch peak of the benchmark): each thread's sum over its
+    rounds of (R of (x, y) + G of (x+1, y)) + (B of (x, y+1) + R of (x+1, y+1)), in single precision, equals the
+    same sum over the oracle's decode of the level (a ragged thread count, several levels); it needs the
+    material's texture objects."""
+    bcf = _bcf()
+    w = workloads.small_screen(res=64, width=16, height=16)
+    m = workloads.upload(w, "fp16")
+    with pytest.raises(bcf.BcfError):  # no texture objects before variant 2 / 3
+        m.texunit_fetch_probe(64, 2)
+    m.set_decode_variant(3)
+    with pytest.raises(bcf.BcfError):
+        m.texunit_fetch_probe(64, 0)
+    n, rounds = 1000, 3
+    for level in (0, 2):
+        got = m.texunit_fetch_probe(n, rounds, texture=1, level=level).cpu().numpy()
+        W = w.res[1] >> level
+        start = sum(((w.res[1] >> l) // 4) ** 2 for l in range(level)) * 16
+        img = oracle.bc6h_decode_image(w.blocks[1].reshape(-1)[start:], W // 4, W // 4)
+        val = img.view(np.float16).astype(np.float32)
+        ref = np.zeros(n, np.float32)
+        per_row = max(W // 8, 1)
+        for t in range(n):
+            lane, patch = t & 31, t >> 5
+            px = (patch % per_row) * 8 + (lane & 7)
+            py = ((patch // per_row) * 4) % W + (lane >> 3)
+            acc = np.float32(0.0)
+            for r in range(rounds):
+                x0, x1 = (px + r) & (W - 1), (px + r + 1) & (W - 1)
+                y0, y1 = py & (W - 1), (py + 1) & (W - 1)
+                acc = np.float32(acc + np.float32(np.float32(val[y0, x0, 0] + val[y0, x1, 1]) +
+                                                  np.float32(val[y1, x0, 2] + val[y1, x1, 0])))
+            ref[t] = acc
+        np.testing.assert_array_equal(got, ref)
