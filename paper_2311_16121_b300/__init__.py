@@ -382,6 +382,19 @@ class MaterialSet:
         return a.value, b.value, c.value
 
 
+def decode(target: "Material | MaterialSet", u: torch.Tensor, v: torch.Tensor, s: torch.Tensor | None,
+           offsets: torch.Tensor | None = None, out_dtype=torch.float16, out: torch.Tensor | None = None):
+    """Decode queries of one material (bcf_decode_material) or of a material set (bcf_decode_material_set,
+    `offsets` [n_materials + 1] int64 on the device) -> [n, C] channels."""
+    if isinstance(target, MaterialSet):
+        if offsets is None:
+            raise ValueError("decode: a material set needs the query offsets")
+        return target.decode(offsets, u, v, s, out_dtype=out_dtype, out=out)
+    if offsets is not None:
+        raise ValueError("decode: offsets apply to material sets only")
+    return target.decode(u, v, s, out_dtype=out_dtype, out=out)
+
+
 # --------------------------------------------------------------------------- training
 
 class Trainer:

@@ -41,10 +41,10 @@ def test_set_decode_equals_per_material_decodes(precision, variant):
         m.set_decode_variant(variant)
     S = bcf.MaterialSet(mats)
     off, u, v, s = _set_inputs(sw)
-    got = S.decode(off, u, v, s).cpu().numpy()
+    got = bcf.decode(S, u, v, s, offsets=off).cpu().numpy()
     for m, w in enumerate(sw.materials):
         a, b = int(sw.offsets[m]), int(sw.offsets[m + 1])
-        one = mats[m].decode(u[a:b], v[a:b], s[a:b], out_dtype=torch.float16).cpu().numpy()
+        one = bcf.decode(mats[m], u[a:b], v[a:b], s[a:b]).cpu().numpy()
         np.testing.assert_array_equal(got[a:b], one)
 
 
