@@ -141,10 +141,14 @@ def _abs_bound(w, feat):
     return h
 
 
-def test_decode_fp32_plain_matches_fp64():
+@pytest.mark.parametrize("variant", [0, 3])
+def test_decode_fp32_plain_matches_fp64(variant):
+    """The plain workload (2 x 256^2 random all-mode blocks, 65,536 queries, FP32 6-16-16-8) whole, through the
+    library's BC6H decoder and through the texture unit's texels (the benchmark's launch)."""
     bcf = _bcf()
     w = workloads.config1()
     m = workloads.upload(w, "fp32")
+    m.set_decode_variant(variant)
     u, v, s = workloads.queries_to_device(w)
     got = m.decode(u, v, s).cpu().numpy().astype(np.float64)
     Wst, bias, _, _ = w.weights("fp32")
