@@ -284,7 +284,7 @@ struct AdamArgs {
     float beta1, beta2, eps, bc1, bc2;
 };
 
-constexpr int kAdamChunk = 4096;  // elements per CTA: 256 threads x 4 float4 groups
+constexpr int kAdamChunk = 1024;  // elements per CTA: 256 threads x 1 float4 (more CTAs in flight; 4096: 1% slower step)
 constexpr int kAdamVec = kAdamChunk / (256 * 4);
 
 __device__ __forceinline__ float adam_one(const AdamArgs &A, float lr, float &p, float g, float &m, float &v)
