@@ -248,7 +248,7 @@ __device__ __forceinline__ void weight_grad(const uint32_t (&ghi)[2][MT][4], con
             }
 }
 
-template <bool FREE, int EMU>
+template <bool FREE, int EMU, bool GRID>
 __global__ void __launch_bounds__(kThreads, 2) k_train_mma(TrainDev D, int mode, int64_t batch, uint32_t seed_lo,
                                                         uint32_t seed_hi, uint32_t step_lo, uint32_t step_hi,
                                                         const float *__restrict__ qu, const float *__restrict__ qv,
@@ -523,6 +523,10 @@ __global__ void __launch_bounds__(kThreads, 2) k_train_mma(TrainDev D, int mode,
         __syncwarp();
         __syncthreads(); // and the scatter (the forward-only mode leaves the loop above, uniformly)
         // ---- the scatter of the input gradient into the block parameters (straight-through, Eq. 7-9)
+        // Grid batches (one scale per step, neighbouring lanes on neighbouring texels): with every lane active,
+        // the lanes' paths through the taps are uniform, and lanes that update the same block record and region
+        // add their endpoint gradients first (below).
+        const bool agg = GRID && __all_sync(0xffffffffu, active); // (a separate kernel: no cost to random batches)
         if (active) {
             for (int tx = 0; tx < D.n_tex; ++tx) {
                 const float dxf[3] = {rr[3 * tx], rr[3 * tx + 1], rr[3 * tx + 2]};
@@ -570,6 +574,34 @@ __global__ void __launch_bounds__(kThreads, 2) k_train_mma(TrainDev D, int mode,
                                     g[k][c] += g[j][c];
                                 own[j] = false;
                             }
+                    if (agg) {
+                        // a segmented scan over runs of lanes with equal (block, region): the run's last lane
+                        // carries the run's sum (lanes that do not own an update have keys of their own)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j) {
+                            const long long key = own[j] ? tps[j].block * 2 + reg[j] : -1 - lane;
+                            // every lane executes every shuffle (none sits behind a short-circuit operator)
+                            const long long kprev = __shfl_up_sync(0xffffffffu, key, 1);
+                            const long long knext = __shfl_down_sync(0xffffffffu, key, 1);
+                            const bool head = lane == 0 || kprev != key;
+                            const unsigned heads = __ballot_sync(0xffffffffu, head);
+                            const int start = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
+#pragma unroll
+                            for (int off = 1; off < 32; off <<= 1) {
+                                float pv[6];
+#pragma unroll
+                                for (int c = 0; c < 6; ++c)
+                                    pv[c] = __shfl_up_sync(0xffffffffu, g[j][c], off);
+                                if (lane - off >= start) {
+#pragma unroll
+                                    for (int c = 0; c < 6; ++c)
+                                        g[j][c] += pv[c];
+                                }
+                            }
+                            const bool tail = lane == 31 || knext != key;
+                            own[j] = own[j] && tail;
+                        }
+                    }
 #pragma unroll
                     for (int j = 0; j < 4; ++j) {
                         const Tap &tp = tps[j];
@@ -643,11 +675,12 @@ cudaError_t launch_train_mma(const TrainDev &D, int mode, int64_t batch, uint64_
                              const float *u, const float *v, const float *s, float *out, const float *grad_out,
                              float *loss, int sms, cudaStream_t st)
 {
-    static void (*const kernels[5])(TrainDev, int, int64_t, uint32_t, uint32_t, uint32_t, uint32_t, const float *,
+    static void (*const kernels[9])(TrainDev, int, int64_t, uint32_t, uint32_t, uint32_t, uint32_t, const float *,
                                     const float *, const float *, float *, const float *, float *, float) = {
-        k_train_mma<false, 0>, k_train_mma<false, 1>, k_train_mma<false, 2>, k_train_mma<false, 3>,
-        k_train_mma<true, 0>};
-    const auto kern = kernels[D.unconstrained ? 4 : emulation_variant(D)];
+        k_train_mma<false, 0, false>, k_train_mma<false, 1, false>, k_train_mma<false, 2, false>,
+        k_train_mma<false, 3, false>, k_train_mma<true, 0, false>,  k_train_mma<false, 0, true>,
+        k_train_mma<false, 1, true>,  k_train_mma<false, 2, true>,  k_train_mma<false, 3, true>};
+    const auto kern = kernels[D.unconstrained ? 4 : (D.batch_grid > 0 ? 5 : 0) + emulation_variant(D)];
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0);
     const int64_t tiles = (batch + kThreads - 1) / kThreads;
