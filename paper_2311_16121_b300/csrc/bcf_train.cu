@@ -51,6 +51,9 @@ __host__ __device__ inline int64_t train_smem_floats(const TrainDev &D)
     return f;
 }
 
+// EMU: the emulation variant of the block features (compile-time: one variant's code per kernel keeps the
+// instruction footprint small; with the variant chosen at run time "no instruction" was the second stall)
+template <int EMU>
 __global__ void __launch_bounds__(kTrainThreads) k_train(TrainDev D, int mode, int64_t batch, uint32_t seed_lo,
                                                          uint32_t seed_hi, uint32_t step_lo, uint32_t step_hi,
                                                          const float *__restrict__ qu, const float *__restrict__ qv,
@@ -93,7 +96,6 @@ __global__ void __launch_bounds__(kTrainThreads) k_train(TrainDev D, int mode, i
     __syncthreads();
     const int tid = threadIdx.x;
     const int nout = D.dims[L];
-    const int emu = emulation_variant(D);
     float loss_acc = 0.0f;
     const int64_t tiles = (batch + kTrainThreads - 1) / kTrainThreads;
     for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
@@ -122,7 +124,7 @@ __global__ void __launch_bounds__(kTrainThreads) k_train(TrainDev D, int mode, i
                 const TrainTexDev &T = D.tex[t];
                 for_each_tap(T, u, v, s, [&](const Tap &tp) {
                     SteTexel tx;
-                    ste_texel_v(T.params + tp.block * 32, read_partition(T, tp.block), tp.texel, emu, tx);
+                    ste_texel_e<EMU>(T.params + tp.block * 32, read_partition(T, tp.block), tp.texel, tx);
 #pragma unroll
                     for (int c = 0; c < 3; ++c)
                         f[c] = fmaf(tp.weight, tx.v[c], f[c]);
@@ -228,7 +230,7 @@ __global__ void __launch_bounds__(kTrainThreads) k_train(TrainDev D, int mode, i
                 for_each_tap(T, u, v, s, [&](const Tap &tp) {
                     const float *p = T.params + tp.block * 32;
                     SteTexel tx;
-                    ste_texel_v(p, read_partition(T, tp.block), tp.texel, emu, tx);
+                    ste_texel_e<EMU>(p, read_partition(T, tp.block), tp.texel, tx);
                     float *gp = T.grad + tp.block * 32;
                     float ga[3], gb[3], gx = 0.0f;
 #pragma unroll
@@ -433,17 +435,22 @@ cudaError_t launch_train(const TrainDev &D, int mode, int64_t batch, uint64_t se
     if (train_mma_supported(D))
         return launch_train_mma(D, mode, batch, seed, step, u, v, s, out, grad_out, loss, train_sms(), st);
     const int64_t smem = train_smem_bytes(D);
-    static int configured = 0;
-    if (!configured) {
-        cudaFuncSetAttribute(k_train, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        configured = 1;
+    static void (*const kernels[4])(TrainDev, int, int64_t, uint32_t, uint32_t, uint32_t, uint32_t, const float *,
+                                    const float *, const float *, float *, const float *, float *, float) = {
+        k_train<0>, k_train<1>, k_train<2>, k_train<3>};
+    const int emu = emulation_variant(D);
+    const auto kern = kernels[emu];
+    static int configured[4] = {0, 0, 0, 0};
+    if (!configured[emu]) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        configured[emu] = 1;
     }
     int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_train, kTrainThreads, (size_t)smem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTrainThreads, (size_t)smem);
     const int64_t tiles = (batch + kTrainThreads - 1) / kTrainThreads;
     const int64_t grid = min(tiles, (int64_t)train_sms() * max(per_sm, 1));
     const float gscale = 2.0f / ((float)batch * (float)D.dims[D.n_layers]);
-    k_train<<<(unsigned)grid, kTrainThreads, (size_t)smem, st>>>(
+    kern<<<(unsigned)grid, kTrainThreads, (size_t)smem, st>>>(
         D, mode, batch, (uint32_t)seed, (uint32_t)(seed >> 32), (uint32_t)step, (uint32_t)((uint64_t)step >> 32), u, v,
         s, out, grad_out, loss, gscale);
     return cudaGetLastError();

@@ -149,18 +149,15 @@ __device__ __forceinline__ void ste_texel(const float *p, int k, int t, SteTexel
     ste_from(P, o);
 }
 
-// runtime-selected variant (the SIMT training kernel)
-__device__ __forceinline__ void ste_texel_v(const float *p, int k, int t, int emu, SteTexel &o)
+// compile-time variant
+template <int EMU>
+__device__ __forceinline__ void ste_texel_e(const float *p, int k, int t, SteTexel &o)
 {
     TexelParams P;
     load_texel(p, k, t, P);
-    switch (emu) {
-    case 1: ste_from_v<1>(P, o); break;
-    case 2: ste_from_v<2>(P, o); break;
-    case 3: ste_from_v<3>(P, o); break;
-    default: ste_from_v<0>(P, o); break;
-    }
+    ste_from_v<EMU>(P, o);
 }
+
 
 // Fire-and-forget vector reductions into the gradient arrays.  The kernels never read a gradient they add
 // to, so the reductions carry no memory clobber: later parameter loads may be issued ahead of them.
