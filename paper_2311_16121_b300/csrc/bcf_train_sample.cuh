@@ -158,7 +158,6 @@ __device__ __forceinline__ void ste_texel_e(const float *p, int k, int t, SteTex
     ste_from_v<EMU>(P, o);
 }
 
-
 // Fire-and-forget vector reductions into the gradient arrays.  The kernels never read a gradient they add
 // to, so the reductions carry no memory clobber: later parameter loads may be issued ahead of them.
 __device__ __forceinline__ void red_add_v4(float *p, float a, float b, float c, float d)
