@@ -250,11 +250,17 @@ def run_reference(args):
     print(json.dumps(line))
 
 
-def _train_bench(torch, workloads, stream, k_train):
+def _train_bench(torch, workloads, stream, k_train, shape="config3"):
     """Training steps/s: 4 block-parameterised 1024^2 textures with mips, 2048^2 9-channel reference,
-    batch 2^20 Philox draws, MLP 13-32-32-9 (BF16 operands), Adam.  Returns (ms/step, last loss, batch)."""
-    tw = workloads.train_workload()
-    tr = workloads.upload_trainer(tw)
+    batch 2^20 Philox draws, MLP 13-32-32-9 (BF16 operands), Adam.  shape="paper": the paper's BCf-1K
+    textures (1024 / 512 / 256 / 128) and its 12-16-9 decoder without the LOD input.  Returns (ms/step, last
+    loss, batch)."""
+    if shape == "paper":
+        tw = workloads.train_workload(res=(1024, 512, 256, 128), target_res=2048, dims=(12, 16, 9))
+        tr = workloads.upload_trainer(tw, lod_input=False)
+    else:
+        tw = workloads.train_workload()
+        tr = workloads.upload_trainer(tw)
     for i in range(3):
         tr.step(tw.batch, 7, i)
     torch.cuda.synchronize()
@@ -277,6 +283,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-train", action="store_true",
                     help="time only the training step (for profiler captures); prints a reduced line")
+    ap.add_argument("--train-shape", default="config3", choices=["config3", "paper"],
+                    help="with --only-train: the timed workload's decoder (paper = BCf-1K textures, 12-16-9)")
     ap.add_argument("--only-headline", action="store_true",
                     help="time only the headline decode (for profiler captures); prints a reduced line")
     args = ap.parse_args()
@@ -301,11 +309,11 @@ def main():
 
     stream = torch.cuda.current_stream()
     if args.only_train:
-        ms, loss, batch = _train_bench(torch, workloads, stream, args.steps)
+        ms, loss, batch = _train_bench(torch, workloads, stream, args.steps, args.train_shape)
         if rank == 0:
             print(json.dumps({"metric": "train steps/s", "value": 1000.0 / ms, "unit": "steps/s", "n_gpus": world,
                               "steps": args.steps, "warmup": 3, "ms_per_step": ms, "batch": batch,
-                              "last_loss": loss, "note": "training step only"}))
+                              "last_loss": loss, "shape": args.train_shape, "note": "training step only"}))
         return
 
     w = workloads.config2()
@@ -505,6 +513,7 @@ def main():
     del scratch, ud, vd, sd
 
     train_ms, train_loss, train_batch = _train_bench(torch, workloads, stream, max(3, args.steps // 2))
+    ptrain_ms, _, _ = _train_bench(torch, workloads, stream, max(3, args.steps // 4), "paper")
     # FP32 atomic-add rate of this GPU for scattered updates into a buffer of the trainer's size (torch
     # index_add_, one atomic per element): the reference for the training scatter's reduction rate
     gbuf = torch.zeros(9_786_368, device="cuda")
@@ -763,6 +772,11 @@ def main():
             "texunit": {"value": w.n / (hw_ms * 1e-3) / 1e9, "unit": "Gsamples/s", "ms_per_step": hw_ms,
                         "precision": HEADLINE_PRECISION, "kernel": "decode variant 2: hardware trilinear filtering of "
                         "mipmapped BC6H texture objects + tensor-core MLP (per-lane)", **hw_stats},
+            "train_paper_decoder": {"metric": "train steps/s", "value": 1000.0 / ptrain_ms, "unit": "steps/s",
+                                    "ms_per_step": ptrain_ms, "batch": train_batch,
+                                    "workload": "the paper's BCf-1K textures (1024/512/256/128 with mips), 2048^2 "
+                                                "reference, its 12-16-9 decoder without the LOD input (SIMT "
+                                                "kernel), Adam"},
             "train_unconstrained": {"metric": "train steps/s", "value": 1000.0 / free_ms, "unit": "steps/s",
                                     "ms_per_step": free_ms, "batch": train_batch,
                                     "workload": "first stage: free per-texel features, 4x 1024^2 with 9 levels"},
