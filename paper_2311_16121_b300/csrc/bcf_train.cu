@@ -122,12 +122,15 @@ __global__ void __launch_bounds__(kTrainThreads) k_train(TrainDev D, int mode, i
             float f[3] = {0.0f, 0.0f, 0.0f};
             if (active) {
                 const TrainTexDev &T = D.tex[t];
-                for_each_tap(T, u, v, s, [&](const Tap &tp) {
-                    SteTexel tx;
-                    ste_texel_e<EMU>(T.params + tp.block * 32, read_partition(T, tp.block), tp.texel, tx);
+                for_each_side(T, u, v, s, [&](const Tap(&tps)[4], const TexelParams(&P)[4]) {
 #pragma unroll
-                    for (int c = 0; c < 3; ++c)
-                        f[c] = fmaf(tp.weight, tx.v[c], f[c]);
+                    for (int j = 0; j < 4; ++j) {
+                        SteTexel tx;
+                        ste_from_v<EMU>(P[j], tx);
+#pragma unroll
+                        for (int c = 0; c < 3; ++c)
+                            f[c] = fmaf(tps[j].weight, tx.v[c], f[c]);
+                    }
                 });
             }
             a0[3 * t] = bf16r(f[0]);
@@ -227,23 +230,26 @@ __global__ void __launch_bounds__(kTrainThreads) k_train(TrainDev D, int mode, i
                     dxf[c] = acc;
                 }
                 const TrainTexDev &T = D.tex[t];
-                for_each_tap(T, u, v, s, [&](const Tap &tp) {
-                    const float *p = T.params + tp.block * 32;
-                    SteTexel tx;
-                    ste_texel_e<EMU>(p, read_partition(T, tp.block), tp.texel, tx);
-                    float *gp = T.grad + tp.block * 32;
-                    float ga[3], gb[3], gx = 0.0f;
+                for_each_side(T, u, v, s, [&](const Tap(&tps)[4], const TexelParams(&P)[4]) {
 #pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        const float dv = dxf[c] * tp.weight;
-                        ga[c] = tx.ina[c] ? dv * tx.dea[c] : 0.0f;
-                        gb[c] = tx.inb[c] ? dv * tx.deb[c] : 0.0f;
-                        gx = fmaf(dv, tx.dx[c], gx);
+                    for (int j = 0; j < 4; ++j) {
+                        const Tap &tp = tps[j];
+                        SteTexel tx;
+                        ste_from_v<EMU>(P[j], tx);
+                        float *gp = T.grad + tp.block * 32;
+                        float ga[3], gb[3], gx = 0.0f;
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {
+                            const float dv = dxf[c] * tp.weight;
+                            ga[c] = tx.ina[c] ? dv * tx.dea[c] : 0.0f;
+                            gb[c] = tx.inb[c] ? dv * tx.deb[c] : 0.0f;
+                            gx = fmaf(dv, tx.dx[c], gx);
+                        }
+                        red_add_v4(gp + 8 * tx.region, ga[0], ga[1], ga[2], gb[0]);
+                        red_add_v2(gp + 8 * tx.region + 4, gb[1], gb[2]);
+                        if (tx.inx)
+                            atomicAdd(gp + 16 + tp.texel, gx);
                     }
-                    red_add_v4(gp + 8 * tx.region, ga[0], ga[1], ga[2], gb[0]);
-                    red_add_v2(gp + 8 * tx.region + 4, gb[1], gb[2]);
-                    if (tx.inx)
-                        atomicAdd(gp + 16 + tp.texel, gx);
                 });
             }
         }

@@ -177,44 +177,6 @@ struct Tap {
     float weight;
 };
 
-template <class F>
-__device__ __forceinline__ void for_each_tap(const TrainTexDev &T, float u, float v, float s, F f)
-{
-    float st = (isnan(s) ? 0.0f : s) + (float)T.lod_bias;
-    st = fminf(fmaxf(st, 0.0f), (float)(T.levels - 1));
-    const float fl = floorf(st);
-    const int l0 = (int)fl;
-    const int l1 = min(l0 + 1, T.levels - 1);
-    const float lam = st - fl;
-#pragma unroll
-    for (int side = 0; side < 2; ++side) {
-        const int level = side ? l1 : l0;
-        const float lw = side ? lam : 1.0f - lam;
-        if (lw == 0.0f)
-            continue;
-        const int W = T.res >> level, wb = W >> 2;
-        const int64_t lbase = (int64_t)((((uint32_t)(T.res >> 2) * (uint32_t)(T.res >> 2)) -
-                                         ((uint32_t)wb * (uint32_t)wb)) * 4u / 3u);
-        const float x = u * (float)W - 0.5f, y = v * (float)W - 0.5f;
-        const float fx0 = floorf(x), fy0 = floorf(y);
-        const float fx = x - fx0, fy = y - fy0;
-        const int i0 = (int)fx0, j0 = (int)fy0;
-#pragma unroll
-        for (int c = 0; c < 4; ++c) {
-            const int i = (i0 + (c & 1)) & (W - 1), j = (j0 + (c >> 1)) & (W - 1);
-            const float bw = ((c & 1) ? fx : 1.0f - fx) * ((c >> 1) ? fy : 1.0f - fy);
-            Tap tp;
-            tp.block = lbase + (int64_t)(j >> 2) * wb + (i >> 2);
-            tp.texel = ((j & 3) << 2) | (i & 3);
-            tp.weight = lw * bw;
-            f(tp);
-        }
-    }
-}
-
-// The same taps grouped by side: f(taps[4]) once per side with a non-zero weight.  The four partition bytes
-// and then the four parameter records of a side are loaded together (two memory latencies per side).
-
 // The parameters of a 2x2 footprint's four taps (0: (i, j), 1: (i+1, j), 2: (i, j+1), 3: (i+1, j+1)).  Taps in
 // one block share its partition read, and taps in one block and region share the endpoint loads; the loads
 // are predicated off lane by lane, which saves L1 wavefronts in the L1-bound training kernel (most footprints
@@ -265,6 +227,9 @@ __device__ __forceinline__ void load_footprint(const TrainTexDev &T, const Tap (
     }
 }
 
+// The trilinear taps grouped by side: f(taps[4], params[4]) once per side with a non-zero weight.  The
+// partition bytes and then the parameter records of a side's four taps are loaded together (two memory
+// latencies per side).
 template <class F>
 __device__ __forceinline__ void for_each_side(const TrainTexDev &T, float u, float v, float s, F f)
 {
