@@ -48,7 +48,7 @@ extern "C" {
 typedef enum {
     BCF_OK = 0,
     BCF_ERR_INVALID_ARG = 1,  /* a size, pointer, alignment or descriptor field is invalid */
-    BCF_ERR_UNSUPPORTED = 2,  /* valid but outside what this build implements */
+    BCF_ERR_UNSUPPORTED = 2,  /* valid but outside what the library implements */
     BCF_ERR_CUDA = 3,         /* a CUDA runtime call or kernel launch failed */
     BCF_ERR_OOM = 4,          /* a create-time allocation failed */
     BCF_ERR_TIMEOUT = 5,      /* a bounded device-side wait ran out */
