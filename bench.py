@@ -258,6 +258,9 @@ def _train_bench(torch, workloads, stream, k_train, shape="config3"):
     if shape == "paper":
         tw = workloads.train_workload(res=(1024, 512, 256, 128), target_res=2048, dims=(12, 16, 9))
         tr = workloads.upload_trainer(tw, lod_input=False)
+    elif shape == "grid":  # the paper's batch form: a jittered 1024 x 1024 uv grid with one scale per step
+        tw = workloads.train_workload()
+        tr = workloads.upload_trainer(tw, batch_grid=1024)
     else:
         tw = workloads.train_workload()
         tr = workloads.upload_trainer(tw)
@@ -283,7 +286,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only-train", action="store_true",
                     help="time only the training step (for profiler captures); prints a reduced line")
-    ap.add_argument("--train-shape", default="config3", choices=["config3", "paper"],
+    ap.add_argument("--train-shape", default="config3", choices=["config3", "paper", "grid"],
                     help="with --only-train: the timed workload's decoder (paper = BCf-1K textures, 12-16-9)")
     ap.add_argument("--only-headline", action="store_true",
                     help="time only the headline decode (for profiler captures); prints a reduced line")
@@ -514,6 +517,7 @@ def main():
 
     train_ms, train_loss, train_batch = _train_bench(torch, workloads, stream, max(3, args.steps // 2))
     ptrain_ms, _, _ = _train_bench(torch, workloads, stream, max(3, args.steps // 4), "paper")
+    gtrain_ms, _, _ = _train_bench(torch, workloads, stream, max(3, args.steps // 4), "grid")
     # FP32 atomic-add rate of this GPU for scattered updates into a buffer of the trainer's size (torch
     # index_add_, one atomic per element): the reference for the training scatter's reduction rate
     gbuf = torch.zeros(9_786_368, device="cuda")
@@ -772,6 +776,10 @@ def main():
             "texunit": {"value": w.n / (hw_ms * 1e-3) / 1e9, "unit": "Gsamples/s", "ms_per_step": hw_ms,
                         "precision": HEADLINE_PRECISION, "kernel": "decode variant 2: hardware trilinear filtering of "
                         "mipmapped BC6H texture objects + tensor-core MLP (per-lane)", **hw_stats},
+            "train_grid_batches": {"metric": "train steps/s", "value": 1000.0 / gtrain_ms, "unit": "steps/s",
+                                   "ms_per_step": gtrain_ms, "batch": train_batch,
+                                   "workload": "the training workload with the paper's batch form: a jittered "
+                                               "1024 x 1024 uv grid and one scale per step"},
             "train_paper_decoder": {"metric": "train steps/s", "value": 1000.0 / ptrain_ms, "unit": "steps/s",
                                     "ms_per_step": ptrain_ms, "batch": train_batch,
                                     "workload": "the paper's BCf-1K textures (1024/512/256/128 with mips), 2048^2 "
