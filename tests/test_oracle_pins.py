@@ -1074,3 +1074,19 @@ def test_grid_batches_are_a_jittered_grid_with_one_scale():
     assert 0.0 <= ou[0] < 1.0 and 0.0 <= ov[0] < 1.0
     u2, _, s2 = oracle.train_queries(9, 5, G * G, 7.0, grid=G)
     assert u2[0] != u[0] and s2[0] != s[0]
+
+
+def test_threaded_loss_equals_the_sequential_loss():
+    """The threaded loss used for full-size batches equals the sequential one up to the order of the partial
+    sums (each thread sums a contiguous range of queries)."""
+    from paper_2311_16121_b300 import workloads
+
+    w = workloads.train_workload(res=(32, 32), target_res=64, batch=256, dims=(7, 8, 8, 9))
+    F = oracle.TrainFeatures([workloads.params32_to_28(p).astype(np.float64) for p in w.params], w.partition,
+                             w.res, w.levels, w.res_ref, lod_input=True)
+    P = oracle.TrainMlp(w.dims, w.W, w.b, bf16=True)
+    T = oracle.Target(w.target8, w.target1, w.target_res, w.target_levels)
+    u, v, s = oracle.train_queries(11, 2, 3001, float(w.target_levels - 1))
+    seq = oracle.train_loss_grad(F, P, T, u, v, s, want_grad=False)[0]
+    for threads in (1, 3, 7):
+        assert oracle.train_loss_mt(F, P, T, u, v, s, threads=threads) == pytest.approx(seq, rel=1e-12)
