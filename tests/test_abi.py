@@ -104,3 +104,19 @@ def test_compressor_and_packer_host_validation():
     assert L.bcf_pack_mode10(4096, 4096, 0, 0, None, None) == 0  # nothing to do
     assert L.bcf_pack_mode10(4100, 4096, 8, 0, 4096, None) == 1  # params not 16-byte aligned
     assert L.bcf_pack_mode10(4096, None, 8, 0, 4096, None) == 1  # no partitions
+
+
+def test_material_bytes_reproduce_table2_sizes():
+    """The storage the schedule reports for a block-compressed material (16 bytes per 4 x 4 block, full mip
+    chains) reproduces the sizes printed for the paper's profiles (Table 2 with Table 1's resolutions)."""
+    from paper_2311_16121_b300 import schedule
+
+    here = os.path.dirname(os.path.abspath(__file__))
+    with open(os.path.join(here, "golden", "table2_sizes.txt")) as f:
+        rows = [ln.split() for ln in f if ln.strip() and not ln.startswith("#")]
+    assert len(rows) == 4
+    for r in rows:
+        res = [int(r[1]), int(r[3]), int(r[5]), int(r[7])]
+        levels = [int(r[2]), int(r[4]), int(r[6]), int(r[8])]
+        mib = schedule.material_bytes(res, levels) / 2 ** 20
+        assert round(mib, 2) == float(r[9]), (r[0], mib)
