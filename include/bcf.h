@@ -439,6 +439,9 @@ bcf_status bcf_train_backward(bcf_trainer tr, const float *d_u, const float *d_v
  * before accumulating (the array keeps the last call's contents).  All calls
  * on a device share the one array: calls whose work overlaps on the GPU
  * (different streams, or different threads) race and give wrong results.
+ * The looked-up address belongs to the device's primary context: after a
+ * cudaDeviceReset (which also invalidates every material and trainer made
+ * before it) the library must not be called again in that process.
  * Errors: those of bcf_train_step; BCF_ERR_UNSUPPORTED when the trainer has
  * more gradient values than the array holds (each texture's block records
  * and the weights and biases, each rounded up to 32 floats); BCF_ERR_CUDA

@@ -161,6 +161,14 @@ def lib():
         L.oracle_compress_bc6h_block.argtypes = [c_void_p, c_void_p, POINTER(c_float), POINTER(c_int)]
         L.oracle_compress_bc6h_texture.restype = None
         L.oracle_compress_bc6h_texture.argtypes = [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]
+        L.oracle_mlp_explain.restype = c_int
+        L.oracle_mlp_explain.argtypes = [POINTER(_Mlp), c_void_p, c_void_p, c_void_p, c_double, c_int, ctypes.c_long]
+        L.oracle_train_mlp_explain.restype = c_int
+        L.oracle_train_mlp_explain.argtypes = [POINTER(_TrainMlp), c_void_p, c_void_p, c_void_p, c_double,
+                                               ctypes.c_long]
+        L.oracle_train_backward_bounds.restype = None
+        L.oracle_train_backward_bounds.argtypes = [POINTER(_TrainFeatures), POINTER(_TrainMlp), c_int64, c_void_p,
+                                                   c_void_p, c_void_p, c_void_p, c_void_p, c_void_p]
         L.oracle_adam.restype = None
         L.oracle_adam.argtypes = [c_int64, c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_double, c_double, c_double,
                                   c_double, c_double, c_double, c_double]
@@ -338,6 +346,64 @@ def mlp_one(mlp: Mlp, x: np.ndarray, quant_aware: bool = False) -> np.ndarray:
     out = np.zeros(mlp.dims[-1], dtype=np.float64)
     lib().oracle_mlp_one(ctypes.byref(mlp.c), _ptr(x), int(quant_aware), _ptr(out))
     return out
+
+
+def mlp_explain(mlp: Mlp, x: np.ndarray, x_err: np.ndarray, y_dev: np.ndarray, tol: float, out_half: bool = False,
+                max_leaves: int = 1 << 16) -> int:
+    """Whether a device output y_dev that misses the tolerance is a rounding flip (oracle_mlp_explain): 1 if a
+    combination of the operand roundings that the device's FP32 error windows allow reproduces y_dev within
+    tol, 0 if none does, -1 if the enumeration would exceed max_leaves combinations."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    e = np.ascontiguousarray(x_err, dtype=np.float64)
+    y = np.ascontiguousarray(y_dev, dtype=np.float64)
+    return int(lib().oracle_mlp_explain(ctypes.byref(mlp.c), _ptr(x), _ptr(e), _ptr(y), float(tol), int(out_half),
+                                        int(max_leaves)))
+
+
+def mlp_inputs(mat: Material, u, v, s) -> tuple[np.ndarray, np.ndarray]:
+    """Exact (FP64) MLP inputs of queries -- the filtered features, then the LOD input max(s, 0) with NaN read as
+    0 when the material has one -- and a bound on the device's FP32 error in each: 2^-21 + 2^-20 |x| for a
+    feature (a few single-precision roundings of a sum of at most 8 texels of magnitude <= 1 per channel of
+    the test materials), 0 for the LOD input (the same float on both sides)."""
+    f = sample_features(mat, u, v, s)
+    e = 2.0 ** -21 + 2.0 ** -20 * np.abs(f)
+    if mat.lod_input:
+        sq = np.zeros(f.shape[0]) if s is None else np.asarray(s, np.float64)
+        lod = np.where(np.isnan(sq), 0.0, np.maximum(sq, 0.0))
+        f = np.concatenate([f, lod[:, None]], axis=1)
+        e = np.concatenate([e, np.zeros((e.shape[0], 1))], axis=1)
+    return f, e
+
+
+def check_outputs(got: np.ndarray, ref_q: np.ndarray, tol: float, out_half: bool, explain) -> dict:
+    """Strict comparison of device outputs with the quantisation-aware oracle: every output within tol
+    (plus half an FP16 unit of the reference when the device stored FP16) of ref_q, except in rows that
+    explain(rows) -> list of mlp_explain results shows to be operand-rounding flips.  Returns counts: outputs
+    beyond the tolerance, rows holding them, rows explained as flips, the unexplained rows (which fail a
+    test), and the per-channel maximum error."""
+    got = np.asarray(got, np.float64)
+    ref_q = np.asarray(ref_q, np.float64)
+    if out_half:
+        ref_q = ref_q.astype(np.float16).astype(np.float64)
+    t = tol + (np.abs(ref_q) * 2.0 ** -11 if out_half else 0.0)
+    err = np.abs(got - ref_q)
+    beyond = ~(err <= t)
+    rows = np.nonzero(beyond.any(axis=1))[0]
+    verdict = explain(rows) if rows.size else []
+    unexplained = [int(r) for r, k in zip(rows, verdict) if k != 1]
+    return {"outputs": int(got.size), "beyond_tol": int(beyond.sum()), "rows_beyond": int(rows.size),
+            "flips": int(rows.size - len(unexplained)), "unexplained": unexplained,
+            "worst": err.max(axis=0) if err.size else np.zeros(0)}
+
+
+def decode_explainer(mat: Material, mlp: Mlp, u, v, s, got: np.ndarray, tol: float, out_half: bool):
+    """explain(rows) for check_outputs on a decode: mlp_explain of each row with its exact inputs."""
+    def explain(rows):
+        su = None if s is None else np.asarray(s)[rows]
+        x, e = mlp_inputs(mat, np.asarray(u)[rows], np.asarray(v)[rows], su)
+        return [mlp_explain(mlp, x[i], e[i], np.asarray(got, np.float64)[r], tol, out_half)
+                for i, r in enumerate(rows)]
+    return explain
 
 
 # --------------------------------------------------------------------------- random draws
@@ -549,6 +615,58 @@ def train_backward_given(F: TrainFeatures, P: TrainMlp, u, v, s, grad_out):
     lib().oracle_train_backward_given(ctypes.byref(F.c), ctypes.byref(P.c), u.size, _ptr(u), _ptr(v), _ptr(s),
                                       _ptr(go), ctypes.byref(G))
     return [g.reshape(-1, 3 if F.free else 28) for g in gf], gW, gb
+
+
+def train_mlp_explain(P: TrainMlp, x: np.ndarray, x_err: np.ndarray, y_dev: np.ndarray, tol: float,
+                      max_leaves: int = 1 << 16) -> int:
+    """mlp_explain for the training network (bfloat16 operands, FP32 outputs)."""
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    e = np.ascontiguousarray(x_err, dtype=np.float64)
+    y = np.ascontiguousarray(y_dev, dtype=np.float64)
+    return int(lib().oracle_train_mlp_explain(ctypes.byref(P.c), _ptr(x), _ptr(e), _ptr(y), float(tol),
+                                              int(max_leaves)))
+
+
+def train_explainer(F: TrainFeatures, P: TrainMlp, u, v, s, got: np.ndarray, tol: float, lod_input: bool = True):
+    """explain(rows) for check_outputs on a training forward (emulated features, bfloat16 network)."""
+    def explain(rows):
+        out = []
+        for r in rows:
+            f = train_features_one(F, float(u[r]), float(v[r]), float(s[r]))
+            e = 2.0 ** -21 + 2.0 ** -20 * np.abs(f)
+            if lod_input:
+                sq = float(s[r])
+                f = np.append(f, 0.0 if np.isnan(sq) else max(sq, 0.0))
+                e = np.append(e, 0.0)
+            out.append(train_mlp_explain(P, f, e, np.asarray(got, np.float64)[r], tol))
+        return out
+    return explain
+
+
+def train_backward_bounds(F: TrainFeatures, P: TrainMlp, u, v, s, grad_out):
+    """Per-element bounds of the device gradients (oracle_train_backward_bounds): (A, R), each as
+    (feature arrays per texture, W array, b array) in the layout of train_backward_given; the device gradient
+    lies within c A + R of the oracle's."""
+    u = np.ascontiguousarray(u, np.float32)
+    v = np.ascontiguousarray(v, np.float32)
+    s = np.ascontiguousarray(s, np.float32)
+    go = np.ascontiguousarray(grad_out, np.float64)
+    out = []
+    Gs = []
+    for _ in range(2):
+        gf = [np.zeros_like(p) for p in F._p]
+        gW = np.zeros(P._W.size, np.float64)
+        gb = np.zeros(P._b.size, np.float64)
+        G = _TrainGrads()
+        for t, g in enumerate(gf):
+            G.feat_grad[t] = g.ctypes.data
+        G.W_grad = gW.ctypes.data
+        G.b_grad = gb.ctypes.data
+        out.append((gf, gW, gb))
+        Gs.append(G)
+    lib().oracle_train_backward_bounds(ctypes.byref(F.c), ctypes.byref(P.c), u.size, _ptr(u), _ptr(v), _ptr(s),
+                                       _ptr(go), ctypes.byref(Gs[0]), ctypes.byref(Gs[1]))
+    return tuple(([g.reshape(-1, 3 if F.free else 28) for g in gf], gW, gb) for gf, gW, gb in out)
 
 
 # --------------------------------------------------------------------------- mode-10 encoder

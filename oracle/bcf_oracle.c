@@ -1518,6 +1518,344 @@ void oracle_train_backward_given(const oracle_train_features *F, const oracle_tr
 }
 
 /* ------------------------------------------------------------------------- */
+/* Rounding flips of the low-precision networks (test support)               */
+/* ------------------------------------------------------------------------- */
+/*
+ * A low-precision evaluation rounds every layer input to its storage format.
+ * The quantisation-aware forward above computes the value that is rounded in
+ * FP64; the device computes it in FP32 (filter, accumulation, scale, bias).
+ * Where that value lies within the device's FP32 error of a rounding
+ * boundary, the two sides may round it to neighbouring representable values
+ * (a flip), and the outputs then differ by the effect of one operand unit in
+ * the last place, which for E4M3 and bfloat16 can exceed the absolute output
+ * tolerance.  The functions below decide whether a device output that misses
+ * the tolerance is such a case, and nothing else: they enumerate every
+ * combination of roundings that the FP32 error windows allow (layer by
+ * layer, through the ReLU) and report whether one combination reproduces the
+ * device output within the tolerance on every channel.
+ *
+ * Error windows, bounds on |device value - exact value| before a rounding:
+ *   layer-0 inputs: x_err[i], from the caller (the FP32 filter's bound);
+ *   a hidden or output pre-activation: 4 (n_in + 2) 2^-24 (|scale| sum_i
+ *   |w_i x_i| + |b|), the worst case of an FP32 sum of n_in products, one
+ *   scaling and one bias addition (with a factor 2 for truncating adders).
+ */
+typedef struct {
+    int n_layers;
+    const int *dims;
+    const double *W;      /* per layer [out][in]: the operand values the device multiplies */
+    const double *b;      /* per layer [out] */
+    const double *scale;  /* per layer: factor of the product sums (E4M3: act_scale * w_scale, else 1) */
+    const double *in_div; /* per layer: the layer input is divided by this before rounding (E4M3: act_scale) */
+    int precision;        /* rounding of every layer input (OR_FP16 / OR_BF16 / OR_FP8; OR_FP32: none) */
+    const double *y_dev;  /* the device's outputs */
+    double tol;
+    int out_half;         /* the device output was stored as binary16 */
+    long leaves, max_leaves;
+    int64_t woff[OR_MAX_LAYERS], boff[OR_MAX_LAYERS];
+} flip_ctx;
+
+static double flip_round(const flip_ctx *C, int l, double h) { return quantize_input(C->precision, h / C->in_div[l]); }
+
+/* the rounded values an input of layer l can take when its exact value is v and the device's lies within e */
+static int flip_candidates(const flip_ctx *C, int l, double v, double e, int relu, double out[3])
+{
+    double lo = v - e, hi = v + e;
+    if (relu) {
+        lo = lo > 0.0 ? lo : 0.0;
+        hi = hi > 0.0 ? hi : 0.0;
+        v = v > 0.0 ? v : 0.0;
+    }
+    double a = flip_round(C, l, lo), m = flip_round(C, l, v), z = flip_round(C, l, hi);
+    int n = 0;
+    out[n++] = m;
+    if (a != m)
+        out[n++] = a;
+    if (z != m && z != a)
+        out[n++] = z;
+    return n;
+}
+
+static int flip_layer(flip_ctx *C, int l, const double *xq);
+
+/* fix inputs i .. n_in - 1 of layer l to each of their candidates in turn, then evaluate the layer */
+static int flip_choose(flip_ctx *C, int l, double *xq, double (*cand)[3], const int *nc, int i, int n_in)
+{
+    while (i < n_in && nc[i] == 1) {
+        xq[i] = cand[i][0];
+        ++i;
+    }
+    if (i == n_in) {
+        if (++C->leaves > C->max_leaves)
+            return -1;
+        return flip_layer(C, l, xq);
+    }
+    for (int k = 0; k < nc[i]; ++k) {
+        xq[i] = cand[i][k];
+        int r = flip_choose(C, l, xq, cand, nc, i + 1, n_in);
+        if (r != 0)
+            return r;
+    }
+    return 0;
+}
+
+/* layer l with rounded inputs xq: 1 when some rounding of the later layers matches the device, 0 when none,
+ * -1 when the enumeration exceeds its limit */
+static int flip_layer(flip_ctx *C, int l, const double *xq)
+{
+    int ni = C->dims[l], no = C->dims[l + 1];
+    double pre[256], err[256];
+    for (int o = 0; o < no; ++o) {
+        double acc = 0.0, mag = 0.0;
+        for (int i = 0; i < ni; ++i) {
+            double p = C->W[C->woff[l] + (int64_t)o * ni + i] * xq[i];
+            acc += p;
+            mag += fabs(p);
+        }
+        double bb = C->b[C->boff[l] + o];
+        pre[o] = acc * C->scale[l] + bb;
+        err[o] = 4.0 * (ni + 2) * ldexp(1.0, -24) * (mag * fabs(C->scale[l]) + fabs(bb));
+    }
+    if (l + 1 == C->n_layers) {
+        for (int c = 0; c < no; ++c) {
+            double y = pre[c], t = C->tol + err[c];
+            if (C->out_half) {
+                y = oracle_round_half(y);
+                t += fabs(y) * ldexp(1.0, -11);
+            }
+            if (!(fabs(C->y_dev[c] - y) <= t))
+                return 0;
+        }
+        return 1;
+    }
+    double cand[256][3], xn[256];
+    int nc[256];
+    for (int o = 0; o < no; ++o)
+        nc[o] = flip_candidates(C, l + 1, pre[o], err[o], 1, cand[o]);
+    return flip_choose(C, l + 1, xn, cand, nc, 0, no);
+}
+
+static int flip_run(flip_ctx *C, const double *x, const double *x_err)
+{
+    int64_t wo = 0, bo = 0;
+    for (int l = 0; l < C->n_layers; ++l) {
+        C->woff[l] = wo;
+        C->boff[l] = bo;
+        wo += (int64_t)C->dims[l] * C->dims[l + 1];
+        bo += C->dims[l + 1];
+    }
+    double cand[256][3], xq[256];
+    int nc[256];
+    for (int i = 0; i < C->dims[0]; ++i)
+        nc[i] = flip_candidates(C, 0, x[i], x_err[i], 0, cand[i]);
+    C->leaves = 0;
+    return flip_choose(C, 0, xq, cand, nc, 0, C->dims[0]);
+}
+
+/* Decode network: x[dims[0]] = the exact (FP64) MLP input of one query, x_err[dims[0]] its device error bound,
+ * y_dev[C] the device's outputs.  Returns 1 if a combination of roundings within the error windows gives
+ * outputs within tol (plus half an FP16 unit of the output when out_half) of y_dev, 0 if none does, -1 if more
+ * than max_leaves combinations would have to be tried. */
+int oracle_mlp_explain(const oracle_mlp *P, const double *x, const double *x_err, const double *y_dev, double tol,
+                       int out_half, long max_leaves)
+{
+    int64_t nw = 0, nb = 0;
+    for (int l = 0; l < P->n_layers; ++l) {
+        nw += (int64_t)P->dims[l] * P->dims[l + 1];
+        nb += P->dims[l + 1];
+    }
+    double *W = malloc(sizeof(double) * (size_t)nw), *b = malloc(sizeof(double) * (size_t)nb);
+    double scale[OR_MAX_LAYERS], in_div[OR_MAX_LAYERS];
+    for (int64_t i = 0; i < nw; ++i)
+        W[i] = weight_value(P, i);
+    for (int64_t i = 0; i < nb; ++i)
+        b[i] = (double)P->biases[i];
+    for (int l = 0; l < P->n_layers; ++l) {
+        int e4 = P->precision == OR_FP8;
+        in_div[l] = e4 ? (double)P->act_scale[l] : 1.0;
+        scale[l] = e4 ? (double)P->act_scale[l] * (double)P->w_scale[l] : 1.0;
+    }
+    flip_ctx C = {P->n_layers, P->dims, W, b, scale, in_div, P->precision, y_dev, tol, out_half, 0, max_leaves,
+                  {0}, {0}};
+    int r = flip_run(&C, x, x_err);
+    free(W);
+    free(b);
+    return r;
+}
+
+/* Training network (bfloat16 operands when P->bf16): as oracle_mlp_explain, with FP32 outputs. */
+int oracle_train_mlp_explain(const oracle_train_mlp *P, const double *x, const double *x_err, const double *y_dev,
+                             double tol, long max_leaves)
+{
+    int64_t nw = 0;
+    for (int l = 0; l < P->n_layers; ++l)
+        nw += (int64_t)P->dims[l] * P->dims[l + 1];
+    double *W = malloc(sizeof(double) * (size_t)nw);
+    double one[OR_MAX_LAYERS];
+    for (int64_t i = 0; i < nw; ++i)
+        W[i] = rnd_t(P, P->W[i]);
+    for (int l = 0; l < P->n_layers; ++l)
+        one[l] = 1.0;
+    flip_ctx C = {P->n_layers, P->dims, W, P->b, one, one, P->bf16 ? OR_BF16 : OR_FP32, y_dev, tol, 0, 0,
+                  max_leaves, {0}, {0}};
+    int r = flip_run(&C, x, x_err);
+    free(W);
+    return r;
+}
+
+/*
+ * Per-element bounds for the device's training gradients (given output
+ * gradients grad_out[n][C], as oracle_train_backward_given):
+ *   A = the sum over queries and terms of |term| of every gradient element
+ *       (the same products as the gradient, each taken in absolute value);
+ *   R = the part of the device-minus-oracle difference that operand flips can
+ *       cause beyond FP32 rounding (none without bfloat16 operands, whose
+ *       rounding is the only one): for a layer input whose rounding the
+ *       error windows leave open (as in oracle_mlp_explain, with a window
+ *       grown by the flips of the layer inputs before it), |g| times the
+ *       flip's size in the weight gradient; for a ReLU unit whose
+ *       pre-activation lies within its window of 0, every term that passes
+ *       through it, in absolute value.
+ * The device gradient then lies within c A + R of the oracle's, c covering
+ * the FP32 accumulation over the batch and the two-term bfloat16 split of
+ * the output gradient.  A and R have the layout of the gradients and are
+ * accumulated into (zero them first).
+ */
+void oracle_train_backward_bounds(const oracle_train_features *F, const oracle_train_mlp *P, int64_t n,
+                                  const float *u, const float *v, const float *s, const double *grad_out,
+                                  oracle_train_grads *A, oracle_train_grads *R)
+{
+    const double ulp24 = ldexp(1.0, -24);
+    int nout = P->dims[P->n_layers];
+    for (int64_t q = 0; q < n; ++q) {
+        tap_list L;
+        train_taps(F, u[q], v[q], s[q], &L);
+        texel_eval taps[64];
+        int nin = 3 * F->n_tex + (F->lod_input ? 1 : 0);
+        double x[64], xmag[64];
+        memset(x, 0, sizeof x);
+        memset(xmag, 0, sizeof xmag);
+        for (int k = 0; k < L.n; ++k) {
+            int t = L.tex[k];
+            const double *p = F->params[t] + L.block[k] * (F->free_texels ? 3 : OR_BLOCK_PARAMS);
+            if (F->free_texels)
+                texel_free(p, &taps[k]);
+            else
+                texel_ste_v(p, F->partition[t][L.block[k]], L.texel[k], F->is_signed, F->literal, &taps[k]);
+            for (int c = 0; c < 3; ++c) {
+                x[3 * t + c] += L.weight[k] * taps[k].value[c];
+                xmag[3 * t + c] += fabs(L.weight[k] * taps[k].value[c]);
+            }
+        }
+        if (F->lod_input) {
+            double sq = isnan(s[q]) ? 0.0 : (double)s[q];
+            x[3 * F->n_tex] = sq > 0.0 ? sq : 0.0;
+        }
+        /* forward with error windows and flip sizes */
+        double act[OR_MAX_LAYERS + 1][64], fr[OR_MAX_LAYERS + 1][64], pre[OR_MAX_LAYERS][64];
+        int amb[OR_MAX_LAYERS][64];
+        for (int i = 0; i < nin; ++i) {
+            double e = 8.0 * ulp24 * xmag[i];
+            act[0][i] = rnd_t(P, x[i]);
+            double lo = rnd_t(P, x[i] - e), hi = rnd_t(P, x[i] + e);
+            fr[0][i] = P->bf16 ? fmax(fabs(hi - act[0][i]), fabs(act[0][i] - lo)) : 0.0;
+        }
+        int64_t woff = 0, boff = 0, woffs[OR_MAX_LAYERS], boffs[OR_MAX_LAYERS];
+        for (int l = 0; l < P->n_layers; ++l) {
+            int ni = P->dims[l], no = P->dims[l + 1];
+            woffs[l] = woff;
+            boffs[l] = boff;
+            for (int o = 0; o < no; ++o) {
+                double acc = 0.0, mag = 0.0, flip = 0.0;
+                for (int i = 0; i < ni; ++i) {
+                    double w = rnd_t(P, P->W[woff + (int64_t)o * ni + i]);
+                    acc += w * act[l][i];
+                    mag += fabs(w * act[l][i]);
+                    flip += fabs(w) * fr[l][i];
+                }
+                double bb = P->b[boff + o];
+                pre[l][o] = acc + bb;
+                double we = 4.0 * (ni + 2) * ulp24 * (mag + fabs(bb)) + flip;
+                amb[l][o] = 0;
+                if (l + 1 < P->n_layers) {
+                    double h = pre[l][o] > 0.0 ? pre[l][o] : 0.0;
+                    double hl = pre[l][o] - we, hh = pre[l][o] + we;
+                    act[l + 1][o] = rnd_t(P, h);
+                    double lo = rnd_t(P, hl > 0.0 ? hl : 0.0), hi = rnd_t(P, hh > 0.0 ? hh : 0.0);
+                    fr[l + 1][o] = P->bf16 ? fmax(fabs(hi - act[l + 1][o]), fabs(act[l + 1][o] - lo)) : 0.0;
+                    amb[l][o] = fabs(pre[l][o]) <= we;
+                }
+            }
+            woff += (int64_t)ni * no;
+            boff += no;
+        }
+        /* backward in absolute values: a = all terms, r = the terms the flips leave open */
+        double a[64], r[64];
+        for (int c = 0; c < nout; ++c) {
+            a[c] = fabs(grad_out[q * nout + c]);
+            r[c] = 0.0;
+        }
+        for (int l = P->n_layers - 1; l >= 0; --l) {
+            int ni = P->dims[l], no = P->dims[l + 1];
+            double ad[64], rd[64];
+            for (int i = 0; i < ni; ++i)
+                ad[i] = rd[i] = 0.0;
+            for (int o = 0; o < no; ++o) {
+                double ga = a[o], gr = r[o];
+                if (l + 1 < P->n_layers) {
+                    if (amb[l][o])
+                        gr = ga;
+                    else if (!(pre[l][o] > 0.0))
+                        ga = gr = 0.0;
+                }
+                A->b_grad[boffs[l] + o] += ga;
+                R->b_grad[boffs[l] + o] += gr;
+                for (int i = 0; i < ni; ++i) {
+                    double w = fabs(rnd_t(P, P->W[woffs[l] + (int64_t)o * ni + i]));
+                    A->W_grad[woffs[l] + (int64_t)o * ni + i] += ga * fabs(act[l][i]);
+                    R->W_grad[woffs[l] + (int64_t)o * ni + i] += gr * fabs(act[l][i]) + ga * fr[l][i];
+                    ad[i] += ga * w;
+                    rd[i] += gr * w;
+                }
+            }
+            for (int i = 0; i < ni; ++i) {
+                a[i] = ad[i];
+                r[i] = rd[i];
+            }
+        }
+        for (int k = 0; k < L.n; ++k) {
+            int t = L.tex[k];
+            texel_eval *T = &taps[k];
+            if (F->free_texels) {
+                double *ga = A->feat_grad[t] + L.block[k] * 3, *gr = R->feat_grad[t] + L.block[k] * 3;
+                for (int c = 0; c < 3; ++c) {
+                    ga[c] += a[3 * t + c] * L.weight[k] * fabs(T->d_ea[c]);
+                    gr[c] += r[3 * t + c] * L.weight[k] * fabs(T->d_ea[c]);
+                }
+                continue;
+            }
+            double *ga = A->feat_grad[t] + L.block[k] * OR_BLOCK_PARAMS;
+            double *gr = R->feat_grad[t] + L.block[k] * OR_BLOCK_PARAMS;
+            for (int c = 0; c < 3; ++c) {
+                double da = a[3 * t + c] * L.weight[k], dr = r[3 * t + c] * L.weight[k];
+                if (T->e_in_a[c]) {
+                    ga[(2 * T->region) * 3 + c] += da * fabs(T->d_ea[c]);
+                    gr[(2 * T->region) * 3 + c] += dr * fabs(T->d_ea[c]);
+                }
+                if (T->e_in_b[c]) {
+                    ga[(2 * T->region + 1) * 3 + c] += da * fabs(T->d_eb[c]);
+                    gr[(2 * T->region + 1) * 3 + c] += dr * fabs(T->d_eb[c]);
+                }
+                if (T->x_in) {
+                    ga[12 + L.texel[k]] += da * fabs(T->d_x[c]);
+                    gr[12 + L.texel[k]] += dr * fabs(T->d_x[c]);
+                }
+            }
+        }
+    }
+}
+
+/* ------------------------------------------------------------------------- */
 /* BC6H mode-10 block encoder: partition selection and initial block         */
 /* parameters from free per-texel features (Sec. 5.1)                         */
 /* ------------------------------------------------------------------------- */

@@ -22,7 +22,9 @@ static std::mutex g_scratch_mu;
 static float *g_scratch_ptr[kMaxDevices];
 
 // Device address of the scratch array on the current device (looked up on
-// the first call made with that device current).
+// the first call made with that device current).  The address stays valid
+// for the life of the device's primary context: a cudaDeviceReset ends it,
+// as it ends every material and trainer created before it.
 static cudaError_t scratch_address(float **out)
 {
     int dev = 0;
@@ -59,6 +61,10 @@ extern "C" bcf_status bcf_train_step_noalloc(bcf_trainer tr, int64_t batch, uint
     }
     if ((d_u != nullptr) != (d_v != nullptr) || (d_u != nullptr) != (d_s != nullptr)) {
         set_error("bcf_train_step_noalloc: give all of u, v, s or none");
+        return BCF_ERR_INVALID_ARG;
+    }
+    if (!d_u && tr->dev.batch_grid > 0 && batch != (int64_t)tr->dev.batch_grid * tr->dev.batch_grid) {
+        set_error("bcf_train_step_noalloc: grid batches need batch = %d^2", tr->dev.batch_grid);
         return BCF_ERR_INVALID_ARG;
     }
     TrainDev D = tr->dev;

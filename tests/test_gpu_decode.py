@@ -8,8 +8,9 @@ binding) and the oracle on the same seeded inputs:
   - trilinear features: FP32 filtering vs FP64 (relative to the magnitudes);
   - fused decode: FP32 plain path vs FP64; FP16 / BF16 / FP8 tensor-core
     paths vs the quantisation-aware FP64 oracle within 1e-3 (FP16) and 4e-3
-    (BF16, FP8) absolute per channel, error vs the unquantised FP64 oracle
-    reported.
+    (BF16, FP8) absolute per channel, every output, except rows the oracle
+    shows to be operand-rounding flips (counted); error vs the unquantised
+    FP64 oracle reported.
 """
 import math
 
@@ -160,15 +161,15 @@ def test_decode_fp32_plain_matches_fp64(variant):
     assert (np.abs(got - ref) <= tol).all(), np.max(np.abs(got - ref) / np.maximum(tol, 1e-30))
 
 
-def _quant_check(got, ref_q, tol, what):
-    err = np.abs(got - ref_q)
-    worst = err.max(axis=0)
-    frac = float((err > tol).mean())
-    # rounding-boundary flips (FP32 accumulation in the kernel vs FP64 in the oracle at an operand
-    # rounding step) may move isolated values by one operand ulp; anything systematic fails here
-    assert frac <= 1e-3, f"{what}: {frac:.2e} of outputs beyond {tol}; per-channel max {worst}"
-    assert np.all(err <= 8 * tol), f"{what}: max error {err.max()} per channel {worst}"
-    return worst, frac
+def _quant_check(got, ref_q, tol, what, mat, P, u, v, s, out_half=False):
+    """Strict parity against the quantisation-aware oracle: every output within the absolute tolerance of its
+    channel (plus half an FP16 unit when the kernel stored FP16), except where the oracle shows the miss to
+    be an operand-rounding flip -- some combination of the roundings that the kernel's FP32 error windows
+    leave open reproduces the output within the tolerance (oracle.mlp_explain).  Flips are counted."""
+    r = oracle.check_outputs(got, ref_q, tol, out_half, oracle.decode_explainer(mat, P, u, v, s, got, tol, out_half))
+    assert not r["unexplained"], (f"{what}: {len(r['unexplained'])} rows beyond {tol} are not rounding flips "
+                                  f"(first {r['unexplained'][:5]}); per-channel max {r['worst']}")
+    return r["worst"], r
 
 
 @pytest.mark.parametrize("variant", [0, 3])
@@ -186,12 +187,11 @@ def test_decode_tensor_core_paths_match_quant_aware_oracle(precision, out_dtype,
     mat = _oracle_material(w)
     ref_q = oracle.decode(mat, P, w.u, w.v, w.s, quant_aware=True, threads=8)
     ref = oracle.decode(mat, P, w.u, w.v, w.s, quant_aware=False, threads=8)
-    if out_dtype == torch.float16:
-        ref_q = ref_q.astype(np.float16).astype(np.float64)
-    tol = TOL[precision] + (np.abs(ref_q) * 2.0 ** -11 if out_dtype == torch.float16 else 0.0)
-    worst, frac = _quant_check(got, ref_q, tol, precision)
+    worst, r = _quant_check(got, ref_q, TOL[precision], precision, mat, P, w.u, w.v, w.s,
+                            out_half=out_dtype == torch.float16)
     print(f"{precision} out={out_dtype}: per-channel max |gpu - quant-aware oracle| {np.round(worst, 6)}, "
-          f"beyond-tolerance fraction {frac:.1e}; vs unquantised FP64: max {np.abs(got - ref).max(axis=0).round(5)}")
+          f"{r['beyond_tol']} of {r['outputs']} outputs beyond the tolerance, in {r['flips']} rows explained as "
+          f"rounding flips; vs unquantised FP64: max {np.abs(got - ref).max(axis=0).round(5)}")
 
 
 @pytest.mark.parametrize("variant", [0, 3])
@@ -211,7 +211,11 @@ def test_decode_edge_sizes(precision, variant):
         got = m.decode(u, v, s).cpu().numpy()
         ref = oracle.decode(_oracle_material(w), P, w.u[:n], w.v[:n], w.s[:n], quant_aware=True)
         assert got.shape == (n, 9)
-        assert np.abs(got - ref).max() <= (1e-4 if precision == "fp32" else 2e-3)
+        if precision == "fp32":
+            assert np.abs(got - ref).max() <= 1e-4
+        else:
+            _quant_check(got.astype(np.float64), ref, TOL[precision], "edge", _oracle_material(w), P, w.u[:n],
+                         w.v[:n], w.s[:n])
     e = torch.empty(0, device="cuda")
     assert m.decode(e, e, e).shape == (0, 9)
 
@@ -281,9 +285,9 @@ def test_tiled_fallbacks_and_addressing_match_oracle(case):
     a, b = _decode_both(w, "fp16", also_texunit=True)
     np.testing.assert_array_equal(a, b)
     Wst, bias, _, _ = w.weights("fp16")
-    ref_q = oracle.decode(_oracle_material(w), oracle.Mlp(w.dims, "fp16", Wst, bias), w.u, w.v, w.s,
-                          quant_aware=True, threads=8)
-    _quant_check(a.astype(np.float64), ref_q, TOL["fp16"], case)
+    P = oracle.Mlp(w.dims, "fp16", Wst, bias)
+    ref_q = oracle.decode(_oracle_material(w), P, w.u, w.v, w.s, quant_aware=True, threads=8)
+    _quant_check(a.astype(np.float64), ref_q, TOL["fp16"], case, _oracle_material(w), P, w.u, w.v, w.s)
 
 
 # --------------------------------------------------------------------------- texture-unit comparator (Sec. 5.2)
@@ -349,10 +353,10 @@ def test_full_size_screen_decode_sampled_against_oracle(variant):
     idx = np.random.default_rng(17).choice(w.n, 20000, replace=False)
     got = out[torch.from_numpy(idx).cuda()].float().cpu().numpy().astype(np.float64)
     Wst, bias, a, ws = w.weights("fp16")
-    ref_q = oracle.decode(_oracle_material(w), oracle.Mlp(w.dims, "fp16", Wst, bias, a, ws), w.u[idx], w.v[idx],
-                          w.s[idx], quant_aware=True, threads=8).astype(np.float16).astype(np.float64)
-    tol = TOL["fp16"] + np.abs(ref_q) * 2.0 ** -11
-    worst, frac = _quant_check(got, ref_q, tol, "fp16")
+    P = oracle.Mlp(w.dims, "fp16", Wst, bias, a, ws)
+    ref_q = oracle.decode(_oracle_material(w), P, w.u[idx], w.v[idx], w.s[idx], quant_aware=True, threads=8)
+    _quant_check(got, ref_q, TOL["fp16"], "fp16", _oracle_material(w), P, w.u[idx], w.v[idx], w.s[idx],
+                 out_half=True)
 
 
 @pytest.fixture(scope="module")
@@ -382,8 +386,7 @@ def test_full_size_large_frame_sampled_against_oracle(large_frame, precision):
     mat = _oracle_material(w)
     if precision != "fp32":
         ref_q = oracle.decode(mat, P, w.u[idx], w.v[idx], w.s[idx], quant_aware=True, threads=8)
-        ref_q = ref_q.astype(np.float16).astype(np.float64)
-        _quant_check(got, ref_q, TOL[precision] + np.abs(ref_q) * 2.0 ** -11, precision)
+        _quant_check(got, ref_q, TOL[precision], precision, mat, P, w.u[idx], w.v[idx], w.s[idx], out_half=True)
         return
     ref = oracle.decode(mat, P, w.u[idx], w.v[idx], w.s[idx], threads=8)
     feat = oracle.sample_features(mat, w.u[idx], w.v[idx], w.s[idx])
@@ -425,9 +428,9 @@ def test_paper_decoder_shape_12_16_9(precision):
     a, b = _decode_both(w, precision, also_texunit=True)
     np.testing.assert_array_equal(a, b)
     Wst, bias, sa, ws = w.weights(precision)
-    ref_q = oracle.decode(_oracle_material(w), oracle.Mlp(w.dims, precision, Wst, bias, sa, ws), w.u, w.v, w.s,
-                          quant_aware=True, threads=8)
-    _quant_check(a.astype(np.float64), ref_q, TOL[precision], precision)
+    P = oracle.Mlp(w.dims, precision, Wst, bias, sa, ws)
+    ref_q = oracle.decode(_oracle_material(w), P, w.u, w.v, w.s, quant_aware=True, threads=8)
+    _quant_check(a.astype(np.float64), ref_q, TOL[precision], precision, _oracle_material(w), P, w.u, w.v, w.s)
 
 
 def test_texunit_fetch_probe_sums_the_decoded_footprints():
