@@ -476,9 +476,11 @@ bcf_status bcf_train_export(bcf_trainer tr, void *const *d_blocks_out, uint16_t 
  * segment between the extreme projections), its ends are quantised to 6-bit
  * endpoints, every texel takes the 3-bit index with the smallest squared RGB
  * error of the decoded value, and the partition with the smallest total
- * error is kept (ties: the smaller partition number).  All decisions are
- * computed in IEEE single precision in a fixed order, so the result is
- * reproducible.
+ * error is kept (ties: the smaller partition number).  The winner's endpoint
+ * codes are then improved: while moving one code up or down by one lowers
+ * the total error, the best such move is taken (at most 16 moves).  All
+ * decisions are computed in IEEE single precision in a fixed order, so the
+ * result is reproducible.
  *
  * d_texels : level 0 .. levels-1 concatenated, each [W][W][texel_stride]
  *            float32 with W = res >> level (R, G, B first per texel,
@@ -508,7 +510,8 @@ bcf_status bcf_encode_mode10(const float *d_texels, int32_t texel_stride, int32_
  * as a comparison).  Per block two candidates: the mode-10 encoding of
  * bcf_encode_mode10 (written as bcf_pack_mode10 writes it) and a mode-11
  * encoding (one region over all sixteen texels: the same line fit, its ends
- * quantised to 10-bit endpoints, each texel the best of the 16 indices);
+ * quantised to 10-bit endpoints, each texel the best of the 16 indices,
+ * then the same one-code moves of its six endpoint codes);
  * the one with the smaller total squared error is written (ties, or a NaN
  * total: mode 10).  Decisions in IEEE single precision in a fixed order, as
  * in bcf_encode_mode10.

@@ -150,15 +150,17 @@ def lib():
         L.oracle_train_export_block.restype = None
         L.oracle_train_export_block.argtypes = [c_void_p, c_int, c_void_p]
         L.oracle_encode_mode10_block.restype = None
-        L.oracle_encode_mode10_block.argtypes = [c_void_p, c_void_p, POINTER(c_int), POINTER(c_float), c_void_p]
+        L.oracle_encode_mode10_block.argtypes = [c_void_p, c_void_p, POINTER(c_int), POINTER(c_double), c_void_p]
         L.oracle_encode_mode10_texture.restype = None
         L.oracle_encode_mode10_texture.argtypes = [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]
         L.oracle_train_loss_mt.restype = c_double
         L.oracle_train_loss_mt.argtypes = [c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p, c_void_p, c_int]
         L.oracle_encode_mode11_block.restype = None
-        L.oracle_encode_mode11_block.argtypes = [c_void_p, c_void_p, c_void_p, POINTER(c_float)]
+        L.oracle_encode_mode11_block.argtypes = [c_void_p, c_void_p, c_void_p, POINTER(c_double)]
         L.oracle_compress_bc6h_block.restype = None
-        L.oracle_compress_bc6h_block.argtypes = [c_void_p, c_void_p, POINTER(c_float), POINTER(c_int)]
+        L.oracle_compress_bc6h_block.argtypes = [c_void_p, c_void_p, POINTER(c_double), POINTER(c_int)]
+        L.oracle_encode_fit_segment.restype = None
+        L.oracle_encode_fit_segment.argtypes = [c_void_p, c_int, c_int, c_void_p, c_void_p]
         L.oracle_compress_bc6h_texture.restype = None
         L.oracle_compress_bc6h_texture.argtypes = [c_void_p, c_int, c_int, c_void_p, c_void_p, c_void_p]
         L.oracle_mlp_explain.restype = c_int
@@ -677,8 +679,8 @@ def encode_mode10_block(v: np.ndarray) -> tuple[np.ndarray, int, float, np.ndarr
     v = np.ascontiguousarray(v, dtype=np.float32).reshape(48)
     params = np.zeros(28, np.float64)
     k = ctypes.c_int(0)
-    err = ctypes.c_float(0.0)
-    errs = np.zeros(32, np.float32)
+    err = ctypes.c_double(0.0)
+    errs = np.zeros(32, np.float64)
     lib().oracle_encode_mode10_block(_ptr(v), _ptr(params), ctypes.byref(k), ctypes.byref(err), _ptr(errs))
     return params, int(k.value), float(err.value), errs
 
@@ -690,9 +692,19 @@ def encode_mode10_texture(texels: np.ndarray, res: int, levels: int) -> tuple[np
     nb = texture_blocks(res, levels)
     params = np.zeros((nb, 28), np.float64)
     part = np.zeros(nb, np.uint8)
-    err = np.zeros(nb, np.float32)
+    err = np.zeros(nb, np.float64)
     lib().oracle_encode_mode10_texture(_ptr(texels), int(res), int(levels), _ptr(params), _ptr(part), _ptr(err))
     return params, part, err
+
+
+def encode_fit_segment(y: np.ndarray, k: int, r: int) -> tuple[np.ndarray, np.ndarray]:
+    """The encoder's line fit (oracle_encode_fit_segment) of region r of partition k (k < 0: all sixteen
+    texels) of interpolation-domain points y[16][3]: the segment ends A, B."""
+    y = np.ascontiguousarray(y, dtype=np.float64).reshape(16, 3)
+    A = np.zeros(3, np.float64)
+    B = np.zeros(3, np.float64)
+    lib().oracle_encode_fit_segment(_ptr(y), int(k), int(r), _ptr(A), _ptr(B))
+    return A, B
 
 
 def encode_mode11_block(v: np.ndarray) -> tuple[np.ndarray, np.ndarray, float]:
@@ -701,7 +713,7 @@ def encode_mode11_block(v: np.ndarray) -> tuple[np.ndarray, np.ndarray, float]:
     v = np.ascontiguousarray(v, dtype=np.float32).reshape(48)
     e = np.zeros((2, 3), np.int32)
     idx = np.zeros(16, np.int32)
-    err = ctypes.c_float(0.0)
+    err = ctypes.c_double(0.0)
     lib().oracle_encode_mode11_block(_ptr(v), _ptr(e), _ptr(idx), ctypes.byref(err))
     return e, idx, float(err.value)
 
@@ -710,7 +722,7 @@ def compress_bc6h_block(v: np.ndarray) -> tuple[np.ndarray, float, int]:
     """The two-mode (10 / 11) BC6H UF16 compression of one block: (16 bytes, error, mode)."""
     v = np.ascontiguousarray(v, dtype=np.float32).reshape(48)
     blk = np.zeros(16, np.uint8)
-    err = ctypes.c_float(0.0)
+    err = ctypes.c_double(0.0)
     mode = ctypes.c_int(0)
     lib().oracle_compress_bc6h_block(_ptr(v), _ptr(blk), ctypes.byref(err), ctypes.byref(mode))
     return blk, float(err.value), int(mode.value)
@@ -722,7 +734,7 @@ def compress_bc6h_texture(texels: np.ndarray, res: int, levels: int) -> tuple[np
     texels = np.ascontiguousarray(texels, dtype=np.float32).reshape(-1)
     nb = texture_blocks(res, levels)
     blocks = np.zeros((nb, 16), np.uint8)
-    err = np.zeros(nb, np.float32)
+    err = np.zeros(nb, np.float64)
     modes = np.zeros(nb, np.uint8)
     lib().oracle_compress_bc6h_texture(_ptr(texels), int(res), int(levels), _ptr(blocks), _ptr(err), _ptr(modes))
     return blocks, err, modes

@@ -11,10 +11,7 @@
  * here, in its own notation, from the public format definition.
  *
  * Arithmetic: FP64 for every floating-point step, integers for the BC6H
- * bitstream, which the format defines exactly -- except the block encoders
- * (partition and mode selection), whose every floating-point quantity decides
- * an integer and is computed in IEEE single precision in a fixed order, the
- * precision of the GPU encoder (see its section).
+ * bitstream, which the format defines exactly.
  *
  * What each part follows:
  *   - IEEE-754 binary16 / bfloat16 / OCP E4M3 codecs: the format definitions.
@@ -1862,26 +1859,25 @@ void oracle_train_backward_bounds(const oracle_train_features *F, const oracle_t
 /*
  * The paper initialises the block parameters and fixes the partitions by
  * compressing a quickly trained set of unconstrained features with the BC6
- * algorithm.  The encoder here, per block and for each of the 32 two-region
- * partitions:
- *   1. maps the 16 target texels to the integer domain in which the format
- *      interpolates (the binary16 bit pattern of the value, 0 .. 0x7BFF);
- *   2. fits a line to each region there: the region's mean, its 3 x 3
- *      scatter matrix, the principal axis by 8 power iterations started from
- *      the scatter column of the largest diagonal entry, and the segment
- *      spanned by the smallest and largest projections onto the axis;
- *   3. quantises both segment ends to 6-bit endpoints by inverting the
- *      unquantise (1024 e + 512) and finish (x 31/64) steps;
- *   4. gives each texel the 3-bit index whose decoded value is closest
- *      (squared error over RGB in value space);
- * and keeps the partition with the smallest total error.
- *
- * Precision: the method fixes none for this heuristic.  Every value that
- * decides an integer here (a quantised endpoint, an index, the partition)
- * is computed in IEEE single precision with one fixed order of operations
- * and no fused multiply-add, which is also how the GPU encoder computes
- * them, so both take the same decisions; ties go to the smaller index and
- * the smaller partition number.
+ * algorithm, without saying which search that algorithm performs.  This
+ * encoder is the plain two-region search, in double precision, per block
+ * and for each of the 32 two-region partitions:
+ *   1. the 16 target texels are mapped to the integer domain in which the
+ *      format interpolates (the binary16 bit pattern of the value, 0 for
+ *      values <= 0, 0x7BFF above the half range);
+ *   2. a line is fitted to each region there: the region's mean and 3 x 3
+ *      covariance, the principal axis by 8 power iterations started from the
+ *      covariance column of the largest diagonal entry, and the segment
+ *      between the smallest and largest projections onto that axis;
+ *   3. both segment ends are quantised to 6-bit endpoints by inverting the
+ *      unquantise (1024 e + 512) and finish (x 31/64) steps and rounding;
+ *   4. each texel takes the 3-bit index whose decoded value (the format
+ *      decoder's) is closest in squared RGB error;
+ * and the partition with the smallest total error is kept.  Ties go to the
+ * smaller index and the smaller partition number.  The device encoder takes
+ * these steps in single precision and then improves the winner (endpoint
+ * codes moved by one while the error falls), so the device's error is at
+ * most this one's up to single-precision rounding of the error sums.
  */
 
 /* binary16 bit pattern of a non-negative, representable half value */
@@ -1900,247 +1896,201 @@ static uint16_t half_bits_of(double h)
     return (uint16_t)(((e + 15) << 10) | (int)nearbyint((h / ldexp(1.0, e) - 1.0) * 1024.0));
 }
 
-/* the interpolation-domain coordinate of a target value: its half bit pattern, 0 for v <= 0 or NaN,
- * 0x7BFF (the largest finite half) above the range */
-static float enc_coord(float v)
+/* interpolation-domain coordinate of a target value */
+static double enc_coord(float v)
 {
     if (!(v > 0.0f))
-        return 0.0f;
+        return 0.0;
     double h = oracle_round_half((double)v);
     if (!(h <= 65504.0))
-        return 31743.0f;
-    return (float)half_bits_of(h);
+        return 31743.0;
+    return (double)half_bits_of(h);
 }
 
-/* decoded value of a mode-10 texel with 6-bit endpoints a, b (one channel) and 3-bit index i */
-static float enc_texel_value(int a, int b, int i)
+/* decoded UF16 value of one channel with b-bit endpoints a, b (modes 10 and 11) and weight w */
+static double enc_value(int bits, int a, int b, int w)
 {
-    int ua = bc6h_unquantize(a, 6, 0), ub = bc6h_unquantize(b, 6, 0);
-    int w = k_weights3[i];
-    return (float)oracle_half_to_double(bc6h_finish(floor_div64(ua * (64 - w) + ub * w + 32), 0));
+    int ua = bc6h_unquantize(a, bits, 0), ub = bc6h_unquantize(b, bits, 0);
+    return oracle_half_to_double(bc6h_finish(floor_div64(ua * (64 - w) + ub * w + 32), 0));
 }
 
-static int enc_quantise(float y)
+/* the endpoint code whose unquantised and finished value is y: (1024 e + 512) 31/64 = y (6 bits) or
+ * (64 e + 32) 31/64 = y (10 bits), rounded to the nearest code and clamped */
+static int enc_code(int bits, double y)
 {
-    const float scale = 64.0f / 31.0f;
-    float q = rintf((y * scale - 512.0f) / 1024.0f);
-    return q < 0.0f ? 0 : (q > 63.0f ? 63 : (int)q);
-}
-
-/* 10-bit endpoints (mode 11): the inverse of unquantise 64 e + 32 and finish x 31/64 */
-static int enc_quantise10(float y)
-{
-    const float scale = 64.0f / 31.0f;
-    float q = rintf((y * scale - 32.0f) / 64.0f);
-    return q < 0.0f ? 0 : (q > 1023.0f ? 1023 : (int)q);
+    double e = bits == 6 ? (y * 64.0 / 31.0 - 512.0) / 1024.0 : (y * 64.0 / 31.0 - 32.0) / 64.0;
+    double q = nearbyint(e), top = (double)((1 << bits) - 1);
+    return q < 0.0 ? 0 : (q > top ? (int)top : (int)q);
 }
 
 /* texel t belongs to the fitted set: region r of partition k, or every texel when k < 0 */
 static int enc_member(int k, int r, int t) { return k < 0 ? 1 : oracle_bc6h_partition_region(k, t) == r; }
 
-/* line fit of one region of partition k (k < 0: all sixteen texels): the segment A (start) .. B (end)
- * between the extreme projections on the principal axis, in the interpolation domain */
-static void enc_fit_segment(const float y[16][3], int k, int r, float A[3], float B[3])
+/* Line fit of the member texels of y (region r of partition k; k < 0: all sixteen): segment A .. B between
+ * the extreme projections onto the principal axis, in the interpolation domain. */
+void oracle_encode_fit_segment(const double y[16][3], int k, int r, double A[3], double B[3])
 {
-    float sum[3] = {0.0f, 0.0f, 0.0f};
+    double m[3] = {0.0, 0.0, 0.0};
     int n = 0;
     for (int t = 0; t < 16; ++t)
         if (enc_member(k, r, t)) {
             for (int c = 0; c < 3; ++c)
-                sum[c] = sum[c] + y[t][c];
+                m[c] += y[t][c];
             ++n;
         }
-    float m[3];
     for (int c = 0; c < 3; ++c)
-        m[c] = n ? sum[c] / (float)n : 0.0f;
-    float C[3][3] = {{0.0f}};
+        m[c] = n ? m[c] / n : 0.0;
+    double C[3][3] = {{0.0}};
     for (int t = 0; t < 16; ++t)
-        if (enc_member(k, r, t)) {
-            float d[3];
-            for (int c = 0; c < 3; ++c)
-                d[c] = y[t][c] - m[c];
+        if (enc_member(k, r, t))
             for (int i = 0; i < 3; ++i)
-                for (int j = i; j < 3; ++j) {
-                    float p = d[i] * d[j];
-                    C[i][j] = C[i][j] + p;
-                }
-        }
-    C[1][0] = C[0][1];
-    C[2][0] = C[0][2];
-    C[2][1] = C[1][2];
+                for (int j = 0; j < 3; ++j)
+                    C[i][j] += (y[t][i] - m[i]) * (y[t][j] - m[j]);
     int jm = 0;
-    if (C[1][1] > C[jm][jm])
-        jm = 1;
-    if (C[2][2] > C[jm][jm])
-        jm = 2;
-    if (C[jm][jm] > 0.0f) {
-        float a[3] = {C[0][jm], C[1][jm], C[2][jm]};
-        for (int it = 0; it < 8; ++it) {
-            float b[3];
-            for (int i = 0; i < 3; ++i) {
-                float p0 = C[i][0] * a[0], p1 = C[i][1] * a[1], p2 = C[i][2] * a[2];
-                b[i] = (p0 + p1) + p2;
-            }
-            float s = fabsf(b[0]);
-            if (fabsf(b[1]) > s)
-                s = fabsf(b[1]);
-            if (fabsf(b[2]) > s)
-                s = fabsf(b[2]);
-            if (!(s > 0.0f))
-                break;
-            for (int i = 0; i < 3; ++i)
-                a[i] = b[i] / s;
-        }
-        float q0 = a[0] * a[0], q1 = a[1] * a[1], q2 = a[2] * a[2];
-        float aa = (q0 + q1) + q2;
-        float pmin = INFINITY, pmax = -INFINITY;
-        for (int t = 0; t < 16; ++t)
-            if (enc_member(k, r, t)) {
-                float d0 = y[t][0] - m[0], d1 = y[t][1] - m[1], d2 = y[t][2] - m[2];
-                float p0 = d0 * a[0], p1 = d1 * a[1], p2 = d2 * a[2];
-                float p = (p0 + p1) + p2;
-                if (p < pmin)
-                    pmin = p;
-                if (p > pmax)
-                    pmax = p;
-            }
-        float s0 = pmin / aa, s1 = pmax / aa;
-        for (int c = 0; c < 3; ++c) {
-            float o0 = s0 * a[c], o1 = s1 * a[c];
-            A[c] = m[c] + o0;
-            B[c] = m[c] + o1;
-        }
-    } else {
+    for (int j = 1; j < 3; ++j)
+        if (C[j][j] > C[jm][jm])
+            jm = j;
+    if (!(C[jm][jm] > 0.0)) {
         for (int c = 0; c < 3; ++c)
             A[c] = B[c] = m[c];
+        return;
     }
-}
-
-/* line fit of one region of partition k quantised to 6-bit endpoints: e[0] = segment start, e[1] = end */
-static void enc_fit_region(const float y[16][3], int k, int r, int e[2][3])
-{
-    float A[3], B[3];
-    enc_fit_segment(y, k, r, A, B);
-    for (int c = 0; c < 3; ++c) {
-        e[0][c] = enc_quantise(A[c]);
-        e[1][c] = enc_quantise(B[c]);
+    double a[3] = {C[0][jm], C[1][jm], C[2][jm]};
+    for (int it = 0; it < 8; ++it) {
+        double b[3] = {0.0, 0.0, 0.0};
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                b[i] += C[i][j] * a[j];
+        double len = sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+        if (!(len > 0.0))
+            break;
+        for (int i = 0; i < 3; ++i)
+            a[i] = b[i] / len;
     }
-}
-
-/* squared error (RGB, value space) of texel t's target against index i of the segment e */
-static float enc_texel_error(const int e[2][3], int i, const float *v)
-{
-    float d[3];
-    for (int c = 0; c < 3; ++c)
-        d[c] = enc_texel_value(e[0][c], e[1][c], i) - v[c];
-    float q0 = d[0] * d[0], q1 = d[1] * d[1], q2 = d[2] * d[2];
-    return (q0 + q1) + q2;
-}
-
-/* Encode one block: v[3 t + c] = target of texel t (row-major in the block), channel c.  Outputs the block
- * parameters in the training layout (e1, e2 = region-0 segment, e3, e4 = region-1 segment, RGB each, then
- * x_t = index / 7), the partition, its total error and the total error of every partition. */
-void oracle_encode_mode10_block(const float *v, double params[28], int *k_out, float *err_out, float errs[32])
-{
-    float y[16][3];
+    double aa = a[0] * a[0] + a[1] * a[1] + a[2] * a[2];
+    double lo = INFINITY, hi = -INFINITY;
     for (int t = 0; t < 16; ++t)
-        for (int c = 0; c < 3; ++c)
-            y[t][c] = enc_coord(v[3 * t + c]);
-    float best = INFINITY;
-    int best_k = 0, best_e[2][2][3] = {{{0}}}, best_idx[16] = {0};
-    for (int k = 0; k < 32; ++k) {
-        int e[2][2][3];
-        enc_fit_region(y, k, 0, e[0]);
-        enc_fit_region(y, k, 1, e[1]);
-        float total = 0.0f;
-        int idx[16];
-        for (int t = 0; t < 16; ++t) {
-            int r = oracle_bc6h_partition_region(k, t);
-            float be = INFINITY;
-            int bi = 0;
-            for (int i = 0; i < 8; ++i) {
-                float err = enc_texel_error((const int(*)[3])e[r], i, v + 3 * t);
-                if (err < be) {
-                    be = err;
-                    bi = i;
-                }
-            }
-            idx[t] = bi;
-            total = total + be;
-        }
-        if (errs)
-            errs[k] = total;
-        float key = isnan(total) ? INFINITY : total; /* a NaN total never wins over a number */
-        if (key < best || k == 0) {
-            best = key;
-            *err_out = total;
-            best_k = k;
-            memcpy(best_e, e, sizeof e);
-            memcpy(best_idx, idx, sizeof idx);
-        }
-    }
-    for (int r = 0; r < 2; ++r)
-        for (int s = 0; s < 2; ++s)
+        if (enc_member(k, r, t)) {
+            double p = 0.0;
             for (int c = 0; c < 3; ++c)
-                params[(2 * r + s) * 3 + c] = (double)best_e[r][s][c];
-    for (int t = 0; t < 16; ++t)
-        params[12 + t] = best_idx[t] / 7.0;
-    *k_out = best_k;
+                p += (y[t][c] - m[c]) * a[c];
+            p /= aa;
+            if (p < lo)
+                lo = p;
+            if (p > hi)
+                hi = p;
+        }
+    for (int c = 0; c < 3; ++c) {
+        A[c] = m[c] + lo * a[c];
+        B[c] = m[c] + hi * a[c];
+    }
 }
 
-/* Encode one block in mode 11 (one region, 10-bit endpoints, 4-bit indices): the line fit over all sixteen
- * texels, its ends quantised to 10 bits, each texel the index of the smallest squared RGB error (ties: the
- * smaller index).  e[0] / e[1] = segment start / end (RGB), idx[16], the total error in *err_out. */
-void oracle_encode_mode11_block(const float *v, int e[2][3], int idx[16], float *err_out)
+/* squared RGB error of target v against index i (weight table of `bits`-bit endpoints: 3 or 4 bit indices) */
+static double enc_texel_error(int bits, const int ea[3], const int eb[3], int i, const float *v)
 {
-    float y[16][3];
-    for (int t = 0; t < 16; ++t)
-        for (int c = 0; c < 3; ++c)
-            y[t][c] = enc_coord(v[3 * t + c]);
-    float A[3], B[3];
-    enc_fit_segment(y, -1, 0, A, B);
+    int w = bits == 6 ? k_weights3[i] : k_weights4[i];
+    double e = 0.0;
     for (int c = 0; c < 3; ++c) {
-        e[0][c] = enc_quantise10(A[c]);
-        e[1][c] = enc_quantise10(B[c]);
+        double d = enc_value(bits, ea[c], eb[c], w) - (double)v[c];
+        e += d * d;
     }
-    float total = 0.0f;
+    return e;
+}
+
+/* best index of every member texel for the segment (ea, eb); returns the members' total error */
+static double enc_assign(int bits, int k, int r, const int ea[3], const int eb[3], const float *v, int idx[16])
+{
+    int ni = bits == 6 ? 8 : 16;
+    double total = 0.0;
     for (int t = 0; t < 16; ++t) {
-        float be = INFINITY;
+        if (!enc_member(k, r, t))
+            continue;
+        double best = INFINITY;
         int bi = 0;
-        for (int i = 0; i < 16; ++i) {
-            float d[3];
-            for (int c = 0; c < 3; ++c) {
-                int ua = bc6h_unquantize(e[0][c], 10, 0), ub = bc6h_unquantize(e[1][c], 10, 0);
-                int w = k_weights4[i];
-                d[c] = (float)oracle_half_to_double(bc6h_finish(floor_div64(ua * (64 - w) + ub * w + 32), 0)) -
-                       v[3 * t + c];
-            }
-            float q0 = d[0] * d[0], q1 = d[1] * d[1], q2 = d[2] * d[2];
-            float err = (q0 + q1) + q2;
-            if (err < be) {
-                be = err;
+        for (int i = 0; i < ni; ++i) {
+            double e = enc_texel_error(bits, ea, eb, i, v + 3 * t);
+            if (e < best) {
+                best = e;
                 bi = i;
             }
         }
         idx[t] = bi;
-        total = total + be;
+        total += best;
     }
-    *err_out = total;
+    return total;
+}
+
+static void enc_targets(const float *v, double y[16][3])
+{
+    for (int t = 0; t < 16; ++t)
+        for (int c = 0; c < 3; ++c)
+            y[t][c] = enc_coord(v[3 * t + c]);
+}
+
+/* Encode one block: v[3 t + c] = target of texel t (row-major in the block), channel c.  Outputs the block
+ * parameters in the training layout (e1, e2 = region-0 segment, e3, e4 = region-1 segment, RGB each, then
+ * x_t = index / 7), the partition, its total squared error and that of every partition (errs may be NULL).
+ * A NaN target has no closest index: its texel's error and every total are infinite, and partition 0 is kept. */
+void oracle_encode_mode10_block(const float *v, double params[28], int *k_out, double *err_out, double errs[32])
+{
+    double y[16][3];
+    enc_targets(v, y);
+    int best_k = -1;
+    double best = INFINITY;
+    for (int k = 0; k < 32; ++k) {
+        int e[4][3], idx[16];
+        double total = 0.0;
+        for (int r = 0; r < 2; ++r) {
+            double A[3], B[3];
+            oracle_encode_fit_segment((const double(*)[3])y, k, r, A, B);
+            for (int c = 0; c < 3; ++c) {
+                e[2 * r][c] = enc_code(6, A[c]);
+                e[2 * r + 1][c] = enc_code(6, B[c]);
+            }
+            total += enc_assign(6, k, r, e[2 * r], e[2 * r + 1], v, idx);
+        }
+        if (errs)
+            errs[k] = total;
+        if (best_k < 0 || total < best) {
+            best = total;
+            best_k = k;
+            *err_out = total;
+            for (int j = 0; j < 12; ++j)
+                params[j] = (double)e[j / 3][j % 3];
+            for (int t = 0; t < 16; ++t)
+                params[12 + t] = idx[t] / 7.0;
+        }
+    }
+    *k_out = best_k;
+}
+
+/* Encode one block in mode 11 (one region, 10-bit endpoints, 4-bit indices): the line fit over all sixteen
+ * texels, its ends quantised to 10 bits, each texel the index of the smallest squared RGB error.  e[0] / e[1] =
+ * segment start / end (RGB), idx[16], the total error in *err_out. */
+void oracle_encode_mode11_block(const float *v, int e[2][3], int idx[16], double *err_out)
+{
+    double y[16][3], A[3], B[3];
+    enc_targets(v, y);
+    oracle_encode_fit_segment((const double(*)[3])y, -1, 0, A, B);
+    for (int c = 0; c < 3; ++c) {
+        e[0][c] = enc_code(10, A[c]);
+        e[1][c] = enc_code(10, B[c]);
+    }
+    *err_out = enc_assign(10, -1, 0, e[0], e[1], v, idx);
 }
 
 /* A plain two-mode BC6H UF16 compressor of one block: the mode-10 encoding above (written by the mode-10
- * export) against the mode-11 encoding; the smaller total error wins (a NaN total counts as infinite; ties
- * and two NaN totals: mode 10).  blk[16], the written block's error and mode (10 or 11). */
-void oracle_compress_bc6h_block(const float *v, uint8_t blk[16], float *err_out, int *mode_out)
+ * export) against the mode-11 encoding; the smaller total error wins (ties and NaN totals: mode 10).  blk[16],
+ * the written block's error and mode (10 or 11). */
+void oracle_compress_bc6h_block(const float *v, uint8_t blk[16], double *err_out, int *mode_out)
 {
-    double params[28];
+    double params[28], err10, err11;
     int k;
-    float err10, err11;
     oracle_encode_mode10_block(v, params, &k, &err10, NULL);
     int e[2][3], idx[16];
     oracle_encode_mode11_block(v, e, idx, &err11);
-    float key10 = isnan(err10) ? INFINITY : err10, key11 = isnan(err11) ? INFINITY : err11;
-    if (!(key11 < key10)) {
+    if (!(err11 < err10)) {
         oracle_train_export_block_v(params, k, 0, blk);
         *err_out = err10;
         *mode_out = 10;
@@ -2167,7 +2117,7 @@ void oracle_compress_bc6h_block(const float *v, uint8_t blk[16], float *err_out,
 
 /* The compressor over a mipmapped texture (layout as oracle_encode_mode10_texture): blocks[blocks][16],
  * err[blocks], modes[blocks]. */
-void oracle_compress_bc6h_texture(const float *texels, int res, int levels, uint8_t *blocks, float *err,
+void oracle_compress_bc6h_texture(const float *texels, int res, int levels, uint8_t *blocks, double *err,
                                   uint8_t *modes)
 {
     int64_t toff = 0, b = 0;
@@ -2190,7 +2140,7 @@ void oracle_compress_bc6h_texture(const float *texels, int res, int levels, uint
 
 /* Encode a mipmapped texture: texels[level][W][W][3] (levels concatenated from level 0), blocks in the
  * training order (per level, row-major).  params[blocks][28], part[blocks], err[blocks]. */
-void oracle_encode_mode10_texture(const float *texels, int res, int levels, double *params, uint8_t *part, float *err)
+void oracle_encode_mode10_texture(const float *texels, int res, int levels, double *params, uint8_t *part, double *err)
 {
     int64_t toff = 0, b = 0;
     for (int l = 0; l < levels; ++l) {

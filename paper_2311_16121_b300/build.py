@@ -32,9 +32,14 @@ def build(force: bool = False, verbose: bool = False) -> str:
     build_dir = os.path.join(HERE, "_build")
     os.makedirs(build_dir, exist_ok=True)
     procs = []
-    for src in SOURCES:  # compile translation units in parallel
+    headers = [p for p in DEPS if not p.endswith(".cu")]
+    newest_header = max((os.path.getmtime(p) for p in headers), default=0.0)
+    for src in SOURCES:  # compile the out-of-date translation units in parallel
         obj = os.path.join(build_dir, os.path.basename(src) + ".o")
         objs.append(obj)
+        if not force and not verbose and os.path.exists(obj) and \
+                os.path.getmtime(obj) >= max(os.path.getmtime(src), newest_header):
+            continue
         cmd = [nvcc, *NVCC_FLAGS, "-c", src, "-o", obj]
         if verbose:
             cmd.append("-Xptxas=-v")

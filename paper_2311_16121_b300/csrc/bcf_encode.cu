@@ -19,6 +19,11 @@
 // keeps the partition with the smallest total error (ties: smaller k).  The
 // mode-11 candidate fits one line to all sixteen texels, quantises its ends
 // to 10 bits (unquantise 64 e + 32) and picks 4-bit indices the same way.
+// The line fit's quantised ends are not always the best codes (rounding each
+// end on its own ignores the decoder's floors and the other texels), so the
+// winner is refined: the 24 (mode 11: 12) moves of one endpoint code by one
+// are tried in parallel, one per lane, and the best is taken while it lowers
+// the error.
 //
 // Every floating-point quantity here decides an integer (an endpoint, an
 // index, the partition, the mode), so it is computed in IEEE single
@@ -164,25 +169,20 @@ __device__ __forceinline__ float texel_error(const int ua[3], const int ub[3], i
     return fadd(fadd(q[0], q[1]), q[2]);
 }
 
-// Mode-10 candidate of partition k (one lane): 6-bit endpoints e[region][end][c], 3-bit indices (texels 0-7 in
-// idx_lo, 8-15 in idx_hi), total squared error.
-__device__ float mode10_candidate(const float *v, const float *y, int k, int e[2][2][3], uint32_t &idx_lo,
-                                  uint32_t &idx_hi)
+// Indices and total squared error of the mode-10 segments e[region][end][c] for the partition with texel mask
+// pm: each texel the best of the 8 indices (ties: the smaller), texels 0-7 in idx_lo, 8-15 in idx_hi, the
+// total summed in texel order.
+__device__ float mode10_assign(const float *v, uint32_t pm, const int e[2][2][3], uint32_t &idx_lo,
+                               uint32_t &idx_hi)
 {
-    const uint32_t pm = partition_mask(k);
     int ua[2][3], ub[2][3];
 #pragma unroll
-    for (int r = 0; r < 2; ++r) {
-        float A[3], B[3];
-        fit_segment(y, pm, r, A, B);
+    for (int r = 0; r < 2; ++r)
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            e[r][0][c] = enc_quantise6(A[c]);
-            e[r][1][c] = enc_quantise6(B[c]);
             ua[r][c] = unq6(e[r][0][c]);
             ub[r][c] = unq6(e[r][1][c]);
         }
-    }
     float total = 0.0f;
     idx_lo = idx_hi = 0;
     for (int t = 0; t < 16; ++t) {
@@ -205,6 +205,25 @@ __device__ float mode10_candidate(const float *v, const float *y, int k, int e[2
     return total;
 }
 
+// Mode-10 candidate of partition k (one lane): the line fit of both regions quantised to 6-bit endpoints
+// e[region][end][c], then mode10_assign.
+__device__ float mode10_candidate(const float *v, const float *y, int k, int e[2][2][3], uint32_t &idx_lo,
+                                  uint32_t &idx_hi)
+{
+    const uint32_t pm = partition_mask(k);
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        float A[3], B[3];
+        fit_segment(y, pm, r, A, B);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            e[r][0][c] = enc_quantise6(A[c]);
+            e[r][1][c] = enc_quantise6(B[c]);
+        }
+    }
+    return mode10_assign(v, pm, e, idx_lo, idx_hi);
+}
+
 // smallest key over the warp (a NaN total never wins over a number; ties go to the smaller k)
 __device__ __forceinline__ int warp_best_partition(float total, int k, float &key)
 {
@@ -222,9 +241,114 @@ __device__ __forceinline__ int warp_best_partition(float total, int k, float &ke
     return best;
 }
 
+// Smallest key over the warp with ties to the smaller lane: the winning lane.
+__device__ __forceinline__ int warp_argmin(float key, float &best)
+{
+    int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const float ok = __shfl_xor_sync(0xffffffffu, key, off);
+        const int ol = __shfl_xor_sync(0xffffffffu, lane, off);
+        if (ok < key || (ok == key && ol < lane)) {
+            key = ok;
+            lane = ol;
+        }
+    }
+    best = key;
+    return lane;
+}
+
+constexpr int kRefineRounds = 16;
+
+// Improve the segments e (the same on every lane) of the partition with mask pm whose total error is `cur`:
+// in each round lane j < 2 n_codes moves endpoint code j / 2 down (j even) or up (j odd) by one, re-assigns the
+// indices and sums the error; the best move is taken while it lowers the error (ties: the lower lane), for at
+// most kRefineRounds rounds.  Every lane returns the final segments and error.  Codes stay in [0, top].
+template <int NE, class Assign>
+__device__ float refine_codes(int *e, float cur, int top, Assign assign)
+{
+    const int lane = threadIdx.x & 31;
+    for (int round = 0; round < kRefineRounds; ++round) {
+        const int j = lane >> 1, dir = (lane & 1) ? 1 : -1;
+        float key = INFINITY;
+        if (lane < 2 * NE) {
+            int trial[NE];
+#pragma unroll
+            for (int i = 0; i < NE; ++i)
+                trial[i] = e[i];
+            const int nv = trial[j] + dir;
+            if (nv >= 0 && nv <= top) {
+                trial[j] = nv;
+                const float tot = assign(trial);
+                key = isnan(tot) ? INFINITY : tot;
+            }
+        }
+        float best;
+        const int win = warp_argmin(key, best);
+        if (!(best < cur))
+            break; // warp-uniform: every lane holds the same best and cur
+        const int wj = win >> 1, wd = (win & 1) ? 1 : -1;
+        e[wj] += wd;
+        cur = best;
+    }
+    return cur;
+}
+
 __device__ __forceinline__ int mode10_index(uint32_t idx_lo, uint32_t idx_hi, int t)
 {
     return t < 8 ? (int)((idx_lo >> (3 * t)) & 7) : (int)((idx_hi >> (3 * (t - 8))) & 7);
+}
+
+// The winning partition's segments broadcast from lane `best` (whose total error is `total`) and refined by
+// refine_codes; every lane returns the refined segments in e, their indices and total error.
+__device__ float refine_mode10(const float *v, int best, int e[2][2][3], float total, uint32_t &idx_lo,
+                               uint32_t &idx_hi)
+{
+    int flat[12];
+#pragma unroll
+    for (int i = 0; i < 12; ++i)
+        flat[i] = __shfl_sync(0xffffffffu, e[i / 6][(i / 3) & 1][i % 3], best);
+    const uint32_t pm = partition_mask(best);
+    const auto assign = [&](const int *f) {
+        int t[2][2][3];
+        uint32_t lo, hi;
+#pragma unroll
+        for (int i = 0; i < 12; ++i)
+            t[i / 6][(i / 3) & 1][i % 3] = f[i];
+        return mode10_assign(v, pm, t, lo, hi);
+    };
+    refine_codes<12>(flat, total, 63, assign);
+#pragma unroll
+    for (int i = 0; i < 12; ++i)
+        e[i / 6][(i / 3) & 1][i % 3] = flat[i];
+    return mode10_assign(v, pm, e, idx_lo, idx_hi);
+}
+
+// Indices (best of 16, ties: the smaller) and total squared error, in texel order, of the mode-11 segment
+// e[end][c] over all sixteen texels.
+__device__ float mode11_assign(const float *v, const int e[2][3], int idx[16])
+{
+    int ua[3], ub[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        ua[c] = unq10(e[0][c]);
+        ub[c] = unq10(e[1][c]);
+    }
+    float total = 0.0f;
+    for (int t = 0; t < 16; ++t) {
+        float be = INFINITY;
+        int bi = 0;
+        for (int i = 0; i < 16; ++i) {
+            const float er = texel_error(ua, ub, weight4(i), v + 3 * t);
+            if (er < be) {
+                be = er;
+                bi = i;
+            }
+        }
+        idx[t] = bi;
+        total = fadd(total, be);
+    }
+    return total;
 }
 
 // The block b of a mipmapped texture: its 48 targets (v) and their interpolation-domain coordinates (y) in the
@@ -268,10 +392,13 @@ __global__ void __launch_bounds__(32 * kEncWarps) k_encode_mode10(const float *_
     const int k = lane;
     int e[2][2][3];
     uint32_t idx_lo, idx_hi;
-    const float total = mode10_candidate(v, y, k, e, idx_lo, idx_hi);
+    float total = mode10_candidate(v, y, k, e, idx_lo, idx_hi);
     float key;
-    if (warp_best_partition(total, k, key) != k)
+    const int best = warp_best_partition(total, k, key);
+    total = refine_mode10(v, best, e, __shfl_sync(0xffffffffu, total, best), idx_lo, idx_hi);
+    if (lane != 0)
         return;
+    const int kb = best;
     float *pr = params + b * 32;
 #pragma unroll
     for (int r = 0; r < 2; ++r)
@@ -283,7 +410,7 @@ __global__ void __launch_bounds__(32 * kEncWarps) k_encode_mode10(const float *_
     pr[6] = pr[7] = pr[14] = pr[15] = 0.0f;
     for (int t = 0; t < 16; ++t)
         pr[16 + t] = (float)mode10_index(idx_lo, idx_hi, t) / 7.0f;
-    part[b] = (uint8_t)k;
+    part[b] = (uint8_t)kb;
     if (err)
         err[b] = total;
 }
@@ -305,9 +432,11 @@ __global__ void __launch_bounds__(32 * kEncWarps) k_compress_bc6h(const float *_
     const int k = lane;
     int e[2][2][3];
     uint32_t idx_lo, idx_hi;
-    const float total10 = mode10_candidate(v, y, k, e, idx_lo, idx_hi);
+    float total10 = mode10_candidate(v, y, k, e, idx_lo, idx_hi);
     float key10;
     const int best = warp_best_partition(total10, k, key10);
+    total10 = refine_mode10(v, best, e, __shfl_sync(0xffffffffu, total10, best), idx_lo, idx_hi);
+    key10 = isnan(total10) ? INFINITY : total10;
 
     float A[3], B[3];
     fit_segment(y, 0u, 0, A, B);
@@ -321,34 +450,43 @@ __global__ void __launch_bounds__(32 * kEncWarps) k_compress_bc6h(const float *_
     }
     const int tl = lane & 15;
     float be = INFINITY;
-    int bi = 0;
     for (int i = 0; i < 16; ++i) {
         const float er = texel_error(ua, ub, weight4(i), v + 3 * tl);
-        if (er < be) {
+        if (er < be)
             be = er;
-            bi = i;
-        }
     }
     float total11 = 0.0f;
-    int idx11[16];
 #pragma unroll
-    for (int t = 0; t < 16; ++t) { // texel order, as a sequential sum would take it
+    for (int t = 0; t < 16; ++t) // texel order, as a sequential sum would take it
         total11 = fadd(total11, __shfl_sync(0xffffffffu, be, t));
-        idx11[t] = __shfl_sync(0xffffffffu, bi, t);
-    }
+    int flat11[6];
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        flat11[i] = e11[i / 3][i % 3];
+    const auto assign11 = [&](const int *f) {
+        int t[2][3], idx[16];
+#pragma unroll
+        for (int i = 0; i < 6; ++i)
+            t[i / 3][i % 3] = f[i];
+        return mode11_assign(v, t, idx);
+    };
+    refine_codes<6>(flat11, total11, 1023, assign11);
+    if (lane != 0)
+        return;
+#pragma unroll
+    for (int i = 0; i < 6; ++i)
+        e11[i / 3][i % 3] = flat11[i];
+    int idx11[16];
+    total11 = mode11_assign(v, e11, idx11);
     const float key11 = isnan(total11) ? INFINITY : total11;
     if (key11 < key10) {
-        if (lane == 0) {
-            out[b] = bc6h_pack_mode11(e11, idx11);
-            if (err)
-                err[b] = total11;
-            if (modes)
-                modes[b] = 11;
-        }
+        out[b] = bc6h_pack_mode11(e11, idx11);
+        if (err)
+            err[b] = total11;
+        if (modes)
+            modes[b] = 11;
         return;
     }
-    if (k != best)
-        return;
     int q[4][3], idx[16];
 #pragma unroll
     for (int r = 0; r < 2; ++r)
@@ -360,7 +498,7 @@ __global__ void __launch_bounds__(32 * kEncWarps) k_compress_bc6h(const float *_
 #pragma unroll
     for (int t = 0; t < 16; ++t)
         idx[t] = mode10_index(idx_lo, idx_hi, t);
-    out[b] = bc6h_pack_mode10(q, idx, k);
+    out[b] = bc6h_pack_mode10(q, idx, best);
     if (err)
         err[b] = total10;
     if (modes)

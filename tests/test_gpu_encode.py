@@ -1,7 +1,13 @@
-"""GPU parity of the BC6H mode-10 partition-selection encoder (Sec. 5.1)
-against the CPU oracle: block parameters, partitions and errors are
-compared bit for bit (both take every decision in IEEE single precision in
-the same order)."""
+"""GPU BC6H encoders (Sec. 5.1 partition selection; the plain two-mode
+compressor) against the CPU oracle's double-precision search, by what is
+fixed whatever the summation order:
+  - the GPU's encoding, read back through the oracle's format decoder, has
+    the squared error the GPU reports;
+  - every index is the best one for its endpoints;
+  - the GPU's decoded error is at most the oracle's (the GPU refines the
+    winner of the same search), up to single-precision error sums;
+  - blocks that are themselves encodings are reproduced exactly.
+"""
 import zlib
 
 import numpy as np
@@ -61,20 +67,69 @@ def _texture(rng, res, levels, kinds):
     return np.concatenate([_level_texels(rng, res >> l, kinds[l % len(kinds)]).reshape(-1) for l in range(levels)])
 
 
+def _block_targets(tex, res, levels, stride=3):
+    """The input texels of every block, [blocks][16][3] float32 in the encoders' block order."""
+    out, off = [], 0
+    for l in range(levels):
+        W = res >> l
+        img = tex[off:off + W * W * stride].reshape(W, W, stride)[:, :, :3]
+        out.append(img.reshape(W // 4, 4, W // 4, 4, 3).transpose(0, 2, 1, 3, 4).reshape(-1, 16, 3))
+        off += W * W * stride
+    return np.concatenate(out)
+
+
+def _values(blk):
+    _, tex = oracle.bc6h_decode_block(blk)
+    return tex.view(np.float16).astype(np.float64)
+
+
+def _index_errors_mode10(p28, k, target):
+    """[8][16] squared error of every texel at each 3-bit index for the record's endpoints (each plane is the
+    record with all positions at one index, exported and read by the oracle's format decoder)."""
+    out = np.zeros((8, 16))
+    for i in range(8):
+        q = p28.copy()
+        q[12:] = i / 7.0
+        out[i] = ((_values(oracle.train_export_block(q, k)) - target) ** 2).sum(axis=1)
+    return out
+
+
+def _check_mode10(p32, part, err, targets, ref_err, what):
+    """Validity of the GPU's mode-10 encodings, and its error against the oracle's search: returns how many
+    blocks the GPU encodes strictly better."""
+    assert not p32[:, [6, 7, 14, 15]].any()
+    better = 0
+    for b in range(p32.shape[0]):
+        p28 = np.concatenate([p32[b, 0:6], p32[b, 8:14], p32[b, 16:32]]).astype(np.float64)
+        k = int(part[b])
+        assert 0 <= k < 32 and np.array_equal(p28[:12], np.round(p28[:12])) and (0 <= p28[:12]).all() and \
+            (p28[:12] <= 63).all(), (what, b)
+        idx = np.rint(p28[12:] * 7).astype(int)
+        assert np.allclose(p28[12:], idx / 7.0, rtol=0, atol=1e-7), (what, b)
+        tgt = targets[b].astype(np.float64)
+        e_idx = _index_errors_mode10(p28, k, tgt)
+        chosen = e_idx[idx, np.arange(16)]
+        assert (chosen <= e_idx.min(axis=0) * (1 + 1e-6) + 1e-12).all(), (what, b, "index not optimal")
+        dec = chosen.sum()
+        assert err[b] == pytest.approx(dec, rel=1e-5, abs=1e-9), (what, b, err[b], dec)
+        assert dec <= ref_err[b] * (1 + 1e-5) + 1e-12, (what, b, dec, ref_err[b])
+        better += dec < ref_err[b] * (1 - 1e-5)
+    return better
+
+
 def _compare(bcf, tex, res, levels):
     p, part, err = bcf.encode_mode10(torch.from_numpy(tex).cuda(), res, levels)
     p, part, err = p.cpu().numpy(), part.cpu().numpy(), err.cpu().numpy()
-    rp, rpart, rerr = oracle.encode_mode10_texture(tex, res, levels)
-    np.testing.assert_array_equal(part, rpart)
-    np.testing.assert_array_equal(err, rerr)
-    got28 = np.concatenate([p[:, 0:6], p[:, 8:14], p[:, 16:32]], axis=1)
-    np.testing.assert_array_equal(got28, rp.astype(np.float32))
-    assert not p[:, [6, 7, 14, 15]].any()
+    _, _, rerr = oracle.encode_mode10_texture(tex, res, levels)
+    better = _check_mode10(p, part, err, _block_targets(tex, res, levels), rerr, (res, levels))
+    print(f"{res}^2 x {levels} levels: {p.shape[0]} blocks, GPU error below the oracle's on {better}")
     return part, err
 
 
 @pytest.mark.parametrize("kinds", [("noise",), ("smooth", "wide"), ("exact", "constant", "noise")])
-def test_encoder_matches_oracle_bit_for_bit(kinds):
+def test_encoder_is_valid_and_at_least_as_good_as_the_oracle(kinds):
+    """bcf_encode_mode10 on noise, smooth, wide-range, exactly encodable and constant levels: valid records,
+    optimal indices, the reported error, and an error at most the oracle's search's."""
     bcf = _bcf()
     rng = np.random.default_rng(zlib.crc32("/".join(kinds).encode()))
     res, levels = 64, 5
@@ -104,7 +159,7 @@ def test_encoder_edge_sizes():
 
 
 def test_encoder_full_size_sampled():
-    """4 x 1024^2 with 9 levels (87,381 blocks per texture): sampled blocks against the oracle."""
+    """1024^2 with 9 levels (87,381 blocks): 600 sampled blocks checked as in the small cases."""
     bcf = _bcf()
     rng = np.random.default_rng(8)
     res, levels = 1024, 9
@@ -120,15 +175,17 @@ def test_encoder_full_size_sampled():
         toffs.append(t)
         b += (W // 4) ** 2
         t += W * W * 3
-    for bi in rng.choice(nb, 600, replace=False):
+    pick = np.sort(rng.choice(nb, 600, replace=False))
+    targets, rerr = [], []
+    for bi in pick:
         l = max(i for i in range(levels) if boffs[i] <= bi)
         W = res >> l
         by, bx = divmod(int(bi - boffs[l]), W // 4)
         img = tex[toffs[l]:toffs[l] + W * W * 3].reshape(W, W, 3)
         blk = img[4 * by:4 * by + 4, 4 * bx:4 * bx + 4].reshape(16, 3)
-        rp, rk, rerr, _ = oracle.encode_mode10_block(blk)
-        assert part[bi] == rk and err[bi] == np.float32(rerr), bi
-        np.testing.assert_array_equal(np.concatenate([p[bi, 0:6], p[bi, 8:14], p[bi, 16:32]]), rp.astype(np.float32))
+        targets.append(blk)
+        rerr.append(oracle.encode_mode10_block(blk)[2])
+    _check_mode10(p[pick], part[pick], err[pick], np.stack(targets), np.array(rerr), "full size")
 
 
 def test_encoder_rejects_bad_arguments():
@@ -204,8 +261,10 @@ def _mode11_level(rng, W):
 
 
 @pytest.mark.parametrize("kinds", [("noise",), ("smooth", "wide"), ("exact", "constant", "mode11")])
-def test_compressor_matches_oracle_bit_for_bit(kinds):
-    """bcf_compress_bc6h: blocks, errors and modes equal the oracle's two-mode compressor bit for bit."""
+def test_compressor_is_valid_and_at_least_as_good_as_the_oracle(kinds):
+    """bcf_compress_bc6h: every block is mode 10 or 11, decodes (oracle format decoder) to the reported error, is
+    at most the oracle's two-mode compressor's error, and a mode-11 block's indices are each the best of the 16
+    for its endpoints; mode-11 lattice blocks are reproduced exactly, in mode 11."""
     bcf = _bcf()
     rng = np.random.default_rng(zlib.crc32(("c/" + "/".join(kinds)).encode()))
     res, levels = 32, 4
@@ -213,16 +272,46 @@ def test_compressor_matches_oracle_bit_for_bit(kinds):
                            else _level_texels(rng, res >> l, kinds[l % len(kinds)])).reshape(-1)
                           for l in range(levels)])
     blocks, err, modes = bcf.compress_bc6h(torch.from_numpy(tex).cuda(), res, levels)
-    rb, rerr, rmodes = oracle.compress_bc6h_texture(tex, res, levels)
-    np.testing.assert_array_equal(modes.cpu().numpy(), rmodes)
-    np.testing.assert_array_equal(err.cpu().numpy(), rerr)
-    np.testing.assert_array_equal(blocks.cpu().numpy().reshape(-1, 16), rb)
+    blocks, err, modes = blocks.cpu().numpy().reshape(-1, 16), err.cpu().numpy(), modes.cpu().numpy()
+    _, rerr, rmodes = oracle.compress_bc6h_texture(tex, res, levels)
+    targets = _block_targets(tex, res, levels)
+    for b in range(blocks.shape[0]):
+        mode = oracle.bc6h_block_mode(blocks[b])
+        assert mode == modes[b] and mode in (10, 11), (b, mode, modes[b])
+        tgt = targets[b].astype(np.float64)
+        dec = ((_values(blocks[b]) - tgt) ** 2).sum()
+        assert err[b] == pytest.approx(dec, rel=1e-5, abs=1e-9), (b, err[b], dec)
+        assert dec <= rerr[b] * (1 + 1e-5) + 1e-12, (b, dec, rerr[b], mode, rmodes[b])
+        if mode == 11:
+            e = _mode11_endpoints(blocks[b])
+            for t in range(16):
+                errs = [((oracle_mode11_value(e, i) - tgt[t]) ** 2).sum() for i in range(16)]
+                got = ((_values(blocks[b])[t] - tgt[t]) ** 2).sum()
+                assert got <= min(errs) * (1 + 1e-6) + 1e-12, (b, t)
     if "mode11" in kinds:  # the mode-11 lattice level is reproduced exactly, in mode 11
         lv = kinds.index("mode11")
         a = sum(((res >> l) // 4) ** 2 for l in range(lv))
         b = a + ((res >> lv) // 4) ** 2
-        assert (rmodes[a:b] == 11).all() and not rerr[a:b].any()
-    assert set(np.unique(rmodes)) <= {10, 11}
+        assert (modes[a:b] == 11).all() and not err[a:b].any()
+
+
+def _mode11_endpoints(blk):
+    """The two 10-bit endpoints (RGB) of a mode-11 block, read from its fields: bits 5..64, RGB of the first
+    endpoint then of the second, 10 bits each."""
+    bits = np.unpackbits(np.asarray(blk, np.uint8), bitorder="little")
+    vals = [int(sum(int(bits[5 + 10 * j + i]) << i for i in range(10))) for j in range(6)]
+    return np.array(vals).reshape(2, 3)
+
+
+def oracle_mode11_value(e, i):
+    """Value of index i between 10-bit endpoints e[0], e[1], through the format decoder (a block whose texel 0
+    carries the index; mirrored when the anchor rule requires)."""
+    raw = [int(v) for v in np.asarray(e).reshape(-1)] + [0] * 6
+    ii = [int(i)] + [0] * 15
+    if i >= 8:
+        raw = raw[3:6] + raw[0:3] + [0] * 6
+        ii = [15 - j for j in ii]
+    return _values(oracle.bc6h_encode_fields(11, raw, 0, ii))[0]
 
 
 def test_compressor_output_is_a_texture_the_decoder_takes():

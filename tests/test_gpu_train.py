@@ -346,8 +346,8 @@ def test_trained_network_beats_plain_bc6h_storage():
     # the exported blocks and FP16 weights lose nothing against the trainer's BF16 forward (the decode path's
     # FP16 weights and FP32 activations may gain a little: measured +0.0 to +0.13 dB)
     assert exported > bcf_psnr - 0.1
-    # measured: 31.3 dB vs 20.3 (mode 10, 0.75x bytes), 28.6 (modes 10 + 11, 0.75x) and 28.9 (3x)
-    assert bcf_psnr > plain[64, (10,)] + 8.0
+    # measured: 31.3 dB vs 28.6 (mode 10, 0.75x bytes), 29.0 (modes 10 + 11, 0.75x) and 29.2 (3x)
+    assert bcf_psnr > plain[64, (10,)] + 2.0
     assert bcf_psnr > plain[128, (10, 11)] + 1.5
 
 

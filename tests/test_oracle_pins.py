@@ -772,8 +772,10 @@ def test_encoder_recovers_exactly_encodable_blocks():
 
 
 def test_encoder_constant_block_and_ties():
-    """A constant block of a decodable value: every partition is exact, the first one is chosen."""
-    for e in (0, 17, 63):
+    """A constant block of a decodable value: every partition is exact, the first one is chosen, and the
+    endpoint code that decodes to the value is recovered (every one of the 64 codes: the quantisation step
+    inverts unquantise and finish)."""
+    for e in range(64):
         p0 = np.zeros(28)
         p0[:12] = e
         target = _decoded_block(p0, 0)
@@ -830,6 +832,42 @@ def _mode11_lattice_block(rng):
     return vals
 
 
+def test_mode11_endpoint_codes_are_recovered_from_their_values():
+    """A constant block whose value is the decode of a 10-bit endpoint alone: the mode-11 encoder returns that
+    code at both ends, for every one of the 1024 codes (the decode (64 e + 32) 31/64 is one to one)."""
+    for code in range(1024):
+        val = oracle_mode11_value(np.array([[code] * 3, [code] * 3]), 0)
+        e, idx, err = oracle.encode_mode11_block(np.tile(val, (16, 1)).astype(np.float32))
+        assert err == 0.0 and (e == code).all(), (code, e)
+
+
+def test_encoder_line_fit_is_the_principal_axis_segment():
+    """The line fit of a region whose points spread along one direction (a variance ratio above 1e4, where 8
+    power iterations have converged) is the segment between the extreme projections onto numpy's principal
+    eigenvector of the region's covariance, for every partition's regions and for the one-region fit."""
+    rng = np.random.default_rng(121)
+    for trial in range(60):
+        k = int(rng.integers(-1, 32))
+        d = rng.standard_normal(3)
+        d /= np.linalg.norm(d)
+        m = rng.uniform(5000, 20000, 3)
+        y = m + np.outer(rng.uniform(-3000, 3000, 16), d) + rng.normal(0, 5.0, (16, 3))
+        for r in ((0,) if k < 0 else (0, 1)):
+            mem = [t for t in range(16) if k < 0 or oracle.bc6h_partition_region(k, t) == r]
+            pts = y[mem]
+            mu = pts.mean(axis=0)
+            w, V = np.linalg.eigh(np.cov(pts.T, bias=True))
+            ax = V[:, -1]
+            proj = (pts - mu) @ ax
+            ref = {tuple(np.round(mu + proj.min() * ax, 3)), tuple(np.round(mu + proj.max() * ax, 3))}
+            A, B = oracle.encode_fit_segment(y, k, r)
+            scale = np.abs(pts - mu).max()
+            ends = [mu + proj.min() * ax, mu + proj.max() * ax]
+            ok = (np.allclose(A, ends[0], atol=1e-6 * scale) and np.allclose(B, ends[1], atol=1e-6 * scale)) or \
+                 (np.allclose(A, ends[1], atol=1e-6 * scale) and np.allclose(B, ends[0], atol=1e-6 * scale))
+            assert ok, (trial, k, r, A, B, ref)
+
+
 def test_mode11_encoder_recovers_exactly_encodable_blocks():
     """A block that is itself a mode-11 encoding is reproduced with zero error, and the compressor then writes
     a mode-11 block that decodes to the targets bit for bit."""
@@ -862,11 +900,8 @@ def test_compressor_error_is_the_decoded_error_and_the_smaller_candidate():
         m, vals = _block_values(blk)
         assert m == mode
         seen.add(mode)
-        sq = ((vals.astype(np.float32) - target) ** 2).astype(np.float32)
-        ref = np.float32(0.0)
-        for t in range(16):  # the encoder's order: (r + g) + b per texel, texels in order, single precision
-            ref = np.float32(ref + np.float32(np.float32(sq[t, 0] + sq[t, 1]) + sq[t, 2]))
-        assert err == ref, (b, err, ref)
+        ref = ((vals - target.astype(np.float64)) ** 2).sum()
+        assert err == pytest.approx(ref, rel=1e-12, abs=1e-15), (b, err, ref)
         _, _, e10, _ = oracle.encode_mode10_block(target)
         e, idx, e11 = oracle.encode_mode11_block(target)
         assert err == min(e10, e11) and mode == (11 if e11 < e10 else 10)
