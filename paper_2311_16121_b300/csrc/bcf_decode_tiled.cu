@@ -736,6 +736,511 @@ __global__ void __launch_bounds__(kTileQ, 3) k_decode_set(const MaterialDev *__r
     }
 }
 
+// ------------------------------------------------- single-geometry tiles
+
+// Materials whose textures all share one resolution and level count (one geometry group) take a leaner tile
+// kernel: the footprint geometry is computed once per query and kept in registers, the tile's block boxes are
+// kept per absolute level (no separate LOD-range pass), every thread sizes the block set itself (no planning
+// warp), and a tile costs four CTA barriers:
+//   1. per query: LOD, levels and footprint per side; per warp and level the block box by warp reductions,
+//      merged into the tile's boxes with shared atomics (block coordinates relative to the tile's first query,
+//      so that boxes across the repeat seam stay compact)                                   -- barrier 1
+//   2. the textures in rounds that fit the arena; per round every block of every texture of the round is
+//      loaded once with a 16-byte load and ranked among the round's blocks of its BC6H mode  -- barrier 2
+//   3. scattered into mode order (so that a warp decodes blocks of few modes)               -- barrier 3
+//   4. decoded, all 16 texels, into the texel arena                                         -- barrier 4
+//   5. filtered per query from the arena (exact FP32, the per-lane decode's operation order) into the warp's
+//      MLP input rows; then per warp the register-chained MLP and coalesced stores.
+// A tile whose blocks of one texture alone exceed the arena is filtered by the per-lane decode.
+#ifndef BCF_GEO_MIN_BLOCKS
+#define BCF_GEO_MIN_BLOCKS 4
+#endif
+constexpr int kGeoMinBlocks = BCF_GEO_MIN_BLOCKS; // resident CTAs per SM the register budget is sized for
+
+struct GeoMeta {
+    int box[BCF_MAX_LEVELS][4]; // per level: min x, max x, min y, max y (relative block coordinates)
+    unsigned levmask;           // levels holding footprints of the tile
+    int hist[16];               // blocks per mode bin of the current round
+};
+
+struct GeoLayout {
+    int w_bytes, b_bytes, meta, sraw, sidx, arena, per_warp, tmp8, total;
+};
+
+template <int PREC>
+__host__ __device__ inline GeoLayout geo_layout(const MlpDev &P, int cap)
+{
+    GeoLayout L;
+    const int C = P.dims[P.n_layers];
+    int off = 0;
+    L.w_bytes = mlp_smem_weight_bytes<PREC>(P);
+    off += L.w_bytes;
+    L.b_bytes = off;
+    off += (mlp_smem_bias_floats(P) * 4 + 15) & ~15;
+    L.meta = off;
+    off += (int)((2 * sizeof(GeoMeta) + 15) & ~15);
+    L.sraw = off;
+    off += cap * 16;
+    L.sidx = off;
+    off += (cap * 2 + 15) & ~15;
+    L.arena = off;
+    off += cap * 16 * 8;
+    int maxn = 0;
+    for (int l = 0; l < P.n_layers; ++l)
+        maxn = maxn > P.npad[l] ? maxn : P.npad[l];
+    const int tmp = PREC == BCF_FP8_E4M3 ? ((16 * (maxn + 16) + 15) & ~15) : 0;
+    const int ostb = (32 * C * 4 + 15) & ~15;
+    const int in_stride = tile_stride_bytes<PREC>(P.kpad[0]);
+    const int in0 = (32 * in_stride + 15) & ~15;
+    const bool alias = 16 * C * 4 <= 16 * in_stride; // output staging inside the input tile (as tiled_layout)
+    const int a0 = alias ? (in0 > ostb ? in0 : ostb) : in0 + ostb;
+    L.tmp8 = a0;
+    L.per_warp = a0 + tmp;
+    L.total = off + (kTileQ / 32) * L.per_warp;
+    return L;
+}
+
+__device__ __forceinline__ void reset_geo_meta(GeoMeta &G)
+{
+    for (int i = threadIdx.x; i < BCF_MAX_LEVELS; i += kTileQ) {
+        G.box[i][0] = G.box[i][2] = INT_MAX;
+        G.box[i][1] = G.box[i][3] = INT_MIN;
+    }
+    if (threadIdx.x < 16)
+        G.hist[threadIdx.x] = 0;
+    if (threadIdx.x == 0)
+        G.levmask = 0u;
+}
+
+// Size of the box of level lev (0 if the level holds no footprint).
+__device__ __forceinline__ int box_size(const GeoMeta &G, int lev)
+{
+    const int *b = G.box[lev];
+    return b[0] == INT_MAX ? 0 : (b[1] - b[0] + 1) * (b[3] - b[2] + 1);
+}
+
+// First block item of level lev's box within one texture's block set (boxes in level order).
+__device__ __forceinline__ int box_offset(const GeoMeta &G, unsigned mask, int lev)
+{
+    int off = 0;
+    mask &= (1u << lev) - 1u;
+    while (mask) {
+        const int l = __ffs(mask) - 1;
+        off += box_size(G, l);
+        mask &= mask - 1u;
+    }
+    return off;
+}
+
+// The per-lane decode of one texture, out of line: the rare tiles whose blocks exceed the arena take it, and
+// keeping its copy of the BC6H decoder out of the tile kernel's body keeps that body's code small.
+__device__ __noinline__ float3 sample_texture_ool(const TexDev &T, int wrap, bool sgn, float u, float v, float s)
+{
+    return sample_texture(T, wrap, sgn, u, v, s);
+}
+
+// Coalesced store of a warp's rows [q0, q0 + rows) from the FP32 staging tile ost[rows][C]: FP16 output in
+// 16-byte chunks of 8 values (q0 is a multiple of 32, so a chunk never straddles the 16-byte alignment of out),
+// the tail value by value; FP32 output in chunks of 4.
+__device__ __forceinline__ void store_warp_rows(const float *ost, void *out, int64_t q0, int rows, int C, int out_fp16,
+                                                int lane)
+{
+    const int tot = rows * C;
+    if (out_fp16) {
+        __half *o = (__half *)out + q0 * C;
+        const int full = tot >> 3;
+        for (int k = lane; k < full; k += 32) {
+            const float4 a = *reinterpret_cast<const float4 *>(ost + 8 * k);
+            const float4 b = *reinterpret_cast<const float4 *>(ost + 8 * k + 4);
+            const __half2 h0 = __floats2half2_rn(a.x, a.y), h1 = __floats2half2_rn(a.z, a.w);
+            const __half2 h2 = __floats2half2_rn(b.x, b.y), h3 = __floats2half2_rn(b.z, b.w);
+            uint4 w;
+            w.x = *reinterpret_cast<const uint32_t *>(&h0);
+            w.y = *reinterpret_cast<const uint32_t *>(&h1);
+            w.z = *reinterpret_cast<const uint32_t *>(&h2);
+            w.w = *reinterpret_cast<const uint32_t *>(&h3);
+            *reinterpret_cast<uint4 *>(o + 8 * k) = w;
+        }
+        for (int i = (full << 3) + lane; i < tot; i += 32)
+            o[i] = __float2half_rn(ost[i]);
+    } else {
+        float *o = (float *)out + q0 * C;
+        const int full = tot >> 2;
+        for (int k = lane; k < full; k += 32)
+            *reinterpret_cast<float4 *>(o + 4 * k) = *reinterpret_cast<const float4 *>(ost + 4 * k);
+        for (int i = (full << 2) + lane; i < tot; i += 32)
+            o[i] = ost[i];
+    }
+}
+
+// Decode arena blocks [first, items) (sorted by mode) with 1 << lk threads per block: each thread decodes the
+// header and 16 >> lk texels; sgn is a template parameter so that the unsigned and signed paths are each
+// specialised (the caller branches once, uniformly, on the material's format).
+template <bool SGN>
+__device__ __forceinline__ void decode_arena_blocks(const uint4 *sraw, const uint16_t *sidx, uint2 *arena, int items,
+                                                    int lk)
+{
+    for (int i = threadIdx.x; i < (items << lk); i += kTileQ) {
+        const int e = i >> lk, part = i & ((1 << lk) - 1);
+        const uint4 rr = sraw[e];
+        const int tag = sidx[e];
+        uint2 *dst = arena + (tag & 255) * 16;
+        const int swz = tag >> 8;
+        Bc6hBlock bk;
+        bk.lo = (uint64_t)rr.x | ((uint64_t)rr.y << 32);
+        bk.hi = (uint64_t)rr.z | ((uint64_t)rr.w << 32);
+        Bc6hHeader H;
+        bc6h_header(bk, SGN, H);
+        Bc6hTexels X;
+        bc6h_prepare_texels(bk, H, X);
+        const auto put = [&](int t, uint32_t rg, uint32_t bb) { dst[t ^ swz] = make_uint2(rg, bb); };
+        if (lk == 0)
+            bc6h_texels<16>(X, SGN, 0, put);
+        else
+            bc6h_texels<8>(X, SGN, part * 8, put);
+    }
+}
+
+// Writes a query's MLP input row column by column, in increasing column order: 16-bit operands go out in
+// pairs (one 4-byte store per two columns), E4M3 bytes one by one.
+template <int PREC>
+struct RowWriter {
+    unsigned char *row;
+    float inv; // FP8: the first layer's inverse activation scale
+    float pend; // the value of an even column waiting for its odd neighbour
+    __device__ __forceinline__ void put(int col, float x)
+    {
+        if constexpr (PREC == BCF_FP8_E4M3) {
+            store_feature<PREC>(row, col, x, inv);
+        } else if (col & 1) {
+            *reinterpret_cast<uint32_t *>(row + 2 * (col - 1)) = Op<PREC>::pack2(pend, x);
+        } else {
+            pend = x;
+        }
+    }
+    // after the last column: an unpaired even column is written alone
+    __device__ __forceinline__ void finish(int ncols)
+    {
+        if constexpr (PREC != BCF_FP8_E4M3)
+            if (ncols & 1)
+                store_feature<PREC>(row, ncols - 1, pend, inv);
+    }
+};
+
+template <int PREC, int CAP, int K0, int N1, int N2, int NO>
+__global__ void __launch_bounds__(kTileQ, kGeoMinBlocks) k_decode_geo(MaterialDev M, const float *__restrict__ qu,
+                                                          const float *__restrict__ qv, const float *__restrict__ qs,
+                                                          int64_t n, void *__restrict__ out, int out_fp16)
+{
+    static_assert(CAP <= kTileQ, "one block item per thread while loading");
+    extern __shared__ __align__(16) unsigned char smem[];
+    const MlpDev &P = M.mlp;
+    const GeoLayout LY = geo_layout<PREC>(P, CAP);
+    unsigned char *sw = smem;
+    float *sb = (float *)(smem + LY.b_bytes);
+    GeoMeta *meta = (GeoMeta *)(smem + LY.meta);
+    uint4 *sraw = (uint4 *)(smem + LY.sraw);
+    uint16_t *sidx = (uint16_t *)(smem + LY.sidx);
+    uint2 *arena = (uint2 *)(smem + LY.arena);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    unsigned char *act0 = smem + LY.total - (kTileQ / 32 - warp) * LY.per_warp;
+    unsigned char *tmp8 = act0 + LY.tmp8;
+    float *ost = (float *)act0; // output staging aliases the input tile or follows it (geo_layout)
+    {
+        const int C = P.dims[P.n_layers];
+        const int in_stride = tile_stride_bytes<PREC>(P.kpad[0]);
+        if (!(16 * C * 4 <= 16 * in_stride))
+            ost = (float *)(act0 + ((32 * in_stride + 15) & ~15));
+    }
+    const int Cn = P.dims[P.n_layers];
+    const int row_stride = tile_stride_bytes<PREC>(P.kpad[0]);
+    unsigned char *myrow = act0 + lane * row_stride;
+    const float inv0 = PREC == BCF_FP8_E4M3 ? P.inv_act_scale[0] : 1.0f;
+    RowWriter<PREC> rw{myrow, inv0, 0.0f};
+    const int nt = M.n_tex;
+    const int wrap = M.wrap;
+    const bool sgn = M.is_signed != 0;
+    const TexDev &T0 = M.tex[0];
+    const unsigned lanes_lt = (1u << lane) - 1u;
+
+    load_mlp_smem<PREC>(P, sw, sb);
+    reset_geo_meta(meta[0]);
+    reset_geo_meta(meta[1]);
+    __syncthreads();
+
+    const int64_t tiles = (n + kTileQ - 1) / kTileQ;
+    float nu = 0.0f, nv = 0.0f, ns = 0.0f, nu_ref = 0.0f, nv_ref = 0.0f;
+    {
+        const int64_t q = (int64_t)blockIdx.x * kTileQ + threadIdx.x;
+        if (blockIdx.x < tiles && q < n) {
+            nu = qu[q];
+            nv = qv[q];
+            ns = qs ? qs[q] : 0.0f;
+        }
+        if (blockIdx.x < tiles) {
+            nu_ref = qu[(int64_t)blockIdx.x * kTileQ];
+            nv_ref = qv[(int64_t)blockIdx.x * kTileQ];
+        }
+    }
+    int parity = 0;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, parity ^= 1) {
+        GeoMeta &G = meta[parity];
+        const int64_t q_first = tile * kTileQ;
+        const int64_t q = q_first + threadIdx.x;
+        const bool active = q < n;
+        const float u = active ? sanitize(nu, wrap) : 0.0f;
+        const float v = active ? sanitize(nv, wrap) : 0.0f;
+        const float s = active ? ns : 0.0f;
+        // the tile's first query: the reference of the relative block coordinates
+        const float u_ref = sanitize(nu_ref, wrap), v_ref = sanitize(nv_ref, wrap);
+        {
+            const int64_t qn = (tile + gridDim.x) * kTileQ + threadIdx.x;
+            if (tile + gridDim.x < tiles && qn < n) {
+                nu = qu[qn];
+                nv = qv[qn];
+                ns = qs ? qs[qn] : 0.0f;
+            }
+            if (tile + gridDim.x < tiles) {
+                nu_ref = qu[(tile + gridDim.x) * kTileQ];
+                nv_ref = qv[(tile + gridDim.x) * kTileQ];
+            }
+        }
+        // ---- 1. footprint geometry per side, block boxes per level
+        const Lod L = lod_of(T0, s);
+        int i0s[2], j0s[2];
+        float fxs[2], fys[2];
+#pragma unroll
+        for (int side = 0; side < 2; ++side) {
+            const int level = min(L.l0 + side, T0.levels - 1);
+            const int W = T0.res >> level;
+            const float x = u * (float)W - 0.5f, y = v * (float)W - 0.5f;
+            const float fx0 = floorf(x), fy0 = floorf(y);
+            fxs[side] = x - fx0;
+            fys[side] = y - fy0;
+            i0s[side] = (int)fx0;
+            j0s[side] = (int)fy0;
+        }
+        const bool warp2 = __any_sync(0xffffffffu, active && L.nlev == 2);
+        {
+            int bxl[2], bxh[2], byl[2], byh[2];
+#pragma unroll
+            for (int side = 0; side < 2; ++side) {
+                if (side == 1 && !warp2) { // warp-uniform
+                    bxl[1] = bxh[1] = byl[1] = byh[1] = 0;
+                    break;
+                }
+                const int W = T0.res >> min(L.l0 + side, T0.levels - 1);
+                const int rbx = wrap ? ref_block(u_ref, W) : 0, rby = wrap ? ref_block(v_ref, W) : 0;
+                bxl[side] = rel_block(i0s[side], i0s[side], rbx, W, wrap);
+                bxh[side] = rel_block(i0s[side] + 1, i0s[side], rbx, W, wrap);
+                byl[side] = rel_block(j0s[side], j0s[side], rby, W, wrap);
+                byh[side] = rel_block(j0s[side] + 1, j0s[side], rby, W, wrap);
+            }
+            const int lo = __reduce_min_sync(0xffffffffu, active ? L.l0 : INT_MAX);
+            const int hi = __reduce_max_sync(0xffffffffu, active ? L.l0 + L.nlev - 1 : INT_MIN);
+            for (int lev = lo; lev <= hi; ++lev) { // warp-uniform
+                const int side = lev - L.l0;
+                const bool use = active && side >= 0 && side < L.nlev;
+                const int mnx = __reduce_min_sync(0xffffffffu, use ? (side ? bxl[1] : bxl[0]) : INT_MAX);
+                const int mxx = __reduce_max_sync(0xffffffffu, use ? (side ? bxh[1] : bxh[0]) : INT_MIN);
+                const int mny = __reduce_min_sync(0xffffffffu, use ? (side ? byl[1] : byl[0]) : INT_MAX);
+                const int mxy = __reduce_max_sync(0xffffffffu, use ? (side ? byh[1] : byh[0]) : INT_MIN);
+                if (lane == 0 && mnx != INT_MAX) {
+                    int *b = G.box[lev];
+                    atomicMin(&b[0], mnx);
+                    atomicMax(&b[1], mxx);
+                    atomicMin(&b[2], mny);
+                    atomicMax(&b[3], mxy);
+                    atomicOr(&G.levmask, 1u << lev);
+                }
+            }
+        }
+        __syncthreads(); // barrier 1
+        // the other buffer's last readers (the previous tile) are behind this barrier: reset it for the next tile
+        reset_geo_meta(meta[parity ^ 1]);
+        const unsigned mask = G.levmask;
+        int nb = 0; // blocks of one texture's block set
+        {
+            unsigned mm = mask;
+            while (mm) {
+                nb += box_size(G, __ffs(mm) - 1);
+                mm &= mm - 1u;
+            }
+        }
+        const int per_round = nb > 0 ? min(nt, CAP / nb) : nt;
+        if (per_round == 0) {
+            // one texture's blocks exceed the arena: the per-lane decode for this tile
+            for (int t = 0; t < nt; ++t) {
+                float3 f = make_float3(0.f, 0.f, 0.f);
+                if (active)
+                    f = sample_texture_ool(M.tex[t], wrap, sgn, u, v, s);
+                rw.put(3 * t, f.x);
+                rw.put(3 * t + 1, f.y);
+                rw.put(3 * t + 2, f.z);
+            }
+            __syncthreads(); // the next tile's box atomics stay behind this tile's reset of their buffer
+        } else {
+            const float inv_nb = 1.0f / (float)max(nb, 1);
+            for (int t0 = 0; t0 < nt; t0 += per_round) {
+                const int rt = min(per_round, nt - t0);
+                const int items = nb * rt;
+                // ---- 2. load each block of the round once; rank it among the round's blocks of its mode
+                const int it = threadIdx.x;
+                const bool valid = it < items;
+                uint4 blk = make_uint4(0, 0, 0, 0);
+                int bin = kBins + lane; // unique per lane when invalid: no aggregation
+                int jlow = 0; // item within its texture's block set, low 4 bits: the arena swizzle
+                if (valid) {
+                    const int tt = (int)(((float)it + 0.5f) * inv_nb);
+                    int j = it - tt * nb;
+                    jlow = j & 15;
+                    unsigned mm = mask;
+                    int lev = __ffs(mm) - 1;
+                    for (;;) { // the level whose box holds item j
+                        const int sz = box_size(G, lev);
+                        if (j < sz)
+                            break;
+                        j -= sz;
+                        mm &= mm - 1u;
+                        lev = __ffs(mm) - 1;
+                    }
+                    const int *b = G.box[lev];
+                    const int bw = b[1] - b[0] + 1;
+                    const int ry = (int)(((float)j + 0.5f) / (float)bw);
+                    const TexDev &T = M.tex[t0 + tt];
+                    const int W = T.res >> lev, wb = W >> 2;
+                    int bxa = b[0] + (j - ry * bw), bya = b[2] + ry;
+                    if (wrap) {
+                        bxa = (ref_block(u_ref, W) + bxa) & (wb - 1);
+                        bya = (ref_block(v_ref, W) + bya) & (wb - 1);
+                    }
+                    blk = __ldg(T.blocks + T.level_off[lev] + (uint32_t)bya * (uint32_t)wb + (uint32_t)bxa);
+                    const int mi = mode_index(blk.x);
+                    bin = mi < 0 ? kBins - 1 : mi;
+                }
+                const unsigned peers = __match_any_sync(0xffffffffu, bin);
+                const int leader = __ffs(peers) - 1;
+                int base = 0;
+                if (valid && lane == leader)
+                    base = atomicAdd(&G.hist[bin], __popc(peers));
+                const int rank = __shfl_sync(0xffffffffu, base, leader) + __popc(peers & lanes_lt);
+                __syncthreads(); // barrier 2
+                // ---- 3. scatter into mode order: position = blocks of smaller modes + rank
+                {
+                    const int h = lane < 16 ? G.hist[lane] : 0;
+                    int incl = h;
+#pragma unroll
+                    for (int d = 1; d < 16; d <<= 1) {
+                        const int o = __shfl_up_sync(0xffffffffu, incl, d);
+                        if (lane >= d)
+                            incl += o;
+                    }
+                    const int excl = incl - h;
+                    const int start = __shfl_sync(0xffffffffu, excl, valid ? bin : 0);
+                    if (valid) {
+                        sraw[start + rank] = blk;
+                        sidx[start + rank] = (uint16_t)(it | (jlow << 8));
+                    }
+                }
+                __syncthreads(); // barrier 3
+                if (threadIdx.x < 16)
+                    G.hist[threadIdx.x] = 0; // for the next round (read again only after its barrier 2)
+                // ---- 4. decode the sorted blocks into the arena: one thread per block, two when there are few
+                const int lk = items <= 64 ? 1 : 0;
+                if (sgn)
+                    decode_arena_blocks<true>(sraw, sidx, arena, items, lk);
+                else
+                    decode_arena_blocks<false>(sraw, sidx, arena, items, lk);
+                __syncthreads(); // barrier 4
+                // ---- 5. filter the round's textures from the arena: per side the corner geometry, shared by
+                // every texture (item offsets within one texture's block set), then 4 arena texels per texture
+                const bool any2 = warp2;
+                int cb[2][4]; // arena texel of each corner within texture 0's block set (swizzled)
+                float cw[2][4];
+#pragma unroll
+                for (int side = 0; side < 2; ++side) {
+                    if (side == 1 && !any2)
+                        break; // warp-uniform: no lane of the warp samples a second level
+                    const int level = min(L.l0 + side, T0.levels - 1);
+                    const float scale = L.nlev == 1 ? 1.0f : (side ? L.lam : 1.0f - L.lam);
+                    const int W = T0.res >> level;
+                    const int *b = G.box[level];
+                    const bool in_box = active && side < L.nlev; // the box of this level holds the footprint
+                    const int bw = in_box ? b[1] - b[0] + 1 : 1, bh = in_box ? b[3] - b[2] + 1 : 1;
+                    const int bx0 = in_box ? b[0] : 0, by0 = in_box ? b[2] : 0;
+                    const int o = in_box ? box_offset(G, mask, level) : 0;
+                    const int rbx = wrap ? ref_block(u_ref, W) : 0, rby = wrap ? ref_block(v_ref, W) : 0;
+                    const int i0 = i0s[side], j0 = j0s[side];
+                    // the box was built from the same coordinates, so these lie inside it; the clamps only keep
+                    // shared-memory reads in bounds
+                    const int xl = min(max(rel_block(i0, i0, rbx, W, wrap) - bx0, 0), bw - 1);
+                    const int xh = min(max(rel_block(i0 + 1, i0, rbx, W, wrap) - bx0, 0), bw - 1);
+                    const int yl = min(max(rel_block(j0, j0, rby, W, wrap) - by0, 0), bh - 1);
+                    const int yh = min(max(rel_block(j0 + 1, j0, rby, W, wrap) - by0, 0), bh - 1);
+                    const int cl = texel_col(i0, W, wrap), ch = texel_col(i0 + 1, W, wrap);
+                    const int rl = texel_col(j0, W, wrap) * 4, rh = texel_col(j0 + 1, W, wrap) * 4;
+                    const int j00 = o + yl * bw + xl, j01 = o + yl * bw + xh, j10 = o + yh * bw + xl,
+                              j11 = o + yh * bw + xh;
+                    cb[side][0] = j00 * 16 + ((rl + cl) ^ (j00 & 15));
+                    cb[side][1] = j01 * 16 + ((rl + ch) ^ (j01 & 15));
+                    cb[side][2] = j10 * 16 + ((rh + cl) ^ (j10 & 15));
+                    cb[side][3] = j11 * 16 + ((rh + ch) ^ (j11 & 15));
+                    const float fx = fxs[side], fy = fys[side];
+                    cw[side][0] = (1.0f - fx) * (1.0f - fy) * scale;
+                    cw[side][1] = fx * (1.0f - fy) * scale;
+                    cw[side][2] = (1.0f - fx) * fy * scale;
+                    cw[side][3] = fx * fy * scale;
+                }
+                for (int tt = 0; tt < rt; ++tt) {
+                    float f0 = 0.0f, f1 = 0.0f, f2 = 0.0f;
+                    if (active) {
+                        const uint2 *at = arena + tt * nb * 16;
+#pragma unroll
+                        for (int side = 0; side < 2; ++side) {
+                            if (side < L.nlev) {
+#pragma unroll
+                                for (int c = 0; c < 4; ++c) {
+                                    const uint2 tx = at[cb[side][c]];
+                                    const float2 rg = __half22float2(*reinterpret_cast<const __half2 *>(&tx.x));
+                                    f0 = fmaf(cw[side][c], rg.x, f0);
+                                    f1 = fmaf(cw[side][c], rg.y, f1);
+                                    f2 = fmaf(cw[side][c], __half2float(__ushort_as_half((unsigned short)tx.y)), f2);
+                                }
+                            }
+                        }
+                    }
+                    const int t = t0 + tt;
+                    rw.put(3 * t, f0);
+                    rw.put(3 * t + 1, f1);
+                    rw.put(3 * t + 2, f2);
+                }
+            }
+        }
+        {
+            int col = 3 * nt;
+            if (M.lod_input) {
+                rw.put(col, active ? (isnan(s) ? 0.0f : fmaxf(s, 0.0f)) : 0.0f);
+                ++col;
+            }
+            for (; col < P.kpad[0]; ++col)
+                rw.put(col, 0.0f);
+            rw.finish(col);
+        }
+        __syncwarp();
+        // ---- 6. MLP on the tensor cores, coalesced store
+        if constexpr (N2 == 0)
+            warp_mlp2<PREC, K0, N1, NO>(sw, sb, act0, row_stride, ost, Cn);
+        else
+            warp_mlp3<PREC, K0, N1, N2, NO>(P, sw, sb, act0, row_stride, tmp8,
+                                            tile_stride_bytes<BCF_FP8_E4M3>(N1 > N2 ? N1 : N2), ost, Cn);
+        __syncwarp();
+        const int64_t q0 = q_first + warp * 32;
+        if (q0 < n)
+            store_warp_rows(ost, out, q0, (int)min((int64_t)32, n - q0), Cn, out_fp16, lane);
+        __syncwarp();
+    }
+}
+
 // ---------------------------------------------------------------- launcher
 
 constexpr int kArenaCap = 320;
@@ -753,10 +1258,36 @@ static int tiled_sms()
     return sms;
 }
 
+constexpr int kGeoCap = 224; // block arena of the single-geometry kernel (4 CTAs of 256 threads per SM)
+
+template <int PREC, int K0, int N1, int N2, int NO>
+static cudaError_t launch_geo_shape(const MaterialDev &M, const float *u, const float *v, const float *s, int64_t n,
+                                    void *out, int out_fp16, cudaStream_t st)
+{
+    const int64_t smem = geo_layout<PREC>(M.mlp, kGeoCap).total;
+    if (smem > 227 * 1024)
+        return cudaErrorInvalidConfiguration;
+    auto kern = k_decode_geo<PREC, kGeoCap, K0, N1, N2, NO>;
+    static int configured = 0;
+    if (!configured) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        configured = 1;
+    }
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTileQ, (size_t)smem);
+    const int64_t tiles = (n + kTileQ - 1) / kTileQ;
+    const int64_t grid = min(tiles, (int64_t)tiled_sms() * max(per_sm, 1));
+    kern<<<(unsigned)grid, kTileQ, (size_t)smem, st>>>(M, u, v, s, n, out, out_fp16);
+    return cudaGetLastError();
+}
+
 template <int PREC, int K0, int N1, int N2, int NO>
 static cudaError_t launch_tiled_shape(const MaterialDev &M, const float *u, const float *v, const float *s, int64_t n,
                                       void *out, int out_fp16, cudaStream_t st)
 {
+    if constexpr (K0 != 0)
+        if (M.n_groups == 1)
+            return launch_geo_shape<PREC, K0, N1, N2, NO>(M, u, v, s, n, out, out_fp16, st);
     const int64_t smem = tiled_layout<PREC>(M.mlp, kArenaCap, K0 == 0).total;
     if (smem > 227 * 1024)
         return cudaErrorInvalidConfiguration;

@@ -56,6 +56,13 @@ struct Op<BCF_FP16> {
         __half2 h = __floats2half2_rn(a, b);
         return *reinterpret_cast<uint32_t *>(&h);
     }
+    // max(a, 0), max(b, 0) rounded to nearest-even halves in one conversion (a in the low half)
+    __device__ static uint32_t pack2_relu(float a, float b)
+    {
+        uint32_t d;
+        asm("cvt.rn.relu.f16x2.f32 %0, %2, %1;" : "=r"(d) : "f"(a), "f"(b));
+        return d;
+    }
     __device__ static void mma(float d[4], const uint32_t a[4], const uint32_t b[2]) { mma_f16(d, a, b); }
 };
 
@@ -66,6 +73,12 @@ struct Op<BCF_BF16> {
     {
         __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
         return *reinterpret_cast<uint32_t *>(&h);
+    }
+    __device__ static uint32_t pack2_relu(float a, float b)
+    {
+        uint32_t d;
+        asm("cvt.rn.relu.bf16x2.f32 %0, %2, %1;" : "=r"(d) : "f"(a), "f"(b));
+        return d;
     }
     __device__ static void mma(float d[4], const uint32_t a[4], const uint32_t b[2]) { mma_bf16(d, a, b); }
 };
@@ -306,14 +319,19 @@ __device__ __forceinline__ void load_a(const unsigned char *A, int stride, int r
 // fragment is loaded once and used for all MT row tiles.
 template <int PREC, int MT, int KP, int NP>
 __device__ __forceinline__ void mma_layer(const uint32_t (&a)[MT][KP / Op<PREC>::kK][4], const unsigned char *W,
-                                          int stride, int g, int t, float (&d)[MT][NP / 8][4])
+                                          int stride, int g, int t, float (&d)[MT][NP / 8][4],
+                                          const float *bias = nullptr)
 {
     constexpr int KK = Op<PREC>::kK, EB = Op<PREC>::kBytes;
 #pragma unroll
     for (int nt = 0; nt < NP / 8; ++nt) {
+        // accumulators start at the bias (columns 8 nt + 2 t, + 1) when one is given, else at 0
+        const float c0 = bias ? bias[nt * 8 + 2 * t] : 0.0f, c1 = bias ? bias[nt * 8 + 2 * t + 1] : 0.0f;
 #pragma unroll
-        for (int m = 0; m < MT; ++m)
-            d[m][nt][0] = d[m][nt][1] = d[m][nt][2] = d[m][nt][3] = 0.0f;
+        for (int m = 0; m < MT; ++m) {
+            d[m][nt][0] = d[m][nt][2] = c0;
+            d[m][nt][1] = d[m][nt][3] = c1;
+        }
 #pragma unroll
         for (int kt = 0; kt < KP / KK; ++kt) {
             uint32_t b[2];
@@ -325,22 +343,18 @@ __device__ __forceinline__ void mma_layer(const uint32_t (&a)[MT][KP / Op<PREC>:
     }
 }
 
-// Hidden epilogue for 16-bit operands: bias + ReLU, rounded straight into the
-// next layer's A fragments (D tile columns 8 nt + 2 t map onto A fragment
-// nt / 2, registers 0/1 for even nt and 2/3 for odd nt).
+// Hidden epilogue for 16-bit operands: the accumulators already hold bias + sum (mma_layer with a bias); ReLU
+// and rounding in one conversion, straight into the next layer's A fragments (D tile columns 8 nt + 2 t map
+// onto A fragment nt / 2, registers 0/1 for even nt and 2/3 for odd nt).
 template <int PREC, int MT, int NP>
-__device__ __forceinline__ void hidden_to_a16(const float (&d)[MT][NP / 8][4], const float *bias, int t,
-                                              uint32_t (&a)[MT][NP / 16][4])
+__device__ __forceinline__ void hidden_to_a16(const float (&d)[MT][NP / 8][4], uint32_t (&a)[MT][NP / 16][4])
 {
 #pragma unroll
     for (int nt = 0; nt < NP / 8; ++nt) {
-        const float b0 = bias[nt * 8 + 2 * t], b1 = bias[nt * 8 + 2 * t + 1];
 #pragma unroll
         for (int m = 0; m < MT; ++m) {
-            a[m][nt >> 1][(nt & 1) * 2 + 0] =
-                Op<PREC>::pack2(fmaxf(d[m][nt][0] + b0, 0.f), fmaxf(d[m][nt][1] + b1, 0.f));
-            a[m][nt >> 1][(nt & 1) * 2 + 1] =
-                Op<PREC>::pack2(fmaxf(d[m][nt][2] + b0, 0.f), fmaxf(d[m][nt][3] + b1, 0.f));
+            a[m][nt >> 1][(nt & 1) * 2 + 0] = Op<PREC>::pack2_relu(d[m][nt][0], d[m][nt][1]);
+            a[m][nt >> 1][(nt & 1) * 2 + 1] = Op<PREC>::pack2_relu(d[m][nt][2], d[m][nt][3]);
         }
     }
 }
@@ -411,7 +425,7 @@ __device__ __forceinline__ void warp_mlp3(const MlpDev &P, const unsigned char *
             for (int kt = 0; kt < K0 / KK; ++kt)
                 load_a<EB, KK>(in, in_stride, (m0 + m) * 16, kt * KK, g, t, a0[m][kt]);
         float d1[MT][N1 / 8][4];
-        mma_layer<PREC, MT, K0, N1>(a0, W0, s0, g, t, d1);
+        mma_layer<PREC, MT, K0, N1>(a0, W0, s0, g, t, d1, PREC == BCF_FP8_E4M3 ? nullptr : b0);
         uint32_t a1[MT][N1 / KK][4];
         if constexpr (PREC == BCF_FP8_E4M3) {
             hidden_to_tile8<MT, N1>(d1, b0, sc0, in1, g, t, tmp8, tmp_stride);
@@ -423,10 +437,10 @@ __device__ __forceinline__ void warp_mlp3(const MlpDev &P, const unsigned char *
                     load_a<EB, KK>(tmp8, tmp_stride, m * 16, kt * KK, g, t, a1[m][kt]);
             __syncwarp();
         } else {
-            hidden_to_a16<PREC, MT, N1>(d1, b0, t, a1);
+            hidden_to_a16<PREC, MT, N1>(d1, a1);
         }
         float d2[MT][N2 / 8][4];
-        mma_layer<PREC, MT, N1, N2>(a1, W1, s1, g, t, d2);
+        mma_layer<PREC, MT, N1, N2>(a1, W1, s1, g, t, d2, PREC == BCF_FP8_E4M3 ? nullptr : b1);
         uint32_t a2[MT][N2 / KK][4];
         if constexpr (PREC == BCF_FP8_E4M3) {
             hidden_to_tile8<MT, N2>(d2, b1, sc1, in2, g, t, tmp8, tmp_stride);
@@ -438,23 +452,34 @@ __device__ __forceinline__ void warp_mlp3(const MlpDev &P, const unsigned char *
                     load_a<EB, KK>(tmp8, tmp_stride, m * 16, kt * KK, g, t, a2[m][kt]);
             __syncwarp();
         } else {
-            hidden_to_a16<PREC, MT, N2>(d2, b1, t, a2);
+            hidden_to_a16<PREC, MT, N2>(d2, a2);
         }
         float d3[MT][NO / 8][4];
-        mma_layer<PREC, MT, N2, NO>(a2, W2, s2, g, t, d3);
+        mma_layer<PREC, MT, N2, NO>(a2, W2, s2, g, t, d3, PREC == BCF_FP8_E4M3 ? nullptr : b2);
 #pragma unroll
         for (int nt = 0; nt < NO / 8; ++nt) {
             const int c = nt * 8 + 2 * t;
 #pragma unroll
             for (int m = 0; m < MT; ++m) {
                 const int r0 = (m0 + m) * 16 + g, r1 = r0 + 8;
-                if (c < C) {
-                    ost[r0 * C + c] = d3[m][nt][0] * sc2 + b2[c];
-                    ost[r1 * C + c] = d3[m][nt][2] * sc2 + b2[c];
-                }
-                if (c + 1 < C) {
-                    ost[r0 * C + c + 1] = d3[m][nt][1] * sc2 + b2[c + 1];
-                    ost[r1 * C + c + 1] = d3[m][nt][3] * sc2 + b2[c + 1];
+                if constexpr (PREC == BCF_FP8_E4M3) {
+                    if (c < C) {
+                        ost[r0 * C + c] = d3[m][nt][0] * sc2 + b2[c];
+                        ost[r1 * C + c] = d3[m][nt][2] * sc2 + b2[c];
+                    }
+                    if (c + 1 < C) {
+                        ost[r0 * C + c + 1] = d3[m][nt][1] * sc2 + b2[c + 1];
+                        ost[r1 * C + c + 1] = d3[m][nt][3] * sc2 + b2[c + 1];
+                    }
+                } else { // the bias is in the accumulators
+                    if (c < C) {
+                        ost[r0 * C + c] = d3[m][nt][0];
+                        ost[r1 * C + c] = d3[m][nt][2];
+                    }
+                    if (c + 1 < C) {
+                        ost[r0 * C + c + 1] = d3[m][nt][1];
+                        ost[r1 * C + c + 1] = d3[m][nt][3];
+                    }
                 }
             }
         }
@@ -481,22 +506,22 @@ __device__ __forceinline__ void warp_mlp2(const unsigned char *sw, const float *
         for (int kt = 0; kt < K0 / KK; ++kt)
             load_a<EB, KK>(in, in_stride, m0 * 16, kt * KK, g, t, a0[0][kt]);
         float d1[1][N1 / 8][4];
-        mma_layer<PREC, 1, K0, N1>(a0, W0, s0, g, t, d1);
+        mma_layer<PREC, 1, K0, N1>(a0, W0, s0, g, t, d1, b0);
         uint32_t a1[1][N1 / KK][4];
-        hidden_to_a16<PREC, 1, N1>(d1, b0, t, a1);
+        hidden_to_a16<PREC, 1, N1>(d1, a1);
         float d2[1][NO / 8][4];
-        mma_layer<PREC, 1, N1, NO>(a1, W1, s1, g, t, d2);
+        mma_layer<PREC, 1, N1, NO>(a1, W1, s1, g, t, d2, b1);
 #pragma unroll
         for (int nt = 0; nt < NO / 8; ++nt) {
             const int c = nt * 8 + 2 * t;
             const int r0 = m0 * 16 + g, r1 = r0 + 8;
             if (c < C) {
-                ost[r0 * C + c] = d2[0][nt][0] + b1[c];
-                ost[r1 * C + c] = d2[0][nt][2] + b1[c];
+                ost[r0 * C + c] = d2[0][nt][0];
+                ost[r1 * C + c] = d2[0][nt][2];
             }
             if (c + 1 < C) {
-                ost[r0 * C + c + 1] = d2[0][nt][1] + b1[c + 1];
-                ost[r1 * C + c + 1] = d2[0][nt][3] + b1[c + 1];
+                ost[r0 * C + c + 1] = d2[0][nt][1];
+                ost[r1 * C + c + 1] = d2[0][nt][3];
             }
         }
     }
