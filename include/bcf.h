@@ -88,9 +88,14 @@ int bcf_version(void);
  *   BCF_CHECK_OFFSETS    material-set query offsets decrease
  *                        (d_offsets[m+1] < d_offsets[m]); that material's
  *                        range is decoded as empty.
+ *   BCF_CHECK_TIMEOUT    a bounded wait of a decode for its tcgen05 MMAs
+ *                        ran out (bcf_set_mlp_engine, BCF_MLP_TCGEN05); the
+ *                        kernel stopped taking tiles, so part of the output
+ *                        is missing.
  */
 #define BCF_CHECK_PARTITION 0x1u
 #define BCF_CHECK_OFFSETS 0x2u
+#define BCF_CHECK_TIMEOUT 0x4u
 
 /*
  * bcf_device_check -- wait for all work on the current device (every
@@ -580,6 +585,31 @@ bcf_status bcf_pack_mode10(const float *d_params, const uint8_t *d_partitions, i
  * texture objects cannot be created.
  */
 bcf_status bcf_set_decode_variant(bcf_material mat, int32_t variant);
+
+/*
+ * bcf_set_mlp_engine -- choose the tensor-core instructions of a material's
+ * MLP (Eq. 3) in its single-material decodes: decode variants 1, 2 and 3,
+ * and variant 0 for materials whose textures share one resolution and
+ * level count (material sets keep the warp-level MMAs).
+ * BCF_MLP_MMA_SYNC (default): every warp evaluates its 32 queries with
+ * warp-level MMAs, layers chained through registers.
+ * BCF_MLP_TCGEN05: the CTA's tile of queries (256 on variant 0, 128 on the
+ * others) goes through the fifth-generation tensor cores -- one thread
+ * issues 128-row MMAs per layer (FP16 / BF16
+ * kind::f16, E4M3 kind::f8f6f4) from operand tiles in shared memory, FP32
+ * accumulators in tensor memory, read back per row for the bias / ReLU /
+ * rounding epilogue.  Both evaluate the same arithmetic (FP32 sums of exact
+ * products, FP32 bias, rounding to the operand type between layers); the
+ * summation order inside the tensor cores may differ, so outputs agree
+ * within FP32 rounding (and its operand-rounding flips), not bit for bit.
+ * A decode whose bounded wait for its MMAs runs out sets BCF_CHECK_TIMEOUT.
+ * Errors: BCF_ERR_INVALID_ARG (null material, another engine),
+ * BCF_ERR_UNSUPPORTED (FP32 materials; MLPs other than three layers
+ * K0 -> 32 -> 32 -> C or 32 -> 64 -> 64 -> C with C <= 16).
+ */
+#define BCF_MLP_MMA_SYNC 0
+#define BCF_MLP_TCGEN05 1
+bcf_status bcf_set_mlp_engine(bcf_material mat, int32_t engine);
 
 /*
  * bcf_texunit_fetch_probe -- measurement only: the rate at which the texture

@@ -81,6 +81,8 @@ def lib() -> ctypes.CDLL:
         L.bcf_sample_features.argtypes = [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_void_p, c_void_p]
         L.bcf_set_decode_variant.restype = c_int
         L.bcf_set_decode_variant.argtypes = [c_void_p, c_int32]
+        L.bcf_set_mlp_engine.restype = c_int
+        L.bcf_set_mlp_engine.argtypes = [c_void_p, c_int32]
         L.bcf_texunit_fetch_probe.restype = c_int
         L.bcf_texunit_fetch_probe.argtypes = [c_void_p, c_int32, c_int32, c_int64, c_int32, c_void_p, c_void_p]
         L.bcf_decode_material.restype = c_int
@@ -288,6 +290,12 @@ class Material:
         """bcf_set_decode_variant: 0 tile-cooperative (default), 1 per-lane, 2 texture unit (hardware trilinear),
         3 texture-unit texels with the exact FP32 filter."""
         _check(lib().bcf_set_decode_variant(self.handle, int(variant)), "bcf_set_decode_variant")
+
+    def set_mlp_engine(self, engine: str) -> None:
+        """bcf_set_mlp_engine: "mma_sync" (warp-level MMAs, default) or "tcgen05" (CTA-level MMAs with tensor-memory
+        accumulators)."""
+        code = {"mma_sync": 0, "tcgen05": 1}[engine]
+        _check(lib().bcf_set_mlp_engine(self.handle, code), "bcf_set_mlp_engine")
 
     def texunit_fetch_probe(self, n_threads: int, rounds: int, texture: int = 0, level: int = 0,
                             sink: torch.Tensor | None = None) -> torch.Tensor:

@@ -119,9 +119,12 @@ bcf_status bcf_device_check(uint32_t *h_word)
         *h_word = h;
     if (!h)
         return BCF_OK;
-    return fail(BCF_ERR_DEVICE_CHECK, "device checks fired (word 0x%x):%s%s", h,
+    return fail(BCF_ERR_DEVICE_CHECK, "device checks fired (word 0x%x):%s%s%s", h,
                 (h & BCF_CHECK_PARTITION) ? " a training block's partition id is above 31 (read as id & 31);" : "",
                 (h & BCF_CHECK_OFFSETS) ? " material-set query offsets decrease (that range was decoded as empty);"
+                                        : "",
+                (h & BCF_CHECK_TIMEOUT) ? " a decode's bounded wait for its tensor-core MMAs ran out (output "
+                                          "incomplete);"
                                         : "");
 }
 
@@ -294,6 +297,27 @@ bcf_status bcf_set_decode_variant(bcf_material m, int32_t variant)
         }
     }
     m->variant = variant;
+    return BCF_OK;
+}
+
+bcf_status bcf_set_mlp_engine(bcf_material m, int32_t engine)
+{
+    if (!m || (engine != BCF_MLP_MMA_SYNC && engine != BCF_MLP_TCGEN05))
+        return fail(BCF_ERR_INVALID_ARG, "bcf_set_mlp_engine: null material or engine not in {0, 1}");
+    if (engine == BCF_MLP_TCGEN05) {
+        const MlpDev &P = m->host.mlp;
+        const bool shape = P.n_layers == 3 && P.npad[2] == 16 &&
+                           ((P.npad[0] == 32 && P.npad[1] == 32 &&
+                             P.kpad[0] == (P.precision == BCF_FP8_E4M3 ? 32 : 16)) ||
+                            (P.npad[0] == 64 && P.npad[1] == 64 && P.kpad[0] == 32));
+        if (P.precision == BCF_FP32 || !shape)
+            return fail(BCF_ERR_UNSUPPORTED, "bcf_set_mlp_engine: tcgen05 covers FP16 / BF16 / FP8 MLPs of three "
+                                             "layers K0 -> 32 -> 32 -> C or 32 -> 64 -> 64 -> C (C <= 16)");
+    }
+    m->host.mlp_engine = engine;
+    cudaError_t e = cudaMemcpy(&m->dev->mlp_engine, &m->host.mlp_engine, sizeof(int32_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess)
+        return cuda_status(e, "bcf_set_mlp_engine");
     return BCF_OK;
 }
 

@@ -5,6 +5,7 @@
 #include "bc6h_unpack.cuh"
 #include "bcf_kernels.h"
 #include "bcf_mlp.cuh"
+#include "bcf_tcmlp.cuh"
 #include "bcf_sample.cuh"
 
 namespace bcf {
@@ -265,6 +266,104 @@ __global__ void __launch_bounds__(128) k_decode_mma(MaterialDev M, TexUnitObjs T
     }
 }
 
+// The same decode with the MLP on tcgen05 (bcf_set_mlp_engine): persistent CTAs of 4 warps over 128-query tiles;
+// each thread computes its query's features (texture-unit texels or trilinear, or the per-lane BC6H decode,
+// exactly as k_decode_mma) into the CTA's canonical A0 tile, the tile goes through tc_mlp3 (one thread issues
+// 128-row MMAs per layer, accumulators in tensor memory), and every warp stores its 32 rows.
+template <int PREC, int HW, int K0, int N1, int N2, int NO>
+struct MmaTcLayout {
+    using T = TcMlp<PREC, 4, K0, N1, N2, NO>;
+    int b_off, x_off, y_off, bar_off, tslot_off, total;
+    __host__ __device__ explicit MmaTcLayout(const MlpDev &P)
+    {
+        const int C = P.dims[P.n_layers];
+        b_off = (T::W_BYTES + 127) & ~127;
+        x_off = b_off + ((mlp_smem_bias_floats(P) * 4 + 127) & ~127);
+        y_off = x_off + ((T::X_BYTES + 127) & ~127);
+        const int yb = T::Y_BYTES > 128 * C * 4 ? T::Y_BYTES : 128 * C * 4;
+        bar_off = y_off + ((yb + 127) & ~127);
+        tslot_off = bar_off + 16;
+        total = tslot_off + 16;
+    }
+};
+
+template <int PREC, int HW, int K0, int N1, int N2, int NO>
+__global__ void __launch_bounds__(128) k_decode_mma_tc(MaterialDev M, TexUnitObjs T, const float *__restrict__ u,
+                                                       const float *__restrict__ v, const float *__restrict__ s,
+                                                       int64_t n, void *__restrict__ out, int out_fp16,
+                                                       unsigned *__restrict__ check)
+{
+    using TM = TcMlp<PREC, 4, K0, N1, N2, NO>;
+    extern __shared__ __align__(16) unsigned char smem[];
+    const MlpDev &P = M.mlp;
+    const MmaTcLayout<PREC, HW, K0, N1, N2, NO> LY(P);
+    unsigned char *sw = smem;
+    float *sb = (float *)(smem + LY.b_off);
+    unsigned char *x = smem + LY.x_off, *y = smem + LY.y_off;
+    uint64_t *bar = (uint64_t *)(smem + LY.bar_off);
+    uint32_t *tslot = (uint32_t *)(smem + LY.tslot_off);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int C = P.dims[P.n_layers];
+    tc_load_weights<PREC, 4, K0, N1, N2, NO>(P, sw, sb);
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_init_fence();
+    }
+    if (warp == 0)
+        tc_alloc(tslot, TM::NCOLS);
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tslot;
+    uint32_t phase = 0;
+    const float inv0 = PREC == BCF_FP8_E4M3 ? P.inv_act_scale[0] : 1.0f;
+    const int64_t tiles = (n + 127) / 128;
+    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
+        const int64_t q = tile * 128 + threadIdx.x;
+        const bool live = q < n;
+        TcRowWriter<PREC, 4, K0, N1, N2, NO> tw{x, (int)threadIdx.x, inv0, 0.0f};
+        const float sq = live && s ? s[q] : 0.0f;
+        const float uu = sanitize(live ? u[q] : 0.0f, M.wrap), vv = sanitize(live ? v[q] : 0.0f, M.wrap);
+#pragma unroll 1
+        for (int t = 0; t < M.n_tex; ++t) {
+            float3 f = make_float3(0.0f, 0.0f, 0.0f);
+            if (live) {
+                if (HW == 1)
+                    f = texture_trilinear_hw(M.tex[t], T.tex[t], uu, vv, sq);
+                else if (HW == 2)
+                    f = sample_texture_hwpoint(M.tex[t], T.texp[t], M.wrap, uu, vv, sq);
+                else
+                    f = sample_texture(M.tex[t], M.wrap, M.is_signed != 0, uu, vv, sq);
+            }
+            tw.put(3 * t, f.x);
+            tw.put(3 * t + 1, f.y);
+            tw.put(3 * t + 2, f.z);
+        }
+        int col = 3 * M.n_tex;
+        if (M.lod_input)
+            tw.put(col++, live ? (isnan(sq) ? 0.0f : fmaxf(sq, 0.0f)) : 0.0f);
+        for (; col < K0; ++col)
+            tw.put(col, 0.0f);
+        tw.finish(col);
+        bool ok = tc_mlp3<PREC, 4, K0, N1, N2, NO>(P, sw, sb, x, y, (float *)y, C, bar, phase, tmem, 1 << 20);
+        ok = __syncthreads_and(ok) != 0;
+        if (!ok) {
+            if (threadIdx.x == 0 && check)
+                atomicOr(check, BCF_CHECK_TIMEOUT);
+            break; // uniform: stop taking tiles
+        }
+        const int64_t q0 = tile * 128 + warp * 32;
+        if (q0 < n)
+            store_warp_rows((const float *)y + warp * 32 * C, out, q0, (int)min((int64_t)32, n - q0), C, out_fp16,
+                            lane);
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        tc_dealloc(tmem, TM::NCOLS);
+    }
+}
+
 // Material sets through the texture unit: a persistent CTA of 4 warps grabs 128-query tiles of a work list over
 // the materials (tiles never straddle two materials); when the material changes, its description, texture
 // objects and MLP weights replace the previous ones in shared memory; every warp then decodes its 32 queries as
@@ -494,9 +593,43 @@ int64_t mma_smem_bytes(const MlpDev &P, int warps)
 }
 
 template <int PREC, int HW, int K0, int N1, int N2, int NO>
+static cudaError_t launch_mma_tc_shape(const MaterialDev &M, const TexUnitObjs &T, const float *u, const float *v,
+                                       const float *s, int64_t n, void *out, int out_fp16, cudaStream_t st)
+{
+    using TM = TcMlp<PREC, 4, K0, N1, N2, NO>;
+    const int64_t smem = MmaTcLayout<PREC, HW, K0, N1, N2, NO>(M.mlp).total;
+    if (smem > 200 * 1024)
+        return cudaErrorInvalidConfiguration;
+    auto kern = k_decode_mma_tc<PREC, HW, K0, N1, N2, NO>;
+    static int per_sm = 0;
+    if (!per_sm) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        // resident CTAs per SM from registers, shared memory and tensor-memory columns (512 per SM; every
+        // CTA holds its columns for its whole life)
+        cudaFuncAttributes fa{};
+        int regs = 64;
+        if (cudaFuncGetAttributes(&fa, kern) == cudaSuccess && fa.numRegs > 0)
+            regs = fa.numRegs;
+        int dev = 0, smem_sm = 228 * 1024;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        const int by_regs = 65536 / (128 * ((regs + 7) & ~7));
+        const int by_smem = smem_sm / (int)(smem + 1024);
+        per_sm = max(1, min(min(by_regs, by_smem), min(512 / TM::NCOLS, 16)));
+    }
+    const int64_t tiles = (n + 127) / 128;
+    const int64_t grid = min(tiles, (int64_t)sm_count() * per_sm);
+    kern<<<(unsigned)grid, 128, (size_t)smem, st>>>(M, T, u, v, s, n, out, out_fp16, check_word());
+    return cudaGetLastError();
+}
+
+template <int PREC, int HW, int K0, int N1, int N2, int NO>
 static cudaError_t launch_mma_shape(const MaterialDev &M, const TexUnitObjs &T, const float *u, const float *v,
                                     const float *s, int64_t n, void *out, int out_fp16, cudaStream_t st)
 {
+    if constexpr (K0 != 0 && N2 != 0)
+        if (M.mlp_engine == BCF_MLP_TCGEN05)
+            return launch_mma_tc_shape<PREC, HW, K0, N1, N2, NO>(M, T, u, v, s, n, out, out_fp16, st);
     const int threads = 128;
     const int64_t smem = mma_smem_bytes<PREC, K0, N1, N2>(M.mlp, threads / 32);
     if (smem > 200 * 1024)

@@ -28,6 +28,7 @@
 #include "bcf_kernels.h"
 #include "bcf_mlp.cuh"
 #include "bcf_sample.cuh"
+#include "bcf_tcmlp.cuh"
 
 namespace bcf {
 
@@ -800,6 +801,45 @@ __host__ __device__ inline GeoLayout geo_layout(const MlpDev &P, int cap)
     return L;
 }
 
+// Layout with the MLP on tcgen05 (bcf_tcmlp.cuh): the canonical weight tiles, the A0 / A2 tile (x), the
+// mbarrier and the tensor-memory address; the A1 tile and the output staging live in the arena (free once the
+// last round's filter is done, which the MLP's first CTA barrier guarantees).
+struct GeoTcLayout {
+    int w_bytes, b_bytes, meta, sraw, sidx, arena, x, bar, tslot, total;
+};
+
+template <int PREC, int K0, int N1, int N2, int NO>
+__host__ __device__ inline GeoTcLayout geo_tc_layout(const MlpDev &P, int cap)
+{
+    using T = TcMlp<PREC, 8, K0, N1, N2, NO>;
+    GeoTcLayout L;
+    int off = 0;
+    L.w_bytes = T::W_BYTES;
+    off += (T::W_BYTES + 127) & ~127;
+    L.b_bytes = off;
+    off += (mlp_smem_bias_floats(P) * 4 + 15) & ~15;
+    L.meta = off;
+    off += (int)((2 * sizeof(GeoMeta) + 15) & ~15);
+    L.sraw = off;
+    off += cap * 16;
+    L.sidx = off;
+    off += (cap * 2 + 127) & ~127;
+    L.arena = off;
+    const int ostb = 32 * 8 * P.dims[P.n_layers] * 4;
+    int ab = cap * 16 * 8;
+    ab = ab > T::Y_BYTES ? ab : T::Y_BYTES;
+    ab = ab > ostb ? ab : ostb;
+    off += (ab + 127) & ~127;
+    L.x = off;
+    off += (T::X_BYTES + 127) & ~127;
+    L.bar = off;
+    off += 16;
+    L.tslot = off;
+    off += 16;
+    L.total = off;
+    return L;
+}
+
 __device__ __forceinline__ void reset_geo_meta(GeoMeta &G)
 {
     for (int i = threadIdx.x; i < BCF_MAX_LEVELS; i += kTileQ) {
@@ -837,40 +877,6 @@ __device__ __forceinline__ int box_offset(const GeoMeta &G, unsigned mask, int l
 __device__ __noinline__ float3 sample_texture_ool(const TexDev &T, int wrap, bool sgn, float u, float v, float s)
 {
     return sample_texture(T, wrap, sgn, u, v, s);
-}
-
-// Coalesced store of a warp's rows [q0, q0 + rows) from the FP32 staging tile ost[rows][C]: FP16 output in
-// 16-byte chunks of 8 values (q0 is a multiple of 32, so a chunk never straddles the 16-byte alignment of out),
-// the tail value by value; FP32 output in chunks of 4.
-__device__ __forceinline__ void store_warp_rows(const float *ost, void *out, int64_t q0, int rows, int C, int out_fp16,
-                                                int lane)
-{
-    const int tot = rows * C;
-    if (out_fp16) {
-        __half *o = (__half *)out + q0 * C;
-        const int full = tot >> 3;
-        for (int k = lane; k < full; k += 32) {
-            const float4 a = *reinterpret_cast<const float4 *>(ost + 8 * k);
-            const float4 b = *reinterpret_cast<const float4 *>(ost + 8 * k + 4);
-            const __half2 h0 = __floats2half2_rn(a.x, a.y), h1 = __floats2half2_rn(a.z, a.w);
-            const __half2 h2 = __floats2half2_rn(b.x, b.y), h3 = __floats2half2_rn(b.z, b.w);
-            uint4 w;
-            w.x = *reinterpret_cast<const uint32_t *>(&h0);
-            w.y = *reinterpret_cast<const uint32_t *>(&h1);
-            w.z = *reinterpret_cast<const uint32_t *>(&h2);
-            w.w = *reinterpret_cast<const uint32_t *>(&h3);
-            *reinterpret_cast<uint4 *>(o + 8 * k) = w;
-        }
-        for (int i = (full << 3) + lane; i < tot; i += 32)
-            o[i] = __float2half_rn(ost[i]);
-    } else {
-        float *o = (float *)out + q0 * C;
-        const int full = tot >> 2;
-        for (int k = lane; k < full; k += 32)
-            *reinterpret_cast<float4 *>(o + 4 * k) = *reinterpret_cast<const float4 *>(ost + 4 * k);
-        for (int i = (full << 2) + lane; i < tot; i += 32)
-            o[i] = ost[i];
-    }
 }
 
 // Decode arena blocks [first, items) (sorted by mode) with 1 << lk threads per block: each thread decodes the
@@ -927,46 +933,91 @@ struct RowWriter {
     }
 };
 
-template <int PREC, int CAP, int K0, int N1, int N2, int NO>
+template <int PREC, int CAP, int K0, int N1, int N2, int NO, bool TC>
 __global__ void __launch_bounds__(kTileQ, kGeoMinBlocks) k_decode_geo(MaterialDev M, const float *__restrict__ qu,
                                                           const float *__restrict__ qv, const float *__restrict__ qs,
-                                                          int64_t n, void *__restrict__ out, int out_fp16)
+                                                          int64_t n, void *__restrict__ out, int out_fp16,
+                                                          unsigned *__restrict__ check)
 {
     static_assert(CAP <= kTileQ, "one block item per thread while loading");
     extern __shared__ __align__(16) unsigned char smem[];
     const MlpDev &P = M.mlp;
-    const GeoLayout LY = geo_layout<PREC>(P, CAP);
-    unsigned char *sw = smem;
-    float *sb = (float *)(smem + LY.b_bytes);
-    GeoMeta *meta = (GeoMeta *)(smem + LY.meta);
-    uint4 *sraw = (uint4 *)(smem + LY.sraw);
-    uint16_t *sidx = (uint16_t *)(smem + LY.sidx);
-    uint2 *arena = (uint2 *)(smem + LY.arena);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    unsigned char *act0 = smem + LY.total - (kTileQ / 32 - warp) * LY.per_warp;
-    unsigned char *tmp8 = act0 + LY.tmp8;
-    float *ost = (float *)act0; // output staging aliases the input tile or follows it (geo_layout)
-    {
-        const int C = P.dims[P.n_layers];
-        const int in_stride = tile_stride_bytes<PREC>(P.kpad[0]);
-        if (!(16 * C * 4 <= 16 * in_stride))
-            ost = (float *)(act0 + ((32 * in_stride + 15) & ~15));
-    }
     const int Cn = P.dims[P.n_layers];
     const int row_stride = tile_stride_bytes<PREC>(P.kpad[0]);
-    unsigned char *myrow = act0 + lane * row_stride;
     const float inv0 = PREC == BCF_FP8_E4M3 ? P.inv_act_scale[0] : 1.0f;
-    RowWriter<PREC> rw{myrow, inv0, 0.0f};
+    unsigned char *sw;
+    float *sb;
+    GeoMeta *meta;
+    uint4 *sraw;
+    uint16_t *sidx;
+    uint2 *arena;
+    unsigned char *act0 = nullptr, *tmp8 = nullptr, *xtile = nullptr;
+    float *ost;
+    uint64_t *bar = nullptr;
+    uint32_t *tslot = nullptr;
+    if constexpr (TC) {
+        const GeoTcLayout LY = geo_tc_layout<PREC, K0, N1, N2, NO>(P, CAP);
+        sw = smem;
+        sb = (float *)(smem + LY.b_bytes);
+        meta = (GeoMeta *)(smem + LY.meta);
+        sraw = (uint4 *)(smem + LY.sraw);
+        sidx = (uint16_t *)(smem + LY.sidx);
+        arena = (uint2 *)(smem + LY.arena);
+        xtile = smem + LY.x;
+        ost = (float *)(smem + LY.arena); // the output staging: rows [32 warp, 32 warp + 32) of [256][C]
+        bar = (uint64_t *)(smem + LY.bar);
+        tslot = (uint32_t *)(smem + LY.tslot);
+    } else {
+        const GeoLayout LY = geo_layout<PREC>(P, CAP);
+        sw = smem;
+        sb = (float *)(smem + LY.b_bytes);
+        meta = (GeoMeta *)(smem + LY.meta);
+        sraw = (uint4 *)(smem + LY.sraw);
+        sidx = (uint16_t *)(smem + LY.sidx);
+        arena = (uint2 *)(smem + LY.arena);
+        act0 = smem + LY.total - (kTileQ / 32 - warp) * LY.per_warp;
+        tmp8 = act0 + LY.tmp8;
+        ost = (float *)act0; // output staging aliases the input tile or follows it (geo_layout)
+        if (!(16 * Cn * 4 <= 16 * row_stride))
+            ost = (float *)(act0 + ((32 * row_stride + 15) & ~15));
+    }
+    RowWriter<PREC> rw{act0 + lane * row_stride, inv0, 0.0f};
+    TcRowWriter<PREC, 8, (K0 > 0 ? K0 : 16), (N1 > 0 ? N1 : 16), (N2 > 0 ? N2 : 16), (NO > 0 ? NO : 16)> tw{
+        xtile, (int)threadIdx.x, inv0, 0.0f};
+    const auto put = [&](int col, float x) {
+        if constexpr (TC)
+            tw.put(col, x);
+        else
+            rw.put(col, x);
+    };
     const int nt = M.n_tex;
     const int wrap = M.wrap;
     const bool sgn = M.is_signed != 0;
     const TexDev &T0 = M.tex[0];
     const unsigned lanes_lt = (1u << lane) - 1u;
 
-    load_mlp_smem<PREC>(P, sw, sb);
+    uint32_t tmem = 0, phase = 0;
+    constexpr int kTcCols = TcMlp<PREC, 8, (K0 > 0 ? K0 : 16), (N1 > 0 ? N1 : 16), (N2 > 0 ? N2 : 16),
+                                  (NO > 0 ? NO : 16)>::NCOLS;
+    if constexpr (TC) {
+        tc_load_weights<PREC, 8, K0, N1, N2, NO>(P, sw, sb);
+        if (threadIdx.x == 0) {
+            mbar_init(bar, 1);
+            mbar_init_fence();
+        }
+        if (warp == 0)
+            tc_alloc(tslot, kTcCols);
+    } else {
+        load_mlp_smem<PREC>(P, sw, sb);
+    }
     reset_geo_meta(meta[0]);
     reset_geo_meta(meta[1]);
     __syncthreads();
+    if constexpr (TC) {
+        tc_fence_after();
+        tmem = *tslot;
+    }
 
     const int64_t tiles = (n + kTileQ - 1) / kTileQ;
     float nu = 0.0f, nv = 0.0f, ns = 0.0f, nu_ref = 0.0f, nv_ref = 0.0f;
@@ -1074,9 +1125,9 @@ __global__ void __launch_bounds__(kTileQ, kGeoMinBlocks) k_decode_geo(MaterialDe
                 float3 f = make_float3(0.f, 0.f, 0.f);
                 if (active)
                     f = sample_texture_ool(M.tex[t], wrap, sgn, u, v, s);
-                rw.put(3 * t, f.x);
-                rw.put(3 * t + 1, f.y);
-                rw.put(3 * t + 2, f.z);
+                put(3 * t, f.x);
+                put(3 * t + 1, f.y);
+                put(3 * t + 2, f.z);
             }
             __syncthreads(); // the next tile's box atomics stay behind this tile's reset of their buffer
         } else {
@@ -1210,34 +1261,62 @@ __global__ void __launch_bounds__(kTileQ, kGeoMinBlocks) k_decode_geo(MaterialDe
                         }
                     }
                     const int t = t0 + tt;
-                    rw.put(3 * t, f0);
-                    rw.put(3 * t + 1, f1);
-                    rw.put(3 * t + 2, f2);
+                    put(3 * t, f0);
+                    put(3 * t + 1, f1);
+                    put(3 * t + 2, f2);
                 }
             }
         }
         {
             int col = 3 * nt;
             if (M.lod_input) {
-                rw.put(col, active ? (isnan(s) ? 0.0f : fmaxf(s, 0.0f)) : 0.0f);
+                put(col, active ? (isnan(s) ? 0.0f : fmaxf(s, 0.0f)) : 0.0f);
                 ++col;
             }
             for (; col < P.kpad[0]; ++col)
-                rw.put(col, 0.0f);
-            rw.finish(col);
+                put(col, 0.0f);
+            if constexpr (TC)
+                tw.finish(col);
+            else
+                rw.finish(col);
         }
-        __syncwarp();
         // ---- 6. MLP on the tensor cores, coalesced store
-        if constexpr (N2 == 0)
-            warp_mlp2<PREC, K0, N1, NO>(sw, sb, act0, row_stride, ost, Cn);
-        else
-            warp_mlp3<PREC, K0, N1, N2, NO>(P, sw, sb, act0, row_stride, tmp8,
-                                            tile_stride_bytes<BCF_FP8_E4M3>(N1 > N2 ? N1 : N2), ost, Cn);
-        __syncwarp();
-        const int64_t q0 = q_first + warp * 32;
-        if (q0 < n)
-            store_warp_rows(ost, out, q0, (int)min((int64_t)32, n - q0), Cn, out_fp16, lane);
-        __syncwarp();
+        if constexpr (TC) {
+            // the CTA tile's 256 rows through tcgen05 (its first barrier also ends every warp's filter)
+            bool ok = tc_mlp3<PREC, 8, K0, N1, N2, NO>(P, sw, sb, xtile, (unsigned char *)arena, ost, Cn, bar, phase,
+                                                       tmem, 1 << 20);
+            ok = __syncthreads_and(ok) != 0;
+            if (!ok) {
+                if (threadIdx.x == 0 && check)
+                    atomicOr(check, BCF_CHECK_TIMEOUT);
+                break; // uniform: stop taking tiles
+            }
+            const int64_t q0 = q_first + warp * 32;
+            if (q0 < n)
+                store_warp_rows(ost + warp * 32 * Cn, out, q0, (int)min((int64_t)32, n - q0), Cn, out_fp16, lane);
+        } else {
+            __syncwarp();
+            if constexpr (N2 == 0)
+                warp_mlp2<PREC, K0, N1, NO>(sw, sb, act0, row_stride, ost, Cn);
+            else
+                warp_mlp3<PREC, K0, N1, N2, NO>(P, sw, sb, act0, row_stride, tmp8,
+                                                tile_stride_bytes<BCF_FP8_E4M3>(N1 > N2 ? N1 : N2), ost, Cn);
+            __syncwarp();
+            const int64_t q0 = q_first + warp * 32;
+            if (q0 < n)
+                store_warp_rows(ost, out, q0, (int)min((int64_t)32, n - q0), Cn, out_fp16, lane);
+            __syncwarp();
+        }
+    }
+    if constexpr (TC) {
+        // every MMA of this CTA has completed (each was waited for, or the bounded wait below gives up): free
+        // the tensor memory
+        tc_fence_before();
+        __syncthreads();
+        if (warp == 0) {
+            tc_fence_after();
+            tc_dealloc(tmem, kTcCols);
+        }
     }
 }
 
@@ -1260,25 +1339,56 @@ static int tiled_sms()
 
 constexpr int kGeoCap = 224; // block arena of the single-geometry kernel (4 CTAs of 256 threads per SM)
 
-template <int PREC, int K0, int N1, int N2, int NO>
-static cudaError_t launch_geo_shape(const MaterialDev &M, const float *u, const float *v, const float *s, int64_t n,
-                                    void *out, int out_fp16, cudaStream_t st)
+template <int PREC, int K0, int N1, int N2, int NO, bool TC>
+static cudaError_t launch_geo_engine(const MaterialDev &M, const float *u, const float *v, const float *s, int64_t n,
+                                     void *out, int out_fp16, cudaStream_t st)
 {
-    const int64_t smem = geo_layout<PREC>(M.mlp, kGeoCap).total;
+    int64_t smem;
+    int max_per_sm = 32;
+    if constexpr (TC) {
+        smem = geo_tc_layout<PREC, K0, N1, N2, NO>(M.mlp, kGeoCap).total;
+        // every resident CTA holds its tensor-memory columns for its whole life: at most 512 columns per SM
+        max_per_sm = 512 / TcMlp<PREC, 8, K0, N1, N2, NO>::NCOLS;
+    } else {
+        smem = geo_layout<PREC>(M.mlp, kGeoCap).total;
+    }
     if (smem > 227 * 1024)
         return cudaErrorInvalidConfiguration;
-    auto kern = k_decode_geo<PREC, kGeoCap, K0, N1, N2, NO>;
+    auto kern = k_decode_geo<PREC, kGeoCap, K0, N1, N2, NO, TC>;
     static int configured = 0;
     if (!configured) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
         configured = 1;
     }
-    int per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTileQ, (size_t)smem);
+    static int per_sm = 0;
+    if (!per_sm) {
+        // resident CTAs per SM from the kernel's registers and shared memory (the occupancy query reports a
+        // single CTA for kernels that use tensor memory)
+        cudaFuncAttributes fa{};
+        int regs = 64;
+        if (cudaFuncGetAttributes(&fa, kern) == cudaSuccess && fa.numRegs > 0)
+            regs = fa.numRegs;
+        int dev = 0, smem_sm = 228 * 1024;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        const int by_regs = 65536 / (kTileQ * ((regs + 7) & ~7));
+        const int by_smem = smem_sm / (int)(smem + 1024);
+        per_sm = max(1, min(min(by_regs, by_smem), max_per_sm));
+    }
     const int64_t tiles = (n + kTileQ - 1) / kTileQ;
-    const int64_t grid = min(tiles, (int64_t)tiled_sms() * max(per_sm, 1));
-    kern<<<(unsigned)grid, kTileQ, (size_t)smem, st>>>(M, u, v, s, n, out, out_fp16);
+    const int64_t grid = min(tiles, (int64_t)tiled_sms() * per_sm);
+    kern<<<(unsigned)grid, kTileQ, (size_t)smem, st>>>(M, u, v, s, n, out, out_fp16, check_word());
     return cudaGetLastError();
+}
+
+template <int PREC, int K0, int N1, int N2, int NO>
+static cudaError_t launch_geo_shape(const MaterialDev &M, const float *u, const float *v, const float *s, int64_t n,
+                                    void *out, int out_fp16, cudaStream_t st)
+{
+    if constexpr (N2 != 0)
+        if (M.mlp_engine == 1)
+            return launch_geo_engine<PREC, K0, N1, N2, NO, true>(M, u, v, s, n, out, out_fp16, st);
+    return launch_geo_engine<PREC, K0, N1, N2, NO, false>(M, u, v, s, n, out, out_fp16, st);
 }
 
 template <int PREC, int K0, int N1, int N2, int NO>

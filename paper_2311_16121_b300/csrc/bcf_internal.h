@@ -58,6 +58,7 @@ struct MaterialDev {
     int32_t group_first[BCF_MAX_TEX];  // a texture of each group (its geometry)
     TexDev tex[BCF_MAX_TEX];
     MlpDev mlp;
+    int32_t mlp_engine;                // BCF_MLP_MMA_SYNC or BCF_MLP_TCGEN05 (bcf_set_mlp_engine)
 };
 
 // The current device's check word (include/bcf.h, BCF_CHECK_*), created on the first call; nullptr if that

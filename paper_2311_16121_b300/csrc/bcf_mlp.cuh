@@ -265,6 +265,40 @@ __device__ __forceinline__ void store_feature(unsigned char *row, int col, float
     }
 }
 
+// Coalesced store of a warp's rows [q0, q0 + rows) from the FP32 staging tile ost[rows][C]: FP16 output in
+// 16-byte chunks of 8 values (q0 is a multiple of 32, so a chunk never straddles the 16-byte alignment of out),
+// the tail value by value; FP32 output in chunks of 4.
+__device__ __forceinline__ void store_warp_rows(const float *ost, void *out, int64_t q0, int rows, int C, int out_fp16,
+                                                int lane)
+{
+    const int tot = rows * C;
+    if (out_fp16) {
+        __half *o = (__half *)out + q0 * C;
+        const int full = tot >> 3;
+        for (int k = lane; k < full; k += 32) {
+            const float4 a = *reinterpret_cast<const float4 *>(ost + 8 * k);
+            const float4 b = *reinterpret_cast<const float4 *>(ost + 8 * k + 4);
+            const __half2 h0 = __floats2half2_rn(a.x, a.y), h1 = __floats2half2_rn(a.z, a.w);
+            const __half2 h2 = __floats2half2_rn(b.x, b.y), h3 = __floats2half2_rn(b.z, b.w);
+            uint4 w;
+            w.x = *reinterpret_cast<const uint32_t *>(&h0);
+            w.y = *reinterpret_cast<const uint32_t *>(&h1);
+            w.z = *reinterpret_cast<const uint32_t *>(&h2);
+            w.w = *reinterpret_cast<const uint32_t *>(&h3);
+            *reinterpret_cast<uint4 *>(o + 8 * k) = w;
+        }
+        for (int i = (full << 3) + lane; i < tot; i += 32)
+            o[i] = __float2half_rn(ost[i]);
+    } else {
+        float *o = (float *)out + q0 * C;
+        const int full = tot >> 2;
+        for (int k = lane; k < full; k += 32)
+            *reinterpret_cast<float4 *>(o + 4 * k) = *reinterpret_cast<const float4 *>(ost + 4 * k);
+        for (int i = (full << 2) + lane; i < tot; i += 32)
+            o[i] = ost[i];
+    }
+}
+
 // ----------------------------------------------------------- FP32 SIMT MLP
 
 // Fully unrolled dense layer y = W x + b (W row-major [NO][NI] in shared

@@ -467,3 +467,55 @@ def test_texunit_fetch_probe_sums_the_decoded_footprints():
                                                   np.float32(val[y1, x0, 2] + val[y1, x1, 0])))
             ref[t] = acc
         np.testing.assert_array_equal(got, ref)
+
+
+# --------------------------------------------------------------------------- tcgen05 MLP engine
+
+@pytest.mark.parametrize("precision", ["fp16", "bf16", "fp8"])
+@pytest.mark.parametrize("shape", ["13-32-32-9", "25-64-64-9"])
+def test_tcgen05_mlp_engine_matches_oracle(precision, shape):
+    """bcf_set_mlp_engine(BCF_MLP_TCGEN05): the software tile decode with the MLP on tcgen05 (CTA-level MMAs,
+    tensor-memory accumulators) against the quantisation-aware oracle under the strict check, and against the
+    warp-level MMA engine within the tolerance (the two sum in different orders)."""
+    bcf = _bcf()
+    if shape == "13-32-32-9":
+        w = workloads.small_screen(res=128, width=200, height=61)
+    else:
+        w = workloads.small_screen(n_tex=8, res=64, dims=(25, 64, 64, 9), width=150, height=53)
+    m = workloads.upload(w, precision)
+    u, v, s = workloads.queries_to_device(w)
+    ref_engine = m.decode(u, v, s, out_dtype=torch.float32).cpu().numpy().astype(np.float64)
+    m.set_mlp_engine("tcgen05")
+    got = m.decode(u, v, s, out_dtype=torch.float32).cpu().numpy().astype(np.float64)
+    again = m.decode(u, v, s, out_dtype=torch.float32).cpu().numpy().astype(np.float64)
+    np.testing.assert_array_equal(got, again)  # deterministic
+    assert bcf.device_check() == 0
+    Wst, bias, a, ws = w.weights(precision)
+    P = oracle.Mlp(w.dims, precision, Wst, bias, a, ws)
+    mat = _oracle_material(w)
+    ref_q = oracle.decode(mat, P, w.u, w.v, w.s, quant_aware=True, threads=8)
+    worst, r = _quant_check(got, ref_q, TOL[precision], f"tcgen05 {precision} {shape}", mat, P, w.u, w.v, w.s)
+    print(f"tcgen05 {precision} {shape}: per-channel max {np.round(worst, 6)}, flips {r['flips']}, "
+          f"max |tcgen05 - mma.sync| {np.abs(got - ref_engine).max():.2e}")
+    # the texture-unit texels (variant 3) and the per-lane decode (variant 1) with the tcgen05 MLP: the same
+    # features and the same MMAs, so the same outputs
+    for variant in (3, 1):
+        m.set_decode_variant(variant)
+        other = m.decode(u, v, s, out_dtype=torch.float32).cpu().numpy().astype(np.float64)
+        np.testing.assert_array_equal(other, got)
+    m.set_decode_variant(0)
+    m.set_mlp_engine("mma_sync")
+    np.testing.assert_array_equal(m.decode(u, v, s, out_dtype=torch.float32).cpu().numpy().astype(np.float64),
+                                  ref_engine)
+
+
+def test_tcgen05_mlp_engine_rejects_other_shapes():
+    bcf = _bcf()
+    w = workloads.small_screen(res=32, width=8, height=8, dims=(13, 16, 16, 9))
+    m = workloads.upload(w, "fp16")
+    with pytest.raises(bcf.BcfError) as e:
+        m.set_mlp_engine("tcgen05")
+    assert e.value.status == 2
+    m32 = workloads.upload(workloads.small_screen(res=32, width=8, height=8), "fp32")
+    with pytest.raises(bcf.BcfError):
+        m32.set_mlp_engine("tcgen05")
