@@ -215,8 +215,11 @@ bcf_status bcf_decode_material(bcf_material mat, const float *d_u, const float *
  * 2 x (8 + 4 [with s] + C x out bytes) per query plus 1 KB of alignment, and
  * the chunk size is chosen so the call runs in at least about four chunks.
  * h_u, h_v, h_s (may be NULL when the material has no LOD input): n floats;
- * h_out: [n][C] in out_precision.  No allocation besides the streams and
- * events, which are released when their work completes.
+ * h_out: [n][C] in out_precision.  The three streams and eight events of
+ * the pipeline belong to the material: the first call creates them (the
+ * only allocation), bcf_destroy_material releases them.  Calls on one
+ * material therefore must not overlap (issue them from one host thread, or
+ * serialise them); later calls create nothing.
  * Errors: BCF_ERR_INVALID_ARG for null pointers, scratch not 256-byte aligned
  * or too small for one 256-query chunk; the errors of bcf_decode_material;
  * BCF_ERR_CUDA.
@@ -246,8 +249,9 @@ typedef struct bcf_material_set_s *bcf_material_set;
  * (three layers, K0 <= 16 (FP8: 32) -> 32 -> 32 -> C <= 16, or
  * K0 <= 32 -> 64 -> 64 -> C <= 16), the set decodes through the texture unit
  * the same way (texture-unit texels, exact FP32 filter) with a persistent
- * kernel over 128-query tiles, and bcf_autotune_material_set has nothing to
- * tune; otherwise it uses the tile-cooperative software decode.
+ * kernel over 128-query tiles (bcf_autotune_material_set picks its CTAs per
+ * SM and tiles per grab); otherwise it uses the tile-cooperative software
+ * decode.
  * Errors: BCF_ERR_INVALID_ARG (n out of [1, BCF_MAX_SET], null
  * materials, materials that do not share the MLP / texture count),
  * BCF_ERR_UNSUPPORTED (FP32 materials: the set path is the tensor-core
@@ -275,8 +279,10 @@ bcf_status bcf_decode_material_set(bcf_material_set set, const int64_t *d_offset
 
 /*
  * bcf_autotune_material_set -- time the set-decode launch configurations
- * (shared-memory block arena 256 / 320 blocks, 1-3 persistent CTAs per SM,
- * 1 / 2 / 4 / 8 tiles per work-counter grab) on the given workload with
+ * (software sets: shared-memory block arena 256 / 320 blocks, 1-3 persistent
+ * CTAs per SM; texture-unit sets: 4 / 6 / 8 CTAs per SM, capped by
+ * occupancy; both: 1 / 2 / 4 / 8 tiles per work-counter grab) on the given
+ * workload with
  * CUDA events (synchronises the stream; the output is overwritten), keep the
  * fastest for the set, and return it in *cap, *ctas_per_sm, *chunk (any may
  * be NULL).  bcf_material_set_config reads the current configuration.
@@ -337,8 +343,13 @@ bcf_status bcf_material_set_config(bcf_material_set set, int32_t *cap, int32_t *
  * texels row-major per level; d_params, d_grad, d_adam_m, d_adam_v have
  * that layout, d_partition is ignored, the texel values are filtered
  * trilinearly (Eq. 10) without any compression emulation or bound, and
- * bcf_train_export does not apply.  Supported for three-layer MLPs
- * dims[0] <= 16 -> 32 -> 32 -> 9 (BCF_ERR_UNSUPPORTED otherwise).
+ * bcf_train_export does not apply.  Supported for MLPs dims[0] <= 16 ->
+ * 32 -> 32 -> C and for the paper's two-layer dims[0] <= 16 -> 16 -> C
+ * (C <= 9; BCF_ERR_UNSUPPORTED otherwise).
+ *
+ * Kernels: those two MLP shapes train on the tensor cores (BF16 products,
+ * FP32 sums, the output gradient split into two BF16 terms); other shapes
+ * on a SIMT kernel with the same rounding of weights and layer inputs.
  *
  * Reference material F(M) (Sec. 5.1): 9 channels, FP16, a mip chain from
  * target_res down to 4 x 4 (level l is target_res >> l), channels 0..7
@@ -575,9 +586,13 @@ bcf_status bcf_pack_mode10(const float *d_params, const uint8_t *d_partitions, i
  * the outputs equal those of variants 0 and 1 bit for bit.  The fastest
  * exact variant.
  * Setting variant 2 or 3 allocates the mipmapped arrays and copies the
- * blocks into them (synchronously, once per material; later changes of the
- * caller's block arrays are not seen by these variants); they are freed
- * with the material.  FP32 materials use the per-lane SIMT MLP; on variant 3
+ * blocks into them (synchronously, once per material); they are freed with
+ * the material.  This is the one exception to caller-owned bulk memory: the
+ * arrays are a library-owned second copy of every texture's blocks (as many
+ * bytes as the blocks: 179 MB for eight 4096^2 textures), because the
+ * texture unit reads block-compressed data only from CUDA arrays.  The copy
+ * does not follow later changes of the caller's block arrays: after
+ * rewriting them, call bcf_material_refresh.  FP32 materials use the per-lane SIMT MLP; on variant 3
  * their texels come from the texture unit as above (same features), on the
  * other variants from the software decoder.
  * Errors: BCF_ERR_INVALID_ARG for a null material or another variant;
@@ -585,6 +600,17 @@ bcf_status bcf_pack_mode10(const float *d_params, const uint8_t *d_partitions, i
  * texture objects cannot be created.
  */
 bcf_status bcf_set_decode_variant(bcf_material mat, int32_t variant);
+
+/*
+ * bcf_material_refresh -- copy the caller's block arrays into the material's
+ * texture-unit arrays again (decode variants 2 and 3 sample those arrays, a
+ * copy made when the variant was first set).  Asynchronous on `stream`:
+ * issue it after the rewrite of the blocks (on the stream that wrote them,
+ * or after synchronising it) and before the decodes that must see the new
+ * blocks.  A no-op for a material without texture-unit arrays.
+ * Errors: BCF_ERR_INVALID_ARG (null material), BCF_ERR_CUDA.
+ */
+bcf_status bcf_material_refresh(bcf_material mat, bcf_stream stream);
 
 /*
  * bcf_set_mlp_engine -- choose the tensor-core instructions of a material's

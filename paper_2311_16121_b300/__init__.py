@@ -83,6 +83,8 @@ def lib() -> ctypes.CDLL:
         L.bcf_set_decode_variant.argtypes = [c_void_p, c_int32]
         L.bcf_set_mlp_engine.restype = c_int
         L.bcf_set_mlp_engine.argtypes = [c_void_p, c_int32]
+        L.bcf_material_refresh.restype = c_int
+        L.bcf_material_refresh.argtypes = [c_void_p, c_void_p]
         L.bcf_texunit_fetch_probe.restype = c_int
         L.bcf_texunit_fetch_probe.argtypes = [c_void_p, c_int32, c_int32, c_int64, c_int32, c_void_p, c_void_p]
         L.bcf_decode_material.restype = c_int
@@ -290,6 +292,10 @@ class Material:
         """bcf_set_decode_variant: 0 tile-cooperative (default), 1 per-lane, 2 texture unit (hardware trilinear),
         3 texture-unit texels with the exact FP32 filter."""
         _check(lib().bcf_set_decode_variant(self.handle, int(variant)), "bcf_set_decode_variant")
+
+    def refresh(self) -> None:
+        """bcf_material_refresh: the texture-unit copy of the blocks follows a rewrite of the caller's blocks."""
+        _check(lib().bcf_material_refresh(self.handle, _stream()), "bcf_material_refresh")
 
     def set_mlp_engine(self, engine: str) -> None:
         """bcf_set_mlp_engine: "mma_sync" (warp-level MMAs, default) or "tcgen05" (CTA-level MMAs with tensor-memory

@@ -265,6 +265,11 @@ bcf_status bcf_create_material(const bcf_material_desc *d, bcf_material *out)
     for (int t = 0; t < BCF_MAX_TEX; ++t)
         m->hw_arrays[t] = nullptr;
     m->hw_ready = 0;
+    m->pipe_ready = 0;
+    for (cudaStream_t &x : m->pipe_streams)
+        x = nullptr;
+    for (cudaEvent_t &x : m->pipe_events)
+        x = nullptr;
     cudaGetDevice(&m->device);
     cudaError_t e = cudaMalloc(&m->dev, sizeof(MaterialDev));
     if (e != cudaSuccess) {
@@ -298,6 +303,15 @@ bcf_status bcf_set_decode_variant(bcf_material m, int32_t variant)
     }
     m->variant = variant;
     return BCF_OK;
+}
+
+bcf_status bcf_material_refresh(bcf_material m, bcf_stream stream)
+{
+    if (!m)
+        return fail(BCF_ERR_INVALID_ARG, "bcf_material_refresh: null material");
+    if (!m->hw_ready)
+        return BCF_OK;
+    return cuda_status(texunit_refresh(m->host, m->hw_arrays, (cudaStream_t)stream), "bcf_material_refresh");
 }
 
 bcf_status bcf_set_mlp_engine(bcf_material m, int32_t engine)
@@ -342,6 +356,12 @@ bcf_status bcf_destroy_material(bcf_material m)
         return BCF_OK;
     if (m->hw_ready)
         texunit_destroy(m->hw, m->hw_arrays, m->host.n_tex);
+    if (m->pipe_ready) { // released once their pending work completes
+        for (cudaStream_t x : m->pipe_streams)
+            cudaStreamDestroy(x);
+        for (cudaEvent_t x : m->pipe_events)
+            cudaEventDestroy(x);
+    }
     cudaError_t e = cudaFree(m->dev);
     delete m;
     return cuda_status(e, "cudaFree(material metadata)");
@@ -418,18 +438,22 @@ bcf_status bcf_decode_material_host(bcf_material m, const float *h_u, const floa
     auto up = [](int64_t b) { return (b + 255) / 256 * 256; };
     const int64_t buf = up(chunk * 4) * (h_s ? 3 : 2) + up(chunk * out_b);
     char *base[2] = {(char *)d_scratch, (char *)d_scratch + buf};
-    cudaStream_t cs = (cudaStream_t)stream, sin = nullptr, scomp = nullptr, sout = nullptr;
-    cudaEvent_t start = nullptr, done = nullptr, in_done[2] = {}, comp_done[2] = {}, free_ev[2] = {};
-    cudaError_t e = cudaStreamCreateWithFlags(&sin, cudaStreamNonBlocking);
-    if (e == cudaSuccess)
-        e = cudaStreamCreateWithFlags(&scomp, cudaStreamNonBlocking);
-    if (e == cudaSuccess)
-        e = cudaStreamCreateWithFlags(&sout, cudaStreamNonBlocking);
-    cudaEvent_t *evs[] = {&start, &done, &in_done[0], &in_done[1], &comp_done[0], &comp_done[1], &free_ev[0],
-                          &free_ev[1]};
-    for (cudaEvent_t *ev : evs)
-        if (e == cudaSuccess)
-            e = cudaEventCreateWithFlags(ev, cudaEventDisableTiming);
+    cudaError_t e = cudaSuccess;
+    if (!m->pipe_ready) { // the material's pipeline streams and events, created once
+        for (int i = 0; i < 3 && e == cudaSuccess; ++i)
+            e = cudaStreamCreateWithFlags(&m->pipe_streams[i], cudaStreamNonBlocking);
+        for (int i = 0; i < 8 && e == cudaSuccess; ++i)
+            e = cudaEventCreateWithFlags(&m->pipe_events[i], cudaEventDisableTiming);
+        if (e != cudaSuccess)
+            return cuda_status(e, "bcf_decode_material_host: pipeline streams and events");
+        m->pipe_ready = 1;
+    }
+    cudaStream_t cs = (cudaStream_t)stream, sin = m->pipe_streams[0], scomp = m->pipe_streams[1],
+                 sout = m->pipe_streams[2];
+    cudaEvent_t start = m->pipe_events[0], done = m->pipe_events[1];
+    cudaEvent_t in_done[2] = {m->pipe_events[2], m->pipe_events[3]};
+    cudaEvent_t comp_done[2] = {m->pipe_events[4], m->pipe_events[5]};
+    cudaEvent_t free_ev[2] = {m->pipe_events[6], m->pipe_events[7]};
     if (e == cudaSuccess)
         e = cudaEventRecord(start, cs); // the pipeline starts after the caller's earlier work
     if (e == cudaSuccess)
@@ -469,13 +493,6 @@ bcf_status bcf_decode_material_host(bcf_material m, const float *h_u, const floa
         e = cudaEventRecord(done, sout);
     if (e == cudaSuccess && st == BCF_OK)
         e = cudaStreamWaitEvent(cs, done, 0); // the caller's stream continues after the last download
-    // streams and events are released once their pending work completes
-    for (cudaStream_t x : {sin, scomp, sout})
-        if (x)
-            cudaStreamDestroy(x);
-    for (cudaEvent_t *ev : evs)
-        if (*ev)
-            cudaEventDestroy(*ev);
     if (st != BCF_OK)
         return st;
     return cuda_status(e, "bcf_decode_material_host");
@@ -575,6 +592,8 @@ bcf_status bcf_create_material_set(const bcf_material *mats, int32_t n, bcf_mate
     set->texunit = set_tex_supported(mats[0]->host);
     for (int m = 0; m < n; ++m)
         set->texunit = set->texunit && mats[m]->hw_ready && mats[m]->variant == 3;
+    if (set->texunit)
+        set->cfg = {320, 6, 8}; // the autotuner's pick on the 64-material benchmark workload
     MaterialDev *host = new (std::nothrow) MaterialDev[n];
     if (!host) {
         delete set;
@@ -646,7 +665,7 @@ bcf_status bcf_decode_material_set(bcf_material_set set, const int64_t *d_offset
     if (set->texunit)
         return cuda_status(launch_decode_set_tex(set->first, set->table, set->tex_table, set->n, d_offsets, d_u, d_v,
                                                  d_s, n_queries, d_out, out_precision == BCF_FP16, set->counter,
-                                                 set->check, (cudaStream_t)stream),
+                                                 set->check, set->cfg, (cudaStream_t)stream),
                            "bcf_decode_material_set launch");
     return cuda_status(launch_decode_set(set->first, set->table, set->n, d_offsets, d_u, d_v, d_s, n_queries, d_out,
                                          out_precision == BCF_FP16, set->counter, set->check, set->cfg,
@@ -675,8 +694,6 @@ bcf_status bcf_autotune_material_set(bcf_material_set set, const int64_t *d_offs
     bcf_status st = check_set_args(set, d_offsets, d_u, d_v, d_s, n_queries, d_out, out_precision);
     if (st != BCF_OK)
         return st;
-    if (set->texunit) // the texture-unit set kernel has no tunable configuration
-        return bcf_material_set_config(set, cap, ctas_per_sm, chunk);
     cudaStream_t cs = (cudaStream_t)stream;
     if (n_queries > 0) {
         cudaEvent_t a = nullptr, b = nullptr;
@@ -685,17 +702,25 @@ bcf_status bcf_autotune_material_set(bcf_material_set set, const int64_t *d_offs
             e = cudaEventCreate(&b);
         float best = 1e30f;
         SetConfig best_cfg = set->cfg;
-        const int caps[2] = {256, 320}, ctas[3] = {1, 2, 3}, chunks[4] = {1, 2, 4, 8};
-        for (int ic = 0; e == cudaSuccess && ic < 2; ++ic)
+        // the software set kernel: arena size x CTAs per SM x tiles per grab; the texture-unit set kernel
+        // (128-query tiles): CTAs per SM x tiles per grab
+        const int caps[2] = {256, 320}, ctas_sw[3] = {1, 2, 3}, ctas_tex[3] = {4, 6, 8}, chunks[4] = {1, 2, 4, 8};
+        const int ncap = set->texunit ? 1 : 2;
+        for (int ic = 0; e == cudaSuccess && ic < ncap; ++ic)
             for (int ir = 0; e == cudaSuccess && ir < 3; ++ir)
                 for (int ik = 0; e == cudaSuccess && ik < 4; ++ik) {
-                    const SetConfig cfg = {caps[ic], ctas[ir], chunks[ik]};
+                    const SetConfig cfg = {caps[ic], set->texunit ? ctas_tex[ir] : ctas_sw[ir], chunks[ik]};
                     float ms = 0.0f;
                     for (int rep = 0; e == cudaSuccess && rep < 3; ++rep) { // first run warms up
                         e = cudaEventRecord(a, cs);
                         if (e == cudaSuccess)
-                            e = launch_decode_set(set->first, set->table, set->n, d_offsets, d_u, d_v, d_s, n_queries,
-                                                  d_out, out_precision == BCF_FP16, set->counter, set->check, cfg, cs);
+                            e = set->texunit
+                                    ? launch_decode_set_tex(set->first, set->table, set->tex_table, set->n, d_offsets,
+                                                            d_u, d_v, d_s, n_queries, d_out, out_precision == BCF_FP16,
+                                                            set->counter, set->check, cfg, cs)
+                                    : launch_decode_set(set->first, set->table, set->n, d_offsets, d_u, d_v, d_s,
+                                                        n_queries, d_out, out_precision == BCF_FP16, set->counter,
+                                                        set->check, cfg, cs);
                         if (e == cudaSuccess)
                             e = cudaEventRecord(b, cs);
                         if (e == cudaSuccess)

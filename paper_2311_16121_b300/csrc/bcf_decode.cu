@@ -375,7 +375,7 @@ __global__ void __launch_bounds__(32 * kSetTexWarps) k_decode_set_tex(
     const MaterialDev *__restrict__ mats, const TexUnitObjs *__restrict__ texs, int nmat,
     const int64_t *__restrict__ offsets, const float *__restrict__ qu, const float *__restrict__ qv,
     const float *__restrict__ qs, int64_t n, void *__restrict__ out, int out_fp16, int *__restrict__ counter,
-    unsigned *__restrict__ check, int act_bytes)
+    unsigned *__restrict__ check, int act_bytes, int chunk)
 {
     constexpr int kTile = 32 * kSetTexWarps;
     extern __shared__ __align__(16) unsigned char smem[];
@@ -412,12 +412,13 @@ __global__ void __launch_bounds__(32 * kSetTexWarps) k_decode_set_tex(
     int cur = -1;
     for (;;) {
         if (threadIdx.x == 0)
-            grab = atomicAdd(counter, 1);
+            grab = atomicAdd(counter, chunk);
         __syncthreads();
-        const int64_t tile = grab;
+        const int64_t base = grab;
         __syncthreads(); // everyone has read `grab` before thread 0 may overwrite it
-        if (tile >= total)
+        if (base >= total)
             break;
+      for (int64_t tile = base; tile < base + chunk && tile < total; ++tile) {
         int lo = 0, hi = nmat - 1; // last m with tile_first[m] <= tile
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
@@ -427,7 +428,8 @@ __global__ void __launch_bounds__(32 * kSetTexWarps) k_decode_set_tex(
                 hi = mid - 1;
         }
         const int m = lo;
-        if (m != cur) { // (the barriers above ordered the previous tile's MLP reads before these writes)
+        if (m != cur) {
+            __syncthreads(); // the previous tile's MLP may still read the weights being replaced
             const int words = (int)(sizeof(MaterialDev) / 4);
             for (int i = threadIdx.x; i < words; i += kTile)
                 reinterpret_cast<int *>(&Ms)[i] = reinterpret_cast<const int *>(mats + m)[i];
@@ -443,8 +445,8 @@ __global__ void __launch_bounds__(32 * kSetTexWarps) k_decode_set_tex(
         if (q0w < b) { // warp-uniform
             const int64_t q = q0w + lane;
             const bool live = q < b;
-            unsigned char *row = act0 + lane * row_stride;
             const float inv0 = PREC == BCF_FP8_E4M3 ? Ms.mlp.inv_act_scale[0] : 1.0f;
+            RowWriter<PREC> rw{act0 + lane * row_stride, inv0, 0.0f};
             const float sq = live && qs ? qs[q] : 0.0f;
             const float uu = sanitize(live ? qu[q] : 0.0f, Ms.wrap), vv = sanitize(live ? qv[q] : 0.0f, Ms.wrap);
 #pragma unroll 1
@@ -452,15 +454,16 @@ __global__ void __launch_bounds__(32 * kSetTexWarps) k_decode_set_tex(
                 float3 f = make_float3(0.0f, 0.0f, 0.0f);
                 if (live)
                     f = sample_texture_hwpoint(Ms.tex[t], Tp[t], Ms.wrap, uu, vv, sq);
-                store_feature<PREC>(row, 3 * t, f.x, inv0);
-                store_feature<PREC>(row, 3 * t + 1, f.y, inv0);
-                store_feature<PREC>(row, 3 * t + 2, f.z, inv0);
+                rw.put(3 * t, f.x);
+                rw.put(3 * t + 1, f.y);
+                rw.put(3 * t + 2, f.z);
             }
             int col = 3 * Ms.n_tex;
             if (Ms.lod_input)
-                store_feature<PREC>(row, col++, live ? (isnan(sq) ? 0.0f : fmaxf(sq, 0.0f)) : 0.0f, inv0);
+                rw.put(col++, live ? (isnan(sq) ? 0.0f : fmaxf(sq, 0.0f)) : 0.0f);
             for (; col < K0; ++col)
-                store_feature<PREC>(row, col, 0.0f, inv0);
+                rw.put(col, 0.0f);
+            rw.finish(col);
             __syncwarp();
             if constexpr (N2 == 0)
                 warp_mlp2<PREC, K0, N1, NO>(sw, sb, act0, row_stride, ost, C);
@@ -468,19 +471,10 @@ __global__ void __launch_bounds__(32 * kSetTexWarps) k_decode_set_tex(
                 warp_mlp3<PREC, K0, N1, N2, NO>(Ms.mlp, sw, sb, act0, row_stride, act1,
                                             tile_stride_bytes<BCF_FP8_E4M3>(N1 > N2 ? N1 : N2), ost, C);
             __syncwarp();
-            const int rows = (int)min((int64_t)32, b - q0w);
-            const int tot = rows * C;
-            if (out_fp16) {
-                __half *o = (__half *)out + q0w * C;
-                for (int i = lane; i < tot; i += 32)
-                    o[i] = __float2half_rn(ost[i]);
-            } else {
-                float *o = (float *)out + q0w * C;
-                for (int i = lane; i < tot; i += 32)
-                    o[i] = ost[i];
-            }
+            store_rows_any(ost, out, q0w, (int)min((int64_t)32, b - q0w), C, out_fp16, lane);
             __syncwarp();
         }
+      }
     }
 }
 
@@ -711,7 +705,7 @@ template <int PREC, int K0, int N1, int N2, int NO>
 static cudaError_t launch_set_tex_shape(const MaterialDev &M0, const MaterialDev *mats, const TexUnitObjs *texs,
                                         int nmat, const int64_t *offsets, const float *u, const float *v,
                                         const float *s, int64_t n, void *out, int out_fp16, int *counter,
-                                        unsigned *check, cudaStream_t st)
+                                        unsigned *check, const SetConfig &cfg, cudaStream_t st)
 {
     const MlpDev &P = M0.mlp;
     const int act = mma_act_bytes<PREC>(P);
@@ -729,11 +723,13 @@ static cudaError_t launch_set_tex_shape(const MaterialDev &M0, const MaterialDev
     }
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * kSetTexWarps, (size_t)smem);
+    if (cfg.ctas_per_sm > 0)
+        per_sm = min(per_sm, cfg.ctas_per_sm);
     cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
     if (e != cudaSuccess)
         return e;
     kern<<<(unsigned)(sm_count() * max(per_sm, 1)), 32 * kSetTexWarps, (size_t)smem, st>>>(
-        mats, texs, nmat, offsets, u, v, s, n, out, out_fp16, counter, check, act);
+        mats, texs, nmat, offsets, u, v, s, n, out, out_fp16, counter, check, act, max(cfg.chunk, 1));
     return cudaGetLastError();
 }
 
@@ -760,7 +756,8 @@ static bool set_tex_two_layer(const MlpDev &P)
 
 cudaError_t launch_decode_set_tex(const MaterialDev &M0, const MaterialDev *mats, const TexUnitObjs *texs, int nmat,
                                   const int64_t *offsets, const float *u, const float *v, const float *s, int64_t n,
-                                  void *out, int out_fp16, int *counter, unsigned *check, cudaStream_t st)
+                                  void *out, int out_fp16, int *counter, unsigned *check, const SetConfig &cfg,
+                                  cudaStream_t st)
 {
     if (n == 0)
         return cudaSuccess;
@@ -769,15 +766,15 @@ cudaError_t launch_decode_set_tex(const MaterialDev &M0, const MaterialDev *mats
     if (set_tex_two_layer(P)) {
         if (P.precision == BCF_BF16)
             return launch_set_tex_shape<BCF_BF16, 16, 16, 0, 16>(M0, mats, texs, nmat, offsets, u, v, s, n, out,
-                                                                  out_fp16, counter, check, st);
+                                                                  out_fp16, counter, check, cfg, st);
         return launch_set_tex_shape<BCF_FP16, 16, 16, 0, 16>(M0, mats, texs, nmat, offsets, u, v, s, n, out,
-                                                              out_fp16, counter, check, st);
+                                                              out_fp16, counter, check, cfg, st);
     }
 #define BCF_SET_TEX(PR, KQ)                                                                                          \
     return wide ? launch_set_tex_shape<PR, 32, 64, 64, 16>(M0, mats, texs, nmat, offsets, u, v, s, n, out, out_fp16, \
-                                                           counter, check, st)                                              \
+                                                           counter, check, cfg, st)                                         \
                 : launch_set_tex_shape<PR, KQ, 32, 32, 16>(M0, mats, texs, nmat, offsets, u, v, s, n, out, out_fp16, \
-                                                           counter, check, st)
+                                                           counter, check, cfg, st)
     switch (P.precision) {
     case BCF_FP16: BCF_SET_TEX(BCF_FP16, 16);
     case BCF_BF16: BCF_SET_TEX(BCF_BF16, 16);

@@ -907,31 +907,6 @@ __device__ __forceinline__ void decode_arena_blocks(const uint4 *sraw, const uin
     }
 }
 
-// Writes a query's MLP input row column by column, in increasing column order: 16-bit operands go out in
-// pairs (one 4-byte store per two columns), E4M3 bytes one by one.
-template <int PREC>
-struct RowWriter {
-    unsigned char *row;
-    float inv; // FP8: the first layer's inverse activation scale
-    float pend; // the value of an even column waiting for its odd neighbour
-    __device__ __forceinline__ void put(int col, float x)
-    {
-        if constexpr (PREC == BCF_FP8_E4M3) {
-            store_feature<PREC>(row, col, x, inv);
-        } else if (col & 1) {
-            *reinterpret_cast<uint32_t *>(row + 2 * (col - 1)) = Op<PREC>::pack2(pend, x);
-        } else {
-            pend = x;
-        }
-    }
-    // after the last column: an unpaired even column is written alone
-    __device__ __forceinline__ void finish(int ncols)
-    {
-        if constexpr (PREC != BCF_FP8_E4M3)
-            if (ncols & 1)
-                store_feature<PREC>(row, ncols - 1, pend, inv);
-    }
-};
 
 template <int PREC, int CAP, int K0, int N1, int N2, int NO, bool TC>
 __global__ void __launch_bounds__(kTileQ, kGeoMinBlocks) k_decode_geo(MaterialDev M, const float *__restrict__ qu,

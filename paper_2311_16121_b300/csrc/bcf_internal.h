@@ -80,4 +80,9 @@ struct bcf_material_s {
     bcf::TexUnitObjs hw;     // variant 2: BC6H texture objects with hardware trilinear filtering
     void *hw_arrays[BCF_MAX_TEX];
     int hw_ready;
+    // bcf_decode_material_host's pipeline: upload, decode and download streams and their events, created by
+    // the first such call and released with the material
+    cudaStream_t pipe_streams[3];
+    cudaEvent_t pipe_events[8];
+    int pipe_ready;
 };

@@ -299,6 +299,53 @@ __device__ __forceinline__ void store_warp_rows(const float *ost, void *out, int
     }
 }
 
+// store_warp_rows for rows starting anywhere (material-set ranges): the 16-byte path when the first output
+// element is 16-byte aligned, element by element otherwise.
+__device__ __forceinline__ void store_rows_any(const float *ost, void *out, int64_t q0, int rows, int C, int out_fp16,
+                                               int lane)
+{
+    if (((q0 * C * (out_fp16 ? 2 : 4)) & 15) == 0) {
+        store_warp_rows(ost, out, q0, rows, C, out_fp16, lane);
+        return;
+    }
+    const int tot = rows * C;
+    if (out_fp16) {
+        __half *o = (__half *)out + q0 * C;
+        for (int i = lane; i < tot; i += 32)
+            o[i] = __float2half_rn(ost[i]);
+    } else {
+        float *o = (float *)out + q0 * C;
+        for (int i = lane; i < tot; i += 32)
+            o[i] = ost[i];
+    }
+}
+
+// Writes a query's MLP input row column by column, in increasing column order: 16-bit operands go out in
+// pairs (one 4-byte store per two columns), E4M3 bytes one by one.
+template <int PREC>
+struct RowWriter {
+    unsigned char *row;
+    float inv; // FP8: the first layer's inverse activation scale
+    float pend; // the value of an even column waiting for its odd neighbour
+    __device__ __forceinline__ void put(int col, float x)
+    {
+        if constexpr (PREC == BCF_FP8_E4M3) {
+            store_feature<PREC>(row, col, x, inv);
+        } else if (col & 1) {
+            *reinterpret_cast<uint32_t *>(row + 2 * (col - 1)) = Op<PREC>::pack2(pend, x);
+        } else {
+            pend = x;
+        }
+    }
+    // after the last column: an unpaired even column is written alone
+    __device__ __forceinline__ void finish(int ncols)
+    {
+        if constexpr (PREC != BCF_FP8_E4M3)
+            if (ncols & 1)
+                store_feature<PREC>(row, ncols - 1, pend, inv);
+    }
+};
+
 // ----------------------------------------------------------- FP32 SIMT MLP
 
 // Fully unrolled dense layer y = W x + b (W row-major [NO][NI] in shared

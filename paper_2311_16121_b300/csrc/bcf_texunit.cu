@@ -160,6 +160,28 @@ cudaError_t texunit_create(const MaterialDev &M, TexUnitObjs &T, void **arrays)
     return e;
 }
 
+// Copy the caller's block arrays into the material's mipmapped arrays again, level by level, ordered on `st`
+// (after the caller's rewrite of the blocks when issued on the same stream, before later decodes on it).
+cudaError_t texunit_refresh(const MaterialDev &M, void *const *arrays, cudaStream_t st)
+{
+    cudaError_t e = cudaSuccess;
+    for (int t = 0; t < M.n_tex && e == cudaSuccess; ++t) {
+        const TexDev &X = M.tex[t];
+        const int wb0 = X.res / 4;
+        for (int l = 0; l < X.levels && e == cudaSuccess; ++l) {
+            cudaArray_t lvl = nullptr;
+            e = cudaGetMipmappedArrayLevel(&lvl, (cudaMipmappedArray_t)arrays[t], (unsigned)l);
+            const size_t wb = (size_t)max(wb0 >> l, 1);
+            if (e == cudaSuccess)
+                e = cudaMemcpy2DToArrayAsync(lvl, 0, 0, X.blocks + X.level_off[l], wb * 16, wb * 16, wb,
+                                             cudaMemcpyDeviceToDevice, st);
+            if (e != cudaSuccess)
+                set_error("refresh of level %d of texture %d: %s", l, t, cudaGetErrorString(e));
+        }
+    }
+    return e;
+}
+
 // Point-fetch rate probe (measurement only): every lane fetches the 2 x 2 footprint around its own texel of one
 // level, as a query's bilinear taps do, with the 32 lanes of a warp on an 8 x 4 patch of neighbouring texels
 // (a warp of screen-coherent queries) and the warps' patches in row-major order over the level; each of the

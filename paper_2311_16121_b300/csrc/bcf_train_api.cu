@@ -128,7 +128,8 @@ bcf_status bcf_trainer_create(const bcf_trainer_desc *d, bcf_trainer *out)
         return tfail(BCF_ERR_INVALID_ARG, "invalid hyper-parameters");
     D.s_max = d->s_max;
     if (D.unconstrained && !train_mma_supported(D))
-        return tfail(BCF_ERR_UNSUPPORTED, "unconstrained features need a dims[0] <= 16 -> 32 -> 32 -> 9 MLP");
+        return tfail(BCF_ERR_UNSUPPORTED, "unconstrained features need a dims[0] <= 16 -> 32 -> 32 -> C or "
+                                          "dims[0] <= 16 -> 16 -> C MLP (C <= 9)");
     if (train_smem_bytes(D) > 227 * 1024)
         return tfail(BCF_ERR_UNSUPPORTED, "MLP too wide for the training kernel's shared memory");
     unsigned *check = check_word(); // after every argument check: the first call allocates on the device

@@ -248,7 +248,7 @@ __device__ __forceinline__ void weight_grad(const uint32_t (&ghi)[2][MT][4], con
             }
 }
 
-template <bool FREE, int EMU, bool GRID>
+template <bool FREE, int EMU, bool GRID, bool TWO>
 __global__ void __launch_bounds__(kThreads, 2) k_train_mma(TrainDev D, int mode, int64_t batch, uint32_t seed_lo,
                                                         uint32_t seed_hi, uint32_t step_lo, uint32_t step_hi,
                                                         const float *__restrict__ qu, const float *__restrict__ qv,
@@ -256,33 +256,40 @@ __global__ void __launch_bounds__(kThreads, 2) k_train_mma(TrainDev D, int mode,
                                                         const float *__restrict__ grad_out, float *loss, float gscale)
 {
     __shared__ __align__(16) MmaSmem S;
-    const int K0 = D.dims[0], C = D.dims[3];
+    // TWO: the paper's two-layer decoder K0 <= 16 -> 16 -> C (Sec. 5.1): its hidden layer takes the first 16
+    // rows of the W1 tiles, its output layer the W3 tiles (K = 16 of their 32 columns), its biases b1 and b3
+    constexpr int H1 = TWO ? 16 : N1; // first hidden width
+    const int K0 = D.dims[0], C = D.dims[TWO ? 2 : 3];
+    const int wout = TWO ? 1 : 2;     // layer index of the output layer
     // weights as BF16 operand tiles (zero padded), biases, zeroed gradient accumulators
     for (int e = threadIdx.x; e < N1 * K0P; e += kThreads) {
         const int o = e / K0P, i = e % K0P;
-        const bf16 w = __float2bfloat16_rn(i < K0 ? D.W[D.w_off[0] + o * K0 + i] : 0.0f);
+        const bf16 w = __float2bfloat16_rn(i < K0 && o < H1 ? D.W[D.w_off[0] + o * K0 + i] : 0.0f);
         S.W1[o * S16 + i] = w;
         S.W1T[i * S32 + o] = w;
     }
-    for (int e = threadIdx.x; e < N2 * N1; e += kThreads) {
-        const int o = e / N1, i = e % N1;
-        const bf16 w = __float2bfloat16_rn(D.W[D.w_off[1] + o * N1 + i]);
-        S.W2[o * S32 + i] = w;
-        S.W2T[i * S32 + o] = w;
-    }
+    if constexpr (!TWO)
+        for (int e = threadIdx.x; e < N2 * N1; e += kThreads) {
+            const int o = e / N1, i = e % N1;
+            const bf16 w = __float2bfloat16_rn(D.W[D.w_off[1] + o * N1 + i]);
+            S.W2[o * S32 + i] = w;
+            S.W2T[i * S32 + o] = w;
+        }
+    constexpr int KO = TWO ? H1 : N2; // inputs of the output layer
     for (int e = threadIdx.x; e < NOP * N2; e += kThreads) {
         const int o = e / N2, i = e % N2;
-        const bf16 w = __float2bfloat16_rn(o < C ? D.W[D.w_off[2] + o * N2 + i] : 0.0f);
+        const bf16 w = __float2bfloat16_rn(o < C && i < KO ? D.W[D.w_off[wout] + o * KO + i] : 0.0f);
         S.W3[o * S32 + i] = w;
-        S.W3T[i * S16 + o] = w;
+        if (i < 16 || !TWO)
+            S.W3T[i * S16 + o] = w;
     }
     for (int e = threadIdx.x; e < kMaxB; e += kThreads) {
         if (e < N1)
-            S.b1[e] = D.b[D.b_off[0] + e];
+            S.b1[e] = e < H1 ? D.b[D.b_off[0] + e] : 0.0f;
         else if (e < N1 + N2)
-            S.b2[e - N1] = D.b[D.b_off[1] + e - N1];
+            S.b2[e - N1] = TWO ? 0.0f : D.b[D.b_off[1] + e - N1];
         else
-            S.b3[e - N1 - N2] = e - N1 - N2 < C ? D.b[D.b_off[2] + e - N1 - N2] : 0.0f;
+            S.b3[e - N1 - N2] = e - N1 - N2 < C ? D.b[D.b_off[wout] + e - N1 - N2] : 0.0f;
         S.db[e] = 0.0f;
     }
     for (int e = threadIdx.x; e < kMaxW; e += kThreads)
@@ -355,8 +362,45 @@ __global__ void __launch_bounds__(kThreads, 2) k_train_mma(TrainDev D, int mode,
         frag_a<S16>(X, 16, g, t, xa[1][0]);
 
         __syncthreads(); // the CTA's warps enter the MLP together (instruction-cache locality)
-        // ---- forward: h1 = relu(x W1^T + b1), h2 = relu(h1 W2^T + b2) (both rounded to BF16), y = h2 W3^T + b3
+        // ---- forward: h1 = relu(x W1^T + b1), h2 = relu(h1 W2^T + b2) (both rounded to BF16), y = h2 W3^T + b3;
+        // two layers: h1 (16 wide) = relu(x W1^T + b1), y = h1 W3^T + b3
         uint32_t a1[2][2][4], a2[2][2][4];
+        if constexpr (TWO) {
+            {
+                float c[2][2][4] = {};
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt) {
+                    uint32_t b[2];
+                    frag_b<S16>(S.W1, nt * 8, 0, g, t, b);
+                    mma_bf16(c[0][nt], xa[0][0], b);
+                    mma_bf16(c[1][nt], xa[1][0], b);
+                }
+                uint32_t h[2][1][4];
+                hidden_a<2>(c, S.b1, t, h);
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+                        a1[mt][0][r] = h[mt][0][r];
+            }
+            float c[2][2][4] = {};
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                uint32_t b[2];
+                frag_b<S32>(S.W3, nt * 8, 0, g, t, b);
+                mma_bf16(c[0][nt], a1[0][0], b);
+                mma_bf16(c[1][nt], a1[1][0], b);
+            }
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                    for (int cc = 0; cc < 4; ++cc) {
+                        const int row = mt * 16 + g + (cc >> 1) * 8, col = nt * 8 + 2 * t + (cc & 1);
+                        R[row * kRowF + col] = c[mt][nt][cc] + S.b3[col];
+                    }
+        } else {
         {
             float c[2][4][4] = {};
 #pragma unroll
@@ -401,6 +445,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_train_mma(TrainDev D, int mode,
                         const int row = mt * 16 + g + (cc >> 1) * 8, col = nt * 8 + 2 * t + (cc & 1);
                         R[row * kRowF + col] = c[mt][nt][cc] + S.b3[col];
                     }
+        }
         }
         __syncwarp();
         float *rr = R + lane * kRowF;
@@ -457,6 +502,53 @@ __global__ void __launch_bounds__(kThreads, 2) k_train_mma(TrainDev D, int mode,
             split_bf16(p[8], p[9], g3h[mt][0][2], g3l[mt][0][2]);
             split_bf16(p[8 * kRowF + 8], p[8 * kRowF + 9], g3h[mt][0][3], g3l[mt][0][3]);
         }
+        if constexpr (TWO) {
+            // ---- output layer: dW3 = g3^T h1; dh1 = g3 W3, masked by relu'
+            uint32_t h1[2][1][4];
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int r = 0; r < 4; ++r)
+                    h1[mt][0][r] = a1[mt][0][r];
+            weight_grad<1, 2>(g3h, g3l, h1, S.dW + D.w_off[1], H1, C, H1, g, t);
+            uint32_t g1h[2][1][4], g1l[2][1][4];
+            {
+                float d[2][2][4] = {};
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt) {
+                    uint32_t b[2];
+                    frag_b<S16>(S.W3T, nt * 8, 0, g, t, b);
+#pragma unroll
+                    for (int mt = 0; mt < 2; ++mt) {
+                        mma_bf16(d[mt][nt], g3h[mt][0], b);
+                        mma_bf16(d[mt][nt], g3l[mt][0], b);
+                    }
+                }
+                grad_a<2>(d, h1, g1h, g1l);
+                add_bias_grad<2>(d, S.db, lane, t);
+            }
+            // ---- hidden layer: dW1 = g1^T x; dx = g1 W1, staged per row for the scatter
+            weight_grad<1, 2>(g1h, g1l, xa, S.dW + D.w_off[0], K0, H1, K0, g, t);
+            float d[2][2][4] = {};
+#pragma unroll
+            for (int nt = 0; nt < 2; ++nt) {
+                uint32_t b[2];
+                frag_b<S32>(S.W1T, nt * 8, 0, g, t, b);
+#pragma unroll
+                for (int mt = 0; mt < 2; ++mt) {
+                    mma_bf16(d[mt][nt], g1h[mt][0], b);
+                    mma_bf16(d[mt][nt], g1l[mt][0], b);
+                }
+            }
+            __syncwarp();
+#pragma unroll
+            for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+                for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+                    for (int cc = 0; cc < 4; ++cc)
+                        R[(mt * 16 + g + (cc >> 1) * 8) * kRowF + nt * 8 + 2 * t + (cc & 1)] = d[mt][nt][cc];
+        } else {
         // ---- layer 3: dW3 = g3^T h2; dh2 = g3 W3, masked by relu'
         weight_grad<1, 4>(g3h, g3l, a2, S.dW + D.w_off[2], N2, C, N2, g, t);
         uint32_t g2h[2][2][4], g2l[2][2][4];
@@ -519,6 +611,7 @@ __global__ void __launch_bounds__(kThreads, 2) k_train_mma(TrainDev D, int mode,
 #pragma unroll
                     for (int cc = 0; cc < 4; ++cc)
                         R[(mt * 16 + g + (cc >> 1) * 8) * kRowF + nt * 8 + 2 * t + (cc & 1)] = d[mt][nt][cc];
+        }
         }
         __syncwarp();
         __syncthreads(); // and the scatter (the forward-only mode leaves the loop above, uniformly)
@@ -644,9 +737,13 @@ __global__ void __launch_bounds__(kThreads, 2) k_train_mma(TrainDev D, int mode,
         for (int i = threadIdx.x; i < w_total; i += kThreads)
             if (S.dW[i] != 0.0f)
                 atomicAdd(D.Wg + i, S.dW[i]);
-        for (int i = threadIdx.x; i < N1 + N2 + C; i += kThreads)
-            if (S.db[i] != 0.0f)
-                atomicAdd(D.bg + i, S.db[i]);
+        // S.db holds b1 at [0, N1), b2 at [N1, N1 + N2), the output bias at [N1 + N2, N1 + N2 + C); two layers:
+        // b1 (H1) and the output bias, which the caller stores as b_off 0 and b_off 1
+        for (int i = threadIdx.x; i < N1 + N2 + C; i += kThreads) {
+            const int dst = !TWO ? i : (i < H1 ? i : (i >= N1 + N2 ? H1 + (i - N1 - N2) : -1));
+            if (dst >= 0 && S.db[i] != 0.0f)
+                atomicAdd(D.bg + dst, S.db[i]);
+        }
         for (int tx = 0; tx < (FREE ? 0 : min(D.n_tex, kCoarseTex)); ++tx) {
             const TrainTexDev &T = D.tex[tx];
             const int64_t cst = coarse_start(T);
@@ -665,22 +762,32 @@ __global__ void __launch_bounds__(kThreads, 2) k_train_mma(TrainDev D, int mode,
 
 } // namespace
 
+static bool train_mma_two_layer(const TrainDev &D)
+{
+    return D.n_layers == 2 && D.dims[0] <= K0P && D.dims[1] == 16 && D.dims[2] <= 9 && D.b_off[1] == 16;
+}
+
 bool train_mma_supported(const TrainDev &D)
 {
-    return D.n_layers == 3 && D.dims[0] <= K0P && D.dims[1] == N1 && D.dims[2] == N2 && D.dims[3] <= NOP &&
-           D.dims[3] <= 9 && D.b_off[1] == N1 && D.b_off[2] == N1 + N2;
+    return train_mma_two_layer(D) || (D.n_layers == 3 && D.dims[0] <= K0P && D.dims[1] == N1 && D.dims[2] == N2 &&
+                                      D.dims[3] <= NOP && D.dims[3] <= 9 && D.b_off[1] == N1 &&
+                                      D.b_off[2] == N1 + N2);
 }
 
 cudaError_t launch_train_mma(const TrainDev &D, int mode, int64_t batch, uint64_t seed, int64_t step,
                              const float *u, const float *v, const float *s, float *out, const float *grad_out,
                              float *loss, int sms, cudaStream_t st)
 {
-    static void (*const kernels[9])(TrainDev, int, int64_t, uint32_t, uint32_t, uint32_t, uint32_t, const float *,
-                                    const float *, const float *, float *, const float *, float *, float) = {
-        k_train_mma<false, 0, false>, k_train_mma<false, 1, false>, k_train_mma<false, 2, false>,
-        k_train_mma<false, 3, false>, k_train_mma<true, 0, false>,  k_train_mma<false, 0, true>,
-        k_train_mma<false, 1, true>,  k_train_mma<false, 2, true>,  k_train_mma<false, 3, true>};
-    const auto kern = kernels[D.unconstrained ? 4 : (D.batch_grid > 0 ? 5 : 0) + emulation_variant(D)];
+    static void (*const kernels[18])(TrainDev, int, int64_t, uint32_t, uint32_t, uint32_t, uint32_t, const float *,
+                                     const float *, const float *, float *, const float *, float *, float) = {
+        k_train_mma<false, 0, false, false>, k_train_mma<false, 1, false, false>, k_train_mma<false, 2, false, false>,
+        k_train_mma<false, 3, false, false>, k_train_mma<true, 0, false, false>,  k_train_mma<false, 0, true, false>,
+        k_train_mma<false, 1, true, false>,  k_train_mma<false, 2, true, false>,  k_train_mma<false, 3, true, false>,
+        k_train_mma<false, 0, false, true>,  k_train_mma<false, 1, false, true>,  k_train_mma<false, 2, false, true>,
+        k_train_mma<false, 3, false, true>,  k_train_mma<true, 0, false, true>,   k_train_mma<false, 0, true, true>,
+        k_train_mma<false, 1, true, true>,   k_train_mma<false, 2, true, true>,   k_train_mma<false, 3, true, true>};
+    const auto kern = kernels[(train_mma_two_layer(D) ? 9 : 0) +
+                              (D.unconstrained ? 4 : (D.batch_grid > 0 ? 5 : 0) + emulation_variant(D))];
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, 0);
     const int64_t tiles = (batch + kThreads - 1) / kThreads;

@@ -519,3 +519,25 @@ def test_tcgen05_mlp_engine_rejects_other_shapes():
     m32 = workloads.upload(workloads.small_screen(res=32, width=8, height=8), "fp32")
     with pytest.raises(bcf.BcfError):
         m32.set_mlp_engine("tcgen05")
+
+
+def test_texture_unit_copy_follows_rewritten_blocks_after_refresh():
+    """Decode variants 2 and 3 sample a library-owned copy of the blocks: after the caller rewrites a texture's
+    blocks, bcf_material_refresh brings the copy up to date, and variant 3 again equals the software decode of
+    the caller's (new) blocks bit for bit; before the refresh it still samples the old blocks."""
+    _bcf()
+    w = workloads.small_screen(res=64, width=64, height=36)
+    m = workloads.upload(w, "fp16")
+    u, v, s = workloads.queries_to_device(w)
+    m.set_decode_variant(3)
+    before = m.decode(u, v, s)
+    dev_blocks = m._keep[0][0]
+    fresh_blocks = synth.bounded_blocks(workloads.seed_rng(2, 123), w.blocks[0].reshape(-1, 16).shape[0])
+    dev_blocks.view(-1).copy_(torch.from_numpy(np.ascontiguousarray(fresh_blocks, np.uint8).reshape(-1)).cuda())
+    stale = m.decode(u, v, s)
+    assert torch.equal(stale, before)
+    m.refresh()
+    after = m.decode(u, v, s)
+    m.set_decode_variant(0)
+    software = m.decode(u, v, s)
+    assert torch.equal(after, software) and not torch.equal(after, before)

@@ -473,3 +473,42 @@ def test_checkpoint_resume_reproduces_the_run():
     np.testing.assert_allclose(c.W.cpu().numpy(), a.W.cpu().numpy(), rtol=0, atol=3e-3)
     for pa, pc in zip(a.params, c.params):
         assert np.abs(pa.cpu().numpy() - pc.cpu().numpy()).max() <= 3e-2
+
+
+# --------------------------------------------------------------------------- the paper's decoder on the tensor cores
+
+PAPER = dict(res=(64, 32, 16, 16), target_res=128, batch=700, dims=(12, 16, 9))
+
+
+@pytest.mark.parametrize("free", [False, True])
+def test_paper_decoder_trains_on_the_tensor_cores_and_matches_oracle(free):
+    """The paper's two-layer decoder (12 inputs, one hidden layer of 16, 9 outputs; Sec. 5.1) runs the
+    tensor-core training kernel: forward under the strict output check, every gradient value within its
+    per-element bound of the oracle's (block features and unconstrained features)."""
+    _bcf()
+    w = workloads.train_workload(**PAPER)
+    if free:
+        tex = workloads.free_texels(w)
+        tr = workloads.upload_free_trainer(w, tex, lod_input=False)
+        F = oracle.TrainFeatures([t[:, :3].astype(np.float64) for t in tex], None, w.res, w.levels, w.res_ref,
+                                 lod_input=False, free=True)
+    else:
+        tr = workloads.upload_trainer(w, lod_input=False)
+        F = oracle.TrainFeatures([workloads.params32_to_28(p).astype(np.float64) for p in w.params], w.partition,
+                                 w.res, w.levels, w.res_ref, lod_input=False)
+    P = oracle.TrainMlp(w.dims, w.W, w.b, bf16=True)
+    u, v, s = _queries(w.batch, w.target_levels - 1, seed=51)
+    q = [torch.from_numpy(a).cuda() for a in (u, v, s)]
+    got = tr.forward(*q).cpu().numpy().astype(np.float64)
+    ref = oracle.train_outputs(F, P, u, v, s)
+    r = oracle.check_outputs(got, ref, TOL_BF16, False,
+                             oracle.train_explainer(F, P, u, v, s, got, TOL_BF16, lod_input=False))
+    assert not r["unexplained"], (r["unexplained"][:5], r["worst"])
+    go = np.random.default_rng(52).standard_normal((w.batch, 9)).astype(np.float32) * 1e-2
+    tr.zero_grad()
+    tr.backward(*q, torch.from_numpy(go).cuda())
+    gf, gW, gb = oracle.train_backward_given(F, P, u, v, s, go.astype(np.float64))
+    feats = [(f"texels{t}", tr.grads[t].cpu().numpy()[:, :3], gf[t], t) for t in range(len(gf))] if free else \
+        [(f"features{t}", workloads.params32_to_28(tr.grads[t].cpu().numpy()), gf[t], t) for t in range(len(gf))]
+    _grad_checks(F, P, u, v, s, go.astype(np.float64),
+                 [("W", tr.W_grad.cpu().numpy(), gW, "W"), ("b", tr.b_grad.cpu().numpy(), gb, "b")] + feats)
