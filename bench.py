@@ -4,13 +4,17 @@ One step = one full decode of the screen workload through ``bcf_decode_material`
 4 BC6H feature textures of 2048^2 with full mip chains (value-bounded random
 blocks over all 14 modes), 3840x2160 queries of a perspective-viewed tiled
 plane (uv and LOD from the per-pixel screen Jacobian), MLP 13-32-32-9 on the
-tensor cores.  The timed configuration is decode variant 3: the footprint
-texels are decoded by the texture unit's BC6H decoder (point sampling), then
-filtered exactly in FP32 and run through the MLP in the library's kernel; its
-output is bit-identical to the library's software decoders, whose own time
-(variant 0) is reported beside it.  ``value`` is the whole-job decode throughput in Gsamples/s with
-inputs resident in HBM; ``e2e`` is the same metric through the C ABI with the
-queries in pinned host memory and the decoded channels read back every step.
+tensor cores.  The timed configuration is decode variant 0 with the tcgen05
+MLP engine: the library's own BC6H decoder (16-byte block loads, blocks
+mode-sorted and decoded into a shared-memory texel arena per 256-query tile),
+the exact FP32 trilinear filter, and the MLP on the fifth-generation tensor
+cores (128-row MMAs, accumulators in tensor memory).  Beside it: the same
+decode with the texels fetched through the texture unit's BC6H decoder
+(variant 3, the paper's render-time design; bit-identical texels), the
+warp-level MMA engine, and the hardware-trilinear comparator.  ``value`` is the
+whole-job decode throughput in Gsamples/s with inputs resident in HBM;
+``e2e`` is the same metric through the C ABI with the queries in pinned host
+memory and the decoded channels read back every step.
 
 Extra keys report the FP32 SIMT plain path and the FP8 path on the same frame,
 the batched 64-material launch, the 8x4096^2 frame (FP8 / FP16 / FP32), the
@@ -44,10 +48,11 @@ sys.path.insert(0, ROOT)
 
 METRIC = "Gsamples/s BCf decode (BC6H+filter+MLP) low-prec vs FP32 plain; train steps/s"
 HEADLINE_PRECISION = "fp16"
-# bcf_set_decode_variant of the timed low-precision paths: 3 = every footprint texel decoded by the texture
-# unit (point sampling: the hardware BC6H decoder, bit-exact), the exact FP32 filter and the register-chained
-# tensor-core MLP in the library's kernel; bit-identical to the software decoders (variants 0 and 1)
-HEADLINE_VARIANT = 3
+# bcf_set_decode_variant / bcf_set_mlp_engine of the timed low-precision paths: variant 0 = the library's
+# BC6H decoder (tile-cooperative, shared-memory texel arena), the exact FP32 filter, the MLP on tcgen05
+HEADLINE_VARIANT = 0
+HEADLINE_ENGINE = "tcgen05"
+TEXUNIT_VARIANT = 3  # the same decode on the texture unit's BC6H texels (point sampling, bit-exact)
 
 
 def _peaks():
@@ -62,10 +67,10 @@ def _peaks():
 # DRAM traffic and executed warp instructions of one launch of the headline kernel, from one full ncu
 # capture of it on the same workload.  They are reported only while the
 # kernel's sources hash to the value the capture was taken on; after any change they read as null.
-KERNEL_SOURCES = ["bcf_decode.cu", "bcf_texunit.cu", "bc6h_unpack.cuh", "bcf_sample.cuh", "bcf_mlp.cuh",
+KERNEL_SOURCES = ["bcf_decode_tiled.cu", "bc6h_unpack.cuh", "bcf_sample.cuh", "bcf_mlp.cuh", "bcf_tcmlp.cuh",
                   "bcf_internal.h"]
-NCU_CAPTURE = {"source_sha256": "180a8e69f4bb67ea", "dram_bytes": 120741120 + 102364416, "warp_inst": 321041160,
-               "tex_pipe_pct": 70.30, "issue_active_pct": 60.89, "tensor_active_pct": 12.59}
+NCU_CAPTURE = {"source_sha256": "a94f903dac228a05", "dram_bytes": 121604352 + 112405504, "warp_inst": 597675400,
+               "issue_active_pct": 56.30, "tensor_pipe_pct": 1.56, "warps_active_pct": 47.28}
 SM_COUNT, SMSP_PER_SM, FP32_LANES_PER_SM = 148, 4, 128
 
 
@@ -342,6 +347,7 @@ def main():
     mats = {p: workloads.upload(w, p) for p in (HEADLINE_PRECISION, "fp32", "fp8")}
     for p in (HEADLINE_PRECISION, "fp8"):
         mats[p].set_decode_variant(HEADLINE_VARIANT)
+        mats[p].set_mlp_engine(HEADLINE_ENGINE)
     out = torch.empty((w.n, 9), dtype=torch.float16, device="cuda")
     out32 = torch.empty((w.n, 9), dtype=torch.float32, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 126 MB L2
@@ -397,10 +403,14 @@ def main():
     fp32_ms = timed(mats["fp32"], k_extra, 3, out=out32) / k_extra
     # the FP32 MLP on the texture unit's texels (variant 3): the same precision gap with the same texel path
     m32t = workloads.upload(w, "fp32")
-    m32t.set_decode_variant(HEADLINE_VARIANT)
+    m32t.set_decode_variant(TEXUNIT_VARIANT)
     fp32t_ms = timed(m32t, k_extra, 3, out=out32) / k_extra
     del m32t
     fp8_ms = timed(mats["fp8"], k_extra, 3) / k_extra
+    # the same decode with the warp-level MMA engine (the MLP per warp on mma.sync), bit for bit the texel path
+    mats[HEADLINE_PRECISION].set_mlp_engine("mma_sync")
+    warp_mma_ms = timed(mats[HEADLINE_PRECISION], k_extra, 3) / k_extra
+    mats[HEADLINE_PRECISION].set_mlp_engine(HEADLINE_ENGINE)
 
     # the texture-unit comparator (decode variant 2: hardware trilinear filtering of BC6H texture objects)
     m_hw = workloads.upload(w, HEADLINE_PRECISION)
@@ -411,16 +421,18 @@ def main():
     hw_err = (hw_out.float() - out.float()).abs()
     hw_stats = {"mean_abs_vs_exact": float(hw_err.mean()), "max_abs_vs_exact": float(hw_err.max())}
     del hw_out, hw_err
-    # the library's own BC6H decoder: the tile-cooperative software decode (variant 0), bit-identical output
-    m_hw.set_decode_variant(0)
-    sw_ms = timed(m_hw, k_extra, 3) / k_extra
-    m_hw.set_decode_variant(HEADLINE_VARIANT)
+    # the texture unit's BC6H decoder for the footprint texels (variant 3, the paper's render-time design), the
+    # exact filter: with the warp-level MMA engine (its fastest form) and with the headline's tcgen05 engine,
+    # whose outputs equal the headline's bit for bit
+    m_hw.set_decode_variant(TEXUNIT_VARIANT)
+    tex_ms = timed(m_hw, k_extra, 3) / k_extra
+    m_hw.set_mlp_engine(HEADLINE_ENGINE)
+    tex_tc_ms = timed(m_hw, k_extra, 3) / k_extra
     sw_out = torch.empty_like(out)
     m_hw.decode(u, v, s, out=sw_out)
-    m_hw.set_decode_variant(0)
-    m_hw.decode(u, v, s, out=out)
-    sw_identical = bool(torch.equal(out, sw_out))
-    del m_hw, sw_out
+    mats[HEADLINE_PRECISION].decode(u, v, s, out=out)
+    tex_identical = bool(torch.equal(out, sw_out))
+    del sw_out
 
     # the texel-fetch roofline of the headline: the texture unit's point-fetch rate on the same material's
     # level-0 texels in screen-coherent order (bcf_texunit_fetch_probe), against the fetches one headline launch
@@ -428,16 +440,16 @@ def main():
     probe_rounds = 8
     sink = torch.empty(w.n, dtype=torch.float32, device="cuda")
     for _ in range(3):
-        mats[HEADLINE_PRECISION].texunit_fetch_probe(w.n, probe_rounds, sink=sink)
+        m_hw.texunit_fetch_probe(w.n, probe_rounds, sink=sink)
     torch.cuda.synchronize()
     pa, pb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     pa.record(stream)
     for _ in range(5):
-        mats[HEADLINE_PRECISION].texunit_fetch_probe(w.n, probe_rounds, sink=sink)
+        m_hw.texunit_fetch_probe(w.n, probe_rounds, sink=sink)
     pb.record(stream)
     pb.synchronize()
     probe_rate = 5 * 4 * probe_rounds * w.n / (pa.elapsed_time(pb) * 1e-3)
-    del sink
+    del sink, m_hw
     head_fetches = 0
     s_clean = np.where(np.isnan(w.s), np.float32(0.0), w.s).astype(np.float32)
     for res_t, lev_t in zip(w.res, w.levels):
@@ -471,7 +483,7 @@ def main():
         return a1.elapsed_time(b1) * 10.0
 
     small_sw_us = launch_us()  # the library's per-lane BC6H decoder (random blocks of all 14 modes)
-    m1.set_decode_variant(HEADLINE_VARIANT)  # the texture unit's texels, the same FP32 filter and MLP
+    m1.set_decode_variant(TEXUNIT_VARIANT)  # the texture unit's texels, the same FP32 filter and MLP
     small_us = launch_us()
     del m1, u1, v1, o1
 
@@ -610,8 +622,8 @@ def main():
         sw_set_total += a.elapsed_time(b)
     sw_set_ms = sw_set_total / k_extra
     del S0
-    for m in set_mats:  # the timed set: every material on the headline variant
-        m.set_decode_variant(HEADLINE_VARIANT)
+    for m in set_mats:  # the texture-unit set: every material on variant 3
+        m.set_decode_variant(TEXUNIT_VARIANT)
     S = bcf.MaterialSet(set_mats)
     tex_cfg = S.autotune(soff, su, sv, ss, sout)  # CTAs per SM and tiles per grab of the texture-unit set kernel
     side = torch.cuda.Stream()
@@ -660,22 +672,25 @@ def main():
     wp = workloads.paper_bcf1k()
     up_, vp_, sp_ = workloads.queries_to_device(wp)
     mp_ = workloads.upload(wp, "fp16")
-    mp_.set_decode_variant(HEADLINE_VARIANT)
     outp = torch.empty((wp.n, 9), dtype=torch.float16, device="cuda")
-    for _ in range(3):
-        mp_.decode(up_, vp_, sp_, out=outp)
-    torch.cuda.synchronize()
-    tot = 0.0
-    for _ in range(k_extra):
-        flush.zero_()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        mp_.decode(up_, vp_, sp_, out=outp)
-        b.record(stream)
-        b.synchronize()
-        tot += a.elapsed_time(b)
-    paper_ms = tot / k_extra
+    paper_ms_v = {}
+    for var in (TEXUNIT_VARIANT, 0):  # the texture unit's texels, as the paper's shader; the library's decoder
+        mp_.set_decode_variant(var)
+        for _ in range(3):
+            mp_.decode(up_, vp_, sp_, out=outp)
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(k_extra):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            mp_.decode(up_, vp_, sp_, out=outp)
+            b.record(stream)
+            b.synchronize()
+            tot += a.elapsed_time(b)
+        paper_ms_v[var] = tot / k_extra
+    paper_ms = paper_ms_v[TEXUNIT_VARIANT]
     paper_n = wp.n
     del mp_, up_, vp_, sp_, outp, wp
 
@@ -684,15 +699,12 @@ def main():
     u5, v5, s5 = workloads.queries_to_device(w5)
     out5 = torch.empty((w5.n, 9), dtype=torch.float16, device="cuda")
     cfg5 = {}
-    for prec in ("fp8", "fp16", "fp32"):
-        m5 = workloads.upload(w5, prec)
-        if prec != "fp32":
-            m5.set_decode_variant(HEADLINE_VARIANT)
+
+    def time5(m5, k5):
         for _ in range(2):
             m5.decode(u5, v5, s5, out=out5)
         torch.cuda.synchronize()
         tot = 0.0
-        k5 = 3 if prec != "fp32" else 2
         for _ in range(k5):
             flush.zero_()
             a = torch.cuda.Event(enable_timing=True)
@@ -702,7 +714,24 @@ def main():
             b.record(stream)
             b.synchronize()
             tot += a.elapsed_time(b)
-        cfg5[prec] = {"value": w5.n / (tot / k5 * 1e-3) / 1e9, "unit": "Gsamples/s", "ms_per_step": tot / k5}
+        return tot / k5
+
+    tex5_paths = {}
+    for prec in ("fp8", "fp16", "fp32"):
+        m5 = workloads.upload(w5, prec)
+        if prec != "fp32":
+            m5.set_decode_variant(HEADLINE_VARIANT)
+            m5.set_mlp_engine(HEADLINE_ENGINE)
+        ms5 = time5(m5, 3 if prec != "fp32" else 2)
+        cfg5[prec] = {"value": w5.n / (ms5 * 1e-3) / 1e9, "unit": "Gsamples/s", "ms_per_step": ms5}
+        if prec != "fp32":
+            # the texture unit's texels (variant 3) with either MLP engine
+            m5.set_decode_variant(TEXUNIT_VARIANT)
+            for eng in ("mma_sync", "tcgen05"):
+                m5.set_mlp_engine(eng)
+                ms5 = time5(m5, 3)
+                tex5_paths[f"{prec}_{eng}"] = {"value": w5.n / (ms5 * 1e-3) / 1e9, "unit": "Gsamples/s",
+                                               "ms_per_step": ms5}
         del m5
     n5 = w5.n
     del u5, v5, s5, out5, w5
@@ -717,7 +746,8 @@ def main():
     head_launch_s = head_ms / args.steps * 1e-3
     achieved = alg_bytes / head_launch_s / 1e9
     counters_valid = _kernel_sha() == NCU_CAPTURE["source_sha256"] and HEADLINE_PRECISION == "fp16"
-    counters_valid = counters_valid and HEADLINE_VARIANT == 3
+    counters_valid = counters_valid and HEADLINE_VARIANT == 0 and HEADLINE_ENGINE == "tcgen05"
+    tex_launch_s = tex_ms * 1e-3
     mlp_flops = 2 * sum(a * b for a, b in zip(w.dims[:-1], w.dims[1:]))  # 3,456 per query for 13-32-32-9
 
     # large frame: tensor roofline of the MLP (25-64-64-9, 12,544 flop/query) and HBM bytes per path
@@ -735,6 +765,7 @@ def main():
         if not args.no_cpu_baseline and world == 1:
             mats["bf16"] = workloads.upload(w, "bf16")
             mats["bf16"].set_decode_variant(HEADLINE_VARIANT)
+            mats["bf16"].set_mlp_engine(HEADLINE_ENGINE)
             cpu, acc = _cpu_baseline(w, HEADLINE_PRECISION,
                                      {p: gathered(p) for p in ("fp16", "bf16", "fp8", "fp32")})
         line = {
@@ -744,8 +775,11 @@ def main():
             "config": {"workload": "screen decode: 4x BC6H 2048^2 full mips (value-bounded, all 14 modes), "
                                    "3840x2160 perspective-plane queries, MLP 13-32-32-9",
                        "queries_per_step": w.n, "precision": HEADLINE_PRECISION, "out": "fp16 [N][9]",
-                       "decode_variant": "3: BC6H texels decoded by the texture unit (point sampling, bit-exact), "
-                                         "exact FP32 trilinear filter, tensor-core MLP",
+                       "decode_variant": "0: the library's BC6H decoder (16-byte block loads, mode-sorted blocks "
+                                         "decoded into a shared-memory texel arena per 256-query tile), exact "
+                                         "FP32 trilinear filter",
+                       "mlp_engine": "tcgen05: 128-row MMAs from shared-memory tiles, FP32 accumulators in "
+                                     "tensor memory",
                        "l2": "256 MB buffer written between timed steps",
                        "parallelism": f"replicas x{world}"},
             "fp32_plain": {"value": w.n / (fp32_ms * 1e-3) / 1e9, "unit": "Gsamples/s", "ms_per_step": fp32_ms,
@@ -763,7 +797,7 @@ def main():
             "batched": {"value": set_n / (set_ms * 1e-3) / 1e9, "unit": "Gsamples/s", "ms_per_step": set_ms,
                         "queries": set_n, "materials": 64, "precision": "fp16",
                         "launch": "one persistent launch replayed from a CUDA graph",
-                        "decode_variant": HEADLINE_VARIANT,
+                        "decode_variant": TEXUNIT_VARIANT,
                         "autotuned": {"ctas_per_sm": tex_cfg[1], "tiles_per_grab": tex_cfg[2]},
                         "software_decode": {"value": set_n / (sw_set_ms * 1e-3) / 1e9, "unit": "Gsamples/s",
                                             "ms_per_step": sw_set_ms,
@@ -774,13 +808,17 @@ def main():
             "paper_bcf1k_2160p": {"value": paper_n / (paper_ms * 1e-3) / 1e9, "unit": "Gsamples/s",
                                   "ms_per_step": paper_ms, "queries": paper_n,
                                   "workload": "BC6H 1024/512/256/128 with 9/8/7/6 levels, MLP 12-16-9, FP16, "
-                                              "variant 3, 3840x2160 plane queries",
+                                              "variant 3 (texture-unit texels), 3840x2160 plane queries",
+                                  "software_decode": {"value": paper_n / (paper_ms_v[0] * 1e-3) / 1e9,
+                                                      "unit": "Gsamples/s", "ms_per_step": paper_ms_v[0]},
                                   "context": "the paper's neural overhead at 2160p: 0.640 ms on an RTX 2070 "
                                              "(hardware trilinear, graphics pipeline)"},
-            "large_8x4096": {"queries": n5, "mlp": "25-64-64-9", "flop_per_query": flops5, **cfg5},
+            "large_8x4096": {"queries": n5, "mlp": "25-64-64-9", "flop_per_query": flops5,
+                             "paths": "fp8 / fp16: the headline path (variant 0, tcgen05); fp32: the plain SIMT path",
+                             **cfg5, "texture_unit_texels": tex5_paths},
             "small_2x256": {"queries": 65536, "mlp": "6-16-16-8 fp32", "us_per_launch": small_us,
                             "value": 65536 / (small_us * 1e-6) / 1e9, "unit": "Gsamples/s",
-                            "decode_variant": HEADLINE_VARIANT,
+                            "decode_variant": TEXUNIT_VARIANT,
                             "software_decode_us_per_launch": small_sw_us,
                             "note": "launch-latency bound: 100 back-to-back launches, no flush"},
             "train": {"metric": "train steps/s", "value": 1000.0 / train_ms, "unit": "steps/s",
@@ -792,10 +830,25 @@ def main():
                                                 "workload": "torch index_add_ of 2^24 random updates into "
                                                             "9.79 M floats"},
                       "adam_algorithmic_bytes_per_step": 313_000_000},
-            "software_decode": {"value": w.n / (sw_ms * 1e-3) / 1e9, "unit": "Gsamples/s", "ms_per_step": sw_ms,
-                                "precision": HEADLINE_PRECISION, "kernel": "k_decode_tiled (decode variant 0: "
-                                "tile-cooperative software BC6H decode into shared memory)",
-                                "identical_to_headline": sw_identical},
+            "warp_mma_engine": {"value": w.n / (warp_mma_ms * 1e-3) / 1e9, "unit": "Gsamples/s",
+                                "ms_per_step": warp_mma_ms, "precision": HEADLINE_PRECISION,
+                                "kernel": "the headline decode with the MLP per warp on mma.sync"},
+            "texture_unit_texels": {
+                "value": w.n / (tex_ms * 1e-3) / 1e9, "unit": "Gsamples/s", "ms_per_step": tex_ms,
+                "precision": HEADLINE_PRECISION,
+                "kernel": "decode variant 3: every footprint texel fetched through the texture unit's BC6H decoder "
+                          "(point sampling, bit-exact), the same exact filter, warp-level MMA MLP (the paper's "
+                          "render-time design for the unpack)",
+                "tcgen05_engine": {"value": w.n / (tex_tc_ms * 1e-3) / 1e9, "unit": "Gsamples/s",
+                                   "ms_per_step": tex_tc_ms, "identical_to_headline": tex_identical},
+                "roofline": {"bound": "hbm", "achieved": alg_bytes / tex_launch_s / 1e9, "peak": hbm_peak,
+                             "unit": "GB/s", "frac": alg_bytes / tex_launch_s / 1e9 / hbm_peak,
+                             "peak_kind": peak_kind},
+                "texel_fetch": {"unit": "texel fetches/s", "achieved": head_fetches / tex_launch_s,
+                                "peak": probe_rate, "frac": head_fetches / tex_launch_s / probe_rate,
+                                "fetches_per_launch": head_fetches,
+                                "peak_source": "bcf_texunit_fetch_probe: 2x2 point-fetch footprints of the same "
+                                               "material's level-0 texels, screen-coherent, measured in this run"}},
             "texunit": {"value": w.n / (hw_ms * 1e-3) / 1e9, "unit": "Gsamples/s", "ms_per_step": hw_ms,
                         "precision": HEADLINE_PRECISION, "kernel": "decode variant 2: hardware trilinear filtering of "
                         "mipmapped BC6H texture objects + tensor-core MLP (per-lane)", **hw_stats},
@@ -806,8 +859,8 @@ def main():
             "train_paper_decoder": {"metric": "train steps/s", "value": 1000.0 / ptrain_ms, "unit": "steps/s",
                                     "ms_per_step": ptrain_ms, "batch": train_batch,
                                     "workload": "the paper's BCf-1K textures (1024/512/256/128 with mips), 2048^2 "
-                                                "reference, its 12-16-9 decoder without the LOD input (SIMT "
-                                                "kernel), Adam"},
+                                                "reference, its 12-16-9 decoder without the LOD input "
+                                                "(tensor-core kernel), Adam"},
             "train_unconstrained": {"metric": "train steps/s", "value": 1000.0 / free_ms, "unit": "steps/s",
                                     "ms_per_step": free_ms, "batch": train_batch,
                                     "workload": "first stage: free per-texel features, 4x 1024^2 with 9 levels"},
@@ -822,7 +875,7 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak,
                          "traffic": NCU_CAPTURE["dram_bytes"] if counters_valid else None, "peak_kind": peak_kind,
-                         "kernel": f"k_decode_mma<{HEADLINE_PRECISION}, texture-unit texels, 16-32-32-16>",
+                         "kernel": f"k_decode_geo<{HEADLINE_PRECISION}, 16-32-32-16, tcgen05 MLP>",
                          "algorithmic_bytes_per_launch": alg_bytes,
                          "co_bound": {"bound": "issue", "unit": "G warp-instructions/s",
                                       "achieved": (NCU_CAPTURE["warp_inst"] / head_launch_s / 1e9
@@ -831,21 +884,9 @@ def main():
                                       "frac": (NCU_CAPTURE["warp_inst"] / head_launch_s / 1e9 / issue_peak
                                                if counters_valid else None),
                                       "note": "executed (not algorithmic) instructions per launch from ncu; "
-                                              "peak = 148 SMs x 4 partitions x 1 issue/clock at the max SM clock"},
-                         "limiter": {"unit": "texture data pipe, pct of peak (ncu l1tex__data_pipe_tex_wavefronts)",
-                                     "value": NCU_CAPTURE["tex_pipe_pct"] if counters_valid else None,
-                                     "texel_fetch": {"unit": "texel fetches/s",
-                                                     "achieved": head_fetches / head_launch_s,
-                                                     "peak": probe_rate,
-                                                     "frac": head_fetches / head_launch_s / probe_rate,
-                                                     "fetches_per_launch": head_fetches,
-                                                     "peak_source": "bcf_texunit_fetch_probe: 2x2 point-fetch "
-                                                                    "footprints of the headline material's level-0 "
-                                                                    "texels, screen-coherent, measured in this run"},
-                                     "note": "the busiest unit of the headline kernel: 32 point-sampled texel "
-                                             "fetches per query; issue active and tensor pipe " +
-                                             (f"{NCU_CAPTURE['issue_active_pct']}% / {NCU_CAPTURE['tensor_active_pct']}%"
-                                              if counters_valid else "n/a")},
+                                              "peak = 148 SMs x 4 partitions x 1 issue/clock at the max SM clock: "
+                                              "the BC6H unpack, filter and MLP epilogue are instruction-issue "
+                                              "work, the bytes they move are few"},
                          "tensor": {"achieved_tflops": mlp_flops * w.n / head_launch_s / 1e12,
                                     "peak_tflops": bf16_peak,
                                     "frac": mlp_flops * w.n / head_launch_s / 1e12 / bf16_peak}},
