@@ -40,6 +40,12 @@ def test_clean_work_leaves_the_word_clear():
     S = bcf.MaterialSet([workloads.upload(m, "fp16") for m in sw.materials])
     u, v, s = (torch.from_numpy(a).cuda() for a in sw.concat())
     S.decode(torch.from_numpy(sw.offsets).cuda(), u, v, s)
+    # a decode with the MLP on tcgen05 (its bounded MMA waits are what BCF_CHECK_TIMEOUT reports)
+    m = workloads.upload(sw.materials[0], "fp16")
+    m.set_decode_variant(0)
+    m.set_mlp_engine("tcgen05")
+    a, b = int(sw.offsets[0]), int(sw.offsets[1])
+    m.decode(u[a:b], v[a:b], s[a:b])
     assert bcf.device_check() == 0
 
 

@@ -339,14 +339,16 @@ def test_texture_unit_texels_with_exact_filter_equal_the_software_decode(precisi
     assert torch.equal(got, ref)
 
 
-@pytest.mark.parametrize("variant", [0, 3])
-def test_full_size_screen_decode_sampled_against_oracle(variant):
-    """The 4 x 2048^2 / 3840x2160 FP16 workload in the launch configuration the benchmark times (whole frame,
-    FP16 output), checked on 20,000 sampled queries against the quantisation-aware oracle."""
+@pytest.mark.parametrize("variant,engine", [(0, "tcgen05"), (0, "mma_sync"), (3, "mma_sync")])
+def test_full_size_screen_decode_sampled_against_oracle(variant, engine):
+    """The 4 x 2048^2 / 3840x2160 FP16 workload in the launch configurations the benchmark times (whole frame,
+    FP16 output; the headline is variant 0 with the tcgen05 MLP), checked on 20,000 sampled queries against the
+    quantisation-aware oracle."""
     bcf = _bcf()
     w = workloads.config2()
     m = workloads.upload(w, "fp16")
     m.set_decode_variant(variant)
+    m.set_mlp_engine(engine)
     u, v, s = workloads.queries_to_device(w)
     out = torch.empty((w.n, 9), dtype=torch.float16, device="cuda")
     m.decode(u, v, s, out=out)
@@ -364,16 +366,21 @@ def large_frame():
     return workloads.config5()
 
 
-@pytest.mark.parametrize("precision", ["fp8", "fp16", "fp32"])
-def test_full_size_large_frame_sampled_against_oracle(large_frame, precision):
-    """The 8 x 4096^2 / 7680x4320 workload (MLP 25-64-64-9) at full size in the launch configuration the
-    benchmark times (whole frame, FP16 output; FP8 and FP16 on decode variant 3, FP32 on the plain path),
-    checked on 8,192 sampled queries: the low-precision paths against the quantisation-aware oracle, the FP32
-    path against FP64 within a few FP32 roundings of the network's magnitude bound."""
+@pytest.mark.parametrize("precision,path", [("fp8", "v0_tcgen05"), ("fp16", "v0_tcgen05"), ("fp8", "v3_mma_sync"),
+                                            ("fp16", "v3_mma_sync"), ("fp32", "plain")])
+def test_full_size_large_frame_sampled_against_oracle(large_frame, precision, path):
+    """The 8 x 4096^2 / 7680x4320 workload (MLP 25-64-64-9) at full size in the launch configurations the
+    benchmark times (whole frame, FP16 output; FP8 and FP16 on the hand-written decode with the tcgen05 MLP and
+    on decode variant 3, FP32 on the plain path), checked on 8,192 sampled queries: the low-precision paths
+    against the quantisation-aware oracle, the FP32 path against FP64 within a few FP32 roundings of the
+    network's magnitude bound."""
     bcf = _bcf()
     w = large_frame
     m = workloads.upload(w, precision)
-    if precision != "fp32":
+    if path == "v0_tcgen05":
+        m.set_decode_variant(0)
+        m.set_mlp_engine("tcgen05")
+    elif path == "v3_mma_sync":
         m.set_decode_variant(3)
     u, v, s = workloads.queries_to_device(w)
     out = torch.empty((w.n, 9), dtype=torch.float16, device="cuda")
