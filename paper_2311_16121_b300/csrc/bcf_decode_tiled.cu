@@ -740,7 +740,8 @@ __global__ void __launch_bounds__(kTileQ, 3) k_decode_set(const MaterialDev *__r
 // ------------------------------------------------- single-geometry tiles
 
 // Materials whose textures all share one resolution and level count (one geometry group) take a leaner tile
-// kernel: the footprint geometry is computed once per query and kept in registers, the tile's block boxes are
+// kernel over tiles of TQ queries (one per thread; 512 or 256, see geo_tq): the footprint geometry is computed
+// once per query and kept in registers, the tile's block boxes are
 // kept per absolute level (no separate LOD-range pass), every thread sizes the block set itself (no planning
 // warp), and a tile costs four CTA barriers:
 //   1. per query: LOD, levels and footprint per side; per warp and level the block box by warp reductions,
@@ -768,7 +769,7 @@ struct GeoLayout {
     int w_bytes, b_bytes, meta, sraw, sidx, arena, per_warp, tmp8, total;
 };
 
-template <int PREC>
+template <int PREC, int TQ>
 __host__ __device__ inline GeoLayout geo_layout(const MlpDev &P, int cap)
 {
     GeoLayout L;
@@ -797,7 +798,7 @@ __host__ __device__ inline GeoLayout geo_layout(const MlpDev &P, int cap)
     const int a0 = alias ? (in0 > ostb ? in0 : ostb) : in0 + ostb;
     L.tmp8 = a0;
     L.per_warp = a0 + tmp;
-    L.total = off + (kTileQ / 32) * L.per_warp;
+    L.total = off + (TQ / 32) * L.per_warp;
     return L;
 }
 
@@ -808,10 +809,10 @@ struct GeoTcLayout {
     int w_bytes, b_bytes, meta, sraw, sidx, arena, x, bar, tslot, total;
 };
 
-template <int PREC, int K0, int N1, int N2, int NO>
+template <int PREC, int K0, int N1, int N2, int NO, int TQ>
 __host__ __device__ inline GeoTcLayout geo_tc_layout(const MlpDev &P, int cap)
 {
-    using T = TcMlp<PREC, 8, K0, N1, N2, NO>;
+    using T = TcMlp<PREC, TQ / 32, K0, N1, N2, NO>;
     GeoTcLayout L;
     int off = 0;
     L.w_bytes = T::W_BYTES;
@@ -825,7 +826,7 @@ __host__ __device__ inline GeoTcLayout geo_tc_layout(const MlpDev &P, int cap)
     L.sidx = off;
     off += (cap * 2 + 127) & ~127;
     L.arena = off;
-    const int ostb = 32 * 8 * P.dims[P.n_layers] * 4;
+    const int ostb = TQ * P.dims[P.n_layers] * 4;
     int ab = cap * 16 * 8;
     ab = ab > T::Y_BYTES ? ab : T::Y_BYTES;
     ab = ab > ostb ? ab : ostb;
@@ -842,7 +843,7 @@ __host__ __device__ inline GeoTcLayout geo_tc_layout(const MlpDev &P, int cap)
 
 __device__ __forceinline__ void reset_geo_meta(GeoMeta &G)
 {
-    for (int i = threadIdx.x; i < BCF_MAX_LEVELS; i += kTileQ) {
+    for (int i = threadIdx.x; i < BCF_MAX_LEVELS; i += blockDim.x) {
         G.box[i][0] = G.box[i][2] = INT_MAX;
         G.box[i][1] = G.box[i][3] = INT_MIN;
     }
@@ -879,19 +880,23 @@ __device__ __noinline__ float3 sample_texture_ool(const TexDev &T, int wrap, boo
     return sample_texture(T, wrap, sgn, u, v, s);
 }
 
+// Arena item tags (shared-memory sort keys of the decode phase): item index in the low kGeoTagBits bits, the
+// item's arena swizzle (4 bits) above them.
+constexpr int kGeoTagBits = 10;
+
 // Decode arena blocks [first, items) (sorted by mode) with 1 << lk threads per block: each thread decodes the
 // header and 16 >> lk texels; sgn is a template parameter so that the unsigned and signed paths are each
 // specialised (the caller branches once, uniformly, on the material's format).
-template <bool SGN>
+template <bool SGN, int TQ>
 __device__ __forceinline__ void decode_arena_blocks(const uint4 *sraw, const uint16_t *sidx, uint2 *arena, int items,
                                                     int lk)
 {
-    for (int i = threadIdx.x; i < (items << lk); i += kTileQ) {
+    for (int i = threadIdx.x; i < (items << lk); i += TQ) {
         const int e = i >> lk, part = i & ((1 << lk) - 1);
         const uint4 rr = sraw[e];
         const int tag = sidx[e];
-        uint2 *dst = arena + (tag & 255) * 16;
-        const int swz = tag >> 8;
+        uint2 *dst = arena + (tag & ((1 << kGeoTagBits) - 1)) * 16;
+        const int swz = tag >> kGeoTagBits;
         Bc6hBlock bk;
         bk.lo = (uint64_t)rr.x | ((uint64_t)rr.y << 32);
         bk.hi = (uint64_t)rr.z | ((uint64_t)rr.w << 32);
@@ -908,13 +913,14 @@ __device__ __forceinline__ void decode_arena_blocks(const uint4 *sraw, const uin
 }
 
 
-template <int PREC, int CAP, int K0, int N1, int N2, int NO, bool TC>
-__global__ void __launch_bounds__(kTileQ, kGeoMinBlocks) k_decode_geo(MaterialDev M, const float *__restrict__ qu,
+template <int PREC, int CAP, int K0, int N1, int N2, int NO, bool TC, int TQ>
+__global__ void __launch_bounds__(TQ, kGeoMinBlocks * 256 / TQ) k_decode_geo(MaterialDev M, const float *__restrict__ qu,
                                                           const float *__restrict__ qv, const float *__restrict__ qs,
                                                           int64_t n, void *__restrict__ out, int out_fp16,
                                                           unsigned *__restrict__ check)
 {
-    static_assert(CAP <= kTileQ, "one block item per thread while loading");
+    static_assert(CAP <= TQ && CAP <= (1 << kGeoTagBits), "one block item per thread while loading; item tags");
+    constexpr int NW = TQ / 32;
     extern __shared__ __align__(16) unsigned char smem[];
     const MlpDev &P = M.mlp;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -932,7 +938,7 @@ __global__ void __launch_bounds__(kTileQ, kGeoMinBlocks) k_decode_geo(MaterialDe
     uint64_t *bar = nullptr;
     uint32_t *tslot = nullptr;
     if constexpr (TC) {
-        const GeoTcLayout LY = geo_tc_layout<PREC, K0, N1, N2, NO>(P, CAP);
+        const GeoTcLayout LY = geo_tc_layout<PREC, K0, N1, N2, NO, TQ>(P, CAP);
         sw = smem;
         sb = (float *)(smem + LY.b_bytes);
         meta = (GeoMeta *)(smem + LY.meta);
@@ -944,21 +950,21 @@ __global__ void __launch_bounds__(kTileQ, kGeoMinBlocks) k_decode_geo(MaterialDe
         bar = (uint64_t *)(smem + LY.bar);
         tslot = (uint32_t *)(smem + LY.tslot);
     } else {
-        const GeoLayout LY = geo_layout<PREC>(P, CAP);
+        const GeoLayout LY = geo_layout<PREC, TQ>(P, CAP);
         sw = smem;
         sb = (float *)(smem + LY.b_bytes);
         meta = (GeoMeta *)(smem + LY.meta);
         sraw = (uint4 *)(smem + LY.sraw);
         sidx = (uint16_t *)(smem + LY.sidx);
         arena = (uint2 *)(smem + LY.arena);
-        act0 = smem + LY.total - (kTileQ / 32 - warp) * LY.per_warp;
+        act0 = smem + LY.total - (NW - warp) * LY.per_warp;
         tmp8 = act0 + LY.tmp8;
         ost = (float *)act0; // output staging aliases the input tile or follows it (geo_layout)
         if (!(16 * Cn * 4 <= 16 * row_stride))
             ost = (float *)(act0 + ((32 * row_stride + 15) & ~15));
     }
     RowWriter<PREC> rw{act0 + lane * row_stride, inv0, 0.0f};
-    TcRowWriter<PREC, 8, (K0 > 0 ? K0 : 16), (N1 > 0 ? N1 : 16), (N2 > 0 ? N2 : 16), (NO > 0 ? NO : 16)> tw{
+    TcRowWriter<PREC, NW, (K0 > 0 ? K0 : 16), (N1 > 0 ? N1 : 16), (N2 > 0 ? N2 : 16), (NO > 0 ? NO : 16)> tw{
         xtile, (int)threadIdx.x, inv0, 0.0f};
     const auto put = [&](int col, float x) {
         if constexpr (TC)
@@ -973,10 +979,10 @@ __global__ void __launch_bounds__(kTileQ, kGeoMinBlocks) k_decode_geo(MaterialDe
     const unsigned lanes_lt = (1u << lane) - 1u;
 
     uint32_t tmem = 0, phase = 0;
-    constexpr int kTcCols = TcMlp<PREC, 8, (K0 > 0 ? K0 : 16), (N1 > 0 ? N1 : 16), (N2 > 0 ? N2 : 16),
+    constexpr int kTcCols = TcMlp<PREC, NW, (K0 > 0 ? K0 : 16), (N1 > 0 ? N1 : 16), (N2 > 0 ? N2 : 16),
                                   (NO > 0 ? NO : 16)>::NCOLS;
     if constexpr (TC) {
-        tc_load_weights<PREC, 8, K0, N1, N2, NO>(P, sw, sb);
+        tc_load_weights<PREC, NW, K0, N1, N2, NO>(P, sw, sb);
         if (threadIdx.x == 0) {
             mbar_init(bar, 1);
             mbar_init_fence();
@@ -994,24 +1000,24 @@ __global__ void __launch_bounds__(kTileQ, kGeoMinBlocks) k_decode_geo(MaterialDe
         tmem = *tslot;
     }
 
-    const int64_t tiles = (n + kTileQ - 1) / kTileQ;
+    const int64_t tiles = (n + TQ - 1) / TQ;
     float nu = 0.0f, nv = 0.0f, ns = 0.0f, nu_ref = 0.0f, nv_ref = 0.0f;
     {
-        const int64_t q = (int64_t)blockIdx.x * kTileQ + threadIdx.x;
+        const int64_t q = (int64_t)blockIdx.x * TQ + threadIdx.x;
         if (blockIdx.x < tiles && q < n) {
             nu = qu[q];
             nv = qv[q];
             ns = qs ? qs[q] : 0.0f;
         }
         if (blockIdx.x < tiles) {
-            nu_ref = qu[(int64_t)blockIdx.x * kTileQ];
-            nv_ref = qv[(int64_t)blockIdx.x * kTileQ];
+            nu_ref = qu[(int64_t)blockIdx.x * TQ];
+            nv_ref = qv[(int64_t)blockIdx.x * TQ];
         }
     }
     int parity = 0;
     for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, parity ^= 1) {
         GeoMeta &G = meta[parity];
-        const int64_t q_first = tile * kTileQ;
+        const int64_t q_first = tile * TQ;
         const int64_t q = q_first + threadIdx.x;
         const bool active = q < n;
         const float u = active ? sanitize(nu, wrap) : 0.0f;
@@ -1020,15 +1026,15 @@ __global__ void __launch_bounds__(kTileQ, kGeoMinBlocks) k_decode_geo(MaterialDe
         // the tile's first query: the reference of the relative block coordinates
         const float u_ref = sanitize(nu_ref, wrap), v_ref = sanitize(nv_ref, wrap);
         {
-            const int64_t qn = (tile + gridDim.x) * kTileQ + threadIdx.x;
+            const int64_t qn = (tile + gridDim.x) * TQ + threadIdx.x;
             if (tile + gridDim.x < tiles && qn < n) {
                 nu = qu[qn];
                 nv = qv[qn];
                 ns = qs ? qs[qn] : 0.0f;
             }
             if (tile + gridDim.x < tiles) {
-                nu_ref = qu[(tile + gridDim.x) * kTileQ];
-                nv_ref = qv[(tile + gridDim.x) * kTileQ];
+                nu_ref = qu[(tile + gridDim.x) * TQ];
+                nv_ref = qv[(tile + gridDim.x) * TQ];
             }
         }
         // ---- 1. footprint geometry per side, block boxes per level
@@ -1165,18 +1171,18 @@ __global__ void __launch_bounds__(kTileQ, kGeoMinBlocks) k_decode_geo(MaterialDe
                     const int start = __shfl_sync(0xffffffffu, excl, valid ? bin : 0);
                     if (valid) {
                         sraw[start + rank] = blk;
-                        sidx[start + rank] = (uint16_t)(it | (jlow << 8));
+                        sidx[start + rank] = (uint16_t)(it | (jlow << kGeoTagBits));
                     }
                 }
                 __syncthreads(); // barrier 3
                 if (threadIdx.x < 16)
                     G.hist[threadIdx.x] = 0; // for the next round (read again only after its barrier 2)
-                // ---- 4. decode the sorted blocks into the arena: one thread per block, two when there are few
-                const int lk = items <= 64 ? 1 : 0;
+                // ---- 4. decode the sorted blocks into the arena: one thread per block, two when that fills the CTA
+                const int lk = items * 2 <= TQ ? 1 : 0;
                 if (sgn)
-                    decode_arena_blocks<true>(sraw, sidx, arena, items, lk);
+                    decode_arena_blocks<true, TQ>(sraw, sidx, arena, items, lk);
                 else
-                    decode_arena_blocks<false>(sraw, sidx, arena, items, lk);
+                    decode_arena_blocks<false, TQ>(sraw, sidx, arena, items, lk);
                 __syncthreads(); // barrier 4
                 // ---- 5. filter the round's textures from the arena: per side the corner geometry, shared by
                 // every texture (item offsets within one texture's block set), then 4 arena texels per texture
@@ -1258,7 +1264,7 @@ __global__ void __launch_bounds__(kTileQ, kGeoMinBlocks) k_decode_geo(MaterialDe
         // ---- 6. MLP on the tensor cores, coalesced store
         if constexpr (TC) {
             // the CTA tile's 256 rows through tcgen05 (its first barrier also ends every warp's filter)
-            bool ok = tc_mlp3<PREC, 8, K0, N1, N2, NO>(P, sw, sb, xtile, (unsigned char *)arena, ost, Cn, bar, phase,
+            bool ok = tc_mlp3<PREC, NW, K0, N1, N2, NO>(P, sw, sb, xtile, (unsigned char *)arena, ost, Cn, bar, phase,
                                                        tmem, 1 << 20);
             ok = __syncthreads_and(ok) != 0;
             if (!ok) {
@@ -1312,24 +1318,40 @@ static int tiled_sms()
     return sms;
 }
 
-constexpr int kGeoCap = 224; // block arena of the single-geometry kernel (4 CTAs of 256 threads per SM)
+// Tile size of the single-geometry kernel: 512 queries where the MLP's operand tiles are small (hidden width
+// <= 32, or E4M3 operands), which halves the per-query share of the tile's fixed work (the BC6H header paths,
+// run once per mode present in a warp, and the barriers) at two resident CTAs of 16 warps per SM; 256 queries
+// for the 64-wide 16-bit MLP, whose 512-row operand tiles would leave room for one CTA per SM (measured on the
+// 8 x 4096^2 frame: 7.13 ms at 256, 7.43 ms at 512; E4M3 6.88 ms at 256, 5.49 ms at 512).
+#ifndef BCF_GEO_TQ_NARROW
+#define BCF_GEO_TQ_NARROW 512
+#endif
+#ifndef BCF_GEO_TQ_WIDE
+#define BCF_GEO_TQ_WIDE 256
+#endif
+template <int PREC, int N1>
+constexpr int geo_tq() { return (N1 <= 32 || PREC == BCF_FP8_E4M3) ? BCF_GEO_TQ_NARROW : BCF_GEO_TQ_WIDE; }
+// block arena: one block per thread (one round for almost every tile); 224 blocks for 256-query tiles, which
+// keeps 4 CTAs per SM
+constexpr int geo_cap(int tq) { return tq >= 512 ? 512 : 224; }
 
 template <int PREC, int K0, int N1, int N2, int NO, bool TC>
 static cudaError_t launch_geo_engine(const MaterialDev &M, const float *u, const float *v, const float *s, int64_t n,
                                      void *out, int out_fp16, cudaStream_t st)
 {
+    constexpr int TQ = geo_tq<PREC, N1>(), CAP = geo_cap(TQ);
     int64_t smem;
     int max_per_sm = 32;
     if constexpr (TC) {
-        smem = geo_tc_layout<PREC, K0, N1, N2, NO>(M.mlp, kGeoCap).total;
+        smem = geo_tc_layout<PREC, K0, N1, N2, NO, TQ>(M.mlp, CAP).total;
         // every resident CTA holds its tensor-memory columns for its whole life: at most 512 columns per SM
-        max_per_sm = 512 / TcMlp<PREC, 8, K0, N1, N2, NO>::NCOLS;
+        max_per_sm = 512 / TcMlp<PREC, TQ / 32, K0, N1, N2, NO>::NCOLS;
     } else {
-        smem = geo_layout<PREC>(M.mlp, kGeoCap).total;
+        smem = geo_layout<PREC, TQ>(M.mlp, CAP).total;
     }
     if (smem > 227 * 1024)
         return cudaErrorInvalidConfiguration;
-    auto kern = k_decode_geo<PREC, kGeoCap, K0, N1, N2, NO, TC>;
+    auto kern = k_decode_geo<PREC, CAP, K0, N1, N2, NO, TC, TQ>;
     static int configured = 0;
     if (!configured) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
@@ -1346,13 +1368,13 @@ static cudaError_t launch_geo_engine(const MaterialDev &M, const float *u, const
         int dev = 0, smem_sm = 228 * 1024;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-        const int by_regs = 65536 / (kTileQ * ((regs + 7) & ~7));
+        const int by_regs = 65536 / (TQ * ((regs + 7) & ~7));
         const int by_smem = smem_sm / (int)(smem + 1024);
         per_sm = max(1, min(min(by_regs, by_smem), max_per_sm));
     }
-    const int64_t tiles = (n + kTileQ - 1) / kTileQ;
+    const int64_t tiles = (n + TQ - 1) / TQ;
     const int64_t grid = min(tiles, (int64_t)tiled_sms() * per_sm);
-    kern<<<(unsigned)grid, kTileQ, (size_t)smem, st>>>(M, u, v, s, n, out, out_fp16, check_word());
+    kern<<<(unsigned)grid, TQ, (size_t)smem, st>>>(M, u, v, s, n, out, out_fp16, check_word());
     return cudaGetLastError();
 }
 

@@ -133,7 +133,7 @@ __host__ __device__ constexpr int tc_pow2_cols(int n) { return n <= 32 ? 32 : n 
 
 template <int PREC, int NW, int K0, int N1, int N2, int NO>
 struct TcMlp {
-    static_assert(NW == 4 || NW == 8, "128-row MMA halves");
+    static_assert(NW == 4 || NW == 8 || NW == 16 || NW == 32, "whole 128-row MMA quarters of the tile");
     static constexpr int EB = PREC == BCF_FP8_E4M3 ? 1 : 2;
     static constexpr int KS = PREC == BCF_FP8_E4M3 ? 32 : 16; // K per MMA instruction
     static constexpr int ROWS = 32 * NW, HALVES = NW / 4;
