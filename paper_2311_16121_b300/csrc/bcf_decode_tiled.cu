@@ -1263,7 +1263,7 @@ __global__ void __launch_bounds__(TQ, kGeoMinBlocks * 256 / TQ) k_decode_geo(Mat
         }
         // ---- 6. MLP on the tensor cores, coalesced store
         if constexpr (TC) {
-            // the CTA tile's 256 rows through tcgen05 (its first barrier also ends every warp's filter)
+            // the CTA tile's TQ rows through tcgen05 (its first barrier also ends every warp's filter)
             bool ok = tc_mlp3<PREC, NW, K0, N1, N2, NO>(P, sw, sb, xtile, (unsigned char *)arena, ost, Cn, bar, phase,
                                                        tmem, 1 << 20);
             ok = __syncthreads_and(ok) != 0;

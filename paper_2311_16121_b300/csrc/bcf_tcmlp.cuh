@@ -1,20 +1,24 @@
 // bcf_tcmlp.cuh -- the MLP decoder f_eta of Eq. 3 on the fifth-generation tensor cores (tcgen05) for a CTA tile
-// of 32 NW queries (NW = 4 or 8 warps).
+// of 32 NW queries (NW = 4, 8 or 16 warps).
 //
-// One thread issues the layer's MMAs (M = 128 rows per instruction, one per 128-row half of the tile, K = 16
-// for FP16 / BF16 and 32 for E4M3 per instruction, FP32 accumulation in tensor memory); every thread then
-// reads its own row's accumulators from tensor memory (tcgen05.ld, 32 lanes x 32-bit columns per warp), adds
-// the FP32 bias, applies ReLU and rounds to the next layer's operand type straight into that layer's A tile in
-// shared memory.  Operand tiles use the canonical K-major layout without swizzling: 8-row groups of 16-byte
+// Every thread first writes the layer's FP32 bias into its own row's accumulator columns in tensor memory
+// (tcgen05.st; for E4M3 the bias divided by the layer's power-of-two product scale, which is exact); one
+// thread then issues the layer's MMAs (M = 128 rows per instruction, one per 128-row part of the tile, K = 16
+// for FP16 / BF16 and 32 for E4M3 per instruction), which accumulate onto the bias in FP32; every thread reads
+// its own row's accumulators back (tcgen05.ld, 32 lanes x 32-bit columns per warp), applies ReLU and rounds to
+// the next layer's operand type straight into that layer's A tile in shared memory.  The part of the tile a
+// row lies in owns one block of MAXN accumulator columns for all three layers (the parts share the 128 lanes).
+// Operand tiles use the canonical K-major layout without swizzling: 8-row groups of 16-byte
 // core matrices, core matrices along K 128 bytes apart (the descriptor's leading byte offset), 8-row groups
 // (K bytes / 16) x 128 bytes apart (its stride byte offset).
 //
-// Synchronisation per layer: the A tile's writers fence their generic-proxy stores for the async proxy and
-// meet at a CTA barrier; the issuing thread orders the MMAs after it (tcgen05.fence::after_thread_sync) and
-// commits them to an mbarrier; every thread waits on that mbarrier (a bounded wait: when it runs out, the
-// caller's check word gets BCF_CHECK_TIMEOUT and the kernel stops taking tiles) and reads the accumulators;
-// before the next layer overwrites the same tensor-memory columns the readers fence their loads
-// (tcgen05.fence::before_thread_sync) ahead of the next barrier.
+// Synchronisation per layer: every thread waits for its bias stores (tcgen05.wait::st) and orders them, and
+// its reads of the previous layer's accumulators, before the barrier (tcgen05.fence::before_thread_sync); the
+// A tile's writers fence their generic-proxy stores for the async proxy; all meet at a CTA barrier (which also
+// keeps the A tiles in y, aliasing the caller's texel arena, from being written before every warp's filter is
+// done); the issuing thread orders the MMAs after it (tcgen05.fence::after_thread_sync) and commits them to an
+// mbarrier; every thread waits on that mbarrier (a bounded wait: when it runs out, the caller's check word gets
+// BCF_CHECK_TIMEOUT and the kernel stops taking tiles) and reads the accumulators.
 #pragma once
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -110,6 +114,22 @@ __device__ __forceinline__ void tc_commit(uint64_t *bar)
                      smem_addr(bar))
                  : "memory");
 }
+
+// Store 16 consecutive 32-bit columns of the calling thread's tensor-memory lane (completion: tc_wait_st).
+__device__ __forceinline__ void tc_st16(uint32_t taddr, const float (&v)[16])
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                 "%13, %14, %15, %16};" ::"r"(taddr),
+                 "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+                 "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+                 "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+                 "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+                 "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+                 "r"(__float_as_uint(v[15]))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 // 16 consecutive 32-bit accumulator columns of the calling thread's tensor-memory lane.
 __device__ __forceinline__ void tc_ld16(uint32_t taddr, float (&v)[16])
@@ -213,10 +233,11 @@ struct TcRowWriter {
     }
 };
 
-// Issue one layer: for every 128-row half, K / KS MMAs accumulating A (rows of that half, K columns) x B^T
-// into tensor-memory columns [col0 + half N, col0 + half N + N), then commit them to the mbarrier.
-template <int PREC, int NW, int K, int N>
-__device__ __forceinline__ void tc_issue_layer(uint32_t tmem, int col0, const unsigned char *a, const unsigned char *b,
+// Issue one layer: for every 128-row part h of the tile, K / KS MMAs accumulating A (rows of that part, K
+// columns) x B^T onto tensor-memory columns [h CS, h CS + N) (which hold the bias), then commit them to the
+// mbarrier.
+template <int PREC, int NW, int K, int N, int CS>
+__device__ __forceinline__ void tc_issue_layer(uint32_t tmem, const unsigned char *a, const unsigned char *b,
                                                uint64_t *bar)
 {
     constexpr int EB = PREC == BCF_FP8_E4M3 ? 1 : 2, KS = PREC == BCF_FP8_E4M3 ? 32 : 16;
@@ -231,17 +252,37 @@ __device__ __forceinline__ void tc_issue_layer(uint32_t tmem, int col0, const un
             // K step s covers KS elements = 2 core matrices along K (2 x 128 bytes)
             const uint64_t ad = tc_smem_desc(smem_addr(a) + h * 16 * SBO + s * 256, 128, SBO);
             const uint64_t bd = tc_smem_desc(smem_addr(b) + s * 256, 128, SBO);
-            tc_mma<PREC>(tmem + (uint32_t)(col0 + h * N), ad, bd, idesc, s > 0 ? 1u : 0u);
+            tc_mma<PREC>(tmem + (uint32_t)(h * CS), ad, bd, idesc, 1u);
         }
     tc_commit(bar);
 }
 
-// Hidden epilogue of one layer for the calling thread's row: accumulators (N columns) + bias, ReLU, rounding to
-// the operand type (E4M3: after the product scale and the next layer's inverse activation scale) into the next
-// A tile (row r, N columns), 16 bytes at a time.
+// Write the bias of a layer (N columns; multiplied by inv, the inverse of the layer's product scale) into the
+// calling thread's accumulator columns starting at trow, and wait for the stores.
+template <int N>
+__device__ __forceinline__ void tc_bias_init(uint32_t trow, const float *bias, float inv)
+{
+#pragma unroll
+    for (int c0 = 0; c0 < N; c0 += 16) {
+        float v[16];
+#pragma unroll
+        for (int j = 0; j < 16; j += 4) {
+            const float4 b4 = *reinterpret_cast<const float4 *>(bias + c0 + j);
+            v[j] = b4.x * inv;
+            v[j + 1] = b4.y * inv;
+            v[j + 2] = b4.z * inv;
+            v[j + 3] = b4.w * inv;
+        }
+        tc_st16(trow + (uint32_t)c0, v);
+    }
+    tc_wait_st();
+}
+
+// Hidden epilogue of one layer for the calling thread's row: accumulators (N columns, bias included), ReLU,
+// rounding to the operand type (E4M3: after the product scale and the next layer's inverse activation scale)
+// into the next A tile (row r, N columns), 16 bytes at a time.
 template <int PREC, int NW, int K0, int N1, int N2, int NO, int N>
-__device__ __forceinline__ void tc_hidden(uint32_t trow, const float *bias, float oscale, float next_inv,
-                                          unsigned char *anext, int r)
+__device__ __forceinline__ void tc_hidden(uint32_t trow, float oscale, float next_inv, unsigned char *anext, int r)
 {
     using T = TcMlp<PREC, NW, K0, N1, N2, NO>;
 #pragma unroll
@@ -252,10 +293,10 @@ __device__ __forceinline__ void tc_hidden(uint32_t trow, const float *bias, floa
             uint32_t w[4];
 #pragma unroll
             for (int j = 0; j < 4; ++j) {
-                const float x0 = fmaxf(v[4 * j] * oscale + bias[c0 + 4 * j], 0.f) * next_inv;
-                const float x1 = fmaxf(v[4 * j + 1] * oscale + bias[c0 + 4 * j + 1], 0.f) * next_inv;
-                const float x2 = fmaxf(v[4 * j + 2] * oscale + bias[c0 + 4 * j + 2], 0.f) * next_inv;
-                const float x3 = fmaxf(v[4 * j + 3] * oscale + bias[c0 + 4 * j + 3], 0.f) * next_inv;
+                const float x0 = fmaxf(v[4 * j] * oscale, 0.f) * next_inv;
+                const float x1 = fmaxf(v[4 * j + 1] * oscale, 0.f) * next_inv;
+                const float x2 = fmaxf(v[4 * j + 2] * oscale, 0.f) * next_inv;
+                const float x3 = fmaxf(v[4 * j + 3] * oscale, 0.f) * next_inv;
                 w[j] = Op<PREC>::pack2(x0, x1) | (Op<PREC>::pack2(x2, x3) << 16);
             }
             *reinterpret_cast<uint4 *>(anext + T::off(r, c0, N)) = make_uint4(w[0], w[1], w[2], w[3]);
@@ -263,7 +304,7 @@ __device__ __forceinline__ void tc_hidden(uint32_t trow, const float *bias, floa
             uint32_t w[8];
 #pragma unroll
             for (int j = 0; j < 8; ++j)
-                w[j] = Op<PREC>::pack2_relu(v[2 * j] + bias[c0 + 2 * j], v[2 * j + 1] + bias[c0 + 2 * j + 1]);
+                w[j] = Op<PREC>::pack2_relu(v[2 * j], v[2 * j + 1]);
             *reinterpret_cast<uint4 *>(anext + T::off(r, c0, N)) = make_uint4(w[0], w[1], w[2], w[3]);
             *reinterpret_cast<uint4 *>(anext + T::off(r, c0 + 8, N)) = make_uint4(w[4], w[5], w[6], w[7]);
         }
@@ -281,10 +322,11 @@ __device__ __forceinline__ bool tc_mlp3(const MlpDev &P, const unsigned char *w,
                                         uint32_t tmem, int wait_limit)
 {
     using T = TcMlp<PREC, NW, K0, N1, N2, NO>;
+    constexpr int CS = T::MAXN; // accumulator columns of one 128-row part
     const int warp = threadIdx.x >> 5, r = threadIdx.x;
     const int half = warp >> 2;
-    // this thread's tensor-memory lane: lane quarter (warp % 4) of the CTA's allocation
-    const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+    // this thread's tensor-memory lane (lane quarter warp % 4 of the CTA's allocation) and its part's columns
+    const uint32_t trow = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(half * CS);
     const unsigned char *W0 = w, *W1 = w + T::W0B, *W2 = W1 + T::W1B;
     const float *b0 = sb, *b1 = sb + N1, *b2 = sb + N1 + N2;
     float sc0 = 1.f, sc1 = 1.f, sc2 = 1.f, in1 = 1.f, in2 = 1.f;
@@ -295,43 +337,51 @@ __device__ __forceinline__ bool tc_mlp3(const MlpDev &P, const unsigned char *w,
         in1 = P.inv_act_scale[1];
         in2 = P.inv_act_scale[2];
     }
+    // the products of an E4M3 layer are scaled by sc after the sum: its bias enters the sum as b / sc (exact:
+    // the scales are powers of two)
+    const float ib0 = PREC == BCF_FP8_E4M3 ? 1.0f / sc0 : 1.0f, ib1 = PREC == BCF_FP8_E4M3 ? 1.0f / sc1 : 1.0f,
+                ib2 = PREC == BCF_FP8_E4M3 ? 1.0f / sc2 : 1.0f;
     bool ok = true;
-    // layer 1: A0 (x) -> columns [0, HALVES N1)
+    // layer 1: bias, then A0 (x) accumulated onto it
+    tc_bias_init<N1>(trow, b0, ib0);
+    tc_fence_before();
     fence_async_smem();
     __syncthreads();
     if (threadIdx.x == 0)
-        tc_issue_layer<PREC, NW, K0, N1>(tmem, 0, x, W0, bar);
+        tc_issue_layer<PREC, NW, K0, N1, CS>(tmem, x, W0, bar);
     ok = mbar_wait_bounded(bar, phase, wait_limit) && ok;
     phase ^= 1u;
     tc_fence_after();
-    tc_hidden<PREC, NW, K0, N1, N2, NO, N1>(tmem + lane_base + (uint32_t)(half * N1), b0, sc0, in1, y, r);
+    tc_hidden<PREC, NW, K0, N1, N2, NO, N1>(trow, sc0, in1, y, r);
+    // layer 2 into the same columns (read above); A2 then overwrites A1 in y
+    tc_bias_init<N2>(trow, b1, ib1);
     tc_fence_before();
-    // layer 2: A1 (y) -> the same columns (read above); A2 then overwrites A1 in y
     fence_async_smem();
     __syncthreads();
     if (threadIdx.x == 0)
-        tc_issue_layer<PREC, NW, N1, N2>(tmem, 0, y, W1, bar);
+        tc_issue_layer<PREC, NW, N1, N2, CS>(tmem, y, W1, bar);
     ok = mbar_wait_bounded(bar, phase, wait_limit) && ok;
     phase ^= 1u;
     tc_fence_after();
-    tc_hidden<PREC, NW, K0, N1, N2, NO, N2>(tmem + lane_base + (uint32_t)(half * N2), b1, sc1, in2, y, r);
-    tc_fence_before();
+    tc_hidden<PREC, NW, K0, N1, N2, NO, N2>(trow, sc1, in2, y, r);
     // layer 3: A2 (y) -> outputs
+    tc_bias_init<NO>(trow, b2, ib2);
+    tc_fence_before();
     fence_async_smem();
     __syncthreads();
     if (threadIdx.x == 0)
-        tc_issue_layer<PREC, NW, N2, NO>(tmem, 0, y, W2, bar);
+        tc_issue_layer<PREC, NW, N2, NO, CS>(tmem, y, W2, bar);
     ok = mbar_wait_bounded(bar, phase, wait_limit) && ok;
     phase ^= 1u;
     tc_fence_after();
 #pragma unroll
     for (int c0 = 0; c0 < NO; c0 += 16) {
         float v[16];
-        tc_ld16(tmem + lane_base + (uint32_t)(half * NO + c0), v);
+        tc_ld16(trow + (uint32_t)c0, v);
 #pragma unroll
         for (int j = 0; j < 16; ++j)
             if (c0 + j < C)
-                ost[r * C + c0 + j] = PREC == BCF_FP8_E4M3 ? v[j] * sc2 + b2[c0 + j] : v[j] + b2[c0 + j];
+                ost[r * C + c0 + j] = PREC == BCF_FP8_E4M3 ? v[j] * sc2 : v[j];
     }
     tc_fence_before();
     return ok;
