@@ -4,14 +4,15 @@ One step = one full decode of the screen workload through ``bcf_decode_material`
 4 BC6H feature textures of 2048^2 with full mip chains (value-bounded random
 blocks over all 14 modes), 3840x2160 queries of a perspective-viewed tiled
 plane (uv and LOD from the per-pixel screen Jacobian), MLP 13-32-32-9 on the
-tensor cores.  The timed configuration is decode variant 0 with the tcgen05
-MLP engine: the library's own BC6H decoder (16-byte block loads, blocks
-mode-sorted and decoded into a shared-memory texel arena per 256-query tile),
-the exact FP32 trilinear filter, and the MLP on the fifth-generation tensor
-cores (128-row MMAs, accumulators in tensor memory).  Beside it: the same
-decode with the texels fetched through the texture unit's BC6H decoder
-(variant 3, the paper's render-time design; bit-identical texels), the
-warp-level MMA engine, and the hardware-trilinear comparator.  ``value`` is the
+tensor cores.  The timed configuration is decode variant 0: the library's own
+BC6H decoder (16-byte block loads, blocks mode-sorted and decoded into a
+shared-memory texel arena per 512-query tile), the exact FP32 trilinear
+filter, and the MLP per warp on mma.sync (for this narrow 16-bit network the
+faster engine; the tcgen05 engine -- 128-row MMAs, accumulators in tensor
+memory -- is timed beside it and runs the FP8 and 25-64-64-9 paths).  Beside
+it: the same decode with the texels fetched through the texture unit's BC6H
+decoder (variant 3, the paper's render-time design; bit-identical texels) and
+the hardware-trilinear comparator.  ``value`` is the
 whole-job decode throughput in Gsamples/s with inputs resident in HBM;
 ``e2e`` is the same metric through the C ABI with the queries in pinned host
 memory and the decoded channels read back every step.
@@ -49,9 +50,15 @@ sys.path.insert(0, ROOT)
 METRIC = "Gsamples/s BCf decode (BC6H+filter+MLP) low-prec vs FP32 plain; train steps/s"
 HEADLINE_PRECISION = "fp16"
 # bcf_set_decode_variant / bcf_set_mlp_engine of the timed low-precision paths: variant 0 = the library's
-# BC6H decoder (tile-cooperative, shared-memory texel arena), the exact FP32 filter, the MLP on tcgen05
+# BC6H decoder (tile-cooperative, shared-memory texel arena), the exact FP32 filter.  The MLP engine per path is
+# the faster of the two measured on it: the per-warp mma.sync MLP for the narrow 16-bit 13-32-32-9 network (no
+# per-layer MMA round trip through tensor memory to wait for), tcgen05 for E4M3 operands and for the 64-wide
+# 25-64-64-9 network; the other engine is timed beside each.
 HEADLINE_VARIANT = 0
-HEADLINE_ENGINE = "tcgen05"
+HEADLINE_ENGINE = "mma_sync"
+FP8_ENGINE = "tcgen05"
+LARGE_ENGINE = "tcgen05"
+OTHER_ENGINE = {"mma_sync": "tcgen05", "tcgen05": "mma_sync"}
 TEXUNIT_VARIANT = 3  # the same decode on the texture unit's BC6H texels (point sampling, bit-exact)
 
 
@@ -69,8 +76,8 @@ def _peaks():
 # kernel's sources hash to the value the capture was taken on; after any change they read as null.
 KERNEL_SOURCES = ["bcf_decode_tiled.cu", "bc6h_unpack.cuh", "bcf_sample.cuh", "bcf_mlp.cuh", "bcf_tcmlp.cuh",
                   "bcf_internal.h"]
-NCU_CAPTURE = {"source_sha256": "a94f903dac228a05", "dram_bytes": 121604352 + 112405504, "warp_inst": 597675400,
-               "issue_active_pct": 56.30, "tensor_pipe_pct": 1.56, "warps_active_pct": 47.28}
+NCU_CAPTURE = {"engine": "mma_sync", "source_sha256": "d8db9472b5ae2c74", "dram_bytes": 121664256 + 113799936,
+               "warp_inst": 561838783, "issue_active_pct": 62.15, "tensor_pipe_pct": 7.34, "warps_active_pct": 46.71}
 SM_COUNT, SMSP_PER_SM, FP32_LANES_PER_SM = 148, 4, 128
 
 
@@ -347,7 +354,7 @@ def main():
     mats = {p: workloads.upload(w, p) for p in (HEADLINE_PRECISION, "fp32", "fp8")}
     for p in (HEADLINE_PRECISION, "fp8"):
         mats[p].set_decode_variant(HEADLINE_VARIANT)
-        mats[p].set_mlp_engine(HEADLINE_ENGINE)
+        mats[p].set_mlp_engine(HEADLINE_ENGINE if p == HEADLINE_PRECISION else FP8_ENGINE)
     out = torch.empty((w.n, 9), dtype=torch.float16, device="cuda")
     out32 = torch.empty((w.n, 9), dtype=torch.float32, device="cuda")
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")  # > 126 MB L2
@@ -407,10 +414,13 @@ def main():
     fp32t_ms = timed(m32t, k_extra, 3, out=out32) / k_extra
     del m32t
     fp8_ms = timed(mats["fp8"], k_extra, 3) / k_extra
-    # the same decode with the warp-level MMA engine (the MLP per warp on mma.sync), bit for bit the texel path
-    mats[HEADLINE_PRECISION].set_mlp_engine("mma_sync")
-    warp_mma_ms = timed(mats[HEADLINE_PRECISION], k_extra, 3) / k_extra
+    # the same decode with the other MLP engine (the texel path bit for bit the same)
+    mats[HEADLINE_PRECISION].set_mlp_engine(OTHER_ENGINE[HEADLINE_ENGINE])
+    other_engine_ms = timed(mats[HEADLINE_PRECISION], k_extra, 3) / k_extra
     mats[HEADLINE_PRECISION].set_mlp_engine(HEADLINE_ENGINE)
+    mats["fp8"].set_mlp_engine(OTHER_ENGINE[FP8_ENGINE])
+    fp8_other_ms = timed(mats["fp8"], k_extra, 3) / k_extra
+    mats["fp8"].set_mlp_engine(FP8_ENGINE)
 
     # the texture-unit comparator (decode variant 2: hardware trilinear filtering of BC6H texture objects)
     m_hw = workloads.upload(w, HEADLINE_PRECISION)
@@ -422,12 +432,14 @@ def main():
     hw_stats = {"mean_abs_vs_exact": float(hw_err.mean()), "max_abs_vs_exact": float(hw_err.max())}
     del hw_out, hw_err
     # the texture unit's BC6H decoder for the footprint texels (variant 3, the paper's render-time design), the
-    # exact filter: with the warp-level MMA engine (its fastest form) and with the headline's tcgen05 engine,
-    # whose outputs equal the headline's bit for bit
+    # exact filter: with the warp-level MMA engine (its fastest form; outputs equal to the headline's bit for bit)
+    # and with the tcgen05 engine
     m_hw.set_decode_variant(TEXUNIT_VARIANT)
+    m_hw.set_mlp_engine("mma_sync")
     tex_ms = timed(m_hw, k_extra, 3) / k_extra
-    m_hw.set_mlp_engine(HEADLINE_ENGINE)
+    m_hw.set_mlp_engine("tcgen05")
     tex_tc_ms = timed(m_hw, k_extra, 3) / k_extra
+    m_hw.set_mlp_engine(HEADLINE_ENGINE)
     sw_out = torch.empty_like(out)
     m_hw.decode(u, v, s, out=sw_out)
     mats[HEADLINE_PRECISION].decode(u, v, s, out=out)
@@ -598,75 +610,62 @@ def main():
     enc_blocks = 4 * bcf.texture_blocks(enc_res, enc_levels)
     del enc_tex, enc_out
 
-    # batched multi-material decode: 64 materials, one persistent graph-captured launch, autotuned
+    # batched multi-material decode: 64 materials, one persistent graph-captured launch, autotuned, against the
+    # same materials as 64 separate single-material launches (own 16-byte-aligned outputs); the hand-written
+    # decode (variant 0, the headline's engine) and the texture unit's texels (variant 3)
     sw = workloads.config4()
     set_mats = [workloads.upload(m, "fp16") for m in sw.materials]
     su, sv, ss = (torch.from_numpy(a).cuda() for a in sw.concat())
     soff = torch.from_numpy(sw.offsets).cuda()
     sout = torch.empty((sw.n, 9), dtype=torch.float16, device="cuda")
-    # the tile-cooperative software decode of the set (materials on variant 0), autotuned, for reference
-    S0 = bcf.MaterialSet(set_mats)
-    set_cfg = S0.autotune(soff, su, sv, ss, sout)
-    for _ in range(3):
-        S0.decode(soff, su, sv, ss, out=sout)
-    torch.cuda.synchronize()
-    sw_set_total = 0.0
-    for _ in range(k_extra):
-        flush.zero_()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        S0.decode(soff, su, sv, ss, out=sout)
-        b.record(stream)
-        b.synchronize()
-        sw_set_total += a.elapsed_time(b)
-    sw_set_ms = sw_set_total / k_extra
-    del S0
-    for m in set_mats:  # the texture-unit set: every material on variant 3
-        m.set_decode_variant(TEXUNIT_VARIANT)
-    S = bcf.MaterialSet(set_mats)
-    tex_cfg = S.autotune(soff, su, sv, ss, sout)  # CTAs per SM and tiles per grab of the texture-unit set kernel
-    side = torch.cuda.Stream()
-    side.wait_stream(torch.cuda.current_stream())
-    with torch.cuda.stream(side):
-        S.decode(soff, su, sv, ss, out=sout)
-    torch.cuda.current_stream().wait_stream(side)
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph):
-        S.decode(soff, su, sv, ss, out=sout)
-    for _ in range(3):
-        graph.replay()
-    torch.cuda.synchronize()
-    set_total = 0.0
-    for _ in range(k_extra):
-        flush.zero_()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        graph.replay()
-        b.record(stream)
-        b.synchronize()
-        set_total += a.elapsed_time(b)
-    set_ms = set_total / k_extra
-    # the same materials as 64 separate single-material launches (own 16-byte-aligned outputs)
     seq_out = [torch.empty((int(sw.offsets[m + 1] - sw.offsets[m]), 9), dtype=torch.float16, device="cuda")
                for m in range(len(set_mats))]
     seq_q = [tuple(t[int(sw.offsets[m]):int(sw.offsets[m + 1])].clone() for t in (su, sv, ss))
              for m in range(len(set_mats))]
-    seq_total = 0.0
-    for _ in range(k_extra):
-        flush.zero_()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for m, mat in enumerate(set_mats):
-            mat.decode(*seq_q[m], out=seq_out[m])
-        b.record(stream)
-        b.synchronize()
-        seq_total += a.elapsed_time(b)
-    seq_ms = seq_total / k_extra
+
+    def time_steps(fn):
+        for _ in range(3):
+            fn()
+        torch.cuda.synchronize()
+        tot = 0.0
+        for _ in range(k_extra):
+            flush.zero_()
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            b.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / k_extra
+
+    def set_vs_sequential(variant, engine):
+        for m in set_mats:
+            m.set_decode_variant(variant)
+            m.set_mlp_engine(engine)
+        S = bcf.MaterialSet(set_mats)
+        cfg = S.autotune(soff, su, sv, ss, sout)
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            S.decode(soff, su, sv, ss, out=sout)
+        torch.cuda.current_stream().wait_stream(side)
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            S.decode(soff, su, sv, ss, out=sout)
+        one_ms = time_steps(graph.replay)
+        seq = time_steps(lambda: [mat.decode(*seq_q[m], out=seq_out[m]) for m, mat in enumerate(set_mats)])
+        graph.replay()
+        torch.cuda.synchronize()
+        same = all(torch.equal(sout[int(sw.offsets[m]):int(sw.offsets[m + 1])], seq_out[m])
+                   for m in range(len(set_mats)))
+        del graph, S
+        return one_ms, seq, cfg, same
+
+    set_ms, seq_ms, set_cfg, set_same = set_vs_sequential(HEADLINE_VARIANT, HEADLINE_ENGINE)
+    tset_ms, tseq_ms, tex_cfg, tset_same = set_vs_sequential(TEXUNIT_VARIANT, "mma_sync")
     set_n = sw.n
-    del graph, S, set_mats, su, sv, ss, sout, seq_out, seq_q
+    del set_mats, su, sv, ss, sout, seq_out, seq_q
 
     # the paper's own decode configuration (Table 1 BCf-1K, decoder 12-16-9) at 3840x2160, FP16, variant 3
     wp = workloads.paper_bcf1k()
@@ -721,7 +720,7 @@ def main():
         m5 = workloads.upload(w5, prec)
         if prec != "fp32":
             m5.set_decode_variant(HEADLINE_VARIANT)
-            m5.set_mlp_engine(HEADLINE_ENGINE)
+            m5.set_mlp_engine(LARGE_ENGINE)
         ms5 = time5(m5, 3 if prec != "fp32" else 2)
         cfg5[prec] = {"value": w5.n / (ms5 * 1e-3) / 1e9, "unit": "Gsamples/s", "ms_per_step": ms5}
         if prec != "fp32":
@@ -746,7 +745,7 @@ def main():
     head_launch_s = head_ms / args.steps * 1e-3
     achieved = alg_bytes / head_launch_s / 1e9
     counters_valid = _kernel_sha() == NCU_CAPTURE["source_sha256"] and HEADLINE_PRECISION == "fp16"
-    counters_valid = counters_valid and HEADLINE_VARIANT == 0 and HEADLINE_ENGINE == "tcgen05"
+    counters_valid = counters_valid and HEADLINE_VARIANT == 0 and HEADLINE_ENGINE == NCU_CAPTURE["engine"]
     tex_launch_s = tex_ms * 1e-3
     mlp_flops = 2 * sum(a * b for a, b in zip(w.dims[:-1], w.dims[1:]))  # 3,456 per query for 13-32-32-9
 
@@ -765,7 +764,7 @@ def main():
         if not args.no_cpu_baseline and world == 1:
             mats["bf16"] = workloads.upload(w, "bf16")
             mats["bf16"].set_decode_variant(HEADLINE_VARIANT)
-            mats["bf16"].set_mlp_engine(HEADLINE_ENGINE)
+            mats["bf16"].set_mlp_engine(HEADLINE_ENGINE)  # the 16-bit path's engine
             cpu, acc = _cpu_baseline(w, HEADLINE_PRECISION,
                                      {p: gathered(p) for p in ("fp16", "bf16", "fp8", "fp32")})
         line = {
@@ -776,10 +775,12 @@ def main():
                                    "3840x2160 perspective-plane queries, MLP 13-32-32-9",
                        "queries_per_step": w.n, "precision": HEADLINE_PRECISION, "out": "fp16 [N][9]",
                        "decode_variant": "0: the library's BC6H decoder (16-byte block loads, mode-sorted blocks "
-                                         "decoded into a shared-memory texel arena per 256-query tile), exact "
+                                         "decoded into a shared-memory texel arena per 512-query tile), exact "
                                          "FP32 trilinear filter",
-                       "mlp_engine": "tcgen05: 128-row MMAs from shared-memory tiles, FP32 accumulators in "
-                                     "tensor memory",
+                       "mlp_engine": {"mma_sync": "mma.sync per warp (m16n8k16, register-chained layers, FP32 "
+                                                  "accumulators in registers)",
+                                      "tcgen05": "tcgen05: 128-row MMAs from shared-memory tiles, FP32 accumulators "
+                                                 "in tensor memory"}[HEADLINE_ENGINE],
                        "l2": "256 MB buffer written between timed steps",
                        "parallelism": f"replicas x{world}"},
             "fp32_plain": {"value": w.n / (fp32_ms * 1e-3) / 1e9, "unit": "Gsamples/s", "ms_per_step": fp32_ms,
@@ -787,7 +788,10 @@ def main():
                            "fp32_simt": {"achieved_tflops": mlp_flops * w.n / (fp32_ms * 1e-3) / 1e12,
                                          "peak_tflops": fp32_simt_peak, "peak_kind": "derived: 148 SMs x 128 "
                                          "lanes x 2 flop x max SM clock"}},
-            "fp8": {"value": w.n / (fp8_ms * 1e-3) / 1e9, "unit": "Gsamples/s", "ms_per_step": fp8_ms},
+            "fp8": {"value": w.n / (fp8_ms * 1e-3) / 1e9, "unit": "Gsamples/s", "ms_per_step": fp8_ms,
+                    "mlp_engine": FP8_ENGINE,
+                    "other_mlp_engine": {"engine": OTHER_ENGINE[FP8_ENGINE], "ms_per_step": fp8_other_ms,
+                                         "value": w.n / (fp8_other_ms * 1e-3) / 1e9, "unit": "Gsamples/s"}},
             "fp32_texunit_texels": {"value": w.n / (fp32t_ms * 1e-3) / 1e9, "unit": "Gsamples/s",
                                     "ms_per_step": fp32t_ms, "out": "fp32 [N][9]",
                                     "kernel": "k_decode_fp32 on decode variant 3 (texture-unit texels, exact filter, "
@@ -797,14 +801,23 @@ def main():
             "batched": {"value": set_n / (set_ms * 1e-3) / 1e9, "unit": "Gsamples/s", "ms_per_step": set_ms,
                         "queries": set_n, "materials": 64, "precision": "fp16",
                         "launch": "one persistent launch replayed from a CUDA graph",
-                        "decode_variant": TEXUNIT_VARIANT,
-                        "autotuned": {"ctas_per_sm": tex_cfg[1], "tiles_per_grab": tex_cfg[2]},
-                        "software_decode": {"value": set_n / (sw_set_ms * 1e-3) / 1e9, "unit": "Gsamples/s",
-                                            "ms_per_step": sw_set_ms,
-                                            "autotuned": {"arena_blocks": set_cfg[0], "ctas_per_sm": set_cfg[1],
-                                                          "tiles_per_grab": set_cfg[2]}},
+                        "decode_variant": HEADLINE_VARIANT, "mlp_engine": HEADLINE_ENGINE,
+                        "kernel": "the single-geometry tile kernel over the set's work list (512-query tiles "
+                                  "never straddling materials, grabbed from a device counter; a material's "
+                                  "description and weights reloaded on change)",
+                        "autotuned": {"ctas_per_sm": set_cfg[1], "tiles_per_grab": set_cfg[2]},
+                        "identical_to_sequential": set_same,
                         "sequential_64_launches": {"value": set_n / (seq_ms * 1e-3) / 1e9, "unit": "Gsamples/s",
-                                                   "ms_per_step": seq_ms}},
+                                                   "ms_per_step": seq_ms},
+                        "speedup_vs_sequential": seq_ms / set_ms,
+                        "texture_unit_texels": {"value": set_n / (tset_ms * 1e-3) / 1e9, "unit": "Gsamples/s",
+                                                "ms_per_step": tset_ms, "decode_variant": TEXUNIT_VARIANT,
+                                                "autotuned": {"ctas_per_sm": tex_cfg[1],
+                                                              "tiles_per_grab": tex_cfg[2]},
+                                                "identical_to_sequential": tset_same,
+                                                "sequential_64_launches": {
+                                                    "value": set_n / (tseq_ms * 1e-3) / 1e9, "unit": "Gsamples/s",
+                                                    "ms_per_step": tseq_ms}}},
             "paper_bcf1k_2160p": {"value": paper_n / (paper_ms * 1e-3) / 1e9, "unit": "Gsamples/s",
                                   "ms_per_step": paper_ms, "queries": paper_n,
                                   "workload": "BC6H 1024/512/256/128 with 9/8/7/6 levels, MLP 12-16-9, FP16, "
@@ -830,17 +843,21 @@ def main():
                                                 "workload": "torch index_add_ of 2^24 random updates into "
                                                             "9.79 M floats"},
                       "adam_algorithmic_bytes_per_step": 313_000_000},
-            "warp_mma_engine": {"value": w.n / (warp_mma_ms * 1e-3) / 1e9, "unit": "Gsamples/s",
-                                "ms_per_step": warp_mma_ms, "precision": HEADLINE_PRECISION,
-                                "kernel": "the headline decode with the MLP per warp on mma.sync"},
+            "other_mlp_engine": {"engine": OTHER_ENGINE[HEADLINE_ENGINE],
+                                 "value": w.n / (other_engine_ms * 1e-3) / 1e9, "unit": "Gsamples/s",
+                                 "ms_per_step": other_engine_ms, "precision": HEADLINE_PRECISION,
+                                 "kernel": "the headline decode with the MLP on the other tensor-core engine "
+                                           "(tcgen05: 128-row MMAs per 128-query part of the tile, FP32 "
+                                           "accumulators in tensor memory; mma.sync: per warp, register-chained)"},
             "texture_unit_texels": {
                 "value": w.n / (tex_ms * 1e-3) / 1e9, "unit": "Gsamples/s", "ms_per_step": tex_ms,
                 "precision": HEADLINE_PRECISION,
                 "kernel": "decode variant 3: every footprint texel fetched through the texture unit's BC6H decoder "
                           "(point sampling, bit-exact), the same exact filter, warp-level MMA MLP (the paper's "
                           "render-time design for the unpack)",
+                "identical_to_headline": tex_identical,
                 "tcgen05_engine": {"value": w.n / (tex_tc_ms * 1e-3) / 1e9, "unit": "Gsamples/s",
-                                   "ms_per_step": tex_tc_ms, "identical_to_headline": tex_identical},
+                                   "ms_per_step": tex_tc_ms},
                 "roofline": {"bound": "hbm", "achieved": alg_bytes / tex_launch_s / 1e9, "peak": hbm_peak,
                              "unit": "GB/s", "frac": alg_bytes / tex_launch_s / 1e9 / hbm_peak,
                              "peak_kind": peak_kind},
@@ -875,7 +892,7 @@ def main():
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                          "frac": achieved / hbm_peak,
                          "traffic": NCU_CAPTURE["dram_bytes"] if counters_valid else None, "peak_kind": peak_kind,
-                         "kernel": f"k_decode_geo<{HEADLINE_PRECISION}, 16-32-32-16, tcgen05 MLP>",
+                         "kernel": f"k_decode_geo<{HEADLINE_PRECISION}, 16-32-32-16, {HEADLINE_ENGINE} MLP>",
                          "algorithmic_bytes_per_launch": alg_bytes,
                          "co_bound": {"bound": "issue", "unit": "G warp-instructions/s",
                                       "achieved": (NCU_CAPTURE["warp_inst"] / head_launch_s / 1e9

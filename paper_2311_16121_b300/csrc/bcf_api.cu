@@ -555,6 +555,7 @@ struct bcf_material_set_s {
     bcf::SetConfig cfg;
     bcf::TexUnitObjs *tex_table; // device table of the materials' texture objects (texture-unit sets)
     int texunit;             // 1: every material was on decode variant 3 at creation
+    bool single_geometry;    // every material's textures share one resolution and level count
     unsigned *check;         // the device's check word (BCF_CHECK_OFFSETS)
 };
 
@@ -592,8 +593,13 @@ bcf_status bcf_create_material_set(const bcf_material *mats, int32_t n, bcf_mate
     set->texunit = set_tex_supported(mats[0]->host);
     for (int m = 0; m < n; ++m)
         set->texunit = set->texunit && mats[m]->hw_ready && mats[m]->variant == 3;
+    set->single_geometry = true;
+    for (int m = 0; m < n; ++m)
+        set->single_geometry = set->single_geometry && mats[m]->host.n_groups == 1;
     if (set->texunit)
         set->cfg = {320, 6, 8}; // the autotuner's pick on the 64-material benchmark workload
+    else if (set->single_geometry)
+        set->cfg = {512, 2, 2}; // the single-geometry kernel: two resident CTAs of 512 queries per SM
     MaterialDev *host = new (std::nothrow) MaterialDev[n];
     if (!host) {
         delete set;
@@ -669,7 +675,7 @@ bcf_status bcf_decode_material_set(bcf_material_set set, const int64_t *d_offset
                            "bcf_decode_material_set launch");
     return cuda_status(launch_decode_set(set->first, set->table, set->n, d_offsets, d_u, d_v, d_s, n_queries, d_out,
                                          out_precision == BCF_FP16, set->counter, set->check, set->cfg,
-                                         (cudaStream_t)stream),
+                                         set->single_geometry, (cudaStream_t)stream),
                        "bcf_decode_material_set launch");
 }
 
@@ -705,7 +711,7 @@ bcf_status bcf_autotune_material_set(bcf_material_set set, const int64_t *d_offs
         // the software set kernel: arena size x CTAs per SM x tiles per grab; the texture-unit set kernel
         // (128-query tiles): CTAs per SM x tiles per grab
         const int caps[2] = {256, 320}, ctas_sw[3] = {1, 2, 3}, ctas_tex[3] = {4, 6, 8}, chunks[4] = {1, 2, 4, 8};
-        const int ncap = set->texunit ? 1 : 2;
+        const int ncap = set->texunit || set->single_geometry ? 1 : 2; // the single-geometry kernel's arena is fixed
         for (int ic = 0; e == cudaSuccess && ic < ncap; ++ic)
             for (int ir = 0; e == cudaSuccess && ir < 3; ++ir)
                 for (int ik = 0; e == cudaSuccess && ik < 4; ++ik) {
@@ -720,7 +726,7 @@ bcf_status bcf_autotune_material_set(bcf_material_set set, const int64_t *d_offs
                                                             set->counter, set->check, cfg, cs)
                                     : launch_decode_set(set->first, set->table, set->n, d_offsets, d_u, d_v, d_s,
                                                         n_queries, d_out, out_precision == BCF_FP16, set->counter,
-                                                        set->check, cfg, cs);
+                                                        set->check, cfg, set->single_geometry, cs);
                         if (e == cudaSuccess)
                             e = cudaEventRecord(b, cs);
                         if (e == cudaSuccess)

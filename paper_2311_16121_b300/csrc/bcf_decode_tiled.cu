@@ -913,20 +913,30 @@ __device__ __forceinline__ void decode_arena_blocks(const uint4 *sraw, const uin
 }
 
 
-template <int PREC, int CAP, int K0, int N1, int N2, int NO, bool TC, int TQ>
-__global__ void __launch_bounds__(TQ, kGeoMinBlocks * 256 / TQ) k_decode_geo(MaterialDev M, const float *__restrict__ qu,
+// With SET, the kernel decodes a material set: M0 is material 0 (the set's MLP shape and shared-memory layout),
+// the materials' descriptions are the device table mats, material m's queries are [offsets[m], offsets[m+1]) of
+// the concatenated arrays (clipped to [0, n]; a decreasing pair sets BCF_CHECK_OFFSETS and decodes as empty).
+// Tiles are numbered material by material (a tile never straddles two materials); persistent CTAs take `chunk`
+// consecutive tiles at a time from the work counter (zeroed before the launch) and reload the material's
+// description and MLP weights into shared memory when a tile belongs to a new material.  Without SET, M0 is the
+// material and tiles go round-robin to the CTAs, each tile's queries loaded one tile ahead.
+template <int PREC, int CAP, int K0, int N1, int N2, int NO, bool TC, int TQ, bool SET>
+__global__ void __launch_bounds__(TQ, kGeoMinBlocks * 256 / TQ) k_decode_geo(MaterialDev M0, const float *__restrict__ qu,
                                                           const float *__restrict__ qv, const float *__restrict__ qs,
                                                           int64_t n, void *__restrict__ out, int out_fp16,
-                                                          unsigned *__restrict__ check)
+                                                          unsigned *__restrict__ check,
+                                                          const MaterialDev *__restrict__ mats, int nmat,
+                                                          const int64_t *__restrict__ offsets,
+                                                          int *__restrict__ counter, int chunk)
 {
     static_assert(CAP <= TQ && CAP <= (1 << kGeoTagBits), "one block item per thread while loading; item tags");
     constexpr int NW = TQ / 32;
     extern __shared__ __align__(16) unsigned char smem[];
-    const MlpDev &P = M.mlp;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int Cn = P.dims[P.n_layers];
-    const int row_stride = tile_stride_bytes<PREC>(P.kpad[0]);
-    const float inv0 = PREC == BCF_FP8_E4M3 ? P.inv_act_scale[0] : 1.0f;
+    // the MLP shape (and so the layout) is material 0's; every material of a set shares it
+    const int Cn = M0.mlp.dims[M0.mlp.n_layers];
+    const int row_stride = tile_stride_bytes<PREC>(M0.mlp.kpad[0]);
+    int smem_used = 0;
     unsigned char *sw;
     float *sb;
     GeoMeta *meta;
@@ -938,7 +948,8 @@ __global__ void __launch_bounds__(TQ, kGeoMinBlocks * 256 / TQ) k_decode_geo(Mat
     uint64_t *bar = nullptr;
     uint32_t *tslot = nullptr;
     if constexpr (TC) {
-        const GeoTcLayout LY = geo_tc_layout<PREC, K0, N1, N2, NO, TQ>(P, CAP);
+        const GeoTcLayout LY = geo_tc_layout<PREC, K0, N1, N2, NO, TQ>(M0.mlp, CAP);
+        smem_used = LY.total;
         sw = smem;
         sb = (float *)(smem + LY.b_bytes);
         meta = (GeoMeta *)(smem + LY.meta);
@@ -950,7 +961,8 @@ __global__ void __launch_bounds__(TQ, kGeoMinBlocks * 256 / TQ) k_decode_geo(Mat
         bar = (uint64_t *)(smem + LY.bar);
         tslot = (uint32_t *)(smem + LY.tslot);
     } else {
-        const GeoLayout LY = geo_layout<PREC, TQ>(P, CAP);
+        const GeoLayout LY = geo_layout<PREC, TQ>(M0.mlp, CAP);
+        smem_used = LY.total;
         sw = smem;
         sb = (float *)(smem + LY.b_bytes);
         meta = (GeoMeta *)(smem + LY.meta);
@@ -963,34 +975,49 @@ __global__ void __launch_bounds__(TQ, kGeoMinBlocks * 256 / TQ) k_decode_geo(Mat
         if (!(16 * Cn * 4 <= 16 * row_stride))
             ost = (float *)(act0 + ((32 * row_stride + 15) & ~15));
     }
-    RowWriter<PREC> rw{act0 + lane * row_stride, inv0, 0.0f};
-    TcRowWriter<PREC, NW, (K0 > 0 ? K0 : 16), (N1 > 0 ? N1 : 16), (N2 > 0 ? N2 : 16), (NO > 0 ? NO : 16)> tw{
-        xtile, (int)threadIdx.x, inv0, 0.0f};
-    const auto put = [&](int col, float x) {
-        if constexpr (TC)
-            tw.put(col, x);
-        else
-            rw.put(col, x);
-    };
-    const int nt = M.n_tex;
-    const int wrap = M.wrap;
-    const bool sgn = M.is_signed != 0;
-    const TexDev &T0 = M.tex[0];
+    // material sets: the current material's description, the tile table and the work grab, after the layout
+    MaterialDev *Ms = nullptr;
+    int64_t *tile_first = nullptr;
+    int *grab = nullptr;
+    if constexpr (SET) {
+        unsigned char *x = smem + ((smem_used + 15) & ~15);
+        Ms = (MaterialDev *)x;
+        x += (sizeof(MaterialDev) + 15) & ~(size_t)15;
+        tile_first = (int64_t *)x;
+        x += 8 * (BCF_MAX_SET + 1);
+        grab = (int *)x;
+    }
+    const MaterialDev &M = SET ? *Ms : M0; // the current material
+    const MlpDev &P = M.mlp;
     const unsigned lanes_lt = (1u << lane) - 1u;
 
     uint32_t tmem = 0, phase = 0;
     constexpr int kTcCols = TcMlp<PREC, NW, (K0 > 0 ? K0 : 16), (N1 > 0 ? N1 : 16), (N2 > 0 ? N2 : 16),
                                   (NO > 0 ? NO : 16)>::NCOLS;
     if constexpr (TC) {
-        tc_load_weights<PREC, NW, K0, N1, N2, NO>(P, sw, sb);
+        if constexpr (!SET)
+            tc_load_weights<PREC, NW, K0, N1, N2, NO>(P, sw, sb);
         if (threadIdx.x == 0) {
             mbar_init(bar, 1);
             mbar_init_fence();
         }
         if (warp == 0)
             tc_alloc(tslot, kTcCols);
-    } else {
+    } else if constexpr (!SET) {
         load_mlp_smem<PREC>(P, sw, sb);
+    }
+    if constexpr (SET) {
+        if (threadIdx.x == 0) {
+            int64_t acc = 0;
+            for (int m = 0; m < nmat; ++m) {
+                tile_first[m] = acc;
+                const int64_t a = min(max(offsets[m], (int64_t)0), n), b = min(max(offsets[m + 1], (int64_t)0), n);
+                acc += b > a ? (b - a + TQ - 1) / TQ : 0;
+                if (blockIdx.x == 0 && offsets[m + 1] < offsets[m] && check)
+                    atomicOr(check, BCF_CHECK_OFFSETS);
+            }
+            tile_first[nmat] = acc;
+        }
     }
     reset_geo_meta(meta[0]);
     reset_geo_meta(meta[1]);
@@ -1000,9 +1027,9 @@ __global__ void __launch_bounds__(TQ, kGeoMinBlocks * 256 / TQ) k_decode_geo(Mat
         tmem = *tslot;
     }
 
-    const int64_t tiles = (n + TQ - 1) / TQ;
+    const int64_t tiles = SET ? 0 : (n + TQ - 1) / TQ;
     float nu = 0.0f, nv = 0.0f, ns = 0.0f, nu_ref = 0.0f, nv_ref = 0.0f;
-    {
+    if constexpr (!SET) {
         const int64_t q = (int64_t)blockIdx.x * TQ + threadIdx.x;
         if (blockIdx.x < tiles && q < n) {
             nu = qu[q];
@@ -1015,17 +1042,25 @@ __global__ void __launch_bounds__(TQ, kGeoMinBlocks * 256 / TQ) k_decode_geo(Mat
         }
     }
     int parity = 0;
-    for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x, parity ^= 1) {
-        GeoMeta &G = meta[parity];
-        const int64_t q_first = tile * TQ;
-        const int64_t q = q_first + threadIdx.x;
-        const bool active = q < n;
-        const float u = active ? sanitize(nu, wrap) : 0.0f;
-        const float v = active ? sanitize(nv, wrap) : 0.0f;
-        const float s = active ? ns : 0.0f;
-        // the tile's first query: the reference of the relative block coordinates
-        const float u_ref = sanitize(nu_ref, wrap), v_ref = sanitize(nv_ref, wrap);
-        {
+    int64_t tile = blockIdx.x; // without SET: this CTA's next tile
+    int64_t gbase = 0;         // SET: the current grab's first tile, and how many of its tiles are taken
+    int gtaken = chunk;
+    int cur = -1;              // SET: the material whose description and weights are in shared memory
+    for (;; parity ^= 1) {
+        int64_t q_first, q_end; // this tile's queries: [q_first, min(q_first + TQ, q_end))
+        float u, v, s, u_ref, v_ref;
+        if constexpr (!SET) {
+            if (tile >= tiles)
+                break;
+            q_first = tile * TQ;
+            q_end = n;
+            const bool act = q_first + threadIdx.x < n;
+            u = act ? sanitize(nu, M.wrap) : 0.0f;
+            v = act ? sanitize(nv, M.wrap) : 0.0f;
+            s = act ? ns : 0.0f;
+            // the tile's first query: the reference of the relative block coordinates
+            u_ref = sanitize(nu_ref, M.wrap);
+            v_ref = sanitize(nv_ref, M.wrap);
             const int64_t qn = (tile + gridDim.x) * TQ + threadIdx.x;
             if (tile + gridDim.x < tiles && qn < n) {
                 nu = qu[qn];
@@ -1036,7 +1071,70 @@ __global__ void __launch_bounds__(TQ, kGeoMinBlocks * 256 / TQ) k_decode_geo(Mat
                 nu_ref = qu[(tile + gridDim.x) * TQ];
                 nv_ref = qv[(tile + gridDim.x) * TQ];
             }
+            tile += gridDim.x;
+        } else {
+            if (gtaken == chunk) {
+                if (threadIdx.x == 0)
+                    *grab = atomicAdd(counter, chunk);
+                __syncthreads();
+                gbase = *grab;
+                gtaken = 0;
+                __syncthreads(); // everyone has read the grab before thread 0 may overwrite it
+            }
+            const int64_t t = gbase + gtaken;
+            if (t >= tile_first[nmat])
+                break; // uniform
+            if (++gtaken == chunk || t + 1 >= tile_first[nmat])
+                gtaken = chunk;
+            int lo = 0, hi = nmat - 1; // the last material m with tile_first[m] <= t
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (tile_first[mid] <= t)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            const int m = lo;
+            if (m != cur) {
+                __syncthreads(); // the previous tile's filter and MLP are done with the description and weights
+                const int words = (int)(sizeof(MaterialDev) / 4);
+                for (int i = threadIdx.x; i < words; i += TQ)
+                    reinterpret_cast<int *>(Ms)[i] = reinterpret_cast<const int *>(mats + m)[i];
+                __syncthreads();
+                if constexpr (TC)
+                    tc_load_weights<PREC, NW, K0, N1, N2, NO>(P, sw, sb);
+                else
+                    load_mlp_smem<PREC>(P, sw, sb);
+                cur = m; // (the weights are read after the tile's first barrier)
+            }
+            const int64_t a = min(max(offsets[m], (int64_t)0), n);
+            q_end = min(max(offsets[m + 1], (int64_t)0), n);
+            q_first = a + (t - tile_first[m]) * TQ;
+            const int64_t q = q_first + threadIdx.x;
+            const bool act = q < q_end;
+            u = act ? sanitize(qu[q], M.wrap) : 0.0f;
+            v = act ? sanitize(qv[q], M.wrap) : 0.0f;
+            s = act ? (qs ? qs[q] : 0.0f) : 0.0f;
+            u_ref = sanitize(qu[q_first], M.wrap);
+            v_ref = sanitize(qv[q_first], M.wrap);
         }
+        const float inv0 = PREC == BCF_FP8_E4M3 ? P.inv_act_scale[0] : 1.0f;
+        RowWriter<PREC> rw{act0 + lane * row_stride, inv0, 0.0f};
+        TcRowWriter<PREC, NW, (K0 > 0 ? K0 : 16), (N1 > 0 ? N1 : 16), (N2 > 0 ? N2 : 16), (NO > 0 ? NO : 16)> tw{
+            xtile, (int)threadIdx.x, inv0, 0.0f};
+        const auto put = [&](int col, float x) {
+            if constexpr (TC)
+                tw.put(col, x);
+            else
+                rw.put(col, x);
+        };
+        const int nt = M.n_tex;
+        const int wrap = M.wrap;
+        const bool sgn = M.is_signed != 0;
+        const TexDev &T0 = M.tex[0];
+        GeoMeta &G = meta[parity];
+        const int64_t q = q_first + threadIdx.x;
+        const bool active = q < q_end;
         // ---- 1. footprint geometry per side, block boxes per level
         const Lod L = lod_of(T0, s);
         int i0s[2], j0s[2];
@@ -1273,8 +1371,14 @@ __global__ void __launch_bounds__(TQ, kGeoMinBlocks * 256 / TQ) k_decode_geo(Mat
                 break; // uniform: stop taking tiles
             }
             const int64_t q0 = q_first + warp * 32;
-            if (q0 < n)
-                store_warp_rows(ost + warp * 32 * Cn, out, q0, (int)min((int64_t)32, n - q0), Cn, out_fp16, lane);
+            if (q0 < q_end) {
+                if constexpr (SET) // a set's tiles start at any query: outputs aligned or not
+                    store_rows_any(ost + warp * 32 * Cn, out, q0, (int)min((int64_t)32, q_end - q0), Cn, out_fp16,
+                                   lane);
+                else
+                    store_warp_rows(ost + warp * 32 * Cn, out, q0, (int)min((int64_t)32, q_end - q0), Cn, out_fp16,
+                                    lane);
+            }
         } else {
             __syncwarp();
             if constexpr (N2 == 0)
@@ -1284,8 +1388,12 @@ __global__ void __launch_bounds__(TQ, kGeoMinBlocks * 256 / TQ) k_decode_geo(Mat
                                                 tile_stride_bytes<BCF_FP8_E4M3>(N1 > N2 ? N1 : N2), ost, Cn);
             __syncwarp();
             const int64_t q0 = q_first + warp * 32;
-            if (q0 < n)
-                store_warp_rows(ost, out, q0, (int)min((int64_t)32, n - q0), Cn, out_fp16, lane);
+            if (q0 < q_end) {
+                if constexpr (SET) // a set's tiles start at any query: outputs aligned or not
+                    store_rows_any(ost, out, q0, (int)min((int64_t)32, q_end - q0), Cn, out_fp16, lane);
+                else
+                    store_warp_rows(ost, out, q0, (int)min((int64_t)32, q_end - q0), Cn, out_fp16, lane);
+            }
             __syncwarp();
         }
     }
@@ -1351,7 +1459,7 @@ static cudaError_t launch_geo_engine(const MaterialDev &M, const float *u, const
     }
     if (smem > 227 * 1024)
         return cudaErrorInvalidConfiguration;
-    auto kern = k_decode_geo<PREC, CAP, K0, N1, N2, NO, TC, TQ>;
+    auto kern = k_decode_geo<PREC, CAP, K0, N1, N2, NO, TC, TQ, false>;
     static int configured = 0;
     if (!configured) {
         cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
@@ -1374,8 +1482,106 @@ static cudaError_t launch_geo_engine(const MaterialDev &M, const float *u, const
     }
     const int64_t tiles = (n + TQ - 1) / TQ;
     const int64_t grid = min(tiles, (int64_t)tiled_sms() * per_sm);
-    kern<<<(unsigned)grid, TQ, (size_t)smem, st>>>(M, u, v, s, n, out, out_fp16, check_word());
+    kern<<<(unsigned)grid, TQ, (size_t)smem, st>>>(M, u, v, s, n, out, out_fp16, check_word(), nullptr, 0, nullptr,
+                                                   nullptr, 1);
     return cudaGetLastError();
+}
+
+// Shared memory of the material-set instance: the single-material layout, then the current material's
+// description, the tile table and the work grab.
+constexpr int64_t geo_set_extra_bytes()
+{
+    return 16 + (((int64_t)sizeof(MaterialDev) + 15) & ~15) + 8 * (BCF_MAX_SET + 1) + 16;
+}
+
+// Material sets whose materials are single-geometry (every texture of a material at one resolution and level
+// count) take the single-geometry kernel with SET: persistent CTAs (cfg.ctas_per_sm per SM, capped by residency)
+// grabbing cfg.chunk tiles at a time.
+template <int PREC, int K0, int N1, int N2, int NO, bool TC>
+static cudaError_t launch_geo_set_engine(const MaterialDev &M0, const MaterialDev *mats, int nmat,
+                                         const int64_t *offsets, const float *u, const float *v, const float *s,
+                                         int64_t n, void *out, int out_fp16, int *counter, unsigned *check,
+                                         const SetConfig &cfg, cudaStream_t st)
+{
+    constexpr int TQ = geo_tq<PREC, N1>(), CAP = geo_cap(TQ);
+    int64_t smem;
+    int max_per_sm = 32;
+    if constexpr (TC) {
+        smem = geo_tc_layout<PREC, K0, N1, N2, NO, TQ>(M0.mlp, CAP).total;
+        max_per_sm = 512 / TcMlp<PREC, TQ / 32, K0, N1, N2, NO>::NCOLS;
+    } else {
+        smem = geo_layout<PREC, TQ>(M0.mlp, CAP).total;
+    }
+    smem += geo_set_extra_bytes();
+    if (smem > 227 * 1024)
+        return cudaErrorInvalidConfiguration;
+    auto kern = k_decode_geo<PREC, CAP, K0, N1, N2, NO, TC, TQ, true>;
+    static int configured = 0;
+    if (!configured) {
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+        configured = 1;
+    }
+    static int per_sm = 0;
+    if (!per_sm) {
+        cudaFuncAttributes fa{};
+        int regs = 64;
+        if (cudaFuncGetAttributes(&fa, kern) == cudaSuccess && fa.numRegs > 0)
+            regs = fa.numRegs;
+        int dev = 0, smem_sm = 228 * 1024;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        const int by_regs = 65536 / (TQ * ((regs + 7) & ~7));
+        const int by_smem = smem_sm / (int)(smem + 1024);
+        per_sm = max(1, min(min(by_regs, by_smem), max_per_sm));
+    }
+    const int ctas = max(1, min(per_sm, cfg.ctas_per_sm));
+    cudaError_t e = cudaMemsetAsync(counter, 0, sizeof(int), st);
+    if (e != cudaSuccess)
+        return e;
+    kern<<<(unsigned)(tiled_sms() * ctas), TQ, (size_t)smem, st>>>(M0, u, v, s, n, out, out_fp16, check, mats, nmat,
+                                                                    offsets, counter, max(cfg.chunk, 1));
+    return cudaGetLastError();
+}
+
+template <int PREC, int K0, int N1, int N2, int NO>
+static cudaError_t launch_geo_set_shape(const MaterialDev &M0, const MaterialDev *mats, int nmat,
+                                        const int64_t *offsets, const float *u, const float *v, const float *s,
+                                        int64_t n, void *out, int out_fp16, int *counter, unsigned *check,
+                                        const SetConfig &cfg, cudaStream_t st)
+{
+    if constexpr (N2 != 0)
+        if (M0.mlp_engine == 1)
+            return launch_geo_set_engine<PREC, K0, N1, N2, NO, true>(M0, mats, nmat, offsets, u, v, s, n, out,
+                                                                      out_fp16, counter, check, cfg, st);
+    return launch_geo_set_engine<PREC, K0, N1, N2, NO, false>(M0, mats, nmat, offsets, u, v, s, n, out, out_fp16,
+                                                               counter, check, cfg, st);
+}
+
+// 1 when the set's MLP shape has a single-geometry instance (the shapes launch_tiled_prec dispatches to it)
+template <int PREC>
+static cudaError_t launch_geo_set_prec(const MaterialDev &M0, const MaterialDev *mats, int nmat,
+                                       const int64_t *offsets, const float *u, const float *v, const float *s,
+                                       int64_t n, void *out, int out_fp16, int *counter, unsigned *check,
+                                       const SetConfig &cfg, cudaStream_t st, bool &done)
+{
+    done = true;
+    const MlpDev &P = M0.mlp;
+    if (P.n_layers == 3) {
+        const int k0 = P.kpad[0], n1 = P.npad[0], n2 = P.npad[1], no = P.npad[2];
+        constexpr int kq = PREC == BCF_FP8_E4M3 ? 32 : 16;
+        if (k0 == kq && n1 == 32 && n2 == 32 && no == 16)
+            return launch_geo_set_shape<PREC, kq, 32, 32, 16>(M0, mats, nmat, offsets, u, v, s, n, out, out_fp16,
+                                                               counter, check, cfg, st);
+        if (k0 == 32 && n1 == 64 && n2 == 64 && no == 16)
+            return launch_geo_set_shape<PREC, 32, 64, 64, 16>(M0, mats, nmat, offsets, u, v, s, n, out, out_fp16,
+                                                               counter, check, cfg, st);
+    }
+    if constexpr (PREC != BCF_FP8_E4M3)
+        if (P.n_layers == 2 && P.kpad[0] == 16 && P.npad[0] == 16 && P.npad[1] == 16)
+            return launch_geo_set_shape<PREC, 16, 16, 0, 16>(M0, mats, nmat, offsets, u, v, s, n, out, out_fp16,
+                                                              counter, check, cfg, st);
+    done = false;
+    return cudaSuccess;
 }
 
 template <int PREC, int K0, int N1, int N2, int NO>
@@ -1500,8 +1706,30 @@ static cudaError_t launch_set_prec(const MaterialDev &M0, const MaterialDev *mat
 
 cudaError_t launch_decode_set(const MaterialDev &M0, const MaterialDev *mats, int nmat, const int64_t *offsets,
                               const float *u, const float *v, const float *s, int64_t n, void *out, int out_fp16,
-                              int *counter, unsigned *check, const SetConfig &cfg, cudaStream_t st)
+                              int *counter, unsigned *check, const SetConfig &cfg, bool single_geometry,
+                              cudaStream_t st)
 {
+    if (single_geometry) {
+        bool done = false;
+        cudaError_t e = cudaSuccess;
+        switch (M0.mlp.precision) {
+        case BCF_FP16:
+            e = launch_geo_set_prec<BCF_FP16>(M0, mats, nmat, offsets, u, v, s, n, out, out_fp16, counter, check, cfg,
+                                              st, done);
+            break;
+        case BCF_BF16:
+            e = launch_geo_set_prec<BCF_BF16>(M0, mats, nmat, offsets, u, v, s, n, out, out_fp16, counter, check, cfg,
+                                              st, done);
+            break;
+        case BCF_FP8_E4M3:
+            e = launch_geo_set_prec<BCF_FP8_E4M3>(M0, mats, nmat, offsets, u, v, s, n, out, out_fp16, counter, check,
+                                                  cfg, st, done);
+            break;
+        default: break;
+        }
+        if (done)
+            return e;
+    }
     switch (M0.mlp.precision) {
     case BCF_FP16:
         return launch_set_prec<BCF_FP16>(M0, mats, nmat, offsets, u, v, s, n, out, out_fp16, counter, check, cfg, st);

@@ -45,7 +45,8 @@ cudaError_t launch_decode_set_tex(const MaterialDev &M0, const MaterialDev *mats
                                   cudaStream_t st);
 cudaError_t launch_decode_set(const MaterialDev &M0, const MaterialDev *mats, int nmat, const int64_t *offsets,
                               const float *u, const float *v, const float *s, int64_t n, void *out, int out_fp16,
-                              int *counter, unsigned *check, const SetConfig &cfg, cudaStream_t st);
+                              int *counter, unsigned *check, const SetConfig &cfg, bool single_geometry,
+                              cudaStream_t st);
 cudaError_t texunit_decode(const void *d_blocks, int bw, int bh, int is_signed, uint16_t *d_out, cudaStream_t st);
 
 // thread-local error text

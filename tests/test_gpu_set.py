@@ -30,15 +30,17 @@ def _set_inputs(sw):
     return off, u, v, s
 
 
-@pytest.mark.parametrize("variant", [0, 3])
+@pytest.mark.parametrize("variant,engine", [(0, "mma_sync"), (0, "tcgen05"), (3, "mma_sync")])
 @pytest.mark.parametrize("precision", ["fp16", "fp8"])
-def test_set_decode_equals_per_material_decodes(precision, variant):
-    """One launch over the set equals the per-material decodes bit for bit: the tile-cooperative software decode
-    (materials on variant 0) and the texture-unit decode (materials on variant 3)."""
+def test_set_decode_equals_per_material_decodes(precision, variant, engine):
+    """One launch over the set equals the per-material decodes bit for bit: the hand-written single-geometry tile
+    decode (materials on variant 0; tiles of a material start at its first query, any alignment) with either MLP
+    engine, and the texture-unit decode (materials on variant 3)."""
     bcf = _bcf()
     sw, mats = _small_set(precision)
     for m in mats:
         m.set_decode_variant(variant)
+        m.set_mlp_engine(engine)
     S = bcf.MaterialSet(mats)
     off, u, v, s = _set_inputs(sw)
     got = bcf.decode(S, u, v, s, offsets=off).cpu().numpy()
@@ -126,8 +128,8 @@ def full_set():
 @pytest.mark.parametrize("variant", [0, 3])
 def test_full_size_batched_decode_sampled_against_oracle(full_set, variant):
     """The 64-material workload at full size (4 textures of 256^2 .. 4096^2 each, 1e4 .. 4e6 queries per
-    material, FP16) in the benchmark's launch configuration -- variant 0 autotuned, variant 3 replayed from a
-    CUDA graph -- checked on 32 sampled queries per material against the quantisation-aware oracle."""
+    material, FP16) in the benchmark's launch configuration -- one launch replayed from a CUDA graph, autotuned
+    first on variant 0 -- checked on 32 sampled queries per material against the quantisation-aware oracle."""
     bcf = _bcf()
     sw = full_set
     mats = [workloads.upload(m, "fp16") for m in sw.materials]
@@ -139,18 +141,16 @@ def test_full_size_batched_decode_sampled_against_oracle(full_set, variant):
     out = torch.empty((sw.n, 9), dtype=torch.float16, device="cuda")
     if variant == 0:
         S.autotune(off, u, v, s, out)
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
         S.decode(off, u, v, s, out=out)
-    else:
-        side = torch.cuda.Stream()
-        side.wait_stream(torch.cuda.current_stream())
-        with torch.cuda.stream(side):
-            S.decode(off, u, v, s, out=out)
-        torch.cuda.current_stream().wait_stream(side)
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g):
-            S.decode(off, u, v, s, out=out)
-        out.zero_()
-        g.replay()
+    torch.cuda.current_stream().wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        S.decode(off, u, v, s, out=out)
+    out.zero_()
+    g.replay()
     torch.cuda.synchronize()
     rng = np.random.default_rng(29 + variant)
     su, sv, ss = sw.concat()
