@@ -318,6 +318,12 @@ def main():
                     help="time only the training step (for profiler captures); prints a reduced line")
     ap.add_argument("--train-shape", default="config3", choices=["config3", "paper", "grid"],
                     help="with --only-train: the timed workload's decoder (paper = BCf-1K textures, 12-16-9)")
+    ap.add_argument("--only-large", action="store_true",
+                    help="time only the 8 x 4096^2 frame on the hand-written decode, FP16 and FP8 (for profiler "
+                         "captures); prints a reduced line")
+    ap.add_argument("--only-batched", action="store_true",
+                    help="time only the 64-material set, one graph-replayed launch on the hand-written decode (for "
+                         "profiler captures); prints a reduced line")
     ap.add_argument("--only-headline", action="store_true",
                     help="time only the headline decode (for profiler captures); prints a reduced line")
     args = ap.parse_args()
@@ -341,6 +347,58 @@ def main():
     assert args.warmup >= 3, "at least 3 warm-up steps"
 
     stream = torch.cuda.current_stream()
+    if args.only_large or args.only_batched:
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+        def steps(fn, k):
+            for _ in range(args.warmup):
+                fn()
+            torch.cuda.synchronize()
+            tot = 0.0
+            for _ in range(k):
+                flush.zero_()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                b.record(stream)
+                b.synchronize()
+                tot += a.elapsed_time(b)
+            return tot / k
+
+        res = {}
+        if args.only_large:
+            w5 = workloads.config5()
+            u5, v5, s5 = workloads.queries_to_device(w5)
+            out5 = torch.empty((w5.n, 9), dtype=torch.float16, device="cuda")
+            for prec in ("fp16", "fp8"):
+                m5 = workloads.upload(w5, prec)
+                m5.set_decode_variant(HEADLINE_VARIANT)
+                m5.set_mlp_engine(LARGE_ENGINE)
+                res[f"large_{prec}_ms"] = steps(lambda: m5.decode(u5, v5, s5, out=out5), args.steps)
+                del m5
+        else:
+            sw = workloads.config4()
+            set_mats = [workloads.upload(m, "fp16") for m in sw.materials]
+            for m in set_mats:
+                m.set_decode_variant(HEADLINE_VARIANT)
+                m.set_mlp_engine(HEADLINE_ENGINE)
+            su, sv, ss = (torch.from_numpy(a).cuda() for a in sw.concat())
+            soff = torch.from_numpy(sw.offsets).cuda()
+            sout = torch.empty((sw.n, 9), dtype=torch.float16, device="cuda")
+            S = bcf.MaterialSet(set_mats)
+            S.decode(soff, su, sv, ss, out=sout)
+            torch.cuda.synchronize()
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph):
+                S.decode(soff, su, sv, ss, out=sout)
+            res["batched_ms"] = steps(graph.replay, args.steps)
+            res["set_config"] = S.config()
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "unit": "ms", "n_gpus": world, "steps": args.steps,
+                              "warmup": args.warmup, **res, "note": "capture mode: one workload only"}))
+        return
+
     if args.only_train:
         ms, loss, batch = _train_bench(torch, workloads, stream, args.steps, args.train_shape)
         if rank == 0:
