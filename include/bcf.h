@@ -250,8 +250,11 @@ typedef struct bcf_material_set_s *bcf_material_set;
  * K0 <= 32 -> 64 -> 64 -> C <= 16), the set decodes through the texture unit
  * the same way (texture-unit texels, exact FP32 filter) with a persistent
  * kernel over 128-query tiles (bcf_autotune_material_set picks its CTAs per
- * SM and tiles per grab); otherwise it uses the tile-cooperative software
- * decode.
+ * SM and tiles per grab); otherwise it uses the library's own BC6H decode:
+ * for the register-chained shapes, the tile kernel of bcf_decode_material
+ * (tiles of 512 queries, 256 for 16-bit 64-wide MLPs; each material's
+ * textures of one resolution and level count), else the multi-group tile
+ * decode (256-query tiles).
  * Errors: BCF_ERR_INVALID_ARG (n out of [1, BCF_MAX_SET], null
  * materials, materials that do not share the MLP / texture count),
  * BCF_ERR_UNSUPPORTED (FP32 materials: the set path is the tensor-core
@@ -267,7 +270,8 @@ bcf_status bcf_destroy_material_set(bcf_material_set set);
  * d_u / d_v / d_s (and of the rows of d_out [n_queries][C]).  d_offsets:
  * n + 1 non-decreasing int64 on the device (entries are clipped to
  * [0, n_queries]; a decreasing pair sets BCF_CHECK_OFFSETS).  Queries are
- * processed in tiles (256 queries; 128 on the texture-unit path) taken from an
+ * processed in tiles (see bcf_create_material_set; a tile never spans two
+ * materials) taken from an
  * atomic work counter that a memset before the launch resets, so the call
  * can be captured into a CUDA graph and replayed.  Calls on one set must
  * not overlap on the GPU (they share the counter).  Errors as
@@ -279,9 +283,11 @@ bcf_status bcf_decode_material_set(bcf_material_set set, const int64_t *d_offset
 
 /*
  * bcf_autotune_material_set -- time the set-decode launch configurations
- * (software sets: shared-memory block arena 256 / 320 blocks, 1-3 persistent
- * CTAs per SM; texture-unit sets: 4 / 6 / 8 CTAs per SM, capped by
- * occupancy; both: 1 / 2 / 4 / 8 tiles per work-counter grab) on the given
+ * (sets on the tile kernel of bcf_decode_material: 1-3 persistent CTAs per
+ * SM, capped by residency, *cap = 0 since its arena is fixed by its tile;
+ * multi-group software sets: shared-memory block arena 256 / 320 blocks,
+ * 1-3 CTAs per SM; texture-unit sets: 4 / 6 / 8 CTAs per SM, capped by
+ * occupancy; all: 1 / 2 / 4 / 8 tiles per work-counter grab) on the given
  * workload with
  * CUDA events (synchronises the stream; the output is overwritten), keep the
  * fastest for the set, and return it in *cap, *ctas_per_sm, *chunk (any may

@@ -555,9 +555,22 @@ struct bcf_material_set_s {
     bcf::SetConfig cfg;
     bcf::TexUnitObjs *tex_table; // device table of the materials' texture objects (texture-unit sets)
     int texunit;             // 1: every material was on decode variant 3 at creation
-    bool single_geometry;    // every material's textures share one resolution and level count
+    bool single_geometry;    // decoded by the single-material tile kernel: one geometry group per material and an
+                             // MLP shape that kernel has an instance for
     unsigned *check;         // the device's check word (BCF_CHECK_OFFSETS)
 };
+
+// The MLP shapes the single-material tile kernel has instances for (launch_tiled_prec): three layers
+// K0 -> 32 -> 32 -> C or 32 -> 64 -> 64 -> C (K0 padded to 16, or 32 for E4M3; C padded to 16), or two 16-bit
+// layers 16 -> 16 -> C.
+static bool geo_shape(const MlpDev &P)
+{
+    const int kq = P.precision == BCF_FP8_E4M3 ? 32 : 16;
+    if (P.n_layers == 3)
+        return P.npad[2] == 16 && ((P.kpad[0] == kq && P.npad[0] == 32 && P.npad[1] == 32) ||
+                                   (P.kpad[0] == 32 && P.npad[0] == 64 && P.npad[1] == 64));
+    return P.n_layers == 2 && P.precision != BCF_FP8_E4M3 && P.kpad[0] == 16 && P.npad[0] == 16 && P.npad[1] == 16;
+}
 
 extern "C" {
 
@@ -593,13 +606,13 @@ bcf_status bcf_create_material_set(const bcf_material *mats, int32_t n, bcf_mate
     set->texunit = set_tex_supported(mats[0]->host);
     for (int m = 0; m < n; ++m)
         set->texunit = set->texunit && mats[m]->hw_ready && mats[m]->variant == 3;
-    set->single_geometry = true;
+    set->single_geometry = geo_shape(mats[0]->host.mlp);
     for (int m = 0; m < n; ++m)
         set->single_geometry = set->single_geometry && mats[m]->host.n_groups == 1;
     if (set->texunit)
         set->cfg = {320, 6, 8}; // the autotuner's pick on the 64-material benchmark workload
     else if (set->single_geometry)
-        set->cfg = {512, 2, 2}; // the single-geometry kernel: two resident CTAs of 512 queries per SM
+        set->cfg = {0, 2, 2}; // the single-geometry kernel (arena fixed by its tile): two CTAs of 512 queries per SM
     MaterialDev *host = new (std::nothrow) MaterialDev[n];
     if (!host) {
         delete set;
@@ -711,11 +724,12 @@ bcf_status bcf_autotune_material_set(bcf_material_set set, const int64_t *d_offs
         // the software set kernel: arena size x CTAs per SM x tiles per grab; the texture-unit set kernel
         // (128-query tiles): CTAs per SM x tiles per grab
         const int caps[2] = {256, 320}, ctas_sw[3] = {1, 2, 3}, ctas_tex[3] = {4, 6, 8}, chunks[4] = {1, 2, 4, 8};
-        const int ncap = set->texunit || set->single_geometry ? 1 : 2; // the single-geometry kernel's arena is fixed
+        const int ncap = set->texunit || set->single_geometry ? 1 : 2; // the tile kernel's arena is fixed
         for (int ic = 0; e == cudaSuccess && ic < ncap; ++ic)
             for (int ir = 0; e == cudaSuccess && ir < 3; ++ir)
                 for (int ik = 0; e == cudaSuccess && ik < 4; ++ik) {
-                    const SetConfig cfg = {caps[ic], set->texunit ? ctas_tex[ir] : ctas_sw[ir], chunks[ik]};
+                    const SetConfig cfg = {set->single_geometry && !set->texunit ? 0 : caps[ic],
+                                           set->texunit ? ctas_tex[ir] : ctas_sw[ir], chunks[ik]};
                     float ms = 0.0f;
                     for (int rep = 0; e == cudaSuccess && rep < 3; ++rep) { // first run warms up
                         e = cudaEventRecord(a, cs);

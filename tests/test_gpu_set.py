@@ -77,8 +77,8 @@ def test_set_decode_in_a_cuda_graph_and_autotune(variant):
     off, u, v, s = _set_inputs(sw)
     ref = S.decode(off, u, v, s).clone()
     cfg = S.autotune(off, u, v, s, torch.empty_like(ref))
-    if variant == 0:
-        assert cfg[0] in (256, 320) and 1 <= cfg[1] <= 3 and cfg[2] in (1, 2, 4, 8)
+    if variant == 0:  # the tile kernel of the single-material decode: its arena is fixed by the tile (cap 0)
+        assert cfg[0] == 0 and 1 <= cfg[1] <= 3 and cfg[2] in (1, 2, 4, 8)
     else:  # texture-unit set kernel: CTAs per SM and tiles per grab
         assert cfg[1] in (4, 6, 8) and cfg[2] in (1, 2, 4, 8)
     assert S.config() == cfg
