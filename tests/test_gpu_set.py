@@ -169,3 +169,25 @@ def test_full_size_batched_decode_sampled_against_oracle(full_set, variant):
         assert not r["unexplained"], (m, r["unexplained"][:5], r["worst"])
         flips += r["flips"]
     print(f"rows explained as rounding flips: {flips} of {32 * len(sw.materials)}")
+
+
+@pytest.mark.parametrize("engine", ["mma_sync", "tcgen05"])
+def test_set_decode_tiny_and_unaligned_ranges(engine):
+    """Materials with 1, 31, 33 and 513 queries (tiles that end inside a warp, outputs that start at any row
+    alignment, a material spanning two tiles) in one launch equal the per-material decodes bit for bit."""
+    bcf = _bcf()
+    sw, mats = _small_set("fp16", n_materials=4, seed_config=46)
+    for m in mats:
+        m.set_decode_variant(0)
+        m.set_mlp_engine(engine)
+    S = bcf.MaterialSet(mats)
+    _, u, v, s = _set_inputs(sw)
+    sizes = [1, 31, 33, 513]
+    offs = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    assert offs[-1] <= u.numel()
+    n = int(offs[-1])
+    got = S.decode(torch.from_numpy(offs).cuda(), u[:n], v[:n], s[:n]).cpu().numpy()
+    for m in range(len(sizes)):
+        a, b = int(offs[m]), int(offs[m + 1])
+        one = mats[m].decode(u[a:b], v[a:b], s[a:b], out_dtype=torch.float16).cpu().numpy()
+        np.testing.assert_array_equal(got[a:b], one)
