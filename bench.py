@@ -558,10 +558,10 @@ def main():
     del m1, u1, v1, o1
 
     # end to end through the C ABI with host buffers: bcf_decode_material_host uploads the pinned queries,
-    # decodes and downloads the channels chunk by chunk with the three overlapping (64 MB device scratch)
+    # decodes and downloads the channels chunk by chunk with the three overlapping (128 MB device scratch)
     uh, vh, sh = (torch.from_numpy(a).pin_memory() for a in (w.u, w.v, w.s))
     oh = torch.empty((w.n, 9), dtype=torch.float16).pin_memory()
-    scratch = torch.empty(64 << 20, dtype=torch.uint8, device="cuda")
+    scratch = torch.empty(128 << 20, dtype=torch.uint8, device="cuda")
     m = mats[HEADLINE_PRECISION]
     e2e_total = 0.0
     for i in range(3 + k_extra):

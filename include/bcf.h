@@ -206,14 +206,16 @@ bcf_status bcf_decode_material(bcf_material mat, const float *d_u, const float *
  * bcf_decode_material_host -- bcf_decode_material for queries and outputs in
  * host memory (page-locked memory gives overlapped copies; pageable memory
  * works but serialises).  The n queries are processed in chunks through two
- * alternating buffers carved from the caller's device scratch; the upload of
+ * rotating buffers carved from the caller's device scratch; the upload of
  * the next chunk, the decode of the current one and the download of the
  * previous one run concurrently on three library streams, ordered after the
  * work already on `stream`, and `stream` waits for the last download, so the
  * call is asynchronous like the others (h_out is complete once `stream`
  * reaches that point).  Each chunk is a multiple of 256 queries: a chunk needs
- * 2 x (8 + 4 [with s] + C x out bytes) per query plus 1 KB of alignment, and
- * the chunk size is chosen so the call runs in at least about four chunks.
+ * 3 x (8 + 4 [with s] + C x out bytes) per query plus 1 KB per buffer of
+ * alignment; the chunk size is the largest the scratch allows, up to n / 4
+ * (a 128 MB scratch gives six chunks for a 3840 x 2160 frame of FP16
+ * outputs).
  * h_u, h_v, h_s (may be NULL when the material has no LOD input): n floats;
  * h_out: [n][C] in out_precision.  The three streams and eight events of
  * the pipeline belong to the material: the first call creates them (the

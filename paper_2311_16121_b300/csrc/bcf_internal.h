@@ -71,6 +71,11 @@ unsigned *check_word();
 #define BCF_MAX_SET 256 // materials per material set
 #endif
 
+// Buffers of bcf_decode_material_host's pipeline (each holds one chunk's queries and outputs).
+#ifndef BCF_PIPE_BUFS
+#define BCF_PIPE_BUFS 3
+#endif
+
 struct bcf_material_s {
     bcf::MaterialDev host;   // host copy (passed by value to single-material kernels)
     bcf::MaterialDev *dev;   // device copy (batched kernels)
@@ -83,6 +88,6 @@ struct bcf_material_s {
     // bcf_decode_material_host's pipeline: upload, decode and download streams and their events, created by
     // the first such call and released with the material
     cudaStream_t pipe_streams[3];
-    cudaEvent_t pipe_events[8];
+    cudaEvent_t pipe_events[2 + 3 * BCF_PIPE_BUFS];
     int pipe_ready;
 };
