@@ -251,8 +251,8 @@ typedef struct bcf_material_set_s *bcf_material_set;
  * (three layers, K0 <= 16 (FP8: 32) -> 32 -> 32 -> C <= 16, or
  * K0 <= 32 -> 64 -> 64 -> C <= 16), the set decodes through the texture unit
  * the same way (texture-unit texels, exact FP32 filter) with a persistent
- * kernel over 128-query tiles (bcf_autotune_material_set picks its CTAs per
- * SM and tiles per grab); otherwise it uses the library's own BC6H decode:
+ * kernel whose warps each take 32-query tiles (bcf_autotune_material_set
+ * picks its CTAs per SM and tiles per grab); otherwise it uses the library's own BC6H decode:
  * for the register-chained shapes, the tile kernel of bcf_decode_material
  * (tiles of 512 queries, 256 for 16-bit 64-wide MLPs; each material's
  * textures of one resolution and level count), else the multi-group tile
@@ -289,7 +289,8 @@ bcf_status bcf_decode_material_set(bcf_material_set set, const int64_t *d_offset
  * SM, capped by residency, *cap = 0 since its arena is fixed by its tile;
  * multi-group software sets: shared-memory block arena 256 / 320 blocks,
  * 1-3 CTAs per SM; texture-unit sets: 4 / 6 / 8 CTAs per SM, capped by
- * occupancy; all: 1 / 2 / 4 / 8 tiles per work-counter grab) on the given
+ * occupancy, and 8 / 16 / 32 / 64 warp tiles per grab; the others: 1 / 2 / 4 /
+ * 8 tiles per work-counter grab) on the given
  * workload with
  * CUDA events (synchronises the stream; the output is overwritten), keep the
  * fastest for the set, and return it in *cap, *ctas_per_sm, *chunk (any may

@@ -615,7 +615,7 @@ bcf_status bcf_create_material_set(const bcf_material *mats, int32_t n, bcf_mate
     for (int m = 0; m < n; ++m)
         set->single_geometry = set->single_geometry && mats[m]->host.n_groups == 1;
     if (set->texunit)
-        set->cfg = {320, 6, 8}; // the autotuner's pick on the 64-material benchmark workload
+        set->cfg = {320, 6, 32}; // the autotuner's pick on the 64-material benchmark workload
     else if (set->single_geometry)
         set->cfg = {0, 2, 2}; // the single-geometry kernel (arena fixed by its tile): two CTAs of 512 queries per SM
     MaterialDev *host = new (std::nothrow) MaterialDev[n];
@@ -728,13 +728,16 @@ bcf_status bcf_autotune_material_set(bcf_material_set set, const int64_t *d_offs
         SetConfig best_cfg = set->cfg;
         // the software set kernel: arena size x CTAs per SM x tiles per grab; the texture-unit set kernel
         // (128-query tiles): CTAs per SM x tiles per grab
-        const int caps[2] = {256, 320}, ctas_sw[3] = {1, 2, 3}, ctas_tex[3] = {4, 6, 8}, chunks[4] = {1, 2, 4, 8};
+        // tiles per grab: the texture-unit kernel's tiles are one warp's 32 queries
+        const int caps[2] = {256, 320}, ctas_sw[3] = {1, 2, 3}, ctas_tex[3] = {4, 6, 8}, chunks_sw[4] = {1, 2, 4, 8},
+                  chunks_tex[4] = {8, 16, 32, 64};
         const int ncap = set->texunit || set->single_geometry ? 1 : 2; // the tile kernel's arena is fixed
         for (int ic = 0; e == cudaSuccess && ic < ncap; ++ic)
             for (int ir = 0; e == cudaSuccess && ir < 3; ++ir)
                 for (int ik = 0; e == cudaSuccess && ik < 4; ++ik) {
                     const SetConfig cfg = {set->single_geometry && !set->texunit ? 0 : caps[ic],
-                                           set->texunit ? ctas_tex[ir] : ctas_sw[ir], chunks[ik]};
+                                           set->texunit ? ctas_tex[ir] : ctas_sw[ir],
+                                           set->texunit ? chunks_tex[ik] : chunks_sw[ik]};
                     float ms = 0.0f;
                     for (int rep = 0; e == cudaSuccess && rep < 3; ++rep) { // first run warms up
                         e = cudaEventRecord(a, cs);

@@ -364,11 +364,23 @@ __global__ void __launch_bounds__(128) k_decode_mma_tc(MaterialDev M, TexUnitObj
     }
 }
 
-// Material sets through the texture unit: a persistent CTA of 4 warps grabs 128-query tiles of a work list over
-// the materials (tiles never straddle two materials); when the material changes, its description, texture
-// objects and MLP weights replace the previous ones in shared memory; every warp then decodes its 32 queries as
-// variant 3 does (texture-unit texels, exact FP32 filter, register-chained tensor-core MLP).
+// Material sets through the texture unit: every warp of the persistent CTAs works on its own -- it takes
+// `chunk` consecutive 32-query tiles at a time from the work counter (tiles are numbered material by material
+// and never straddle two materials), keeps its own copy of its current material's MLP weights in shared memory
+// (reloaded by the warp alone when its tile belongs to a new material), reads the material's description and
+// texture objects from the device tables, and decodes its 32 queries as variant 3 does (texture-unit texels,
+// exact FP32 filter, register-chained tensor-core MLP).  No CTA barrier after the start: the warps run as
+// independently as in the single-material kernel.
 constexpr int kSetTexWarps = 4;
+
+// Shared bytes of one warp of k_decode_set_tex: its weights, biases and MLP operand rows.
+template <int PREC, int K0, int N1, int N2>
+__host__ __device__ inline int set_tex_warp_bytes(const MlpDev &P, int act_bytes)
+{
+    const int w = (mlp_smem_weight_bytes<PREC>(P) + 15) & ~15, bb = (mlp_smem_bias_floats(P) * 4 + 15) & ~15;
+    return w + bb + mma_per_warp_bytes(act_bytes, mma_act1_bytes<PREC, K0, N1, N2>(act_bytes), P.dims[P.n_layers], 0,
+                                       false);
+}
 
 template <int PREC, int K0, int N1, int N2, int NO>
 __global__ void __launch_bounds__(32 * kSetTexWarps) k_decode_set_tex(
@@ -377,22 +389,16 @@ __global__ void __launch_bounds__(32 * kSetTexWarps) k_decode_set_tex(
     const float *__restrict__ qs, int64_t n, void *__restrict__ out, int out_fp16, int *__restrict__ counter,
     unsigned *__restrict__ check, int act_bytes, int chunk)
 {
-    constexpr int kTile = 32 * kSetTexWarps;
+    constexpr int kTile = 32; // one warp's tile
     extern __shared__ __align__(16) unsigned char smem[];
-    __shared__ MaterialDev Ms;
-    __shared__ unsigned long long Tp[BCF_MAX_TEX];
     __shared__ int64_t tile_first[BCF_MAX_SET + 1];
-    __shared__ int grab;
     const MlpDev &P0 = mats[0].mlp; // every material shares the MLP shape (checked when the set is created)
-    const int wbytes = mlp_smem_weight_bytes<PREC>(P0);
-    unsigned char *sw = smem;
-    float *sb = (float *)(smem + wbytes);
-    unsigned char *wbase = smem + wbytes + ((mlp_smem_bias_floats(P0) * 4 + 15) & ~15);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int C = P0.dims[P0.n_layers];
+    unsigned char *sw = smem + warp * set_tex_warp_bytes<PREC, K0, N1, N2>(P0, act_bytes);
+    float *sb = (float *)(sw + ((mlp_smem_weight_bytes<PREC>(P0) + 15) & ~15));
+    unsigned char *act0 = (unsigned char *)sb + ((mlp_smem_bias_floats(P0) * 4 + 15) & ~15);
     const int act1_bytes = mma_act1_bytes<PREC, K0, N1, N2>(act_bytes);
-    const int per_warp = mma_per_warp_bytes(act_bytes, act1_bytes, C, 0, false);
-    unsigned char *act0 = wbase + warp * per_warp;
     unsigned char *act1 = act0 + act_bytes;
     float *ost = (float *)(act1 + act1_bytes);
     const int row_stride = tile_stride_bytes<PREC>(K0);
@@ -411,55 +417,49 @@ __global__ void __launch_bounds__(32 * kSetTexWarps) k_decode_set_tex(
     const int64_t total = tile_first[nmat];
     int cur = -1;
     for (;;) {
-        if (threadIdx.x == 0)
-            grab = atomicAdd(counter, chunk);
-        __syncthreads();
-        const int64_t base = grab;
-        __syncthreads(); // everyone has read `grab` before thread 0 may overwrite it
+        int64_t base = 0;
+        if (lane == 0)
+            base = atomicAdd(counter, chunk);
+        base = __shfl_sync(0xffffffffu, base, 0);
         if (base >= total)
-            break;
-      for (int64_t tile = base; tile < base + chunk && tile < total; ++tile) {
-        int lo = 0, hi = nmat - 1; // last m with tile_first[m] <= tile
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (tile_first[mid] <= tile)
-                lo = mid;
-            else
-                hi = mid - 1;
-        }
-        const int m = lo;
-        if (m != cur) {
-            __syncthreads(); // the previous tile's MLP may still read the weights being replaced
-            const int words = (int)(sizeof(MaterialDev) / 4);
-            for (int i = threadIdx.x; i < words; i += kTile)
-                reinterpret_cast<int *>(&Ms)[i] = reinterpret_cast<const int *>(mats + m)[i];
-            if (threadIdx.x < BCF_MAX_TEX)
-                Tp[threadIdx.x] = texs[m].texp[threadIdx.x];
-            __syncthreads();
-            load_mlp_smem<PREC>(Ms.mlp, sw, sb);
-            __syncthreads();
-            cur = m;
-        }
-        const int64_t a = min(max(offsets[m], (int64_t)0), n), b = min(max(offsets[m + 1], (int64_t)0), n);
-        const int64_t q0w = a + (tile - tile_first[m]) * kTile + warp * 32;
-        if (q0w < b) { // warp-uniform
+            break; // warp-uniform
+        for (int64_t tile = base; tile < base + chunk && tile < total; ++tile) {
+            int lo = 0, hi = nmat - 1; // last m with tile_first[m] <= tile
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (tile_first[mid] <= tile)
+                    lo = mid;
+                else
+                    hi = mid - 1;
+            }
+            const int m = lo;
+            const MaterialDev &M = mats[m];
+            if (m != cur) {
+                __syncwarp(); // the warp's previous MLP is done with the weights being replaced
+                load_mlp_smem<PREC>(M.mlp, sw, sb, lane, 32);
+                __syncwarp();
+                cur = m;
+            }
+            const int64_t a = min(max(offsets[m], (int64_t)0), n), b = min(max(offsets[m + 1], (int64_t)0), n);
+            const int64_t q0w = a + (tile - tile_first[m]) * kTile;
             const int64_t q = q0w + lane;
             const bool live = q < b;
-            const float inv0 = PREC == BCF_FP8_E4M3 ? Ms.mlp.inv_act_scale[0] : 1.0f;
+            const float inv0 = PREC == BCF_FP8_E4M3 ? M.mlp.inv_act_scale[0] : 1.0f;
+            const int wrap = M.wrap, nt = M.n_tex;
             RowWriter<PREC> rw{act0 + lane * row_stride, inv0, 0.0f};
             const float sq = live && qs ? qs[q] : 0.0f;
-            const float uu = sanitize(live ? qu[q] : 0.0f, Ms.wrap), vv = sanitize(live ? qv[q] : 0.0f, Ms.wrap);
+            const float uu = sanitize(live ? qu[q] : 0.0f, wrap), vv = sanitize(live ? qv[q] : 0.0f, wrap);
 #pragma unroll 1
-            for (int t = 0; t < Ms.n_tex; ++t) {
+            for (int t = 0; t < nt; ++t) {
                 float3 f = make_float3(0.0f, 0.0f, 0.0f);
                 if (live)
-                    f = sample_texture_hwpoint(Ms.tex[t], Tp[t], Ms.wrap, uu, vv, sq);
+                    f = sample_texture_hwpoint(M.tex[t], texs[m].texp[t], wrap, uu, vv, sq);
                 rw.put(3 * t, f.x);
                 rw.put(3 * t + 1, f.y);
                 rw.put(3 * t + 2, f.z);
             }
-            int col = 3 * Ms.n_tex;
-            if (Ms.lod_input)
+            int col = 3 * nt;
+            if (M.lod_input)
                 rw.put(col++, live ? (isnan(sq) ? 0.0f : fmaxf(sq, 0.0f)) : 0.0f);
             for (; col < K0; ++col)
                 rw.put(col, 0.0f);
@@ -468,13 +468,12 @@ __global__ void __launch_bounds__(32 * kSetTexWarps) k_decode_set_tex(
             if constexpr (N2 == 0)
                 warp_mlp2<PREC, K0, N1, NO>(sw, sb, act0, row_stride, ost, C);
             else
-                warp_mlp3<PREC, K0, N1, N2, NO>(Ms.mlp, sw, sb, act0, row_stride, act1,
-                                            tile_stride_bytes<BCF_FP8_E4M3>(N1 > N2 ? N1 : N2), ost, C);
+                warp_mlp3<PREC, K0, N1, N2, NO>(M.mlp, sw, sb, act0, row_stride, act1,
+                                                tile_stride_bytes<BCF_FP8_E4M3>(N1 > N2 ? N1 : N2), ost, C);
             __syncwarp();
             store_rows_any(ost, out, q0w, (int)min((int64_t)32, b - q0w), C, out_fp16, lane);
             __syncwarp();
         }
-      }
     }
 }
 
@@ -709,10 +708,7 @@ static cudaError_t launch_set_tex_shape(const MaterialDev &M0, const MaterialDev
 {
     const MlpDev &P = M0.mlp;
     const int act = mma_act_bytes<PREC>(P);
-    const int per_warp = mma_per_warp_bytes(act, mma_act1_bytes<PREC, K0, N1, N2>(act), P.dims[P.n_layers], 0,
-                                            false);
-    const int64_t smem = (int64_t)mlp_smem_weight_bytes<PREC>(P) + ((mlp_smem_bias_floats(P) * 4 + 15) & ~15) +
-                         (int64_t)kSetTexWarps * per_warp;
+    const int64_t smem = (int64_t)kSetTexWarps * set_tex_warp_bytes<PREC, K0, N1, N2>(P, act);
     if (smem > 160 * 1024)
         return cudaErrorInvalidConfiguration;
     auto kern = k_decode_set_tex<PREC, K0, N1, N2, NO>;

@@ -110,16 +110,17 @@ struct MlpSmem {
 };
 
 // Load the caller-layout weights into the padded shared tiles (zeros in the
-// padding).  Called by all threads of the CTA, followed by __syncthreads().
+// padding) by threads tid = 0 .. nthreads - 1 of a group (the CTA, followed by
+// __syncthreads(), or one warp, followed by __syncwarp()).
 template <int PREC>
-__device__ void load_mlp_smem(const MlpDev &P, unsigned char *sw, float *sb)
+__device__ void load_mlp_smem(const MlpDev &P, unsigned char *sw, float *sb, int tid, int nthreads)
 {
     int woff = 0, boff = 0;
     for (int l = 0; l < P.n_layers; ++l) {
         const int kin = P.dims[l], nout = P.dims[l + 1];
         const int kp = P.kpad[l], np = P.npad[l];
         const int stride = tile_stride_bytes<PREC>(kp);
-        for (int e = threadIdx.x; e < np * kp; e += blockDim.x) {
+        for (int e = tid; e < np * kp; e += nthreads) {
             const int n = e / kp, k = e % kp;
             unsigned char *dst = sw + woff + n * stride + k * Op<PREC>::kBytes;
             const bool in = n < nout && k < kin;
@@ -129,11 +130,18 @@ __device__ void load_mlp_smem(const MlpDev &P, unsigned char *sw, float *sb)
             else
                 *(uint16_t *)dst = in ? ((const uint16_t *)P.weights)[src] : 0;
         }
-        for (int e = threadIdx.x; e < np; e += blockDim.x)
+        for (int e = tid; e < np; e += nthreads)
             sb[boff + e] = e < nout ? P.biases[P.b_off[l] + e] : 0.0f;
         woff += np * stride;
         boff += np;
     }
+}
+
+// The whole CTA loads the weights and biases.
+template <int PREC>
+__device__ void load_mlp_smem(const MlpDev &P, unsigned char *sw, float *sb)
+{
+    load_mlp_smem<PREC>(P, sw, sb, threadIdx.x, blockDim.x);
 }
 
 template <int PREC>

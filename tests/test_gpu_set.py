@@ -79,8 +79,8 @@ def test_set_decode_in_a_cuda_graph_and_autotune(variant):
     cfg = S.autotune(off, u, v, s, torch.empty_like(ref))
     if variant == 0:  # the tile kernel of the single-material decode: its arena is fixed by the tile (cap 0)
         assert cfg[0] == 0 and 1 <= cfg[1] <= 3 and cfg[2] in (1, 2, 4, 8)
-    else:  # texture-unit set kernel: CTAs per SM and tiles per grab
-        assert cfg[1] in (4, 6, 8) and cfg[2] in (1, 2, 4, 8)
+    else:  # texture-unit set kernel: CTAs per SM and 32-query warp tiles per grab
+        assert cfg[1] in (4, 6, 8) and cfg[2] in (8, 16, 32, 64)
     assert S.config() == cfg
     out = torch.zeros_like(ref)
     stream = torch.cuda.Stream()
