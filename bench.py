@@ -324,6 +324,9 @@ def main():
     ap.add_argument("--only-batched", action="store_true",
                     help="time only the 64-material set, one graph-replayed launch on the hand-written decode (for "
                          "profiler captures); prints a reduced line")
+    ap.add_argument("--only-encode", action="store_true",
+                    help="time only the partition-selection encoder, 4 x 1024^2 with 9 levels (for profiler captures); "
+                         "prints a reduced line")
     ap.add_argument("--only-headline", action="store_true",
                     help="time only the headline decode (for profiler captures); prints a reduced line")
     args = ap.parse_args()
@@ -347,6 +350,31 @@ def main():
     assert args.warmup >= 3, "at least 3 warm-up steps"
 
     stream = torch.cuda.current_stream()
+    if args.only_encode:
+        enc_res, enc_levels = 1024, 9
+        n_texels = sum((enc_res >> l) ** 2 for l in range(enc_levels))
+        g = torch.Generator(device="cuda").manual_seed(5)
+        enc_tex = [torch.rand(n_texels * 3, device="cuda", generator=g) for _ in range(4)]
+        enc_out = [bcf.encode_mode10(t, enc_res, enc_levels) for t in enc_tex]
+        for _ in range(args.warmup - 1):
+            for t, (pp, pk, pe) in zip(enc_tex, enc_out):
+                bcf.encode_mode10(t, enc_res, enc_levels, pp, pk, pe)
+        torch.cuda.synchronize()
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record(stream)
+        for _ in range(args.steps):
+            for t, (pp, pk, pe) in zip(enc_tex, enc_out):
+                bcf.encode_mode10(t, enc_res, enc_levels, pp, pk, pe)
+        eb.record(stream)
+        eb.synchronize()
+        ms = ea.elapsed_time(eb) / args.steps
+        blocks = 4 * bcf.texture_blocks(enc_res, enc_levels)
+        if rank == 0:
+            print(json.dumps({"metric": "blocks/s", "value": blocks / (ms * 1e-3), "unit": "blocks/s", "n_gpus": world,
+                              "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+                              "note": "capture mode: the encoder only"}))
+        return
+
     if args.only_large or args.only_batched:
         flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
