@@ -531,6 +531,17 @@ def main():
     mats[HEADLINE_PRECISION].decode(u, v, s, out=out)
     tex_identical = bool(torch.equal(out, sw_out))
     del sw_out
+    # the same frame on the trained features' own format: every block in BC6H mode 10 (the two-region 6-bit mode
+    # of Sec. 4.2); the same seeds give the same queries and weights
+    w10 = workloads.screen_material(2, 4, 2048, [13, 32, 32, 9], 3840, 2160, modes=(10,))
+    assert np.array_equal(w10.u, w.u) and np.array_equal(w10.s, w.s)
+    m10 = workloads.upload(w10, HEADLINE_PRECISION)
+    m10.set_decode_variant(HEADLINE_VARIANT)
+    m10.set_mlp_engine(HEADLINE_ENGINE)
+    mode10_ms = timed(m10, k_extra, 3) / k_extra
+    m10.set_mlp_engine(OTHER_ENGINE[HEADLINE_ENGINE])
+    mode10_other_ms = timed(m10, k_extra, 3) / k_extra
+    del m10, w10
 
     # the texel-fetch roofline of the headline: the texture unit's point-fetch rate on the same material's
     # level-0 texels in screen-coherent order (bcf_texunit_fetch_probe), against the fetches one headline launch
@@ -952,6 +963,14 @@ def main():
                                 "fetches_per_launch": head_fetches,
                                 "peak_source": "bcf_texunit_fetch_probe: 2x2 point-fetch footprints of the same "
                                                "material's level-0 texels, screen-coherent, measured in this run"}},
+            "bcf_mode10_features": {
+                "value": w.n / (mode10_ms * 1e-3) / 1e9, "unit": "Gsamples/s", "ms_per_step": mode10_ms,
+                "precision": HEADLINE_PRECISION, "decode_variant": HEADLINE_VARIANT, "mlp_engine": HEADLINE_ENGINE,
+                "workload": "the headline frame and network with every block in BC6H mode 10 (value-bounded), "
+                            "the format trained BCf features are stored in",
+                "kernel": "the headline kernel (one mode: every sorted warp decodes one mode's header)",
+                "other_mlp_engine": {"engine": OTHER_ENGINE[HEADLINE_ENGINE], "ms_per_step": mode10_other_ms,
+                                     "value": w.n / (mode10_other_ms * 1e-3) / 1e9, "unit": "Gsamples/s"}},
             "texunit": {"value": w.n / (hw_ms * 1e-3) / 1e9, "unit": "Gsamples/s", "ms_per_step": hw_ms,
                         "precision": HEADLINE_PRECISION, "kernel": "decode variant 2: hardware trilinear filtering of "
                         "mipmapped BC6H texture objects + tensor-core MLP (per-lane)", **hw_stats},

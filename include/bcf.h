@@ -577,7 +577,8 @@ bcf_status bcf_pack_mode10(const float *d_params, const uint8_t *d_partitions, i
 /*
  * bcf_set_decode_variant -- choose the kernel bcf_decode_material uses for a
  * tensor-core (FP16 / BF16 / FP8) material.  0 (default): tile-cooperative
- * decode -- 256 screen-coherent queries share one decode of each BC6H block
+ * decode -- 512 screen-coherent queries (256 for textures of several
+ * resolutions, or a 64-wide 16-bit MLP) share one decode of each BC6H block
  * their footprints touch (blocks mode-sorted, texels staged in shared
  * memory); falls back per tile to 1 when the tile's blocks do not fit.
  * 1: per-lane decode -- every query decodes the blocks of its own
@@ -628,8 +629,8 @@ bcf_status bcf_material_refresh(bcf_material mat, bcf_stream stream);
  * level count (material sets keep the warp-level MMAs).
  * BCF_MLP_MMA_SYNC (default): every warp evaluates its 32 queries with
  * warp-level MMAs, layers chained through registers.
- * BCF_MLP_TCGEN05: the CTA's tile of queries (256 on variant 0, 128 on the
- * others) goes through the fifth-generation tensor cores -- one thread
+ * BCF_MLP_TCGEN05: the CTA's tile of queries (512 on variant 0, 256 there
+ * for the 64-wide 16-bit MLPs, 128 on the others) goes through the fifth-generation tensor cores -- one thread
  * issues 128-row MMAs per layer (FP16 / BF16
  * kind::f16, E4M3 kind::f8f6f4) from operand tiles in shared memory, FP32
  * accumulators in tensor memory, read back per row for the bias / ReLU /

@@ -290,6 +290,59 @@ def test_tiled_fallbacks_and_addressing_match_oracle(case):
     _quant_check(a.astype(np.float64), ref_q, TOL["fp16"], case, _oracle_material(w), P, w.u, w.v, w.s)
 
 
+def _split_mode_blocks(rng, w, signed=False):
+    """Per level, the block columns left of the middle hold mode-10 blocks (the two-region 6-bit format the
+    trained features are stored in, Sec. 4.2), the others blocks of any mode: tiles and warps whose blocks
+    all have one mode sit beside tiles and warps that mix modes."""
+    out = []
+    for b, res, levels in zip(w.blocks, w.res, w.levels):
+        one = synth.bounded_blocks(rng, b.shape[0], modes=(10,), signed=signed)
+        mixed = synth.bounded_blocks(rng, b.shape[0], signed=signed)
+        cols = np.concatenate([np.tile(np.arange(max((res >> l) // 4, 1)), max((res >> l) // 4, 1))
+                               for l in range(levels)])
+        wb = np.concatenate([np.full(max((res >> l) // 4, 1) ** 2, max((res >> l) // 4, 1)) for l in range(levels)])
+        out.append(np.where((cols < wb // 2)[:, None], one, mixed))
+    return out
+
+
+@pytest.mark.parametrize("case", ["mode10", "mode10_signed", "mode11", "split", "split_signed", "reserved"])
+@pytest.mark.parametrize("engine", ["mma_sync", "tcgen05"])
+def test_one_mode_textures_and_mixed_tiles(case, engine):
+    """The tile decode's mode sort at its extremes: textures of one mode (the trained features' mode 10, a
+    one-region mode, all-reserved blocks: one sort bin holds every block of a round) and textures in which
+    tiles of one mode sit beside tiles of all modes.  Against the per-lane decode (bit for bit) and the
+    oracle."""
+    _bcf()
+    w = workloads.small_screen(res=128, width=200, height=61)
+    rng = workloads.seed_rng(2, 98)
+    signed = case.endswith("signed")
+    w.is_signed = signed
+    if case.startswith("mode10"):
+        w.blocks = [synth.bounded_blocks(rng, b.shape[0], modes=(10,), signed=signed) for b in w.blocks]
+    elif case == "mode11":
+        w.blocks = [synth.bounded_blocks(rng, b.shape[0], modes=(11,)) for b in w.blocks]
+    elif case == "reserved":  # mode field 10011 (reserved): every texel decodes to zero
+        blocks = [synth.bounded_blocks(rng, b.shape[0]) for b in w.blocks]
+        for b in blocks:
+            b[:, 0] = (b[:, 0] & 0xE0) | 0x13
+        w.blocks = blocks
+    else:
+        w.blocks = _split_mode_blocks(rng, w, signed)
+    m = workloads.upload(w, "fp16")
+    u, v, s = workloads.queries_to_device(w)
+    m.set_mlp_engine(engine)
+    m.set_decode_variant(0)
+    a = m.decode(u, v, s).cpu().numpy()
+    m.set_decode_variant(1)
+    b = m.decode(u, v, s).cpu().numpy()
+    np.testing.assert_array_equal(a, b)
+    Wst, bias, _, _ = w.weights("fp16")
+    P = oracle.Mlp(w.dims, "fp16", Wst, bias)
+    mat = _oracle_material(w)
+    ref_q = oracle.decode(mat, P, w.u, w.v, w.s, quant_aware=True, threads=8)
+    _quant_check(a.astype(np.float64), ref_q, TOL["fp16"], case, mat, P, w.u, w.v, w.s)
+
+
 # --------------------------------------------------------------------------- texture-unit comparator (Sec. 5.2)
 
 @pytest.mark.parametrize("precision", ["fp16", "fp8"])
