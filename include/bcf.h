@@ -205,7 +205,7 @@ bcf_status bcf_decode_material(bcf_material mat, const float *d_u, const float *
 /*
  * bcf_decode_material_host -- bcf_decode_material for queries and outputs in
  * host memory (page-locked memory gives overlapped copies; pageable memory
- * works but serialises).  The n queries are processed in chunks through two
+ * works but serialises).  The n queries are processed in chunks through three
  * rotating buffers carved from the caller's device scratch; the upload of
  * the next chunk, the decode of the current one and the download of the
  * previous one run concurrently on three library streams, ordered after the
@@ -217,7 +217,7 @@ bcf_status bcf_decode_material(bcf_material mat, const float *d_u, const float *
  * (a 128 MB scratch gives six chunks for a 3840 x 2160 frame of FP16
  * outputs).
  * h_u, h_v, h_s (may be NULL when the material has no LOD input): n floats;
- * h_out: [n][C] in out_precision.  The three streams and eight events of
+ * h_out: [n][C] in out_precision.  The three streams and eleven events of
  * the pipeline belong to the material: the first call creates them (the
  * only allocation), bcf_destroy_material releases them.  Calls on one
  * material therefore must not overlap (issue them from one host thread, or

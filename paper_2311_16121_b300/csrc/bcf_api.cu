@@ -412,9 +412,9 @@ bcf_status bcf_decode_material(bcf_material m, const float *d_u, const float *d_
 // ------------------------------------------------------------ host-resident queries
 
 // The decode of queries and outputs that live in host memory, pipelined in chunks over three streams: the
-// upload of chunk i + 1, the decode of chunk i and the download of chunk i - 1 overlap.  Two chunk buffers
-// alternate in the caller's device scratch; per buffer an event marks when its download has finished so the
-// next upload into it may start.
+// upload of chunk i + 1, the decode of chunk i and the download of chunk i - 1 overlap.  BCF_PIPE_BUFS (three)
+// chunk buffers rotate in the caller's device scratch; per buffer an event marks when its download has
+// finished so the next upload into it may start.
 bcf_status bcf_decode_material_host(bcf_material m, const float *h_u, const float *h_v, const float *h_s, int64_t n,
                                     void *h_out, bcf_precision out_precision, void *d_scratch, int64_t scratch_bytes,
                                     bcf_stream stream)
