@@ -191,3 +191,43 @@ def test_set_decode_tiny_and_unaligned_ranges(engine):
         a, b = int(offs[m]), int(offs[m + 1])
         one = mats[m].decode(u[a:b], v[a:b], s[a:b], out_dtype=torch.float16).cpu().numpy()
         np.testing.assert_array_equal(got[a:b], one)
+
+
+@pytest.mark.parametrize("engine", ["mma_sync", "tcgen05"])
+@pytest.mark.parametrize("precision", ["fp16", "bf16"])
+def test_set_mixing_formats_and_addressing(precision, engine):
+    """One set whose materials differ in what the tile kernel reloads per material: signed (SF16) blocks,
+    clamp addressing, textures of one mode (the trained features' mode 10) and plain unsigned repeat-addressed
+    all-mode textures.  The launch equals the per-material decodes bit for bit, and every material's rows
+    match the oracle."""
+    from paper_2311_16121_b300 import synth
+
+    bcf = _bcf()
+    sw = workloads.config4(n_materials=4, q_range=(2000, 6000), res_choices=(64, 128), pool=1 << 14, config=47)
+    rng = workloads.seed_rng(47, 9)
+    w0, w1, w2, _ = sw.materials
+    w0.is_signed = True
+    w0.blocks = [synth.bounded_blocks(rng, b.shape[0], signed=True) for b in w0.blocks]
+    w1.wrap = False
+    w1.u = (w1.u * 1.3 - 0.15).astype(np.float32)
+    w2.blocks = [synth.bounded_blocks(rng, b.shape[0], modes=(10,)) for b in w2.blocks]
+    mats = [workloads.upload(m, precision) for m in sw.materials]
+    for m in mats:
+        m.set_decode_variant(0)
+        m.set_mlp_engine(engine)
+    S = bcf.MaterialSet(mats)
+    off, u, v, s = _set_inputs(sw)
+    got = S.decode(off, u, v, s, out_dtype=torch.float32).cpu().numpy()
+    tol = {"fp16": 1e-3, "bf16": 4e-3}[precision]
+    for m, w in enumerate(sw.materials):
+        a, b = int(sw.offsets[m]), int(sw.offsets[m + 1])
+        one = mats[m].decode(u[a:b], v[a:b], s[a:b], out_dtype=torch.float32).cpu().numpy()
+        np.testing.assert_array_equal(got[a:b], one)
+        Wst, bias, _, _ = w.weights(precision)
+        mat = oracle.Material(w.blocks, w.res, w.levels, w.res_ref, w.is_signed, w.wrap, w.lod_input)
+        P = oracle.Mlp(w.dims, precision, Wst, bias)
+        ref = oracle.decode(mat, P, w.u, w.v, w.s, quant_aware=True, threads=8)
+        r = oracle.check_outputs(got[a:b].astype(np.float64), ref, tol, False,
+                                 oracle.decode_explainer(mat, P, w.u, w.v, w.s, got[a:b].astype(np.float64), tol,
+                                                         False))
+        assert not r["unexplained"], (m, r["unexplained"][:5], r["worst"])
