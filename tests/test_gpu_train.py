@@ -452,6 +452,28 @@ def test_grid_batches_loss_and_step_match_oracle():
         tr.step(G * G + 1, seed, step)
 
 
+@pytest.mark.parametrize("s_const", [0.3, 1.6, 3.2])
+def test_grid_batch_gradients_match_oracle(s_const):
+    """Grid trainers (the paper's batch form, Sec. 5.1) sum the endpoint updates of neighbouring lanes that share
+    a block and region (a segmented warp scan) before their reductions; at a fine, a middle and a coarse scale
+    (few blocks, most lanes sharing them) their gradients match the oracle's element by element."""
+    _bcf()
+    w = workloads.train_workload(**MEDIUM)
+    G = 32
+    tr = workloads.upload_trainer(w, batch_grid=G)
+    u, v, _ = oracle.train_queries(4242, 3, G * G, float(w.target_levels - 1), grid=G)
+    s = np.full(G * G, s_const, np.float32)
+    go = np.random.default_rng(6).standard_normal((G * G, 9)).astype(np.float32) * 1e-2
+    tr.zero_grad()
+    tr.backward(*(torch.from_numpy(a).cuda() for a in (u, v, s)), torch.from_numpy(go).cuda())
+    F, P, _ = _oracle_parts(w)
+    gf, gW, gb = oracle.train_backward_given(F, P, u, v, s, go.astype(np.float64))
+    _grad_checks(F, P, u, v, s, go.astype(np.float64),
+                 [("W", tr.W_grad.cpu().numpy(), gW, "W"), ("b", tr.b_grad.cpu().numpy(), gb, "b")] +
+                 [(f"features{t}", workloads.params32_to_28(tr.grads[t].cpu().numpy()), gf[t], t)
+                  for t in range(len(gf))])
+
+
 def test_checkpoint_resume_reproduces_the_run():
     """state_dict / load_state_dict: training 6 steps straight equals training 3, checkpointing into a fresh
     trainer, and training 3 more (same draws, since they depend only on seed and step)."""
