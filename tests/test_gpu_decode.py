@@ -477,6 +477,30 @@ def test_host_memory_decode_equals_device_decode(n, scratch_kb):
         m.decode_host(uh, vh, sh, oh, scratch[:4096])  # too small for one 256-query chunk
 
 
+@pytest.mark.parametrize("out_dtype", [torch.float16, torch.float32])
+@pytest.mark.parametrize("lod_input", [True, False])
+def test_host_memory_decode_on_the_headline_kernel(out_dtype, lod_input):
+    """bcf_decode_material_host on the hand-written decode (variant 0), FP16 and FP32 channels, with the LOD
+    input and without it (the paper's 12-input decoder: no s array is passed or copied); several chunks, the
+    last one ragged.  Equal to the device-resident decode bit for bit."""
+    _bcf()
+    dims = (13, 32, 32, 9) if lod_input else (12, 32, 32, 9)
+    w = workloads.small_screen(res=128, width=200, height=61, dims=dims)
+    assert w.lod_input == lod_input
+    m = workloads.upload(w, "fp16")
+    m.set_decode_variant(0)
+    n = w.n
+    u, v, s = (torch.from_numpy(a[:n].copy()) for a in (w.u, w.v, w.s))
+    ref = m.decode(u.cuda(), v.cuda(), s.cuda() if lod_input else None, out_dtype=out_dtype)
+    uh, vh = u.pin_memory(), v.pin_memory()
+    sh = s.pin_memory() if lod_input else None
+    oh = torch.zeros((n, 9), dtype=out_dtype).pin_memory()
+    scratch = torch.empty(96 * 1024, dtype=torch.uint8, device="cuda")
+    m.decode_host(uh, vh, sh, oh, scratch)
+    torch.cuda.synchronize()
+    assert torch.equal(oh, ref.cpu())
+
+
 @pytest.mark.parametrize("precision", ["fp16", "bf16", "fp8"])
 def test_paper_decoder_shape_12_16_9(precision):
     """The paper's own decoder: 12 inputs (4 textures, no LOD input), one hidden layer of 16 (Sec. 5.1).  The
