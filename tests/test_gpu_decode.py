@@ -477,6 +477,34 @@ def test_host_memory_decode_equals_device_decode(n, scratch_kb):
         m.decode_host(uh, vh, sh, oh, scratch[:4096])  # too small for one 256-query chunk
 
 
+@pytest.mark.parametrize("variant,engine", [(0, "mma_sync"), (0, "tcgen05"), (3, "mma_sync")])
+def test_single_material_decode_replays_from_a_cuda_graph(variant, engine):
+    """bcf_decode_material makes no allocation and no synchronisation once a material has decoded once, so a
+    decode captured in a CUDA graph replays with new query values in the captured buffers and gives what a
+    direct decode of those values gives."""
+    _bcf()
+    w = workloads.small_screen(res=128, width=200, height=61)
+    m = workloads.upload(w, "fp16")
+    m.set_decode_variant(variant)
+    m.set_mlp_engine(engine)
+    u, v, s = workloads.queries_to_device(w)
+    out = torch.empty((w.n, 9), dtype=torch.float16, device="cuda")
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        m.decode(u, v, s, out=out)  # warm-up: first-use configuration happens outside the capture
+    torch.cuda.current_stream().wait_stream(side)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        m.decode(u, v, s, out=out)
+    for shift in (0.0, 0.37):
+        u.copy_(torch.from_numpy((w.u + np.float32(shift)) % np.float32(1.0)).cuda())
+        g.replay()
+        torch.cuda.synchronize()
+        ref = m.decode(u, v, s, out_dtype=torch.float16)
+        assert torch.equal(out, ref)
+
+
 @pytest.mark.parametrize("out_dtype", [torch.float16, torch.float32])
 @pytest.mark.parametrize("lod_input", [True, False])
 def test_host_memory_decode_on_the_headline_kernel(out_dtype, lod_input):
