@@ -391,8 +391,8 @@ def check_outputs(got: np.ndarray, ref_q: np.ndarray, tol: float, out_half: bool
     err = np.abs(got - ref_q)
     beyond = ~(err <= t)
     rows = np.nonzero(beyond.any(axis=1))[0]
-    verdict = explain(rows) if rows.size else []
-    unexplained = [int(r) for r, k in zip(rows, verdict) if k != 1]
+    kinds = explain(rows) if rows.size else []
+    unexplained = [int(r) for r, k in zip(rows, kinds) if k != 1]
     return {"outputs": int(got.size), "beyond_tol": int(beyond.sum()), "rows_beyond": int(rows.size),
             "flips": int(rows.size - len(unexplained)), "unexplained": unexplained,
             "worst": err.max(axis=0) if err.size else np.zeros(0)}
