@@ -329,6 +329,9 @@ def main():
                          "prints a reduced line")
     ap.add_argument("--only-headline", action="store_true",
                     help="time only the headline decode (for profiler captures); prints a reduced line")
+    ap.add_argument("--only-fp8", action="store_true",
+                    help="time only the headline frame in E4M3 on its engine (for profiler captures); prints a "
+                         "reduced line")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -464,6 +467,15 @@ def main():
         torch.cuda.synchronize()
         replicas.barrier()
         return total
+
+    if args.only_fp8:
+        fp8_only_ms = timed(mats["fp8"], args.steps, args.warmup) / args.steps
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": w.n / (fp8_only_ms * 1e-3) / 1e9, "unit": "Gsamples/s",
+                              "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+                              "ms_per_step": fp8_only_ms, "mlp_engine": FP8_ENGINE,
+                              "note": "capture mode: the headline frame in E4M3 only"}))
+        return
 
     # headline: low-precision path.  Its K steps last milliseconds, shorter than the sampler's 100 ms interval,
     # so the same decode runs back to back for 0.5 s first and the sampling window spans that load, the
