@@ -341,9 +341,7 @@ __global__ void __launch_bounds__(128) k_decode_mma_tc(MaterialDev M, TexUnitObj
         int col = 3 * M.n_tex;
         if (M.lod_input)
             tw.put(col++, live ? (isnan(sq) ? 0.0f : fmaxf(sq, 0.0f)) : 0.0f);
-        for (; col < K0; ++col)
-            tw.put(col, 0.0f);
-        tw.finish(col);
+        tw.finish(col); // pads the row to K0
         bool ok = tc_mlp3<PREC, 4, K0, N1, N2, NO>(P, sw, sb, x, y, (float *)y, C, bar, phase, tmem, 1 << 20);
         ok = __syncthreads_and(ok) != 0;
         if (!ok) {

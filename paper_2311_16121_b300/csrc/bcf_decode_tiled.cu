@@ -1352,12 +1352,13 @@ __global__ void __launch_bounds__(TQ, kGeoMinBlocks * 256 / TQ) k_decode_geo(Mat
                 put(col, active ? (isnan(s) ? 0.0f : fmaxf(s, 0.0f)) : 0.0f);
                 ++col;
             }
-            for (; col < P.kpad[0]; ++col)
-                put(col, 0.0f);
-            if constexpr (TC)
-                tw.finish(col);
-            else
+            if constexpr (TC) {
+                tw.finish(col); // pads the row to K0
+            } else {
+                for (; col < P.kpad[0]; ++col)
+                    put(col, 0.0f);
                 rw.finish(col);
+            }
         }
         // ---- 6. MLP on the tensor cores, coalesced store
         if constexpr (TC) {

@@ -211,25 +211,40 @@ struct TcRowWriter {
     unsigned char *a0;
     int r;
     float inv;
-    float pend;
+    float pend;        // 16-bit: the value of an even column waiting for its odd neighbour
+    uint32_t word = 0; // E4M3: the bytes of the current group of four columns
+    // columns in increasing order from 0; each group of two (16-bit) or four (E4M3) columns is one 4-byte store
     __device__ __forceinline__ void put(int col, float x)
     {
         using T = TcMlp<PREC, NW, K0, N1, N2, NO>;
         if constexpr (PREC == BCF_FP8_E4M3) {
-            a0[T::off(r, col, K0)] = (unsigned char)__nv_cvt_float_to_fp8(x * inv, __NV_SATFINITE, __NV_E4M3);
+            word |= (uint32_t)(unsigned char)__nv_cvt_float_to_fp8(x * inv, __NV_SATFINITE, __NV_E4M3)
+                    << (8 * (col & 3));
+            if ((col & 3) == 3) {
+                *reinterpret_cast<uint32_t *>(a0 + T::off(r, col - 3, K0)) = word;
+                word = 0u;
+            }
         } else if (col & 1) {
             *reinterpret_cast<uint32_t *>(a0 + T::off(r, col - 1, K0)) = Op<PREC>::pack2(pend, x);
         } else {
             pend = x;
         }
     }
+    // after the last column written: its partial group, then zeros up to the padded width K0
     __device__ __forceinline__ void finish(int ncols)
     {
         using T = TcMlp<PREC, NW, K0, N1, N2, NO>;
-        if constexpr (PREC != BCF_FP8_E4M3)
-            if (ncols & 1)
-                *reinterpret_cast<uint16_t *>(a0 + T::off(r, ncols - 1, K0)) =
-                    (uint16_t)Op<PREC>::pack2(pend, 0.0f);
+        constexpr int G = PREC == BCF_FP8_E4M3 ? 4 : 2; // columns per 4-byte store
+        int c = ncols & ~(G - 1);
+        if (ncols & (G - 1)) {
+            if constexpr (PREC == BCF_FP8_E4M3)
+                *reinterpret_cast<uint32_t *>(a0 + T::off(r, c, K0)) = word;
+            else
+                *reinterpret_cast<uint32_t *>(a0 + T::off(r, c, K0)) = Op<PREC>::pack2(pend, 0.0f);
+            c += G;
+        }
+        for (; c < K0; c += G)
+            *reinterpret_cast<uint32_t *>(a0 + T::off(r, c, K0)) = 0u;
     }
 };
 
